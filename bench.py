@@ -1,0 +1,395 @@
+"""Benchmark: trial-event-ELT evaluations per second of one ARA layer.
+
+Workload (the paper-shaped single layer): a YET of 1,000,000 trials with
+Poisson(1000) events drawn uniformly from a catalogue of 2,000,000 event ids,
+one layer over 15 ELTs of 10,000 records each (mean ~ LogNormal(10, 2),
+exposure = mean * U(2, 20), sigma = mean * U(0.1, 1.0) clipped so both Beta
+shapes stay >= 0.05), percentile-set layer terms, Philox seed 0, PML and TVaR
+at return periods 100 and 250.  Synthetic stand-in for the paper's
+proprietary industry YET/ELTs (Section 5).
+
+One step = the whole hot path: per-layer index build, the fused layer kernel
+(YET stream, lookup, Philox, inverse Beta, ELT terms, sum over ELTs,
+occurrence terms, FP64 running sum, aggregate terms, YLT), and PML/TVaR by
+radix select.  ``value`` is evals / second with the inputs resident in HBM
+(the 4 GB YET exceeds the 129 MB L2, so no L2 flush is needed); ``e2e`` is
+the same metric through the C ABI with the YET, the ELTs and the results in
+host memory, the copies inside the timed region.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm: there is
+no reference implementation to install, only the paper) on a bounded sample
+of the same workload.
+
+Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 under
+torchrun (one process per GPU, weak scaling: every rank runs its own
+1M-trial shard with its own seed; the exact global PML/TVaR comes from one
+all-gather of each rank's top m = ceil(N_total / RP) year losses).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "paper-1m"
+RETURN_PERIODS = (100.0, 250.0)
+METRIC = "trial-event-ELT evals/s (1M-trial ARA)"
+UNIT = "evals/s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _terms():
+    with open(os.path.join(ROOT, "tests", "golden", "workload_terms.json")) as fh:
+        return json.load(fh)[WORKLOAD]["layer_terms"]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1501_06326_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the layer kernel from the committed ncu summary,
+    if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_layer_paper-1m.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"source hash:\s*`?([0-9a-f]{16})", text)
+    m_bytes = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != _kernel_source_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5], parts[6], parts[7], parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        for r in rows:
+            for name, flag in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[2:]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _algorithmic_bytes(offsets_span: int, n_events: int, n_trials: int, n_records: int) -> int:
+    """Bytes the method must move per layer: YET ids (4 B / occurrence), trial
+    offsets (8 B / trial), each record of the layer once (16 B: mean, sigma,
+    exposure, event id), and the YLT (8 B / trial)."""
+    return 4 * n_events + 8 * (n_trials + 1) + 16 * n_records + 8 * n_trials
+
+
+# ------------------------------------------------------------------ CPU legs (oracle)
+def _oracle_leg(yet, pool, terms, seed, sample_trials: int):
+    import oracle
+
+    trials = np.arange(sample_trials, dtype=np.int64)
+    evals = int(yet.offsets[sample_trials] - yet.offsets[0]) * pool.n_elts
+    t = time.perf_counter()
+    oracle.run_layer(yet, pool, terms, seed=seed, trials=trials)
+    dt = time.perf_counter() - t
+    return evals / dt, dt, evals
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1501_06326_gb300 import synth
+
+    n_sample = args.ref_trials
+    yet, pool, spec = synth.workload(WORKLOAD, n_trials=n_sample)
+    terms = _terms()
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        _oracle_leg(yet, pool, terms, 0, min(n_sample, 200))
+    times, evals = [], 0
+    for _ in range(args.steps):
+        v, dt, evals = _oracle_leg(yet, pool, terms, 0, n_sample)
+        times.append(dt)
+    value = evals / float(np.mean(times))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD} (sample: first {n_sample} trials per step)", "trials": n_sample,
+                   "elts": pool.n_elts, "return_periods": list(RETURN_PERIODS)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {n_sample} trials of the 1M-trial YET, all 15 ELTs"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+
+    from paper_1501_06326_gb300 import ara, build, synth
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+
+    spec = dict(synth.WORKLOADS[WORKLOAD])
+    n_trials = spec["n_trials"]
+    seed = 0 + rank  # weak scaling: each rank its own shard / stream
+    yet_seed = spec["seed"] + 1000 * rank
+    offsets = synth.yet_offsets(n_trials, spec["mean_events"], yet_seed)
+    n_events = int(offsets[-1])
+    # generate the ids straight into pinned host memory (also the e2e source buffer)
+    ids_host = torch.empty(n_events, dtype=torch.int32, pin_memory=True)
+    synth.fill_yet_ids(ids_host.numpy(), spec["catalogue"], yet_seed)
+    offsets_host = torch.from_numpy(offsets).pin_memory()
+    pool = synth.make_elt_pool(spec["n_elts"], spec["entries"], spec["catalogue"], spec["seed"], recipe=spec["recipe"])
+    terms = _terms()
+    n_recs = int(pool.rec_offsets[-1])
+    evals_per_step = n_events * pool.n_elts
+
+    stream = torch.cuda.current_stream(dev)
+    eng = ara.Ara(local, 0, stream.cuda_stream)
+    eng.load_yet(offsets_host, ids_host, spec["catalogue"])
+    eng.load_pool(pool)
+    ylt = torch.empty(n_trials, dtype=torch.float64, device=dev)
+    rps = np.array(RETURN_PERIODS)
+    pml = torch.empty(len(rps), dtype=torch.float64, device=dev)
+    tvar = torch.empty(len(rps), dtype=torch.float64, device=dev)
+
+    def step():
+        eng.run_layer(pool.elt_ids, terms, seed, 0, n_trials, ylt)
+        eng.pml_tvar(ylt, rps, pml, tvar)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    eng.timing(reset=True)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        start.record(stream)
+        for _ in range(args.steps):
+            step()
+        end.record(stream)
+        barrier()
+    ms = start.elapsed_time(end) / args.steps
+    tm = eng.timing(reset=True)
+    st = eng.stats()
+    ms_max = ms
+    if ws > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = ws * evals_per_step / (ms_max * 1e-3)
+
+    # ---- global PML/TVaR across ranks: all-gather of each rank's top m year losses
+    global_pml = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        from paper_1501_06326_gb300.shard import global_pml_tvar, local_top
+
+        total = ws * n_trials
+        m_max = int(math.ceil(total / min(RETURN_PERIODS)))
+        top = torch.from_numpy(local_top(ylt.cpu().numpy(), m_max)).to(dev)
+        gathered = [torch.empty_like(top) for _ in range(ws)]
+        dist.all_gather(gathered, top)
+        global_pml = global_pml_tvar([g.cpu().numpy() for g in gathered], total, RETURN_PERIODS)
+
+    # ---- roofline of the dominant kernel (the fused layer kernel)
+    kernel_ms = tm["kernel_ms"] / max(tm["layer_calls"], 1)
+    algo = _algorithmic_bytes(n_events, n_events, n_trials, n_recs)
+    peak, peak_kind = _peaks()
+    achieved = algo / (kernel_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": _profiled_traffic(), "kernel": "k_layer", "kernel_ms": kernel_ms,
+                "algorithmic_bytes": algo, "peak_source": f"hbm_gbs of {peak_kind}"}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        ylt_host = torch.empty(n_trials, dtype=torch.float64, pin_memory=True)
+        pml_h, tvar_h = np.zeros(len(rps)), np.zeros(len(rps))
+        terms_arr = pool.terms
+
+        def e2e_step():
+            eng.load_yet(offsets_host, ids_host, spec["catalogue"])
+            eng.load_elts(pool.elt_ids, pool.rec_offsets, pool.event_ids, pool.mean, pool.sigma, pool.exposure,
+                          terms_arr)
+            eng.run_layer(pool.elt_ids, terms, seed, 0, n_trials, ylt_host)
+            eng.pml_tvar(ylt_host, rps, pml_h, tvar_h)
+
+        e2e_step()
+        barrier()
+        n_e2e = max(2, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            e2e_step()
+        barrier()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
+        if ws > 1:
+            import torch.distributed as dist
+
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        pool_bytes = (pool.elt_ids.nbytes + pool.rec_offsets.nbytes + pool.event_ids.nbytes + pool.mean.nbytes
+                      + pool.sigma.nbytes + pool.exposure.nbytes + pool.terms.nbytes)
+        h2d = offsets.nbytes + 4 * n_events + pool_bytes + 8 * n_trials  # ylt host -> device staging for PML
+        d2h = 8 * n_trials + 16 * len(rps)
+        e2e = {"value": ws * evals_per_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        yet_view = synth.YET(offsets=offsets, event_ids=ids_host.numpy(), catalogue_size=spec["catalogue"])
+        v, dt, ev = _oracle_leg(yet_view, pool, terms, seed, args.cpu_trials)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+               "sample": f"first {args.cpu_trials} trials of the workload ({ev} evals, {dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: 1,000,000 trials x Poisson(1000) events, catalogue 2,000,000, "
+                                   "one layer of 15 ELTs x 10,000 records, percentile terms, RP 100/250",
+                       "trials": n_trials, "events": n_events, "elts": pool.n_elts,
+                       "evals_per_step": evals_per_step, "l2": "inputs (4 GB YET) larger than L2; no flush",
+                       "accumulation": "FP32 loss arithmetic, FP64 per-trial running sum",
+                       "parallelism": f"trial shards x{ws}"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": tm["kernel_launches"] // max(args.steps, 1),
+            "clocks": clocks.summary(),
+            "stats": {"index_ms": tm["index_ms"] / max(tm["layer_calls"], 1),
+                      "pml_ms": tm["pml_ms"] / max(tm["pml_calls"], 1), "pairs_hit": st["n_pairs_hit"],
+                      "nonconverged": st["n_nonconverged"], "grid": st["grid"], "block": st["block"],
+                      "smem_bytes": st["smem_bytes"], "filter_bits": st["filter_bits"]},
+        }
+        if global_pml is not None:
+            line["global_pml_tvar"] = {"pml": list(global_pml[0]), "tvar": list(global_pml[1])}
+        print(json.dumps(line))
+    eng.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    ap.add_argument("--cpu-trials", type=int, default=20000, help="trials in the oracle's CPU-baseline sample")
+    ap.add_argument("--ref-trials", type=int, default=20000, help="trials per step of the reference arm")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

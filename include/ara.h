@@ -1,0 +1,226 @@
+/*
+ * ara.h -- C ABI of the GB300 (sm_103a) Aggregate Risk Analysis engine.
+ *
+ * The engine runs the data-parallel hot path of Aggregate Risk Analysis (ARA)
+ * with secondary uncertainty (B. Varghese, "The GPU vs Phi Debate: Risk
+ * Analytics Using Many-Core Computing"): for each trial of a Year Event Table
+ * (YET), for each event in time order, for each Event Loss Table (ELT) of a
+ * layer, look up the event's loss record, draw a loss from the record's Beta
+ * distribution (Section 3.4), apply the ELT financial terms, sum over the
+ * layer's ELTs, apply the occurrence terms, and apply the aggregate terms to
+ * the running sum of occurrence losses (Algorithm 1, Section 2.2).  The result
+ * is the Year Loss Table (YLT), from which PML and TVaR are read (Section 2.3).
+ *
+ * Conventions for every entry point:
+ *   - Return value: ARA_OK (0) on success, a negative ARA_E* code on failure.
+ *     On failure ara_last_error() describes the cause.  No entry point aborts,
+ *     traps on the device or throws across this boundary.
+ *   - Pointers: input arrays may be host or device memory (the kind is
+ *     detected per pointer).  Inputs are read during the call only; the
+ *     library copies what it keeps into device memory that it owns and frees
+ *     in ara_destroy().  Output arrays are owned by the caller and may be host
+ *     or device memory.
+ *   - Ordering: all device work is issued on the context's CUDA stream.  A call
+ *     whose outputs are all device memory returns without synchronising; a
+ *     call with a host output synchronises the stream before returning.
+ *   - Threading: a context is used by one host thread at a time.
+ *   - Device: a context binds one CUDA device (chosen at ara_create) and makes
+ *     it current on every call.
+ */
+#ifndef ARA_H
+#define ARA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ARA_API __attribute__((visibility("default")))
+#else
+#define ARA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define ARA_OK 0
+#define ARA_EINVAL (-1)     /* invalid argument or input data */
+#define ARA_ENOMEM (-2)     /* device allocation failed or over the HBM budget */
+#define ARA_ENOTLOADED (-3) /* the YET or a referenced ELT is not loaded */
+#define ARA_ECUDA (-4)      /* a CUDA runtime call failed */
+#define ARA_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+
+/* Largest number of ELTs in one layer.  The paper's layers cover 3 to 30
+ * ELTs (Section 2.1 (iii)). */
+#define ARA_MAX_LAYER_ELTS 32
+
+/* Relative gap below sigma_bmax used when sigma_b is clipped: the paper
+ * clips sigma_b to "a value very close to sigma_bmax" (Section 3.4); this
+ * library uses (1 - ARA_SIGMA_CLIP) * sigma_bmax whenever
+ * sigma_b >= (1 - ARA_SIGMA_CLIP) * sigma_bmax. */
+#define ARA_SIGMA_CLIP 1e-6
+
+/* Layer flags */
+#define ARA_PRIMARY_ONLY 1u /* no secondary uncertainty: every record's loss is its mean */
+
+typedef struct ara_ctx ara_ctx;
+
+/* Per-ELT financial terms I (Section 2.1 (ii)), read as retention R, limit L
+ * and share s: l' = s * min(max(l - R, 0), L).  Identity: {0, +INF, 1}. */
+typedef struct {
+    float retention;
+    float limit;
+    float share;
+} ara_elt_terms;
+
+/* A layer (Section 2.1 (iii)): a set of ELTs from the resident pool and the
+ * layer terms T = (OccR, OccL, AggR, AggL).  Occurrence terms apply to the
+ * event loss combined over the layer's ELTs, l = min(max(l - OccR, 0), OccL);
+ * aggregate terms to the running sum S of occurrence losses,
+ * l = min(max(S - AggR, 0), AggL) (Section 2.2).  Retentions are >= 0, limits
+ * > 0 and may be +INF. */
+typedef struct {
+    int32_t n_elts;         /* 1 .. ARA_MAX_LAYER_ELTS */
+    const int32_t *elt_ids; /* host array of n_elts distinct pool ids */
+    double occ_retention;
+    double occ_limit;
+    double agg_retention;
+    double agg_limit;
+    uint32_t flags; /* ARA_PRIMARY_ONLY or 0 */
+} ara_layer;
+
+/* Optional per-trial diagnostics of ara_run_layer_diag(); any pointer may be
+ * NULL.  Arrays have trial_end - trial_begin entries, host or device. */
+typedef struct {
+    int64_t *hits;      /* number of (event, ELT) lookups that found a record */
+    uint64_t *hit_hash; /* sum over hits of fmix64((k << 32) | elt_id), k = event index in the trial */
+} ara_diag;
+
+/* Counters of the last ara_run_layer* call (read back with ara_get_stats). */
+typedef struct {
+    int64_t n_events;        /* YET entries scanned */
+    int64_t n_evals;         /* n_events x n_elts: trial-event-ELT evaluations */
+    int64_t n_pairs_hit;     /* (event, ELT) lookups that found a record */
+    int64_t n_nonconverged;  /* Beta inversions that hit the iteration cap */
+    float index_ms;          /* per-layer index build, device time */
+    float kernel_ms;         /* main layer kernel, device time */
+    int32_t grid;            /* CTAs of the main kernel */
+    int32_t block;           /* threads per CTA */
+    int32_t smem_bytes;      /* dynamic shared memory per CTA */
+    int32_t filter_bits;     /* shared-memory membership filter size in bits */
+} ara_stats;
+
+/* Device time accumulated over the ara_run_layer* and ara_pml_tvar calls
+ * since the last reset (CUDA events recorded on the context's stream around
+ * each launch group). */
+typedef struct {
+    int64_t layer_calls;     /* ara_run_layer* calls */
+    double kernel_ms;        /* sum of the main layer kernel's durations */
+    double index_ms;         /* sum of the per-layer index builds */
+    int64_t pml_calls;       /* ara_pml_tvar calls */
+    double pml_ms;           /* sum of the PML/TVaR selections */
+    int64_t kernel_launches; /* kernels this library launched (all calls) */
+} ara_timing;
+
+/* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the
+ * device memory the library allocates (0: no cap).  `cuda_stream` is a
+ * cudaStream_t to issue work on (NULL: the legacy default stream).
+ * Errors: ARA_EINVAL (bad device), ARA_ECUDA. */
+ARA_API int ara_create(ara_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream);
+
+/* Switch the stream used by later calls.  Synchronises the previous stream. */
+ARA_API int ara_set_stream(ara_ctx *ctx, void *cuda_stream);
+
+/* Load (replace) the Year Event Table (Section 2.1 (i)).  Trial t owns
+ * event_ids[offsets[t] .. offsets[t+1]), in time order.  offsets has
+ * n_trials + 1 entries, offsets[0] == 0 and non-decreasing; every id lies in
+ * [0, catalogue_size).  Time stamps are not needed: they only fix the order.
+ * Errors: ARA_EINVAL (bad sizes, offsets or ids), ARA_ENOMEM, ARA_ECUDA. */
+ARA_API int ara_load_yet(ara_ctx *ctx, int64_t n_trials, const int64_t *offsets, const int32_t *event_ids,
+                 int32_t catalogue_size);
+
+/* Load ELTs into the resident pool (Sections 2.1 (ii), 3.1): ELT i has pool id
+ * elt_ids[i] (>= 0) and records rec_offsets[i] .. rec_offsets[i+1] of
+ * (event_ids, mean, sigma, exposure), with strictly increasing event ids.
+ * `exposure` is the maximum loss max_l; a record with mean > 0 and sigma > 0
+ * needs exposure > mean.  mean == 0 gives no loss; sigma == 0 gives the mean
+ * (no secondary uncertainty).  `terms` (n_elts entries, NULL: identity) are
+ * the ELT financial terms.  Loading a pool id that is already resident
+ * replaces it.  The Beta shapes of every record are derived here (Section
+ * 3.4), once per record.
+ * Errors: ARA_EINVAL (unsorted or duplicate ids, negative or non-finite
+ * values, exposure <= mean), ARA_ENOMEM, ARA_ECUDA. */
+ARA_API int ara_load_elts(ara_ctx *ctx, int32_t n_elts, const int32_t *elt_ids, const int64_t *rec_offsets,
+                  const int32_t *event_ids, const float *mean, const float *sigma,
+                  const float *exposure, const ara_elt_terms *terms);
+
+/* Run one layer over trials [trial_begin, trial_end) (Algorithm 1 with the
+ * secondary uncertainty of Section 3.4) and write one year loss per trial to
+ * ylt_out (FP64, trial_end - trial_begin entries).  The uniform of trial t,
+ * event index k (position in the trial, from 0) and ELT pool id j is word 0
+ * of Philox4x32-10 with counter (t mod 2^32, k, j, t >> 32) and key
+ * (seed mod 2^32, seed >> 32), mapped to ((w >> 9) + 0.5) * 2^-23.
+ * The loss arithmetic is FP32; each trial's running sum of occurrence losses
+ * is FP64.  Event ids outside the catalogue were rejected at load.
+ * Errors: ARA_EINVAL (bad layer or range), ARA_ENOTLOADED, ARA_ENOMEM,
+ * ARA_ECUDA. */
+ARA_API int ara_run_layer(ara_ctx *ctx, const ara_layer *layer, uint64_t seed, int64_t trial_begin,
+                  int64_t trial_end, double *ylt_out);
+
+/* ara_run_layer plus the per-trial diagnostics of ara_diag (hit counts and
+ * an order-free hash of the hit list), used to check event indexing. */
+ARA_API int ara_run_layer_diag(ara_ctx *ctx, const ara_layer *layer, uint64_t seed, int64_t trial_begin,
+                       int64_t trial_end, double *ylt_out, const ara_diag *diag);
+
+/* PML and TVaR of a YLT (Section 2.3) at n_rp return periods (each >= 1):
+ * with m = ceil(n / RP), PML is the m-th largest year loss and TVaR the mean
+ * of the m largest (FP64).  Computed on the device by a radix select over
+ * order-preserving 64-bit keys.  ylt may be host or device memory; pml_out
+ * and tvar_out have n_rp entries.
+ * Errors: ARA_EINVAL (n < 1, RP < 1), ARA_ENOMEM, ARA_ECUDA. */
+ARA_API int ara_pml_tvar(ara_ctx *ctx, const double *ylt, int64_t n, const double *return_periods,
+                 int32_t n_rp, double *pml_out, double *tvar_out);
+
+/* Trial order of a YLT, largest year loss first, ties by ascending trial
+ * index, by an on-device LSD radix sort of 64-bit keys.  order_out has n
+ * entries (host or device).  Errors: ARA_EINVAL, ARA_ENOMEM, ARA_ECUDA. */
+ARA_API int ara_sort_ylt(ara_ctx *ctx, const double *ylt, int64_t n, int64_t *order_out);
+
+/* Check entry points: the hot path's own device functions on caller-chosen
+ * inputs, for parity tests against an independent implementation.
+ *
+ * ara_debug_uniforms: out[i] = the uniform of (trials[i], ks[i], elts[i])
+ * under `seed`, exactly as ara_run_layer draws it (FP32 values; n entries).
+ *
+ * ara_debug_record_losses: for n XELT records (mean, sigma, exposure) and
+ * uniforms z (FP32, in (0, 1)), out[i] = the secondary-uncertainty loss
+ * max_l * InvCDF_beta(z[i]; alpha_i, beta_i) (Section 3.4) computed with the
+ * same record preparation and FP32 inverse as ara_run_layer (the mean for
+ * sigma == 0, 0 for mean == 0).  iters_out (NULL allowed) receives the
+ * iteration count of each inversion (negative: hit the iteration cap).
+ * All arrays may be host or device memory.  Errors: ARA_EINVAL, ARA_ENOMEM,
+ * ARA_ECUDA. */
+ARA_API int ara_debug_uniforms(ara_ctx *ctx, uint64_t seed, int64_t n, const int64_t *trials, const int32_t *ks,
+                               const int32_t *elts, float *out);
+ARA_API int ara_debug_record_losses(ara_ctx *ctx, int64_t n, const float *mean, const float *sigma,
+                                    const float *exposure, const float *z, float *out, int32_t *iters_out);
+
+/* Counters of the last ara_run_layer* call. */
+ARA_API int ara_get_stats(const ara_ctx *ctx, ara_stats *out);
+
+/* Accumulated device times since the last reset; waits for the recorded
+ * events.  reset != 0 clears the accumulators after reading. */
+ARA_API int ara_get_timing(ara_ctx *ctx, ara_timing *out, int reset);
+
+/* Message of the last failed call on this context (never NULL). */
+ARA_API const char *ara_last_error(const ara_ctx *ctx);
+
+/* Release every device buffer and the context.  NULL is ignored. */
+ARA_API void ara_destroy(ara_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARA_H */

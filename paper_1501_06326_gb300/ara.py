@@ -1,0 +1,340 @@
+"""Python binding of the ``libara`` C ABI (``include/ara.h``).
+
+Argument marshalling only: every step of the ARA hot path runs in the CUDA
+kernels of ``libara.so``.  The module-level functions mirror the C entry
+points one to one (``ara_create``, ``ara_load_yet``, ``ara_load_elts``,
+``ara_run_layer``, ``ara_run_layer_diag``, ``ara_pml_tvar``, ``ara_sort_ylt``,
+``ara_get_stats``, ``ara_last_error``, ``ara_destroy``); ``Ara`` wraps them
+with error checking.  Arrays may be numpy arrays (host memory) or torch
+tensors (host, pinned or CUDA): only their data pointers cross the boundary.
+
+There is no fallback: if ``libara.so`` cannot be loaded (not built, or no
+CUDA driver) every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libara.so")
+
+ARA_OK, ARA_EINVAL, ARA_ENOMEM, ARA_ENOTLOADED, ARA_ECUDA, ARA_ETIMEOUT = 0, -1, -2, -3, -4, -5
+ARA_PRIMARY_ONLY = 1
+ARA_MAX_LAYER_ELTS = 32
+_ERR_NAMES = {
+    ARA_EINVAL: "ARA_EINVAL", ARA_ENOMEM: "ARA_ENOMEM", ARA_ENOTLOADED: "ARA_ENOTLOADED",
+    ARA_ECUDA: "ARA_ECUDA", ARA_ETIMEOUT: "ARA_ETIMEOUT",
+}
+
+# Every function the header declares (checked by the tests against the .so).
+EXPORTED = (
+    "ara_create", "ara_set_stream", "ara_load_yet", "ara_load_elts", "ara_run_layer",
+    "ara_run_layer_diag", "ara_pml_tvar", "ara_sort_ylt", "ara_debug_uniforms",
+    "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
+)
+
+
+class AraError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{_ERR_NAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+class EltTerms(ctypes.Structure):
+    _fields_ = [("retention", ctypes.c_float), ("limit", ctypes.c_float), ("share", ctypes.c_float)]
+
+
+class Layer(ctypes.Structure):
+    _fields_ = [
+        ("n_elts", ctypes.c_int32),
+        ("elt_ids", ctypes.POINTER(ctypes.c_int32)),
+        ("occ_retention", ctypes.c_double),
+        ("occ_limit", ctypes.c_double),
+        ("agg_retention", ctypes.c_double),
+        ("agg_limit", ctypes.c_double),
+        ("flags", ctypes.c_uint32),
+    ]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("hits", ctypes.c_void_p), ("hit_hash", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("n_events", ctypes.c_int64),
+        ("n_evals", ctypes.c_int64),
+        ("n_pairs_hit", ctypes.c_int64),
+        ("n_nonconverged", ctypes.c_int64),
+        ("index_ms", ctypes.c_float),
+        ("kernel_ms", ctypes.c_float),
+        ("grid", ctypes.c_int32),
+        ("block", ctypes.c_int32),
+        ("smem_bytes", ctypes.c_int32),
+        ("filter_bits", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [
+        ("layer_calls", ctypes.c_int64),
+        ("kernel_ms", ctypes.c_double),
+        ("index_ms", ctypes.c_double),
+        ("pml_calls", ctypes.c_int64),
+        ("pml_ms", ctypes.c_double),
+        ("kernel_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load ``libara.so`` and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: build it with paper_1501_06326_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    lib.ara_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t, P]
+    lib.ara_set_stream.argtypes = [P, P]
+    lib.ara_load_yet.argtypes = [P, i64, P, P, i32]
+    lib.ara_load_elts.argtypes = [P, i32, P, P, P, P, P, P, P]
+    lib.ara_run_layer.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P]
+    lib.ara_run_layer_diag.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P, ctypes.POINTER(Diag)]
+    lib.ara_pml_tvar.argtypes = [P, P, i64, P, i32, P, P]
+    lib.ara_sort_ylt.argtypes = [P, P, i64, P]
+    lib.ara_debug_uniforms.argtypes = [P, u64, i64, P, P, P, P]
+    lib.ara_debug_record_losses.argtypes = [P, i64, P, P, P, P, P, P]
+    lib.ara_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.ara_get_timing.argtypes = [P, ctypes.POINTER(Timing), ctypes.c_int]
+    lib.ara_last_error.argtypes = [P]
+    lib.ara_last_error.restype = ctypes.c_char_p
+    lib.ara_destroy.argtypes = [P]
+    lib.ara_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("ara_last_error", "ara_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------ marshalling
+def _ptr(a, dtype=None) -> Optional[int]:
+    """Data pointer of a numpy array or torch tensor (C-contiguous, exact dtype)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if dtype is not None and a.dtype != np.dtype(dtype):
+            raise TypeError(f"expected dtype {np.dtype(dtype)}, got {a.dtype}")
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if dtype is not None:
+            import torch
+
+            want = {np.int32: torch.int32, np.int64: torch.int64, np.float32: torch.float32,
+                    np.float64: torch.float64, np.uint64: torch.uint64}[np.dtype(dtype).type]
+            if a.dtype != want:
+                raise TypeError(f"expected dtype {want}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _len(a) -> int:
+    return int(a.shape[0])
+
+
+# ------------------------------------------------------------------ C ABI mirror
+def ara_create(device: int = 0, hbm_budget_bytes: int = 0, cuda_stream: int = 0):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    rc = lib.ara_create(ctypes.byref(h), int(device), int(hbm_budget_bytes), ctypes.c_void_p(cuda_stream or None))
+    return rc, h
+
+
+def ara_set_stream(h, cuda_stream: int):
+    return load_library().ara_set_stream(h, ctypes.c_void_p(cuda_stream or None))
+
+
+def ara_load_yet(h, n_trials, offsets, event_ids, catalogue_size):
+    return load_library().ara_load_yet(h, int(n_trials), _ptr(offsets, np.int64), _ptr(event_ids, np.int32),
+                                       int(catalogue_size))
+
+
+def ara_load_elts(h, n_elts, elt_ids, rec_offsets, event_ids, mean, sigma, exposure, terms=None):
+    return load_library().ara_load_elts(
+        h, int(n_elts), _ptr(elt_ids, np.int32), _ptr(rec_offsets, np.int64), _ptr(event_ids, np.int32),
+        _ptr(mean, np.float32), _ptr(sigma, np.float32), _ptr(exposure, np.float32), _ptr(terms, np.float32),
+    )
+
+
+def ara_run_layer(h, layer: Layer, seed, trial_begin, trial_end, ylt_out):
+    return load_library().ara_run_layer(h, ctypes.byref(layer), int(seed), int(trial_begin), int(trial_end),
+                                        _ptr(ylt_out, np.float64))
+
+
+def ara_run_layer_diag(h, layer: Layer, seed, trial_begin, trial_end, ylt_out, diag: Diag):
+    return load_library().ara_run_layer_diag(h, ctypes.byref(layer), int(seed), int(trial_begin),
+                                             int(trial_end), _ptr(ylt_out, np.float64), ctypes.byref(diag))
+
+
+def ara_pml_tvar(h, ylt, n, return_periods, n_rp, pml_out, tvar_out):
+    return load_library().ara_pml_tvar(h, _ptr(ylt, np.float64), int(n), _ptr(return_periods, np.float64),
+                                       int(n_rp), _ptr(pml_out, np.float64), _ptr(tvar_out, np.float64))
+
+
+def ara_sort_ylt(h, ylt, n, order_out):
+    return load_library().ara_sort_ylt(h, _ptr(ylt, np.float64), int(n), _ptr(order_out, np.int64))
+
+
+def ara_debug_uniforms(h, seed, n, trials, ks, elts, out):
+    return load_library().ara_debug_uniforms(h, int(seed), int(n), _ptr(trials, np.int64), _ptr(ks, np.int32),
+                                             _ptr(elts, np.int32), _ptr(out, np.float32))
+
+
+def ara_debug_record_losses(h, n, mean, sigma, exposure, z, out, iters_out=None):
+    return load_library().ara_debug_record_losses(h, int(n), _ptr(mean, np.float32), _ptr(sigma, np.float32),
+                                                  _ptr(exposure, np.float32), _ptr(z, np.float32),
+                                                  _ptr(out, np.float32), _ptr(iters_out, np.int32))
+
+
+def ara_get_stats(h, out: Stats):
+    return load_library().ara_get_stats(h, ctypes.byref(out))
+
+
+def ara_get_timing(h, out: Timing, reset: int):
+    return load_library().ara_get_timing(h, ctypes.byref(out), int(reset))
+
+
+def ara_last_error(h) -> str:
+    msg = load_library().ara_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def ara_destroy(h) -> None:
+    load_library().ara_destroy(h)
+
+
+# ------------------------------------------------------------------ wrapper
+class Ara:
+    """One engine context on one CUDA device (see ``include/ara.h``)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, cuda_stream: int = 0):
+        rc, h = ara_create(device, hbm_budget_bytes, cuda_stream)
+        if rc != ARA_OK:
+            raise AraError(rc, f"ara_create(device={device}) failed")
+        self._h = h
+
+    # -- lifecycle
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            ara_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int) -> None:
+        if rc != ARA_OK:
+            raise AraError(rc, ara_last_error(self._h))
+
+    # -- calls
+    def set_stream(self, cuda_stream: int) -> None:
+        self._check(ara_set_stream(self._h, cuda_stream))
+
+    def load_yet(self, offsets, event_ids, catalogue_size: int) -> None:
+        self._check(ara_load_yet(self._h, _len(offsets) - 1, offsets, event_ids, catalogue_size))
+
+    def load_elts(self, elt_ids, rec_offsets, event_ids, mean, sigma, exposure, terms=None) -> None:
+        if terms is not None and isinstance(terms, np.ndarray):
+            terms = np.ascontiguousarray(terms, dtype=np.float32)
+        self._check(ara_load_elts(self._h, _len(elt_ids), elt_ids, rec_offsets, event_ids, mean, sigma, exposure,
+                                  terms))
+
+    def load_pool(self, pool) -> None:
+        """Load an ``ELTPool`` (see ``synth``)."""
+        self.load_elts(pool.elt_ids, pool.rec_offsets, pool.event_ids, pool.mean, pool.sigma, pool.exposure,
+                       pool.terms)
+
+    @staticmethod
+    def make_layer(elt_ids: Sequence[int], layer_terms, primary_only: bool = False):
+        ids = (ctypes.c_int32 * len(elt_ids))(*[int(i) for i in elt_ids])
+        occ_r, occ_l, agg_r, agg_l = (float(v) for v in layer_terms)
+        lay = Layer(len(elt_ids), ids, occ_r, occ_l, agg_r, agg_l, ARA_PRIMARY_ONLY if primary_only else 0)
+        lay._ids = ids  # keep the id array alive with the struct
+        return lay
+
+    def run_layer(self, elt_ids, layer_terms, seed: int, trial_begin: int, trial_end: int, ylt_out,
+                  primary_only: bool = False, hits_out=None, hash_out=None) -> None:
+        lay = self.make_layer(elt_ids, layer_terms, primary_only)
+        if hits_out is None and hash_out is None:
+            self._check(ara_run_layer(self._h, lay, seed, trial_begin, trial_end, ylt_out))
+        else:
+            d = Diag(_ptr(hits_out, np.int64), _ptr(hash_out, np.uint64))
+            self._check(ara_run_layer_diag(self._h, lay, seed, trial_begin, trial_end, ylt_out, d))
+
+    def pml_tvar(self, ylt, return_periods, pml_out=None, tvar_out=None):
+        rps = np.ascontiguousarray(return_periods, dtype=np.float64)
+        pml = np.zeros(rps.shape[0]) if pml_out is None else pml_out
+        tvar = np.zeros(rps.shape[0]) if tvar_out is None else tvar_out
+        self._check(ara_pml_tvar(self._h, ylt, _len(ylt), rps, rps.shape[0], pml, tvar))
+        return pml, tvar
+
+    def sort_ylt(self, ylt, order_out=None):
+        order = np.zeros(_len(ylt), np.int64) if order_out is None else order_out
+        self._check(ara_sort_ylt(self._h, ylt, _len(ylt), order))
+        return order
+
+    def debug_uniforms(self, seed, trials, ks, elts) -> np.ndarray:
+        t = np.ascontiguousarray(trials, np.int64)
+        k = np.ascontiguousarray(ks, np.int32)
+        e = np.ascontiguousarray(elts, np.int32)
+        out = np.zeros(t.shape[0], np.float32)
+        self._check(ara_debug_uniforms(self._h, seed, t.shape[0], t, k, e, out))
+        return out
+
+    def debug_record_losses(self, mean, sigma, exposure, z):
+        mu = np.ascontiguousarray(mean, np.float32)
+        sg = np.ascontiguousarray(sigma, np.float32)
+        ex = np.ascontiguousarray(exposure, np.float32)
+        zz = np.ascontiguousarray(z, np.float32)
+        out = np.zeros(mu.shape[0], np.float32)
+        iters = np.zeros(mu.shape[0], np.int32)
+        self._check(ara_debug_record_losses(self._h, mu.shape[0], mu, sg, ex, zz, out, iters))
+        return out, iters
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(ara_get_stats(self._h, s))
+        return s.as_dict()
+
+    def timing(self, reset: bool = False) -> dict:
+        t = Timing()
+        self._check(ara_get_timing(self._h, t, 1 if reset else 0))
+        return t.as_dict()

@@ -1,0 +1,725 @@
+// C-ABI host side of the ARA engine: context, device residency of the YET and
+// the ELT pool, validation, per-layer index build and kernel orchestration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ara.h"
+#include "ara_internal.h"
+
+namespace {
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct Elt {
+  DevBuf events;  // int32 [n] (+ padding)
+  DevBuf recs;    // ara::Pair [n]
+  int64_t n = 0;
+  int32_t max_event = -1;
+  ara_elt_terms terms{0.0f, INFINITY, 1.0f};
+};
+
+}  // namespace
+
+struct ara_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0;
+  size_t used = 0;
+  std::string err;
+  // YET
+  DevBuf yet_off, yet_ids;
+  std::vector<int64_t> h_off;
+  int64_t n_trials = 0;
+  int64_t n_events = 0;
+  int32_t catalogue = 0;
+  bool yet_loaded = false;
+  // ELT pool
+  std::map<int32_t, Elt> pool;
+  // per-layer index (grown on demand)
+  DevBuf bits, word_cnt, rankdir, mask, slot_cnt, pairs, scan_tmp;
+  // misc scratch
+  DevBuf flags;     // uint32 flags + int32 max event
+  DevBuf counters;  // 4 x u64
+  DevBuf ylt_tmp;   // device YLT when the caller's output is on the host
+  DevBuf diag_tmp;  // device diagnostics when the caller's outputs are on the host
+  DevBuf sel;       // select / sort scratch
+  DevBuf in_tmp;    // staging of host inputs for pml/sort
+  DevBuf out_tmp;   // small device outputs
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  ara_stats stats{};
+  // timing accumulators: event pairs recorded around launch groups since the last reset
+  struct Timed {
+    int kind;  // 0 layer kernel, 1 index build, 2 pml/tvar
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<Timed> timed;
+  int64_t launches = 0;
+  int num_sms = 0;
+  int max_smem = 0;
+};
+
+namespace {
+
+// Two events for one timed launch group (reused after a reset).
+bool timed_pair(ara_ctx* c, int kind, cudaEvent_t* a, cudaEvent_t* b) {
+  const size_t need = 2 * (c->timed.size() + 1);
+  while (c->ev_pool.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return false;
+    c->ev_pool.push_back(e);
+  }
+  *a = c->ev_pool[need - 2];
+  *b = c->ev_pool[need - 1];
+  c->timed.push_back({kind, *a, *b});
+  return true;
+}
+
+int fail(ara_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define ARA_CUDA(c, call)                                                                      \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail((c), ARA_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+void release(ara_ctx* c, DevBuf& b) {
+  if (b.ptr) {
+    cudaFree(b.ptr);
+    c->used -= b.bytes;
+  }
+  b.ptr = nullptr;
+  b.bytes = 0;
+}
+
+// Make b hold at least `bytes` (contents are not preserved).
+int reserve(ara_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return ARA_OK;
+  const size_t old = b.bytes;
+  release(c, b);
+  if (c->budget && c->used + bytes > c->budget)
+    return fail(c, ARA_ENOMEM, "allocation of %zu bytes exceeds the HBM budget (%zu of %zu in use, %zu released)",
+                bytes, c->used, c->budget, old);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, ARA_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  b.ptr = p;
+  b.bytes = bytes;
+  c->used += bytes;
+  return ARA_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaMemcpyKind kind_to_device(const void* src) {
+  return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+
+int bind(ara_ctx* c) {
+  if (!c) return ARA_EINVAL;
+  ARA_CUDA(c, cudaSetDevice(c->device));
+  return ARA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ara_create(ara_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
+  if (!out) return ARA_EINVAL;
+  *out = nullptr;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || n_dev == 0) {
+    cudaGetLastError();
+    return ARA_ECUDA;
+  }
+  if (device < 0 || device >= n_dev) return ARA_EINVAL;
+  ara_ctx* c = new ara_ctx();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return ARA_ECUDA;
+  }
+  for (auto& e : c->ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      ara_destroy(c);
+      return ARA_ECUDA;
+    }
+  }
+  if (reserve(c, c->flags, 64) != ARA_OK || reserve(c, c->counters, 64) != ARA_OK) {
+    ara_destroy(c);
+    return ARA_ENOMEM;
+  }
+  *out = c;
+  return ARA_OK;
+}
+
+int ara_set_stream(ara_ctx* c, void* cuda_stream) {
+  int rc = bind(c);
+  if (rc) return rc;
+  ARA_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  return ARA_OK;
+}
+
+int ara_load_yet(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int32_t* event_ids,
+                 int32_t catalogue_size) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (n_trials < 1 || !offsets || catalogue_size < 1)
+    return fail(c, ARA_EINVAL, "ara_load_yet: need n_trials >= 1, offsets and catalogue_size >= 1");
+  c->yet_loaded = false;
+  // offsets: keep a host copy (sizes and ranges are planned on the host)
+  c->h_off.resize(static_cast<size_t>(n_trials) + 1);
+  ARA_CUDA(c, cudaMemcpyAsync(c->h_off.data(), offsets, sizeof(int64_t) * (n_trials + 1), cudaMemcpyDefault,
+                              c->stream));
+  ARA_CUDA(c, cudaStreamSynchronize(c->stream));
+  const int64_t n_events = c->h_off[n_trials];
+  if (c->h_off[0] != 0 || n_events < 0) return fail(c, ARA_EINVAL, "ara_load_yet: offsets[0] must be 0 and offsets[n] >= 0");
+  if (n_events > 0 && !event_ids) return fail(c, ARA_EINVAL, "ara_load_yet: event_ids is NULL");
+  if ((rc = reserve(c, c->yet_off, sizeof(int64_t) * (n_trials + 1)))) return rc;
+  // ids: padded by 4 entries so that 16-byte loads near the end stay inside the buffer
+  if ((rc = reserve(c, c->yet_ids, sizeof(int32_t) * (n_events + 4)))) return rc;
+  ARA_CUDA(c, cudaMemcpyAsync(c->yet_off.ptr, c->h_off.data(), sizeof(int64_t) * (n_trials + 1),
+                              cudaMemcpyHostToDevice, c->stream));
+  if (n_events > 0)
+    ARA_CUDA(c, cudaMemcpyAsync(c->yet_ids.ptr, event_ids, sizeof(int32_t) * n_events, kind_to_device(event_ids),
+                                c->stream));
+  ARA_CUDA(c, cudaMemsetAsync(static_cast<int32_t*>(c->yet_ids.ptr) + n_events, 0, sizeof(int32_t) * 4, c->stream));
+  uint32_t* flags = static_cast<uint32_t*>(c->flags.ptr);
+  ARA_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(uint32_t), c->stream));
+  ARA_CUDA(c, ara::launch_check_offsets(static_cast<const int64_t*>(c->yet_off.ptr), n_trials, n_events, flags,
+                                        c->stream));
+  ARA_CUDA(c, ara::launch_check_ids(static_cast<const int32_t*>(c->yet_ids.ptr), n_events, catalogue_size, flags,
+                                    c->stream));
+  uint32_t h_flags = 0;
+  ARA_CUDA(c, cudaMemcpyAsync(&h_flags, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+  ARA_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (h_flags & ara::kBadOffsets) return fail(c, ARA_EINVAL, "ara_load_yet: offsets are not non-decreasing");
+  if (h_flags & ara::kLongTrial) return fail(c, ARA_EINVAL, "ara_load_yet: a trial has 2^24 or more events");
+  if (h_flags & ara::kBadEventId)
+    return fail(c, ARA_EINVAL, "ara_load_yet: an event id lies outside [0, %d)", catalogue_size);
+  c->n_trials = n_trials;
+  c->n_events = n_events;
+  c->catalogue = catalogue_size;
+  c->yet_loaded = true;
+  return ARA_OK;
+}
+
+int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int64_t* rec_offsets,
+                  const int32_t* event_ids, const float* mean, const float* sigma, const float* exposure,
+                  const ara_elt_terms* terms) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (n_elts < 1 || !elt_ids || !rec_offsets) return fail(c, ARA_EINVAL, "ara_load_elts: bad arguments");
+  std::vector<int32_t> ids(n_elts);
+  std::vector<int64_t> offs(static_cast<size_t>(n_elts) + 1);
+  std::vector<ara_elt_terms> tm(n_elts, ara_elt_terms{0.0f, INFINITY, 1.0f});
+  ARA_CUDA(c, cudaMemcpy(ids.data(), elt_ids, sizeof(int32_t) * n_elts, cudaMemcpyDefault));
+  ARA_CUDA(c, cudaMemcpy(offs.data(), rec_offsets, sizeof(int64_t) * (n_elts + 1), cudaMemcpyDefault));
+  if (terms) ARA_CUDA(c, cudaMemcpy(tm.data(), terms, sizeof(ara_elt_terms) * n_elts, cudaMemcpyDefault));
+  if (offs[0] != 0) return fail(c, ARA_EINVAL, "ara_load_elts: rec_offsets[0] must be 0");
+  for (int32_t i = 0; i < n_elts; ++i) {
+    if (ids[i] < 0) return fail(c, ARA_EINVAL, "ara_load_elts: pool id %d is negative", ids[i]);
+    if (offs[i + 1] < offs[i]) return fail(c, ARA_EINVAL, "ara_load_elts: rec_offsets decrease at %d", i);
+    if (offs[i + 1] - offs[i] >= (int64_t(1) << 31))
+      return fail(c, ARA_EINVAL, "ara_load_elts: ELT %d has too many records", ids[i]);
+    const ara_elt_terms& t = tm[i];
+    if (!(t.retention >= 0.0f) || !(t.limit >= 0.0f) || !(t.share >= 0.0f) || std::isnan(t.limit) ||
+        !std::isfinite(t.retention) || !std::isfinite(t.share))
+      return fail(c, ARA_EINVAL, "ara_load_elts: ELT %d has invalid financial terms", ids[i]);
+    for (int32_t j = 0; j < i; ++j)
+      if (ids[j] == ids[i]) return fail(c, ARA_EINVAL, "ara_load_elts: pool id %d appears twice", ids[i]);
+  }
+  if (offs[n_elts] > 0 && (!event_ids || !mean || !sigma || !exposure))
+    return fail(c, ARA_EINVAL, "ara_load_elts: record arrays are NULL");
+  // stage all records on the device once, then split per ELT
+  const int64_t R = offs[n_elts];
+  DevBuf stage;
+  const size_t stage_bytes = static_cast<size_t>(R) * (sizeof(int32_t) + 3 * sizeof(float)) + 64;
+  if ((rc = reserve(c, stage, stage_bytes))) return rc;
+  int32_t* d_ev = static_cast<int32_t*>(stage.ptr);
+  float* d_mu = reinterpret_cast<float*>(d_ev + R);
+  float* d_sg = d_mu + R;
+  float* d_ex = d_sg + R;
+  auto cleanup = [&](int code) {
+    release(c, stage);
+    return code;
+  };
+  if (R > 0) {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ev, event_ids, sizeof(int32_t) * R, kind_to_device(event_ids), c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_mu, mean, sizeof(float) * R, kind_to_device(mean), c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_sg, sigma, sizeof(float) * R, kind_to_device(sigma), c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ex, exposure, sizeof(float) * R, kind_to_device(exposure), c->stream);
+    if (e != cudaSuccess) return cleanup(fail(c, ARA_ECUDA, "ara_load_elts: copy failed: %s", cudaGetErrorString(e)));
+  }
+  std::vector<Elt> fresh(n_elts);
+  uint32_t* flags = static_cast<uint32_t*>(c->flags.ptr);
+  int32_t* max_ev = reinterpret_cast<int32_t*>(flags + 1);
+  std::vector<int32_t> maxes(n_elts, -1);
+  for (int32_t i = 0; i < n_elts; ++i) {
+    Elt& el = fresh[i];
+    el.n = offs[i + 1] - offs[i];
+    el.terms = tm[i];
+    if ((rc = reserve(c, el.events, sizeof(int32_t) * (el.n + 4))) ||
+        (rc = reserve(c, el.recs, sizeof(ara::Pair) * (el.n > 0 ? el.n : 1)))) {
+      for (auto& f : fresh) {
+        release(c, f.events);
+        release(c, f.recs);
+      }
+      return cleanup(rc);
+    }
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(max_ev, 0xFF, sizeof(int32_t), c->stream);
+    if (e == cudaSuccess && el.n > 0)
+      e = cudaMemcpyAsync(el.events.ptr, d_ev + offs[i], sizeof(int32_t) * el.n, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = ara::launch_prepare_records(d_ev + offs[i], d_mu + offs[i], d_sg + offs[i], d_ex + offs[i], el.n,
+                                      static_cast<ara::Pair*>(el.recs.ptr), flags, max_ev, c->stream);
+    uint32_t hf[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    int bad = 0;
+    const char* why = "";
+    if (e != cudaSuccess) {
+      bad = ARA_ECUDA;
+      why = cudaGetErrorString(e);
+    } else if (hf[0] & ara::kBadOrder) {
+      bad = ARA_EINVAL;
+      why = "event ids are not strictly increasing";
+    } else if (hf[0] & ara::kBadEventId) {
+      bad = ARA_EINVAL;
+      why = "an event id is negative";
+    } else if (hf[0] & ara::kBadValue) {
+      bad = ARA_EINVAL;
+      why = "a mean, sigma or exposure is negative or not finite";
+    } else if (hf[0] & ara::kBadExposure) {
+      bad = ARA_EINVAL;
+      why = "a record with mean > 0 and sigma > 0 has exposure <= mean";
+    }
+    if (bad) {
+      for (auto& f : fresh) {
+        release(c, f.events);
+        release(c, f.recs);
+      }
+      return cleanup(fail(c, bad, "ara_load_elts: ELT %d: %s", ids[i], why));
+    }
+    el.max_event = static_cast<int32_t>(hf[1]);
+  }
+  for (int32_t i = 0; i < n_elts; ++i) {
+    auto it = c->pool.find(ids[i]);
+    if (it != c->pool.end()) {
+      release(c, it->second.events);
+      release(c, it->second.recs);
+      c->pool.erase(it);
+    }
+    c->pool[ids[i]] = fresh[i];
+  }
+  return cleanup(ARA_OK);
+}
+
+static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out,
+                          const ara_diag* diag) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (!L || !ylt_out) return fail(c, ARA_EINVAL, "ara_run_layer: layer and ylt_out are required");
+  if (!c->yet_loaded) return fail(c, ARA_ENOTLOADED, "ara_run_layer: no YET loaded");
+  if (t0 < 0 || t1 > c->n_trials || t0 >= t1)
+    return fail(c, ARA_EINVAL, "ara_run_layer: trial range [%lld, %lld) outside [0, %lld)", (long long)t0,
+                (long long)t1, (long long)c->n_trials);
+  if (L->n_elts < 1 || L->n_elts > ARA_MAX_LAYER_ELTS || !L->elt_ids)
+    return fail(c, ARA_EINVAL, "ara_run_layer: a layer needs 1..%d ELTs", ARA_MAX_LAYER_ELTS);
+  if (!(L->occ_retention >= 0.0) || !(L->agg_retention >= 0.0) || !(L->occ_limit >= 0.0) ||
+      !(L->agg_limit >= 0.0) || !std::isfinite(L->occ_retention) || !std::isfinite(L->agg_retention))
+    return fail(c, ARA_EINVAL, "ara_run_layer: retentions must be finite and >= 0, limits >= 0");
+  std::vector<int32_t> ids(L->elt_ids, L->elt_ids + L->n_elts);
+  std::sort(ids.begin(), ids.end());  // canonical order: the layer's result does not depend on ELT order
+  for (size_t i = 1; i < ids.size(); ++i)
+    if (ids[i] == ids[i - 1]) return fail(c, ARA_EINVAL, "ara_run_layer: pool id %d repeated in the layer", ids[i]);
+  ara::LayerEltRefs refs{};
+  refs.n_elts = L->n_elts;
+  refs.rec_begin[0] = 0;
+  ara::LayerParams p{};
+  for (int i = 0; i < L->n_elts; ++i) {
+    auto it = c->pool.find(ids[i]);
+    if (it == c->pool.end()) return fail(c, ARA_ENOTLOADED, "ara_run_layer: ELT %d is not loaded", ids[i]);
+    const Elt& el = it->second;
+    if (el.max_event >= c->catalogue)
+      return fail(c, ARA_EINVAL, "ara_run_layer: ELT %d holds event id %d outside the catalogue of %d", ids[i],
+                  el.max_event, c->catalogue);
+    refs.events[i] = static_cast<const int32_t*>(el.events.ptr);
+    refs.recs[i] = static_cast<const ara::Pair*>(el.recs.ptr);
+    refs.rec_begin[i + 1] = refs.rec_begin[i] + el.n;
+    p.elt_id[i] = ids[i];
+    p.t_ret[i] = el.terms.retention;
+    p.t_lim[i] = el.terms.limit;
+    p.t_share[i] = el.terms.share;
+  }
+  const int64_t n_recs = refs.rec_begin[L->n_elts];
+  if (n_recs >= (int64_t(1) << 32) - 1) return fail(c, ARA_EINVAL, "ara_run_layer: layer holds too many records");
+  // ---- per-layer index
+  const int64_t n_words = (static_cast<int64_t>(c->catalogue) + 31) / 32;
+  const size_t tmp_words = std::max(ara::scan_tmp_words(n_words), ara::scan_tmp_words(n_recs));
+  if ((rc = reserve(c, c->bits, sizeof(uint32_t) * n_words)) ||
+      (rc = reserve(c, c->word_cnt, sizeof(uint32_t) * (n_words + 1))) ||
+      (rc = reserve(c, c->rankdir, sizeof(uint2) * n_words)) ||
+      (rc = reserve(c, c->mask, sizeof(uint32_t) * (n_recs + 1))) ||
+      (rc = reserve(c, c->slot_cnt, sizeof(uint32_t) * (n_recs + 2))) ||
+      (rc = reserve(c, c->pairs, sizeof(ara::Pair) * (n_recs + 1))) ||
+      (rc = reserve(c, c->scan_tmp, sizeof(uint32_t) * (tmp_words + 8))))
+    return rc;
+  ara::LayerIndex ix{};
+  ix.bits = static_cast<uint32_t*>(c->bits.ptr);
+  ix.word_cnt = static_cast<uint32_t*>(c->word_cnt.ptr);
+  ix.rankdir = static_cast<uint2*>(c->rankdir.ptr);
+  ix.mask = static_cast<uint32_t*>(c->mask.ptr);
+  ix.slot_cnt = static_cast<uint32_t*>(c->slot_cnt.ptr);
+  ix.pairs = static_cast<ara::Pair*>(c->pairs.ptr);
+  ix.scan_tmp = static_cast<uint32_t*>(c->scan_tmp.ptr);
+  ix.n_words = n_words;
+  ix.n_recs = n_recs;
+  // ---- outputs
+  const int64_t n_out = t1 - t0;
+  const bool ylt_dev = is_device_ptr(ylt_out);
+  double* d_ylt = ylt_out;
+  if (!ylt_dev) {
+    if ((rc = reserve(c, c->ylt_tmp, sizeof(double) * n_out))) return rc;
+    d_ylt = static_cast<double*>(c->ylt_tmp.ptr);
+  }
+  int64_t* d_hits = nullptr;
+  uint64_t* d_hash = nullptr;
+  const bool hits_dev = diag && diag->hits && is_device_ptr(diag->hits);
+  const bool hash_dev = diag && diag->hit_hash && is_device_ptr(diag->hit_hash);
+  if (diag && (diag->hits || diag->hit_hash)) {
+    if ((rc = reserve(c, c->diag_tmp, 2 * sizeof(int64_t) * n_out))) return rc;
+    if (diag->hits) d_hits = hits_dev ? diag->hits : static_cast<int64_t*>(c->diag_tmp.ptr);
+    if (diag->hit_hash) d_hash = hash_dev ? diag->hit_hash : reinterpret_cast<uint64_t*>(static_cast<int64_t*>(c->diag_tmp.ptr) + n_out);
+  }
+  // ---- launch
+  cudaEvent_t ia, ib, ka, kb;
+  if (!timed_pair(c, 1, &ia, &ib) || !timed_pair(c, 0, &ka, &kb))
+    return fail(c, ARA_ECUDA, "ara_run_layer: cannot create timing events");
+  int launched = 0;
+  ARA_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+  ARA_CUDA(c, cudaEventRecord(ia, c->stream));
+  ARA_CUDA(c, ara::build_layer_index(refs, ix, c->stream, &launched));
+  ARA_CUDA(c, cudaEventRecord(ib, c->stream));
+  ARA_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+  // filter: the largest power-of-two word count that fits next to the fixed shared-memory use
+  int filt_words = 1;
+  const size_t fixed = ara::layer_smem_bytes(0);
+  while (filt_words < n_words && fixed + sizeof(uint32_t) * (filt_words * 2) <= static_cast<size_t>(c->max_smem))
+    filt_words *= 2;
+  const size_t smem = ara::layer_smem_bytes(filt_words);
+  if (smem > static_cast<size_t>(c->max_smem))
+    return fail(c, ARA_ECUDA, "ara_run_layer: kernel needs %zu bytes of shared memory, device allows %d", smem,
+                c->max_smem);
+  const int64_t n_tiles = (n_out + ara::kTileTrials - 1) / ara::kTileTrials;
+  p.off = static_cast<const int64_t*>(c->yet_off.ptr);
+  p.ids = static_cast<const int32_t*>(c->yet_ids.ptr);
+  p.t_begin = t0;
+  p.t_end = t1;
+  p.rankdir = ix.rankdir;
+  p.n_words = n_words;
+  p.slot_start = ix.slot_cnt;
+  p.pairs = ix.pairs;
+  p.filt_words = filt_words;
+  p.n_elts = L->n_elts;
+  p.occ_r = static_cast<float>(L->occ_retention);
+  p.occ_l = static_cast<float>(L->occ_limit);
+  p.agg_r = L->agg_retention;
+  p.agg_l = L->agg_limit;
+  p.seed_lo = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
+  p.seed_hi = static_cast<uint32_t>(seed >> 32);
+  p.primary_only = (L->flags & ARA_PRIMARY_ONLY) ? 1 : 0;
+  p.n_tiles = static_cast<int32_t>(n_tiles);
+  p.ylt = d_ylt;
+  p.diag_hits = d_hits;
+  p.diag_hash = d_hash;
+  p.counters = static_cast<unsigned long long*>(c->counters.ptr);
+  ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 4 * sizeof(unsigned long long), c->stream));
+  const int grid = static_cast<int>(std::min<int64_t>(c->num_sms, n_tiles));
+  ARA_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+  ARA_CUDA(c, cudaEventRecord(ka, c->stream));
+  ARA_CUDA(c, ara::launch_layer_kernel(p, grid, smem, c->stream));
+  ARA_CUDA(c, cudaEventRecord(kb, c->stream));
+  ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
+  launched += 1;
+  c->launches += launched;
+  if (!ylt_dev)
+    ARA_CUDA(c, cudaMemcpyAsync(ylt_out, d_ylt, sizeof(double) * n_out, cudaMemcpyDeviceToHost, c->stream));
+  if (d_hits && !hits_dev)
+    ARA_CUDA(c, cudaMemcpyAsync(diag->hits, d_hits, sizeof(int64_t) * n_out, cudaMemcpyDeviceToHost, c->stream));
+  if (d_hash && !hash_dev)
+    ARA_CUDA(c, cudaMemcpyAsync(diag->hit_hash, d_hash, sizeof(uint64_t) * n_out, cudaMemcpyDeviceToHost, c->stream));
+  if (!ylt_dev || (d_hits && !hits_dev) || (d_hash && !hash_dev)) ARA_CUDA(c, cudaStreamSynchronize(c->stream));
+  // ---- stats (device times are read lazily by ara_get_stats)
+  c->stats = ara_stats{};
+  c->stats.n_events = c->h_off[t1] - c->h_off[t0];
+  c->stats.n_evals = c->stats.n_events * L->n_elts;
+  c->stats.grid = grid;
+  c->stats.block = ara::kLayerThreads;
+  c->stats.smem_bytes = static_cast<int32_t>(smem);
+  c->stats.filter_bits = filt_words * 32;
+  c->stats.kernel_ms = -1.0f;
+  return ARA_OK;
+}
+
+int ara_run_layer(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out) {
+  return run_layer_impl(c, L, seed, t0, t1, ylt_out, nullptr);
+}
+
+int ara_run_layer_diag(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out,
+                       const ara_diag* diag) {
+  return run_layer_impl(c, L, seed, t0, t1, ylt_out, diag);
+}
+
+int ara_get_stats(const ara_ctx* cc, ara_stats* out) {
+  ara_ctx* c = const_cast<ara_ctx*>(cc);
+  int rc = bind(c);
+  if (rc) return rc;
+  if (!out) return fail(c, ARA_EINVAL, "ara_get_stats: out is NULL");
+  if (c->stats.kernel_ms < 0.0f) {
+    ARA_CUDA(c, cudaEventSynchronize(c->ev[3]));
+    float ms = 0.0f;
+    ARA_CUDA(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    c->stats.index_ms = ms;
+    ARA_CUDA(c, cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+    c->stats.kernel_ms = ms;
+    unsigned long long h[4];
+    ARA_CUDA(c, cudaMemcpy(h, c->counters.ptr, sizeof h, cudaMemcpyDeviceToHost));
+    c->stats.n_pairs_hit = static_cast<int64_t>(h[1]);
+    c->stats.n_nonconverged = static_cast<int64_t>(h[2]);
+  }
+  *out = c->stats;
+  return ARA_OK;
+}
+
+int ara_get_timing(ara_ctx* c, ara_timing* out, int reset) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (!out) return fail(c, ARA_EINVAL, "ara_get_timing: out is NULL");
+  *out = ara_timing{};
+  for (const auto& t : c->timed) {
+    ARA_CUDA(c, cudaEventSynchronize(t.b));
+    float ms = 0.0f;
+    ARA_CUDA(c, cudaEventElapsedTime(&ms, t.a, t.b));
+    if (t.kind == 0) {
+      out->layer_calls += 1;
+      out->kernel_ms += ms;
+    } else if (t.kind == 1) {
+      out->index_ms += ms;
+    } else {
+      out->pml_calls += 1;
+      out->pml_ms += ms;
+    }
+  }
+  out->kernel_launches = c->launches;
+  if (reset) {
+    c->timed.clear();
+    c->launches = 0;
+  }
+  return ARA_OK;
+}
+
+int ara_pml_tvar(ara_ctx* c, const double* ylt, int64_t n, const double* rps, int32_t n_rp, double* pml_out,
+                 double* tvar_out) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (!ylt || n < 1 || !rps || n_rp < 1 || !pml_out || !tvar_out)
+    return fail(c, ARA_EINVAL, "ara_pml_tvar: bad arguments");
+  std::vector<double> h_rps(n_rp);
+  ARA_CUDA(c, cudaMemcpy(h_rps.data(), rps, sizeof(double) * n_rp, cudaMemcpyDefault));
+  for (double r : h_rps)
+    if (!(r >= 1.0) || !std::isfinite(r)) return fail(c, ARA_EINVAL, "ara_pml_tvar: return periods must be >= 1");
+  const double* d_ylt = ylt;
+  if (!is_device_ptr(ylt)) {
+    if ((rc = reserve(c, c->in_tmp, sizeof(double) * n))) return rc;
+    ARA_CUDA(c, cudaMemcpyAsync(c->in_tmp.ptr, ylt, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    d_ylt = static_cast<const double*>(c->in_tmp.ptr);
+  }
+  const bool pml_dev = is_device_ptr(pml_out), tvar_dev = is_device_ptr(tvar_out);
+  if ((rc = reserve(c, c->sel, ara::select_scratch_bytes(n))) ||
+      (rc = reserve(c, c->out_tmp, 2 * sizeof(double) * n_rp)))
+    return rc;
+  double* d_pml = pml_dev ? pml_out : static_cast<double*>(c->out_tmp.ptr);
+  double* d_tvar = tvar_dev ? tvar_out : static_cast<double*>(c->out_tmp.ptr) + n_rp;
+  cudaEvent_t pa, pb;
+  if (!timed_pair(c, 2, &pa, &pb)) return fail(c, ARA_ECUDA, "ara_pml_tvar: cannot create timing events");
+  int launched = 0;
+  ARA_CUDA(c, cudaEventRecord(pa, c->stream));
+  ARA_CUDA(c, ara::pml_tvar_device(d_ylt, n, h_rps.data(), n_rp, d_pml, d_tvar, c->sel.ptr, c->stream, &launched));
+  ARA_CUDA(c, cudaEventRecord(pb, c->stream));
+  c->launches += launched;
+  if (!pml_dev) ARA_CUDA(c, cudaMemcpyAsync(pml_out, d_pml, sizeof(double) * n_rp, cudaMemcpyDeviceToHost, c->stream));
+  if (!tvar_dev)
+    ARA_CUDA(c, cudaMemcpyAsync(tvar_out, d_tvar, sizeof(double) * n_rp, cudaMemcpyDeviceToHost, c->stream));
+  if (!pml_dev || !tvar_dev || !is_device_ptr(ylt)) ARA_CUDA(c, cudaStreamSynchronize(c->stream));
+  return ARA_OK;
+}
+
+int ara_sort_ylt(ara_ctx* c, const double* ylt, int64_t n, int64_t* order_out) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (!ylt || n < 1 || !order_out) return fail(c, ARA_EINVAL, "ara_sort_ylt: bad arguments");
+  if (n >= (int64_t(1) << 31)) return fail(c, ARA_EINVAL, "ara_sort_ylt: at most 2^31 - 1 trials");
+  const double* d_ylt = ylt;
+  if (!is_device_ptr(ylt)) {
+    if ((rc = reserve(c, c->in_tmp, sizeof(double) * n))) return rc;
+    ARA_CUDA(c, cudaMemcpyAsync(c->in_tmp.ptr, ylt, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    d_ylt = static_cast<const double*>(c->in_tmp.ptr);
+  }
+  const bool out_dev = is_device_ptr(order_out);
+  if ((rc = reserve(c, c->sel, ara::sort_scratch_bytes(n)))) return rc;
+  int64_t* d_order = order_out;
+  if (!out_dev) {
+    if ((rc = reserve(c, c->out_tmp, sizeof(int64_t) * n))) return rc;
+    d_order = static_cast<int64_t*>(c->out_tmp.ptr);
+  }
+  int launched = 0;
+  ARA_CUDA(c, ara::sort_desc_device(d_ylt, n, d_order, c->sel.ptr, c->stream, &launched));
+  c->launches += launched;
+  if (!out_dev) {
+    ARA_CUDA(c, cudaMemcpyAsync(order_out, d_order, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->stream));
+    ARA_CUDA(c, cudaStreamSynchronize(c->stream));
+  } else if (!is_device_ptr(ylt)) {
+    ARA_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return ARA_OK;
+}
+
+int ara_debug_uniforms(ara_ctx* c, uint64_t seed, int64_t n, const int64_t* trials, const int32_t* ks,
+                       const int32_t* elts, float* out) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && (!trials || !ks || !elts || !out))) return fail(c, ARA_EINVAL, "ara_debug_uniforms: bad arguments");
+  if (n == 0) return ARA_OK;
+  DevBuf tmp;
+  const size_t bytes = static_cast<size_t>(n) * (sizeof(int64_t) + 2 * sizeof(int32_t) + sizeof(float));
+  if ((rc = reserve(c, tmp, bytes))) return rc;
+  int64_t* d_t = static_cast<int64_t*>(tmp.ptr);
+  int32_t* d_k = reinterpret_cast<int32_t*>(d_t + n);
+  int32_t* d_e = d_k + n;
+  float* d_o = reinterpret_cast<float*>(d_e + n);
+  cudaError_t e = cudaMemcpyAsync(d_t, trials, sizeof(int64_t) * n, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_k, ks, sizeof(int32_t) * n, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_e, elts, sizeof(int32_t) * n, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess)
+    e = ara::launch_debug_uniforms(static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), n, d_t, d_k, d_e, d_o,
+                                   c->stream);
+  c->launches += 1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_o, sizeof(float) * n, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  release(c, tmp);
+  if (e != cudaSuccess) return fail(c, ARA_ECUDA, "ara_debug_uniforms: %s", cudaGetErrorString(e));
+  return ARA_OK;
+}
+
+int ara_debug_record_losses(ara_ctx* c, int64_t n, const float* mean, const float* sigma, const float* exposure,
+                            const float* z, float* out, int32_t* iters_out) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && (!mean || !sigma || !exposure || !z || !out)))
+    return fail(c, ARA_EINVAL, "ara_debug_record_losses: bad arguments");
+  if (n == 0) return ARA_OK;
+  DevBuf tmp;
+  const size_t bytes = static_cast<size_t>(n) * (sizeof(ara::Pair) + 6 * sizeof(float) + sizeof(int32_t)) + 64;
+  if ((rc = reserve(c, tmp, bytes))) return rc;
+  ara::Pair* d_p = static_cast<ara::Pair*>(tmp.ptr);
+  float* d_mu = reinterpret_cast<float*>(d_p + n);
+  float* d_sg = d_mu + n;
+  float* d_ex = d_sg + n;
+  float* d_z = d_ex + n;
+  float* d_o = d_z + n;
+  int32_t* d_ev = reinterpret_cast<int32_t*>(d_o + n);
+  int32_t* d_it = d_ev + n;
+  uint32_t* flags = static_cast<uint32_t*>(c->flags.ptr);
+  int32_t* max_ev = reinterpret_cast<int32_t*>(flags + 1);
+  cudaError_t e = cudaMemcpyAsync(d_mu, mean, sizeof(float) * n, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_sg, sigma, sizeof(float) * n, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ex, exposure, sizeof(float) * n, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_z, z, sizeof(float) * n, cudaMemcpyDefault, c->stream);
+  // the preparation kernel checks event order; give it strictly increasing ids
+  std::vector<int32_t> ev(static_cast<size_t>(n));
+  for (int64_t i = 0; i < n; ++i) ev[i] = static_cast<int32_t>(i);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_ev, ev.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 2 * sizeof(uint32_t), c->stream);
+  if (e == cudaSuccess) e = ara::launch_prepare_records(d_ev, d_mu, d_sg, d_ex, n, d_p, flags, max_ev, c->stream);
+  if (e == cudaSuccess) e = ara::launch_debug_losses(d_p, d_z, n, d_o, d_it, c->stream);
+  c->launches += 2;
+  uint32_t hf = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_o, sizeof(float) * n, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess && iters_out)
+    e = cudaMemcpyAsync(iters_out, d_it, sizeof(int32_t) * n, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  release(c, tmp);
+  if (e != cudaSuccess) return fail(c, ARA_ECUDA, "ara_debug_record_losses: %s", cudaGetErrorString(e));
+  if (hf & (ara::kBadValue | ara::kBadExposure))
+    return fail(c, ARA_EINVAL, "ara_debug_record_losses: invalid record values");
+  return ARA_OK;
+}
+
+const char* ara_last_error(const ara_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+void ara_destroy(ara_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->pool) {
+    release(c, kv.second.events);
+    release(c, kv.second.recs);
+  }
+  DevBuf* bufs[] = {&c->yet_off, &c->yet_ids, &c->bits,  &c->word_cnt, &c->rankdir, &c->mask,   &c->slot_cnt,
+                    &c->pairs,   &c->scan_tmp, &c->flags, &c->counters, &c->ylt_tmp, &c->diag_tmp, &c->sel,
+                    &c->in_tmp,  &c->out_tmp};
+  for (DevBuf* b : bufs) release(c, *b);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : c->ev_pool) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal interface between the C-ABI host code (ara_abi.cu) and the
+// kernels (ara_kernels.cu, ara_select.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ara_device_math.cuh"
+
+namespace ara {
+
+// --------------------------------------------------------------- load time
+// Validation flags written by the check kernels (bitwise OR).
+enum : uint32_t {
+  kBadOffsets = 1u,    // offsets[0] != 0 or offsets decrease
+  kBadEventId = 2u,    // id outside [0, catalogue)
+  kBadOrder = 4u,      // ELT event ids not strictly increasing
+  kBadValue = 8u,      // negative / non-finite mean, sigma or exposure
+  kBadExposure = 16u,  // exposure <= mean for a record with mean > 0 and sigma > 0
+  kLongTrial = 32u,    // a trial with 2^24 or more events
+};
+
+cudaError_t launch_check_offsets(const int64_t* off, int64_t n_trials, int64_t n_events, uint32_t* flags,
+                                 cudaStream_t s);
+cudaError_t launch_check_ids(const int32_t* ids, int64_t n, int32_t catalogue, uint32_t* flags, cudaStream_t s);
+
+// Prepare the Pair records of one ELT from (mean, sigma, exposure) in FP64:
+// Beta shapes, x0/y0, C, I_{1/2}(a, b), kind.  Also checks order and values
+// and reduces the largest event id into *max_event (atomicMax).
+cudaError_t launch_prepare_records(const int32_t* events, const float* mean, const float* sigma,
+                                   const float* exposure, int64_t n, Pair* out, uint32_t* flags,
+                                   int32_t* max_event, cudaStream_t s);
+
+// Check kernels (device functions of the hot path on given inputs).
+cudaError_t launch_debug_uniforms(uint32_t seed_lo, uint32_t seed_hi, int64_t n, const int64_t* trials,
+                                  const int32_t* ks, const int32_t* elts, float* out, cudaStream_t s);
+cudaError_t launch_debug_losses(const Pair* recs, const float* z, int64_t n, float* out, int32_t* iters,
+                                cudaStream_t s);
+
+// --------------------------------------------------------------- scan
+// Exclusive prefix sum of n uint32 values; out[n] receives the total.
+// `tmp` must hold scan_tmp_words(n) words.
+size_t scan_tmp_words(int64_t n);
+cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp, cudaStream_t s,
+                               int* n_launch = nullptr);
+
+// --------------------------------------------------------------- layer index
+struct LayerEltRefs {
+  int32_t n_elts;
+  const int32_t* events[32];  // sorted event ids of the layer's ELT at position p
+  const Pair* recs[32];       // prepared records
+  int64_t rec_begin[33];      // prefix sums of record counts over positions
+};
+
+struct LayerIndex {
+  uint32_t* bits;        // [n_words] membership bitmap over the catalogue
+  uint32_t* word_cnt;    // [n_words + 1] scratch: popcounts, then exclusive scan
+  uint2* rankdir;        // [n_words] {bits, set bits before the word}
+  uint32_t* mask;        // [n_recs] per slot: bitmask of layer positions
+  uint32_t* slot_cnt;    // [n_recs + 1] scratch -> slot_start
+  Pair* pairs;           // [n_recs]
+  uint32_t* scan_tmp;
+  int64_t n_words;
+  int64_t n_recs;
+};
+
+cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStream_t s, int* n_launch);
+
+// --------------------------------------------------------------- main kernel
+constexpr int kLayerThreads = 1024;
+constexpr int kTileTrials = 128;
+constexpr int kChunk = kLayerThreads * 4;   // YET ids scanned per block step
+constexpr int kFlush = 1024;                // queued hits that trigger the SU phase
+constexpr int kQCap = kFlush + kChunk;      // queue capacity
+constexpr int kWin = 2048;                  // pairs per SU window
+
+struct LayerParams {
+  const int64_t* off;
+  const int32_t* ids;
+  int64_t t_begin, t_end;
+  const uint2* rankdir;
+  int64_t n_words;
+  const uint32_t* slot_start;
+  const Pair* pairs;
+  int32_t filt_words;  // power of two
+  int32_t n_elts;
+  int32_t elt_id[32];
+  float t_ret[32], t_lim[32], t_share[32];
+  float occ_r, occ_l;  // occurrence terms in FP32 (the loss arithmetic)
+  double agg_r, agg_l;
+  uint32_t seed_lo, seed_hi;
+  int32_t primary_only;
+  int32_t n_tiles;
+  double* ylt;
+  int64_t* diag_hits;
+  uint64_t* diag_hash;
+  unsigned long long* counters;  // [0] tile queue, [1] pairs hit, [2] non-converged
+};
+
+size_t layer_smem_bytes(int filt_words);
+cudaError_t launch_layer_kernel(const LayerParams& p, int grid, size_t smem, cudaStream_t s);
+
+// --------------------------------------------------------------- PML / TVaR / sort
+// Scratch sizes in bytes for n year losses.
+size_t select_scratch_bytes(int64_t n);
+// pml/tvar: n_rp device doubles each; rps: host array.
+cudaError_t pml_tvar_device(const double* ylt, int64_t n, const double* rps_host, int32_t n_rp, double* pml,
+                            double* tvar, void* scratch, cudaStream_t s, int* n_launch);
+size_t sort_scratch_bytes(int64_t n);
+cudaError_t sort_desc_device(const double* ylt, int64_t n, int64_t* order, void* scratch, cudaStream_t s,
+                             int* n_launch);
+
+}  // namespace ara

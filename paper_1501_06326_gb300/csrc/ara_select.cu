@@ -1,0 +1,277 @@
+// PML / TVaR (Section 2.3) and the YLT trial order on the device.
+//
+// Year losses are mapped to order-preserving 64-bit keys (sign-flipped IEEE
+// bits).  PML(RP) is the m-th largest year loss, m = ceil(n / RP): an MSB-first
+// radix select with 8-bit digits narrows the key prefix in eight histogram
+// passes.  TVaR(RP) is the mean of the m largest: the sum of the values whose
+// key exceeds the m-th key plus the tied remainder times the m-th value, in
+// FP64 with a fixed reduction order (deterministic).  The full trial order
+// (largest first, ties by index) is an LSD radix sort of the complemented keys
+// with stable per-tile scatter (warp match + per-warp digit offsets).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "ara_internal.h"
+
+namespace ara {
+
+namespace {
+
+constexpr int kSelBlocks = 304;  // fixed grid: deterministic reduction order
+constexpr int kSelThreads = 256;
+
+__device__ __forceinline__ unsigned long long key_of(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double value_of(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double(static_cast<long long>(b));
+}
+
+struct SelState {
+  unsigned long long prefix;  // key bits fixed so far
+  unsigned long long mask;    // which bits are fixed
+  unsigned long long want;    // rank (1-based, from the top) within the prefix bucket
+  unsigned long long m;       // target rank
+  unsigned int bad;           // a NaN was seen
+  unsigned int pad;
+};
+
+__global__ void k_sel_init(SelState* st, unsigned long long m, unsigned int* hist) {
+  st->prefix = 0;
+  st->mask = 0;
+  st->want = m;
+  st->m = m;
+  st->bad = 0;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+}
+
+__global__ void k_sel_hist(const double* ylt, int64_t n, const SelState* st, int shift, unsigned int* hist,
+                           unsigned int* bad) {
+  __shared__ unsigned int sh[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const unsigned long long prefix = st->prefix, mask = st->mask;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  bool nan = false;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+    const double v = ylt[i];
+    nan |= (v != v);
+    const unsigned long long k = key_of(v);
+    if ((k & mask) == prefix) atomicAdd(&sh[(k >> shift) & 255u], 1u);
+  }
+  if (nan) atomicOr(bad, 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+__global__ void k_sel_pick(SelState* st, int shift, unsigned int* hist) {
+  if (threadIdx.x == 0) {
+    unsigned long long above = 0;
+    int d = 255;
+    for (; d > 0; --d) {
+      if (above + hist[d] >= st->want) break;
+      above += hist[d];
+    }
+    st->want -= above;
+    st->prefix |= static_cast<unsigned long long>(d) << shift;
+    st->mask |= 255ull << shift;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+}
+
+// Sum and count of the values whose key exceeds the selected key.
+__global__ void k_sel_tail(const double* ylt, int64_t n, const SelState* st, double* part_sum,
+                           unsigned long long* part_cnt) {
+  __shared__ double s_sum[kSelThreads / 32];
+  __shared__ unsigned long long s_cnt[kSelThreads / 32];
+  const unsigned long long kth = st->prefix;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  double sum = 0.0;
+  unsigned long long cnt = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+    const double v = ylt[i];
+    if (key_of(v) > kth) {
+      sum += v;
+      ++cnt;
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    sum += __shfl_down_sync(0xffffffffu, sum, d);
+    cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_sum[threadIdx.x >> 5] = sum;
+    s_cnt[threadIdx.x >> 5] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    unsigned long long c = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) {
+      t += s_sum[w];
+      c += s_cnt[w];
+    }
+    part_sum[blockIdx.x] = t;
+    part_cnt[blockIdx.x] = c;
+  }
+}
+
+__global__ void k_sel_finish(const SelState* st, const double* part_sum, const unsigned long long* part_cnt,
+                             int n_parts, double* pml, double* tvar) {
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    unsigned long long c = 0;
+    for (int i = 0; i < n_parts; ++i) {
+      s += part_sum[i];
+      c += part_cnt[i];
+    }
+    const double v = value_of(st->prefix);
+    const unsigned long long m = st->m;
+    *pml = v;
+    *tvar = (s + static_cast<double>(m - c) * v) / static_cast<double>(m);
+  }
+}
+
+}  // namespace
+
+size_t select_scratch_bytes(int64_t /*n*/) {
+  return sizeof(SelState) + 256 * sizeof(unsigned int) + kSelBlocks * (sizeof(double) + sizeof(unsigned long long)) +
+         64;
+}
+
+cudaError_t pml_tvar_device(const double* ylt, int64_t n, const double* rps_host, int32_t n_rp, double* pml,
+                            double* tvar, void* scratch, cudaStream_t s, int* n_launch) {
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  SelState* st = reinterpret_cast<SelState*>(base);
+  unsigned int* hist = reinterpret_cast<unsigned int*>(base + sizeof(SelState));
+  double* part_sum = reinterpret_cast<double*>(base + sizeof(SelState) + 256 * sizeof(unsigned int));
+  unsigned long long* part_cnt = reinterpret_cast<unsigned long long*>(part_sum + kSelBlocks);
+  int64_t blocks = (n + kSelThreads - 1) / kSelThreads;
+  const int grid = static_cast<int>(blocks < kSelBlocks ? blocks : kSelBlocks);
+  for (int32_t r = 0; r < n_rp; ++r) {
+    int64_t m = static_cast<int64_t>(std::ceil(static_cast<double>(n) / rps_host[r]));
+    if (m < 1) m = 1;
+    if (m > n) m = n;
+    k_sel_init<<<1, 256, 0, s>>>(st, static_cast<unsigned long long>(m), hist);
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, st, shift, hist, &st->bad);
+      k_sel_pick<<<1, 256, 0, s>>>(st, shift, hist);
+    }
+    k_sel_tail<<<grid, kSelThreads, 0, s>>>(ylt, n, st, part_sum, part_cnt);
+    k_sel_finish<<<1, 32, 0, s>>>(st, part_sum, part_cnt, grid, pml + r, tvar + r);
+    if (n_launch) *n_launch += 19;
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+// =============================================================== LSD radix sort (descending)
+namespace {
+
+constexpr int kSortThreads = 1024;  // one key per thread per tile
+
+__global__ void k_sort_keys(const double* ylt, int64_t n, unsigned long long* keys, int64_t* idx) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+    keys[i] = ~key_of(ylt[i]);  // ascending order of ~key = descending year loss
+    idx[i] = i;
+  }
+}
+
+__global__ void k_sort_count(const unsigned long long* keys, int64_t n, int shift, unsigned int* counts,
+                             int n_tiles) {
+  __shared__ unsigned int sh[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * kSortThreads + threadIdx.x;
+  if (i < n) atomicAdd(&sh[(keys[i] >> shift) & 255u], 1u);
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) counts[static_cast<int64_t>(d) * n_tiles + blockIdx.x] = sh[d];
+}
+
+__global__ void k_sort_scatter(const unsigned long long* keys_in, const int64_t* idx_in, int64_t n, int shift,
+                               const unsigned int* offsets, int n_tiles, unsigned long long* keys_out,
+                               int64_t* idx_out) {
+  __shared__ unsigned int s_wc[32][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < 32 * 256; i += blockDim.x) (&s_wc[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * kSortThreads + threadIdx.x;
+  const bool valid = i < n;
+  const unsigned long long key = valid ? keys_in[i] : 0ull;
+  const unsigned int d = valid ? static_cast<unsigned int>((key >> shift) & 255u) : 256u;
+  const unsigned int peers = __match_any_sync(0xffffffffu, d);
+  const unsigned int rank = __popc(peers & ((1u << lane) - 1u));
+  if (valid && rank == 0) s_wc[warp][d] = __popc(peers);
+  __syncthreads();
+  if (threadIdx.x < 256) {
+    const int dd = threadIdx.x;
+    unsigned int run = offsets[static_cast<int64_t>(dd) * n_tiles + blockIdx.x];
+    for (int w = 0; w < 32; ++w) {
+      const unsigned int c = s_wc[w][dd];
+      s_wc[w][dd] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (valid) {
+    const unsigned int dst = s_wc[warp][d] + rank;
+    keys_out[dst] = key;
+    idx_out[dst] = idx_in[i];
+  }
+}
+
+}  // namespace
+
+size_t sort_scratch_bytes(int64_t n) {
+  const int64_t tiles = (n + kSortThreads - 1) / kSortThreads;
+  const int64_t cnt = 256 * tiles;
+  return static_cast<size_t>(n) * (2 * sizeof(unsigned long long) + sizeof(int64_t)) +
+         sizeof(unsigned int) * (2 * static_cast<size_t>(cnt) + 1 + scan_tmp_words(cnt)) + 256;
+}
+
+cudaError_t sort_desc_device(const double* ylt, int64_t n, int64_t* order, void* scratch, cudaStream_t s,
+                             int* n_launch) {
+  const int64_t tiles = (n + kSortThreads - 1) / kSortThreads;
+  const int64_t cnt = 256 * tiles;
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  unsigned long long* keys_a = reinterpret_cast<unsigned long long*>(base);
+  unsigned long long* keys_b = keys_a + n;
+  int64_t* idx_b = reinterpret_cast<int64_t*>(keys_b + n);
+  unsigned int* counts = reinterpret_cast<unsigned int*>(idx_b + n);
+  unsigned int* offsets = counts + cnt;
+  unsigned int* tmp = offsets + cnt + 1;
+  // the final pass must land in `order`; with 8 passes the ping-pong ends where it started
+  int64_t* idx_a = order;
+  const int grid = static_cast<int>((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
+  k_sort_keys<<<grid, 256, 0, s>>>(ylt, n, keys_a, idx_a);
+  if (n_launch) *n_launch += 1 + 8 * 2;
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  unsigned long long *ki = keys_a, *ko = keys_b;
+  int64_t *ii = idx_a, *io = idx_b;
+  for (int shift = 0; shift < 64; shift += 8) {
+    k_sort_count<<<static_cast<int>(tiles), kSortThreads, 0, s>>>(ki, n, shift, counts, static_cast<int>(tiles));
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if ((err = scan_exclusive_u32(counts, offsets, cnt, tmp, s, n_launch)) != cudaSuccess) return err;
+    k_sort_scatter<<<static_cast<int>(tiles), kSortThreads, 0, s>>>(ki, ii, n, shift, offsets,
+                                                                   static_cast<int>(tiles), ko, io);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    unsigned long long* tk = ki;
+    ki = ko;
+    ko = tk;
+    int64_t* ti = ii;
+    ii = io;
+    io = ti;
+  }
+  return cudaSuccess;  // 8 swaps: the result is back in idx_a == order
+}
+
+}  // namespace ara
