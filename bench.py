@@ -360,7 +360,8 @@ def run_gpu(args):
             "clocks": clocks.summary(),
             "stats": {"index_ms": tm["index_ms"] / max(tm["layer_calls"], 1),
                       "pml_ms": tm["pml_ms"] / max(tm["pml_calls"], 1), "pairs_hit": st["n_pairs_hit"],
-                      "nonconverged": st["n_nonconverged"], "grid": st["grid"], "block": st["block"],
+                      "nonconverged": st["n_nonconverged"], "newton_pairs": st["n_newton"],
+                      "grid": st["grid"], "block": st["block"],
                       "smem_bytes": st["smem_bytes"], "filter_bits": st["filter_bits"]},
         }
         if global_pml is not None:

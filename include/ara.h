@@ -63,6 +63,7 @@ extern "C" {
 
 /* Layer flags */
 #define ARA_PRIMARY_ONLY 1u /* no secondary uncertainty: every record's loss is its mean */
+#define ARA_NEWTON_ONLY 2u  /* invert every Beta by the FP32 Halley iteration, not the record's quantile table */
 
 typedef struct ara_ctx ara_ctx;
 
@@ -87,7 +88,7 @@ typedef struct {
     double occ_limit;
     double agg_retention;
     double agg_limit;
-    uint32_t flags; /* ARA_PRIMARY_ONLY or 0 */
+    uint32_t flags; /* ARA_PRIMARY_ONLY, ARA_NEWTON_ONLY or 0 */
 } ara_layer;
 
 /* Optional per-trial diagnostics of ara_run_layer_diag(); any pointer may be
@@ -103,6 +104,7 @@ typedef struct {
     int64_t n_evals;         /* n_events x n_elts: trial-event-ELT evaluations */
     int64_t n_pairs_hit;     /* (event, ELT) lookups that found a record */
     int64_t n_nonconverged;  /* Beta inversions that hit the iteration cap */
+    int64_t n_newton;        /* pairs inverted by the Halley iteration (not the table alone) */
     float index_ms;          /* per-layer index build, device time */
     float kernel_ms;         /* main layer kernel, device time */
     int32_t grid;            /* CTAs of the main kernel */
@@ -148,7 +150,9 @@ ARA_API int ara_load_yet(ara_ctx *ctx, int64_t n_trials, const int64_t *offsets,
  * (no secondary uncertainty).  `terms` (n_elts entries, NULL: identity) are
  * the ELT financial terms.  Loading a pool id that is already resident
  * replaces it.  The Beta shapes of every record are derived here (Section
- * 3.4), once per record.
+ * 3.4), once per record, together with a 32-node quantile table of each
+ * record's Beta built in FP64 (512 bytes per record).  At most 2^23 - 1
+ * records per ELT.
  * Errors: ARA_EINVAL (unsorted or duplicate ids, negative or non-finite
  * values, exposure <= mean), ARA_ENOMEM, ARA_ECUDA. */
 ARA_API int ara_load_elts(ara_ctx *ctx, int32_t n_elts, const int32_t *elt_ids, const int64_t *rec_offsets,
@@ -196,15 +200,18 @@ ARA_API int ara_sort_ylt(ara_ctx *ctx, const double *ylt, int64_t n, int64_t *or
  * ara_debug_record_losses: for n XELT records (mean, sigma, exposure) and
  * uniforms z (FP32, in (0, 1)), out[i] = the secondary-uncertainty loss
  * max_l * InvCDF_beta(z[i]; alpha_i, beta_i) (Section 3.4) computed with the
- * same record preparation and FP32 inverse as ara_run_layer (the mean for
- * sigma == 0, 0 for mean == 0).  iters_out (NULL allowed) receives the
- * iteration count of each inversion (negative: hit the iteration cap).
+ * same record preparation, quantile table and FP32 inverse as
+ * ara_run_layer (the mean for sigma == 0, 0 for mean == 0); newton_only != 0
+ * uses the Halley iteration for every record, as ARA_NEWTON_ONLY does.
+ * iters_out (NULL allowed) receives the Halley iteration count of each
+ * inversion (0: the table alone; negative: hit the iteration cap).
  * All arrays may be host or device memory.  Errors: ARA_EINVAL, ARA_ENOMEM,
  * ARA_ECUDA. */
 ARA_API int ara_debug_uniforms(ara_ctx *ctx, uint64_t seed, int64_t n, const int64_t *trials, const int32_t *ks,
                                const int32_t *elts, float *out);
 ARA_API int ara_debug_record_losses(ara_ctx *ctx, int64_t n, const float *mean, const float *sigma,
-                                    const float *exposure, const float *z, float *out, int32_t *iters_out);
+                                    const float *exposure, const float *z, int32_t newton_only, float *out,
+                                    int32_t *iters_out);
 
 /* Counters of the last ara_run_layer* call. */
 ARA_API int ara_get_stats(const ara_ctx *ctx, ara_stats *out);

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libara.so")
 
 ARA_OK, ARA_EINVAL, ARA_ENOMEM, ARA_ENOTLOADED, ARA_ECUDA, ARA_ETIMEOUT = 0, -1, -2, -3, -4, -5
 ARA_PRIMARY_ONLY = 1
+ARA_NEWTON_ONLY = 2
 ARA_MAX_LAYER_ELTS = 32
 _ERR_NAMES = {
     ARA_EINVAL: "ARA_EINVAL", ARA_ENOMEM: "ARA_ENOMEM", ARA_ENOTLOADED: "ARA_ENOTLOADED",
@@ -71,6 +72,7 @@ class Stats(ctypes.Structure):
         ("n_evals", ctypes.c_int64),
         ("n_pairs_hit", ctypes.c_int64),
         ("n_nonconverged", ctypes.c_int64),
+        ("n_newton", ctypes.c_int64),
         ("index_ms", ctypes.c_float),
         ("kernel_ms", ctypes.c_float),
         ("grid", ctypes.c_int32),
@@ -118,7 +120,7 @@ def load_library(path: str = LIB_PATH):
     lib.ara_pml_tvar.argtypes = [P, P, i64, P, i32, P, P]
     lib.ara_sort_ylt.argtypes = [P, P, i64, P]
     lib.ara_debug_uniforms.argtypes = [P, u64, i64, P, P, P, P]
-    lib.ara_debug_record_losses.argtypes = [P, i64, P, P, P, P, P, P]
+    lib.ara_debug_record_losses.argtypes = [P, i64, P, P, P, P, i32, P, P]
     lib.ara_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
     lib.ara_get_timing.argtypes = [P, ctypes.POINTER(Timing), ctypes.c_int]
     lib.ara_last_error.argtypes = [P]
@@ -209,10 +211,11 @@ def ara_debug_uniforms(h, seed, n, trials, ks, elts, out):
                                              _ptr(elts, np.int32), _ptr(out, np.float32))
 
 
-def ara_debug_record_losses(h, n, mean, sigma, exposure, z, out, iters_out=None):
+def ara_debug_record_losses(h, n, mean, sigma, exposure, z, newton_only, out, iters_out=None):
     return load_library().ara_debug_record_losses(h, int(n), _ptr(mean, np.float32), _ptr(sigma, np.float32),
                                                   _ptr(exposure, np.float32), _ptr(z, np.float32),
-                                                  _ptr(out, np.float32), _ptr(iters_out, np.int32))
+                                                  int(newton_only), _ptr(out, np.float32),
+                                                  _ptr(iters_out, np.int32))
 
 
 def ara_get_stats(h, out: Stats):
@@ -283,16 +286,17 @@ class Ara:
                        pool.terms)
 
     @staticmethod
-    def make_layer(elt_ids: Sequence[int], layer_terms, primary_only: bool = False):
+    def make_layer(elt_ids: Sequence[int], layer_terms, primary_only: bool = False, newton_only: bool = False):
         ids = (ctypes.c_int32 * len(elt_ids))(*[int(i) for i in elt_ids])
         occ_r, occ_l, agg_r, agg_l = (float(v) for v in layer_terms)
-        lay = Layer(len(elt_ids), ids, occ_r, occ_l, agg_r, agg_l, ARA_PRIMARY_ONLY if primary_only else 0)
+        flags = (ARA_PRIMARY_ONLY if primary_only else 0) | (ARA_NEWTON_ONLY if newton_only else 0)
+        lay = Layer(len(elt_ids), ids, occ_r, occ_l, agg_r, agg_l, flags)
         lay._ids = ids  # keep the id array alive with the struct
         return lay
 
     def run_layer(self, elt_ids, layer_terms, seed: int, trial_begin: int, trial_end: int, ylt_out,
-                  primary_only: bool = False, hits_out=None, hash_out=None) -> None:
-        lay = self.make_layer(elt_ids, layer_terms, primary_only)
+                  primary_only: bool = False, hits_out=None, hash_out=None, newton_only: bool = False) -> None:
+        lay = self.make_layer(elt_ids, layer_terms, primary_only, newton_only)
         if hits_out is None and hash_out is None:
             self._check(ara_run_layer(self._h, lay, seed, trial_begin, trial_end, ylt_out))
         else:
@@ -319,14 +323,14 @@ class Ara:
         self._check(ara_debug_uniforms(self._h, seed, t.shape[0], t, k, e, out))
         return out
 
-    def debug_record_losses(self, mean, sigma, exposure, z):
+    def debug_record_losses(self, mean, sigma, exposure, z, newton_only: bool = False):
         mu = np.ascontiguousarray(mean, np.float32)
         sg = np.ascontiguousarray(sigma, np.float32)
         ex = np.ascontiguousarray(exposure, np.float32)
         zz = np.ascontiguousarray(z, np.float32)
         out = np.zeros(mu.shape[0], np.float32)
         iters = np.zeros(mu.shape[0], np.int32)
-        self._check(ara_debug_record_losses(self._h, mu.shape[0], mu, sg, ex, zz, out, iters))
+        self._check(ara_debug_record_losses(self._h, mu.shape[0], mu, sg, ex, zz, int(newton_only), out, iters))
         return out, iters
 
     def stats(self) -> dict:

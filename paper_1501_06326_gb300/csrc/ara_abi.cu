@@ -24,6 +24,7 @@ struct DevBuf {
 struct Elt {
   DevBuf events;  // int32 [n] (+ padding)
   DevBuf recs;    // ara::Pair [n]
+  DevBuf tab;     // float4 [n * kTabNodes] quantile tables
   int64_t n = 0;
   int32_t max_event = -1;
   ara_elt_terms terms{0.0f, INFINITY, 1.0f};
@@ -272,13 +273,19 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     return fail(c, ARA_EINVAL, "ara_load_elts: record arrays are NULL");
   // stage all records on the device once, then split per ELT
   const int64_t R = offs[n_elts];
+  for (int32_t i = 0; i < n_elts; ++i)
+    if (offs[i + 1] - offs[i] >= static_cast<int64_t>(ara::kMaxEltRecords))
+      return fail(c, ARA_EINVAL, "ara_load_elts: ELT %d has %lld records (at most %u)", ids[i],
+                  (long long)(offs[i + 1] - offs[i]), ara::kMaxEltRecords - 1);
   DevBuf stage;
-  const size_t stage_bytes = static_cast<size_t>(R) * (sizeof(int32_t) + 3 * sizeof(float)) + 64;
+  const size_t stage_bytes = static_cast<size_t>(R) * (sizeof(int32_t) + 3 * sizeof(float) + sizeof(double2)) + 64;
   if ((rc = reserve(c, stage, stage_bytes))) return rc;
   int32_t* d_ev = static_cast<int32_t*>(stage.ptr);
   float* d_mu = reinterpret_cast<float*>(d_ev + R);
   float* d_sg = d_mu + R;
   float* d_ex = d_sg + R;
+  double2* d_shapes = reinterpret_cast<double2*>(
+      (reinterpret_cast<uintptr_t>(d_ex + R) + 15) & ~uintptr_t(15));
   auto cleanup = [&](int code) {
     release(c, stage);
     return code;
@@ -300,10 +307,12 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     el.n = offs[i + 1] - offs[i];
     el.terms = tm[i];
     if ((rc = reserve(c, el.events, sizeof(int32_t) * (el.n + 4))) ||
-        (rc = reserve(c, el.recs, sizeof(ara::Pair) * (el.n > 0 ? el.n : 1)))) {
+        (rc = reserve(c, el.recs, sizeof(ara::Pair) * (el.n > 0 ? el.n : 1))) ||
+        (rc = reserve(c, el.tab, sizeof(float4) * ara::kTabNodes * (el.n > 0 ? el.n : 1)))) {
       for (auto& f : fresh) {
         release(c, f.events);
         release(c, f.recs);
+        release(c, f.tab);
       }
       return cleanup(rc);
     }
@@ -313,7 +322,12 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
       e = cudaMemcpyAsync(el.events.ptr, d_ev + offs[i], sizeof(int32_t) * el.n, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess)
       e = ara::launch_prepare_records(d_ev + offs[i], d_mu + offs[i], d_sg + offs[i], d_ex + offs[i], el.n,
-                                      static_cast<ara::Pair*>(el.recs.ptr), flags, max_ev, c->stream);
+                                      static_cast<ara::Pair*>(el.recs.ptr), d_shapes + offs[i], flags, max_ev,
+                                      c->stream);
+    if (e == cudaSuccess)
+      e = ara::launch_build_tables(static_cast<ara::Pair*>(el.recs.ptr), d_shapes + offs[i], el.n,
+                                   static_cast<float4*>(el.tab.ptr), c->stream);
+    c->launches += 2;
     uint32_t hf[2] = {0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -339,6 +353,7 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
       for (auto& f : fresh) {
         release(c, f.events);
         release(c, f.recs);
+        release(c, f.tab);
       }
       return cleanup(fail(c, bad, "ara_load_elts: ELT %d: %s", ids[i], why));
     }
@@ -349,6 +364,7 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     if (it != c->pool.end()) {
       release(c, it->second.events);
       release(c, it->second.recs);
+      release(c, it->second.tab);
       c->pool.erase(it);
     }
     c->pool[ids[i]] = fresh[i];
@@ -389,6 +405,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
     refs.recs[i] = static_cast<const ara::Pair*>(el.recs.ptr);
     refs.rec_begin[i + 1] = refs.rec_begin[i] + el.n;
     p.elt_id[i] = ids[i];
+    p.tab[i] = static_cast<const float4*>(el.tab.ptr);
     p.t_ret[i] = el.terms.retention;
     p.t_lim[i] = el.terms.limit;
     p.t_share[i] = el.terms.share;
@@ -470,6 +487,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   p.seed_lo = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
   p.seed_hi = static_cast<uint32_t>(seed >> 32);
   p.primary_only = (L->flags & ARA_PRIMARY_ONLY) ? 1 : 0;
+  p.newton_only = (L->flags & ARA_NEWTON_ONLY) ? 1 : 0;
   p.n_tiles = static_cast<int32_t>(n_tiles);
   p.ylt = d_ylt;
   p.diag_hits = d_hits;
@@ -528,6 +546,7 @@ int ara_get_stats(const ara_ctx* cc, ara_stats* out) {
     ARA_CUDA(c, cudaMemcpy(h, c->counters.ptr, sizeof h, cudaMemcpyDeviceToHost));
     c->stats.n_pairs_hit = static_cast<int64_t>(h[1]);
     c->stats.n_nonconverged = static_cast<int64_t>(h[2]);
+    c->stats.n_newton = static_cast<int64_t>(h[3]);
   }
   *out = c->stats;
   return ARA_OK;
@@ -654,14 +673,17 @@ int ara_debug_uniforms(ara_ctx* c, uint64_t seed, int64_t n, const int64_t* tria
 }
 
 int ara_debug_record_losses(ara_ctx* c, int64_t n, const float* mean, const float* sigma, const float* exposure,
-                            const float* z, float* out, int32_t* iters_out) {
+                            const float* z, int32_t newton_only, float* out, int32_t* iters_out) {
   int rc = bind(c);
   if (rc) return rc;
   if (n < 0 || (n > 0 && (!mean || !sigma || !exposure || !z || !out)))
     return fail(c, ARA_EINVAL, "ara_debug_record_losses: bad arguments");
   if (n == 0) return ARA_OK;
   DevBuf tmp;
-  const size_t bytes = static_cast<size_t>(n) * (sizeof(ara::Pair) + 6 * sizeof(float) + sizeof(int32_t)) + 64;
+  if (n >= static_cast<int64_t>(ara::kMaxEltRecords))
+    return fail(c, ARA_EINVAL, "ara_debug_record_losses: at most %u records per call", ara::kMaxEltRecords - 1);
+  const size_t bytes = static_cast<size_t>(n) * (sizeof(ara::Pair) + 6 * sizeof(float) + sizeof(int32_t) +
+                                                 sizeof(double2) + sizeof(float4) * ara::kTabNodes) + 128;
   if ((rc = reserve(c, tmp, bytes))) return rc;
   ara::Pair* d_p = static_cast<ara::Pair*>(tmp.ptr);
   float* d_mu = reinterpret_cast<float*>(d_p + n);
@@ -671,6 +693,8 @@ int ara_debug_record_losses(ara_ctx* c, int64_t n, const float* mean, const floa
   float* d_o = d_z + n;
   int32_t* d_ev = reinterpret_cast<int32_t*>(d_o + n);
   int32_t* d_it = d_ev + n;
+  double2* d_sh = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(d_it + n) + 15) & ~uintptr_t(15));
+  float4* d_tab = reinterpret_cast<float4*>(d_sh + n);
   uint32_t* flags = static_cast<uint32_t*>(c->flags.ptr);
   int32_t* max_ev = reinterpret_cast<int32_t*>(flags + 1);
   cudaError_t e = cudaMemcpyAsync(d_mu, mean, sizeof(float) * n, cudaMemcpyDefault, c->stream);
@@ -682,9 +706,10 @@ int ara_debug_record_losses(ara_ctx* c, int64_t n, const float* mean, const floa
   for (int64_t i = 0; i < n; ++i) ev[i] = static_cast<int32_t>(i);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_ev, ev.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 2 * sizeof(uint32_t), c->stream);
-  if (e == cudaSuccess) e = ara::launch_prepare_records(d_ev, d_mu, d_sg, d_ex, n, d_p, flags, max_ev, c->stream);
-  if (e == cudaSuccess) e = ara::launch_debug_losses(d_p, d_z, n, d_o, d_it, c->stream);
-  c->launches += 2;
+  if (e == cudaSuccess) e = ara::launch_prepare_records(d_ev, d_mu, d_sg, d_ex, n, d_p, d_sh, flags, max_ev, c->stream);
+  if (e == cudaSuccess) e = ara::launch_build_tables(d_p, d_sh, n, d_tab, c->stream);
+  if (e == cudaSuccess) e = ara::launch_debug_losses(d_p, d_tab, d_z, n, newton_only, d_o, d_it, c->stream);
+  c->launches += 3;
   uint32_t hf = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_o, sizeof(float) * n, cudaMemcpyDefault, c->stream);
@@ -710,6 +735,7 @@ void ara_destroy(ara_ctx* c) {
   for (auto& kv : c->pool) {
     release(c, kv.second.events);
     release(c, kv.second.recs);
+    release(c, kv.second.tab);
   }
   DevBuf* bufs[] = {&c->yet_off, &c->yet_ids, &c->bits,  &c->word_cnt, &c->rankdir, &c->mask,   &c->slot_cnt,
                     &c->pairs,   &c->scan_tmp, &c->flags, &c->counters, &c->ylt_tmp, &c->diag_tmp, &c->sel,

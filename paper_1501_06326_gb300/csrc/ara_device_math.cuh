@@ -20,6 +20,15 @@
 // I_r(A, B) = 1 - I_{1-r}(B, A) past r = (A + 1)/(A + B + 2).  The starting
 // point is Carter's normal approximation (Abramowitz & Stegun 26.5.22) for
 // A, B >= 1 and the small-x / small-(1-x) power laws otherwise.
+//
+// Quantile tables.  Each record also carries a table of its quantile built in
+// FP64 at load time: kTabNodes nodes uniform in t = Phi^-1(z) over
+// [Phi^-1(2^-24), Phi^-1(1 - 2^-24)] (the whole range of the uniform grid),
+// with w = ln x, dw/dt and d2w/dt2 at each node.  Between nodes w follows the
+// quintic Hermite interpolant, evaluated as x = x_i exp(w - w_i) so that x
+// keeps FP32 relative precision.  Records whose table reproduces the FP64
+// quantile to kTabTol (checked at load at three points per segment) use the
+// table alone; the others start the Halley iteration from the table's value.
 #pragma once
 
 #include <cstdint>
@@ -42,13 +51,24 @@ struct __align__(16) Pair {
   float max_l;    // exposure (maximum loss)
   float mu;       // mean loss
   float p_half;   // I_{1/2}(a, b)
-  uint32_t meta;  // bits 0-4 layer position, 5-6 kind, 7: m0 is x0
+  uint32_t meta;  // bits 0-4 layer position, 5-6 kind, 7: m0 is x0, 8: table exact, 9-31 record index
 };
 static_assert(sizeof(Pair) == 32, "Pair must be one 32-byte sector");
+
+constexpr uint32_t kMaxEltRecords = 1u << 23;  // record index field of meta
 
 __host__ __device__ inline uint32_t pair_pos(uint32_t meta) { return meta & 31u; }
 __host__ __device__ inline uint32_t pair_kind(uint32_t meta) { return (meta >> 5) & 3u; }
 __host__ __device__ inline bool pair_m0_is_x0(uint32_t meta) { return (meta >> 7) & 1u; }
+__host__ __device__ inline bool pair_tab_exact(uint32_t meta) { return (meta >> 8) & 1u; }
+__host__ __device__ inline uint32_t pair_rec(uint32_t meta) { return meta >> 9; }
+
+// ------------------------------------------------------------------ tables
+constexpr int kTabNodes = 32;
+constexpr double kTabT1 = 5.294704084854597;  // Phi^-1(1 - 2^-24)
+constexpr float kTabT1f = 5.294704f;
+constexpr float kTabInvH = static_cast<float>((kTabNodes - 1) / (2.0 * kTabT1));
+constexpr float kTabTol = 5e-7f;  // relative error allowed to the table alone
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -142,21 +162,52 @@ __device__ __forceinline__ float beta_cf(float A, float B, float x, int max_term
   return 1.0f / K;
 }
 
+// Quintic Hermite weights on [0, 1] for the increment w(s) - w_0 given the
+// node data (x_i, w_{i+1} - w_i, h w'_i, h^2 w''_i) and (h w'_{i+1}, h^2 w''_{i+1}).
+__device__ __forceinline__ float tab_increment(float s, float dw, float d0, float e0, float d1, float e1) {
+  const float s2 = s * s, s3 = s2 * s;
+  const float g0 = s3 * fmaf(s, fmaf(6.0f, s, -15.0f), 10.0f);                // 10s^3 - 15s^4 + 6s^5
+  const float h1 = s * fmaf(s2, fmaf(s, fmaf(-3.0f, s, 8.0f), -6.0f), 1.0f);  // s - 6s^3 + 8s^4 - 3s^5
+  const float g1 = s3 * fmaf(s, fmaf(-3.0f, s, 7.0f), -4.0f);                 // -4s^3 + 7s^4 - 3s^5
+  const float h2 = 0.5f * s2 * fmaf(s, fmaf(s, 3.0f - s, -3.0f), 1.0f);       // (s^2 - 3s^3 + 3s^4 - s^5)/2
+  const float g2 = 0.5f * s3 * fmaf(s, s - 2.0f, 1.0f);                       // (s^3 - 2s^4 + s^5)/2
+  return fmaf(dw, g0, fmaf(d0, h1, fmaf(d1, g1, fmaf(e0, h2, e1 * g2))));
+}
+
+// x = InvCDF_beta(z) from a record's table (nodes are float4 {x_i, w_{i+1} - w_i,
+// h w'_i, h^2 w''_i}).
+__device__ __forceinline__ float tab_quantile(const float4* __restrict__ tab, float z) {
+  const float t = normcdfinvf(z);
+  float u = (t + kTabT1f) * kTabInvH;
+  u = fminf(fmaxf(u, 0.0f), static_cast<float>(kTabNodes - 1));
+  int i = static_cast<int>(u);
+  if (i > kTabNodes - 2) i = kTabNodes - 2;
+  const float s = u - static_cast<float>(i);
+  const float4 n0 = __ldg(tab + i);
+  if (!(n0.x > 0.0f)) return 0.0f;  // below the FP32 range
+  const float2 n1 = __ldg(reinterpret_cast<const float2*>(tab + i + 1) + 1);
+  return n0.x * expf(tab_increment(s, n0.y, n0.z, n0.w, n1.x, n1.y));
+}
+
 struct BetaSolveStats {
   int iters;
   int cf_terms;
   bool converged;
 };
 
-// Root r of I_r(A, B) = P, r expected in (0, ~1/2].  lnA = ln A,
-// lnP = ln P; x0 = A/(A+B), y0 = B/(A+B); C as above.
-__device__ __forceinline__ float beta_solve_oriented(float A, float B, float x0, float y0, float C, float P,
-                                                     BetaSolveStats* st) {
-  const float lnP = logf(P);
+// Root r of I_r(A, B) = P, r expected in (0, ~1/2].  The caller passes
+// lnP = ln P and ln1mP = ln(1 - P), each computed from the uniform itself so
+// that neither loses the precision of a small P or a small 1 - P;
+// x0 = A/(A+B), y0 = B/(A+B); C as above.
+__device__ __forceinline__ float beta_solve_oriented(float A, float B, float x0, float y0, float C, float lnP,
+                                                     float ln1mP, float r_start, BetaSolveStats* st) {
+  const float P = expf(lnP);
   const float lnA = logf(A);
   // ------------------------------------------------------------ start point
   float r;
-  if (A >= 1.0f && B >= 1.0f) {
+  if (r_start > 0.0f && r_start < 1.0f) {
+    r = r_start;
+  } else if (A >= 1.0f && B >= 1.0f) {
     // Carter (A&S 26.5.22): y is the upper-tail normal deviate of P
     const float y = -normcdfinvf(P);
     const float lam = (y * y - 3.0f) * (1.0f / 6.0f);
@@ -171,7 +222,7 @@ __device__ __forceinline__ float beta_solve_oriented(float A, float B, float x0,
     if (rl < x0) {
       r = rl;
     } else {
-      const float ru = 1.0f - expf((log1pf(-P) + logf(B) + lnB) / B);
+      const float ru = 1.0f - expf((ln1mP + logf(B) + lnB) / B);
       r = (ru > x0 && ru < 1.0f) ? ru : x0;
     }
   }
@@ -204,15 +255,20 @@ __device__ __forceinline__ float beta_solve_oriented(float A, float B, float x0,
     const float curv = A - (B - 1.0f) * r / (1.0f - r) - g;
     const float denom = fmaf(0.5f * newton, curv, 1.0f);
     float du = (denom > 0.5f && denom < 2.0f) ? newton / denom : newton;
+    if (fabsf(du) < 4e-4f) {
+      // converged (Halley: the remaining error is O(du^3)); near the root F
+      // carries FP32 rounding noise, so the bracket no longer decides
+      r = fmaf(r, expm1f(du), r);
+      done = true;
+      ++it;
+      break;
+    }
     du = fminf(fmaxf(du, -80.0f), 80.0f);
     float rn = r * expf(du);
-    bool bisect = false;
     if (!(rn > rlo && rn < rhi)) {
       const float lo = fmaxf(rlo, 1e-37f);
       rn = (rhi > 4.0f * lo) ? sqrtf(lo) * sqrtf(rhi) : 0.5f * (rlo + rhi);
-      bisect = true;
     }
-    if (!bisect && fabsf(du) < 4e-4f) { r = rn; done = true; ++it; break; }
     if (rn == r) { done = true; ++it; break; }
     r = rn;
     if (rhi <= 1e-37f) { done = true; ++it; break; }  // root below the FP32 normal range
@@ -223,26 +279,37 @@ __device__ __forceinline__ float beta_solve_oriented(float A, float B, float x0,
   return r;
 }
 
+// InvCDF_beta(z; a, b) of a Beta record by the FP32 Halley iteration; x_start
+// in (0, 1) seeds it (otherwise the analytic start point is used).
+__device__ __forceinline__ float pair_quantile_newton(const Pair& p, float z, float x_start, BetaSolveStats* st) {
+  const bool m0x = pair_m0_is_x0(p.meta);
+  const float x0 = m0x ? p.m0 : 1.0f - p.m0;
+  const float y0 = m0x ? 1.0f - p.m0 : p.m0;
+  const float lnz = logf(z), ln1mz = log1pf(-z);
+  if (z <= p.p_half) return beta_solve_oriented(p.a, p.b, x0, y0, p.c, lnz, ln1mz, x_start, st);
+  // root above 1/2: 1 - x solves I_{1-x}(b, a) = 1 - z
+  const float y_start = (x_start > 0.0f && x_start < 1.0f) ? 1.0f - x_start : -1.0f;
+  return 1.0f - beta_solve_oriented(p.b, p.a, y0, x0, p.c, ln1mz, lnz, y_start, st);
+}
+
 // Loss of one pair: max_l * InvCDF(z; a, b) for Beta records, the mean for
 // sigma == 0 records (and for every record when primary_only), 0 for
-// mean == 0 records.
-__device__ __forceinline__ float pair_loss(const Pair& p, float z, bool primary_only, BetaSolveStats* st) {
+// mean == 0 records.  `tab` (may be null) is the record's quantile table;
+// newton_only forces the Halley iteration for every Beta record.
+__device__ __forceinline__ float pair_loss(const Pair& p, float z, bool primary_only, const float4* tab,
+                                           bool newton_only, BetaSolveStats* st) {
   const uint32_t kind = pair_kind(p.meta);
   st->iters = 0;
   st->cf_terms = 0;
   st->converged = true;
   if (kind == kKindZero) return 0.0f;
   if (primary_only || kind == kKindMean) return p.mu;
-  const bool m0x = pair_m0_is_x0(p.meta);
-  const float x0 = m0x ? p.m0 : 1.0f - p.m0;
-  const float y0 = m0x ? 1.0f - p.m0 : p.m0;
-  if (z <= p.p_half) {
-    const float r = beta_solve_oriented(p.a, p.b, x0, y0, p.c, z, st);
-    return p.max_l * r;
+  if (tab != nullptr && !newton_only) {
+    const float x = tab_quantile(tab, z);
+    if (pair_tab_exact(p.meta)) return p.max_l * x;
+    return p.max_l * pair_quantile_newton(p, z, x, st);
   }
-  // root above 1/2: 1 - x solves I_{1-x}(b, a) = 1 - z (exact in FP32)
-  const float r = beta_solve_oriented(p.b, p.a, y0, x0, p.c, 1.0f - z, st);
-  return p.max_l * (1.0f - r);
+  return p.max_l * pair_quantile_newton(p, z, -1.0f, st);
 }
 
 // fmix64 finaliser (MurmurHash3), for the order-free hit-list checksum.

@@ -28,14 +28,18 @@ cudaError_t launch_check_ids(const int32_t* ids, int64_t n, int32_t catalogue, u
 // Beta shapes, x0/y0, C, I_{1/2}(a, b), kind.  Also checks order and values
 // and reduces the largest event id into *max_event (atomicMax).
 cudaError_t launch_prepare_records(const int32_t* events, const float* mean, const float* sigma,
-                                   const float* exposure, int64_t n, Pair* out, uint32_t* flags,
+                                   const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
                                    int32_t* max_event, cudaStream_t s);
+
+// Quantile tables of prepared records (kTabNodes float4 per record), built in
+// FP64; sets the table-exact bit of each record's meta.
+cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, cudaStream_t s);
 
 // Check kernels (device functions of the hot path on given inputs).
 cudaError_t launch_debug_uniforms(uint32_t seed_lo, uint32_t seed_hi, int64_t n, const int64_t* trials,
                                   const int32_t* ks, const int32_t* elts, float* out, cudaStream_t s);
-cudaError_t launch_debug_losses(const Pair* recs, const float* z, int64_t n, float* out, int32_t* iters,
-                                cudaStream_t s);
+cudaError_t launch_debug_losses(const Pair* recs, const float4* tab, const float* z, int64_t n, int newton_only,
+                                float* out, int32_t* iters, cudaStream_t s);
 
 // --------------------------------------------------------------- scan
 // Exclusive prefix sum of n uint32 values; out[n] receives the total.
@@ -48,7 +52,7 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
 struct LayerEltRefs {
   int32_t n_elts;
   const int32_t* events[32];  // sorted event ids of the layer's ELT at position p
-  const Pair* recs[32];       // prepared records
+  const Pair* recs[32];       // prepared records (meta carries the record index)
   int64_t rec_begin[33];      // prefix sums of record counts over positions
 };
 
@@ -72,7 +76,7 @@ constexpr int kTileTrials = 128;
 constexpr int kChunk = kLayerThreads * 4;   // YET ids scanned per block step
 constexpr int kFlush = 1024;                // queued hits that trigger the SU phase
 constexpr int kQCap = kFlush + kChunk;      // queue capacity
-constexpr int kWin = 2048;                  // pairs per SU window
+constexpr int kWin = 2048;                  // pairs per SU window (also the slow-pair list size)
 
 struct LayerParams {
   const int64_t* off;
@@ -84,6 +88,8 @@ struct LayerParams {
   const Pair* pairs;
   int32_t filt_words;  // power of two
   int32_t n_elts;
+  const float4* tab[32];  // quantile tables of the layer's ELTs (by position)
+  int32_t newton_only;
   int32_t elt_id[32];
   float t_ret[32], t_lim[32], t_share[32];
   float occ_r, occ_l;  // occurrence terms in FP32 (the loss arithmetic)
@@ -94,7 +100,7 @@ struct LayerParams {
   double* ylt;
   int64_t* diag_hits;
   uint64_t* diag_hash;
-  unsigned long long* counters;  // [0] tile queue, [1] pairs hit, [2] non-converged
+  unsigned long long* counters;  // [0] tile queue, [1] pairs hit, [2] non-converged, [3] Halley pairs
 };
 
 size_t layer_smem_bytes(int filt_words);

@@ -120,7 +120,7 @@ __device__ double beta_cf_f64(double a, double b, double x) {
 // sigma_bmax = sqrt(mu_b (1 - mu_b)), sigma_b clipped to (1 - 1e-6) sigma_bmax,
 // alpha = mu_b ((sigma_bmax / sigma_b)^2 - 1), beta = (1 - mu_b)(...).
 __global__ void k_prepare_records(const int32_t* events, const float* mean, const float* sigma,
-                                  const float* exposure, int64_t n, Pair* out, uint32_t* flags,
+                                  const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
                                   int32_t* max_event) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   uint32_t f = 0;
@@ -136,6 +136,7 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
     p.max_l = static_cast<float>(ex);
     p.mu = static_cast<float>(mu);
     uint32_t kind = kKindBeta, m0x = 0;
+    double sa = 0.0, sb_ = 0.0;
     if (!(mu >= 0.0) || !(sg >= 0.0) || !isfinite(mu) || !isfinite(sg) || !isfinite(ex)) {
       f |= kBadValue;
       kind = kKindZero;
@@ -165,13 +166,16 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
       }
       p.a = static_cast<float>(a);
       p.b = static_cast<float>(b);
+      sa = a;
+      sb_ = b;
       m0x = (x0 <= y0) ? 1u : 0u;
       p.m0 = static_cast<float>(m0x ? x0 : y0);
       p.c = static_cast<float>(c);
       p.p_half = static_cast<float>(ph);
     }
-    p.meta = (kind << 5) | (m0x << 7);
+    p.meta = (kind << 5) | (m0x << 7) | (static_cast<uint32_t>(i) << 9);
     out[i] = p;
+    if (shapes) shapes[i] = make_double2(sa, sb_);
   }
   if (f) atomicOr(flags, f);
   // block max of event ids, then one atomic per warp
@@ -180,12 +184,140 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
 }
 
 cudaError_t launch_prepare_records(const int32_t* events, const float* mean, const float* sigma,
-                                   const float* exposure, int64_t n, Pair* out, uint32_t* flags,
+                                   const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
                                    int32_t* max_event, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int64_t blocks = (n + 127) / 128;
   k_prepare_records<<<static_cast<int>(blocks < 65535 ? blocks : 65535), 128, 0, s>>>(
-      events, mean, sigma, exposure, n, out, flags, max_event);
+      events, mean, sigma, exposure, n, out, shapes, flags, max_event);
+  return cudaGetLastError();
+}
+
+// =============================================================== quantile tables (FP64, load time)
+namespace {
+
+// I_x(a, b) and 1 - I_x(a, b), each without cancellation (A&S 26.5.8 with symmetry).
+__device__ void beta_inc_pair_f64(double x, double a, double b, double lnB, double* I, double* Ic) {
+  if (!(x > 0.0)) {
+    *I = 0.0;
+    *Ic = 1.0;
+    return;
+  }
+  if (!(x < 1.0)) {
+    *I = 1.0;
+    *Ic = 0.0;
+    return;
+  }
+  const double front = exp(a * log(x) + b * log1p(-x) - lnB);
+  if (x < (a + 1.0) / (a + b + 2.0)) {
+    const double v = front * beta_cf_f64(a, b, x) / a;
+    *I = v;
+    *Ic = 1.0 - v;
+  } else {
+    const double v = front * beta_cf_f64(b, a, 1.0 - x) / b;
+    *Ic = v;
+    *I = 1.0 - v;
+  }
+}
+
+// Root r of I_r(A, B) = p (p <= 1/2) by bracketed Newton in FP64 from `guess`.
+__device__ double beta_root_f64(double p, double A, double B, double lnB, double guess) {
+  double lo = 0.0, hi = 1.0;
+  double r = (guess > 0.0 && guess < 1.0) ? guess : A / (A + B);
+  for (int it = 0; it < 200; ++it) {
+    double I, Ic;
+    beta_inc_pair_f64(r, A, B, lnB, &I, &Ic);
+    const double f = I - p;
+    if (f == 0.0) return r;
+    if (f < 0.0) lo = r; else hi = r;
+    const double lpdf = (A - 1.0) * log(r) + (B - 1.0) * log1p(-r) - lnB;
+    double rn = r - f * exp(-lpdf);
+    if (!(rn > lo && rn < hi)) {
+      const double l = fmax(lo, 1e-300);
+      if (lo == 0.0 && hi <= 1e-300) return hi;
+      rn = (hi > 4.0 * l) ? sqrt(l) * sqrt(hi) : 0.5 * (lo + hi);
+    }
+    if (fabs(rn - r) <= 1e-14 * rn) return rn;
+    r = rn;
+  }
+  return r;
+}
+
+}  // namespace
+
+// One warp per record, lane i = node i at t_i = -T1 + i h.  Each node: the
+// FP64 root x_i (seeded by the FP32 Halley solver), w = ln x, w' and w''
+// (derivatives in t: w' = phi(t) / (x f(x)), w'' = w' (-t - w' (a - (b-1) x/(1-x)))).
+// The stored float4 is {x_i, w_{i+1} - w_i, h w'_i, h^2 w''_i}.  Then each
+// segment is checked at s = 1/4, 1/2, 3/4: the FP32 interpolant (as the hot
+// path evaluates it) against the FP64 CDF; the record is table-exact when the
+// implied relative error of x is within kTabTol everywhere x >= 1e-30.
+__global__ void k_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab) {
+  const int lane = threadIdx.x & 31;
+  const int64_t rec = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (rec >= n) return;
+  const Pair pr = recs[rec];
+  float4* out = tab + rec * kTabNodes;
+  if (pair_kind(pr.meta) != kKindBeta) {
+    out[lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    return;
+  }
+  const double a = shapes[rec].x, b = shapes[rec].y;
+  const double lnB = lgamma(a) + lgamma(b) - lgamma(a + b);
+  const double h = 2.0 * kTabT1 / (kTabNodes - 1);
+  const double t = -kTabT1 + h * lane;
+  const double zl = normcdf(-fabs(t));  // the smaller tail probability
+  // FP32 seed, then FP64 polish on the side where the root keeps relative precision
+  BetaSolveStats st;
+  const float zf = (t <= 0.0) ? static_cast<float>(zl) : static_cast<float>(1.0 - zl);
+  const float seed = pair_quantile_newton(pr, fminf(fmaxf(zf, 5.9604645e-08f), 0.99999994f), -1.0f, &st);
+  double w, lny, x;
+  if (t <= 0.0) {
+    x = beta_root_f64(zl, a, b, lnB, static_cast<double>(seed));
+    w = log(x);
+    lny = log1p(-x);
+  } else {
+    const double y = beta_root_f64(zl, b, a, lnB, 1.0 - static_cast<double>(seed));
+    x = 1.0 - y;
+    w = log1p(-y);
+    lny = log(y);
+  }
+  const double lpdf = (a - 1.0) * w + (b - 1.0) * lny - lnB;
+  const double lphi = -0.5 * t * t - 0.91893853320467274178;
+  const double D = exp(lphi - w - lpdf);
+  const double E = D * (-t - D * (a - (b - 1.0) * exp(w - lny)));
+  const double w_next = __shfl_down_sync(0xffffffffu, w, 1);
+  const float4 node = make_float4(static_cast<float>(exp(w)), lane < kTabNodes - 1 ? static_cast<float>(w_next - w) : 0.0f,
+                                  static_cast<float>(h * D), static_cast<float>(h * h * E));
+  out[lane] = node;
+  // ---- accuracy check of the interpolant
+  const float d1 = __shfl_down_sync(0xffffffffu, node.z, 1);
+  const float e1 = __shfl_down_sync(0xffffffffu, node.w, 1);
+  bool ok = isfinite(node.x) && isfinite(node.y) && isfinite(node.z) && isfinite(node.w);
+  if (lane < kTabNodes - 1) {
+    for (int q = 1; q <= 3; ++q) {
+      const float sf = 0.25f * q;
+      const float xq = (node.x > 0.0f) ? node.x * expf(tab_increment(sf, node.y, node.z, node.w, d1, e1)) : 0.0f;
+      if (!(xq >= 1e-30f)) continue;  // negligible losses
+      const double tq = t + h * sf;
+      const double zq = normcdf(-fabs(tq));
+      double I, Ic;
+      const double xd = static_cast<double>(xq);
+      beta_inc_pair_f64(xd, a, b, lnB, &I, &Ic);
+      const double err_z = (tq <= 0.0) ? (I - zq) : (Ic - zq);
+      const double lpdf_q = (a - 1.0) * log(xd) + (b - 1.0) * log1p(-xd) - lnB;
+      const double rel = fabs(err_z) * exp(-(log(xd) + lpdf_q));
+      ok = ok && (rel <= kTabTol) && isfinite(rel);
+    }
+  }
+  const bool all_ok = __all_sync(0xffffffffu, ok);
+  if (lane == 0 && all_ok) recs[rec].meta = pr.meta | (1u << 8);
+}
+
+cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t blocks = (n + 7) / 8;  // 8 warps (records) per block
+  k_build_tables<<<static_cast<int>(blocks < 2147483647 ? blocks : 2147483647), 256, 0, s>>>(recs, shapes, n, tab);
   return cudaGetLastError();
 }
 
@@ -197,11 +329,13 @@ __global__ void k_debug_uniforms(uint32_t seed_lo, uint32_t seed_hi, int64_t n, 
     out[i] = philox_uniform(seed_lo, seed_hi, trials[i], static_cast<uint32_t>(ks[i]), static_cast<uint32_t>(elts[i]));
 }
 
-__global__ void k_debug_losses(const Pair* recs, const float* z, int64_t n, float* out, int32_t* iters) {
+__global__ void k_debug_losses(const Pair* recs, const float4* tab, const float* z, int64_t n, int newton_only,
+                               float* out, int32_t* iters) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
     BetaSolveStats st;
-    out[i] = pair_loss(recs[i], z[i], false, &st);
+    const Pair pr = recs[i];
+    out[i] = pair_loss(pr, z[i], false, tab + static_cast<int64_t>(pair_rec(pr.meta)) * kTabNodes, newton_only != 0, &st);
     if (iters) iters[i] = st.converged ? st.iters : -st.iters;
   }
 }
@@ -214,11 +348,11 @@ cudaError_t launch_debug_uniforms(uint32_t seed_lo, uint32_t seed_hi, int64_t n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_debug_losses(const Pair* recs, const float* z, int64_t n, float* out, int32_t* iters,
-                                cudaStream_t s) {
+cudaError_t launch_debug_losses(const Pair* recs, const float4* tab, const float* z, int64_t n, int newton_only,
+                                float* out, int32_t* iters, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int64_t b = (n + 127) / 128;
-  k_debug_losses<<<static_cast<int>(b < 65535 ? b : 65535), 128, 0, s>>>(recs, z, n, out, iters);
+  k_debug_losses<<<static_cast<int>(b < 65535 ? b : 65535), 128, 0, s>>>(recs, tab, z, n, newton_only, out, iters);
   return cudaGetLastError();
 }
 
@@ -432,22 +566,25 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
 //         positives get no pairs, true hits get their slot's pair range;
 //      b. a block scan lays the (event, ELT) pairs out densely, so that every
 //         lane of every warp inverts one Beta (no lanes idle on misses);
-//      c. per pair: Philox uniform, inverse Beta, ELT terms; per event the
-//         pair losses are summed in layer order (FP32) and the occurrence
-//         terms applied;
+//      c. per pair: Philox uniform, inverse Beta (the record's quantile table,
+//         or the Halley iteration for the few records whose table is not
+//         exact, in a second dense pass), ELT terms; per event the pair
+//         losses are summed in layer order (FP32) and the occurrence terms
+//         applied;
 //      d. one thread per trial adds its events' occurrence losses, in YET
 //         order, into the trial's FP64 running sum;
 //   3. at the end of the tile the aggregate terms turn each running sum into
 //      the trial's year loss.
 // Shared memory layout (dynamic):
 //   filt[filt_words] | q_key[kQCap] | q_ps[kQCap] | q_pb[kQCap+1] | q_G[kQCap]
-//   | lp[kWin] | s_off[kTileTrials+1] (8-aligned) | s_S[kTileTrials]
+//   | lp[kWin] | s_slow[kWin] | s_off[kTileTrials+1] (8-aligned) | s_S[kTileTrials]
 //   | s_hits[kTileTrials] | s_hash[kTileTrials] | s_warp[33] | s_misc[4]
 
 size_t layer_smem_bytes(int filt_words) {
   size_t b = sizeof(uint32_t) * static_cast<size_t>(filt_words);
   b += sizeof(uint32_t) * (4 * static_cast<size_t>(kQCap) + 1);
   b += sizeof(float) * kWin;
+  b += sizeof(uint16_t) * kWin;
   b = (b + 7) & ~size_t(7);
   b += sizeof(int64_t) * (kTileTrials + 1);
   b += sizeof(double) * kTileTrials;
@@ -464,7 +601,8 @@ __global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p)
   uint32_t* q_pb = q_ps + kQCap;
   float* q_G = reinterpret_cast<float*>(q_pb + kQCap + 1);
   float* lp = q_G + kQCap;
-  size_t off_bytes = reinterpret_cast<unsigned char*>(lp + kWin) - smem_raw;
+  uint16_t* s_slow = reinterpret_cast<uint16_t*>(lp + kWin);
+  size_t off_bytes = reinterpret_cast<unsigned char*>(s_slow + kWin) - smem_raw;
   off_bytes = (off_bytes + 7) & ~size_t(7);
   int64_t* s_off = reinterpret_cast<int64_t*>(smem_raw + off_bytes);
   double* s_S = reinterpret_cast<double*>(s_off + kTileTrials + 1);
@@ -485,7 +623,7 @@ __global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p)
   }
   __syncthreads();
 
-  unsigned long long local_pairs = 0, local_nc = 0;
+  unsigned long long local_pairs = 0, local_nc = 0, local_slow = 0;
 
   for (;;) {
     if (tid == 0) s_misc[0] = static_cast<uint32_t>(atomicAdd(&p.counters[0], 1ull));
@@ -600,9 +738,14 @@ __global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p)
         __syncthreads();
       }
       const uint32_t n_pairs = q_pb[qn];
-      // ---- 2c. secondary uncertainty over dense pair windows
+      // ---- 2c. secondary uncertainty over dense pair windows.  Pairs whose
+      // record is table-exact (or carries no uncertainty) finish in the first
+      // pass; the rest are listed and run the Halley iteration in a second,
+      // dense pass, so that no warp idles on a few slow lanes.
       for (uint32_t w0 = 0; w0 < n_pairs; w0 += kWin) {
         const uint32_t w1 = (w0 + kWin < n_pairs) ? w0 + kWin : n_pairs;
+        if (tid == 0) s_misc[1] = 0;
+        __syncthreads();
         for (uint32_t pi = w0 + tid; pi < w1; pi += blockDim.x) {
           int lo = 0, hi = qn;  // q_pb[lo] <= pi < q_pb[hi]
           while (hi - lo > 1) {
@@ -615,21 +758,46 @@ __global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p)
           const uint32_t k = key & 0xFFFFFFu;
           const uint32_t pos = pair_pos(pr.meta);
           const uint32_t elt = static_cast<uint32_t>(p.elt_id[pos]);
-          float loss = pr.mu;
-          if (!p.primary_only && pair_kind(pr.meta) == kKindBeta) {
-            const float z = philox_uniform(p.seed_lo, p.seed_hi, ta + tl, k, elt);
-            BetaSolveStats st;
-            loss = pair_loss(pr, z, false, &st);
-            if (!st.converged) ++local_nc;
-          } else if (pair_kind(pr.meta) == kKindZero) {
-            loss = 0.0f;
-          }
-          lp[pi - w0] = p.t_share[pos] * clamp_terms_f(loss, p.t_ret[pos], p.t_lim[pos]);
           ++local_pairs;
           if (diag) {
             atomicAdd(&s_hits[tl], 1ull);
             atomicAdd(&s_hash[tl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(k) << 32) | elt)));
           }
+          const uint32_t kind = pair_kind(pr.meta);
+          float loss = pr.mu;
+          if (kind == kKindZero) {
+            loss = 0.0f;
+          } else if (!p.primary_only && kind == kKindBeta) {
+            if (p.newton_only || !pair_tab_exact(pr.meta)) {
+              s_slow[atomicAdd(&s_misc[1], 1u)] = static_cast<uint16_t>(pi - w0);
+              continue;
+            }
+            const float z = philox_uniform(p.seed_lo, p.seed_hi, ta + tl, k, elt);
+            loss = pr.max_l * tab_quantile(p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes, z);
+          }
+          lp[pi - w0] = p.t_share[pos] * clamp_terms_f(loss, p.t_ret[pos], p.t_lim[pos]);
+        }
+        __syncthreads();
+        const uint32_t n_slow = s_misc[1];
+        for (uint32_t j = tid; j < n_slow; j += blockDim.x) {
+          const uint32_t li = s_slow[j];
+          const uint32_t pi = w0 + li;
+          int lo = 0, hi = qn;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (q_pb[mid] <= pi) lo = mid; else hi = mid;
+          }
+          const Pair pr = p.pairs[q_ps[lo] + (pi - q_pb[lo])];
+          const uint32_t key = q_key[lo];
+          const uint32_t pos = pair_pos(pr.meta);
+          const float z = philox_uniform(p.seed_lo, p.seed_hi, ta + static_cast<int>(key >> 24), key & 0xFFFFFFu,
+                                         static_cast<uint32_t>(p.elt_id[pos]));
+          const float4* tab = p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes;
+          BetaSolveStats st;
+          const float x = pair_quantile_newton(pr, z, p.newton_only ? -1.0f : tab_quantile(tab, z), &st);
+          if (!st.converged) ++local_nc;
+          ++local_slow;
+          lp[li] = p.t_share[pos] * clamp_terms_f(pr.max_l * x, p.t_ret[pos], p.t_lim[pos]);
         }
         __syncthreads();
         // per event: sum its pair losses in layer order
@@ -672,10 +840,12 @@ __global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p)
   for (int d = 16; d > 0; d >>= 1) {
     local_pairs += __shfl_xor_sync(0xffffffffu, local_pairs, d);
     local_nc += __shfl_xor_sync(0xffffffffu, local_nc, d);
+    local_slow += __shfl_xor_sync(0xffffffffu, local_slow, d);
   }
   if ((tid & 31) == 0) {
     if (local_pairs) atomicAdd(&p.counters[1], local_pairs);
     if (local_nc) atomicAdd(&p.counters[2], local_nc);
+    if (local_slow) atomicAdd(&p.counters[3], local_slow);
   }
 }
 

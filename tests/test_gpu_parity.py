@@ -35,7 +35,7 @@ def eng():
     e.close()
 
 
-def run_gpu(eng, yet, pool, terms, seed=0, t0=0, t1=None, primary_only=False, elt_ids=None):
+def run_gpu(eng, yet, pool, terms, seed=0, t0=0, t1=None, primary_only=False, elt_ids=None, newton_only=False):
     t1 = yet.n_trials if t1 is None else t1
     eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
     eng.load_pool(pool)
@@ -44,7 +44,8 @@ def run_gpu(eng, yet, pool, terms, seed=0, t0=0, t1=None, primary_only=False, el
     hits = np.zeros(n, np.int64)
     hh = np.zeros(n, np.uint64)
     ids = pool.elt_ids if elt_ids is None else elt_ids
-    eng.run_layer(ids, terms, seed, t0, t1, ylt, primary_only=primary_only, hits_out=hits, hash_out=hh)
+    eng.run_layer(ids, terms, seed, t0, t1, ylt, primary_only=primary_only, hits_out=hits, hash_out=hh,
+                  newton_only=newton_only)
     return ylt, hits, hh
 
 
@@ -78,30 +79,33 @@ def _record_error_stats(mu, sg, ex, z, got):
     return err, want, shapes
 
 
+@pytest.mark.parametrize("newton_only", [False, True], ids=["table", "newton"])
 @pytest.mark.parametrize("recipe", ["plain", "stress"])
-def test_inverse_beta_records(eng, recipe):
+def test_inverse_beta_records(eng, recipe, newton_only):
     pool = synth.make_elt_pool(2, 20_000, 2_000_000, 77, recipe=recipe)
     mu, sg, ex = pool.mean, pool.sigma, pool.exposure
     rng = np.random.default_rng(2)
     z = ((rng.integers(0, 1 << 23, mu.shape[0]) + 0.5) / 2**23).astype(np.float32)
-    got, iters = eng.debug_record_losses(mu, sg, ex, z)
+    got, iters = eng.debug_record_losses(mu, sg, ex, z, newton_only=newton_only)
     err, want, shapes = _record_error_stats(mu, sg, ex, z, got)
     rel_loss = err / want
     rel_mu = err / mu
-    print(f"\n[{recipe}] rel err vs loss: median {np.median(rel_loss):.2e} p99 {np.percentile(rel_loss, 99):.2e} "
-          f"max {rel_loss.max():.2e}; vs mean: max {rel_mu.max():.2e}; iters mean {np.abs(iters).mean():.2f} "
-          f"max {np.abs(iters).max()} nonconv {(iters < 0).sum()}")
+    print(f"\n[{recipe} {'newton' if newton_only else 'table'}] rel err vs loss: median {np.median(rel_loss):.2e} "
+          f"p99 {np.percentile(rel_loss, 99):.2e} max {rel_loss.max():.2e}; vs mean: max {rel_mu.max():.2e}; "
+          f"iters mean {np.abs(iters).mean():.2f} max {np.abs(iters).max()} nonconv {(iters < 0).sum()} "
+          f"table-only {(iters == 0).mean():.4f}")
     assert (iters >= 0).all()
     # each loss within 1e-5 of itself or, for losses far below the mean, 1e-6 of the mean
     assert np.all(err <= 1e-5 * want + 1e-6 * mu)
 
 
-def test_inverse_beta_extreme_uniforms(eng):
+@pytest.mark.parametrize("newton_only", [False, True], ids=["table", "newton"])
+def test_inverse_beta_extreme_uniforms(eng, newton_only):
     pool = synth.make_elt_pool(1, 4000, 100_000, 5, recipe="stress")
     mu, sg, ex = pool.mean, pool.sigma, pool.exposure
     for zv in (0.5 / 2**23, 1 - 0.5 / 2**23, 0.5, 1e-4, 1 - 1e-4):
         z = np.full(mu.shape[0], zv, np.float32)
-        got, iters = eng.debug_record_losses(mu, sg, ex, z)
+        got, iters = eng.debug_record_losses(mu, sg, ex, z, newton_only=newton_only)
         err, want, _ = _record_error_stats(mu, sg, ex, z, got)
         assert (iters >= 0).all()
         assert np.all(err <= 1e-5 * want + 1e-6 * mu), zv
@@ -115,10 +119,11 @@ def plain_1k():
     return yet, pool, spec, terms
 
 
-def test_layer_parity_plain_1k(eng, plain_1k):
+@pytest.mark.parametrize("newton_only", [False, True], ids=["table", "newton"])
+def test_layer_parity_plain_1k(eng, plain_1k, newton_only):
     yet, pool, spec, terms = plain_1k
     ref = oracle.run_layer(yet, pool, terms, seed=0)
-    ylt, hits, hh = run_gpu(eng, yet, pool, terms, seed=0)
+    ylt, hits, hh = run_gpu(eng, yet, pool, terms, seed=0, newton_only=newton_only)
     assert np.array_equal(hits, ref["hits"])
     assert np.array_equal(hh, ref["hit_hash"])
     worst = check_ylt(ylt, ref)
