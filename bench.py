@@ -218,7 +218,7 @@ def run_gpu(args):
     build.build()
 
     spec = dict(synth.WORKLOADS[WORKLOAD])
-    n_trials = spec["n_trials"]
+    n_trials = spec["n_trials"] if args.trials is None else int(args.trials)
     seed = 0 + rank  # weak scaling: each rank its own shard / stream
     yet_seed = spec["seed"] + 1000 * rank
     offsets = synth.yet_offsets(n_trials, spec["mean_events"], yet_seed)
@@ -383,6 +383,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--cpu-trials", type=int, default=20000, help="trials in the oracle's CPU-baseline sample")
     ap.add_argument("--ref-trials", type=int, default=20000, help="trials per step of the reference arm")
+    ap.add_argument("--trials", type=int, default=None,
+                    help="truncate the YET (profiling of a smaller case); the default is the full workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args(argv)

@@ -48,7 +48,7 @@ struct ara_ctx {
   // ELT pool
   std::map<int32_t, Elt> pool;
   // per-layer index (grown on demand)
-  DevBuf bits, word_cnt, rankdir, mask, slot_cnt, pairs, scan_tmp;
+  DevBuf bits, word_cnt, word_pairs, rankdir, mask, slot_cnt, pairs, scan_tmp;
   // misc scratch
   DevBuf flags;     // uint32 flags + int32 max event
   DevBuf counters;  // 4 x u64
@@ -417,7 +417,8 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   const size_t tmp_words = std::max(ara::scan_tmp_words(n_words), ara::scan_tmp_words(n_recs));
   if ((rc = reserve(c, c->bits, sizeof(uint32_t) * n_words)) ||
       (rc = reserve(c, c->word_cnt, sizeof(uint32_t) * (n_words + 1))) ||
-      (rc = reserve(c, c->rankdir, sizeof(uint2) * n_words)) ||
+      (rc = reserve(c, c->word_pairs, sizeof(uint32_t) * (n_words + 1))) ||
+      (rc = reserve(c, c->rankdir, sizeof(uint4) * n_words)) ||
       (rc = reserve(c, c->mask, sizeof(uint32_t) * (n_recs + 1))) ||
       (rc = reserve(c, c->slot_cnt, sizeof(uint32_t) * (n_recs + 2))) ||
       (rc = reserve(c, c->pairs, sizeof(ara::Pair) * (n_recs + 1))) ||
@@ -426,7 +427,8 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   ara::LayerIndex ix{};
   ix.bits = static_cast<uint32_t*>(c->bits.ptr);
   ix.word_cnt = static_cast<uint32_t*>(c->word_cnt.ptr);
-  ix.rankdir = static_cast<uint2*>(c->rankdir.ptr);
+  ix.word_pairs = static_cast<uint32_t*>(c->word_pairs.ptr);
+  ix.rankdir = static_cast<uint4*>(c->rankdir.ptr);
   ix.mask = static_cast<uint32_t*>(c->mask.ptr);
   ix.slot_cnt = static_cast<uint32_t*>(c->slot_cnt.ptr);
   ix.pairs = static_cast<ara::Pair*>(c->pairs.ptr);
@@ -469,7 +471,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   if (smem > static_cast<size_t>(c->max_smem))
     return fail(c, ARA_ECUDA, "ara_run_layer: kernel needs %zu bytes of shared memory, device allows %d", smem,
                 c->max_smem);
-  const int64_t n_tiles = (n_out + ara::kTileTrials - 1) / ara::kTileTrials;
+  const int64_t n_tiles = (n_out + ara::kWarpTrials - 1) / ara::kWarpTrials;
   p.off = static_cast<const int64_t*>(c->yet_off.ptr);
   p.ids = static_cast<const int32_t*>(c->yet_ids.ptr);
   p.t_begin = t0;
@@ -488,13 +490,13 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   p.seed_hi = static_cast<uint32_t>(seed >> 32);
   p.primary_only = (L->flags & ARA_PRIMARY_ONLY) ? 1 : 0;
   p.newton_only = (L->flags & ARA_NEWTON_ONLY) ? 1 : 0;
-  p.n_tiles = static_cast<int32_t>(n_tiles);
+  p.n_tiles = n_tiles;
   p.ylt = d_ylt;
   p.diag_hits = d_hits;
   p.diag_hash = d_hash;
   p.counters = static_cast<unsigned long long*>(c->counters.ptr);
   ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 4 * sizeof(unsigned long long), c->stream));
-  const int grid = static_cast<int>(std::min<int64_t>(c->num_sms, n_tiles));
+  const int grid = static_cast<int>(std::min<int64_t>(c->num_sms, (n_tiles + 31) / 32));
   ARA_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
   ARA_CUDA(c, cudaEventRecord(ka, c->stream));
   ARA_CUDA(c, ara::launch_layer_kernel(p, grid, smem, c->stream));
@@ -737,7 +739,7 @@ void ara_destroy(ara_ctx* c) {
     release(c, kv.second.recs);
     release(c, kv.second.tab);
   }
-  DevBuf* bufs[] = {&c->yet_off, &c->yet_ids, &c->bits,  &c->word_cnt, &c->rankdir, &c->mask,   &c->slot_cnt,
+  DevBuf* bufs[] = {&c->yet_off, &c->yet_ids, &c->bits,  &c->word_cnt, &c->word_pairs, &c->rankdir, &c->mask,   &c->slot_cnt,
                     &c->pairs,   &c->scan_tmp, &c->flags, &c->counters, &c->ylt_tmp, &c->diag_tmp, &c->sel,
                     &c->in_tmp,  &c->out_tmp};
   for (DevBuf* b : bufs) release(c, *b);

@@ -59,7 +59,8 @@ struct LayerEltRefs {
 struct LayerIndex {
   uint32_t* bits;        // [n_words] membership bitmap over the catalogue
   uint32_t* word_cnt;    // [n_words + 1] scratch: popcounts, then exclusive scan
-  uint2* rankdir;        // [n_words] {bits, set bits before the word}
+  uint32_t* word_pairs;  // [n_words + 1] scratch: pairs per word, then exclusive scan
+  uint4* rankdir;        // [n_words] {bits, slots before the word, pairs before the word, multi-pair flag}
   uint32_t* mask;        // [n_recs] per slot: bitmask of layer positions
   uint32_t* slot_cnt;    // [n_recs + 1] scratch -> slot_start
   Pair* pairs;           // [n_recs]
@@ -71,18 +72,15 @@ struct LayerIndex {
 cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStream_t s, int* n_launch);
 
 // --------------------------------------------------------------- main kernel
-constexpr int kLayerThreads = 1024;
-constexpr int kTileTrials = 128;
-constexpr int kChunk = kLayerThreads * 4;   // YET ids scanned per block step
-constexpr int kFlush = 1024;                // queued hits that trigger the SU phase
-constexpr int kQCap = kFlush + kChunk;      // queue capacity
-constexpr int kWin = 2048;                  // pairs per SU window (also the slow-pair list size)
+constexpr int kLayerThreads = 1024;  // 32 independent warps per CTA, one CTA per SM
+constexpr int kWarpTrials = 8;       // trials per warp tile
+constexpr int kRing = 160;           // per-warp ring of filter positives (>= 31 + 128)
 
 struct LayerParams {
   const int64_t* off;
   const int32_t* ids;
   int64_t t_begin, t_end;
-  const uint2* rankdir;
+  const uint4* rankdir;
   int64_t n_words;
   const uint32_t* slot_start;
   const Pair* pairs;
@@ -96,7 +94,7 @@ struct LayerParams {
   double agg_r, agg_l;
   uint32_t seed_lo, seed_hi;
   int32_t primary_only;
-  int32_t n_tiles;
+  int64_t n_tiles;
   double* ylt;
   int64_t* diag_hits;
   uint64_t* diag_hash;

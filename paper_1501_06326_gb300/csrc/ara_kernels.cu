@@ -12,11 +12,6 @@ namespace ara {
 
 namespace {
 
-__device__ __forceinline__ int4 ld_stream_int4(const int32_t* p) {
-  // streamed once: do not keep the YET in L1, evict it first from L2
-  return __ldcs(reinterpret_cast<const int4*>(p));
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_inclusive_scan(T v) {
   const int lane = threadIdx.x & 31;
@@ -447,13 +442,14 @@ __device__ __forceinline__ int find_pos(const LayerEltRefs& r, int64_t i) {
   return p;
 }
 
-__global__ void k_mark_members(LayerEltRefs r, uint32_t* bits) {
+__global__ void k_mark_members(LayerEltRefs r, uint32_t* bits, uint32_t* word_pairs) {
   const int64_t n = r.rec_begin[r.n_elts];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
     const int p = find_pos(r, i);
     const int32_t e = r.events[p][i - r.rec_begin[p]];
     atomicOr(&bits[e >> 5], 1u << (e & 31));
+    atomicAdd(&word_pairs[e >> 5], 1u);  // every record is one (event, ELT) pair
   }
 }
 
@@ -463,19 +459,23 @@ __global__ void k_word_popc(const uint32_t* bits, int64_t n_words, uint32_t* cnt
     cnt[w] = __popc(bits[w]);
 }
 
-__global__ void k_pack_rankdir(const uint32_t* bits, const uint32_t* base, int64_t n_words, uint2* rankdir) {
+__global__ void k_pack_rankdir(const uint32_t* bits, const uint32_t* base, const uint32_t* pbase, int64_t n_words,
+                               uint4* rankdir) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; w < n_words; w += stride)
-    rankdir[w] = make_uint2(bits[w], base[w]);
+  for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; w < n_words; w += stride) {
+    const uint32_t b = bits[w];
+    const uint32_t multi = (pbase[w + 1] - pbase[w] != static_cast<uint32_t>(__popc(b))) ? 1u : 0u;
+    rankdir[w] = make_uint4(b, base[w], pbase[w], multi);
+  }
 }
 
-__device__ __forceinline__ uint32_t rank_of(const uint2* rankdir, int32_t e) {
-  const uint2 rd = rankdir[e >> 5];
+__device__ __forceinline__ uint32_t rank_of(const uint4* rankdir, int32_t e) {
+  const uint4 rd = rankdir[e >> 5];
   const uint32_t bit = 1u << (e & 31);
   return rd.y + __popc(rd.x & (bit - 1u));
 }
 
-__global__ void k_mark_positions(LayerEltRefs r, const uint2* rankdir, uint32_t* mask) {
+__global__ void k_mark_positions(LayerEltRefs r, const uint4* rankdir, uint32_t* mask) {
   const int64_t n = r.rec_begin[r.n_elts];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
@@ -491,7 +491,7 @@ __global__ void k_slot_counts(const uint32_t* mask, int64_t n, uint32_t* cnt) {
     cnt[i] = __popc(mask[i]);
 }
 
-__global__ void k_fill_pairs(LayerEltRefs r, const uint2* rankdir, const uint32_t* mask,
+__global__ void k_fill_pairs(LayerEltRefs r, const uint4* rankdir, const uint32_t* mask,
                              const uint32_t* slot_start, Pair* pairs) {
   const int64_t n = r.rec_begin[r.n_elts];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -518,11 +518,12 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
   const int64_t n_recs = refs.rec_begin[refs.n_elts];
   cudaError_t err;
   if ((err = cudaMemsetAsync(ix.bits, 0, sizeof(uint32_t) * ix.n_words, s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(ix.word_pairs, 0, sizeof(uint32_t) * (ix.n_words + 1), s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(ix.mask, 0, sizeof(uint32_t) * (n_recs > 0 ? n_recs : 1), s)) != cudaSuccess)
     return err;
   int launched = 0;
   if (n_recs > 0) {
-    k_mark_members<<<grid_for(n_recs, 256), 256, 0, s>>>(refs, ix.bits);
+    k_mark_members<<<grid_for(n_recs, 256), 256, 0, s>>>(refs, ix.bits, ix.word_pairs);
     ++launched;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
@@ -532,7 +533,10 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
   // exclusive scan in place (each tile reads its inputs before writing)
   if ((err = scan_exclusive_u32(ix.word_cnt, ix.word_cnt, ix.n_words, ix.scan_tmp, s, &launched)) != cudaSuccess)
     return err;
-  k_pack_rankdir<<<grid_for(ix.n_words, 256), 256, 0, s>>>(ix.bits, ix.word_cnt, ix.n_words, ix.rankdir);
+  if ((err = scan_exclusive_u32(ix.word_pairs, ix.word_pairs, ix.n_words, ix.scan_tmp, s, &launched)) != cudaSuccess)
+    return err;
+  k_pack_rankdir<<<grid_for(ix.n_words, 256), 256, 0, s>>>(ix.bits, ix.word_cnt, ix.word_pairs, ix.n_words,
+                                                           ix.rankdir);
   ++launched;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (n_recs > 0) {
@@ -554,298 +558,319 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
 
 // =============================================================== fused layer kernel
 //
-// One persistent CTA of 1024 threads per SM takes tiles of kTileTrials
-// consecutive trials from a global queue.  For each tile:
-//   1. the tile's YET ids stream through in chunks of 4096 (one int4 per
-//      thread, evict-first); each id is tested against a shared-memory
-//      membership filter of the layer (the catalogue bitmap folded modulo the
-//      filter size), and the positives are appended, in YET order, to a
-//      shared queue (block scan);
-//   2. when the queue holds kFlush entries (or the tile ends) it is flushed:
-//      a. each entry is resolved against the exact rank directory: false
-//         positives get no pairs, true hits get their slot's pair range;
-//      b. a block scan lays the (event, ELT) pairs out densely, so that every
-//         lane of every warp inverts one Beta (no lanes idle on misses);
-//      c. per pair: Philox uniform, inverse Beta (the record's quantile table,
-//         or the Halley iteration for the few records whose table is not
-//         exact, in a second dense pass), ELT terms; per event the pair
-//         losses are summed in layer order (FP32) and the occurrence terms
-//         applied;
-//      d. one thread per trial adds its events' occurrence losses, in YET
-//         order, into the trial's FP64 running sum;
-//   3. at the end of the tile the aggregate terms turn each running sum into
-//      the trial's year loss.
-// Shared memory layout (dynamic):
-//   filt[filt_words] | q_key[kQCap] | q_ps[kQCap] | q_pb[kQCap+1] | q_G[kQCap]
-//   | lp[kWin] | s_slow[kWin] | s_off[kTileTrials+1] (8-aligned) | s_S[kTileTrials]
-//   | s_hits[kTileTrials] | s_hash[kTileTrials] | s_warp[33] | s_misc[4]
+// One persistent CTA of 32 warps per SM.  The CTA builds a shared-memory
+// membership filter of the layer (the catalogue bitmap folded modulo the
+// filter size) once; after that every warp is an independent pipeline that
+// needs no block-wide barrier.  A warp takes tiles of kWarpTrials consecutive
+// trials from a global queue and, per tile:
+//   1. streams the tile's YET ids, 128 per step (one int4 per lane,
+//      evict-first, the next step prefetched), tests each id against the
+//      filter and appends the positives in YET order to a warp-private ring;
+//   2. for every 32 queued positives (a batch, one per lane):
+//      a. resolves the event against the rank directory (one 16-byte load:
+//         the word's bits and its slot and pair bases); false positives get
+//         no pair, words holding a multi-ELT event read the slot's pair range;
+//      b. lays the batch's (event, ELT) pairs out densely over the lanes
+//         (warp scan), draws the Philox uniform, inverts the Beta through the
+//         record's quantile table and applies the ELT terms;
+//      c. sums each event's pair losses in layer order (FP32) and applies the
+//         occurrence terms;
+//      d. adds the batch's occurrence losses to each trial's FP64 running sum
+//         through a segmented double-float warp reduction (one FP64 add per
+//         trial and batch);
+//      events with a pair whose record's table is not exact are deferred
+//      and resolved, 32 at a time, by the FP32 Halley iteration;
+//   3. turns each running sum into the trial's year loss with the aggregate
+//      terms.
+
+namespace {
+
+struct WarpSmem {
+  uint32_t q_key[kRing];  // (trial in tile << 24) | event index k
+  uint32_t q_ev[kRing];   // event id
+  uint32_t pb[33];        // batch pair bases
+  uint32_t eps[32];       // batch entries' first pair
+  uint32_t eflag[32];     // batch entries that need the Halley iteration
+  float lp[32];           // pair losses of one round
+  uint32_t d_key[32];     // deferred events: key, pair start, pair count
+  uint32_t d_ps[32];
+  uint32_t d_cnt[32];
+  int64_t off[kWarpTrials + 1];
+  double S[kWarpTrials];
+  unsigned long long hits[kWarpTrials];
+  unsigned long long hash[kWarpTrials];
+};
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+// (hi, lo) + (hi2, lo2) in double-float arithmetic (TwoSum, then renormalise).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float hi2, float lo2) {
+  const float s = hi + hi2;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (hi2 - bb);
+  const float e = err + lo + lo2;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// Loss after ELT terms of one pair, for the table path; returns false when the
+// pair needs the Halley iteration.
+__device__ __forceinline__ bool pair_fast(const LayerParams& p, const Pair& pr, int64_t trial, uint32_t k, float* out) {
+  const uint32_t kind = pair_kind(pr.meta);
+  const uint32_t pos = pair_pos(pr.meta);
+  float loss = pr.mu;
+  if (kind == kKindZero) {
+    loss = 0.0f;
+  } else if (!p.primary_only && kind == kKindBeta) {
+    if (p.newton_only || !pair_tab_exact(pr.meta)) return false;
+    const float z = philox_uniform(p.seed_lo, p.seed_hi, trial, k, static_cast<uint32_t>(p.elt_id[pos]));
+    loss = pr.max_l * tab_quantile(p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes, z);
+  }
+  *out = p.t_share[pos] * clamp_terms_f(loss, p.t_ret[pos], p.t_lim[pos]);
+  return true;
+}
+
+__device__ __forceinline__ float pair_slow(const LayerParams& p, const Pair& pr, int64_t trial, uint32_t k,
+                                           unsigned long long* nc) {
+  const uint32_t pos = pair_pos(pr.meta);
+  float v;
+  if (pair_fast(p, pr, trial, k, &v)) return v;
+  const float z = philox_uniform(p.seed_lo, p.seed_hi, trial, k, static_cast<uint32_t>(p.elt_id[pos]));
+  const float4* tab = p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes;
+  BetaSolveStats st;
+  const float x = pair_quantile_newton(pr, z, p.newton_only ? -1.0f : tab_quantile(tab, z), &st);
+  if (!st.converged) ++*nc;
+  return p.t_share[pos] * clamp_terms_f(pr.max_l * x, p.t_ret[pos], p.t_lim[pos]);
+}
+
+// Resolve the deferred events of the warp (all lanes call it).
+__device__ void resolve_deferred(const LayerParams& p, WarpSmem& ws, int nd, int64_t ta, unsigned long long* nc,
+                                 unsigned long long* n_slow) {
+  const uint32_t lane = lane_id();
+  float O = 0.0f;
+  uint32_t tl = 0;
+  if (lane < static_cast<uint32_t>(nd)) {
+    const uint32_t key = ws.d_key[lane];
+    tl = key >> 24;
+    const uint32_t k = key & 0xFFFFFFu;
+    float G = 0.0f;
+    for (uint32_t j = 0; j < ws.d_cnt[lane]; ++j) G += pair_slow(p, p.pairs[ws.d_ps[lane] + j], ta + tl, k, nc);
+    O = clamp_terms_f(G, p.occ_r, p.occ_l);
+    ++*n_slow;
+  }
+  // add in list order (deterministic): lane 0 walks the results
+  for (int i = 0; i < nd; ++i) {
+    const float Oi = __shfl_sync(0xffffffffu, O, i);
+    const uint32_t ti = __shfl_sync(0xffffffffu, tl, i);
+    if (lane == 0) ws.S[ti] += static_cast<double>(Oi);
+  }
+  __syncwarp();
+}
+
+}  // namespace
 
 size_t layer_smem_bytes(int filt_words) {
-  size_t b = sizeof(uint32_t) * static_cast<size_t>(filt_words);
-  b += sizeof(uint32_t) * (4 * static_cast<size_t>(kQCap) + 1);
-  b += sizeof(float) * kWin;
-  b += sizeof(uint16_t) * kWin;
-  b = (b + 7) & ~size_t(7);
-  b += sizeof(int64_t) * (kTileTrials + 1);
-  b += sizeof(double) * kTileTrials;
-  b += sizeof(unsigned long long) * 2 * kTileTrials;
-  b += sizeof(uint32_t) * (33 + 4);
-  return b;
+  return sizeof(uint32_t) * static_cast<size_t>(filt_words) + sizeof(WarpSmem) * (kLayerThreads / 32) + 16;
 }
 
 __global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint32_t* filt = reinterpret_cast<uint32_t*>(smem_raw);
-  uint32_t* q_key = filt + p.filt_words;
-  uint32_t* q_ps = q_key + kQCap;
-  uint32_t* q_pb = q_ps + kQCap;
-  float* q_G = reinterpret_cast<float*>(q_pb + kQCap + 1);
-  float* lp = q_G + kQCap;
-  uint16_t* s_slow = reinterpret_cast<uint16_t*>(lp + kWin);
-  size_t off_bytes = reinterpret_cast<unsigned char*>(s_slow + kWin) - smem_raw;
-  off_bytes = (off_bytes + 7) & ~size_t(7);
-  int64_t* s_off = reinterpret_cast<int64_t*>(smem_raw + off_bytes);
-  double* s_S = reinterpret_cast<double*>(s_off + kTileTrials + 1);
-  unsigned long long* s_hits = reinterpret_cast<unsigned long long*>(s_S + kTileTrials);
-  unsigned long long* s_hash = s_hits + kTileTrials;
-  uint32_t* s_warp = reinterpret_cast<uint32_t*>(s_hash + kTileTrials);
-  uint32_t* s_misc = s_warp + 33;
-
-  const int tid = threadIdx.x;
+  WarpSmem* wsm = reinterpret_cast<WarpSmem*>(smem_raw);
+  uint32_t* filt = reinterpret_cast<uint32_t*>(wsm + (kLayerThreads / 32));
+  const uint32_t lane = lane_id();
+  WarpSmem& ws = wsm[threadIdx.x >> 5];
   const bool diag = (p.diag_hits != nullptr) || (p.diag_hash != nullptr);
   const uint32_t fmask = static_cast<uint32_t>(p.filt_words) - 1u;
+  const uint32_t lt_mask = (1u << lane) - 1u;
 
   // ---- membership filter: catalogue bitmap folded modulo filt_words
-  for (int w = tid; w < p.filt_words; w += blockDim.x) {
+  for (int w = threadIdx.x; w < p.filt_words; w += blockDim.x) {
     uint32_t v = 0;
     for (int64_t k = w; k < p.n_words; k += p.filt_words) v |= p.rankdir[k].x;
     filt[w] = v;
   }
   __syncthreads();
 
-  unsigned long long local_pairs = 0, local_nc = 0, local_slow = 0;
+  unsigned long long n_pairs = 0, n_nc = 0, n_slow = 0;
 
   for (;;) {
-    if (tid == 0) s_misc[0] = static_cast<uint32_t>(atomicAdd(&p.counters[0], 1ull));
-    __syncthreads();
-    const int64_t tile = s_misc[0];
-    __syncthreads();
+    int64_t tile = 0;
+    if (lane == 0) tile = static_cast<int64_t>(atomicAdd(&p.counters[0], 1ull));
+    tile = __shfl_sync(0xffffffffu, tile, 0);
     if (tile >= p.n_tiles) break;
-    const int64_t ta = p.t_begin + tile * kTileTrials;
-    const int64_t tb = (ta + kTileTrials < p.t_end) ? ta + kTileTrials : p.t_end;
+    const int64_t ta = p.t_begin + tile * kWarpTrials;
+    const int64_t tb = (ta + kWarpTrials < p.t_end) ? ta + kWarpTrials : p.t_end;
     const int ntr = static_cast<int>(tb - ta);
-    for (int j = tid; j <= ntr; j += blockDim.x) s_off[j] = p.off[ta + j];
-    for (int j = tid; j < ntr; j += blockDim.x) {
-      s_S[j] = 0.0;
-      s_hits[j] = 0ull;
-      s_hash[j] = 0ull;
+    if (lane <= static_cast<uint32_t>(ntr)) ws.off[lane] = p.off[ta + lane];
+    if (lane < static_cast<uint32_t>(ntr)) {
+      ws.S[lane] = 0.0;
+      ws.hits[lane] = 0ull;
+      ws.hash[lane] = 0ull;
     }
-    __syncthreads();
-    const int64_t ea = s_off[0], eb = s_off[ntr];
-
-    int qn = 0;
+    __syncwarp();
+    const int64_t ea = ws.off[0], eb = ws.off[ntr];
+    uint32_t head = 0, qn = 0;  // ring head and fill (warp-uniform)
+    int nd = 0;                 // deferred events
     int64_t c0 = ea & ~int64_t(3);
     int4 cur = make_int4(0, 0, 0, 0);
-    {
-      const int64_t base = c0 + 4 * tid;
-      if (base < eb) cur = ld_stream_int4(p.ids + base);
-    }
+    if (c0 + 4 * lane < eb) cur = __ldcs(reinterpret_cast<const int4*>(p.ids + c0 + 4 * lane));
     while (c0 < eb) {
-      const int64_t next = c0 + kChunk;
+      const int64_t next = c0 + 128;
       int4 nxt = make_int4(0, 0, 0, 0);
+      if (next + 4 * lane < eb) nxt = __ldcs(reinterpret_cast<const int4*>(p.ids + next + 4 * lane));
+      // ---- 1. filter 128 ids, append positives in order
       {
-        const int64_t base = next + 4 * tid;
-        if (base < eb) nxt = ld_stream_int4(p.ids + base);  // prefetch the next chunk
-      }
-      // ---- 1. filter the chunk
-      const int64_t base = c0 + 4 * tid;
-      const int32_t ev[4] = {cur.x, cur.y, cur.z, cur.w};
-      uint32_t hitmask = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int64_t pos = base + j;
-        if (pos >= ea && pos < eb) {
-          const uint32_t e = static_cast<uint32_t>(ev[j]);
-          const uint32_t word = filt[(e >> 5) & fmask];
-          if ((word >> (e & 31)) & 1u) hitmask |= 1u << j;
-        }
-      }
-      uint32_t total;
-      uint32_t slot = block_exclusive_scan(__popc(hitmask), s_warp, &total);
-      if (hitmask) {
+        const int64_t base = c0 + 4 * lane;
+        const int32_t ev[4] = {cur.x, cur.y, cur.z, cur.w};
+        uint32_t m = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          if (hitmask & (1u << j)) {
+          const int64_t pos = base + j;
+          const uint32_t e = static_cast<uint32_t>(ev[j]);
+          if (pos >= ea && pos < eb && ((filt[(e >> 5) & fmask] >> (e & 31)) & 1u)) m |= 1u << j;
+        }
+        const uint32_t c = __popc(m);
+        const uint32_t incl = warp_inclusive_scan(c);
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t slot = head + qn + incl - c;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (m & (1u << j)) {
             const int64_t pos = base + j;
-            // trial of pos: the last s_off[t] <= pos
-            int lo = 0, hi = ntr;  // s_off[lo] <= pos < s_off[hi]
-            while (hi - lo > 1) {
-              const int mid = (lo + hi) >> 1;
-              if (s_off[mid] <= pos) lo = mid; else hi = mid;
-            }
-            const uint32_t k = static_cast<uint32_t>(pos - s_off[lo]);
-            q_key[qn + slot] = (static_cast<uint32_t>(lo) << 24) | k;
-            q_ps[qn + slot] = static_cast<uint32_t>(ev[j]);
+            int t = 0;
+            while (t + 1 < ntr && ws.off[t + 1] <= pos) ++t;
+            ws.q_key[slot % kRing] = (static_cast<uint32_t>(t) << 24) | static_cast<uint32_t>(pos - ws.off[t]);
+            ws.q_ev[slot % kRing] = static_cast<uint32_t>(ev[j]);
             ++slot;
           }
         }
+        qn += total;
+        __syncwarp();
       }
-      qn += static_cast<int>(total);
-      const bool last = (next >= eb);
       cur = nxt;
       c0 = next;
-      if (qn < kFlush && !last) {
-        __syncthreads();
-        continue;
-      }
-      __syncthreads();
-      // ---- 2a. resolve queued entries against the exact rank directory
-      for (int h = tid; h < qn; h += blockDim.x) {
-        const uint32_t e = q_ps[h];
-        const uint2 rd = __ldg(&p.rankdir[e >> 5]);
-        const uint32_t bit = 1u << (e & 31);
+      // ---- 2. batches of 32 positives (the remainder at the end of the tile)
+      while (qn >= 32 || (c0 >= eb && qn > 0)) {
+        const uint32_t nb = qn < 32 ? qn : 32;
+        const bool valid = lane < nb;
+        const uint32_t qi = (head + lane) % kRing;
+        const uint32_t key = valid ? ws.q_key[qi] : 0u;
+        const uint32_t e = valid ? ws.q_ev[qi] : 0u;
+        // a. rank directory
         uint32_t ps = 0, cnt = 0;
-        if (rd.x & bit) {
-          const uint32_t sl = rd.y + __popc(rd.x & (bit - 1u));
-          ps = __ldg(&p.slot_start[sl]);
-          cnt = __ldg(&p.slot_start[sl + 1]) - ps;
-        }
-        q_ps[h] = ps;
-        q_pb[h] = cnt;
-        q_G[h] = 0.0f;
-      }
-      __syncthreads();
-      // ---- 2b. block scan of pair counts (5 entries per thread)
-      {
-        constexpr int kPer = (kQCap + kLayerThreads - 1) / kLayerThreads;
-        uint32_t vals[kPer];
-        uint32_t sum = 0;
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-          const int h = tid * kPer + j;
-          vals[j] = (h < qn) ? q_pb[h] : 0u;
-          sum += vals[j];
-        }
-        uint32_t tot;
-        uint32_t run = block_exclusive_scan(sum, s_warp, &tot);
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-          const int h = tid * kPer + j;
-          if (h < qn) q_pb[h] = run;
-          run += vals[j];
-        }
-        if (tid == 0) q_pb[qn] = tot;
-        __syncthreads();
-      }
-      const uint32_t n_pairs = q_pb[qn];
-      // ---- 2c. secondary uncertainty over dense pair windows.  Pairs whose
-      // record is table-exact (or carries no uncertainty) finish in the first
-      // pass; the rest are listed and run the Halley iteration in a second,
-      // dense pass, so that no warp idles on a few slow lanes.
-      for (uint32_t w0 = 0; w0 < n_pairs; w0 += kWin) {
-        const uint32_t w1 = (w0 + kWin < n_pairs) ? w0 + kWin : n_pairs;
-        if (tid == 0) s_misc[1] = 0;
-        __syncthreads();
-        for (uint32_t pi = w0 + tid; pi < w1; pi += blockDim.x) {
-          int lo = 0, hi = qn;  // q_pb[lo] <= pi < q_pb[hi]
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (q_pb[mid] <= pi) lo = mid; else hi = mid;
-          }
-          const Pair pr = p.pairs[q_ps[lo] + (pi - q_pb[lo])];
-          const uint32_t key = q_key[lo];
-          const int tl = static_cast<int>(key >> 24);
-          const uint32_t k = key & 0xFFFFFFu;
-          const uint32_t pos = pair_pos(pr.meta);
-          const uint32_t elt = static_cast<uint32_t>(p.elt_id[pos]);
-          ++local_pairs;
-          if (diag) {
-            atomicAdd(&s_hits[tl], 1ull);
-            atomicAdd(&s_hash[tl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(k) << 32) | elt)));
-          }
-          const uint32_t kind = pair_kind(pr.meta);
-          float loss = pr.mu;
-          if (kind == kKindZero) {
-            loss = 0.0f;
-          } else if (!p.primary_only && kind == kKindBeta) {
-            if (p.newton_only || !pair_tab_exact(pr.meta)) {
-              s_slow[atomicAdd(&s_misc[1], 1u)] = static_cast<uint16_t>(pi - w0);
-              continue;
+        if (valid) {
+          const uint4 rd = __ldg(&p.rankdir[e >> 5]);
+          const uint32_t bit = 1u << (e & 31);
+          if (rd.x & bit) {
+            const uint32_t below = __popc(rd.x & (bit - 1u));
+            if (rd.w == 0u) {
+              ps = rd.z + below;
+              cnt = 1;
+            } else {
+              const uint32_t sl = rd.y + below;
+              ps = __ldg(&p.slot_start[sl]);
+              cnt = __ldg(&p.slot_start[sl + 1]) - ps;
             }
-            const float z = philox_uniform(p.seed_lo, p.seed_hi, ta + tl, k, elt);
-            loss = pr.max_l * tab_quantile(p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes, z);
-          }
-          lp[pi - w0] = p.t_share[pos] * clamp_terms_f(loss, p.t_ret[pos], p.t_lim[pos]);
-        }
-        __syncthreads();
-        const uint32_t n_slow = s_misc[1];
-        for (uint32_t j = tid; j < n_slow; j += blockDim.x) {
-          const uint32_t li = s_slow[j];
-          const uint32_t pi = w0 + li;
-          int lo = 0, hi = qn;
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (q_pb[mid] <= pi) lo = mid; else hi = mid;
-          }
-          const Pair pr = p.pairs[q_ps[lo] + (pi - q_pb[lo])];
-          const uint32_t key = q_key[lo];
-          const uint32_t pos = pair_pos(pr.meta);
-          const float z = philox_uniform(p.seed_lo, p.seed_hi, ta + static_cast<int>(key >> 24), key & 0xFFFFFFu,
-                                         static_cast<uint32_t>(p.elt_id[pos]));
-          const float4* tab = p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes;
-          BetaSolveStats st;
-          const float x = pair_quantile_newton(pr, z, p.newton_only ? -1.0f : tab_quantile(tab, z), &st);
-          if (!st.converged) ++local_nc;
-          ++local_slow;
-          lp[li] = p.t_share[pos] * clamp_terms_f(pr.max_l * x, p.t_ret[pos], p.t_lim[pos]);
-        }
-        __syncthreads();
-        // per event: sum its pair losses in layer order
-        for (int h = tid; h < qn; h += blockDim.x) {
-          uint32_t a = q_pb[h], b = q_pb[h + 1];
-          if (a < w0) a = w0;
-          if (b > w1) b = w1;
-          if (a < b) {
-            float g = q_G[h];
-            for (uint32_t q = a; q < b; ++q) g += lp[q - w0];
-            q_G[h] = g;
           }
         }
-        __syncthreads();
+        const uint32_t tl = key >> 24;
+        // b. dense pairs over the lanes
+        const uint32_t pincl = warp_inclusive_scan(cnt);
+        const uint32_t np = __shfl_sync(0xffffffffu, pincl, 31);
+        ws.pb[lane] = pincl - cnt;
+        ws.eps[lane] = ps;
+        ws.eflag[lane] = 0u;
+        if (lane == 31) ws.pb[32] = np;
+        __syncwarp();
+        float G = 0.0f;
+        for (uint32_t r0 = 0; r0 < np; r0 += 32) {
+          const uint32_t pi = r0 + lane;
+          if (pi < np) {
+            int lo = 0, hi = static_cast<int>(nb);  // pb[lo] <= pi < pb[hi]
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (ws.pb[mid] <= pi) lo = mid; else hi = mid;
+            }
+            const uint32_t ekey = ws.q_key[(head + lo) % kRing];
+            const uint32_t etl = ekey >> 24, ek = ekey & 0xFFFFFFu;
+            const Pair pr = p.pairs[ws.eps[lo] + (pi - ws.pb[lo])];
+            float lv = 0.0f;
+            if (!pair_fast(p, pr, ta + etl, ek, &lv)) ws.eflag[lo] = 1u;
+            ws.lp[lane] = lv;
+            ++n_pairs;
+            if (diag) {
+              const uint32_t elt = static_cast<uint32_t>(p.elt_id[pair_pos(pr.meta)]);
+              atomicAdd(&ws.hits[etl], 1ull);
+              atomicAdd(&ws.hash[etl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(ek) << 32) | elt)));
+            }
+          }
+          __syncwarp();
+          // c. each event sums its pairs of this round, in layer order
+          if (valid && cnt) {
+            uint32_t q0 = ws.pb[lane], q1 = q0 + cnt;
+            if (q0 < r0) q0 = r0;
+            if (q1 > r0 + 32) q1 = r0 + 32;
+            for (uint32_t q = q0; q < q1; ++q) G += ws.lp[q - r0];
+          }
+          __syncwarp();
+        }
+        const bool defer = valid && ws.eflag[lane] != 0u;
+        const float O = (valid && !defer) ? clamp_terms_f(G, p.occ_r, p.occ_l) : 0.0f;
+        // deferred events: flush the list first if this batch would overflow it
+        const uint32_t dmask = __ballot_sync(0xffffffffu, defer);
+        if (dmask) {
+          if (nd + __popc(dmask) > 32) {
+            resolve_deferred(p, ws, nd, ta, &n_nc, &n_slow);
+            nd = 0;
+          }
+          if (defer) {
+            const int at = nd + __popc(dmask & lt_mask);
+            ws.d_key[at] = key;
+            ws.d_ps[at] = ps;
+            ws.d_cnt[at] = cnt;
+          }
+          nd += __popc(dmask);
+          __syncwarp();
+        }
+        // d. per-trial running sums: segmented double-float reduction, one FP64 add per trial
+        {
+          float hi = O, lo = 0.0f;
+          const uint32_t seg = valid ? tl : 0xFFFFu;
+#pragma unroll
+          for (int d = 1; d < 32; d <<= 1) {
+            const float h2 = __shfl_up_sync(0xffffffffu, hi, d);
+            const float l2 = __shfl_up_sync(0xffffffffu, lo, d);
+            const uint32_t s2 = __shfl_up_sync(0xffffffffu, seg, d);
+            if (lane >= static_cast<uint32_t>(d) && s2 == seg) df_add(hi, lo, h2, l2);
+          }
+          const uint32_t seg_next = __shfl_down_sync(0xffffffffu, seg, 1);
+          const bool last = valid && (lane == nb - 1 || seg_next != seg);
+          if (last) ws.S[tl] += static_cast<double>(hi) + static_cast<double>(lo);
+          __syncwarp();
+        }
+        head = (head + nb) % kRing;
+        qn -= nb;
       }
-      // ---- 2d. occurrence terms and the trials' FP64 running sums, in YET order
-      for (int h = tid; h < qn; h += blockDim.x) {
-        const uint32_t tr = q_key[h] >> 24;
-        if (h == 0 || (q_key[h - 1] >> 24) != tr) {
-          double S = s_S[tr];
-          for (int i = h; i < qn && (q_key[i] >> 24) == tr; ++i) {
-            S += static_cast<double>(clamp_terms_f(q_G[i], p.occ_r, p.occ_l));
-          }
-          s_S[tr] = S;
-        }
-      }
-      __syncthreads();
-      qn = 0;
     }
-    // ---- 3. aggregate terms: year loss of each trial of the tile
-    for (int j = tid; j < ntr; j += blockDim.x) {
-      const int64_t out = ta + j - p.t_begin;
-      p.ylt[out] = clamp_terms_d(s_S[j], p.agg_r, p.agg_l);
-      if (p.diag_hits) p.diag_hits[out] = static_cast<int64_t>(s_hits[j]);
-      if (p.diag_hash) p.diag_hash[out] = s_hash[j];
+    // ---- 3. deferred events, then the aggregate terms
+    if (nd > 0) resolve_deferred(p, ws, nd, ta, &n_nc, &n_slow);
+    if (lane < static_cast<uint32_t>(ntr)) {
+      const int64_t out = ta + lane - p.t_begin;
+      p.ylt[out] = clamp_terms_d(ws.S[lane], p.agg_r, p.agg_l);
+      if (p.diag_hits) p.diag_hits[out] = static_cast<int64_t>(ws.hits[lane]);
+      if (p.diag_hash) p.diag_hash[out] = ws.hash[lane];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  // counters: pairs evaluated and non-converged inversions
   for (int d = 16; d > 0; d >>= 1) {
-    local_pairs += __shfl_xor_sync(0xffffffffu, local_pairs, d);
-    local_nc += __shfl_xor_sync(0xffffffffu, local_nc, d);
-    local_slow += __shfl_xor_sync(0xffffffffu, local_slow, d);
+    n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, d);
+    n_nc += __shfl_xor_sync(0xffffffffu, n_nc, d);
+    n_slow += __shfl_xor_sync(0xffffffffu, n_slow, d);
   }
-  if ((tid & 31) == 0) {
-    if (local_pairs) atomicAdd(&p.counters[1], local_pairs);
-    if (local_nc) atomicAdd(&p.counters[2], local_nc);
-    if (local_slow) atomicAdd(&p.counters[3], local_slow);
+  if (lane == 0) {
+    if (n_pairs) atomicAdd(&p.counters[1], n_pairs);
+    if (n_nc) atomicAdd(&p.counters[2], n_nc);
+    if (n_slow) atomicAdd(&p.counters[3], n_slow);
   }
 }
 
