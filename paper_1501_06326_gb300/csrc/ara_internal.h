@@ -75,6 +75,7 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
 constexpr int kLayerThreads = 1024;  // 32 independent warps per CTA, one CTA per SM
 constexpr int kWarpTrials = 8;       // trials per warp tile
 constexpr int kRing = 160;           // per-warp ring of filter positives (>= 31 + 128)
+constexpr int kEvRing = 64;          // per-warp ring of resolved events (>= 31 + 32)
 
 struct LayerParams {
   const int64_t* off;

@@ -564,38 +564,37 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
 // needs no block-wide barrier.  A warp takes tiles of kWarpTrials consecutive
 // trials from a global queue and, per tile:
 //   1. streams the tile's YET ids, 128 per step (one int4 per lane,
-//      evict-first, the next step prefetched), tests each id against the
-//      filter and appends the positives in YET order to a warp-private ring;
-//   2. for every 32 queued positives (a batch, one per lane):
-//      a. resolves the event against the rank directory (one 16-byte load:
-//         the word's bits and its slot and pair bases); false positives get
-//         no pair, words holding a multi-ELT event read the slot's pair range;
-//      b. lays the batch's (event, ELT) pairs out densely over the lanes
-//         (warp scan), draws the Philox uniform, inverts the Beta through the
-//         record's quantile table and applies the ELT terms;
-//      c. sums each event's pair losses in layer order (FP32) and applies the
-//         occurrence terms;
-//      d. adds the batch's occurrence losses to each trial's FP64 running sum
-//         through a segmented double-float warp reduction (one FP64 add per
-//         trial and batch);
-//      events with a pair whose record's table is not exact are deferred
-//      and resolved, 32 at a time, by the FP32 Halley iteration;
-//   3. turns each running sum into the trial's year loss with the aggregate
+//      evict-first, two steps prefetched), tests each id against the filter
+//      and appends the positives, in YET order, to a warp-private ring;
+//   2. resolves 32 positives at a time against the rank directory (one
+//      16-byte load gives the word's bits and its slot and pair bases; words
+//      holding a multi-ELT event read the slot's pair range) and appends the
+//      true events, with their pair ranges, to a second ring;
+//   3. takes whole events from that ring, up to 32 (event, ELT) pairs per
+//      batch, one pair per lane: Philox uniform, inverse Beta through the
+//      record's quantile table, ELT terms; a segmented warp reduction sums
+//      each event's pairs in layer order (FP32) and applies the occurrence
+//      terms, and a segmented double-float reduction adds the occurrence
+//      losses of each trial into the trial's FP64 running sum (one FP64 add
+//      per trial and batch);
+//      events with a pair whose record's table is not exact are deferred and
+//      resolved, 32 at a time, by the FP32 Halley iteration;
+//   4. turns each running sum into the trial's year loss with the aggregate
 //      terms.
 
 namespace {
 
 struct WarpSmem {
-  uint32_t q_key[kRing];  // (trial in tile << 24) | event index k
-  uint32_t q_ev[kRing];   // event id
-  uint32_t pb[33];        // batch pair bases
-  uint32_t eps[32];       // batch entries' first pair
-  uint32_t eflag[32];     // batch entries that need the Halley iteration
-  float lp[32];           // pair losses of one round
-  uint32_t d_key[32];     // deferred events: key, pair start, pair count
+  uint32_t q_key[kRing];   // positives: (trial in tile << 24) | event index k
+  uint32_t q_ev[kRing];    //            event id
+  uint32_t e_key[kEvRing]; // true events: key, first pair, pair count
+  uint32_t e_ps[kEvRing];
+  uint32_t e_cnt[kEvRing];
+  uint32_t pb[33];         // batch: first pair lane of each event
+  uint32_t d_key[32];      // deferred events: key, first pair, pair count
   uint32_t d_ps[32];
   uint32_t d_cnt[32];
-  int64_t off[kWarpTrials + 1];
+  int32_t off[kWarpTrials + 1];  // trial offsets relative to the tile's first event
   double S[kWarpTrials];
   unsigned long long hits[kWarpTrials];
   unsigned long long hash[kWarpTrials];
@@ -630,8 +629,8 @@ __device__ __forceinline__ bool pair_fast(const LayerParams& p, const Pair& pr, 
   return true;
 }
 
-__device__ __forceinline__ float pair_slow(const LayerParams& p, const Pair& pr, int64_t trial, uint32_t k,
-                                           unsigned long long* nc) {
+__device__ __noinline__ float pair_slow(const LayerParams& p, const Pair& pr, int64_t trial, uint32_t k,
+                                        unsigned long long* nc) {
   const uint32_t pos = pair_pos(pr.meta);
   float v;
   if (pair_fast(p, pr, trial, k, &v)) return v;
@@ -643,9 +642,10 @@ __device__ __forceinline__ float pair_slow(const LayerParams& p, const Pair& pr,
   return p.t_share[pos] * clamp_terms_f(pr.max_l * x, p.t_ret[pos], p.t_lim[pos]);
 }
 
-// Resolve the deferred events of the warp (all lanes call it).
-__device__ void resolve_deferred(const LayerParams& p, WarpSmem& ws, int nd, int64_t ta, unsigned long long* nc,
-                                 unsigned long long* n_slow) {
+// Resolve the deferred events of the warp (all lanes call it): each lane one
+// event, then the occurrence losses are added to the trial sums in list order.
+__device__ __noinline__ void resolve_deferred(const LayerParams& p, WarpSmem& ws, int nd, int64_t ta,
+                                              unsigned long long* nc, unsigned long long* n_slow) {
   const uint32_t lane = lane_id();
   float O = 0.0f;
   uint32_t tl = 0;
@@ -658,7 +658,6 @@ __device__ void resolve_deferred(const LayerParams& p, WarpSmem& ws, int nd, int
     O = clamp_terms_f(G, p.occ_r, p.occ_l);
     ++*n_slow;
   }
-  // add in list order (deterministic): lane 0 walks the results
   for (int i = 0; i < nd; ++i) {
     const float Oi = __shfl_sync(0xffffffffu, O, i);
     const uint32_t ti = __shfl_sync(0xffffffffu, tl, i);
@@ -691,7 +690,8 @@ __global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p)
   }
   __syncthreads();
 
-  unsigned long long n_pairs = 0, n_nc = 0, n_slow = 0;
+  unsigned long long n_nc = 0, n_slow = 0;
+  uint32_t n_pairs = 0;
 
   for (;;) {
     int64_t tile = 0;
@@ -701,158 +701,227 @@ __global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p)
     const int64_t ta = p.t_begin + tile * kWarpTrials;
     const int64_t tb = (ta + kWarpTrials < p.t_end) ? ta + kWarpTrials : p.t_end;
     const int ntr = static_cast<int>(tb - ta);
-    if (lane <= static_cast<uint32_t>(ntr)) ws.off[lane] = p.off[ta + lane];
+    const int64_t ea = __ldg(&p.off[ta]);
+    if (lane <= static_cast<uint32_t>(ntr)) ws.off[lane] = static_cast<int32_t>(__ldg(&p.off[ta + lane]) - ea);
     if (lane < static_cast<uint32_t>(ntr)) {
       ws.S[lane] = 0.0;
       ws.hits[lane] = 0ull;
       ws.hash[lane] = 0ull;
     }
     __syncwarp();
-    const int64_t ea = ws.off[0], eb = ws.off[ntr];
-    uint32_t head = 0, qn = 0;  // ring head and fill (warp-uniform)
-    int nd = 0;                 // deferred events
-    int64_t c0 = ea & ~int64_t(3);
-    int4 cur = make_int4(0, 0, 0, 0);
-    if (c0 + 4 * lane < eb) cur = __ldcs(reinterpret_cast<const int4*>(p.ids + c0 + 4 * lane));
-    while (c0 < eb) {
-      const int64_t next = c0 + 128;
-      int4 nxt = make_int4(0, 0, 0, 0);
-      if (next + 4 * lane < eb) nxt = __ldcs(reinterpret_cast<const int4*>(p.ids + next + 4 * lane));
-      // ---- 1. filter 128 ids, append positives in order
-      {
-        const int64_t base = c0 + 4 * lane;
-        const int32_t ev[4] = {cur.x, cur.y, cur.z, cur.w};
-        uint32_t m = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int64_t pos = base + j;
-          const uint32_t e = static_cast<uint32_t>(ev[j]);
-          if (pos >= ea && pos < eb && ((filt[(e >> 5) & fmask] >> (e & 31)) & 1u)) m |= 1u << j;
-        }
-        const uint32_t c = __popc(m);
-        const uint32_t incl = warp_inclusive_scan(c);
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        uint32_t slot = head + qn + incl - c;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (m & (1u << j)) {
-            const int64_t pos = base + j;
-            int t = 0;
-            while (t + 1 < ntr && ws.off[t + 1] <= pos) ++t;
-            ws.q_key[slot % kRing] = (static_cast<uint32_t>(t) << 24) | static_cast<uint32_t>(pos - ws.off[t]);
-            ws.q_ev[slot % kRing] = static_cast<uint32_t>(ev[j]);
-            ++slot;
-          }
-        }
-        qn += total;
-        __syncwarp();
-      }
-      cur = nxt;
-      c0 = next;
-      // ---- 2. batches of 32 positives (the remainder at the end of the tile)
-      while (qn >= 32 || (c0 >= eb && qn > 0)) {
-        const uint32_t nb = qn < 32 ? qn : 32;
-        const bool valid = lane < nb;
-        const uint32_t qi = (head + lane) % kRing;
-        const uint32_t key = valid ? ws.q_key[qi] : 0u;
-        const uint32_t e = valid ? ws.q_ev[qi] : 0u;
-        // a. rank directory
-        uint32_t ps = 0, cnt = 0;
-        if (valid) {
-          const uint4 rd = __ldg(&p.rankdir[e >> 5]);
-          const uint32_t bit = 1u << (e & 31);
-          if (rd.x & bit) {
-            const uint32_t below = __popc(rd.x & (bit - 1u));
-            if (rd.w == 0u) {
-              ps = rd.z + below;
-              cnt = 1;
-            } else {
-              const uint32_t sl = rd.y + below;
-              ps = __ldg(&p.slot_start[sl]);
-              cnt = __ldg(&p.slot_start[sl + 1]) - ps;
-            }
-          }
-        }
-        const uint32_t tl = key >> 24;
-        // b. dense pairs over the lanes
-        const uint32_t pincl = warp_inclusive_scan(cnt);
-        const uint32_t np = __shfl_sync(0xffffffffu, pincl, 31);
-        ws.pb[lane] = pincl - cnt;
-        ws.eps[lane] = ps;
-        ws.eflag[lane] = 0u;
-        if (lane == 31) ws.pb[32] = np;
-        __syncwarp();
-        float G = 0.0f;
-        for (uint32_t r0 = 0; r0 < np; r0 += 32) {
-          const uint32_t pi = r0 + lane;
-          if (pi < np) {
-            int lo = 0, hi = static_cast<int>(nb);  // pb[lo] <= pi < pb[hi]
-            while (hi - lo > 1) {
-              const int mid = (lo + hi) >> 1;
-              if (ws.pb[mid] <= pi) lo = mid; else hi = mid;
-            }
-            const uint32_t ekey = ws.q_key[(head + lo) % kRing];
-            const uint32_t etl = ekey >> 24, ek = ekey & 0xFFFFFFu;
-            const Pair pr = p.pairs[ws.eps[lo] + (pi - ws.pb[lo])];
-            float lv = 0.0f;
-            if (!pair_fast(p, pr, ta + etl, ek, &lv)) ws.eflag[lo] = 1u;
-            ws.lp[lane] = lv;
-            ++n_pairs;
-            if (diag) {
-              const uint32_t elt = static_cast<uint32_t>(p.elt_id[pair_pos(pr.meta)]);
-              atomicAdd(&ws.hits[etl], 1ull);
-              atomicAdd(&ws.hash[etl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(ek) << 32) | elt)));
-            }
-          }
-          __syncwarp();
-          // c. each event sums its pairs of this round, in layer order
-          if (valid && cnt) {
-            uint32_t q0 = ws.pb[lane], q1 = q0 + cnt;
-            if (q0 < r0) q0 = r0;
-            if (q1 > r0 + 32) q1 = r0 + 32;
-            for (uint32_t q = q0; q < q1; ++q) G += ws.lp[q - r0];
-          }
-          __syncwarp();
-        }
-        const bool defer = valid && ws.eflag[lane] != 0u;
-        const float O = (valid && !defer) ? clamp_terms_f(G, p.occ_r, p.occ_l) : 0.0f;
-        // deferred events: flush the list first if this batch would overflow it
-        const uint32_t dmask = __ballot_sync(0xffffffffu, defer);
-        if (dmask) {
-          if (nd + __popc(dmask) > 32) {
-            resolve_deferred(p, ws, nd, ta, &n_nc, &n_slow);
-            nd = 0;
-          }
-          if (defer) {
-            const int at = nd + __popc(dmask & lt_mask);
-            ws.d_key[at] = key;
-            ws.d_ps[at] = ps;
-            ws.d_cnt[at] = cnt;
-          }
-          nd += __popc(dmask);
-          __syncwarp();
-        }
-        // d. per-trial running sums: segmented double-float reduction, one FP64 add per trial
+    const int32_t nev = ws.off[ntr];  // events of the tile
+    int tcur = 0;                     // trial of the current chunk's first id (warp-uniform)
+    while (tcur + 1 < ntr && ws.off[tcur + 1] <= 0) ++tcur;
+    const int32_t* ids = p.ids + (ea & ~int64_t(3));
+    const int32_t lead = static_cast<int32_t>(ea & 3);  // ids[0 .. lead) precede the tile
+    const int32_t span = nev + lead;                    // ids to scan, from the aligned start
+    uint32_t qh = 0, qn = 0;  // positives ring head / fill (warp-uniform)
+    uint32_t eh = 0, en = 0;  // events ring head / fill
+    uint32_t epairs = 0;      // pairs queued in the events ring
+    int nd = 0;               // deferred events
+    // One step of the pipeline on 128 ids (in `cur`, starting at c0): filter,
+    // resolve, batches.
+    auto step = [&](const int4 cur, const int32_t c0) {
+      // ---- 1. filter 128 ids, append the positives in order
         {
-          float hi = O, lo = 0.0f;
-          const uint32_t seg = valid ? tl : 0xFFFFu;
+          const int32_t rel0 = c0 + 4 * static_cast<int32_t>(lane) - lead;  // tile-relative position of cur.x
+          const int32_t ev[4] = {cur.x, cur.y, cur.z, cur.w};
+          uint32_t m = 0;
 #pragma unroll
-          for (int d = 1; d < 32; d <<= 1) {
-            const float h2 = __shfl_up_sync(0xffffffffu, hi, d);
-            const float l2 = __shfl_up_sync(0xffffffffu, lo, d);
-            const uint32_t s2 = __shfl_up_sync(0xffffffffu, seg, d);
-            if (lane >= static_cast<uint32_t>(d) && s2 == seg) df_add(hi, lo, h2, l2);
+          for (int j = 0; j < 4; ++j) {
+            const uint32_t e = static_cast<uint32_t>(ev[j]);
+            const bool in = static_cast<uint32_t>(rel0 + j) < static_cast<uint32_t>(nev);
+            if (in && ((filt[(e >> 5) & fmask] >> (e & 31)) & 1u)) m |= 1u << j;
           }
-          const uint32_t seg_next = __shfl_down_sync(0xffffffffu, seg, 1);
-          const bool last = valid && (lane == nb - 1 || seg_next != seg);
-          if (last) ws.S[tl] += static_cast<double>(hi) + static_cast<double>(lo);
+          const uint32_t c = __popc(m);
+          const uint32_t incl = warp_inclusive_scan(c);
+          const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+          if (m) {
+            // trial of each positive: from the warp's cursor (the trial of the
+            // chunk's first id), a chunk crosses at most a few trial boundaries
+            int t = tcur;
+            int32_t tnext = ws.off[t + 1];
+            uint32_t slot = qh + qn + incl - c;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              if (m & (1u << j)) {
+                const int32_t rel = rel0 + j;
+                while (rel >= tnext && t + 1 < ntr) {
+                  ++t;
+                  tnext = ws.off[t + 1];
+                }
+                const uint32_t at = slot >= kRing ? slot - kRing : slot;
+                ws.q_key[at] = (static_cast<uint32_t>(t) << 24) | static_cast<uint32_t>(rel - ws.off[t]);
+                ws.q_ev[at] = static_cast<uint32_t>(ev[j]);
+                ++slot;
+              }
+            }
+          }
+          qn += total;
+          // advance the cursor to the trial of the next chunk's first id
+          {
+            const int32_t nrel = c0 + 128 - lead;
+            while (tcur + 1 < ntr && ws.off[tcur + 1] <= nrel) ++tcur;
+          }
           __syncwarp();
         }
-        head = (head + nb) % kRing;
-        qn -= nb;
+        const bool tile_done = (c0 + 128 >= span);
+      // ---- 2. resolve positives, 32 at a time, into true events; after each
+        // resolve (and once more at the end of the tile) run the batches
+        for (;;) {
+          const bool resolve = (qn >= 32 || (tile_done && qn > 0));
+          if (resolve) {
+          const uint32_t nb = qn < 32 ? qn : 32;
+          const bool valid = lane < nb;
+          uint32_t qi = qh + lane;
+          if (qi >= kRing) qi -= kRing;
+          uint32_t ps = 0, cnt = 0, key = 0;
+          if (valid) {
+            key = ws.q_key[qi];
+            const uint32_t e = ws.q_ev[qi];
+            const uint4 rd = __ldg(&p.rankdir[e >> 5]);
+            const uint32_t bit = 1u << (e & 31);
+            if (rd.x & bit) {
+              const uint32_t below = __popc(rd.x & (bit - 1u));
+              if (rd.w == 0u) {
+                ps = rd.z + below;
+                cnt = 1;
+              } else {
+                const uint32_t sl = rd.y + below;
+                ps = __ldg(&p.slot_start[sl]);
+                cnt = __ldg(&p.slot_start[sl + 1]) - ps;
+              }
+            }
+          }
+          const uint32_t hit = __ballot_sync(0xffffffffu, cnt != 0);
+          if (cnt) {
+            uint32_t at = eh + en + __popc(hit & lt_mask);
+            at &= kEvRing - 1;
+            ws.e_key[at] = key;
+            ws.e_ps[at] = ps;
+            ws.e_cnt[at] = cnt;
+          }
+          en += __popc(hit);
+          epairs += __reduce_add_sync(0xffffffffu, cnt);
+          qh += nb;
+          if (qh >= kRing) qh -= kRing;
+          qn -= nb;
+          __syncwarp();
+          }
+          // ---- 3. batches of whole events, up to 32 pairs
+          while (epairs >= 32 || (tile_done && qn == 0 && en > 0)) {
+            // events taken: the longest prefix with at most 32 pairs
+            const uint32_t ei = (eh + lane) & (kEvRing - 1);
+            const bool ev_ok = lane < en;
+            const uint32_t my_cnt = ev_ok ? ws.e_cnt[ei] : 0u;
+            const uint32_t cincl = warp_inclusive_scan(my_cnt);
+            const uint32_t take = __ballot_sync(0xffffffffu, ev_ok && cincl <= 32u);
+            const uint32_t n_take = __popc(take);  // a prefix: cincl grows with the lane
+            const uint32_t np = __shfl_sync(0xffffffffu, cincl, n_take - 1);
+            ws.pb[lane] = (lane < n_take) ? cincl - my_cnt : np;
+            if (lane == 31) ws.pb[32] = np;
+            __syncwarp();
+            // lane -> (event, pair)
+            int ev = 0;
+            {
+              int lo = 0, hi = static_cast<int>(n_take);  // pb[lo] <= lane < pb[hi]
+              while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (ws.pb[mid] <= lane) lo = mid; else hi = mid;
+              }
+              ev = lo;
+            }
+            const bool pv = lane < np;
+            const uint32_t eslot = (eh + ev) & (kEvRing - 1);
+            const uint32_t ekey = ws.e_key[eslot];
+            const uint32_t etl = ekey >> 24, ek = ekey & 0xFFFFFFu;
+            float lv = 0.0f;
+            bool slow = false;
+            if (pv) {
+              const Pair pr = p.pairs[ws.e_ps[eslot] + (lane - ws.pb[ev])];
+              slow = !pair_fast(p, pr, ta + etl, ek, &lv);
+              if (diag) {
+                const uint32_t elt = static_cast<uint32_t>(p.elt_id[pair_pos(pr.meta)]);
+                atomicAdd(&ws.hits[etl], 1ull);
+                atomicAdd(&ws.hash[etl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(ek) << 32) | elt)));
+              }
+            }
+            n_pairs += pv ? 1 : 0;
+            // event sums: segmented reduction over lanes by event, in lane (= layer) order
+            const uint32_t eseg = pv ? static_cast<uint32_t>(ev) : 0xFFFFu;
+            float G = lv;
+            uint32_t any_slow = slow ? 1u : 0u;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+              const float g2 = __shfl_up_sync(0xffffffffu, G, d);
+              const uint32_t s2 = __shfl_up_sync(0xffffffffu, eseg, d);
+              const uint32_t f2 = __shfl_up_sync(0xffffffffu, any_slow, d);
+              if (lane >= static_cast<uint32_t>(d) && s2 == eseg) {
+                G += g2;
+                any_slow |= f2;
+              }
+            }
+            const uint32_t eseg_next = __shfl_down_sync(0xffffffffu, eseg, 1);
+            const bool ev_last = pv && (lane == np - 1 || eseg_next != eseg);
+            const bool defer = ev_last && any_slow;
+            const float O = (ev_last && !any_slow) ? clamp_terms_f(G, p.occ_r, p.occ_l) : 0.0f;
+            // deferred events
+            const uint32_t dmask = __ballot_sync(0xffffffffu, defer);
+            if (dmask) {
+              if (nd + __popc(dmask) > 32) {
+                resolve_deferred(p, ws, nd, ta, &n_nc, &n_slow);
+                nd = 0;
+              }
+              if (defer) {
+                const int at = nd + __popc(dmask & lt_mask);
+                ws.d_key[at] = ekey;
+                ws.d_ps[at] = ws.e_ps[eslot];
+                ws.d_cnt[at] = ws.e_cnt[eslot];
+              }
+              nd += __popc(dmask);
+              __syncwarp();
+            }
+            // trial sums: segmented double-float reduction by trial, one FP64 add per trial
+            {
+              float hi = O, lo = 0.0f;
+              const uint32_t tseg = pv ? etl : 0xFFFFu;
+#pragma unroll
+              for (int d = 1; d < 32; d <<= 1) {
+                const float h2 = __shfl_up_sync(0xffffffffu, hi, d);
+                const float l2 = __shfl_up_sync(0xffffffffu, lo, d);
+                const uint32_t s2 = __shfl_up_sync(0xffffffffu, tseg, d);
+                if (lane >= static_cast<uint32_t>(d) && s2 == tseg) df_add(hi, lo, h2, l2);
+              }
+              const uint32_t tseg_next = __shfl_down_sync(0xffffffffu, tseg, 1);
+              if (pv && (lane == np - 1 || tseg_next != tseg)) ws.S[etl] += static_cast<double>(hi) + static_cast<double>(lo);
+            }
+            eh = (eh + n_take) & (kEvRing - 1);
+            en -= n_take;
+            epairs -= np;
+            __syncwarp();
+          }
+          if (!resolve) break;
+        }
+        };
+    // YET stream: two int4 registers, unrolled so that each is refilled with
+    // the chunk two steps ahead as soon as it has been consumed (the load
+    // writes the register directly; nothing in flight is moved).
+    int4 bufA = make_int4(0, 0, 0, 0), bufB = bufA;
+    if (4 * static_cast<int32_t>(lane) < span) bufA = __ldcs(reinterpret_cast<const int4*>(ids) + lane);
+    if (128 + 4 * static_cast<int32_t>(lane) < span) bufB = __ldcs(reinterpret_cast<const int4*>(ids) + 32 + lane);
+    for (int32_t c0 = 0; c0 < span; c0 += 256) {
+      const int4 curA = bufA;
+      if (c0 + 256 + 4 * static_cast<int32_t>(lane) < span)
+        bufA = __ldcs(reinterpret_cast<const int4*>(ids + c0 + 256) + lane);
+      step(curA, c0);
+      if (c0 + 128 < span) {
+        const int4 curB = bufB;
+        if (c0 + 384 + 4 * static_cast<int32_t>(lane) < span)
+          bufB = __ldcs(reinterpret_cast<const int4*>(ids + c0 + 384) + lane);
+        step(curB, c0 + 128);
       }
     }
-    // ---- 3. deferred events, then the aggregate terms
+    // ---- 4. deferred events, then the aggregate terms
     if (nd > 0) resolve_deferred(p, ws, nd, ta, &n_nc, &n_slow);
     if (lane < static_cast<uint32_t>(ntr)) {
       const int64_t out = ta + lane - p.t_begin;
@@ -862,13 +931,13 @@ __global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p)
     }
     __syncwarp();
   }
+  n_pairs = __reduce_add_sync(0xffffffffu, n_pairs);
   for (int d = 16; d > 0; d >>= 1) {
-    n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, d);
     n_nc += __shfl_xor_sync(0xffffffffu, n_nc, d);
     n_slow += __shfl_xor_sync(0xffffffffu, n_slow, d);
   }
   if (lane == 0) {
-    if (n_pairs) atomicAdd(&p.counters[1], n_pairs);
+    if (n_pairs) atomicAdd(&p.counters[1], static_cast<unsigned long long>(n_pairs));
     if (n_nc) atomicAdd(&p.counters[2], n_nc);
     if (n_slow) atomicAdd(&p.counters[3], n_slow);
   }
