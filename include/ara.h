@@ -213,6 +213,40 @@ ARA_API int ara_debug_record_losses(ara_ctx *ctx, int64_t n, const float *mean, 
                                     const float *exposure, const float *z, int32_t newton_only, float *out,
                                     int32_t *iters_out);
 
+/* PML and TVaR without any device allocation.
+ *
+ * Same result as ara_pml_tvar, for callers that may not allocate device
+ * memory: code running under a framework's caching allocator, which owns the
+ * device memory budget, or in a latency-critical loop where cudaMalloc and
+ * cudaFree, which can synchronise the whole device, are not acceptable.  It
+ * needs no context (creating one allocates).  The paper has no counterpart:
+ * this is a deployment variant of the Section 2.3 step.
+ *
+ * The select state lives in a fixed block of device memory that belongs to
+ * the library (ARA_NOALLOC_SCRATCH_BYTES per GPU, held from the library's
+ * first use on that GPU until the process exits).  Every call on a GPU
+ * reuses that one block: calls that may overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
+ *
+ *   ylt          device (or managed) memory, n >= 1 year losses
+ *   return_periods, n_rp
+ *                host array, 1 <= n_rp <= ARA_NOALLOC_MAX_RP, each RP >= 1
+ *   pml_out, tvar_out
+ *                n_rp doubles each, host or device memory
+ *   cuda_stream  cudaStream_t to run on (NULL: the legacy default stream);
+ *                the current device must be the device that holds ylt
+ *
+ * The first call on each device looks up the device address of the fixed
+ * block (cudaGetSymbolAddress); make that first call before any stream
+ * capture begins.  With host outputs the call synchronises the stream.
+ * Returns ARA_OK, ARA_EINVAL (NULL or host ylt, n < 1, n_rp outside
+ * 1..ARA_NOALLOC_MAX_RP, RP < 1) or ARA_ECUDA.  It never calls cudaMalloc,
+ * cudaFree or any allocating routine. */
+#define ARA_NOALLOC_MAX_RP 64
+#define ARA_NOALLOC_SCRATCH_BYTES 16384
+ARA_API int ara_pml_tvar_noalloc(const double *ylt, int64_t n, const double *return_periods, int32_t n_rp,
+                                 double *pml_out, double *tvar_out, void *cuda_stream);
+
 /* Counters of the last ara_run_layer* call. */
 ARA_API int ara_get_stats(const ara_ctx *ctx, ara_stats *out);
 

@@ -37,7 +37,9 @@ EXPORTED = (
     "ara_create", "ara_set_stream", "ara_load_yet", "ara_load_elts", "ara_run_layer",
     "ara_run_layer_diag", "ara_pml_tvar", "ara_sort_ylt", "ara_debug_uniforms",
     "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
+    "ara_pml_tvar_noalloc",
 )
+ARA_NOALLOC_MAX_RP = 64
 
 
 class AraError(RuntimeError):
@@ -121,6 +123,7 @@ def load_library(path: str = LIB_PATH):
     lib.ara_sort_ylt.argtypes = [P, P, i64, P]
     lib.ara_debug_uniforms.argtypes = [P, u64, i64, P, P, P, P]
     lib.ara_debug_record_losses.argtypes = [P, i64, P, P, P, P, i32, P, P]
+    lib.ara_pml_tvar_noalloc.argtypes = [P, i64, P, i32, P, P, P]
     lib.ara_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
     lib.ara_get_timing.argtypes = [P, ctypes.POINTER(Timing), ctypes.c_int]
     lib.ara_last_error.argtypes = [P]
@@ -216,6 +219,13 @@ def ara_debug_record_losses(h, n, mean, sigma, exposure, z, newton_only, out, it
                                                   _ptr(exposure, np.float32), _ptr(z, np.float32),
                                                   int(newton_only), _ptr(out, np.float32),
                                                   _ptr(iters_out, np.int32))
+
+
+def ara_pml_tvar_noalloc(ylt, n, return_periods, n_rp, pml_out, tvar_out, cuda_stream: int = 0):
+    """PML / TVaR without device allocation (no context; ylt must be device memory)."""
+    return load_library().ara_pml_tvar_noalloc(_ptr(ylt, np.float64), int(n), _ptr(return_periods, np.float64),
+                                               int(n_rp), _ptr(pml_out, np.float64), _ptr(tvar_out, np.float64),
+                                               ctypes.c_void_p(cuda_stream or None))
 
 
 def ara_get_stats(h, out: Stats):

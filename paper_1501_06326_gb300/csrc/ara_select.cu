@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "../../include/ara.h"
 #include "ara_internal.h"
 
 namespace ara {
@@ -275,3 +276,70 @@ cudaError_t sort_desc_device(const double* ylt, int64_t n, int64_t* order, void*
 }
 
 }  // namespace ara
+
+// =============================================================== allocation-free PML / TVaR
+//
+// A fixed block of device memory, owned by the library, holds the select
+// state of ara_pml_tvar_noalloc and its device outputs.  In host code the
+// name of a __device__ array is only a host-side stand-in; the kernels get
+// the block's device address, looked up once per device.
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ARA_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};  // device address of the block, per device
+
+static_assert(ARA_NOALLOC_SCRATCH_BYTES >= 2 * ARA_NOALLOC_MAX_RP * sizeof(double) + 2048 + 304 * 16 + 256,
+              "fixed block too small for the select state");
+
+}  // namespace
+
+extern "C" ARA_API int ara_pml_tvar_noalloc(const double* ylt, int64_t n, const double* return_periods, int32_t n_rp,
+                                            double* pml_out, double* tvar_out, void* cuda_stream) {
+  if (!ylt || n < 1 || !return_periods || n_rp < 1 || n_rp > ARA_NOALLOC_MAX_RP || !pml_out || !tvar_out)
+    return ARA_EINVAL;
+  for (int32_t r = 0; r < n_rp; ++r)
+    if (!(return_periods[r] >= 1.0) || !std::isfinite(return_periods[r])) return ARA_EINVAL;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ylt) != cudaSuccess) {
+    cudaGetLastError();
+    return ARA_EINVAL;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return ARA_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return ARA_ECUDA;
+  // set-up, once per device (with that device current): the block's device address
+  if (g_noalloc_addr[dev] == nullptr) {
+    void* addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || addr == nullptr) {
+      cudaGetLastError();
+      return ARA_ECUDA;
+    }
+    g_noalloc_addr[dev] = addr;
+  }
+  unsigned char* block = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  double* d_out = reinterpret_cast<double*>(block);                      // 2 * ARA_NOALLOC_MAX_RP doubles
+  void* state = block + 2 * ARA_NOALLOC_MAX_RP * sizeof(double);          // select state (256-aligned)
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  auto is_dev = [](const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  };
+  const bool pml_dev = is_dev(pml_out), tvar_dev = is_dev(tvar_out);
+  double* d_pml = pml_dev ? pml_out : d_out;
+  double* d_tvar = tvar_dev ? tvar_out : d_out + ARA_NOALLOC_MAX_RP;
+  // the select kernels reset their own histogram and state on every call
+  if (ara::pml_tvar_device(ylt, n, return_periods, n_rp, d_pml, d_tvar, state, s, nullptr) != cudaSuccess)
+    return ARA_ECUDA;
+  if (!pml_dev && cudaMemcpyAsync(pml_out, d_pml, sizeof(double) * n_rp, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return ARA_ECUDA;
+  if (!tvar_dev && cudaMemcpyAsync(tvar_out, d_tvar, sizeof(double) * n_rp, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return ARA_ECUDA;
+  if ((!pml_dev || !tvar_dev) && cudaStreamSynchronize(s) != cudaSuccess) return ARA_ECUDA;
+  return ARA_OK;
+}
