@@ -106,7 +106,7 @@ typedef struct {
     int64_t n_nonconverged;  /* Beta inversions that hit the iteration cap */
     int64_t n_newton;        /* pairs inverted by the Halley iteration (not the table alone) */
     float index_ms;          /* per-layer index build, device time */
-    float kernel_ms;         /* main layer kernel, device time */
+    float kernel_ms;         /* layer kernels (gather + losses), device time */
     int32_t grid;            /* CTAs of the main kernel */
     int32_t block;           /* threads per CTA */
     int32_t smem_bytes;      /* dynamic shared memory per CTA */
@@ -118,7 +118,9 @@ typedef struct {
  * each launch group). */
 typedef struct {
     int64_t layer_calls;     /* ara_run_layer* calls */
-    double kernel_ms;        /* sum of the main layer kernel's durations */
+    double kernel_ms;        /* sum of the layer kernels' durations (gather + losses) */
+    double gather_ms;        /* of which the gather kernel (YET stream, filter, hit records) */
+    double losses_ms;        /* of which the losses kernel (Beta inversion, terms, trial sums) */
     double index_ms;         /* sum of the per-layer index builds */
     int64_t pml_calls;       /* ara_pml_tvar calls */
     double pml_ms;           /* sum of the PML/TVaR selections */
@@ -137,7 +139,8 @@ ARA_API int ara_set_stream(ara_ctx *ctx, void *cuda_stream);
 /* Load (replace) the Year Event Table (Section 2.1 (i)).  Trial t owns
  * event_ids[offsets[t] .. offsets[t+1]), in time order.  offsets has
  * n_trials + 1 entries, offsets[0] == 0 and non-decreasing; every id lies in
- * [0, catalogue_size).  Time stamps are not needed: they only fix the order.
+ * [0, catalogue_size); a trial holds fewer than 2^22 events.  Time stamps
+ * are not needed: they only fix the order.
  * Errors: ARA_EINVAL (bad sizes, offsets or ids), ARA_ENOMEM, ARA_ECUDA. */
 ARA_API int ara_load_yet(ara_ctx *ctx, int64_t n_trials, const int64_t *offsets, const int32_t *event_ids,
                  int32_t catalogue_size);
@@ -165,6 +168,8 @@ ARA_API int ara_load_elts(ara_ctx *ctx, int32_t n_elts, const int32_t *elt_ids, 
  * event index k (position in the trial, from 0) and ELT pool id j is word 0
  * of Philox4x32-10 with counter (t mod 2^32, k, j, t >> 32) and key
  * (seed mod 2^32, seed >> 32), mapped to ((w >> 9) + 0.5) * 2^-23.
+ * Working memory: 8 bytes per YET entry of the trial range (hit-event
+ * records), kept by the context between calls.
  * The loss arithmetic is FP32; each trial's running sum of occurrence losses
  * is FP64.  Event ids outside the catalogue were rejected at load.
  * Errors: ARA_EINVAL (bad layer or range), ARA_ENOTLOADED, ARA_ENOMEM,

@@ -91,6 +91,8 @@ class Timing(ctypes.Structure):
     _fields_ = [
         ("layer_calls", ctypes.c_int64),
         ("kernel_ms", ctypes.c_double),
+        ("gather_ms", ctypes.c_double),
+        ("losses_ms", ctypes.c_double),
         ("index_ms", ctypes.c_double),
         ("pml_calls", ctypes.c_int64),
         ("pml_ms", ctypes.c_double),

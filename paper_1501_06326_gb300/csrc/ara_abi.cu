@@ -49,6 +49,7 @@ struct ara_ctx {
   std::map<int32_t, Elt> pool;
   // per-layer index (grown on demand)
   DevBuf bits, word_cnt, word_pairs, rankdir, mask, slot_cnt, pairs, scan_tmp;
+  DevBuf ev_buf, tile_cnt;  // hit-event records of the layer kernels
   // misc scratch
   DevBuf flags;     // uint32 flags + int32 max event
   DevBuf counters;  // 4 x u64
@@ -61,7 +62,7 @@ struct ara_ctx {
   ara_stats stats{};
   // timing accumulators: event pairs recorded around launch groups since the last reset
   struct Timed {
-    int kind;  // 0 layer kernel, 1 index build, 2 pml/tvar
+    int kind;  // 0 gather kernel, 1 index build, 2 pml/tvar, 3 losses kernel
     cudaEvent_t a, b;
   };
   std::vector<cudaEvent_t> ev_pool;
@@ -234,7 +235,7 @@ int ara_load_yet(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int
   ARA_CUDA(c, cudaMemcpyAsync(&h_flags, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
   ARA_CUDA(c, cudaStreamSynchronize(c->stream));
   if (h_flags & ara::kBadOffsets) return fail(c, ARA_EINVAL, "ara_load_yet: offsets are not non-decreasing");
-  if (h_flags & ara::kLongTrial) return fail(c, ARA_EINVAL, "ara_load_yet: a trial has 2^24 or more events");
+  if (h_flags & ara::kLongTrial) return fail(c, ARA_EINVAL, "ara_load_yet: a trial has 2^22 or more events");
   if (h_flags & ara::kBadEventId)
     return fail(c, ARA_EINVAL, "ara_load_yet: an event id lies outside [0, %d)", catalogue_size);
   c->n_trials = n_trials;
@@ -393,7 +394,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   ara::LayerEltRefs refs{};
   refs.n_elts = L->n_elts;
   refs.rec_begin[0] = 0;
-  ara::LayerParams p{};
+  ara::LossParams p{};
   for (int i = 0; i < L->n_elts; ++i) {
     auto it = c->pool.find(ids[i]);
     if (it == c->pool.end()) return fail(c, ARA_ENOTLOADED, "ara_run_layer: ELT %d is not loaded", ids[i]);
@@ -411,14 +412,14 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
     p.t_share[i] = el.terms.share;
   }
   const int64_t n_recs = refs.rec_begin[L->n_elts];
-  if (n_recs >= (int64_t(1) << 32) - 1) return fail(c, ARA_EINVAL, "ara_run_layer: layer holds too many records");
+  if (n_recs >= (int64_t(1) << 31) - 1) return fail(c, ARA_EINVAL, "ara_run_layer: layer holds too many records");
   // ---- per-layer index
   const int64_t n_words = (static_cast<int64_t>(c->catalogue) + 31) / 32;
   const size_t tmp_words = std::max(ara::scan_tmp_words(n_words), ara::scan_tmp_words(n_recs));
   if ((rc = reserve(c, c->bits, sizeof(uint32_t) * n_words)) ||
       (rc = reserve(c, c->word_cnt, sizeof(uint32_t) * (n_words + 1))) ||
       (rc = reserve(c, c->word_pairs, sizeof(uint32_t) * (n_words + 1))) ||
-      (rc = reserve(c, c->rankdir, sizeof(uint4) * n_words)) ||
+      (rc = reserve(c, c->rankdir, sizeof(uint2) * n_words)) ||
       (rc = reserve(c, c->mask, sizeof(uint32_t) * (n_recs + 1))) ||
       (rc = reserve(c, c->slot_cnt, sizeof(uint32_t) * (n_recs + 2))) ||
       (rc = reserve(c, c->pairs, sizeof(ara::Pair) * (n_recs + 1))) ||
@@ -428,7 +429,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   ix.bits = static_cast<uint32_t*>(c->bits.ptr);
   ix.word_cnt = static_cast<uint32_t*>(c->word_cnt.ptr);
   ix.word_pairs = static_cast<uint32_t*>(c->word_pairs.ptr);
-  ix.rankdir = static_cast<uint4*>(c->rankdir.ptr);
+  ix.rankdir = static_cast<uint2*>(c->rankdir.ptr);
   ix.mask = static_cast<uint32_t*>(c->mask.ptr);
   ix.slot_cnt = static_cast<uint32_t*>(c->slot_cnt.ptr);
   ix.pairs = static_cast<ara::Pair*>(c->pairs.ptr);
@@ -462,25 +463,40 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   ARA_CUDA(c, ara::build_layer_index(refs, ix, c->stream, &launched));
   ARA_CUDA(c, cudaEventRecord(ib, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
-  // filter: the largest power-of-two word count that fits next to the fixed shared-memory use
-  int filt_words = 1;
-  const size_t fixed = ara::layer_smem_bytes(0);
-  while (filt_words < n_words && fixed + sizeof(uint32_t) * (filt_words * 2) <= static_cast<size_t>(c->max_smem))
-    filt_words *= 2;
-  const size_t smem = ara::layer_smem_bytes(filt_words);
+  // ---- layer kernels: gather (YET -> hit-event records), then losses
+  const int filt_words = ara::gather_filter_words(n_words, c->max_smem);
+  const size_t smem = ara::gather_smem_bytes(filt_words);
   if (smem > static_cast<size_t>(c->max_smem))
     return fail(c, ARA_ECUDA, "ara_run_layer: kernel needs %zu bytes of shared memory, device allows %d", smem,
                 c->max_smem);
   const int64_t n_tiles = (n_out + ara::kWarpTrials - 1) / ara::kWarpTrials;
-  p.off = static_cast<const int64_t*>(c->yet_off.ptr);
-  p.ids = static_cast<const int32_t*>(c->yet_ids.ptr);
+  const int64_t e0 = c->h_off[t0], e1 = c->h_off[t1];
+  if ((rc = reserve(c, c->ev_buf, sizeof(uint2) * (e1 - e0 + 1))) ||
+      (rc = reserve(c, c->tile_cnt, sizeof(uint32_t) * (n_tiles + 1))))
+    return rc;
+  unsigned long long* counters = static_cast<unsigned long long*>(c->counters.ptr);
+  ara::GatherParams g{};
+  g.off = static_cast<const int64_t*>(c->yet_off.ptr);
+  g.ids = static_cast<const int32_t*>(c->yet_ids.ptr);
+  g.t_begin = t0;
+  g.t_end = t1;
+  g.n_tiles = n_tiles;
+  g.e0 = e0;
+  g.rankdir = ix.rankdir;
+  g.n_words = n_words;
+  g.slot_start = ix.slot_cnt;
+  g.filt_words = filt_words;
+  g.ev_buf = static_cast<uint2*>(c->ev_buf.ptr);
+  g.tile_cnt = static_cast<uint32_t*>(c->tile_cnt.ptr);
+  g.queue = counters + 4;
+  p.off = g.off;
   p.t_begin = t0;
   p.t_end = t1;
-  p.rankdir = ix.rankdir;
-  p.n_words = n_words;
-  p.slot_start = ix.slot_cnt;
+  p.n_tiles = n_tiles;
+  p.e0 = e0;
+  p.ev_buf = g.ev_buf;
+  p.tile_cnt = g.tile_cnt;
   p.pairs = ix.pairs;
-  p.filt_words = filt_words;
   p.n_elts = L->n_elts;
   p.occ_r = static_cast<float>(L->occ_retention);
   p.occ_l = static_cast<float>(L->occ_limit);
@@ -490,19 +506,24 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   p.seed_hi = static_cast<uint32_t>(seed >> 32);
   p.primary_only = (L->flags & ARA_PRIMARY_ONLY) ? 1 : 0;
   p.newton_only = (L->flags & ARA_NEWTON_ONLY) ? 1 : 0;
-  p.n_tiles = n_tiles;
   p.ylt = d_ylt;
   p.diag_hits = d_hits;
   p.diag_hash = d_hash;
-  p.counters = static_cast<unsigned long long*>(c->counters.ptr);
-  ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 4 * sizeof(unsigned long long), c->stream));
-  const int grid = static_cast<int>(std::min<int64_t>(c->num_sms, (n_tiles + 31) / 32));
+  p.counters = counters;
+  ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 8 * sizeof(unsigned long long), c->stream));
+  const int64_t warps_per_sm = ara::kGatherThreads / 32;
+  const int grid = static_cast<int>(std::min<int64_t>(c->num_sms, (n_tiles + warps_per_sm - 1) / warps_per_sm));
+  cudaEvent_t la, lb;
+  if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "ara_run_layer: cannot create timing events");
   ARA_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
   ARA_CUDA(c, cudaEventRecord(ka, c->stream));
-  ARA_CUDA(c, ara::launch_layer_kernel(p, grid, smem, c->stream));
+  ARA_CUDA(c, ara::launch_gather(g, grid, smem, c->stream));
   ARA_CUDA(c, cudaEventRecord(kb, c->stream));
+  ARA_CUDA(c, cudaEventRecord(la, c->stream));
+  ARA_CUDA(c, ara::launch_losses(p, grid, c->stream));
+  ARA_CUDA(c, cudaEventRecord(lb, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
-  launched += 1;
+  launched += 2;
   c->launches += launched;
   if (!ylt_dev)
     ARA_CUDA(c, cudaMemcpyAsync(ylt_out, d_ylt, sizeof(double) * n_out, cudaMemcpyDeviceToHost, c->stream));
@@ -516,7 +537,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   c->stats.n_events = c->h_off[t1] - c->h_off[t0];
   c->stats.n_evals = c->stats.n_events * L->n_elts;
   c->stats.grid = grid;
-  c->stats.block = ara::kLayerThreads;
+  c->stats.block = ara::kGatherThreads;
   c->stats.smem_bytes = static_cast<int32_t>(smem);
   c->stats.filter_bits = filt_words * 32;
   c->stats.kernel_ms = -1.0f;
@@ -566,6 +587,10 @@ int ara_get_timing(ara_ctx* c, ara_timing* out, int reset) {
     if (t.kind == 0) {
       out->layer_calls += 1;
       out->kernel_ms += ms;
+      out->gather_ms += ms;
+    } else if (t.kind == 3) {
+      out->kernel_ms += ms;
+      out->losses_ms += ms;
     } else if (t.kind == 1) {
       out->index_ms += ms;
     } else {
@@ -739,7 +764,7 @@ void ara_destroy(ara_ctx* c) {
     release(c, kv.second.recs);
     release(c, kv.second.tab);
   }
-  DevBuf* bufs[] = {&c->yet_off, &c->yet_ids, &c->bits,  &c->word_cnt, &c->word_pairs, &c->rankdir, &c->mask,   &c->slot_cnt,
+  DevBuf* bufs[] = {&c->ev_buf, &c->tile_cnt, &c->yet_off, &c->yet_ids, &c->bits,  &c->word_cnt, &c->word_pairs, &c->rankdir, &c->mask,   &c->slot_cnt,
                     &c->pairs,   &c->scan_tmp, &c->flags, &c->counters, &c->ylt_tmp, &c->diag_tmp, &c->sel,
                     &c->in_tmp,  &c->out_tmp};
   for (DevBuf* b : bufs) release(c, *b);

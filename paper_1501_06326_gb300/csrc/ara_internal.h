@@ -17,7 +17,7 @@ enum : uint32_t {
   kBadOrder = 4u,      // ELT event ids not strictly increasing
   kBadValue = 8u,      // negative / non-finite mean, sigma or exposure
   kBadExposure = 16u,  // exposure <= mean for a record with mean > 0 and sigma > 0
-  kLongTrial = 32u,    // a trial with 2^24 or more events
+  kLongTrial = 32u,    // a trial with 2^22 or more events
 };
 
 cudaError_t launch_check_offsets(const int64_t* off, int64_t n_trials, int64_t n_events, uint32_t* flags,
@@ -60,7 +60,8 @@ struct LayerIndex {
   uint32_t* bits;        // [n_words] membership bitmap over the catalogue
   uint32_t* word_cnt;    // [n_words + 1] scratch: popcounts, then exclusive scan
   uint32_t* word_pairs;  // [n_words + 1] scratch: pairs per word, then exclusive scan
-  uint4* rankdir;        // [n_words] {bits, slots before the word, pairs before the word, multi-pair flag}
+  uint2* rankdir;        // [n_words] {bits, base}: base = pairs before the word, or (1 << 31) | slots
+                         // before the word when the word holds an event with several ELT records
   uint32_t* mask;        // [n_recs] per slot: bitmask of layer positions
   uint32_t* slot_cnt;    // [n_recs + 1] scratch -> slot_start
   Pair* pairs;           // [n_recs]
@@ -71,39 +72,59 @@ struct LayerIndex {
 
 cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStream_t s, int* n_launch);
 
-// --------------------------------------------------------------- main kernel
-constexpr int kLayerThreads = 1024;  // 32 independent warps per CTA, one CTA per SM
-constexpr int kWarpTrials = 8;       // trials per warp tile
-constexpr int kRing = 160;           // per-warp ring of filter positives (>= 31 + 128)
-constexpr int kEvRing = 64;          // per-warp ring of resolved events (>= 31 + 32)
+// --------------------------------------------------------------- main kernels
+// The layer runs as two kernels over tiles of kWarpTrials consecutive trials:
+//   k_gather  streams the YET, filters the events, resolves the hits and writes
+//             one 8-byte record per hit event into the tile's region of an
+//             event buffer (the region of a tile starts at its first event);
+//   k_losses  reads the records of a tile and computes the pair losses, event
+//             losses, trial sums and year losses.
+// Event record: x = (trial in tile << 27) | ((pairs - 1) << 22) | k, y = first pair.
+constexpr int kGatherThreads = 1024;  // 32 warps per CTA, one CTA per SM
+constexpr int kLossThreads = 1024;
+constexpr int kWarpTrials = 8;        // trials per tile (< 32)
+constexpr int kMaxTrialEvents = 1 << 22;
 
-struct LayerParams {
+struct GatherParams {
   const int64_t* off;
   const int32_t* ids;
-  int64_t t_begin, t_end;
-  const uint4* rankdir;
+  int64_t t_begin, t_end, n_tiles;
+  int64_t e0;  // off[t_begin]: the event buffer is indexed from here
+  const uint2* rankdir;
   int64_t n_words;
   const uint32_t* slot_start;
-  const Pair* pairs;
   int32_t filt_words;  // power of two
+  uint2* ev_buf;
+  uint32_t* tile_cnt;
+  unsigned long long* queue;  // tile counter
+};
+
+struct LossParams {
+  const int64_t* off;
+  int64_t t_begin, t_end, n_tiles;
+  int64_t e0;
+  const uint2* ev_buf;
+  const uint32_t* tile_cnt;
+  const Pair* pairs;
   int32_t n_elts;
-  const float4* tab[32];  // quantile tables of the layer's ELTs (by position)
-  int32_t newton_only;
   int32_t elt_id[32];
+  const float4* tab[32];  // quantile tables of the layer's ELTs (by position)
   float t_ret[32], t_lim[32], t_share[32];
   float occ_r, occ_l;  // occurrence terms in FP32 (the loss arithmetic)
   double agg_r, agg_l;
   uint32_t seed_lo, seed_hi;
   int32_t primary_only;
-  int64_t n_tiles;
+  int32_t newton_only;
   double* ylt;
   int64_t* diag_hits;
   uint64_t* diag_hash;
-  unsigned long long* counters;  // [0] tile queue, [1] pairs hit, [2] non-converged, [3] Halley pairs
+  unsigned long long* counters;  // [0] tile queue, [1] pairs, [2] non-converged, [3] Halley events
 };
 
-size_t layer_smem_bytes(int filt_words);
-cudaError_t launch_layer_kernel(const LayerParams& p, int grid, size_t smem, cudaStream_t s);
+size_t gather_smem_bytes(int filt_words);
+int gather_filter_words(int64_t n_words, int max_smem);
+cudaError_t launch_gather(const GatherParams& p, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_losses(const LossParams& p, int grid, cudaStream_t s);
 
 // --------------------------------------------------------------- PML / TVaR / sort
 // Scratch sizes in bytes for n year losses.

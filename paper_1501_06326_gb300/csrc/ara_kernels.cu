@@ -53,7 +53,7 @@ __global__ void k_check_offsets(const int64_t* off, int64_t n_trials, int64_t n_
   for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < n_trials; t += stride) {
     const int64_t a = off[t], b = off[t + 1];
     if (b < a) f |= kBadOffsets;
-    if (b - a >= (int64_t(1) << 24)) f |= kLongTrial;
+    if (b - a >= static_cast<int64_t>(kMaxTrialEvents)) f |= kLongTrial;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (off[0] != 0 || off[n_trials] != n_events) f |= kBadOffsets;
@@ -459,29 +459,32 @@ __global__ void k_word_popc(const uint32_t* bits, int64_t n_words, uint32_t* cnt
     cnt[w] = __popc(bits[w]);
 }
 
+// rankdir[w] = {bits, base}: base = pairs before the word when every event of
+// the word has one ELT record (its pair is then base + rank in the word), else
+// (1 << 31) | slots before the word (pair range from slot_start).
 __global__ void k_pack_rankdir(const uint32_t* bits, const uint32_t* base, const uint32_t* pbase, int64_t n_words,
-                               uint4* rankdir) {
+                               uint2* rankdir) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t w = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; w < n_words; w += stride) {
     const uint32_t b = bits[w];
-    const uint32_t multi = (pbase[w + 1] - pbase[w] != static_cast<uint32_t>(__popc(b))) ? 1u : 0u;
-    rankdir[w] = make_uint4(b, base[w], pbase[w], multi);
+    const bool multi = (pbase[w + 1] - pbase[w] != static_cast<uint32_t>(__popc(b)));
+    rankdir[w] = make_uint2(b, multi ? (0x80000000u | base[w]) : pbase[w]);
   }
 }
 
-__device__ __forceinline__ uint32_t rank_of(const uint4* rankdir, int32_t e) {
-  const uint4 rd = rankdir[e >> 5];
+// Slot (rank among the layer's events) of a member event e.
+__device__ __forceinline__ uint32_t rank_of(const uint32_t* bits, const uint32_t* slot_base, int32_t e) {
   const uint32_t bit = 1u << (e & 31);
-  return rd.y + __popc(rd.x & (bit - 1u));
+  return slot_base[e >> 5] + __popc(bits[e >> 5] & (bit - 1u));
 }
 
-__global__ void k_mark_positions(LayerEltRefs r, const uint4* rankdir, uint32_t* mask) {
+__global__ void k_mark_positions(LayerEltRefs r, const uint32_t* bits, const uint32_t* slot_base, uint32_t* mask) {
   const int64_t n = r.rec_begin[r.n_elts];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
     const int p = find_pos(r, i);
     const int32_t e = r.events[p][i - r.rec_begin[p]];
-    atomicOr(&mask[rank_of(rankdir, e)], 1u << p);
+    atomicOr(&mask[rank_of(bits, slot_base, e)], 1u << p);
   }
 }
 
@@ -491,7 +494,7 @@ __global__ void k_slot_counts(const uint32_t* mask, int64_t n, uint32_t* cnt) {
     cnt[i] = __popc(mask[i]);
 }
 
-__global__ void k_fill_pairs(LayerEltRefs r, const uint4* rankdir, const uint32_t* mask,
+__global__ void k_fill_pairs(LayerEltRefs r, const uint32_t* bits, const uint32_t* slot_base, const uint32_t* mask,
                              const uint32_t* slot_start, Pair* pairs) {
   const int64_t n = r.rec_begin[r.n_elts];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -499,7 +502,7 @@ __global__ void k_fill_pairs(LayerEltRefs r, const uint4* rankdir, const uint32_
     const int p = find_pos(r, i);
     const int64_t j = i - r.rec_begin[p];
     const int32_t e = r.events[p][j];
-    const uint32_t slot = rank_of(rankdir, e);
+    const uint32_t slot = rank_of(bits, slot_base, e);
     const uint32_t within = __popc(mask[slot] & ((1u << p) - 1u));
     Pair q = r.recs[p][j];
     q.meta = (q.meta & ~31u) | static_cast<uint32_t>(p);
@@ -540,13 +543,13 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
   ++launched;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (n_recs > 0) {
-    k_mark_positions<<<grid_for(n_recs, 256), 256, 0, s>>>(refs, ix.rankdir, ix.mask);
+    k_mark_positions<<<grid_for(n_recs, 256), 256, 0, s>>>(refs, ix.bits, ix.word_cnt, ix.mask);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     k_slot_counts<<<grid_for(n_recs, 256), 256, 0, s>>>(ix.mask, n_recs, ix.slot_cnt);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if ((err = scan_exclusive_u32(ix.slot_cnt, ix.slot_cnt, n_recs, ix.scan_tmp, s, &launched)) != cudaSuccess)
       return err;
-    k_fill_pairs<<<grid_for(n_recs, 256), 256, 0, s>>>(refs, ix.rankdir, ix.mask, ix.slot_cnt, ix.pairs);
+    k_fill_pairs<<<grid_for(n_recs, 256), 256, 0, s>>>(refs, ix.bits, ix.word_cnt, ix.mask, ix.slot_cnt, ix.pairs);
     launched += 3;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   } else {
@@ -556,51 +559,176 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
   return cudaSuccess;
 }
 
-// =============================================================== fused layer kernel
+// =============================================================== layer kernels
 //
-// One persistent CTA of 32 warps per SM.  The CTA builds a shared-memory
-// membership filter of the layer (the catalogue bitmap folded modulo the
-// filter size) once; after that every warp is an independent pipeline that
-// needs no block-wide barrier.  A warp takes tiles of kWarpTrials consecutive
-// trials from a global queue and, per tile:
-//   1. streams the tile's YET ids, 128 per step (one int4 per lane,
-//      evict-first, two steps prefetched), tests each id against the filter
-//      and appends the positives, in YET order, to a warp-private ring;
-//   2. resolves 32 positives at a time against the rank directory (one
-//      16-byte load gives the word's bits and its slot and pair bases; words
-//      holding a multi-ELT event read the slot's pair range) and appends the
-//      true events, with their pair ranges, to a second ring;
-//   3. takes whole events from that ring, up to 32 (event, ELT) pairs per
-//      batch, one pair per lane: Philox uniform, inverse Beta through the
-//      record's quantile table, ELT terms; a segmented warp reduction sums
-//      each event's pairs in layer order (FP32) and applies the occurrence
-//      terms, and a segmented double-float reduction adds the occurrence
-//      losses of each trial into the trial's FP64 running sum (one FP64 add
-//      per trial and batch);
-//      events with a pair whose record's table is not exact are deferred and
-//      resolved, 32 at a time, by the FP32 Halley iteration;
-//   4. turns each running sum into the trial's year loss with the aggregate
-//      terms.
+// k_gather: one persistent CTA of 32 warps per SM.  The CTA folds the layer's
+// catalogue bitmap into a shared-memory membership filter once; then each warp
+// independently takes tiles of kWarpTrials consecutive trials and streams the
+// tile's YET ids, 128 per step (one int4 per lane, evict-first, the next step
+// in flight).  Each id is tested against the filter; each positive is resolved
+// against the rank directory (8 bytes: the word's bits and its pair base) and,
+// if it is a member, becomes an event record written in YET order to the
+// tile's region of the event buffer.
+//
+// k_losses: each warp takes tiles and reads their records in windows of up to
+// 32 events whose (event, ELT) pairs number at most 32, one pair per lane:
+// Philox uniform, inverse Beta through the record's quantile table, ELT terms.
+// A segmented warp reduction sums each event's pair losses in layer order
+// (FP32) and applies the occurrence terms; a segmented double-float reduction
+// adds the window's occurrence losses of each trial into the trial's FP64
+// running sum (one FP64 add per trial and window).  Events with a pair whose
+// record's table is not exact are deferred and resolved, 32 at a time, by the
+// FP32 Halley iteration.  The aggregate terms turn each running sum into the
+// trial's year loss.
 
 namespace {
 
-struct WarpSmem {
-  uint32_t q_key[kRing];   // positives: (trial in tile << 24) | event index k
-  uint32_t q_ev[kRing];    //            event id
-  uint32_t e_key[kEvRing]; // true events: key, first pair, pair count
-  uint32_t e_ps[kEvRing];
-  uint32_t e_cnt[kEvRing];
-  uint32_t pb[33];         // batch: first pair lane of each event
-  uint32_t d_key[32];      // deferred events: key, first pair, pair count
-  uint32_t d_ps[32];
-  uint32_t d_cnt[32];
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
+
+constexpr uint32_t kRecTrialShift = 27;
+constexpr uint32_t kRecCntShift = 22;
+constexpr uint32_t kRecKMask = (1u << 22) - 1u;
+
+struct GatherWarp {
   int32_t off[kWarpTrials + 1];  // trial offsets relative to the tile's first event
+};
+
+}  // namespace
+
+size_t gather_smem_bytes(int filt_words) {
+  return sizeof(uint32_t) * static_cast<size_t>(filt_words) + sizeof(GatherWarp) * (kGatherThreads / 32) + 16;
+}
+
+int gather_filter_words(int64_t n_words, int max_smem) {
+  int fw = 1;
+  while (fw < n_words && gather_smem_bytes(fw * 2) <= static_cast<size_t>(max_smem)) fw *= 2;
+  return fw;
+}
+
+__global__ void __launch_bounds__(kGatherThreads, 1) k_gather(const GatherParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  GatherWarp* gw = reinterpret_cast<GatherWarp*>(smem_raw);
+  uint32_t* filt = reinterpret_cast<uint32_t*>(gw + (kGatherThreads / 32));
+  const uint32_t lane = lane_id();
+  GatherWarp& ws = gw[threadIdx.x >> 5];
+  const uint32_t fmask = static_cast<uint32_t>(p.filt_words) - 1u;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+
+  for (int w = threadIdx.x; w < p.filt_words; w += blockDim.x) {
+    uint32_t v = 0;
+    for (int64_t k = w; k < p.n_words; k += p.filt_words) v |= p.rankdir[k].x;
+    filt[w] = v;
+  }
+  __syncthreads();
+
+  for (;;) {
+    int64_t tile = 0;
+    if (lane == 0) tile = static_cast<int64_t>(atomicAdd(p.queue, 1ull));
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= p.n_tiles) break;
+    const int64_t ta = p.t_begin + tile * kWarpTrials;
+    const int64_t tb = (ta + kWarpTrials < p.t_end) ? ta + kWarpTrials : p.t_end;
+    const int ntr = static_cast<int>(tb - ta);
+    const int64_t ea = __ldg(&p.off[ta]);
+    if (lane <= static_cast<uint32_t>(ntr)) ws.off[lane] = static_cast<int32_t>(__ldg(&p.off[ta + lane]) - ea);
+    __syncwarp();
+    const int32_t nev = ws.off[ntr];
+    const int32_t* ids = p.ids + (ea & ~int64_t(3));
+    const int32_t lead = static_cast<int32_t>(ea & 3);
+    const int32_t span = nev + lead;
+    uint2* out = p.ev_buf + (ea - p.e0);
+    uint32_t nout = 0;
+    int tcur = 0;
+    while (tcur + 1 < ntr && ws.off[tcur + 1] <= 0) ++tcur;
+    int4 cur = make_int4(0, 0, 0, 0);
+    if (4 * static_cast<int32_t>(lane) < span) cur = __ldcs(reinterpret_cast<const int4*>(ids) + lane);
+    for (int32_t c0 = 0; c0 < span; c0 += 128) {
+      int4 nxt = make_int4(0, 0, 0, 0);
+      if (c0 + 128 + 4 * static_cast<int32_t>(lane) < span)
+        nxt = __ldcs(reinterpret_cast<const int4*>(ids + c0 + 128) + lane);
+      const int32_t rel0 = c0 + 4 * static_cast<int32_t>(lane) - lead;
+      const int32_t ev[4] = {cur.x, cur.y, cur.z, cur.w};
+      // filter, then the rank-directory words of the positives (loads in flight together)
+      uint2 rd[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t e = static_cast<uint32_t>(ev[j]);
+        const bool in = static_cast<uint32_t>(rel0 + j) < static_cast<uint32_t>(nev);
+        rd[j] = make_uint2(0u, 0u);
+        if (in && ((filt[(e >> 5) & fmask] >> (e & 31)) & 1u)) rd[j] = __ldg(&p.rankdir[e >> 5]);
+      }
+      uint32_t tm = 0, key[4], ps[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t e = static_cast<uint32_t>(ev[j]);
+        const uint32_t bit = 1u << (e & 31);
+        key[j] = 0;
+        ps[j] = 0;
+        if (rd[j].x & bit) {
+          const uint32_t below = __popc(rd[j].x & (bit - 1u));
+          uint32_t cnt = 1;
+          if (rd[j].y & 0x80000000u) {
+            const uint32_t sl = (rd[j].y & 0x7FFFFFFFu) + below;
+            ps[j] = __ldg(&p.slot_start[sl]);
+            cnt = __ldg(&p.slot_start[sl + 1]) - ps[j];
+          } else {
+            ps[j] = rd[j].y + below;
+          }
+          key[j] = (cnt - 1u) << kRecCntShift;
+          tm |= 1u << j;
+        }
+      }
+      const uint32_t c = __popc(tm);
+      const uint32_t incl = warp_inclusive_scan(c);
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      if (tm) {
+        int t = tcur;
+        int32_t tnext = ws.off[t + 1];
+        uint32_t at = nout + incl - c;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (tm & (1u << j)) {
+            const int32_t rel = rel0 + j;
+            while (rel >= tnext && t + 1 < ntr) {
+              ++t;
+              tnext = ws.off[t + 1];
+            }
+            const uint32_t k = static_cast<uint32_t>(rel - ws.off[t]);
+            out[at] = make_uint2(key[j] | (static_cast<uint32_t>(t) << kRecTrialShift) | k, ps[j]);
+            ++at;
+          }
+        }
+      }
+      nout += total;
+      {
+        const int32_t nrel = c0 + 128 - lead;
+        while (tcur + 1 < ntr && ws.off[tcur + 1] <= nrel) ++tcur;
+      }
+      cur = nxt;
+    }
+    if (lane == 0) p.tile_cnt[tile] = nout;
+    __syncwarp();
+  }
+  (void)lt_mask;
+}
+
+cudaError_t launch_gather(const GatherParams& p, int grid, size_t smem, cudaStream_t s) {
+  cudaError_t err =
+      cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (err != cudaSuccess) return err;
+  k_gather<<<grid, kGatherThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+namespace {
+
+struct LossWarp {
+  uint32_t d_key[32];  // deferred events: record
+  uint32_t d_ps[32];
   double S[kWarpTrials];
   unsigned long long hits[kWarpTrials];
   unsigned long long hash[kWarpTrials];
 };
-
-__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
 // (hi, lo) + (hi2, lo2) in double-float arithmetic (TwoSum, then renormalise).
 __device__ __forceinline__ void df_add(float& hi, float& lo, float hi2, float lo2) {
@@ -614,7 +742,7 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float hi2, float lo
 
 // Loss after ELT terms of one pair, for the table path; returns false when the
 // pair needs the Halley iteration.
-__device__ __forceinline__ bool pair_fast(const LayerParams& p, const Pair& pr, int64_t trial, uint32_t k, float* out) {
+__device__ __forceinline__ bool pair_fast(const LossParams& p, const Pair& pr, int64_t trial, uint32_t k, float* out) {
   const uint32_t kind = pair_kind(pr.meta);
   const uint32_t pos = pair_pos(pr.meta);
   float loss = pr.mu;
@@ -629,7 +757,7 @@ __device__ __forceinline__ bool pair_fast(const LayerParams& p, const Pair& pr, 
   return true;
 }
 
-__device__ __noinline__ float pair_slow(const LayerParams& p, const Pair& pr, int64_t trial, uint32_t k,
+__device__ __noinline__ float pair_slow(const LossParams& p, const Pair& pr, int64_t trial, uint32_t k,
                                         unsigned long long* nc) {
   const uint32_t pos = pair_pos(pr.meta);
   float v;
@@ -644,17 +772,18 @@ __device__ __noinline__ float pair_slow(const LayerParams& p, const Pair& pr, in
 
 // Resolve the deferred events of the warp (all lanes call it): each lane one
 // event, then the occurrence losses are added to the trial sums in list order.
-__device__ __noinline__ void resolve_deferred(const LayerParams& p, WarpSmem& ws, int nd, int64_t ta,
+__device__ __noinline__ void resolve_deferred(const LossParams& p, LossWarp& ws, int nd, int64_t ta,
                                               unsigned long long* nc, unsigned long long* n_slow) {
   const uint32_t lane = lane_id();
   float O = 0.0f;
   uint32_t tl = 0;
   if (lane < static_cast<uint32_t>(nd)) {
     const uint32_t key = ws.d_key[lane];
-    tl = key >> 24;
-    const uint32_t k = key & 0xFFFFFFu;
+    tl = key >> kRecTrialShift;
+    const uint32_t k = key & kRecKMask;
+    const uint32_t cnt = ((key >> kRecCntShift) & 31u) + 1u;
     float G = 0.0f;
-    for (uint32_t j = 0; j < ws.d_cnt[lane]; ++j) G += pair_slow(p, p.pairs[ws.d_ps[lane] + j], ta + tl, k, nc);
+    for (uint32_t j = 0; j < cnt; ++j) G += pair_slow(p, p.pairs[ws.d_ps[lane] + j], ta + tl, k, nc);
     O = clamp_terms_f(G, p.occ_r, p.occ_l);
     ++*n_slow;
   }
@@ -668,28 +797,12 @@ __device__ __noinline__ void resolve_deferred(const LayerParams& p, WarpSmem& ws
 
 }  // namespace
 
-size_t layer_smem_bytes(int filt_words) {
-  return sizeof(uint32_t) * static_cast<size_t>(filt_words) + sizeof(WarpSmem) * (kLayerThreads / 32) + 16;
-}
-
-__global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpSmem* wsm = reinterpret_cast<WarpSmem*>(smem_raw);
-  uint32_t* filt = reinterpret_cast<uint32_t*>(wsm + (kLayerThreads / 32));
+__global__ void __launch_bounds__(kLossThreads, 1) k_losses(const LossParams p) {
+  __shared__ LossWarp lw[kLossThreads / 32];
   const uint32_t lane = lane_id();
-  WarpSmem& ws = wsm[threadIdx.x >> 5];
+  LossWarp& ws = lw[threadIdx.x >> 5];
   const bool diag = (p.diag_hits != nullptr) || (p.diag_hash != nullptr);
-  const uint32_t fmask = static_cast<uint32_t>(p.filt_words) - 1u;
   const uint32_t lt_mask = (1u << lane) - 1u;
-
-  // ---- membership filter: catalogue bitmap folded modulo filt_words
-  for (int w = threadIdx.x; w < p.filt_words; w += blockDim.x) {
-    uint32_t v = 0;
-    for (int64_t k = w; k < p.n_words; k += p.filt_words) v |= p.rankdir[k].x;
-    filt[w] = v;
-  }
-  __syncthreads();
-
   unsigned long long n_nc = 0, n_slow = 0;
   uint32_t n_pairs = 0;
 
@@ -701,233 +814,110 @@ __global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p)
     const int64_t ta = p.t_begin + tile * kWarpTrials;
     const int64_t tb = (ta + kWarpTrials < p.t_end) ? ta + kWarpTrials : p.t_end;
     const int ntr = static_cast<int>(tb - ta);
-    const int64_t ea = __ldg(&p.off[ta]);
-    if (lane <= static_cast<uint32_t>(ntr)) ws.off[lane] = static_cast<int32_t>(__ldg(&p.off[ta + lane]) - ea);
+    const uint2* recs = p.ev_buf + (__ldg(&p.off[ta]) - p.e0);
+    const uint32_t n = __ldg(&p.tile_cnt[tile]);
     if (lane < static_cast<uint32_t>(ntr)) {
       ws.S[lane] = 0.0;
       ws.hits[lane] = 0ull;
       ws.hash[lane] = 0ull;
     }
     __syncwarp();
-    const int32_t nev = ws.off[ntr];  // events of the tile
-    int tcur = 0;                     // trial of the current chunk's first id (warp-uniform)
-    while (tcur + 1 < ntr && ws.off[tcur + 1] <= 0) ++tcur;
-    const int32_t* ids = p.ids + (ea & ~int64_t(3));
-    const int32_t lead = static_cast<int32_t>(ea & 3);  // ids[0 .. lead) precede the tile
-    const int32_t span = nev + lead;                    // ids to scan, from the aligned start
-    uint32_t qh = 0, qn = 0;  // positives ring head / fill (warp-uniform)
-    uint32_t eh = 0, en = 0;  // events ring head / fill
-    uint32_t epairs = 0;      // pairs queued in the events ring
-    int nd = 0;               // deferred events
-    // One step of the pipeline on 128 ids (in `cur`, starting at c0): filter,
-    // resolve, batches.
-    auto step = [&](const int4 cur, const int32_t c0) {
-      // ---- 1. filter 128 ids, append the positives in order
-        {
-          const int32_t rel0 = c0 + 4 * static_cast<int32_t>(lane) - lead;  // tile-relative position of cur.x
-          const int32_t ev[4] = {cur.x, cur.y, cur.z, cur.w};
-          uint32_t m = 0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const uint32_t e = static_cast<uint32_t>(ev[j]);
-            const bool in = static_cast<uint32_t>(rel0 + j) < static_cast<uint32_t>(nev);
-            if (in && ((filt[(e >> 5) & fmask] >> (e & 31)) & 1u)) m |= 1u << j;
-          }
-          const uint32_t c = __popc(m);
-          const uint32_t incl = warp_inclusive_scan(c);
-          const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-          if (m) {
-            // trial of each positive: from the warp's cursor (the trial of the
-            // chunk's first id), a chunk crosses at most a few trial boundaries
-            int t = tcur;
-            int32_t tnext = ws.off[t + 1];
-            uint32_t slot = qh + qn + incl - c;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              if (m & (1u << j)) {
-                const int32_t rel = rel0 + j;
-                while (rel >= tnext && t + 1 < ntr) {
-                  ++t;
-                  tnext = ws.off[t + 1];
-                }
-                const uint32_t at = slot >= kRing ? slot - kRing : slot;
-                ws.q_key[at] = (static_cast<uint32_t>(t) << 24) | static_cast<uint32_t>(rel - ws.off[t]);
-                ws.q_ev[at] = static_cast<uint32_t>(ev[j]);
-                ++slot;
-              }
-            }
-          }
-          qn += total;
-          // advance the cursor to the trial of the next chunk's first id
-          {
-            const int32_t nrel = c0 + 128 - lead;
-            while (tcur + 1 < ntr && ws.off[tcur + 1] <= nrel) ++tcur;
-          }
-          __syncwarp();
-        }
-        const bool tile_done = (c0 + 128 >= span);
-      // ---- 2. resolve positives, 32 at a time, into true events; after each
-        // resolve (and once more at the end of the tile) run the batches
-        for (;;) {
-          const bool resolve = (qn >= 32 || (tile_done && qn > 0));
-          if (resolve) {
-          const uint32_t nb = qn < 32 ? qn : 32;
-          const bool valid = lane < nb;
-          uint32_t qi = qh + lane;
-          if (qi >= kRing) qi -= kRing;
-          uint32_t ps = 0, cnt = 0, key = 0;
-          if (valid) {
-            key = ws.q_key[qi];
-            const uint32_t e = ws.q_ev[qi];
-            const uint4 rd = __ldg(&p.rankdir[e >> 5]);
-            const uint32_t bit = 1u << (e & 31);
-            if (rd.x & bit) {
-              const uint32_t below = __popc(rd.x & (bit - 1u));
-              if (rd.w == 0u) {
-                ps = rd.z + below;
-                cnt = 1;
-              } else {
-                const uint32_t sl = rd.y + below;
-                ps = __ldg(&p.slot_start[sl]);
-                cnt = __ldg(&p.slot_start[sl + 1]) - ps;
-              }
-            }
-          }
-          const uint32_t hit = __ballot_sync(0xffffffffu, cnt != 0);
-          if (cnt) {
-            uint32_t at = eh + en + __popc(hit & lt_mask);
-            at &= kEvRing - 1;
-            ws.e_key[at] = key;
-            ws.e_ps[at] = ps;
-            ws.e_cnt[at] = cnt;
-          }
-          en += __popc(hit);
-          epairs += __reduce_add_sync(0xffffffffu, cnt);
-          qh += nb;
-          if (qh >= kRing) qh -= kRing;
-          qn -= nb;
-          __syncwarp();
-          }
-          // ---- 3. batches of whole events, up to 32 pairs
-          while (epairs >= 32 || (tile_done && qn == 0 && en > 0)) {
-            // events taken: the longest prefix with at most 32 pairs
-            const uint32_t ei = (eh + lane) & (kEvRing - 1);
-            const bool ev_ok = lane < en;
-            const uint32_t my_cnt = ev_ok ? ws.e_cnt[ei] : 0u;
-            const uint32_t cincl = warp_inclusive_scan(my_cnt);
-            const uint32_t take = __ballot_sync(0xffffffffu, ev_ok && cincl <= 32u);
-            const uint32_t n_take = __popc(take);  // a prefix: cincl grows with the lane
-            const uint32_t np = __shfl_sync(0xffffffffu, cincl, n_take - 1);
-            ws.pb[lane] = (lane < n_take) ? cincl - my_cnt : np;
-            if (lane == 31) ws.pb[32] = np;
-            __syncwarp();
-            // lane -> (event, pair)
-            int ev = 0;
-            {
-              int lo = 0, hi = static_cast<int>(n_take);  // pb[lo] <= lane < pb[hi]
-              while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (ws.pb[mid] <= lane) lo = mid; else hi = mid;
-              }
-              ev = lo;
-            }
-            const bool pv = lane < np;
-            const uint32_t eslot = (eh + ev) & (kEvRing - 1);
-            const uint32_t ekey = ws.e_key[eslot];
-            const uint32_t etl = ekey >> 24, ek = ekey & 0xFFFFFFu;
-            float lv = 0.0f;
-            bool slow = false;
-            if (pv) {
-              const Pair pr = p.pairs[ws.e_ps[eslot] + (lane - ws.pb[ev])];
-              slow = !pair_fast(p, pr, ta + etl, ek, &lv);
-              if (diag) {
-                const uint32_t elt = static_cast<uint32_t>(p.elt_id[pair_pos(pr.meta)]);
-                atomicAdd(&ws.hits[etl], 1ull);
-                atomicAdd(&ws.hash[etl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(ek) << 32) | elt)));
-              }
-            }
-            n_pairs += pv ? 1 : 0;
-            // event sums: segmented reduction over lanes by event, in lane (= layer) order
-            const uint32_t eseg = pv ? static_cast<uint32_t>(ev) : 0xFFFFu;
-            float G = lv;
-            uint32_t any_slow = slow ? 1u : 0u;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-              const float g2 = __shfl_up_sync(0xffffffffu, G, d);
-              const uint32_t s2 = __shfl_up_sync(0xffffffffu, eseg, d);
-              const uint32_t f2 = __shfl_up_sync(0xffffffffu, any_slow, d);
-              if (lane >= static_cast<uint32_t>(d) && s2 == eseg) {
-                G += g2;
-                any_slow |= f2;
-              }
-            }
-            const uint32_t eseg_next = __shfl_down_sync(0xffffffffu, eseg, 1);
-            const bool ev_last = pv && (lane == np - 1 || eseg_next != eseg);
-            const bool defer = ev_last && any_slow;
-            const float O = (ev_last && !any_slow) ? clamp_terms_f(G, p.occ_r, p.occ_l) : 0.0f;
-            // deferred events
-            const uint32_t dmask = __ballot_sync(0xffffffffu, defer);
-            if (dmask) {
-              if (nd + __popc(dmask) > 32) {
-                resolve_deferred(p, ws, nd, ta, &n_nc, &n_slow);
-                nd = 0;
-              }
-              if (defer) {
-                const int at = nd + __popc(dmask & lt_mask);
-                ws.d_key[at] = ekey;
-                ws.d_ps[at] = ws.e_ps[eslot];
-                ws.d_cnt[at] = ws.e_cnt[eslot];
-              }
-              nd += __popc(dmask);
-              __syncwarp();
-            }
-            // trial sums: segmented double-float reduction by trial, one FP64 add per trial
-            {
-              float hi = O, lo = 0.0f;
-              const uint32_t tseg = pv ? etl : 0xFFFFu;
-#pragma unroll
-              for (int d = 1; d < 32; d <<= 1) {
-                const float h2 = __shfl_up_sync(0xffffffffu, hi, d);
-                const float l2 = __shfl_up_sync(0xffffffffu, lo, d);
-                const uint32_t s2 = __shfl_up_sync(0xffffffffu, tseg, d);
-                if (lane >= static_cast<uint32_t>(d) && s2 == tseg) df_add(hi, lo, h2, l2);
-              }
-              const uint32_t tseg_next = __shfl_down_sync(0xffffffffu, tseg, 1);
-              if (pv && (lane == np - 1 || tseg_next != tseg)) ws.S[etl] += static_cast<double>(hi) + static_cast<double>(lo);
-            }
-            eh = (eh + n_take) & (kEvRing - 1);
-            en -= n_take;
-            epairs -= np;
-            __syncwarp();
-          }
-          if (!resolve) break;
-        }
-        };
-    // YET stream: two int4 registers, unrolled so that each is refilled with
-    // the chunk two steps ahead as soon as it has been consumed (the load
-    // writes the register directly; nothing in flight is moved).
-    int4 bufA = make_int4(0, 0, 0, 0), bufB = bufA;
-    if (4 * static_cast<int32_t>(lane) < span) bufA = __ldcs(reinterpret_cast<const int4*>(ids) + lane);
-    if (128 + 4 * static_cast<int32_t>(lane) < span) bufB = __ldcs(reinterpret_cast<const int4*>(ids) + 32 + lane);
-    for (int32_t c0 = 0; c0 < span; c0 += 256) {
-      const int4 curA = bufA;
-      if (c0 + 256 + 4 * static_cast<int32_t>(lane) < span)
-        bufA = __ldcs(reinterpret_cast<const int4*>(ids + c0 + 256) + lane);
-      step(curA, c0);
-      if (c0 + 128 < span) {
-        const int4 curB = bufB;
-        if (c0 + 384 + 4 * static_cast<int32_t>(lane) < span)
-          bufB = __ldcs(reinterpret_cast<const int4*>(ids + c0 + 384) + lane);
-        step(curB, c0 + 128);
+    int nd = 0;
+    uint32_t base = 0;
+    uint2 rec = make_uint2(0u, 0u);
+    if (lane < n) rec = __ldcs(recs + lane);
+    while (base < n) {
+      const bool valid = base + lane < n;
+      const uint32_t cnt = valid ? ((rec.x >> kRecCntShift) & 31u) + 1u : 0u;
+      const uint32_t cincl = warp_inclusive_scan(cnt);
+      const uint32_t take = __ballot_sync(0xffffffffu, valid && cincl <= 32u);
+      const uint32_t n_take = __popc(take);  // a prefix: cincl grows with the lane
+      const uint32_t np = __shfl_sync(0xffffffffu, cincl, n_take - 1);
+      // lane -> event: event i starts at lane cincl_i - cnt_i
+      uint32_t ev = lane;
+      if (np != n_take) {
+        const uint32_t starts = __reduce_or_sync(0xffffffffu, (lane < n_take) ? (1u << (cincl - cnt)) : 0u);
+        ev = static_cast<uint32_t>(__popc(starts & ((lt_mask << 1) | 1u))) - 1u;
       }
+      const uint32_t ekey = __shfl_sync(0xffffffffu, rec.x, ev);
+      const uint32_t eps = __shfl_sync(0xffffffffu, rec.y, ev);
+      const uint32_t estart = __shfl_sync(0xffffffffu, cincl - cnt, ev);
+      const uint32_t etl = ekey >> kRecTrialShift, ek = ekey & kRecKMask;
+      const bool pv = lane < np;
+      float lv = 0.0f;
+      bool slow = false;
+      if (pv) {
+        const Pair pr = p.pairs[eps + (lane - estart)];
+        slow = !pair_fast(p, pr, ta + etl, ek, &lv);
+        if (diag) {
+          const uint32_t elt = static_cast<uint32_t>(p.elt_id[pair_pos(pr.meta)]);
+          atomicAdd(&ws.hits[etl], 1ull);
+          atomicAdd(&ws.hash[etl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(ek) << 32) | elt)));
+        }
+      }
+      n_pairs += pv ? 1u : 0u;
+      // next window: starts after the events taken (prefetched now)
+      const uint32_t nbase = base + n_take;
+      uint2 nrec = make_uint2(0u, 0u);
+      if (nbase + lane < n) nrec = __ldcs(recs + nbase + lane);
+      // event sums, in lane (= layer) order
+      const uint32_t eseg = pv ? ev : 0xFFFFu;
+      float G = lv;
+      uint32_t any_slow = slow ? 1u : 0u;
+      if (np != n_take) {
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const float g2 = __shfl_up_sync(0xffffffffu, G, d);
+          const uint32_t s2 = __shfl_up_sync(0xffffffffu, eseg, d);
+          const uint32_t f2 = __shfl_up_sync(0xffffffffu, any_slow, d);
+          if (lane >= static_cast<uint32_t>(d) && s2 == eseg) {
+            G += g2;
+            any_slow |= f2;
+          }
+        }
+      }
+      const uint32_t eseg_next = __shfl_down_sync(0xffffffffu, eseg, 1);
+      const bool ev_last = pv && (lane == np - 1 || eseg_next != eseg);
+      const bool defer = ev_last && any_slow;
+      const float O = (ev_last && !any_slow) ? clamp_terms_f(G, p.occ_r, p.occ_l) : 0.0f;
+      const uint32_t dmask = __ballot_sync(0xffffffffu, defer);
+      if (dmask) {
+        if (nd + __popc(dmask) > 32) {
+          resolve_deferred(p, ws, nd, ta, &n_nc, &n_slow);
+          nd = 0;
+        }
+        if (defer) {
+          const int at = nd + __popc(dmask & lt_mask);
+          ws.d_key[at] = ekey;
+          ws.d_ps[at] = eps;
+        }
+        nd += __popc(dmask);
+        __syncwarp();
+      }
+      // trial sums: segmented double-float reduction by trial, one FP64 add per trial
+      {
+        float hi = O, lo = 0.0f;
+        const uint32_t tseg = pv ? etl : 0xFFFFu;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const float h2 = __shfl_up_sync(0xffffffffu, hi, d);
+          const float l2 = __shfl_up_sync(0xffffffffu, lo, d);
+          const uint32_t s2 = __shfl_up_sync(0xffffffffu, tseg, d);
+          if (lane >= static_cast<uint32_t>(d) && s2 == tseg) df_add(hi, lo, h2, l2);
+        }
+        const uint32_t tseg_next = __shfl_down_sync(0xffffffffu, tseg, 1);
+        if (pv && (lane == np - 1 || tseg_next != tseg)) ws.S[etl] += static_cast<double>(hi) + static_cast<double>(lo);
+        __syncwarp();
+      }
+      base = nbase;
+      rec = nrec;
     }
-    // ---- 4. deferred events, then the aggregate terms
     if (nd > 0) resolve_deferred(p, ws, nd, ta, &n_nc, &n_slow);
     if (lane < static_cast<uint32_t>(ntr)) {
-      const int64_t out = ta + lane - p.t_begin;
-      p.ylt[out] = clamp_terms_d(ws.S[lane], p.agg_r, p.agg_l);
-      if (p.diag_hits) p.diag_hits[out] = static_cast<int64_t>(ws.hits[lane]);
-      if (p.diag_hash) p.diag_hash[out] = ws.hash[lane];
+      const int64_t o = ta + lane - p.t_begin;
+      p.ylt[o] = clamp_terms_d(ws.S[lane], p.agg_r, p.agg_l);
+      if (p.diag_hits) p.diag_hits[o] = static_cast<int64_t>(ws.hits[lane]);
+      if (p.diag_hash) p.diag_hash[o] = ws.hash[lane];
     }
     __syncwarp();
   }
@@ -943,10 +933,8 @@ __global__ void __launch_bounds__(kLayerThreads, 1) k_layer(const LayerParams p)
   }
 }
 
-cudaError_t launch_layer_kernel(const LayerParams& p, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(k_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (err != cudaSuccess) return err;
-  k_layer<<<grid, kLayerThreads, smem, s>>>(p);
+cudaError_t launch_losses(const LossParams& p, int grid, cudaStream_t s) {
+  k_losses<<<grid, kLossThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
