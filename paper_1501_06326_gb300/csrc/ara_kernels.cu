@@ -591,6 +591,8 @@ constexpr uint32_t kRecKMask = (1u << 22) - 1u;
 
 struct GatherWarp {
   int32_t off[kWarpTrials + 1];  // trial offsets relative to the tile's first event
+  uint32_t pos_e[128];           // filter positives of one step: event id
+  int32_t pos_rel[128];          //                               tile-relative position
 };
 
 }  // namespace
@@ -648,58 +650,64 @@ __global__ void __launch_bounds__(kGatherThreads, 1) k_gather(const GatherParams
         nxt = __ldcs(reinterpret_cast<const int4*>(ids + c0 + 128) + lane);
       const int32_t rel0 = c0 + 4 * static_cast<int32_t>(lane) - lead;
       const int32_t ev[4] = {cur.x, cur.y, cur.z, cur.w};
-      // filter, then the rank-directory words of the positives (loads in flight together)
-      uint2 rd[4];
+      // 1. filter the lane's four ids (shift counts of a funnel shift are taken mod 32)
+      uint32_t m = 0;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const uint32_t e = static_cast<uint32_t>(ev[j]);
+        const uint32_t w = filt[(e >> 5) & fmask];
         const bool in = static_cast<uint32_t>(rel0 + j) < static_cast<uint32_t>(nev);
-        rd[j] = make_uint2(0u, 0u);
-        if (in && ((filt[(e >> 5) & fmask] >> (e & 31)) & 1u)) rd[j] = __ldg(&p.rankdir[e >> 5]);
+        m |= (in ? (__funnelshift_r(w, w, e) & 1u) : 0u) << j;
       }
-      uint32_t tm = 0, key[4], ps[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t e = static_cast<uint32_t>(ev[j]);
-        const uint32_t bit = 1u << (e & 31);
-        key[j] = 0;
-        ps[j] = 0;
-        if (rd[j].x & bit) {
-          const uint32_t below = __popc(rd[j].x & (bit - 1u));
-          uint32_t cnt = 1;
-          if (rd[j].y & 0x80000000u) {
-            const uint32_t sl = (rd[j].y & 0x7FFFFFFFu) + below;
-            ps[j] = __ldg(&p.slot_start[sl]);
-            cnt = __ldg(&p.slot_start[sl + 1]) - ps[j];
-          } else {
-            ps[j] = rd[j].y + below;
-          }
-          key[j] = (cnt - 1u) << kRecCntShift;
-          tm |= 1u << j;
-        }
-      }
-      const uint32_t c = __popc(tm);
+      // 2. compact the positives of the warp, in YET order, into the staging list
+      const uint32_t c = __popc(m);
       const uint32_t incl = warp_inclusive_scan(c);
-      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      if (tm) {
-        int t = tcur;
-        int32_t tnext = ws.off[t + 1];
-        uint32_t at = nout + incl - c;
+      const uint32_t npos = __shfl_sync(0xffffffffu, incl, 31);
+      if (m) {
+        uint32_t at = incl - c;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          if (tm & (1u << j)) {
-            const int32_t rel = rel0 + j;
-            while (rel >= tnext && t + 1 < ntr) {
-              ++t;
-              tnext = ws.off[t + 1];
-            }
-            const uint32_t k = static_cast<uint32_t>(rel - ws.off[t]);
-            out[at] = make_uint2(key[j] | (static_cast<uint32_t>(t) << kRecTrialShift) | k, ps[j]);
+          if (m & (1u << j)) {
+            ws.pos_e[at] = static_cast<uint32_t>(ev[j]);
+            ws.pos_rel[at] = rel0 + j;
             ++at;
           }
         }
       }
-      nout += total;
+      __syncwarp();
+      // 3. resolve the positives, one per lane, and write the hit-event records
+      for (uint32_t r0 = 0; r0 < npos; r0 += 32) {
+        const bool valid = r0 + lane < npos;
+        uint32_t key = 0, ps = 0;
+        bool hit = false;
+        int32_t rel = 0;
+        if (valid) {
+          const uint32_t e = ws.pos_e[r0 + lane];
+          rel = ws.pos_rel[r0 + lane];
+          const uint2 rd = __ldg(&p.rankdir[e >> 5]);
+          const uint32_t bit = 1u << (e & 31);
+          if (rd.x & bit) {
+            hit = true;
+            const uint32_t below = __popc(rd.x & (bit - 1u));
+            uint32_t cnt = 1;
+            if (rd.y & 0x80000000u) {
+              const uint32_t sl = (rd.y & 0x7FFFFFFFu) + below;
+              ps = __ldg(&p.slot_start[sl]);
+              cnt = __ldg(&p.slot_start[sl + 1]) - ps;
+            } else {
+              ps = rd.y + below;
+            }
+            int t = tcur;
+            while (t + 1 < ntr && ws.off[t + 1] <= rel) ++t;
+            key = ((cnt - 1u) << kRecCntShift) | (static_cast<uint32_t>(t) << kRecTrialShift) |
+                  static_cast<uint32_t>(rel - ws.off[t]);
+          }
+        }
+        const uint32_t hm = __ballot_sync(0xffffffffu, hit);
+        if (hit) out[nout + __popc(hm & lt_mask)] = make_uint2(key, ps);
+        nout += __popc(hm);
+      }
+      __syncwarp();
       {
         const int32_t nrel = c0 + 128 - lead;
         while (tcur + 1 < ntr && ws.off[tcur + 1] <= nrel) ++tcur;
@@ -709,7 +717,6 @@ __global__ void __launch_bounds__(kGatherThreads, 1) k_gather(const GatherParams
     if (lane == 0) p.tile_cnt[tile] = nout;
     __syncwarp();
   }
-  (void)lt_mask;
 }
 
 cudaError_t launch_gather(const GatherParams& p, int grid, size_t smem, cudaStream_t s) {
