@@ -50,6 +50,7 @@ struct ara_ctx {
   // per-layer index (grown on demand)
   DevBuf bits, word_cnt, word_pairs, rankdir, mask, slot_cnt, pairs, scan_tmp;
   DevBuf ev_buf, tile_cnt;  // hit-event records of the layer kernels
+  DevBuf elt_stage, elt_recs_stage, elt_tab_stage, elt_flags;  // ELT load staging (grow-only)
   // misc scratch
   DevBuf flags;     // uint32 flags + int32 max event
   DevBuf counters;  // 4 x u64
@@ -261,8 +262,9 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
   for (int32_t i = 0; i < n_elts; ++i) {
     if (ids[i] < 0) return fail(c, ARA_EINVAL, "ara_load_elts: pool id %d is negative", ids[i]);
     if (offs[i + 1] < offs[i]) return fail(c, ARA_EINVAL, "ara_load_elts: rec_offsets decrease at %d", i);
-    if (offs[i + 1] - offs[i] >= (int64_t(1) << 31))
-      return fail(c, ARA_EINVAL, "ara_load_elts: ELT %d has too many records", ids[i]);
+    if (offs[i + 1] - offs[i] >= static_cast<int64_t>(ara::kMaxEltRecords))
+      return fail(c, ARA_EINVAL, "ara_load_elts: ELT %d has %lld records (at most %u)", ids[i],
+                  (long long)(offs[i + 1] - offs[i]), ara::kMaxEltRecords - 1);
     const ara_elt_terms& t = tm[i];
     if (!(t.retention >= 0.0f) || !(t.limit >= 0.0f) || !(t.share >= 0.0f) || std::isnan(t.limit) ||
         !std::isfinite(t.retention) || !std::isfinite(t.share))
@@ -270,107 +272,78 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     for (int32_t j = 0; j < i; ++j)
       if (ids[j] == ids[i]) return fail(c, ARA_EINVAL, "ara_load_elts: pool id %d appears twice", ids[i]);
   }
-  if (offs[n_elts] > 0 && (!event_ids || !mean || !sigma || !exposure))
-    return fail(c, ARA_EINVAL, "ara_load_elts: record arrays are NULL");
-  // stage all records on the device once, then split per ELT
   const int64_t R = offs[n_elts];
-  for (int32_t i = 0; i < n_elts; ++i)
-    if (offs[i + 1] - offs[i] >= static_cast<int64_t>(ara::kMaxEltRecords))
-      return fail(c, ARA_EINVAL, "ara_load_elts: ELT %d has %lld records (at most %u)", ids[i],
-                  (long long)(offs[i + 1] - offs[i]), ara::kMaxEltRecords - 1);
-  DevBuf stage;
-  const size_t stage_bytes = static_cast<size_t>(R) * (sizeof(int32_t) + 3 * sizeof(float) + sizeof(double2)) + 64;
-  if ((rc = reserve(c, stage, stage_bytes))) return rc;
-  int32_t* d_ev = static_cast<int32_t*>(stage.ptr);
+  if (R > 0 && (!event_ids || !mean || !sigma || !exposure))
+    return fail(c, ARA_EINVAL, "ara_load_elts: record arrays are NULL");
+  // ---- stage: inputs, prepared records and tables of all ELTs (grow-only context buffers)
+  const size_t in_bytes = static_cast<size_t>(R) * (sizeof(int32_t) + 3 * sizeof(float) + sizeof(double2)) + 64;
+  if ((rc = reserve(c, c->elt_stage, in_bytes)) ||
+      (rc = reserve(c, c->elt_recs_stage, sizeof(ara::Pair) * (R + 1))) ||
+      (rc = reserve(c, c->elt_tab_stage, sizeof(float4) * ara::kTabNodes * (R + 1))) ||
+      (rc = reserve(c, c->elt_flags, sizeof(uint32_t) * 2 * n_elts)))
+    return rc;
+  int32_t* d_ev = static_cast<int32_t*>(c->elt_stage.ptr);
   float* d_mu = reinterpret_cast<float*>(d_ev + R);
   float* d_sg = d_mu + R;
   float* d_ex = d_sg + R;
-  double2* d_shapes = reinterpret_cast<double2*>(
-      (reinterpret_cast<uintptr_t>(d_ex + R) + 15) & ~uintptr_t(15));
-  auto cleanup = [&](int code) {
-    release(c, stage);
-    return code;
-  };
+  double2* d_shapes = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(d_ex + R) + 15) & ~uintptr_t(15));
+  ara::Pair* d_recs = static_cast<ara::Pair*>(c->elt_recs_stage.ptr);
+  float4* d_tab = static_cast<float4*>(c->elt_tab_stage.ptr);
+  uint32_t* d_flags = static_cast<uint32_t*>(c->elt_flags.ptr);
   if (R > 0) {
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ev, event_ids, sizeof(int32_t) * R, kind_to_device(event_ids), c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_mu, mean, sizeof(float) * R, kind_to_device(mean), c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_sg, sigma, sizeof(float) * R, kind_to_device(sigma), c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_ex, exposure, sizeof(float) * R, kind_to_device(exposure), c->stream);
-    if (e != cudaSuccess) return cleanup(fail(c, ARA_ECUDA, "ara_load_elts: copy failed: %s", cudaGetErrorString(e)));
+    ARA_CUDA(c, cudaMemcpyAsync(d_ev, event_ids, sizeof(int32_t) * R, kind_to_device(event_ids), c->stream));
+    ARA_CUDA(c, cudaMemcpyAsync(d_mu, mean, sizeof(float) * R, kind_to_device(mean), c->stream));
+    ARA_CUDA(c, cudaMemcpyAsync(d_sg, sigma, sizeof(float) * R, kind_to_device(sigma), c->stream));
+    ARA_CUDA(c, cudaMemcpyAsync(d_ex, exposure, sizeof(float) * R, kind_to_device(exposure), c->stream));
   }
-  std::vector<Elt> fresh(n_elts);
-  uint32_t* flags = static_cast<uint32_t*>(c->flags.ptr);
-  int32_t* max_ev = reinterpret_cast<int32_t*>(flags + 1);
-  std::vector<int32_t> maxes(n_elts, -1);
+  // per ELT: flags word, then the largest event id (0xFFFFFFFF = none)
+  std::vector<uint32_t> init(2 * static_cast<size_t>(n_elts));
   for (int32_t i = 0; i < n_elts; ++i) {
-    Elt& el = fresh[i];
-    el.n = offs[i + 1] - offs[i];
-    el.terms = tm[i];
-    if ((rc = reserve(c, el.events, sizeof(int32_t) * (el.n + 4))) ||
-        (rc = reserve(c, el.recs, sizeof(ara::Pair) * (el.n > 0 ? el.n : 1))) ||
-        (rc = reserve(c, el.tab, sizeof(float4) * ara::kTabNodes * (el.n > 0 ? el.n : 1)))) {
-      for (auto& f : fresh) {
-        release(c, f.events);
-        release(c, f.recs);
-        release(c, f.tab);
-      }
-      return cleanup(rc);
-    }
-    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(max_ev, 0xFF, sizeof(int32_t), c->stream);
-    if (e == cudaSuccess && el.n > 0)
-      e = cudaMemcpyAsync(el.events.ptr, d_ev + offs[i], sizeof(int32_t) * el.n, cudaMemcpyDeviceToDevice, c->stream);
-    if (e == cudaSuccess)
-      e = ara::launch_prepare_records(d_ev + offs[i], d_mu + offs[i], d_sg + offs[i], d_ex + offs[i], el.n,
-                                      static_cast<ara::Pair*>(el.recs.ptr), d_shapes + offs[i], flags, max_ev,
-                                      c->stream);
-    if (e == cudaSuccess)
-      e = ara::launch_build_tables(static_cast<ara::Pair*>(el.recs.ptr), d_shapes + offs[i], el.n,
-                                   static_cast<float4*>(el.tab.ptr), c->stream);
+    init[2 * i] = 0u;
+    init[2 * i + 1] = 0xFFFFFFFFu;
+  }
+  ARA_CUDA(c, cudaMemcpyAsync(d_flags, init.data(), sizeof(uint32_t) * init.size(), cudaMemcpyHostToDevice, c->stream));
+  for (int32_t i = 0; i < n_elts; ++i) {
+    const int64_t o = offs[i], n = offs[i + 1] - offs[i];
+    uint32_t* f = d_flags + 2 * i;
+    ARA_CUDA(c, ara::launch_prepare_records(d_ev + o, d_mu + o, d_sg + o, d_ex + o, n, d_recs + o, d_shapes + o, f,
+                                            reinterpret_cast<int32_t*>(f + 1), c->stream));
+    ARA_CUDA(c, ara::launch_build_tables(d_recs + o, d_shapes + o, n, d_tab + o * ara::kTabNodes, c->stream));
     c->launches += 2;
-    uint32_t hf[2] = {0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    int bad = 0;
-    const char* why = "";
-    if (e != cudaSuccess) {
-      bad = ARA_ECUDA;
-      why = cudaGetErrorString(e);
-    } else if (hf[0] & ara::kBadOrder) {
-      bad = ARA_EINVAL;
-      why = "event ids are not strictly increasing";
-    } else if (hf[0] & ara::kBadEventId) {
-      bad = ARA_EINVAL;
-      why = "an event id is negative";
-    } else if (hf[0] & ara::kBadValue) {
-      bad = ARA_EINVAL;
-      why = "a mean, sigma or exposure is negative or not finite";
-    } else if (hf[0] & ara::kBadExposure) {
-      bad = ARA_EINVAL;
-      why = "a record with mean > 0 and sigma > 0 has exposure <= mean";
-    }
-    if (bad) {
-      for (auto& f : fresh) {
-        release(c, f.events);
-        release(c, f.recs);
-        release(c, f.tab);
-      }
-      return cleanup(fail(c, bad, "ara_load_elts: ELT %d: %s", ids[i], why));
-    }
-    el.max_event = static_cast<int32_t>(hf[1]);
   }
+  std::vector<uint32_t> hf(2 * static_cast<size_t>(n_elts));
+  ARA_CUDA(c, cudaMemcpyAsync(hf.data(), d_flags, sizeof(uint32_t) * hf.size(), cudaMemcpyDeviceToHost, c->stream));
+  ARA_CUDA(c, cudaStreamSynchronize(c->stream));
   for (int32_t i = 0; i < n_elts; ++i) {
-    auto it = c->pool.find(ids[i]);
-    if (it != c->pool.end()) {
-      release(c, it->second.events);
-      release(c, it->second.recs);
-      release(c, it->second.tab);
-      c->pool.erase(it);
-    }
-    c->pool[ids[i]] = fresh[i];
+    const uint32_t f = hf[2 * i];
+    const char* why = nullptr;
+    if (f & ara::kBadOrder) why = "event ids are not strictly increasing";
+    else if (f & ara::kBadEventId) why = "an event id is negative";
+    else if (f & ara::kBadValue) why = "a mean, sigma or exposure is negative or not finite";
+    else if (f & ara::kBadExposure) why = "a record with mean > 0 and sigma > 0 has exposure <= mean";
+    if (why) return fail(c, ARA_EINVAL, "ara_load_elts: ELT %d: %s", ids[i], why);
   }
-  return cleanup(ARA_OK);
+  // ---- commit: each ELT keeps (or grows) its own buffers; the pool only changes once all checks passed
+  for (int32_t i = 0; i < n_elts; ++i) {
+    const int64_t o = offs[i], n = offs[i + 1] - offs[i];
+    Elt& el = c->pool[ids[i]];
+    if ((rc = reserve(c, el.events, sizeof(int32_t) * (n + 4))) ||
+        (rc = reserve(c, el.recs, sizeof(ara::Pair) * (n > 0 ? n : 1))) ||
+        (rc = reserve(c, el.tab, sizeof(float4) * ara::kTabNodes * (n > 0 ? n : 1)))) {
+      c->pool.erase(ids[i]);
+      return rc;
+    }
+    el.n = n;
+    el.terms = tm[i];
+    el.max_event = static_cast<int32_t>(hf[2 * i + 1]);
+    if (n > 0) {
+      ARA_CUDA(c, cudaMemcpyAsync(el.events.ptr, d_ev + o, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
+      ARA_CUDA(c, cudaMemcpyAsync(el.recs.ptr, d_recs + o, sizeof(ara::Pair) * n, cudaMemcpyDeviceToDevice, c->stream));
+      ARA_CUDA(c, cudaMemcpyAsync(el.tab.ptr, d_tab + o * ara::kTabNodes, sizeof(float4) * ara::kTabNodes * n,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+    }
+  }
+  return ARA_OK;
 }
 
 static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out,
@@ -764,7 +737,7 @@ void ara_destroy(ara_ctx* c) {
     release(c, kv.second.recs);
     release(c, kv.second.tab);
   }
-  DevBuf* bufs[] = {&c->ev_buf, &c->tile_cnt, &c->yet_off, &c->yet_ids, &c->bits,  &c->word_cnt, &c->word_pairs, &c->rankdir, &c->mask,   &c->slot_cnt,
+  DevBuf* bufs[] = {&c->elt_stage, &c->elt_recs_stage, &c->elt_tab_stage, &c->elt_flags, &c->ev_buf, &c->tile_cnt, &c->yet_off, &c->yet_ids, &c->bits,  &c->word_cnt, &c->word_pairs, &c->rankdir, &c->mask,   &c->slot_cnt,
                     &c->pairs,   &c->scan_tmp, &c->flags, &c->counters, &c->ylt_tmp, &c->diag_tmp, &c->sel,
                     &c->in_tmp,  &c->out_tmp};
   for (DevBuf* b : bufs) release(c, *b);

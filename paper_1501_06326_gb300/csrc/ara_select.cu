@@ -20,8 +20,9 @@ namespace ara {
 
 namespace {
 
-constexpr int kSelBlocks = 304;  // fixed grid: deterministic reduction order
+constexpr int kSelBlocks = 152;  // fixed grid: deterministic reduction order
 constexpr int kSelThreads = 256;
+constexpr int kSelGroup = 4;     // return periods selected together (one pass over the YLT serves all)
 
 __device__ __forceinline__ unsigned long long key_of(double v) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
@@ -41,131 +42,168 @@ struct SelState {
   unsigned int pad;
 };
 
-__global__ void k_sel_init(SelState* st, unsigned long long m, unsigned int* hist) {
-  st->prefix = 0;
-  st->mask = 0;
-  st->want = m;
-  st->m = m;
-  st->bad = 0;
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+struct SelScratch {
+  SelState st[kSelGroup];
+  unsigned int hist[kSelGroup][256];
+  double part_sum[kSelBlocks][kSelGroup];
+  unsigned long long part_cnt[kSelBlocks][kSelGroup];
+};
+
+struct SelMs {
+  unsigned long long m[kSelGroup];
+};
+
+__global__ void k_sel_init(SelScratch* sc, SelMs ms, int g) {
+  if (threadIdx.x < g) {
+    SelState& st = sc->st[threadIdx.x];
+    st.prefix = 0;
+    st.mask = 0;
+    st.want = ms.m[threadIdx.x];
+    st.m = ms.m[threadIdx.x];
+    st.bad = 0;
+  }
+  for (int i = threadIdx.x; i < kSelGroup * 256; i += blockDim.x) (&sc->hist[0][0])[i] = 0;
 }
 
-__global__ void k_sel_hist(const double* ylt, int64_t n, const SelState* st, int shift, unsigned int* hist,
-                           unsigned int* bad) {
-  __shared__ unsigned int sh[256];
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0;
+// One MSB-first digit pass for every return period of the group.
+__global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, int shift) {
+  __shared__ unsigned int sh[kSelGroup][256];
+  for (int i = threadIdx.x; i < kSelGroup * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
+  unsigned long long prefix[kSelGroup], mask[kSelGroup];
+#pragma unroll
+  for (int r = 0; r < kSelGroup; ++r) {
+    prefix[r] = r < g ? sc->st[r].prefix : ~0ull;
+    mask[r] = r < g ? sc->st[r].mask : 0ull;
+  }
   __syncthreads();
-  const unsigned long long prefix = st->prefix, mask = st->mask;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   bool nan = false;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
     const double v = ylt[i];
     nan |= (v != v);
     const unsigned long long k = key_of(v);
-    if ((k & mask) == prefix) atomicAdd(&sh[(k >> shift) & 255u], 1u);
+    const unsigned int d = static_cast<unsigned int>((k >> shift) & 255u);
+#pragma unroll
+    for (int r = 0; r < kSelGroup; ++r)
+      if (r < g && (k & mask[r]) == prefix[r]) atomicAdd(&sh[r][d], 1u);
   }
-  if (nan) atomicOr(bad, 1u);
+  if (nan) atomicOr(&sc->st[0].bad, 1u);
   __syncthreads();
-  for (int i = threadIdx.x; i < 256; i += blockDim.x)
-    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+  for (int i = threadIdx.x; i < g * 256; i += blockDim.x) {
+    const unsigned int c = (&sh[0][0])[i];
+    if (c) atomicAdd(&(&sc->hist[0][0])[i], c);
+  }
 }
 
-__global__ void k_sel_pick(SelState* st, int shift, unsigned int* hist) {
-  if (threadIdx.x == 0) {
+__global__ void k_sel_pick(SelScratch* sc, int g, int shift) {
+  if (threadIdx.x < g) {
+    SelState& st = sc->st[threadIdx.x];
+    const unsigned int* h = sc->hist[threadIdx.x];
     unsigned long long above = 0;
     int d = 255;
     for (; d > 0; --d) {
-      if (above + hist[d] >= st->want) break;
-      above += hist[d];
+      if (above + h[d] >= st.want) break;
+      above += h[d];
     }
-    st->want -= above;
-    st->prefix |= static_cast<unsigned long long>(d) << shift;
-    st->mask |= 255ull << shift;
+    st.want -= above;
+    st.prefix |= static_cast<unsigned long long>(d) << shift;
+    st.mask |= 255ull << shift;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+  for (int i = threadIdx.x; i < kSelGroup * 256; i += blockDim.x) (&sc->hist[0][0])[i] = 0;
 }
 
-// Sum and count of the values whose key exceeds the selected key.
-__global__ void k_sel_tail(const double* ylt, int64_t n, const SelState* st, double* part_sum,
-                           unsigned long long* part_cnt) {
-  __shared__ double s_sum[kSelThreads / 32];
-  __shared__ unsigned long long s_cnt[kSelThreads / 32];
-  const unsigned long long kth = st->prefix;
+// Sum and count of the values whose key exceeds each selected key.
+__global__ void k_sel_tail(const double* ylt, int64_t n, SelScratch* sc, int g) {
+  __shared__ double s_sum[kSelThreads / 32][kSelGroup];
+  __shared__ unsigned long long s_cnt[kSelThreads / 32][kSelGroup];
+  unsigned long long kth[kSelGroup];
+#pragma unroll
+  for (int r = 0; r < kSelGroup; ++r) kth[r] = r < g ? sc->st[r].prefix : ~0ull;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  double sum = 0.0;
-  unsigned long long cnt = 0;
+  double sum[kSelGroup];
+  unsigned long long cnt[kSelGroup];
+#pragma unroll
+  for (int r = 0; r < kSelGroup; ++r) {
+    sum[r] = 0.0;
+    cnt[r] = 0;
+  }
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
     const double v = ylt[i];
-    if (key_of(v) > kth) {
-      sum += v;
-      ++cnt;
+    const unsigned long long k = key_of(v);
+#pragma unroll
+    for (int r = 0; r < kSelGroup; ++r)
+      if (k > kth[r]) {
+        sum[r] += v;
+        ++cnt[r];
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < kSelGroup; ++r) {
+    for (int d = 16; d > 0; d >>= 1) {
+      sum[r] += __shfl_down_sync(0xffffffffu, sum[r], d);
+      cnt[r] += __shfl_down_sync(0xffffffffu, cnt[r], d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_sum[threadIdx.x >> 5][r] = sum[r];
+      s_cnt[threadIdx.x >> 5][r] = cnt[r];
     }
   }
-  for (int d = 16; d > 0; d >>= 1) {
-    sum += __shfl_down_sync(0xffffffffu, sum, d);
-    cnt += __shfl_down_sync(0xffffffffu, cnt, d);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    s_sum[threadIdx.x >> 5] = sum;
-    s_cnt[threadIdx.x >> 5] = cnt;
-  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < g) {
+    const int r = threadIdx.x;
     double t = 0.0;
     unsigned long long c = 0;
     for (int w = 0; w < kSelThreads / 32; ++w) {
-      t += s_sum[w];
-      c += s_cnt[w];
+      t += s_sum[w][r];
+      c += s_cnt[w][r];
     }
-    part_sum[blockIdx.x] = t;
-    part_cnt[blockIdx.x] = c;
+    sc->part_sum[blockIdx.x][r] = t;
+    sc->part_cnt[blockIdx.x][r] = c;
   }
 }
 
-__global__ void k_sel_finish(const SelState* st, const double* part_sum, const unsigned long long* part_cnt,
-                             int n_parts, double* pml, double* tvar) {
-  if (threadIdx.x == 0) {
+__global__ void k_sel_finish(const SelScratch* sc, int g, int n_parts, double* pml, double* tvar) {
+  if (threadIdx.x < g) {
+    const int r = threadIdx.x;
     double s = 0.0;
     unsigned long long c = 0;
     for (int i = 0; i < n_parts; ++i) {
-      s += part_sum[i];
-      c += part_cnt[i];
+      s += sc->part_sum[i][r];
+      c += sc->part_cnt[i][r];
     }
-    const double v = value_of(st->prefix);
-    const unsigned long long m = st->m;
-    *pml = v;
-    *tvar = (s + static_cast<double>(m - c) * v) / static_cast<double>(m);
+    const double v = value_of(sc->st[r].prefix);
+    const unsigned long long m = sc->st[r].m;
+    pml[r] = v;
+    tvar[r] = (s + static_cast<double>(m - c) * v) / static_cast<double>(m);
   }
 }
 
 }  // namespace
 
-size_t select_scratch_bytes(int64_t /*n*/) {
-  return sizeof(SelState) + 256 * sizeof(unsigned int) + kSelBlocks * (sizeof(double) + sizeof(unsigned long long)) +
-         64;
-}
+size_t select_scratch_bytes(int64_t /*n*/) { return sizeof(SelScratch) + 64; }
 
 cudaError_t pml_tvar_device(const double* ylt, int64_t n, const double* rps_host, int32_t n_rp, double* pml,
                             double* tvar, void* scratch, cudaStream_t s, int* n_launch) {
-  unsigned char* base = static_cast<unsigned char*>(scratch);
-  SelState* st = reinterpret_cast<SelState*>(base);
-  unsigned int* hist = reinterpret_cast<unsigned int*>(base + sizeof(SelState));
-  double* part_sum = reinterpret_cast<double*>(base + sizeof(SelState) + 256 * sizeof(unsigned int));
-  unsigned long long* part_cnt = reinterpret_cast<unsigned long long*>(part_sum + kSelBlocks);
-  int64_t blocks = (n + kSelThreads - 1) / kSelThreads;
+  SelScratch* sc = static_cast<SelScratch*>(scratch);
+  const int64_t blocks = (n + kSelThreads - 1) / kSelThreads;
   const int grid = static_cast<int>(blocks < kSelBlocks ? blocks : kSelBlocks);
-  for (int32_t r = 0; r < n_rp; ++r) {
-    int64_t m = static_cast<int64_t>(std::ceil(static_cast<double>(n) / rps_host[r]));
-    if (m < 1) m = 1;
-    if (m > n) m = n;
-    k_sel_init<<<1, 256, 0, s>>>(st, static_cast<unsigned long long>(m), hist);
-    for (int shift = 56; shift >= 0; shift -= 8) {
-      k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, st, shift, hist, &st->bad);
-      k_sel_pick<<<1, 256, 0, s>>>(st, shift, hist);
+  for (int32_t r0 = 0; r0 < n_rp; r0 += kSelGroup) {
+    const int g = (n_rp - r0 < kSelGroup) ? (n_rp - r0) : kSelGroup;
+    SelMs ms{};
+    for (int r = 0; r < g; ++r) {
+      int64_t m = static_cast<int64_t>(std::ceil(static_cast<double>(n) / rps_host[r0 + r]));
+      if (m < 1) m = 1;
+      if (m > n) m = n;
+      ms.m[r] = static_cast<unsigned long long>(m);
     }
-    k_sel_tail<<<grid, kSelThreads, 0, s>>>(ylt, n, st, part_sum, part_cnt);
-    k_sel_finish<<<1, 32, 0, s>>>(st, part_sum, part_cnt, grid, pml + r, tvar + r);
+    k_sel_init<<<1, 256, 0, s>>>(sc, ms, g);
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, shift);
+      k_sel_pick<<<1, 256, 0, s>>>(sc, g, shift);
+    }
+    k_sel_tail<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g);
+    k_sel_finish<<<1, 32, 0, s>>>(sc, g, grid, pml + r0, tvar + r0);
     if (n_launch) *n_launch += 19;
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -290,7 +328,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[ARA_NOALLOC_SCR
 constexpr int kNoallocMaxDevices = 64;
 void* g_noalloc_addr[kNoallocMaxDevices] = {};  // device address of the block, per device
 
-static_assert(ARA_NOALLOC_SCRATCH_BYTES >= 2 * ARA_NOALLOC_MAX_RP * sizeof(double) + 2048 + 304 * 16 + 256,
+static_assert(ARA_NOALLOC_SCRATCH_BYTES >= 2 * ARA_NOALLOC_MAX_RP * sizeof(double) + sizeof(ara::SelScratch) + 256,
               "fixed block too small for the select state");
 
 }  // namespace
