@@ -24,8 +24,10 @@ struct DevBuf {
 struct Elt {
   DevBuf events;  // int32 [n] (+ padding)
   DevBuf recs;    // ara::Pair [n]
-  DevBuf tab;     // float4 [n * kTabNodes] quantile tables
+  DevBuf tab;     // float4 [n * kTabNodes] coarse quantile tables
+  DevBuf tabf;    // float4 [n_fine * kTabFineStride] fine quantile tables
   int64_t n = 0;
+  int64_t n_fine = 0;
   int32_t max_event = -1;
   ara_elt_terms terms{0.0f, INFINITY, 1.0f};
 };
@@ -50,7 +52,9 @@ struct ara_ctx {
   // per-layer index (grown on demand)
   DevBuf bits, word_cnt, word_pairs, rankdir, mask, slot_cnt, pairs, scan_tmp;
   DevBuf ev_buf, tile_cnt;  // hit-event records of the layer kernels
+  DevBuf def_acc;           // per-trial FP64 sums of deferred occurrence losses
   DevBuf elt_stage, elt_recs_stage, elt_tab_stage, elt_flags;  // ELT load staging (grow-only)
+  DevBuf elt_tabf_stage, elt_work;
   // misc scratch
   DevBuf flags;     // uint32 flags + int32 max event
   DevBuf counters;  // 4 x u64
@@ -276,11 +280,19 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
   if (R > 0 && (!event_ids || !mean || !sigma || !exposure))
     return fail(c, ARA_EINVAL, "ara_load_elts: record arrays are NULL");
   // ---- stage: inputs, prepared records and tables of all ELTs (grow-only context buffers)
+  std::vector<int64_t> fine_off(static_cast<size_t>(n_elts) + 1, 0), work_off(static_cast<size_t>(n_elts) + 1, 0);
+  for (int32_t i = 0; i < n_elts; ++i) {
+    const int64_t n = offs[i + 1] - offs[i];
+    fine_off[i + 1] = fine_off[i] + ara::fine_table_cap(n);
+    work_off[i + 1] = work_off[i] + static_cast<int64_t>(ara::build_tables_work_words(n));
+  }
   const size_t in_bytes = static_cast<size_t>(R) * (sizeof(int32_t) + 3 * sizeof(float) + sizeof(double2)) + 64;
   if ((rc = reserve(c, c->elt_stage, in_bytes)) ||
       (rc = reserve(c, c->elt_recs_stage, sizeof(ara::Pair) * (R + 1))) ||
       (rc = reserve(c, c->elt_tab_stage, sizeof(float4) * ara::kTabNodes * (R + 1))) ||
-      (rc = reserve(c, c->elt_flags, sizeof(uint32_t) * 2 * n_elts)))
+      (rc = reserve(c, c->elt_tabf_stage, sizeof(float4) * ara::kTabFineStride * (fine_off[n_elts] + 1))) ||
+      (rc = reserve(c, c->elt_work, sizeof(uint32_t) * (work_off[n_elts] + 1))) ||
+      (rc = reserve(c, c->elt_flags, sizeof(uint32_t) * 3 * n_elts)))
     return rc;
   int32_t* d_ev = static_cast<int32_t*>(c->elt_stage.ptr);
   float* d_mu = reinterpret_cast<float*>(d_ev + R);
@@ -289,6 +301,8 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
   double2* d_shapes = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(d_ex + R) + 15) & ~uintptr_t(15));
   ara::Pair* d_recs = static_cast<ara::Pair*>(c->elt_recs_stage.ptr);
   float4* d_tab = static_cast<float4*>(c->elt_tab_stage.ptr);
+  float4* d_tabf = static_cast<float4*>(c->elt_tabf_stage.ptr);
+  uint32_t* d_work = static_cast<uint32_t*>(c->elt_work.ptr);
   uint32_t* d_flags = static_cast<uint32_t*>(c->elt_flags.ptr);
   if (R > 0) {
     ARA_CUDA(c, cudaMemcpyAsync(d_ev, event_ids, sizeof(int32_t) * R, kind_to_device(event_ids), c->stream));
@@ -296,26 +310,32 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     ARA_CUDA(c, cudaMemcpyAsync(d_sg, sigma, sizeof(float) * R, kind_to_device(sigma), c->stream));
     ARA_CUDA(c, cudaMemcpyAsync(d_ex, exposure, sizeof(float) * R, kind_to_device(exposure), c->stream));
   }
-  // per ELT: flags word, then the largest event id (0xFFFFFFFF = none)
-  std::vector<uint32_t> init(2 * static_cast<size_t>(n_elts));
+  // per ELT: flags word, the largest event id (0xFFFFFFFF = none), candidates for fine tables
+  std::vector<uint32_t> init(3 * static_cast<size_t>(n_elts));
   for (int32_t i = 0; i < n_elts; ++i) {
-    init[2 * i] = 0u;
-    init[2 * i + 1] = 0xFFFFFFFFu;
+    init[3 * i] = 0u;
+    init[3 * i + 1] = 0xFFFFFFFFu;
+    init[3 * i + 2] = 0u;
   }
   ARA_CUDA(c, cudaMemcpyAsync(d_flags, init.data(), sizeof(uint32_t) * init.size(), cudaMemcpyHostToDevice, c->stream));
   for (int32_t i = 0; i < n_elts; ++i) {
     const int64_t o = offs[i], n = offs[i + 1] - offs[i];
-    uint32_t* f = d_flags + 2 * i;
+    uint32_t* f = d_flags + 3 * i;
     ARA_CUDA(c, ara::launch_prepare_records(d_ev + o, d_mu + o, d_sg + o, d_ex + o, n, d_recs + o, d_shapes + o, f,
                                             reinterpret_cast<int32_t*>(f + 1), c->stream));
-    ARA_CUDA(c, ara::launch_build_tables(d_recs + o, d_shapes + o, n, d_tab + o * ara::kTabNodes, c->stream));
-    c->launches += 2;
+    int launched = 1;
+    uint32_t* w = d_work + work_off[i];
+    ARA_CUDA(c, ara::launch_build_tables(d_recs + o, d_shapes + o, n, d_tab + o * ara::kTabNodes,
+                                         d_tabf + fine_off[i] * ara::kTabFineStride, w, c->stream, &launched));
+    if (n > 0)
+      ARA_CUDA(c, cudaMemcpyAsync(f + 2, w + n, sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream));
+    c->launches += launched;
   }
-  std::vector<uint32_t> hf(2 * static_cast<size_t>(n_elts));
+  std::vector<uint32_t> hf(3 * static_cast<size_t>(n_elts));
   ARA_CUDA(c, cudaMemcpyAsync(hf.data(), d_flags, sizeof(uint32_t) * hf.size(), cudaMemcpyDeviceToHost, c->stream));
   ARA_CUDA(c, cudaStreamSynchronize(c->stream));
   for (int32_t i = 0; i < n_elts; ++i) {
-    const uint32_t f = hf[2 * i];
+    const uint32_t f = hf[3 * i];
     const char* why = nullptr;
     if (f & ara::kBadOrder) why = "event ids are not strictly increasing";
     else if (f & ara::kBadEventId) why = "an event id is negative";
@@ -326,21 +346,32 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
   // ---- commit: each ELT keeps (or grows) its own buffers; the pool only changes once all checks passed
   for (int32_t i = 0; i < n_elts; ++i) {
     const int64_t o = offs[i], n = offs[i + 1] - offs[i];
+    const int64_t n_fine = std::min<int64_t>(hf[3 * i + 2], ara::fine_table_cap(n));
     Elt& el = c->pool[ids[i]];
     if ((rc = reserve(c, el.events, sizeof(int32_t) * (n + 4))) ||
         (rc = reserve(c, el.recs, sizeof(ara::Pair) * (n > 0 ? n : 1))) ||
-        (rc = reserve(c, el.tab, sizeof(float4) * ara::kTabNodes * (n > 0 ? n : 1)))) {
+        (rc = reserve(c, el.tab, sizeof(float4) * ara::kTabNodes * (n > 0 ? n : 1))) ||
+        (rc = reserve(c, el.tabf, sizeof(float4) * ara::kTabFineStride * (n_fine > 0 ? n_fine : 1)))) {
+      release(c, el.events);
+      release(c, el.recs);
+      release(c, el.tab);
+      release(c, el.tabf);
       c->pool.erase(ids[i]);
       return rc;
     }
     el.n = n;
+    el.n_fine = n_fine;
     el.terms = tm[i];
-    el.max_event = static_cast<int32_t>(hf[2 * i + 1]);
+    el.max_event = static_cast<int32_t>(hf[3 * i + 1]);
     if (n > 0) {
       ARA_CUDA(c, cudaMemcpyAsync(el.events.ptr, d_ev + o, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
       ARA_CUDA(c, cudaMemcpyAsync(el.recs.ptr, d_recs + o, sizeof(ara::Pair) * n, cudaMemcpyDeviceToDevice, c->stream));
       ARA_CUDA(c, cudaMemcpyAsync(el.tab.ptr, d_tab + o * ara::kTabNodes, sizeof(float4) * ara::kTabNodes * n,
                                   cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (n_fine > 0) {
+      ARA_CUDA(c, cudaMemcpyAsync(el.tabf.ptr, d_tabf + fine_off[i] * ara::kTabFineStride,
+                                  sizeof(float4) * ara::kTabFineStride * n_fine, cudaMemcpyDeviceToDevice, c->stream));
     }
   }
   return ARA_OK;
@@ -380,6 +411,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
     refs.rec_begin[i + 1] = refs.rec_begin[i] + el.n;
     p.elt_id[i] = ids[i];
     p.tab[i] = static_cast<const float4*>(el.tab.ptr);
+    p.tabf[i] = static_cast<const float4*>(el.tabf.ptr);
     p.t_ret[i] = el.terms.retention;
     p.t_lim[i] = el.terms.limit;
     p.t_share[i] = el.terms.share;
@@ -445,7 +477,8 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   const int64_t n_tiles = (n_out + ara::kWarpTrials - 1) / ara::kWarpTrials;
   const int64_t e0 = c->h_off[t0], e1 = c->h_off[t1];
   if ((rc = reserve(c, c->ev_buf, sizeof(uint2) * (e1 - e0 + 1))) ||
-      (rc = reserve(c, c->tile_cnt, sizeof(uint32_t) * (n_tiles + 1))))
+      (rc = reserve(c, c->tile_cnt, sizeof(uint32_t) * (n_tiles + 1))) ||
+      (rc = reserve(c, c->def_acc, sizeof(double) * (n_out + 1))))
     return rc;
   unsigned long long* counters = static_cast<unsigned long long*>(c->counters.ptr);
   ara::GatherParams g{};
@@ -477,15 +510,23 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   p.agg_l = L->agg_limit;
   p.seed_lo = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
   p.seed_hi = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {  // Weyl key schedule of Philox4x32
+    p.rk[2 * r] = p.seed_lo + static_cast<uint32_t>(r) * 0x9E3779B9u;
+    p.rk[2 * r + 1] = p.seed_hi + static_cast<uint32_t>(r) * 0xBB67AE85u;
+  }
   p.primary_only = (L->flags & ARA_PRIMARY_ONLY) ? 1 : 0;
   p.newton_only = (L->flags & ARA_NEWTON_ONLY) ? 1 : 0;
   p.ylt = d_ylt;
+  p.def_acc = static_cast<double*>(c->def_acc.ptr);
   p.diag_hits = d_hits;
   p.diag_hash = d_hash;
   p.counters = counters;
   ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 8 * sizeof(unsigned long long), c->stream));
   const int64_t warps_per_sm = ara::kGatherThreads / 32;
   const int grid = static_cast<int>(std::min<int64_t>(c->num_sms, (n_tiles + warps_per_sm - 1) / warps_per_sm));
+  const int64_t loss_warps = ara::kLossThreads / 32;
+  const int loss_grid = static_cast<int>(std::min<int64_t>(c->num_sms * (1024 / ara::kLossThreads),
+                                                           (n_tiles + loss_warps - 1) / loss_warps));
   cudaEvent_t la, lb;
   if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "ara_run_layer: cannot create timing events");
   ARA_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
@@ -493,7 +534,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   ARA_CUDA(c, ara::launch_gather(g, grid, smem, c->stream));
   ARA_CUDA(c, cudaEventRecord(kb, c->stream));
   ARA_CUDA(c, cudaEventRecord(la, c->stream));
-  ARA_CUDA(c, ara::launch_losses(p, grid, c->stream));
+  ARA_CUDA(c, ara::launch_losses(p, loss_grid, c->stream));
   ARA_CUDA(c, cudaEventRecord(lb, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   launched += 2;
@@ -683,7 +724,9 @@ int ara_debug_record_losses(ara_ctx* c, int64_t n, const float* mean, const floa
   if (n >= static_cast<int64_t>(ara::kMaxEltRecords))
     return fail(c, ARA_EINVAL, "ara_debug_record_losses: at most %u records per call", ara::kMaxEltRecords - 1);
   const size_t bytes = static_cast<size_t>(n) * (sizeof(ara::Pair) + 6 * sizeof(float) + sizeof(int32_t) +
-                                                 sizeof(double2) + sizeof(float4) * ara::kTabNodes) + 128;
+                                                 sizeof(double2) + sizeof(float4) * ara::kTabNodes) +
+                       sizeof(float4) * ara::kTabFineStride * (ara::fine_table_cap(n) + 1) +
+                       sizeof(uint32_t) * ara::build_tables_work_words(n) + 256;
   if ((rc = reserve(c, tmp, bytes))) return rc;
   ara::Pair* d_p = static_cast<ara::Pair*>(tmp.ptr);
   float* d_mu = reinterpret_cast<float*>(d_p + n);
@@ -695,6 +738,8 @@ int ara_debug_record_losses(ara_ctx* c, int64_t n, const float* mean, const floa
   int32_t* d_it = d_ev + n;
   double2* d_sh = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(d_it + n) + 15) & ~uintptr_t(15));
   float4* d_tab = reinterpret_cast<float4*>(d_sh + n);
+  float4* d_tabf = d_tab + n * ara::kTabNodes;
+  uint32_t* d_work = reinterpret_cast<uint32_t*>(d_tabf + ara::kTabFineStride * (ara::fine_table_cap(n) + 1));
   uint32_t* flags = static_cast<uint32_t*>(c->flags.ptr);
   int32_t* max_ev = reinterpret_cast<int32_t*>(flags + 1);
   cudaError_t e = cudaMemcpyAsync(d_mu, mean, sizeof(float) * n, cudaMemcpyDefault, c->stream);
@@ -707,9 +752,10 @@ int ara_debug_record_losses(ara_ctx* c, int64_t n, const float* mean, const floa
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_ev, ev.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 2 * sizeof(uint32_t), c->stream);
   if (e == cudaSuccess) e = ara::launch_prepare_records(d_ev, d_mu, d_sg, d_ex, n, d_p, d_sh, flags, max_ev, c->stream);
-  if (e == cudaSuccess) e = ara::launch_build_tables(d_p, d_sh, n, d_tab, c->stream);
-  if (e == cudaSuccess) e = ara::launch_debug_losses(d_p, d_tab, d_z, n, newton_only, d_o, d_it, c->stream);
-  c->launches += 3;
+  int launched = 2;
+  if (e == cudaSuccess) e = ara::launch_build_tables(d_p, d_sh, n, d_tab, d_tabf, d_work, c->stream, &launched);
+  if (e == cudaSuccess) e = ara::launch_debug_losses(d_p, d_tab, d_tabf, d_z, n, newton_only, d_o, d_it, c->stream);
+  c->launches += launched;
   uint32_t hf = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d_o, sizeof(float) * n, cudaMemcpyDefault, c->stream);
@@ -736,10 +782,14 @@ void ara_destroy(ara_ctx* c) {
     release(c, kv.second.events);
     release(c, kv.second.recs);
     release(c, kv.second.tab);
+    release(c, kv.second.tabf);
   }
-  DevBuf* bufs[] = {&c->elt_stage, &c->elt_recs_stage, &c->elt_tab_stage, &c->elt_flags, &c->ev_buf, &c->tile_cnt, &c->yet_off, &c->yet_ids, &c->bits,  &c->word_cnt, &c->word_pairs, &c->rankdir, &c->mask,   &c->slot_cnt,
-                    &c->pairs,   &c->scan_tmp, &c->flags, &c->counters, &c->ylt_tmp, &c->diag_tmp, &c->sel,
-                    &c->in_tmp,  &c->out_tmp};
+  DevBuf* bufs[] = {&c->elt_stage,  &c->elt_recs_stage, &c->elt_tab_stage, &c->elt_tabf_stage, &c->elt_work,
+                    &c->elt_flags,  &c->ev_buf,         &c->tile_cnt,      &c->def_acc,        &c->yet_off,
+                    &c->yet_ids,    &c->bits,           &c->word_cnt,      &c->word_pairs,     &c->rankdir,
+                    &c->mask,       &c->slot_cnt,       &c->pairs,         &c->scan_tmp,       &c->flags,
+                    &c->counters,   &c->ylt_tmp,        &c->diag_tmp,      &c->sel,            &c->in_tmp,
+                    &c->out_tmp};
   for (DevBuf* b : bufs) release(c, *b);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);

@@ -46,12 +46,13 @@ enum : uint32_t {
 
 struct __align__(16) Pair {
   float a, b;     // Beta shapes (kKindBeta)
-  float m0;       // min(x0, y0), x0 = a / (a + b), y0 = b / (a + b)
+  float m0;       // min(x0, y0), x0 = a / (a + b), y0 = b / (a + b); negative when it is x0
   float c;        // a ln x0 + b ln y0 - ln B(a, b)
   float max_l;    // exposure (maximum loss)
   float mu;       // mean loss
   float p_half;   // I_{1/2}(a, b)
-  uint32_t meta;  // bits 0-4 layer position, 5-6 kind, 7: m0 is x0, 8: table exact, 9-31 record index
+  uint32_t meta;  // bits 0-4 layer position, 5-6 kind, 7: fine table, 8: table exact, 9-31 record index
+                  // (the fine-table slot when bit 7 is set)
 };
 static_assert(sizeof(Pair) == 32, "Pair must be one 32-byte sector");
 
@@ -59,7 +60,7 @@ constexpr uint32_t kMaxEltRecords = 1u << 23;  // record index field of meta
 
 __host__ __device__ inline uint32_t pair_pos(uint32_t meta) { return meta & 31u; }
 __host__ __device__ inline uint32_t pair_kind(uint32_t meta) { return (meta >> 5) & 3u; }
-__host__ __device__ inline bool pair_m0_is_x0(uint32_t meta) { return (meta >> 7) & 1u; }
+__host__ __device__ inline bool pair_fine(uint32_t meta) { return (meta >> 7) & 1u; }
 __host__ __device__ inline bool pair_tab_exact(uint32_t meta) { return (meta >> 8) & 1u; }
 __host__ __device__ inline uint32_t pair_rec(uint32_t meta) { return meta >> 9; }
 
@@ -69,6 +70,12 @@ constexpr double kTabT1 = 5.294704084854597;  // Phi^-1(1 - 2^-24)
 constexpr float kTabT1f = 5.294704f;
 constexpr float kTabInvH = static_cast<float>((kTabNodes - 1) / (2.0 * kTabT1));
 constexpr float kTabTol = 5e-7f;  // relative error allowed to the table alone
+// Fine tables: the same t range at 1/8 of the spacing, 8 * 31 + 1 nodes padded
+// to 256, for records whose quantile has features narrower than the coarse
+// spacing (U-shaped Betas, a and b well below 1).
+constexpr int kTabRefine = 8;
+constexpr int kTabFineNodes = kTabRefine * (kTabNodes - 1) + 1;
+constexpr int kTabFineStride = 256;
 
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -85,6 +92,26 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     k.y += 0xBB67AE85u;
   }
   return c;
+}
+
+// Philox4x32-10 with the ten round keys precomputed (k_r = k_0 + r W): the
+// same function, without the key schedule in the loop.
+__device__ __forceinline__ uint32_t philox4x32_10_w0(uint4 c, const uint32_t (&rk)[20]) {
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * i], lo1, hi0 ^ c.w ^ rk[2 * i + 1], lo0);
+  }
+  return c.x;
+}
+
+__device__ __forceinline__ float philox_uniform_rk(const uint32_t (&rk)[20], int64_t trial, uint32_t k, uint32_t elt) {
+  const uint64_t t = static_cast<uint64_t>(trial);
+  const uint32_t w = philox4x32_10_w0(make_uint4(static_cast<uint32_t>(t), k, elt, static_cast<uint32_t>(t >> 32)), rk);
+  return (static_cast<float>(w >> 9) + 0.5f) * 1.1920928955078125e-07f;  // 2^-23
 }
 
 // Uniform of (trial, event index k, ELT pool id): word 0 of the block with
@@ -175,13 +202,14 @@ __device__ __forceinline__ float tab_increment(float s, float dw, float d0, floa
 }
 
 // x = InvCDF_beta(z) from a record's table (nodes are float4 {x_i, w_{i+1} - w_i,
-// h w'_i, h^2 w''_i}).
-__device__ __forceinline__ float tab_quantile(const float4* __restrict__ tab, float z) {
+// h w'_i, h^2 w''_i}); `fine` selects the 8x refined grid.
+__device__ __forceinline__ float tab_quantile(const float4* __restrict__ tab, float z, bool fine) {
   const float t = normcdfinvf(z);
-  float u = (t + kTabT1f) * kTabInvH;
-  u = fminf(fmaxf(u, 0.0f), static_cast<float>(kTabNodes - 1));
+  const int nseg = fine ? kTabFineNodes - 1 : kTabNodes - 1;
+  float u = (t + kTabT1f) * (fine ? kTabInvH * kTabRefine : kTabInvH);
+  u = fminf(fmaxf(u, 0.0f), static_cast<float>(nseg));
   int i = static_cast<int>(u);
-  if (i > kTabNodes - 2) i = kTabNodes - 2;
+  if (i > nseg - 1) i = nseg - 1;
   const float s = u - static_cast<float>(i);
   const float4 n0 = __ldg(tab + i);
   if (!(n0.x > 0.0f)) return 0.0f;  // below the FP32 range
@@ -282,9 +310,10 @@ __device__ __forceinline__ float beta_solve_oriented(float A, float B, float x0,
 // InvCDF_beta(z; a, b) of a Beta record by the FP32 Halley iteration; x_start
 // in (0, 1) seeds it (otherwise the analytic start point is used).
 __device__ __forceinline__ float pair_quantile_newton(const Pair& p, float z, float x_start, BetaSolveStats* st) {
-  const bool m0x = pair_m0_is_x0(p.meta);
-  const float x0 = m0x ? p.m0 : 1.0f - p.m0;
-  const float y0 = m0x ? 1.0f - p.m0 : p.m0;
+  const bool m0x = signbit(p.m0);
+  const float m0 = fabsf(p.m0);
+  const float x0 = m0x ? m0 : 1.0f - m0;
+  const float y0 = m0x ? 1.0f - m0 : m0;
   const float lnz = logf(z), ln1mz = log1pf(-z);
   if (z <= p.p_half) return beta_solve_oriented(p.a, p.b, x0, y0, p.c, lnz, ln1mz, x_start, st);
   // root above 1/2: 1 - x solves I_{1-x}(b, a) = 1 - z
@@ -294,8 +323,9 @@ __device__ __forceinline__ float pair_quantile_newton(const Pair& p, float z, fl
 
 // Loss of one pair: max_l * InvCDF(z; a, b) for Beta records, the mean for
 // sigma == 0 records (and for every record when primary_only), 0 for
-// mean == 0 records.  `tab` (may be null) is the record's quantile table;
-// newton_only forces the Halley iteration for every Beta record.
+// mean == 0 records.  `tab` (may be null) is the record's quantile table (the
+// fine one when meta bit 7 is set); newton_only forces the Halley iteration
+// for every Beta record.
 __device__ __forceinline__ float pair_loss(const Pair& p, float z, bool primary_only, const float4* tab,
                                            bool newton_only, BetaSolveStats* st) {
   const uint32_t kind = pair_kind(p.meta);
@@ -305,7 +335,7 @@ __device__ __forceinline__ float pair_loss(const Pair& p, float z, bool primary_
   if (kind == kKindZero) return 0.0f;
   if (primary_only || kind == kKindMean) return p.mu;
   if (tab != nullptr && !newton_only) {
-    const float x = tab_quantile(tab, z);
+    const float x = tab_quantile(tab, z, pair_fine(p.meta));
     if (pair_tab_exact(p.meta)) return p.max_l * x;
     return p.max_l * pair_quantile_newton(p, z, x, st);
   }

@@ -31,15 +31,22 @@ cudaError_t launch_prepare_records(const int32_t* events, const float* mean, con
                                    const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
                                    int32_t* max_event, cudaStream_t s);
 
-// Quantile tables of prepared records (kTabNodes float4 per record), built in
-// FP64; sets the table-exact bit of each record's meta.
-cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, cudaStream_t s);
+// Quantile tables of prepared records, built in FP64: kTabNodes float4 per
+// record in `tab`; then, for the first fine_table_cap(n) records (in record
+// order) whose coarse table fails its check, kTabFineStride float4 per slot in
+// `tabf`.  Sets each record's table-exact and fine bits.  `work` holds
+// build_tables_work_words(n) words; on return work[n] is the number of
+// candidates for fine tables (min(work[n], cap) slots are used).
+size_t build_tables_work_words(int64_t n);
+uint32_t fine_table_cap(int64_t n);
+cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, float4* tabf,
+                                uint32_t* work, cudaStream_t s, int* n_launch);
 
 // Check kernels (device functions of the hot path on given inputs).
 cudaError_t launch_debug_uniforms(uint32_t seed_lo, uint32_t seed_hi, int64_t n, const int64_t* trials,
                                   const int32_t* ks, const int32_t* elts, float* out, cudaStream_t s);
-cudaError_t launch_debug_losses(const Pair* recs, const float4* tab, const float* z, int64_t n, int newton_only,
-                                float* out, int32_t* iters, cudaStream_t s);
+cudaError_t launch_debug_losses(const Pair* recs, const float4* tab, const float4* tabf, const float* z, int64_t n,
+                                int newton_only, float* out, int32_t* iters, cudaStream_t s);
 
 // --------------------------------------------------------------- scan
 // Exclusive prefix sum of n uint32 values; out[n] receives the total.
@@ -81,7 +88,7 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
 //             losses, trial sums and year losses.
 // Event record: x = (trial in tile << 27) | ((pairs - 1) << 22) | k, y = first pair.
 constexpr int kGatherThreads = 1024;  // 32 warps per CTA, one CTA per SM
-constexpr int kLossThreads = 1024;
+constexpr int kLossThreads = 512;
 constexpr int kWarpTrials = 8;        // trials per tile (< 32)
 constexpr int kMaxTrialEvents = 1 << 22;
 
@@ -108,14 +115,17 @@ struct LossParams {
   const Pair* pairs;
   int32_t n_elts;
   int32_t elt_id[32];
-  const float4* tab[32];  // quantile tables of the layer's ELTs (by position)
+  const float4* tab[32];   // coarse quantile tables of the layer's ELTs (by position)
+  const float4* tabf[32];  // fine quantile tables
   float t_ret[32], t_lim[32], t_share[32];
   float occ_r, occ_l;  // occurrence terms in FP32 (the loss arithmetic)
   double agg_r, agg_l;
   uint32_t seed_lo, seed_hi;
+  uint32_t rk[20];  // Philox round keys of the seed: (seed_lo + r W0, seed_hi + r W1), r = 0..9
   int32_t primary_only;
   int32_t newton_only;
   double* ylt;
+  double* def_acc;  // per trial: deferred occurrence losses of trials still pending at their tile's end
   int64_t* diag_hits;
   uint64_t* diag_hash;
   unsigned long long* counters;  // [0] tile queue, [1] pairs, [2] non-converged, [3] Halley events

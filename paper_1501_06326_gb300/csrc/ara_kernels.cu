@@ -155,7 +155,7 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
     p.a = p.b = p.m0 = p.c = p.p_half = 0.0f;
     p.max_l = static_cast<float>(ex);
     p.mu = static_cast<float>(mu);
-    uint32_t kind = kKindBeta, m0x = 0;
+    uint32_t kind = kKindBeta;
     double sa = 0.0, sb_ = 0.0;
     if (!(mu >= 0.0) || !(sg >= 0.0) || !isfinite(mu) || !isfinite(sg) || !isfinite(ex)) {
       f |= kBadValue;
@@ -188,12 +188,11 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
       p.b = static_cast<float>(b);
       sa = a;
       sb_ = b;
-      m0x = (x0 <= y0) ? 1u : 0u;
-      p.m0 = static_cast<float>(m0x ? x0 : y0);
+      p.m0 = (x0 <= y0) ? -static_cast<float>(x0) : static_cast<float>(y0);
       p.c = static_cast<float>(c);
       p.p_half = static_cast<float>(ph);
     }
-    p.meta = (kind << 5) | (m0x << 7) | (static_cast<uint32_t>(i) << 9);
+    p.meta = (kind << 5) | (static_cast<uint32_t>(i) << 9);
     out[i] = p;
     if (shapes) shapes[i] = make_double2(sa, sb_);
   }
@@ -294,59 +293,85 @@ __device__ double beta_polish_f64(double p, double A, double B, double lnB, doub
 
 }  // namespace
 
-// One warp per record, lane i = node i at t_i = -T1 + i h.  Each node: the
-// FP64 root x_i (seeded by the FP32 Halley solver), w = ln x, w' and w''
-// (derivatives in t: w' = phi(t) / (x f(x)), w'' = w' (-t - w' (a - (b-1) x/(1-x)))).
-// The stored float4 is {x_i, w_{i+1} - w_i, h w'_i, h^2 w''_i}.  Then each
-// segment is checked at s = 1/4, 1/2, 3/4: the FP32 interpolant (as the hot
-// path evaluates it) against the FP64 CDF; the record is table-exact when the
-// implied relative error of x is within kTabTol everywhere x >= 1e-30.
-__global__ void k_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab) {
+// Quantile table of one record on the grid t_j = -T1 + j h / R, j < 31 R + 1
+// (R = 1: the coarse table, R = kTabRefine: the fine one); one warp, lane l
+// holding nodes l + 32 k.  Each node: the FP64 root x_j (seeded by the FP32
+// Halley solver), w = ln x, w' and w'' (derivatives in t: w' = phi(t) / (x f(x)),
+// w'' = w' (-t - w' (a - (b-1) x/(1-x)))).  The stored float4 is
+// {x_j, w_{j+1} - w_j, h w'_j, h^2 w''_j}.  Then each segment is checked at
+// s = 1/4, 1/2, 3/4: the FP32 interpolant (as the hot path evaluates it)
+// against the FP64 CDF.  Returns (to every lane) whether the implied relative
+// error of x is within kTabTol everywhere x >= 1e-30.
+template <int R>
+__device__ bool build_record_table(const Pair& pr, double a, double b, float4* out) {
+  constexpr int kN = R * (kTabNodes - 1) + 1;
+  constexpr int kK = (kN + 31) / 32;
   const int lane = threadIdx.x & 31;
-  const int64_t rec = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if (rec >= n) return;
-  const Pair pr = recs[rec];
-  float4* out = tab + rec * kTabNodes;
-  if (pair_kind(pr.meta) != kKindBeta) {
-    out[lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    return;
-  }
-  const double a = shapes[rec].x, b = shapes[rec].y;
   const double lnB = lgamma(a) + lgamma(b) - lgamma(a + b);
-  const double h = 2.0 * kTabT1 / (kTabNodes - 1);
-  const double t = -kTabT1 + h * lane;
-  const double zl = normcdf(-fabs(t));  // the smaller tail probability
-  // FP32 seed, then FP64 polish on the side where the root keeps relative precision
-  BetaSolveStats st;
-  const float zf = (t <= 0.0) ? static_cast<float>(zl) : static_cast<float>(1.0 - zl);
-  const float seed = pair_quantile_newton(pr, fminf(fmaxf(zf, 5.9604645e-08f), 0.99999994f), -1.0f, &st);
-  double w, lny, x;
-  if (t <= 0.0) {
-    x = beta_polish_f64(zl, a, b, lnB, static_cast<double>(seed));
-    w = log(x);
-    lny = log1p(-x);
-  } else {
-    const double y = beta_polish_f64(zl, b, a, lnB, 1.0 - static_cast<double>(seed));
-    x = 1.0 - y;
-    w = log1p(-y);
-    lny = log(y);
+  const double h = 2.0 * kTabT1 / (kN - 1);
+  float4 node[kK];
+  double w[kK];
+#pragma unroll
+  for (int k = 0; k < kK; ++k) {
+    const int j = lane + 32 * k;
+    const double t = -kTabT1 + h * (j < kN ? j : kN - 1);
+    const double zl = normcdf(-fabs(t));  // the smaller tail probability
+    // FP32 seed, then FP64 polish on the side where the root keeps relative precision
+    BetaSolveStats st;
+    const float zf = (t <= 0.0) ? static_cast<float>(zl) : static_cast<float>(1.0 - zl);
+    const float seed = pair_quantile_newton(pr, fminf(fmaxf(zf, 5.9604645e-08f), 0.99999994f), -1.0f, &st);
+    double lny, x;
+    if (t <= 0.0) {
+      x = beta_polish_f64(zl, a, b, lnB, static_cast<double>(seed));
+      w[k] = log(x);
+      lny = log1p(-x);
+    } else {
+      const double y = beta_polish_f64(zl, b, a, lnB, 1.0 - static_cast<double>(seed));
+      x = 1.0 - y;
+      w[k] = log1p(-y);
+      lny = log(y);
+    }
+    const double lpdf = (a - 1.0) * w[k] + (b - 1.0) * lny - lnB;
+    const double lphi = -0.5 * t * t - 0.91893853320467274178;
+    const double D = exp(lphi - w[k] - lpdf);
+    const double E = D * (-t - D * (a - (b - 1.0) * exp(w[k] - lny)));
+    node[k] = make_float4(static_cast<float>(exp(w[k])), 0.0f, static_cast<float>(h * D), static_cast<float>(h * h * E));
   }
-  const double lpdf = (a - 1.0) * w + (b - 1.0) * lny - lnB;
-  const double lphi = -0.5 * t * t - 0.91893853320467274178;
-  const double D = exp(lphi - w - lpdf);
-  const double E = D * (-t - D * (a - (b - 1.0) * exp(w - lny)));
-  const double w_next = __shfl_down_sync(0xffffffffu, w, 1);
-  const float4 node = make_float4(static_cast<float>(exp(w)), lane < kTabNodes - 1 ? static_cast<float>(w_next - w) : 0.0f,
-                                  static_cast<float>(h * D), static_cast<float>(h * h * E));
-  out[lane] = node;
+  // w_{j+1} - w_j: node j + 1 is the next lane, or lane 0 of the next round
+#pragma unroll
+  for (int k = 0; k < kK; ++k) {
+    double wn = __shfl_down_sync(0xffffffffu, w[k], 1);
+    if (k + 1 < kK) {
+      const double w0 = __shfl_sync(0xffffffffu, w[k + 1], 0);
+      if (lane == 31) wn = w0;
+    }
+    const int j = lane + 32 * k;
+    if (j < kN - 1) node[k].y = static_cast<float>(wn - w[k]);
+    if (j < kN) out[j] = node[k];
+  }
   // ---- accuracy check of the interpolant
-  const float d1 = __shfl_down_sync(0xffffffffu, node.z, 1);
-  const float e1 = __shfl_down_sync(0xffffffffu, node.w, 1);
-  bool ok = isfinite(node.x) && isfinite(node.y) && isfinite(node.z) && isfinite(node.w);
-  if (lane < kTabNodes - 1) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < kK; ++k) {
+    float d1 = __shfl_down_sync(0xffffffffu, node[k].z, 1);
+    float e1 = __shfl_down_sync(0xffffffffu, node[k].w, 1);
+    if (k + 1 < kK) {
+      const float d0n = __shfl_sync(0xffffffffu, node[k + 1].z, 0);
+      const float e0n = __shfl_sync(0xffffffffu, node[k + 1].w, 0);
+      if (lane == 31) {
+        d1 = d0n;
+        e1 = e0n;
+      }
+    }
+    const int j = lane + 32 * k;
+    if (j >= kN) continue;
+    const float4 nd = node[k];
+    ok = ok && isfinite(nd.x) && isfinite(nd.y) && isfinite(nd.z) && isfinite(nd.w);
+    if (j >= kN - 1) continue;
+    const double t = -kTabT1 + h * j;
     for (int q = 1; q <= 3; ++q) {
       const float sf = 0.25f * q;
-      const float xq = (node.x > 0.0f) ? node.x * expf(tab_increment(sf, node.y, node.z, node.w, d1, e1)) : 0.0f;
+      const float xq = (nd.x > 0.0f) ? nd.x * expf(tab_increment(sf, nd.y, nd.z, nd.w, d1, e1)) : 0.0f;
       if (!(xq >= 1e-30f)) continue;  // negligible losses
       const double tq = t + h * sf;
       const double zq = normcdf(-fabs(tq));
@@ -359,14 +384,65 @@ __global__ void k_build_tables(Pair* recs, const double2* shapes, int64_t n, flo
       ok = ok && (rel <= kTabTol) && isfinite(rel);
     }
   }
-  const bool all_ok = __all_sync(0xffffffffu, ok);
-  if (lane == 0 && all_ok) recs[rec].meta = pr.meta | (1u << 8);
+  return __all_sync(0xffffffffu, ok);
 }
 
-cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, cudaStream_t s) {
+// Coarse tables, one warp per record; need[rec] = 1 for a Beta record whose
+// coarse table is not exact (a candidate for a fine table).
+__global__ void k_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, uint32_t* need) {
+  const int lane = threadIdx.x & 31;
+  const int64_t rec = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (rec >= n) return;
+  const Pair pr = recs[rec];
+  float4* out = tab + rec * kTabNodes;
+  if (pair_kind(pr.meta) != kKindBeta) {
+    out[lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (lane == 0) need[rec] = 0u;
+    return;
+  }
+  const bool ok = build_record_table<1>(pr, shapes[rec].x, shapes[rec].y, out);
+  if (lane == 0) {
+    if (ok) recs[rec].meta = pr.meta | (1u << 8);
+    need[rec] = ok ? 0u : 1u;
+  }
+}
+
+// Fine tables for the first `cap` candidates in record order (slot = exclusive
+// prefix of need): the record's meta then addresses its fine table; it is
+// table-exact if the fine table passes the check.
+__global__ void k_build_fine(Pair* recs, const double2* shapes, int64_t n, const uint32_t* slot, uint32_t cap,
+                             float4* tabf) {
+  const int lane = threadIdx.x & 31;
+  const int64_t rec = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (rec >= n) return;
+  const uint32_t sl = slot[rec];
+  if (slot[rec + 1] == sl || sl >= cap) return;
+  const Pair pr = recs[rec];
+  const bool ok = build_record_table<kTabRefine>(pr, shapes[rec].x, shapes[rec].y,
+                                                 tabf + static_cast<int64_t>(sl) * kTabFineStride);
+  if (lane == 0) recs[rec].meta = (pr.meta & 0x7Fu) | (1u << 7) | (ok ? (1u << 8) : 0u) | (sl << 9);
+}
+
+size_t build_tables_work_words(int64_t n) { return static_cast<size_t>(n) + 1 + scan_tmp_words(n + 1); }
+
+uint32_t fine_table_cap(int64_t n) {
+  const int64_t cap = n / 16 + 16;
+  return static_cast<uint32_t>(cap < n ? cap : n);
+}
+
+cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, float4* tabf,
+                                uint32_t* work, cudaStream_t s, int* n_launch) {
   if (n == 0) return cudaSuccess;
   const int64_t blocks = (n + 7) / 8;  // 8 warps (records) per block
-  k_build_tables<<<static_cast<int>(blocks < 2147483647 ? blocks : 2147483647), 256, 0, s>>>(recs, shapes, n, tab);
+  const int grid = static_cast<int>(blocks < 2147483647 ? blocks : 2147483647);
+  k_build_tables<<<grid, 256, 0, s>>>(recs, shapes, n, tab, work);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  int launched = 1;
+  if ((err = scan_exclusive_u32(work, work, n, work + n + 1, s, &launched)) != cudaSuccess) return err;
+  k_build_fine<<<grid, 256, 0, s>>>(recs, shapes, n, work, fine_table_cap(n), tabf);
+  ++launched;
+  if (n_launch) *n_launch += launched;
   return cudaGetLastError();
 }
 
@@ -378,13 +454,15 @@ __global__ void k_debug_uniforms(uint32_t seed_lo, uint32_t seed_hi, int64_t n, 
     out[i] = philox_uniform(seed_lo, seed_hi, trials[i], static_cast<uint32_t>(ks[i]), static_cast<uint32_t>(elts[i]));
 }
 
-__global__ void k_debug_losses(const Pair* recs, const float4* tab, const float* z, int64_t n, int newton_only,
-                               float* out, int32_t* iters) {
+__global__ void k_debug_losses(const Pair* recs, const float4* tab, const float4* tabf, const float* z, int64_t n,
+                               int newton_only, float* out, int32_t* iters) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
     BetaSolveStats st;
     const Pair pr = recs[i];
-    out[i] = pair_loss(pr, z[i], false, tab + static_cast<int64_t>(pair_rec(pr.meta)) * kTabNodes, newton_only != 0, &st);
+    const int64_t r = pair_rec(pr.meta);
+    const float4* tb = pair_fine(pr.meta) ? tabf + r * kTabFineStride : tab + r * kTabNodes;
+    out[i] = pair_loss(pr, z[i], false, tb, newton_only != 0, &st);
     if (iters) iters[i] = st.converged ? st.iters : -st.iters;
   }
 }
@@ -397,11 +475,12 @@ cudaError_t launch_debug_uniforms(uint32_t seed_lo, uint32_t seed_hi, int64_t n,
   return cudaGetLastError();
 }
 
-cudaError_t launch_debug_losses(const Pair* recs, const float4* tab, const float* z, int64_t n, int newton_only,
-                                float* out, int32_t* iters, cudaStream_t s) {
+cudaError_t launch_debug_losses(const Pair* recs, const float4* tab, const float4* tabf, const float* z, int64_t n,
+                                int newton_only, float* out, int32_t* iters, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int64_t b = (n + 127) / 128;
-  k_debug_losses<<<static_cast<int>(b < 65535 ? b : 65535), 128, 0, s>>>(recs, tab, z, n, newton_only, out, iters);
+  k_debug_losses<<<static_cast<int>(b < 65535 ? b : 65535), 128, 0, s>>>(recs, tab, tabf, z, n, newton_only, out,
+                                                                         iters);
   return cudaGetLastError();
 }
 
@@ -644,9 +723,8 @@ constexpr uint32_t kRecCntShift = 22;
 constexpr uint32_t kRecKMask = (1u << 22) - 1u;
 
 struct GatherWarp {
-  int32_t off[kWarpTrials + 1];  // trial offsets relative to the tile's first event
-  uint32_t pos_e[128];           // filter positives of one step: event id
-  int32_t pos_rel[128];          //                               tile-relative position
+  int32_t off[16];  // trial offsets relative to the tile's first event; INT32_MAX past the tile's end
+  uint2 pos[256];   // filter positives of one step: (event id, position in the step)
 };
 
 }  // namespace
@@ -661,6 +739,108 @@ int gather_filter_words(int64_t n_words, int max_smem) {
   return fw;
 }
 
+namespace {
+
+// State of one warp's pass over one tile.
+struct GatherTile {
+  const int4* ids4;  // the tile's ids from the 16-byte boundary at or below its first event
+  int32_t lead;      // ids before the tile's first event in the first int4
+  int32_t nev;       // events of the tile
+  int32_t span;      // nev + lead
+  uint2* out;        // the tile's region of the event buffer
+  uint32_t nout;     // records written
+};
+
+// Loads step c0 (256 ids: int4 lane and int4 32 + lane of the step), evict-first.
+__device__ __forceinline__ void gather_load(const GatherTile& g, int32_t c0, uint32_t lane, int4& v0, int4& v1) {
+  v0 = make_int4(0, 0, 0, 0);
+  v1 = make_int4(0, 0, 0, 0);
+  const int32_t i0 = c0 + 4 * static_cast<int32_t>(lane);
+  if (i0 < g.span) v0 = __ldcs(g.ids4 + (i0 >> 2));
+  if (i0 + 128 < g.span) v1 = __ldcs(g.ids4 + ((i0 + 128) >> 2));
+}
+
+// One step of 256 YET positions: filter, compact the positives in YET order,
+// resolve them against the rank directory and append the hit-event records.
+__device__ __forceinline__ void gather_step(const GatherParams& p, const uint32_t* __restrict__ filt, uint32_t fmask,
+                                            GatherWarp& ws, GatherTile& g, int32_t c0, uint32_t lane, int4 v0,
+                                            int4 v1) {
+  const uint32_t e[8] = {static_cast<uint32_t>(v0.x), static_cast<uint32_t>(v0.y), static_cast<uint32_t>(v0.z),
+                         static_cast<uint32_t>(v0.w), static_cast<uint32_t>(v1.x), static_cast<uint32_t>(v1.y),
+                         static_cast<uint32_t>(v1.z), static_cast<uint32_t>(v1.w)};
+  // 1. filter (the shift count of a funnel shift is taken mod 32)
+  uint32_t m = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t w = filt[(e[j] >> 5) & fmask];
+    m |= (__funnelshift_r(w, w, e[j]) & 1u) << j;
+  }
+  const uint32_t q0 = 4u * lane;  // step positions of the lane's ids: q0 + j, q0 + 128 + j
+  if (c0 == 0 || c0 + 256 > g.span) {
+    uint32_t vm = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int32_t rel = c0 + static_cast<int32_t>(q0 + (j & 3) + (j >> 2) * 128) - g.lead;
+      vm |= (static_cast<uint32_t>(rel) < static_cast<uint32_t>(g.nev) ? 1u : 0u) << j;
+    }
+    m &= vm;
+  }
+  // 2. compaction: one scan over both halves (16-bit fields)
+  const uint32_t cl = __popc(m & 15u), ch = __popc(m >> 4);
+  const uint32_t incl = warp_inclusive_scan(cl | (ch << 16));
+  const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+  const uint32_t nlo = tot & 0xFFFFu;
+  const uint32_t npos = nlo + (tot >> 16);
+  if (npos == 0) return;
+  if (m) {
+    uint32_t at = (incl & 0xFFFFu) - cl;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (m & (1u << j)) ws.pos[at++] = make_uint2(e[j], q0 + j);
+    at = nlo + (incl >> 16) - ch;
+#pragma unroll
+    for (int j = 4; j < 8; ++j)
+      if (m & (1u << j)) ws.pos[at++] = make_uint2(e[j], q0 + 124 + j);
+  }
+  __syncwarp();
+  // 3. resolve, one positive per lane
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (uint32_t r0 = 0; r0 < npos; r0 += 32) {
+    uint32_t key = 0, ps = 0;
+    bool hit = false;
+    if (r0 + lane < npos) {
+      const uint2 q = ws.pos[r0 + lane];
+      const uint2 rd = __ldg(&p.rankdir[q.x >> 5]);
+      const uint32_t bit = 1u << (q.x & 31);
+      if (rd.x & bit) {
+        hit = true;
+        const uint32_t below = __popc(rd.x & (bit - 1u));
+        uint32_t cnt = 1;
+        if (rd.y & 0x80000000u) {
+          const uint32_t sl = (rd.y & 0x7FFFFFFFu) + below;
+          ps = __ldg(&p.slot_start[sl]);
+          cnt = __ldg(&p.slot_start[sl + 1]) - ps;
+        } else {
+          ps = rd.y + below;
+        }
+        // trial: the last t with off[t] <= rel (off is padded with INT32_MAX)
+        const int32_t rel = c0 + static_cast<int32_t>(q.y) - g.lead;
+        int t = (ws.off[4] <= rel) ? 4 : 0;
+        t += (ws.off[t + 2] <= rel) ? 2 : 0;
+        t += (ws.off[t + 1] <= rel) ? 1 : 0;
+        key = ((cnt - 1u) << kRecCntShift) | (static_cast<uint32_t>(t) << kRecTrialShift) |
+              static_cast<uint32_t>(rel - ws.off[t]);
+      }
+    }
+    const uint32_t hm = __ballot_sync(0xffffffffu, hit);
+    if (hit) g.out[g.nout + __popc(hm & lt_mask)] = make_uint2(key, ps);
+    g.nout += __popc(hm);
+  }
+  __syncwarp();
+}
+
+}  // namespace
+
 __global__ void __launch_bounds__(kGatherThreads, 1) k_gather(const GatherParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GatherWarp* gw = reinterpret_cast<GatherWarp*>(smem_raw);
@@ -668,7 +848,6 @@ __global__ void __launch_bounds__(kGatherThreads, 1) k_gather(const GatherParams
   const uint32_t lane = lane_id();
   GatherWarp& ws = gw[threadIdx.x >> 5];
   const uint32_t fmask = static_cast<uint32_t>(p.filt_words) - 1u;
-  const uint32_t lt_mask = (1u << lane) - 1u;
 
   for (int w = threadIdx.x; w < p.filt_words; w += blockDim.x) {
     uint32_t v = 0;
@@ -686,89 +865,33 @@ __global__ void __launch_bounds__(kGatherThreads, 1) k_gather(const GatherParams
     const int64_t tb = (ta + kWarpTrials < p.t_end) ? ta + kWarpTrials : p.t_end;
     const int ntr = static_cast<int>(tb - ta);
     const int64_t ea = __ldg(&p.off[ta]);
-    if (lane <= static_cast<uint32_t>(ntr)) ws.off[lane] = static_cast<int32_t>(__ldg(&p.off[ta + lane]) - ea);
+    if (lane < 16)
+      ws.off[lane] = (lane <= static_cast<uint32_t>(ntr)) ? static_cast<int32_t>(__ldg(&p.off[ta + lane]) - ea)
+                                                          : INT32_MAX;
     __syncwarp();
-    const int32_t nev = ws.off[ntr];
-    const int32_t* ids = p.ids + (ea & ~int64_t(3));
-    const int32_t lead = static_cast<int32_t>(ea & 3);
-    const int32_t span = nev + lead;
-    uint2* out = p.ev_buf + (ea - p.e0);
-    uint32_t nout = 0;
-    int tcur = 0;
-    while (tcur + 1 < ntr && ws.off[tcur + 1] <= 0) ++tcur;
-    int4 cur = make_int4(0, 0, 0, 0);
-    if (4 * static_cast<int32_t>(lane) < span) cur = __ldcs(reinterpret_cast<const int4*>(ids) + lane);
-    for (int32_t c0 = 0; c0 < span; c0 += 128) {
-      int4 nxt = make_int4(0, 0, 0, 0);
-      if (c0 + 128 + 4 * static_cast<int32_t>(lane) < span)
-        nxt = __ldcs(reinterpret_cast<const int4*>(ids + c0 + 128) + lane);
-      const int32_t rel0 = c0 + 4 * static_cast<int32_t>(lane) - lead;
-      const int32_t ev[4] = {cur.x, cur.y, cur.z, cur.w};
-      // 1. filter the lane's four ids (shift counts of a funnel shift are taken mod 32)
-      uint32_t m = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t e = static_cast<uint32_t>(ev[j]);
-        const uint32_t w = filt[(e >> 5) & fmask];
-        const bool in = static_cast<uint32_t>(rel0 + j) < static_cast<uint32_t>(nev);
-        m |= (in ? (__funnelshift_r(w, w, e) & 1u) : 0u) << j;
-      }
-      // 2. compact the positives of the warp, in YET order, into the staging list
-      const uint32_t c = __popc(m);
-      const uint32_t incl = warp_inclusive_scan(c);
-      const uint32_t npos = __shfl_sync(0xffffffffu, incl, 31);
-      if (m) {
-        uint32_t at = incl - c;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (m & (1u << j)) {
-            ws.pos_e[at] = static_cast<uint32_t>(ev[j]);
-            ws.pos_rel[at] = rel0 + j;
-            ++at;
-          }
-        }
-      }
-      __syncwarp();
-      // 3. resolve the positives, one per lane, and write the hit-event records
-      for (uint32_t r0 = 0; r0 < npos; r0 += 32) {
-        const bool valid = r0 + lane < npos;
-        uint32_t key = 0, ps = 0;
-        bool hit = false;
-        int32_t rel = 0;
-        if (valid) {
-          const uint32_t e = ws.pos_e[r0 + lane];
-          rel = ws.pos_rel[r0 + lane];
-          const uint2 rd = __ldg(&p.rankdir[e >> 5]);
-          const uint32_t bit = 1u << (e & 31);
-          if (rd.x & bit) {
-            hit = true;
-            const uint32_t below = __popc(rd.x & (bit - 1u));
-            uint32_t cnt = 1;
-            if (rd.y & 0x80000000u) {
-              const uint32_t sl = (rd.y & 0x7FFFFFFFu) + below;
-              ps = __ldg(&p.slot_start[sl]);
-              cnt = __ldg(&p.slot_start[sl + 1]) - ps;
-            } else {
-              ps = rd.y + below;
-            }
-            int t = tcur;
-            while (t + 1 < ntr && ws.off[t + 1] <= rel) ++t;
-            key = ((cnt - 1u) << kRecCntShift) | (static_cast<uint32_t>(t) << kRecTrialShift) |
-                  static_cast<uint32_t>(rel - ws.off[t]);
-          }
-        }
-        const uint32_t hm = __ballot_sync(0xffffffffu, hit);
-        if (hit) out[nout + __popc(hm & lt_mask)] = make_uint2(key, ps);
-        nout += __popc(hm);
-      }
-      __syncwarp();
-      {
-        const int32_t nrel = c0 + 128 - lead;
-        while (tcur + 1 < ntr && ws.off[tcur + 1] <= nrel) ++tcur;
-      }
-      cur = nxt;
+    GatherTile g;
+    g.nev = ws.off[ntr];
+    g.ids4 = reinterpret_cast<const int4*>(p.ids + (ea & ~int64_t(3)));
+    g.lead = static_cast<int32_t>(ea & 3);
+    g.span = g.nev + g.lead;
+    g.out = p.ev_buf + (ea - p.e0);
+    g.nout = 0;
+    // three steps of ids in registers, two of them in flight while one is filtered;
+    // unrolled by three so that no register of a load in flight is ever moved
+    int4 a0, a1, b0, b1, c0v, c1v;
+    gather_load(g, 0, lane, a0, a1);
+    gather_load(g, 256, lane, b0, b1);
+    for (int32_t c0 = 0; c0 < g.span; c0 += 768) {
+      gather_load(g, c0 + 512, lane, c0v, c1v);
+      gather_step(p, filt, fmask, ws, g, c0, lane, a0, a1);
+      if (c0 + 256 >= g.span) break;
+      gather_load(g, c0 + 768, lane, a0, a1);
+      gather_step(p, filt, fmask, ws, g, c0 + 256, lane, b0, b1);
+      if (c0 + 512 >= g.span) break;
+      gather_load(g, c0 + 1024, lane, b0, b1);
+      gather_step(p, filt, fmask, ws, g, c0 + 512, lane, c0v, c1v);
     }
-    if (lane == 0) p.tile_cnt[tile] = nout;
+    if (lane == 0) p.tile_cnt[tile] = g.nout;
     __syncwarp();
   }
 }
@@ -783,10 +906,23 @@ cudaError_t launch_gather(const GatherParams& p, int grid, size_t smem, cudaStre
 
 namespace {
 
+constexpr int kWin = 128;  // events (and pairs) per window: four per lane
+constexpr uint32_t kDefCur = 1u;   // deferred event of the open tile
+constexpr uint32_t kDefLast = 2u;  // last deferred event of its trial
+
 struct LossWarp {
-  uint32_t d_key[32];  // deferred events: record
-  uint32_t d_ps[32];
-  double S[kWarpTrials];
+  uint2 rec[kWin];        // window records (general path)
+  uint32_t pre[kWin];     // first pair of each event, window-relative
+  uint8_t p2e[kWin];      // pair -> event
+  uint8_t pslow[kWin];    // pair needs the Halley iteration
+  float lp[kWin];         // pair losses
+  uint32_t d_key[32];     // deferred events, in event order: record
+  uint32_t d_ps[32];      //   first pair
+  int64_t d_o[32];        //   trial (output index)
+  uint32_t d_fl[32];      //   kDefCur | kDefLast
+  float d_O[32];          //   occurrence loss, once resolved
+  double S[kWarpTrials];  // sums of the table-path occurrence losses of the tile's trials
+  double Sd[kWarpTrials]; // sums of the deferred occurrence losses resolved while the tile is open
   unsigned long long hits[kWarpTrials];
   unsigned long long hash[kWarpTrials];
 };
@@ -811,8 +947,11 @@ __device__ __forceinline__ bool pair_fast(const LossParams& p, const Pair& pr, i
     loss = 0.0f;
   } else if (!p.primary_only && kind == kKindBeta) {
     if (p.newton_only || !pair_tab_exact(pr.meta)) return false;
-    const float z = philox_uniform(p.seed_lo, p.seed_hi, trial, k, static_cast<uint32_t>(p.elt_id[pos]));
-    loss = pr.max_l * tab_quantile(p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes, z);
+    const float z = philox_uniform_rk(p.rk, trial, k, static_cast<uint32_t>(p.elt_id[pos]));
+    const bool fine = pair_fine(pr.meta);
+    const float4* tb = fine ? p.tabf[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabFineStride
+                            : p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes;
+    loss = pr.max_l * tab_quantile(tb, z, fine);
   }
   *out = p.t_share[pos] * clamp_terms_f(loss, p.t_ret[pos], p.t_lim[pos]);
   return true;
@@ -823,42 +962,73 @@ __device__ __noinline__ float pair_slow(const LossParams& p, const Pair& pr, int
   const uint32_t pos = pair_pos(pr.meta);
   float v;
   if (pair_fast(p, pr, trial, k, &v)) return v;
-  const float z = philox_uniform(p.seed_lo, p.seed_hi, trial, k, static_cast<uint32_t>(p.elt_id[pos]));
-  const float4* tab = p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes;
+  const float z = philox_uniform_rk(p.rk, trial, k, static_cast<uint32_t>(p.elt_id[pos]));
+  const bool fine = pair_fine(pr.meta);
+  const float4* tab = fine ? p.tabf[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabFineStride
+                           : p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes;
   BetaSolveStats st;
-  const float x = pair_quantile_newton(pr, z, p.newton_only ? -1.0f : tab_quantile(tab, z), &st);
+  const float x = pair_quantile_newton(pr, z, p.newton_only ? -1.0f : tab_quantile(tab, z, fine), &st);
   if (!st.converged) ++*nc;
   return p.t_share[pos] * clamp_terms_f(pr.max_l * x, p.t_ret[pos], p.t_lim[pos]);
 }
 
-// Resolve the deferred events of the warp (all lanes call it): each lane one
-// event, then the occurrence losses are added to the trial sums in list order.
-__device__ __noinline__ void resolve_deferred(const LossParams& p, LossWarp& ws, int nd, int64_t ta,
-                                              unsigned long long* nc, unsigned long long* n_slow) {
+// Resolve the warp's deferred events (all lanes call it): lane i computes the
+// occurrence loss of entry i, then lane 0 adds them in list order.  A trial's
+// deferred losses form their own FP64 sum, in event order, so where the list
+// is flushed does not change any result: entries of the open tile go to its
+// shared sums, older ones to def_acc, and the last one of a trial finishes
+// its year loss.
+__device__ __noinline__ void resolve_deferred(const LossParams& p, LossWarp& ws, int nd, unsigned long long* nc,
+                                              unsigned long long* n_slow) {
   const uint32_t lane = lane_id();
   float O = 0.0f;
-  uint32_t tl = 0;
   if (lane < static_cast<uint32_t>(nd)) {
     const uint32_t key = ws.d_key[lane];
-    tl = key >> kRecTrialShift;
     const uint32_t k = key & kRecKMask;
     const uint32_t cnt = ((key >> kRecCntShift) & 31u) + 1u;
+    const int64_t t = p.t_begin + ws.d_o[lane];
     float G = 0.0f;
-    for (uint32_t j = 0; j < cnt; ++j) G += pair_slow(p, p.pairs[ws.d_ps[lane] + j], ta + tl, k, nc);
+    for (uint32_t j = 0; j < cnt; ++j) G += pair_slow(p, p.pairs[ws.d_ps[lane] + j], t, k, nc);
     O = clamp_terms_f(G, p.occ_r, p.occ_l);
     ++*n_slow;
   }
-  for (int i = 0; i < nd; ++i) {
-    const float Oi = __shfl_sync(0xffffffffu, O, i);
-    const uint32_t ti = __shfl_sync(0xffffffffu, tl, i);
-    if (lane == 0) ws.S[ti] += static_cast<double>(Oi);
+  ws.d_O[lane] = O;
+  __syncwarp();
+  if (lane == 0) {
+    double acc = 0.0;
+    bool open = false;  // acc holds def_acc of the current run's trial
+    for (int i = 0; i < nd; ++i) {
+      const float Oi = ws.d_O[i];
+      const uint32_t fl = ws.d_fl[i];
+      const int64_t o = ws.d_o[i];
+      if (fl & kDefCur) {
+        ws.Sd[ws.d_key[i] >> kRecTrialShift] += static_cast<double>(Oi);
+        continue;
+      }
+      if (!open) {
+        acc = p.def_acc[o];
+        open = true;
+      }
+      acc += static_cast<double>(Oi);
+      if (fl & kDefLast) {
+        p.ylt[o] = clamp_terms_d(p.ylt[o] + acc, p.agg_r, p.agg_l);
+        open = false;
+      } else if (i + 1 == nd || ws.d_o[i + 1] != o) {
+        p.def_acc[o] = acc;
+        open = false;
+      }
+    }
   }
   __syncwarp();
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kLossThreads, 1) k_losses(const LossParams p) {
+// k_losses: windows of up to kWin events whose pairs number at most kWin.
+// Event e of a window sits at (round e / 32, lane e % 32), pair q likewise, so
+// every load of records is coalesced and the four rounds of a lane are
+// independent work for the scheduler.
+__global__ void __launch_bounds__(kLossThreads, 1024 / kLossThreads) k_losses(const LossParams p) {
   __shared__ LossWarp lw[kLossThreads / 32];
   const uint32_t lane = lane_id();
   LossWarp& ws = lw[threadIdx.x >> 5];
@@ -866,6 +1036,7 @@ __global__ void __launch_bounds__(kLossThreads, 1) k_losses(const LossParams p) 
   const uint32_t lt_mask = (1u << lane) - 1u;
   unsigned long long n_nc = 0, n_slow = 0;
   uint32_t n_pairs = 0;
+  int nd = 0;  // deferred events listed; the list outlives tiles so that resolving keeps the lanes busy
 
   for (;;) {
     int64_t tile = 0;
@@ -879,109 +1050,180 @@ __global__ void __launch_bounds__(kLossThreads, 1) k_losses(const LossParams p) 
     const uint32_t n = __ldg(&p.tile_cnt[tile]);
     if (lane < static_cast<uint32_t>(ntr)) {
       ws.S[lane] = 0.0;
+      ws.Sd[lane] = 0.0;
       ws.hits[lane] = 0ull;
       ws.hash[lane] = 0ull;
     }
     __syncwarp();
-    int nd = 0;
-    uint32_t base = 0;
-    uint2 rec = make_uint2(0u, 0u);
-    if (lane < n) rec = __ldcs(recs + lane);
-    while (base < n) {
-      const bool valid = base + lane < n;
-      const uint32_t cnt = valid ? ((rec.x >> kRecCntShift) & 31u) + 1u : 0u;
-      const uint32_t cincl = warp_inclusive_scan(cnt);
-      const uint32_t take = __ballot_sync(0xffffffffu, valid && cincl <= 32u);
-      const uint32_t n_take = __popc(take);  // a prefix: cincl grows with the lane
-      const uint32_t np = __shfl_sync(0xffffffffu, cincl, n_take - 1);
-      // lane -> event: event i starts at lane cincl_i - cnt_i
-      uint32_t ev = lane;
-      if (np != n_take) {
-        const uint32_t starts = __reduce_or_sync(0xffffffffu, (lane < n_take) ? (1u << (cincl - cnt)) : 0u);
-        ev = static_cast<uint32_t>(__popc(starts & ((lt_mask << 1) | 1u))) - 1u;
-      }
-      const uint32_t ekey = __shfl_sync(0xffffffffu, rec.x, ev);
-      const uint32_t eps = __shfl_sync(0xffffffffu, rec.y, ev);
-      const uint32_t estart = __shfl_sync(0xffffffffu, cincl - cnt, ev);
-      const uint32_t etl = ekey >> kRecTrialShift, ek = ekey & kRecKMask;
-      const bool pv = lane < np;
-      float lv = 0.0f;
-      bool slow = false;
-      if (pv) {
-        const Pair pr = p.pairs[eps + (lane - estart)];
-        slow = !pair_fast(p, pr, ta + etl, ek, &lv);
-        if (diag) {
-          const uint32_t elt = static_cast<uint32_t>(p.elt_id[pair_pos(pr.meta)]);
-          atomicAdd(&ws.hits[etl], 1ull);
-          atomicAdd(&ws.hash[etl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(ek) << 32) | elt)));
-        }
-      }
-      n_pairs += pv ? 1u : 0u;
-      // next window: starts after the events taken (prefetched now)
-      const uint32_t nbase = base + n_take;
-      uint2 nrec = make_uint2(0u, 0u);
-      if (nbase + lane < n) nrec = __ldcs(recs + nbase + lane);
-      // event sums, in lane (= layer) order
-      const uint32_t eseg = pv ? ev : 0xFFFFu;
-      float G = lv;
-      uint32_t any_slow = slow ? 1u : 0u;
-      if (np != n_take) {
+    for (uint32_t base = 0; base < n;) {
+      // ---- window: records, pair prefix, events taken (at most kWin pairs)
+      uint2 rec[4];
+      uint32_t cnt[4], pre[4];
+      uint32_t carry = 0;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const float g2 = __shfl_up_sync(0xffffffffu, G, d);
-          const uint32_t s2 = __shfl_up_sync(0xffffffffu, eseg, d);
-          const uint32_t f2 = __shfl_up_sync(0xffffffffu, any_slow, d);
-          if (lane >= static_cast<uint32_t>(d) && s2 == eseg) {
-            G += g2;
-            any_slow |= f2;
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t e = base + 32 * j + lane;
+        rec[j] = (e < n) ? __ldcs(recs + e) : make_uint2(0u, 0u);
+        cnt[j] = (e < n) ? ((rec[j].x >> kRecCntShift) & 31u) + 1u : 0u;
+        const uint32_t incl = warp_inclusive_scan(cnt[j]);
+        pre[j] = carry + incl - cnt[j];
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      uint32_t n_take = 0, np_l = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool tk = cnt[j] != 0 && pre[j] + cnt[j] <= static_cast<uint32_t>(kWin);
+        n_take += __popc(__ballot_sync(0xffffffffu, tk));
+        if (tk) np_l = pre[j] + cnt[j];
+      }
+      const uint32_t np = __reduce_max_sync(0xffffffffu, np_l);
+      const bool all_single = (np == n_take);
+      if (!all_single) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t e = 32 * j + lane;
+          ws.rec[e] = rec[j];
+          ws.pre[e] = pre[j];
+          if (e < n_take)
+            for (uint32_t i = 0; i < cnt[j]; ++i) ws.p2e[pre[j] + i] = static_cast<uint8_t>(e);
+        }
+        __syncwarp();
+      }
+      // ---- pairs: Philox, inverse Beta through the table, ELT terms
+      float lv[4];
+      bool pslow[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t q = 32 * j + lane;
+        lv[j] = 0.0f;
+        pslow[j] = false;
+        if (q < np) {
+          uint2 r;
+          uint32_t qoff;
+          if (all_single) {
+            r = rec[j];
+            qoff = 0;
+          } else {
+            const uint32_t e = ws.p2e[q];
+            r = ws.rec[e];
+            qoff = q - ws.pre[e];
           }
+          const uint32_t etl = r.x >> kRecTrialShift, ek = r.x & kRecKMask;
+          const Pair pr = p.pairs[r.y + qoff];
+          pslow[j] = !pair_fast(p, pr, ta + etl, ek, &lv[j]);
+          if (diag) {
+            const uint32_t elt = static_cast<uint32_t>(p.elt_id[pair_pos(pr.meta)]);
+            atomicAdd(&ws.hits[etl], 1ull);
+            atomicAdd(&ws.hash[etl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(ek) << 32) | elt)));
+          }
+          ++n_pairs;
         }
       }
-      const uint32_t eseg_next = __shfl_down_sync(0xffffffffu, eseg, 1);
-      const bool ev_last = pv && (lane == np - 1 || eseg_next != eseg);
-      const bool defer = ev_last && any_slow;
-      const float O = (ev_last && !any_slow) ? clamp_terms_f(G, p.occ_r, p.occ_l) : 0.0f;
-      const uint32_t dmask = __ballot_sync(0xffffffffu, defer);
-      if (dmask) {
-        if (nd + __popc(dmask) > 32) {
-          resolve_deferred(p, ws, nd, ta, &n_nc, &n_slow);
-          nd = 0;
-        }
-        if (defer) {
-          const int at = nd + __popc(dmask & lt_mask);
-          ws.d_key[at] = ekey;
-          ws.d_ps[at] = eps;
-        }
-        nd += __popc(dmask);
-        __syncwarp();
-      }
-      // trial sums: segmented double-float reduction by trial, one FP64 add per trial
-      {
-        float hi = O, lo = 0.0f;
-        const uint32_t tseg = pv ? etl : 0xFFFFu;
+      // ---- events: sum of their pairs in layer order, occurrence terms
+      float O[4];
+      bool defer[4];
+      if (all_single) {
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const float h2 = __shfl_up_sync(0xffffffffu, hi, d);
-          const float l2 = __shfl_up_sync(0xffffffffu, lo, d);
-          const uint32_t s2 = __shfl_up_sync(0xffffffffu, tseg, d);
-          if (lane >= static_cast<uint32_t>(d) && s2 == tseg) df_add(hi, lo, h2, l2);
+        for (int j = 0; j < 4; ++j) {
+          defer[j] = pslow[j];
+          O[j] = (32 * j + lane < n_take && !pslow[j]) ? clamp_terms_f(lv[j], p.occ_r, p.occ_l) : 0.0f;
         }
-        const uint32_t tseg_next = __shfl_down_sync(0xffffffffu, tseg, 1);
-        if (pv && (lane == np - 1 || tseg_next != tseg)) ws.S[etl] += static_cast<double>(hi) + static_cast<double>(lo);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t q = 32 * j + lane;
+          ws.lp[q] = lv[j];
+          ws.pslow[q] = pslow[j] ? 1 : 0;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t e = 32 * j + lane;
+          float G = 0.0f;
+          bool sl = false;
+          if (e < n_take) {
+            for (uint32_t i = 0; i < cnt[j]; ++i) {
+              G += ws.lp[pre[j] + i];
+              sl |= ws.pslow[pre[j] + i] != 0;
+            }
+          }
+          defer[j] = sl;
+          O[j] = (e < n_take && !sl) ? clamp_terms_f(G, p.occ_r, p.occ_l) : 0.0f;
+        }
+      }
+      // ---- deferred events (window order)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t dmask = __ballot_sync(0xffffffffu, defer[j]);
+        if (dmask) {
+          if (nd + __popc(dmask) > 32) {
+            resolve_deferred(p, ws, nd, &n_nc, &n_slow);
+            nd = 0;
+          }
+          if (defer[j]) {
+            const int at = nd + __popc(dmask & lt_mask);
+            ws.d_key[at] = rec[j].x;
+            ws.d_ps[at] = rec[j].y;
+            ws.d_o[at] = ta - p.t_begin + (rec[j].x >> kRecTrialShift);
+            ws.d_fl[at] = kDefCur;
+          }
+          nd += __popc(dmask);
+          __syncwarp();
+        }
+      }
+      // ---- trial sums: for each trial of the window, a double-float butterfly over the lanes
+      {
+        const uint32_t t_first = __shfl_sync(0xffffffffu, rec[0].x, 0) >> kRecTrialShift;
+        const uint32_t last = n_take - 1;
+        uint32_t t_last = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t tj = __shfl_sync(0xffffffffu, rec[j].x, last & 31) >> kRecTrialShift;
+          if (static_cast<int>(last >> 5) == j) t_last = tj;
+        }
+        for (uint32_t t = t_first; t <= t_last; ++t) {
+          float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (32 * j + lane < n_take && (rec[j].x >> kRecTrialShift) == t) df_add(hi, lo, O[j], 0.0f);
+#pragma unroll
+          for (int d = 16; d > 0; d >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, hi, d);
+            const float l2 = __shfl_xor_sync(0xffffffffu, lo, d);
+            df_add(hi, lo, h2, l2);
+          }
+          if (lane == 0) ws.S[t] += static_cast<double>(hi) + static_cast<double>(lo);
+        }
         __syncwarp();
       }
-      base = nbase;
-      rec = nrec;
+      base += n_take;
     }
-    if (nd > 0) resolve_deferred(p, ws, nd, ta, &n_nc, &n_slow);
+    // ---- tile end: a trial whose deferred events are all resolved is final; one
+    // with events still listed keeps its table-path sum in ylt and its partial
+    // deferred sum in def_acc until the last of them is resolved
+    uint32_t pend = 0;
+    if (lane < static_cast<uint32_t>(nd) && (ws.d_fl[lane] & kDefCur)) {
+      const uint32_t tl = ws.d_key[lane] >> kRecTrialShift;
+      pend = 1u << tl;
+      const bool last = (lane + 1 == static_cast<uint32_t>(nd)) || ((ws.d_key[lane + 1] >> kRecTrialShift) != tl);
+      ws.d_fl[lane] = last ? kDefLast : 0u;
+    }
+    pend = __reduce_or_sync(0xffffffffu, pend);
+    __syncwarp();
     if (lane < static_cast<uint32_t>(ntr)) {
       const int64_t o = ta + lane - p.t_begin;
-      p.ylt[o] = clamp_terms_d(ws.S[lane], p.agg_r, p.agg_l);
+      if ((pend >> lane) & 1u) {
+        p.ylt[o] = ws.S[lane];
+        p.def_acc[o] = ws.Sd[lane];
+      } else {
+        p.ylt[o] = clamp_terms_d(ws.S[lane] + ws.Sd[lane], p.agg_r, p.agg_l);
+      }
       if (p.diag_hits) p.diag_hits[o] = static_cast<int64_t>(ws.hits[lane]);
       if (p.diag_hash) p.diag_hash[o] = ws.hash[lane];
     }
     __syncwarp();
   }
+  if (nd > 0) resolve_deferred(p, ws, nd, &n_nc, &n_slow);
   n_pairs = __reduce_add_sync(0xffffffffu, n_pairs);
   for (int d = 16; d > 0; d >>= 1) {
     n_nc += __shfl_xor_sync(0xffffffffu, n_nc, d);
