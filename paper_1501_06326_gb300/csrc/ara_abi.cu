@@ -50,7 +50,7 @@ struct ara_ctx {
   // ELT pool
   std::map<int32_t, Elt> pool;
   // per-layer index (grown on demand)
-  DevBuf bits, word_cnt, word_pairs, rankdir, mask, slot_cnt, pairs, scan_tmp;
+  DevBuf bits, word_cnt, word_pairs, rankdir, mask, slot_cnt, pairs, pairs_hot, scan_tmp;
   DevBuf ev_buf, tile_cnt;  // hit-event records of the layer kernels
   DevBuf def_acc;           // per-trial FP64 sums of deferred occurrence losses
   DevBuf elt_stage, elt_recs_stage, elt_tab_stage, elt_flags;  // ELT load staging (grow-only)
@@ -428,6 +428,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
       (rc = reserve(c, c->mask, sizeof(uint32_t) * (n_recs + 1))) ||
       (rc = reserve(c, c->slot_cnt, sizeof(uint32_t) * (n_recs + 2))) ||
       (rc = reserve(c, c->pairs, sizeof(ara::Pair) * (n_recs + 1))) ||
+      (rc = reserve(c, c->pairs_hot, sizeof(ara::PairHot) * (n_recs + 1))) ||
       (rc = reserve(c, c->scan_tmp, sizeof(uint32_t) * (tmp_words + 8))))
     return rc;
   ara::LayerIndex ix{};
@@ -438,6 +439,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   ix.mask = static_cast<uint32_t*>(c->mask.ptr);
   ix.slot_cnt = static_cast<uint32_t*>(c->slot_cnt.ptr);
   ix.pairs = static_cast<ara::Pair*>(c->pairs.ptr);
+  ix.hot = static_cast<ara::PairHot*>(c->pairs_hot.ptr);
   ix.scan_tmp = static_cast<uint32_t*>(c->scan_tmp.ptr);
   ix.n_words = n_words;
   ix.n_recs = n_recs;
@@ -503,6 +505,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   p.ev_buf = g.ev_buf;
   p.tile_cnt = g.tile_cnt;
   p.pairs = ix.pairs;
+  p.hot = ix.hot;
   p.n_elts = L->n_elts;
   p.occ_r = static_cast<float>(L->occ_retention);
   p.occ_l = static_cast<float>(L->occ_limit);
@@ -525,7 +528,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   const int64_t warps_per_sm = ara::kGatherThreads / 32;
   const int grid = static_cast<int>(std::min<int64_t>(c->num_sms, (n_tiles + warps_per_sm - 1) / warps_per_sm));
   const int64_t loss_warps = ara::kLossThreads / 32;
-  const int loss_grid = static_cast<int>(std::min<int64_t>(c->num_sms * (1024 / ara::kLossThreads),
+  const int loss_grid = static_cast<int>(std::min<int64_t>(c->num_sms * ara::kLossBlocksPerSm,
                                                            (n_tiles + loss_warps - 1) / loss_warps));
   cudaEvent_t la, lb;
   if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "ara_run_layer: cannot create timing events");
@@ -787,7 +790,7 @@ void ara_destroy(ara_ctx* c) {
   DevBuf* bufs[] = {&c->elt_stage,  &c->elt_recs_stage, &c->elt_tab_stage, &c->elt_tabf_stage, &c->elt_work,
                     &c->elt_flags,  &c->ev_buf,         &c->tile_cnt,      &c->def_acc,        &c->yet_off,
                     &c->yet_ids,    &c->bits,           &c->word_cnt,      &c->word_pairs,     &c->rankdir,
-                    &c->mask,       &c->slot_cnt,       &c->pairs,         &c->scan_tmp,       &c->flags,
+                    &c->mask,       &c->slot_cnt,       &c->pairs,         &c->pairs_hot,     &c->scan_tmp,       &c->flags,
                     &c->counters,   &c->ylt_tmp,        &c->diag_tmp,      &c->sel,            &c->in_tmp,
                     &c->out_tmp};
   for (DevBuf* b : bufs) release(c, *b);

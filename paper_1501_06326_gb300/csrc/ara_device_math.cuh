@@ -56,6 +56,15 @@ struct __align__(16) Pair {
 };
 static_assert(sizeof(Pair) == 32, "Pair must be one 32-byte sector");
 
+// What the table path reads of a pair (the layer keeps it beside the full
+// Pair, which only the Halley iteration needs).
+struct __align__(16) PairHot {
+  float max_l;    // exposure (maximum loss)
+  float mu;       // mean loss
+  uint32_t meta;  // as Pair::meta
+  uint32_t node;  // first node of the record's quantile table (coarse or fine table of its ELT)
+};
+
 constexpr uint32_t kMaxEltRecords = 1u << 23;  // record index field of meta
 
 __host__ __device__ inline uint32_t pair_pos(uint32_t meta) { return meta & 31u; }

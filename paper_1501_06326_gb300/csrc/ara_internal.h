@@ -72,6 +72,7 @@ struct LayerIndex {
   uint32_t* mask;        // [n_recs] per slot: bitmask of layer positions
   uint32_t* slot_cnt;    // [n_recs + 1] scratch -> slot_start
   Pair* pairs;           // [n_recs]
+  PairHot* hot;          // [n_recs] the table-path part of each pair
   uint32_t* scan_tmp;
   int64_t n_words;
   int64_t n_recs;
@@ -88,7 +89,8 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
 //             losses, trial sums and year losses.
 // Event record: x = (trial in tile << 27) | ((pairs - 1) << 22) | k, y = first pair.
 constexpr int kGatherThreads = 1024;  // 32 warps per CTA, one CTA per SM
-constexpr int kLossThreads = 512;
+constexpr int kLossThreads = 256;
+constexpr int kLossBlocksPerSm = 3;  // 24 warps per SM at up to 85 registers: no spills in the loss loop
 constexpr int kWarpTrials = 8;        // trials per tile (< 32)
 constexpr int kMaxTrialEvents = 1 << 22;
 
@@ -113,6 +115,7 @@ struct LossParams {
   const uint2* ev_buf;
   const uint32_t* tile_cnt;
   const Pair* pairs;
+  const PairHot* hot;
   int32_t n_elts;
   int32_t elt_id[32];
   const float4* tab[32];   // coarse quantile tables of the layer's ELTs (by position)

@@ -628,7 +628,7 @@ __global__ void k_slot_counts(const uint32_t* mask, int64_t n, uint32_t* cnt) {
 }
 
 __global__ void k_fill_pairs(LayerEltRefs r, const uint32_t* bits, const uint32_t* slot_base, const uint32_t* mask,
-                             const uint32_t* slot_start, Pair* pairs) {
+                             const uint32_t* slot_start, Pair* pairs, PairHot* hot) {
   const int64_t n = r.rec_begin[r.n_elts];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
@@ -639,7 +639,14 @@ __global__ void k_fill_pairs(LayerEltRefs r, const uint32_t* bits, const uint32_
     const uint32_t within = __popc(mask[slot] & ((1u << p) - 1u));
     Pair q = r.recs[p][j];
     q.meta = (q.meta & ~31u) | static_cast<uint32_t>(p);
-    pairs[slot_start[slot] + within] = q;
+    const uint32_t at = slot_start[slot] + within;
+    pairs[at] = q;
+    PairHot hq;
+    hq.max_l = q.max_l;
+    hq.mu = q.mu;
+    hq.meta = q.meta;
+    hq.node = pair_rec(q.meta) * (pair_fine(q.meta) ? kTabFineStride : kTabNodes);
+    hot[at] = hq;
   }
 }
 
@@ -682,7 +689,7 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if ((err = scan_exclusive_u32(ix.slot_cnt, ix.slot_cnt, n_recs, ix.scan_tmp, s, &launched)) != cudaSuccess)
       return err;
-    k_fill_pairs<<<grid_for(n_recs, 256), 256, 0, s>>>(refs, ix.bits, ix.word_cnt, ix.mask, ix.slot_cnt, ix.pairs);
+    k_fill_pairs<<<grid_for(n_recs, 256), 256, 0, s>>>(refs, ix.bits, ix.word_cnt, ix.mask, ix.slot_cnt, ix.pairs, ix.hot);
     launched += 3;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   } else {
@@ -906,25 +913,22 @@ cudaError_t launch_gather(const GatherParams& p, int grid, size_t smem, cudaStre
 
 namespace {
 
-constexpr int kWin = 128;  // events (and pairs) per window: four per lane
+constexpr int kQueue = 64;         // multi-ELT events queued per warp
 constexpr uint32_t kDefCur = 1u;   // deferred event of the open tile
 constexpr uint32_t kDefLast = 2u;  // last deferred event of its trial
 
 struct LossWarp {
-  uint2 rec[kWin];        // window records (general path)
-  uint32_t pre[kWin];     // first pair of each event, window-relative
-  uint8_t p2e[kWin];      // pair -> event
-  uint8_t pslow[kWin];    // pair needs the Halley iteration
-  float lp[kWin];         // pair losses
-  uint32_t d_key[32];     // deferred events, in event order: record
-  uint32_t d_ps[32];      //   first pair
-  int64_t d_o[32];        //   trial (output index)
-  uint32_t d_fl[32];      //   kDefCur | kDefLast
-  float d_O[32];          //   occurrence loss, once resolved
-  double S[kWarpTrials];  // sums of the table-path occurrence losses of the tile's trials
-  double Sd[kWarpTrials]; // sums of the deferred occurrence losses resolved while the tile is open
+  float2 acc[kWarpTrials][32];  // per trial and lane: double-float sum of the lane's occurrence losses
+  uint2 mq[kQueue];             // queued multi-ELT events (event records)
+  uint32_t d_key[32];           // deferred events: record
+  uint32_t d_ps[32];            //   first pair
+  int64_t d_o[32];              //   trial (output index)
+  uint32_t d_fl[32];            //   kDefCur | kDefLast
+  float d_O[32];                //   occurrence loss, once resolved
+  double Sd[kWarpTrials];       // sums of the deferred occurrence losses resolved while the tile is open
   unsigned long long hits[kWarpTrials];
   unsigned long long hash[kWarpTrials];
+  unsigned long long n_nc, n_slow;  // non-converged Halley pairs, Halley events
 };
 
 // (hi, lo) + (hi2, lo2) in double-float arithmetic (TwoSum, then renormalise).
@@ -978,10 +982,11 @@ __device__ __noinline__ float pair_slow(const LossParams& p, const Pair& pr, int
 // is flushed does not change any result: entries of the open tile go to its
 // shared sums, older ones to def_acc, and the last one of a trial finishes
 // its year loss.
-__device__ __noinline__ void resolve_deferred(const LossParams& p, LossWarp& ws, int nd, unsigned long long* nc,
-                                              unsigned long long* n_slow) {
+__device__ __noinline__ void resolve_deferred(const LossParams& p, LossWarp& ws, int nd) {
   const uint32_t lane = lane_id();
   float O = 0.0f;
+  unsigned long long nc_l = 0;
+  unsigned long long* nc = &nc_l;
   if (lane < static_cast<uint32_t>(nd)) {
     const uint32_t key = ws.d_key[lane];
     const uint32_t k = key & kRecKMask;
@@ -990,11 +995,13 @@ __device__ __noinline__ void resolve_deferred(const LossParams& p, LossWarp& ws,
     float G = 0.0f;
     for (uint32_t j = 0; j < cnt; ++j) G += pair_slow(p, p.pairs[ws.d_ps[lane] + j], t, k, nc);
     O = clamp_terms_f(G, p.occ_r, p.occ_l);
-    ++*n_slow;
   }
+  const uint32_t nc_w = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(nc_l));
   ws.d_O[lane] = O;
   __syncwarp();
   if (lane == 0) {
+    ws.n_nc += nc_w;
+    ws.n_slow += static_cast<unsigned long long>(nd);
     double acc = 0.0;
     bool open = false;  // acc holds def_acc of the current run's trial
     for (int i = 0; i < nd; ++i) {
@@ -1024,19 +1031,174 @@ __device__ __noinline__ void resolve_deferred(const LossParams& p, LossWarp& ws,
 
 }  // namespace
 
-// k_losses: windows of up to kWin events whose pairs number at most kWin.
-// Event e of a window sits at (round e / 32, lane e % 32), pair q likewise, so
-// every load of records is coalesced and the four rounds of a lane are
-// independent work for the scheduler.
-__global__ void __launch_bounds__(kLossThreads, 1024 / kLossThreads) k_losses(const LossParams p) {
+namespace {
+
+// Appends this lane's event to the deferred list when `defer` (warp-wide call;
+// events are listed in lane order), resolving the list first when it is full.
+// Returns the new length of the list.
+__device__ __forceinline__ int defer_events(const LossParams& p, LossWarp& ws, int nd, bool defer, uint2 r,
+                                            int64_t o) {
+  const uint32_t dmask = __ballot_sync(0xffffffffu, defer);
+  if (dmask == 0) return nd;
+  if (nd + __popc(dmask) > 32) {
+    resolve_deferred(p, ws, nd);
+    nd = 0;
+  }
+  if (defer) {
+    const int at = nd + __popc(dmask & ((1u << lane_id()) - 1u));
+    ws.d_key[at] = r.x;
+    ws.d_ps[at] = r.y;
+    ws.d_o[at] = o;
+    ws.d_fl[at] = kDefCur;
+  }
+  __syncwarp();
+  return nd + __popc(dmask);
+}
+
+// Adds an occurrence loss to the lane's double-float sum of trial tl.
+__device__ __forceinline__ void acc_add(LossWarp& ws, uint32_t tl, float O) {
+  float2 a = ws.acc[tl][lane_id()];
+  df_add(a.x, a.y, O, 0.0f);
+  ws.acc[tl][lane_id()] = a;
+}
+
+// The layer's ELTs by position, in shared memory (one array per field, so that
+// lanes reading different ELTs hit different banks).
+struct EltShared {
+  const float4* tab[32];
+  const float4* tabf[32];
+  uint32_t elt_id[32];
+  float ret[32], lim[32], share[32];
+};
+
+// Loss after ELT terms of one pair from its hot record, for the table path;
+// returns false when the pair needs the Halley iteration.
+__device__ __forceinline__ bool pair_fast_hot(const LossParams& p, const EltShared& es, const PairHot& h,
+                                              int64_t trial, uint32_t k, float* out) {
+  const uint32_t kind = pair_kind(h.meta);
+  const uint32_t pos = pair_pos(h.meta);
+  float loss = h.mu;
+  if (kind == kKindZero) {
+    loss = 0.0f;
+  } else if (!p.primary_only && kind == kKindBeta) {
+    if (p.newton_only || !pair_tab_exact(h.meta)) return false;
+    const float z = philox_uniform_rk(p.rk, trial, k, es.elt_id[pos]);
+    const bool fine = pair_fine(h.meta);
+    const float4* tb = (fine ? es.tabf[pos] : es.tab[pos]) + h.node;
+    loss = h.max_l * tab_quantile(tb, z, fine);
+  }
+  *out = es.share[pos] * clamp_terms_f(loss, es.ret[pos], es.lim[pos]);
+  return true;
+}
+
+// The queued multi-ELT events, in windows of at most 32 pairs (one per lane):
+// losses of the pairs, a segmented sum per event (pairs in layer order), the
+// occurrence terms at each event's last lane.  Returns (deferred list length,
+// pairs processed).
+__device__ __forceinline__ int2 process_multi(const LossParams& p, const EltShared& es, LossWarp& ws, int nd, int nq,
+                                              int64_t ta, bool diag) {
+  const uint32_t q = lane_id();
+  const uint32_t upto = 0xffffffffu >> (31u - q);  // lanes 0..q
+  int n_pairs = 0;
+#pragma unroll 1
+  for (int i0 = 0; i0 < nq;) {
+    const int ie = i0 + static_cast<int>(q);
+    const uint2 r = (ie < nq) ? ws.mq[ie] : make_uint2(0u, 0u);
+    const uint32_t cnt = (ie < nq) ? ((r.x >> kRecCntShift) & 31u) + 1u : 0u;
+    const uint32_t incl = warp_inclusive_scan(cnt);
+    const uint32_t pre = incl - cnt;
+    const bool take = cnt != 0 && incl <= 32u;
+    const int n_take = __popc(__ballot_sync(0xffffffffu, take));
+    const uint32_t np = __shfl_sync(0xffffffffu, incl, n_take - 1);
+    const uint32_t starts = __reduce_or_sync(0xffffffffu, take ? (1u << pre) : 0u);
+    // lane q's event: the last start at or below q
+    const uint32_t ev = static_cast<uint32_t>(__popc(starts & upto)) - 1u;
+    const uint32_t ex = __shfl_sync(0xffffffffu, r.x, ev);
+    const uint32_t ey = __shfl_sync(0xffffffffu, r.y, ev);
+    const uint32_t epre = __shfl_sync(0xffffffffu, pre, ev);
+    const uint32_t ecnt = __shfl_sync(0xffffffffu, cnt, ev);
+    const uint32_t etl = ex >> kRecTrialShift, ek = ex & kRecKMask;
+    float L = 0.0f;
+    bool slow = false;
+    if (q < np) {
+      const PairHot h = p.hot[ey + (q - epre)];
+      slow = !pair_fast_hot(p, es, h, ta + etl, ek, &L);
+      if (diag) {
+        const uint32_t elt = es.elt_id[pair_pos(h.meta)];
+        atomicAdd(&ws.hits[etl], 1ull);
+        atomicAdd(&ws.hash[etl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(ek) << 32) | elt)));
+      }
+    }
+    n_pairs += static_cast<int>(np);
+    // segmented inclusive sum within each event's lanes
+#pragma unroll
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+      const float o = __shfl_up_sync(0xffffffffu, L, d);
+      if (q >= epre + d) L += o;
+    }
+    const uint32_t smask = __ballot_sync(0xffffffffu, slow);
+    const bool end = q < np && q == epre + ecnt - 1u;
+    const bool seg_slow = ((smask >> epre) & (0xffffffffu >> (31u - (q - epre)))) != 0u;
+    if (end && !seg_slow) acc_add(ws, etl, clamp_terms_f(L, p.occ_r, p.occ_l));
+    nd = defer_events(p, ws, nd, end && seg_slow, make_uint2(ex, ey), ta + etl - p.t_begin);
+    i0 += n_take;
+  }
+  __syncwarp();
+  return make_int2(nd, n_pairs);
+}
+
+// One stage of the reduce-scatter of kWarpTrials double-float values over the
+// warp: lanes with bit (4 HALF) clear keep values 0..HALF-1, the others
+// HALF..2 HALF-1, each adding its partner's copy of the values it keeps.
+template <int HALF>
+__device__ __forceinline__ void reduce_scatter_stage(float (&h)[kWarpTrials], float (&l)[kWarpTrials], uint32_t lane) {
+  constexpr int d = 4 * HALF;
+  const bool up = (lane & d) != 0;
+#pragma unroll
+  for (int j = 0; j < HALF; ++j) {
+    const float sh = up ? h[j] : h[j + HALF], sl = up ? l[j] : l[j + HALF];
+    float kh = up ? h[j + HALF] : h[j], kl = up ? l[j + HALF] : l[j];
+    df_add(kh, kl, __shfl_xor_sync(0xffffffffu, sh, d), __shfl_xor_sync(0xffffffffu, sl, d));
+    h[j] = kh;
+    l[j] = kl;
+  }
+}
+
+}  // namespace
+
+// k_losses: each warp takes tiles and reads their event records one per lane
+// (the records two rounds ahead and the hot pair records one round ahead are
+// in flight).  An event with one (event, ELT) pair -- nearly all of them -- is
+// finished by its lane: Philox uniform, inverse Beta through the record's
+// quantile table, ELT terms, occurrence terms, and a double-float add into the
+// lane's sum for the event's trial.  Events with several pairs are queued and
+// processed in windows of 32 pairs with a segmented sum.  At the end of the
+// tile one reduce-scatter over the lanes turns the per-lane sums into the
+// trials' sums.
+__global__ void __launch_bounds__(kLossThreads, kLossBlocksPerSm) k_losses(const LossParams p) {
   __shared__ LossWarp lw[kLossThreads / 32];
+  __shared__ EltShared es;
   const uint32_t lane = lane_id();
   LossWarp& ws = lw[threadIdx.x >> 5];
+  if (threadIdx.x < 32) {
+    const int i = static_cast<int>(threadIdx.x);
+    const bool in = i < p.n_elts;
+    es.tab[i] = in ? p.tab[i] : nullptr;
+    es.tabf[i] = in ? p.tabf[i] : nullptr;
+    es.elt_id[i] = in ? static_cast<uint32_t>(p.elt_id[i]) : 0u;
+    es.ret[i] = in ? p.t_ret[i] : 0.0f;
+    es.lim[i] = in ? p.t_lim[i] : 0.0f;
+    es.share[i] = in ? p.t_share[i] : 0.0f;
+  }
+  __syncthreads();
   const bool diag = (p.diag_hits != nullptr) || (p.diag_hash != nullptr);
   const uint32_t lt_mask = (1u << lane) - 1u;
-  unsigned long long n_nc = 0, n_slow = 0;
-  uint32_t n_pairs = 0;
   int nd = 0;  // deferred events listed; the list outlives tiles so that resolving keeps the lanes busy
+  uint32_t n_pairs = 0;
+  if (lane == 0) {
+    ws.n_nc = 0ull;
+    ws.n_slow = 0ull;
+  }
 
   for (;;) {
     int64_t tile = 0;
@@ -1048,188 +1210,114 @@ __global__ void __launch_bounds__(kLossThreads, 1024 / kLossThreads) k_losses(co
     const int ntr = static_cast<int>(tb - ta);
     const uint2* recs = p.ev_buf + (__ldg(&p.off[ta]) - p.e0);
     const uint32_t n = __ldg(&p.tile_cnt[tile]);
+#pragma unroll
+    for (int t = 0; t < kWarpTrials; ++t) ws.acc[t][lane] = make_float2(0.0f, 0.0f);
     if (lane < static_cast<uint32_t>(ntr)) {
-      ws.S[lane] = 0.0;
       ws.Sd[lane] = 0.0;
       ws.hits[lane] = 0ull;
       ws.hash[lane] = 0ull;
     }
     __syncwarp();
-    for (uint32_t base = 0; base < n;) {
-      // ---- window: records, pair prefix, events taken (at most kWin pairs)
-      uint2 rec[4];
-      uint32_t cnt[4], pre[4];
-      uint32_t carry = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t e = base + 32 * j + lane;
-        rec[j] = (e < n) ? __ldcs(recs + e) : make_uint2(0u, 0u);
-        cnt[j] = (e < n) ? ((rec[j].x >> kRecCntShift) & 31u) + 1u : 0u;
-        const uint32_t incl = warp_inclusive_scan(cnt[j]);
-        pre[j] = carry + incl - cnt[j];
-        carry += __shfl_sync(0xffffffffu, incl, 31);
-      }
-      uint32_t n_take = 0, np_l = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool tk = cnt[j] != 0 && pre[j] + cnt[j] <= static_cast<uint32_t>(kWin);
-        n_take += __popc(__ballot_sync(0xffffffffu, tk));
-        if (tk) np_l = pre[j] + cnt[j];
-      }
-      const uint32_t np = __reduce_max_sync(0xffffffffu, np_l);
-      const bool all_single = (np == n_take);
-      if (!all_single) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint32_t e = 32 * j + lane;
-          ws.rec[e] = rec[j];
-          ws.pre[e] = pre[j];
-          if (e < n_take)
-            for (uint32_t i = 0; i < cnt[j]; ++i) ws.p2e[pre[j] + i] = static_cast<uint8_t>(e);
-        }
-        __syncwarp();
-      }
-      // ---- pairs: Philox, inverse Beta through the table, ELT terms
-      float lv[4];
-      bool pslow[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t q = 32 * j + lane;
-        lv[j] = 0.0f;
-        pslow[j] = false;
-        if (q < np) {
-          uint2 r;
-          uint32_t qoff;
-          if (all_single) {
-            r = rec[j];
-            qoff = 0;
-          } else {
-            const uint32_t e = ws.p2e[q];
-            r = ws.rec[e];
-            qoff = q - ws.pre[e];
-          }
-          const uint32_t etl = r.x >> kRecTrialShift, ek = r.x & kRecKMask;
-          const Pair pr = p.pairs[r.y + qoff];
-          pslow[j] = !pair_fast(p, pr, ta + etl, ek, &lv[j]);
+    int nq = 0;
+    // pipeline: r1 = records of the next round, r0/h0 = this round's record and hot pair
+    uint2 r0 = (lane < n) ? __ldcs(recs + lane) : make_uint2(0u, 0u);
+    uint2 r1 = (32 + lane < n) ? __ldcs(recs + 32 + lane) : make_uint2(0u, 0u);
+    PairHot h0{0.0f, 0.0f, kKindZero << 5, 0u};
+    if (lane < n && ((r0.x >> kRecCntShift) & 31u) == 0u) h0 = p.hot[r0.y];
+    for (uint32_t base = 0;;) {
+#pragma unroll 1
+      for (; base < n && nq <= kQueue - 32; base += 32) {
+        const uint2 r = r0;
+        const PairHot h = h0;
+        const bool valid = base + lane < n;
+        r0 = r1;
+        if (base + 64 + lane < n) r1 = __ldcs(recs + base + 64 + lane);
+        if (base + 32 + lane < n && ((r0.x >> kRecCntShift) & 31u) == 0u) h0 = p.hot[r0.y];
+        const uint32_t cnt = ((r.x >> kRecCntShift) & 31u) + 1u;
+        const uint32_t tl = r.x >> kRecTrialShift, k = r.x & kRecKMask;
+        const bool single = valid && cnt == 1u;
+        bool slow = false;
+        if (single) {
+          float L;
+          slow = !pair_fast_hot(p, es, h, ta + tl, k, &L);
+          if (!slow) acc_add(ws, tl, clamp_terms_f(L, p.occ_r, p.occ_l));
           if (diag) {
-            const uint32_t elt = static_cast<uint32_t>(p.elt_id[pair_pos(pr.meta)]);
-            atomicAdd(&ws.hits[etl], 1ull);
-            atomicAdd(&ws.hash[etl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(ek) << 32) | elt)));
+            const uint32_t elt = es.elt_id[pair_pos(h.meta)];
+            atomicAdd(&ws.hits[tl], 1ull);
+            atomicAdd(&ws.hash[tl], static_cast<unsigned long long>(fmix64((static_cast<uint64_t>(k) << 32) | elt)));
           }
-          ++n_pairs;
+        }
+        n_pairs += __popc(__ballot_sync(0xffffffffu, single));
+        nd = defer_events(p, ws, nd, slow, r, ta + tl - p.t_begin);
+        const uint32_t mmask = __ballot_sync(0xffffffffu, valid && cnt > 1u);
+        if (mmask) {
+          if (valid && cnt > 1u) ws.mq[nq + __popc(mmask & lt_mask)] = r;
+          nq += __popc(mmask);
         }
       }
-      // ---- events: sum of their pairs in layer order, occurrence terms
-      float O[4];
-      bool defer[4];
-      if (all_single) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          defer[j] = pslow[j];
-          O[j] = (32 * j + lane < n_take && !pslow[j]) ? clamp_terms_f(lv[j], p.occ_r, p.occ_l) : 0.0f;
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint32_t q = 32 * j + lane;
-          ws.lp[q] = lv[j];
-          ws.pslow[q] = pslow[j] ? 1 : 0;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint32_t e = 32 * j + lane;
-          float G = 0.0f;
-          bool sl = false;
-          if (e < n_take) {
-            for (uint32_t i = 0; i < cnt[j]; ++i) {
-              G += ws.lp[pre[j] + i];
-              sl |= ws.pslow[pre[j] + i] != 0;
-            }
-          }
-          defer[j] = sl;
-          O[j] = (e < n_take && !sl) ? clamp_terms_f(G, p.occ_r, p.occ_l) : 0.0f;
-        }
+      __syncwarp();
+      if (nq > 0) {
+        const int2 rv = process_multi(p, es, ws, nd, nq, ta, diag);
+        nd = rv.x;
+        n_pairs += static_cast<uint32_t>(rv.y);
+        nq = 0;
       }
-      // ---- deferred events (window order)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const uint32_t dmask = __ballot_sync(0xffffffffu, defer[j]);
-        if (dmask) {
-          if (nd + __popc(dmask) > 32) {
-            resolve_deferred(p, ws, nd, &n_nc, &n_slow);
-            nd = 0;
-          }
-          if (defer[j]) {
-            const int at = nd + __popc(dmask & lt_mask);
-            ws.d_key[at] = rec[j].x;
-            ws.d_ps[at] = rec[j].y;
-            ws.d_o[at] = ta - p.t_begin + (rec[j].x >> kRecTrialShift);
-            ws.d_fl[at] = kDefCur;
-          }
-          nd += __popc(dmask);
-          __syncwarp();
-        }
-      }
-      // ---- trial sums: for each trial of the window, a double-float butterfly over the lanes
-      {
-        const uint32_t t_first = __shfl_sync(0xffffffffu, rec[0].x, 0) >> kRecTrialShift;
-        const uint32_t last = n_take - 1;
-        uint32_t t_last = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint32_t tj = __shfl_sync(0xffffffffu, rec[j].x, last & 31) >> kRecTrialShift;
-          if (static_cast<int>(last >> 5) == j) t_last = tj;
-        }
-        for (uint32_t t = t_first; t <= t_last; ++t) {
-          float hi = 0.0f, lo = 0.0f;
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (32 * j + lane < n_take && (rec[j].x >> kRecTrialShift) == t) df_add(hi, lo, O[j], 0.0f);
-#pragma unroll
-          for (int d = 16; d > 0; d >>= 1) {
-            const float h2 = __shfl_xor_sync(0xffffffffu, hi, d);
-            const float l2 = __shfl_xor_sync(0xffffffffu, lo, d);
-            df_add(hi, lo, h2, l2);
-          }
-          if (lane == 0) ws.S[t] += static_cast<double>(hi) + static_cast<double>(lo);
-        }
-        __syncwarp();
-      }
-      base += n_take;
+      if (base >= n) break;
     }
+    __syncwarp();
+    // ---- trials' sums: reduce-scatter of the per-lane double-float sums; lane
+    // (b4 b3 b2 b1 b0) ends up holding trial 4 b4 + 2 b3 + b2
+    float h8[kWarpTrials], l8[kWarpTrials];
+#pragma unroll
+    for (int t = 0; t < kWarpTrials; ++t) {
+      const float2 a = ws.acc[t][lane];
+      h8[t] = a.x;
+      l8[t] = a.y;
+    }
+    reduce_scatter_stage<4>(h8, l8, lane);
+    reduce_scatter_stage<2>(h8, l8, lane);
+    reduce_scatter_stage<1>(h8, l8, lane);
+#pragma unroll
+    for (int d = 2; d > 0; d >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, h8[0], d);
+      const float l2 = __shfl_xor_sync(0xffffffffu, l8[0], d);
+      df_add(h8[0], l8[0], h2, l2);
+    }
+    const uint32_t src = ((lane >> 2) & 1u) << 4 | ((lane >> 1) & 1u) << 3 | (lane & 1u) << 2;
+    const float Sh = __shfl_sync(0xffffffffu, h8[0], src);
+    const float Sl = __shfl_sync(0xffffffffu, l8[0], src);
+    const double S = static_cast<double>(Sh) + static_cast<double>(Sl);
     // ---- tile end: a trial whose deferred events are all resolved is final; one
     // with events still listed keeps its table-path sum in ylt and its partial
     // deferred sum in def_acc until the last of them is resolved
     uint32_t pend = 0;
-    if (lane < static_cast<uint32_t>(nd) && (ws.d_fl[lane] & kDefCur)) {
-      const uint32_t tl = ws.d_key[lane] >> kRecTrialShift;
-      pend = 1u << tl;
-      const bool last = (lane + 1 == static_cast<uint32_t>(nd)) || ((ws.d_key[lane + 1] >> kRecTrialShift) != tl);
-      ws.d_fl[lane] = last ? kDefLast : 0u;
+    {
+      const bool cur = lane < static_cast<uint32_t>(nd) && (ws.d_fl[lane] & kDefCur);
+      const uint32_t tl = cur ? (ws.d_key[lane] >> kRecTrialShift) : 0xFFu + lane;
+      const uint32_t same = __match_any_sync(0xffffffffu, tl);
+      if (cur) {
+        pend = 1u << tl;
+        ws.d_fl[lane] = (lane == 31u - __clz(same)) ? kDefLast : 0u;
+      }
     }
     pend = __reduce_or_sync(0xffffffffu, pend);
     __syncwarp();
     if (lane < static_cast<uint32_t>(ntr)) {
       const int64_t o = ta + lane - p.t_begin;
       if ((pend >> lane) & 1u) {
-        p.ylt[o] = ws.S[lane];
+        p.ylt[o] = S;
         p.def_acc[o] = ws.Sd[lane];
       } else {
-        p.ylt[o] = clamp_terms_d(ws.S[lane] + ws.Sd[lane], p.agg_r, p.agg_l);
+        p.ylt[o] = clamp_terms_d(S + ws.Sd[lane], p.agg_r, p.agg_l);
       }
       if (p.diag_hits) p.diag_hits[o] = static_cast<int64_t>(ws.hits[lane]);
       if (p.diag_hash) p.diag_hash[o] = ws.hash[lane];
     }
     __syncwarp();
   }
-  if (nd > 0) resolve_deferred(p, ws, nd, &n_nc, &n_slow);
-  n_pairs = __reduce_add_sync(0xffffffffu, n_pairs);
-  for (int d = 16; d > 0; d >>= 1) {
-    n_nc += __shfl_xor_sync(0xffffffffu, n_nc, d);
-    n_slow += __shfl_xor_sync(0xffffffffu, n_slow, d);
-  }
+  if (nd > 0) resolve_deferred(p, ws, nd);
   if (lane == 0) {
+    const unsigned long long n_nc = ws.n_nc, n_slow = ws.n_slow;
     if (n_pairs) atomicAdd(&p.counters[1], static_cast<unsigned long long>(n_pairs));
     if (n_nc) atomicAdd(&p.counters[2], n_nc);
     if (n_slow) atomicAdd(&p.counters[3], n_slow);
