@@ -291,7 +291,7 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
       (rc = reserve(c, c->elt_recs_stage, sizeof(ara::Pair) * (R + 1))) ||
       (rc = reserve(c, c->elt_tab_stage, sizeof(float4) * ara::kTabNodes * (R + 1))) ||
       (rc = reserve(c, c->elt_tabf_stage, sizeof(float4) * ara::kTabFineStride * (fine_off[n_elts] + 1))) ||
-      (rc = reserve(c, c->elt_work, sizeof(uint32_t) * (work_off[n_elts] + 1))) ||
+      (rc = reserve(c, c->elt_work, sizeof(uint32_t) * (work_off[n_elts] + R + 1))) ||
       (rc = reserve(c, c->elt_flags, sizeof(uint32_t) * 3 * n_elts)))
     return rc;
   int32_t* d_ev = static_cast<int32_t*>(c->elt_stage.ptr);
@@ -303,6 +303,7 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
   float4* d_tab = static_cast<float4*>(c->elt_tab_stage.ptr);
   float4* d_tabf = static_cast<float4*>(c->elt_tabf_stage.ptr);
   uint32_t* d_work = static_cast<uint32_t*>(c->elt_work.ptr);
+  uint32_t* d_need = d_work + work_off[n_elts];  // [R] fine-table candidates, all ELTs
   uint32_t* d_flags = static_cast<uint32_t*>(c->elt_flags.ptr);
   if (R > 0) {
     ARA_CUDA(c, cudaMemcpyAsync(d_ev, event_ids, sizeof(int32_t) * R, kind_to_device(event_ids), c->stream));
@@ -323,12 +324,19 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     uint32_t* f = d_flags + 3 * i;
     ARA_CUDA(c, ara::launch_prepare_records(d_ev + o, d_mu + o, d_sg + o, d_ex + o, n, d_recs + o, d_shapes + o, f,
                                             reinterpret_cast<int32_t*>(f + 1), c->stream));
-    int launched = 1;
+    c->launches += 1;
+  }
+  // coarse tables of every record in one launch, then each ELT's fine tables
+  ARA_CUDA(c, ara::launch_build_coarse(d_recs, d_shapes, R, d_tab, d_need, c->stream));
+  c->launches += (R > 0) ? 1 : 0;
+  for (int32_t i = 0; i < n_elts; ++i) {
+    const int64_t o = offs[i], n = offs[i + 1] - offs[i];
+    if (n == 0) continue;
+    int launched = 0;
     uint32_t* w = d_work + work_off[i];
-    ARA_CUDA(c, ara::launch_build_tables(d_recs + o, d_shapes + o, n, d_tab + o * ara::kTabNodes,
-                                         d_tabf + fine_off[i] * ara::kTabFineStride, w, c->stream, &launched));
-    if (n > 0)
-      ARA_CUDA(c, cudaMemcpyAsync(f + 2, w + n, sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream));
+    ARA_CUDA(c, ara::launch_build_fine(d_recs + o, d_shapes + o, n, d_need + o,
+                                       d_tabf + fine_off[i] * ara::kTabFineStride, w, c->stream, &launched));
+    ARA_CUDA(c, cudaMemcpyAsync(d_flags + 3 * i + 2, w + n, sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream));
     c->launches += launched;
   }
   std::vector<uint32_t> hf(3 * static_cast<size_t>(n_elts));

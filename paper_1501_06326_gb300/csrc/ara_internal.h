@@ -41,6 +41,13 @@ size_t build_tables_work_words(int64_t n);
 uint32_t fine_table_cap(int64_t n);
 cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, float4* tabf,
                                 uint32_t* work, cudaStream_t s, int* n_launch);
+// The two halves of launch_build_tables: coarse tables of n records (need[rec]
+// = 1 marks a candidate for a fine table; one launch may span several ELTs),
+// then the fine tables of one ELT (`work`: build_tables_work_words(n) words).
+cudaError_t launch_build_coarse(Pair* recs, const double2* shapes, int64_t n, float4* tab, uint32_t* need,
+                                cudaStream_t s);
+cudaError_t launch_build_fine(Pair* recs, const double2* shapes, int64_t n, const uint32_t* need, float4* tabf,
+                              uint32_t* work, cudaStream_t s, int* n_launch);
 
 // Check kernels (device functions of the hot path on given inputs).
 cudaError_t launch_debug_uniforms(uint32_t seed_lo, uint32_t seed_hi, int64_t n, const int64_t* trials,

@@ -215,19 +215,25 @@ cudaError_t launch_prepare_records(const int32_t* events, const float* mean, con
 // =============================================================== quantile tables (FP64, load time)
 namespace {
 
-// I_x(a, b) and 1 - I_x(a, b), each without cancellation (A&S 26.5.8 with symmetry).
-__device__ void beta_inc_pair_f64(double x, double a, double b, double lnB, double* I, double* Ic) {
+// I_x(a, b) and 1 - I_x(a, b), each without cancellation (A&S 26.5.8 with
+// symmetry).  *front_out (optional) receives x^a (1-x)^b / B(a, b), which is
+// x (1 - x) f(x) for the Beta density f.
+__device__ void beta_inc_pair_f64(double x, double a, double b, double lnB, double* I, double* Ic,
+                                  double* front_out = nullptr) {
   if (!(x > 0.0)) {
     *I = 0.0;
     *Ic = 1.0;
+    if (front_out) *front_out = 0.0;
     return;
   }
   if (!(x < 1.0)) {
     *I = 1.0;
     *Ic = 0.0;
+    if (front_out) *front_out = 0.0;
     return;
   }
   const double front = exp(a * log(x) + b * log1p(-x) - lnB);
+  if (front_out) *front_out = front;
   if (x < (a + 1.0) / (a + b + 2.0)) {
     const double v = front * beta_cf_f64(a, b, x) / a;
     *I = v;
@@ -268,128 +274,91 @@ __device__ double beta_root_f64(double p, double A, double B, double lnB, double
 }
 
 // Polish of an FP32 root r of I_r(A, B) = p (p <= 1/2): Newton on u = ln r in
-// FP64, where I ~ r^A near 0 makes the step almost exact; at most 3 steps (the
-// seed is good to ~1e-6, so one step reaches 1e-12).  A seed that does not
-// converge goes to the bracketed solver.
+// FP64, where I ~ r^A near 0 makes the step almost exact.  The seed is good to
+// ~1e-6, so a step |du| < 1e-5 leaves an error of order du^2 (~1e-10, below
+// the FP32 resolution of the stored node) and ends the iteration; at most 3
+// steps.  A seed that does not converge goes to the bracketed solver.
 __device__ double beta_polish_f64(double p, double A, double B, double lnB, double seed) {
   double r = seed;
   if (!(r > 0.0 && r < 1.0)) return beta_root_f64(p, A, B, lnB, -1.0);
-  double du = 1.0;
-  for (int it = 0; it < 3 && fabs(du) > 2e-10; ++it) {
-    double I, Ic;
-    beta_inc_pair_f64(r, A, B, lnB, &I, &Ic);
-    if (!(I > 0.0)) return beta_root_f64(p, A, B, lnB, seed);
-    const double lpdf = (A - 1.0) * log(r) + (B - 1.0) * log1p(-r) - lnB;
-    const double g = r * exp(lpdf) / I;  // d ln I / d ln r
-    du = -log1p((I - p) / p) / g;
+  for (int it = 0; it < 3; ++it) {
+    double I, Ic, front;
+    beta_inc_pair_f64(r, A, B, lnB, &I, &Ic, &front);
+    if (!(I > 0.0) || !(front > 0.0)) return beta_root_f64(p, A, B, lnB, seed);
+    const double g = front / ((1.0 - r) * I);  // d ln I / d ln r = r f(r) / I
+    const double du = -log1p((I - p) / p) / g;
     if (!(fabs(du) < 0.5)) return beta_root_f64(p, A, B, lnB, seed);
     const double rn = fma(r, expm1(du), r);
     if (!(rn > 0.0 && rn < 1.0)) return beta_root_f64(p, A, B, lnB, seed);
     r = rn;
+    if (fabs(du) < 1e-5) return r;
   }
-  if (fabs(du) > 1e-8) return beta_root_f64(p, A, B, lnB, r);
-  return r;
+  return beta_root_f64(p, A, B, lnB, r);
 }
 
 }  // namespace
 
-// Quantile table of one record on the grid t_j = -T1 + j h / R, j < 31 R + 1
-// (R = 1: the coarse table, R = kTabRefine: the fine one); one warp, lane l
-// holding nodes l + 32 k.  Each node: the FP64 root x_j (seeded by the FP32
-// Halley solver), w = ln x, w' and w'' (derivatives in t: w' = phi(t) / (x f(x)),
-// w'' = w' (-t - w' (a - (b-1) x/(1-x)))).  The stored float4 is
-// {x_j, w_{j+1} - w_j, h w'_j, h^2 w''_j}.  Then each segment is checked at
-// s = 1/4, 1/2, 3/4: the FP32 interpolant (as the hot path evaluates it)
-// against the FP64 CDF.  Returns (to every lane) whether the implied relative
-// error of x is within kTabTol everywhere x >= 1e-30.
-template <int R>
-__device__ bool build_record_table(const Pair& pr, double a, double b, float4* out) {
-  constexpr int kN = R * (kTabNodes - 1) + 1;
-  constexpr int kK = (kN + 31) / 32;
-  const int lane = threadIdx.x & 31;
-  const double lnB = lgamma(a) + lgamma(b) - lgamma(a + b);
-  const double h = 2.0 * kTabT1 / (kN - 1);
-  float4 node[kK];
-  double w[kK];
-#pragma unroll
-  for (int k = 0; k < kK; ++k) {
-    const int j = lane + 32 * k;
-    const double t = -kTabT1 + h * (j < kN ? j : kN - 1);
-    const double zl = normcdf(-fabs(t));  // the smaller tail probability
-    // FP32 seed, then FP64 polish on the side where the root keeps relative precision
-    BetaSolveStats st;
-    const float zf = (t <= 0.0) ? static_cast<float>(zl) : static_cast<float>(1.0 - zl);
-    const float seed = pair_quantile_newton(pr, fminf(fmaxf(zf, 5.9604645e-08f), 0.99999994f), -1.0f, &st);
-    double lny, x;
-    if (t <= 0.0) {
-      x = beta_polish_f64(zl, a, b, lnB, static_cast<double>(seed));
-      w[k] = log(x);
-      lny = log1p(-x);
-    } else {
-      const double y = beta_polish_f64(zl, b, a, lnB, 1.0 - static_cast<double>(seed));
-      x = 1.0 - y;
-      w[k] = log1p(-y);
-      lny = log(y);
-    }
-    const double lpdf = (a - 1.0) * w[k] + (b - 1.0) * lny - lnB;
-    const double lphi = -0.5 * t * t - 0.91893853320467274178;
-    const double D = exp(lphi - w[k] - lpdf);
-    const double E = D * (-t - D * (a - (b - 1.0) * exp(w[k] - lny)));
-    node[k] = make_float4(static_cast<float>(exp(w[k])), 0.0f, static_cast<float>(h * D), static_cast<float>(h * h * E));
+// One node of a record's quantile table at t: the FP64 root x (seeded by the
+// FP32 Halley solver), w = ln x, and the derivatives in t, w' = phi(t) / (x f(x))
+// and w'' = w' (-t - w' (a - (b-1) x/(1-x))).  Returns {x, 0, h w', h^2 w''}
+// (the caller fills in w_{j+1} - w_j) and w.
+__device__ float4 table_node(const Pair& pr, double a, double b, double lnB, double t, double h, double* w_out) {
+  const double zl = normcdf(-fabs(t));  // the smaller tail probability
+  // FP32 seed, then FP64 polish on the side where the root keeps relative precision
+  BetaSolveStats st;
+  const float zf = (t <= 0.0) ? static_cast<float>(zl) : static_cast<float>(1.0 - zl);
+  const float seed = pair_quantile_newton(pr, fminf(fmaxf(zf, 5.9604645e-08f), 0.99999994f), -1.0f, &st);
+  double w, lny;
+  if (t <= 0.0) {
+    const double x = beta_polish_f64(zl, a, b, lnB, static_cast<double>(seed));
+    w = log(x);
+    lny = log1p(-x);
+  } else {
+    const double y = beta_polish_f64(zl, b, a, lnB, 1.0 - static_cast<double>(seed));
+    w = log1p(-y);
+    lny = log(y);
   }
-  // w_{j+1} - w_j: node j + 1 is the next lane, or lane 0 of the next round
-#pragma unroll
-  for (int k = 0; k < kK; ++k) {
-    double wn = __shfl_down_sync(0xffffffffu, w[k], 1);
-    if (k + 1 < kK) {
-      const double w0 = __shfl_sync(0xffffffffu, w[k + 1], 0);
-      if (lane == 31) wn = w0;
-    }
-    const int j = lane + 32 * k;
-    if (j < kN - 1) node[k].y = static_cast<float>(wn - w[k]);
-    if (j < kN) out[j] = node[k];
-  }
-  // ---- accuracy check of the interpolant
-  bool ok = true;
-#pragma unroll
-  for (int k = 0; k < kK; ++k) {
-    float d1 = __shfl_down_sync(0xffffffffu, node[k].z, 1);
-    float e1 = __shfl_down_sync(0xffffffffu, node[k].w, 1);
-    if (k + 1 < kK) {
-      const float d0n = __shfl_sync(0xffffffffu, node[k + 1].z, 0);
-      const float e0n = __shfl_sync(0xffffffffu, node[k + 1].w, 0);
-      if (lane == 31) {
-        d1 = d0n;
-        e1 = e0n;
-      }
-    }
-    const int j = lane + 32 * k;
-    if (j >= kN) continue;
-    const float4 nd = node[k];
-    ok = ok && isfinite(nd.x) && isfinite(nd.y) && isfinite(nd.z) && isfinite(nd.w);
-    if (j >= kN - 1) continue;
-    const double t = -kTabT1 + h * j;
-    for (int q = 1; q <= 3; ++q) {
-      const float sf = 0.25f * q;
-      const float xq = (nd.x > 0.0f) ? nd.x * expf(tab_increment(sf, nd.y, nd.z, nd.w, d1, e1)) : 0.0f;
-      if (!(xq >= 1e-30f)) continue;  // negligible losses
-      const double tq = t + h * sf;
-      const double zq = normcdf(-fabs(tq));
-      double I, Ic;
-      const double xd = static_cast<double>(xq);
-      beta_inc_pair_f64(xd, a, b, lnB, &I, &Ic);
-      const double err_z = (tq <= 0.0) ? (I - zq) : (Ic - zq);
-      const double lpdf_q = (a - 1.0) * log(xd) + (b - 1.0) * log1p(-xd) - lnB;
-      const double rel = fabs(err_z) * exp(-(log(xd) + lpdf_q));
-      ok = ok && (rel <= kTabTol) && isfinite(rel);
-    }
-  }
-  return __all_sync(0xffffffffu, ok);
+  const double lpdf = (a - 1.0) * w + (b - 1.0) * lny - lnB;
+  const double lphi = -0.5 * t * t - 0.91893853320467274178;
+  const double D = exp(lphi - w - lpdf);
+  const double E = D * (-t - D * (a - (b - 1.0) * exp(w - lny)));
+  *w_out = w;
+  return make_float4(static_cast<float>(exp(w)), 0.0f, static_cast<float>(h * D), static_cast<float>(h * h * E));
 }
 
-// Coarse tables, one warp per record; need[rec] = 1 for a Beta record whose
-// coarse table is not exact (a candidate for a fine table).
-__global__ void k_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, uint32_t* need) {
+// Accuracy of the segment [t, t + h] of a table (node nd = {x, dw, h w', h^2 w''}
+// at t; d1, e1 the derivative terms of the next node), checked at the midpoint,
+// where the error kernel s^3 (1-s)^3 of quintic Hermite interpolation peaks:
+// the FP32 interpolant (as the hot path evaluates it) against the FP64 CDF.
+// True when the implied relative error of x there is within kTabTol (a bound
+// set by the FP32 evaluation of the interpolant, ~2e-7, more than by the
+// interpolation error, which elsewhere in the segment is below its midpoint
+// value), or x < 1e-30 (negligible losses).
+__device__ bool table_segment_ok(float4 nd, float d1, float e1, double t, double h, double a, double b, double lnB) {
+  if (!(isfinite(nd.x) && isfinite(nd.y) && isfinite(nd.z) && isfinite(nd.w))) return false;
+  const float xq = (nd.x > 0.0f) ? nd.x * expf(tab_increment(0.5f, nd.y, nd.z, nd.w, d1, e1)) : 0.0f;
+  if (!(xq >= 1e-30f)) return true;
+  const double tq = t + 0.5 * h;
+  const double zq = normcdf(-fabs(tq));
+  double I, Ic, front, rel;
+  if (xq >= 1.0f) {
+    // the FP32 ceiling: fine iff the quantile itself is within 2^-24 of 1
+    beta_inc_pair_f64(1.0 - 5.9604644775390625e-08, a, b, lnB, &I, &Ic);
+    rel = (tq > 0.0 && Ic >= zq) ? 0.0 : INFINITY;
+  } else {
+    const double xd = static_cast<double>(xq);
+    beta_inc_pair_f64(xd, a, b, lnB, &I, &Ic, &front);
+    const double err_z = (tq <= 0.0) ? (I - zq) : (Ic - zq);
+    rel = fabs(err_z) * (1.0 - xd) / front;  // |dz| / (x f(x))
+  }
+  return (rel <= kTabTol) && isfinite(rel);
+}
+
+// Coarse tables, one warp per record, lane j = node j at t_j = -T1 + j h.  The
+// stored float4 is {x_j, w_{j+1} - w_j, h w'_j, h^2 w''_j}.  need[rec] = 1 for
+// a Beta record whose coarse table is not exact (a candidate for a fine table).
+__global__ void __launch_bounds__(256, 4) k_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab,
+                                                        uint32_t* need) {
   const int lane = threadIdx.x & 31;
   const int64_t rec = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (rec >= n) return;
@@ -400,27 +369,70 @@ __global__ void k_build_tables(Pair* recs, const double2* shapes, int64_t n, flo
     if (lane == 0) need[rec] = 0u;
     return;
   }
-  const bool ok = build_record_table<1>(pr, shapes[rec].x, shapes[rec].y, out);
+  const double a = shapes[rec].x, b = shapes[rec].y;
+  const double lnB = lgamma(a) + lgamma(b) - lgamma(a + b);
+  const double h = 2.0 * kTabT1 / (kTabNodes - 1);
+  const double t = -kTabT1 + h * lane;
+  double w;
+  float4 node = table_node(pr, a, b, lnB, t, h, &w);
+  const double w_next = __shfl_down_sync(0xffffffffu, w, 1);
+  if (lane < kTabNodes - 1) node.y = static_cast<float>(w_next - w);
+  out[lane] = node;
+  const float d1 = __shfl_down_sync(0xffffffffu, node.z, 1);
+  const float e1 = __shfl_down_sync(0xffffffffu, node.w, 1);
+  const bool ok = (lane < kTabNodes - 1) ? table_segment_ok(node, d1, e1, t, h, a, b, lnB)
+                                         : (isfinite(node.x) && isfinite(node.z) && isfinite(node.w));
+  const bool all_ok = __all_sync(0xffffffffu, ok);
   if (lane == 0) {
-    if (ok) recs[rec].meta = pr.meta | (1u << 8);
-    need[rec] = ok ? 0u : 1u;
+    if (all_ok) recs[rec].meta = pr.meta | (1u << 8);
+    need[rec] = all_ok ? 0u : 1u;
   }
 }
 
-// Fine tables for the first `cap` candidates in record order (slot = exclusive
-// prefix of need): the record's meta then addresses its fine table; it is
-// table-exact if the fine table passes the check.
-__global__ void k_build_fine(Pair* recs, const double2* shapes, int64_t n, const uint32_t* slot, uint32_t cap,
-                             float4* tabf) {
-  const int lane = threadIdx.x & 31;
-  const int64_t rec = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if (rec >= n) return;
-  const uint32_t sl = slot[rec];
-  if (slot[rec + 1] == sl || sl >= cap) return;
+// Fine tables: block b builds slot b, for the b-th candidate in record order
+// (slot = exclusive prefix of need, n + 1 entries); thread j = node j at
+// t_j = -T1 + j h / kTabRefine.  The record's meta then addresses its fine
+// table; it is table-exact if the fine table passes the check.
+__global__ void __launch_bounds__(kTabFineStride) k_build_fine(Pair* recs, const double2* shapes, int64_t n,
+                                                              const uint32_t* slot, uint32_t cap, float4* tabf) {
+  __shared__ double s_w[kTabFineStride];
+  __shared__ float4 s_node[kTabFineStride];
+  __shared__ int64_t s_rec;
+  const uint32_t b_slot = blockIdx.x;
+  if (b_slot >= cap || b_slot >= slot[n]) return;
+  if (threadIdx.x == 0) {
+    // the record: the first r with slot[r + 1] > b_slot
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (slot[mid + 1] > b_slot) hi = mid; else lo = mid + 1;
+    }
+    s_rec = lo;
+  }
+  __syncthreads();
+  const int64_t rec = s_rec;
   const Pair pr = recs[rec];
-  const bool ok = build_record_table<kTabRefine>(pr, shapes[rec].x, shapes[rec].y,
-                                                 tabf + static_cast<int64_t>(sl) * kTabFineStride);
-  if (lane == 0) recs[rec].meta = (pr.meta & 0x7Fu) | (1u << 7) | (ok ? (1u << 8) : 0u) | (sl << 9);
+  const double a = shapes[rec].x, b = shapes[rec].y;
+  const double lnB = lgamma(a) + lgamma(b) - lgamma(a + b);
+  const double h = 2.0 * kTabT1 / (kTabFineNodes - 1);
+  const int j = threadIdx.x;
+  const double t = -kTabT1 + h * (j < kTabFineNodes ? j : kTabFineNodes - 1);
+  double w = 0.0;
+  float4 node = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (j < kTabFineNodes) node = table_node(pr, a, b, lnB, t, h, &w);
+  s_w[j] = w;
+  s_node[j] = node;
+  __syncthreads();
+  bool ok = true;
+  if (j < kTabFineNodes - 1) {
+    node.y = static_cast<float>(s_w[j + 1] - w);
+    ok = table_segment_ok(node, s_node[j + 1].z, s_node[j + 1].w, t, h, a, b, lnB);
+  } else if (j == kTabFineNodes - 1) {
+    ok = isfinite(node.x) && isfinite(node.z) && isfinite(node.w);
+  }
+  if (j < kTabFineNodes) tabf[static_cast<int64_t>(b_slot) * kTabFineStride + j] = node;
+  const bool all_ok = __syncthreads_and(ok) != 0;
+  if (j == 0) recs[rec].meta = (pr.meta & 0x7Fu) | (1u << 7) | (all_ok ? (1u << 8) : 0u) | (b_slot << 9);
 }
 
 size_t build_tables_work_words(int64_t n) { return static_cast<size_t>(n) + 1 + scan_tmp_words(n + 1); }
@@ -430,20 +442,35 @@ uint32_t fine_table_cap(int64_t n) {
   return static_cast<uint32_t>(cap < n ? cap : n);
 }
 
-cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, float4* tabf,
-                                uint32_t* work, cudaStream_t s, int* n_launch) {
+cudaError_t launch_build_coarse(Pair* recs, const double2* shapes, int64_t n, float4* tab, uint32_t* need,
+                                cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int64_t blocks = (n + 7) / 8;  // 8 warps (records) per block
-  const int grid = static_cast<int>(blocks < 2147483647 ? blocks : 2147483647);
-  k_build_tables<<<grid, 256, 0, s>>>(recs, shapes, n, tab, work);
-  cudaError_t err = cudaGetLastError();
+  k_build_tables<<<static_cast<int>(blocks < 2147483647 ? blocks : 2147483647), 256, 0, s>>>(recs, shapes, n, tab,
+                                                                                          need);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_fine(Pair* recs, const double2* shapes, int64_t n, const uint32_t* need, float4* tabf,
+                              uint32_t* work, cudaStream_t s, int* n_launch) {
+  if (n == 0) return cudaSuccess;
+  int launched = 0;
+  cudaError_t err = scan_exclusive_u32(need, work, n, work + n + 1, s, &launched);
   if (err != cudaSuccess) return err;
-  int launched = 1;
-  if ((err = scan_exclusive_u32(work, work, n, work + n + 1, s, &launched)) != cudaSuccess) return err;
-  k_build_fine<<<grid, 256, 0, s>>>(recs, shapes, n, work, fine_table_cap(n), tabf);
+  k_build_fine<<<static_cast<int>(fine_table_cap(n)), kTabFineStride, 0, s>>>(recs, shapes, n, work,
+                                                                             fine_table_cap(n), tabf);
   ++launched;
   if (n_launch) *n_launch += launched;
   return cudaGetLastError();
+}
+
+cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, float4* tabf,
+                                uint32_t* work, cudaStream_t s, int* n_launch) {
+  if (n == 0) return cudaSuccess;
+  cudaError_t err = launch_build_coarse(recs, shapes, n, tab, work, s);
+  if (err != cudaSuccess) return err;
+  if (n_launch) *n_launch += 1;
+  return launch_build_fine(recs, shapes, n, work, tabf, work, s, n_launch);
 }
 
 // =============================================================== check kernels
@@ -767,11 +794,59 @@ __device__ __forceinline__ void gather_load(const GatherTile& g, int32_t c0, uin
   if (i0 + 128 < g.span) v1 = __ldcs(g.ids4 + ((i0 + 128) >> 2));
 }
 
+// Positives of one step whose rank-directory words are in flight: entries
+// lane and 32 + lane of the step's staging list.
+struct GatherPending {
+  uint2 q0, q1;    // (event id, position in the step)
+  uint2 rd0, rd1;  // rank-directory words {bits, base}
+  int32_t c0;      // the step's first position
+  uint32_t npos;   // entries (at most 64; 0 = nothing pending)
+};
+
+// Resolves one staged positive per lane (warp-wide call): if the event is a
+// member, its record is appended to the tile's records in lane order.
+__device__ __forceinline__ void gather_resolve(const GatherParams& p, const GatherWarp& ws, GatherTile& g, int32_t c0,
+                                               uint2 q, uint2 rd, bool valid, uint32_t lane) {
+  uint32_t key = 0, ps = 0;
+  const uint32_t bit = 1u << (q.x & 31);
+  const bool hit = valid && (rd.x & bit) != 0u;
+  if (hit) {
+    const uint32_t below = __popc(rd.x & (bit - 1u));
+    uint32_t cnt = 1;
+    if (rd.y & 0x80000000u) {
+      const uint32_t sl = (rd.y & 0x7FFFFFFFu) + below;
+      ps = __ldg(&p.slot_start[sl]);
+      cnt = __ldg(&p.slot_start[sl + 1]) - ps;
+    } else {
+      ps = rd.y + below;
+    }
+    // trial: the last t with off[t] <= rel (off is padded with INT32_MAX)
+    const int32_t rel = c0 + static_cast<int32_t>(q.y) - g.lead;
+    int t = (ws.off[4] <= rel) ? 4 : 0;
+    t += (ws.off[t + 2] <= rel) ? 2 : 0;
+    t += (ws.off[t + 1] <= rel) ? 1 : 0;
+    key = ((cnt - 1u) << kRecCntShift) | (static_cast<uint32_t>(t) << kRecTrialShift) |
+          static_cast<uint32_t>(rel - ws.off[t]);
+  }
+  const uint32_t hm = __ballot_sync(0xffffffffu, hit);
+  if (hit) g.out[g.nout + __popc(hm & ((1u << lane) - 1u))] = make_uint2(key, ps);
+  g.nout += __popc(hm);
+}
+
+// Finishes the pending positives of the previous step.
+__device__ __forceinline__ void gather_complete(const GatherParams& p, const GatherWarp& ws, GatherTile& g,
+                                                const GatherPending& pd, uint32_t lane) {
+  if (pd.npos == 0) return;
+  gather_resolve(p, ws, g, pd.c0, pd.q0, pd.rd0, lane < pd.npos, lane);
+  if (pd.npos > 32) gather_resolve(p, ws, g, pd.c0, pd.q1, pd.rd1, 32 + lane < pd.npos, lane);
+}
+
 // One step of 256 YET positions: filter, compact the positives in YET order,
-// resolve them against the rank directory and append the hit-event records.
+// finish the previous step's positives, then either put this step's in flight
+// (up to 64) or resolve them at once.
 __device__ __forceinline__ void gather_step(const GatherParams& p, const uint32_t* __restrict__ filt, uint32_t fmask,
-                                            GatherWarp& ws, GatherTile& g, int32_t c0, uint32_t lane, int4 v0,
-                                            int4 v1) {
+                                            GatherWarp& ws, GatherTile& g, GatherPending& pd, int32_t c0,
+                                            uint32_t lane, int4 v0, int4 v1) {
   const uint32_t e[8] = {static_cast<uint32_t>(v0.x), static_cast<uint32_t>(v0.y), static_cast<uint32_t>(v0.z),
                          static_cast<uint32_t>(v0.w), static_cast<uint32_t>(v1.x), static_cast<uint32_t>(v1.y),
                          static_cast<uint32_t>(v1.z), static_cast<uint32_t>(v1.w)};
@@ -798,6 +873,9 @@ __device__ __forceinline__ void gather_step(const GatherParams& p, const uint32_
   const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
   const uint32_t nlo = tot & 0xFFFFu;
   const uint32_t npos = nlo + (tot >> 16);
+  // 3. the previous step's positives (their loads had this step's filter to land)
+  gather_complete(p, ws, g, pd, lane);
+  pd.npos = 0;
   if (npos == 0) return;
   if (m) {
     uint32_t at = (incl & 0xFFFFu) - cl;
@@ -810,38 +888,21 @@ __device__ __forceinline__ void gather_step(const GatherParams& p, const uint32_
       if (m & (1u << j)) ws.pos[at++] = make_uint2(e[j], q0 + 124 + j);
   }
   __syncwarp();
-  // 3. resolve, one positive per lane
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  for (uint32_t r0 = 0; r0 < npos; r0 += 32) {
-    uint32_t key = 0, ps = 0;
-    bool hit = false;
-    if (r0 + lane < npos) {
-      const uint2 q = ws.pos[r0 + lane];
-      const uint2 rd = __ldg(&p.rankdir[q.x >> 5]);
-      const uint32_t bit = 1u << (q.x & 31);
-      if (rd.x & bit) {
-        hit = true;
-        const uint32_t below = __popc(rd.x & (bit - 1u));
-        uint32_t cnt = 1;
-        if (rd.y & 0x80000000u) {
-          const uint32_t sl = (rd.y & 0x7FFFFFFFu) + below;
-          ps = __ldg(&p.slot_start[sl]);
-          cnt = __ldg(&p.slot_start[sl + 1]) - ps;
-        } else {
-          ps = rd.y + below;
-        }
-        // trial: the last t with off[t] <= rel (off is padded with INT32_MAX)
-        const int32_t rel = c0 + static_cast<int32_t>(q.y) - g.lead;
-        int t = (ws.off[4] <= rel) ? 4 : 0;
-        t += (ws.off[t + 2] <= rel) ? 2 : 0;
-        t += (ws.off[t + 1] <= rel) ? 1 : 0;
-        key = ((cnt - 1u) << kRecCntShift) | (static_cast<uint32_t>(t) << kRecTrialShift) |
-              static_cast<uint32_t>(rel - ws.off[t]);
-      }
+  // 4. this step's positives: in flight, or resolved now when there are many
+  if (npos <= 64) {
+    pd.npos = npos;
+    pd.c0 = c0;
+    pd.q0 = lane < npos ? ws.pos[lane] : make_uint2(0u, 0u);
+    pd.q1 = 32 + lane < npos ? ws.pos[32 + lane] : make_uint2(0u, 0u);
+    pd.rd0 = lane < npos ? __ldg(&p.rankdir[pd.q0.x >> 5]) : make_uint2(0u, 0u);
+    pd.rd1 = 32 + lane < npos ? __ldg(&p.rankdir[pd.q1.x >> 5]) : make_uint2(0u, 0u);
+  } else {
+    for (uint32_t r0 = 0; r0 < npos; r0 += 32) {
+      const bool valid = r0 + lane < npos;
+      const uint2 q = valid ? ws.pos[r0 + lane] : make_uint2(0u, 0u);
+      const uint2 rd = valid ? __ldg(&p.rankdir[q.x >> 5]) : make_uint2(0u, 0u);
+      gather_resolve(p, ws, g, c0, q, rd, valid, lane);
     }
-    const uint32_t hm = __ballot_sync(0xffffffffu, hit);
-    if (hit) g.out[g.nout + __popc(hm & lt_mask)] = make_uint2(key, ps);
-    g.nout += __popc(hm);
   }
   __syncwarp();
 }
@@ -886,18 +947,21 @@ __global__ void __launch_bounds__(kGatherThreads, 1) k_gather(const GatherParams
     // three steps of ids in registers, two of them in flight while one is filtered;
     // unrolled by three so that no register of a load in flight is ever moved
     int4 a0, a1, b0, b1, c0v, c1v;
+    GatherPending pd;
+    pd.npos = 0;
     gather_load(g, 0, lane, a0, a1);
     gather_load(g, 256, lane, b0, b1);
     for (int32_t c0 = 0; c0 < g.span; c0 += 768) {
       gather_load(g, c0 + 512, lane, c0v, c1v);
-      gather_step(p, filt, fmask, ws, g, c0, lane, a0, a1);
+      gather_step(p, filt, fmask, ws, g, pd, c0, lane, a0, a1);
       if (c0 + 256 >= g.span) break;
       gather_load(g, c0 + 768, lane, a0, a1);
-      gather_step(p, filt, fmask, ws, g, c0 + 256, lane, b0, b1);
+      gather_step(p, filt, fmask, ws, g, pd, c0 + 256, lane, b0, b1);
       if (c0 + 512 >= g.span) break;
       gather_load(g, c0 + 1024, lane, b0, b1);
-      gather_step(p, filt, fmask, ws, g, c0 + 512, lane, c0v, c1v);
+      gather_step(p, filt, fmask, ws, g, pd, c0 + 512, lane, c0v, c1v);
     }
+    gather_complete(p, ws, g, pd, lane);
     if (lane == 0) p.tile_cnt[tile] = g.nout;
     __syncwarp();
   }
