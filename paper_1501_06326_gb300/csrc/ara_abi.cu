@@ -291,7 +291,8 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
       (rc = reserve(c, c->elt_recs_stage, sizeof(ara::Pair) * (R + 1))) ||
       (rc = reserve(c, c->elt_tab_stage, sizeof(float4) * ara::kTabNodes * (R + 1))) ||
       (rc = reserve(c, c->elt_tabf_stage, sizeof(float4) * ara::kTabFineStride * (fine_off[n_elts] + 1))) ||
-      (rc = reserve(c, c->elt_work, sizeof(uint32_t) * (work_off[n_elts] + R + 1))) ||
+      (rc = reserve(c, c->elt_work, sizeof(uint32_t) * (work_off[n_elts] + R + 8) +
+                                        sizeof(ara::FineJob) * static_cast<size_t>(n_elts))) ||
       (rc = reserve(c, c->elt_flags, sizeof(uint32_t) * 3 * n_elts)))
     return rc;
   int32_t* d_ev = static_cast<int32_t*>(c->elt_stage.ptr);
@@ -329,15 +330,26 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
   // coarse tables of every record in one launch, then each ELT's fine tables
   ARA_CUDA(c, ara::launch_build_coarse(d_recs, d_shapes, R, d_tab, d_need, c->stream));
   c->launches += (R > 0) ? 1 : 0;
+  std::vector<ara::FineJob> jobs;
   for (int32_t i = 0; i < n_elts; ++i) {
     const int64_t o = offs[i], n = offs[i + 1] - offs[i];
     if (n == 0) continue;
     int launched = 0;
     uint32_t* w = d_work + work_off[i];
-    ARA_CUDA(c, ara::launch_build_fine(d_recs + o, d_shapes + o, n, d_need + o,
-                                       d_tabf + fine_off[i] * ara::kTabFineStride, w, c->stream, &launched));
+    ARA_CUDA(c, ara::scan_exclusive_u32(d_need + o, w, n, w + n + 1, c->stream, &launched));
     ARA_CUDA(c, cudaMemcpyAsync(d_flags + 3 * i + 2, w + n, sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream));
     c->launches += launched;
+    jobs.push_back(ara::FineJob{o, n, w, fine_off[i], ara::fine_table_cap(n), 0});
+  }
+  if (!jobs.empty()) {
+    // fine tables of every ELT in one launch (the job list is staged after the need flags)
+    ara::FineJob* d_jobs = reinterpret_cast<ara::FineJob*>(
+        (reinterpret_cast<uintptr_t>(d_need + R) + 15) & ~uintptr_t(15));
+    ARA_CUDA(c, cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(ara::FineJob) * jobs.size(), cudaMemcpyHostToDevice,
+                                c->stream));
+    ARA_CUDA(c, ara::launch_build_fine_jobs(d_recs, d_shapes, d_jobs, static_cast<int>(jobs.size()),
+                                            fine_off[n_elts], d_tabf, c->stream));
+    c->launches += 1;
   }
   std::vector<uint32_t> hf(3 * static_cast<size_t>(n_elts));
   ARA_CUDA(c, cudaMemcpyAsync(hf.data(), d_flags, sizeof(uint32_t) * hf.size(), cudaMemcpyDeviceToHost, c->stream));

@@ -48,6 +48,18 @@ cudaError_t launch_build_coarse(Pair* recs, const double2* shapes, int64_t n, fl
                                 cudaStream_t s);
 cudaError_t launch_build_fine(Pair* recs, const double2* shapes, int64_t n, const uint32_t* need, float4* tabf,
                               uint32_t* work, cudaStream_t s, int* n_launch);
+// Fine tables of several ELTs in one launch: job i covers records
+// [rec_begin, rec_begin + n) whose candidates were scanned into `slot` (n + 1
+// words), and owns fine slots [slot_begin, slot_begin + cap) of `tabf`.  `jobs`
+// is a device array, ordered by slot_begin.
+struct FineJob {
+  int64_t rec_begin, n;
+  const uint32_t* slot;
+  int64_t slot_begin;
+  uint32_t cap, pad;
+};
+cudaError_t launch_build_fine_jobs(Pair* recs, const double2* shapes, const FineJob* jobs, int n_jobs,
+                                   int64_t total_slots, float4* tabf, cudaStream_t s);
 
 // Check kernels (device functions of the hot path on given inputs).
 cudaError_t launch_debug_uniforms(uint32_t seed_lo, uint32_t seed_hi, int64_t n, const int64_t* trials,

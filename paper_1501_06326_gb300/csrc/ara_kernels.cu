@@ -389,28 +389,43 @@ __global__ void __launch_bounds__(256, 4) k_build_tables(Pair* recs, const doubl
   }
 }
 
-// Fine tables: block b builds slot b, for the b-th candidate in record order
-// (slot = exclusive prefix of need, n + 1 entries); thread j = node j at
+// Fine tables: global block b is slot b - slot_begin of the job (ELT) whose
+// slot range holds b, for that job's (b - slot_begin)-th candidate in record
+// order (slot = exclusive prefix of its need flags); thread j = node j at
 // t_j = -T1 + j h / kTabRefine.  The record's meta then addresses its fine
-// table; it is table-exact if the fine table passes the check.
-__global__ void __launch_bounds__(kTabFineStride) k_build_fine(Pair* recs, const double2* shapes, int64_t n,
-                                                              const uint32_t* slot, uint32_t cap, float4* tabf) {
+// table (by the ELT-local slot); it is table-exact if the fine table passes
+// the check.
+__global__ void __launch_bounds__(kTabFineStride) k_build_fine(Pair* recs, const double2* shapes,
+                                                              const FineJob* jobs, int n_jobs, float4* tabf) {
   __shared__ double s_w[kTabFineStride];
   __shared__ float4 s_node[kTabFineStride];
   __shared__ int64_t s_rec;
-  const uint32_t b_slot = blockIdx.x;
-  if (b_slot >= cap || b_slot >= slot[n]) return;
+  __shared__ uint32_t s_ls;
+  const int64_t gb = blockIdx.x;
   if (threadIdx.x == 0) {
-    // the record: the first r with slot[r + 1] > b_slot
-    int64_t lo = 0, hi = n - 1;
+    int lo = 0, hi = n_jobs - 1;  // the last job with slot_begin <= gb
     while (lo < hi) {
-      const int64_t mid = (lo + hi) >> 1;
-      if (slot[mid + 1] > b_slot) hi = mid; else lo = mid + 1;
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].slot_begin <= gb) lo = mid; else hi = mid - 1;
     }
-    s_rec = lo;
+    const FineJob jb = jobs[lo];
+    const uint32_t ls = static_cast<uint32_t>(gb - jb.slot_begin);
+    int64_t rec = -1;
+    if (jb.n > 0 && ls < jb.cap && ls < jb.slot[jb.n]) {
+      int64_t l = 0, h = jb.n - 1;  // the first r with slot[r + 1] > ls
+      while (l < h) {
+        const int64_t mid = (l + h) >> 1;
+        if (jb.slot[mid + 1] > ls) h = mid; else l = mid + 1;
+      }
+      rec = jb.rec_begin + l;
+    }
+    s_rec = rec;
+    s_ls = ls;
   }
   __syncthreads();
   const int64_t rec = s_rec;
+  if (rec < 0) return;
+  const uint32_t ls = s_ls;
   const Pair pr = recs[rec];
   const double a = shapes[rec].x, b = shapes[rec].y;
   const double lnB = lgamma(a) + lgamma(b) - lgamma(a + b);
@@ -430,12 +445,15 @@ __global__ void __launch_bounds__(kTabFineStride) k_build_fine(Pair* recs, const
   } else if (j == kTabFineNodes - 1) {
     ok = isfinite(node.x) && isfinite(node.z) && isfinite(node.w);
   }
-  if (j < kTabFineNodes) tabf[static_cast<int64_t>(b_slot) * kTabFineStride + j] = node;
+  if (j < kTabFineNodes) tabf[gb * kTabFineStride + j] = node;
   const bool all_ok = __syncthreads_and(ok) != 0;
-  if (j == 0) recs[rec].meta = (pr.meta & 0x7Fu) | (1u << 7) | (all_ok ? (1u << 8) : 0u) | (b_slot << 9);
+  if (j == 0) recs[rec].meta = (pr.meta & 0x7Fu) | (1u << 7) | (all_ok ? (1u << 8) : 0u) | (ls << 9);
 }
 
-size_t build_tables_work_words(int64_t n) { return static_cast<size_t>(n) + 1 + scan_tmp_words(n + 1); }
+size_t build_tables_work_words(int64_t n) {
+  // need/slot (n + 1), scan scratch, then room for one 16-byte aligned FineJob
+  return static_cast<size_t>(n) + 1 + scan_tmp_words(n + 1) + (sizeof(FineJob) + 16) / sizeof(uint32_t);
+}
 
 uint32_t fine_table_cap(int64_t n) {
   const int64_t cap = n / 16 + 16;
@@ -451,17 +469,29 @@ cudaError_t launch_build_coarse(Pair* recs, const double2* shapes, int64_t n, fl
   return cudaGetLastError();
 }
 
+cudaError_t launch_build_fine_jobs(Pair* recs, const double2* shapes, const FineJob* jobs, int n_jobs,
+                                   int64_t total_slots, float4* tabf, cudaStream_t s) {
+  if (n_jobs == 0 || total_slots == 0) return cudaSuccess;
+  k_build_fine<<<static_cast<int>(total_slots), kTabFineStride, 0, s>>>(recs, shapes, jobs, n_jobs, tabf);
+  return cudaGetLastError();
+}
+
+// One ELT: its scan, then its fine tables (a one-job launch; the job record
+// sits after the scan's scratch in `work`).
 cudaError_t launch_build_fine(Pair* recs, const double2* shapes, int64_t n, const uint32_t* need, float4* tabf,
                               uint32_t* work, cudaStream_t s, int* n_launch) {
   if (n == 0) return cudaSuccess;
   int launched = 0;
   cudaError_t err = scan_exclusive_u32(need, work, n, work + n + 1, s, &launched);
   if (err != cudaSuccess) return err;
-  k_build_fine<<<static_cast<int>(fine_table_cap(n)), kTabFineStride, 0, s>>>(recs, shapes, n, work,
-                                                                             fine_table_cap(n), tabf);
-  ++launched;
-  if (n_launch) *n_launch += launched;
-  return cudaGetLastError();
+  FineJob jb{0, n, work, 0, fine_table_cap(n), 0};
+  FineJob* d_job = reinterpret_cast<FineJob*>(
+      (reinterpret_cast<uintptr_t>(work + n + 1 + scan_tmp_words(n + 1)) + 15) & ~uintptr_t(15));
+  if ((err = cudaMemcpyAsync(d_job, &jb, sizeof(FineJob), cudaMemcpyHostToDevice, s)) != cudaSuccess) return err;
+  if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;  // jb lives on this stack frame
+  if ((err = launch_build_fine_jobs(recs, shapes, d_job, 1, jb.cap, tabf, s)) != cudaSuccess) return err;
+  if (n_launch) *n_launch += launched + 1;
+  return cudaSuccess;
 }
 
 cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, float4* tabf,
