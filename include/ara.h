@@ -6,7 +6,7 @@
  * Analytics Using Many-Core Computing"): for each trial of a Year Event Table
  * (YET), for each event in time order, for each Event Loss Table (ELT) of a
  * layer, look up the event's loss record, draw a loss from the record's Beta
- * distribution (Section 3.4), apply the ELT financial terms, sum over the
+ * distribution (Section 3.3), apply the ELT financial terms, sum over the
  * layer's ELTs, apply the occurrence terms, and apply the aggregate terms to
  * the running sum of occurrence losses (Algorithm 1, Section 2.2).  The result
  * is the Year Loss Table (YLT), from which PML and TVaR are read (Section 2.3).
@@ -56,7 +56,7 @@ extern "C" {
 #define ARA_MAX_LAYER_ELTS 32
 
 /* Relative gap below sigma_bmax used when sigma_b is clipped: the paper
- * clips sigma_b to "a value very close to sigma_bmax" (Section 3.4); this
+ * clips sigma_b to "a value very close to sigma_bmax" (Section 3.3); this
  * library uses (1 - ARA_SIGMA_CLIP) * sigma_bmax whenever
  * sigma_b >= (1 - ARA_SIGMA_CLIP) * sigma_bmax. */
 #define ARA_SIGMA_CLIP 1e-6
@@ -163,7 +163,7 @@ ARA_API int ara_load_elts(ara_ctx *ctx, int32_t n_elts, const int32_t *elt_ids, 
                   const float *exposure, const ara_elt_terms *terms);
 
 /* Run one layer over trials [trial_begin, trial_end) (Algorithm 1 with the
- * secondary uncertainty of Section 3.4) and write one year loss per trial to
+ * secondary uncertainty of Section 3.3) and write one year loss per trial to
  * ylt_out (FP64, trial_end - trial_begin entries).  The uniform of trial t,
  * event index k (position in the trial, from 0) and ELT pool id j is word 0
  * of Philox4x32-10 with counter (t mod 2^32, k, j, t >> 32) and key
@@ -204,7 +204,7 @@ ARA_API int ara_sort_ylt(ara_ctx *ctx, const double *ylt, int64_t n, int64_t *or
  *
  * ara_debug_record_losses: for n XELT records (mean, sigma, exposure) and
  * uniforms z (FP32, in (0, 1)), out[i] = the secondary-uncertainty loss
- * max_l * InvCDF_beta(z[i]; alpha_i, beta_i) (Section 3.4) computed with the
+ * max_l * InvCDF_beta(z[i]; alpha_i, beta_i) (Section 3.3) computed with the
  * same record preparation, quantile table and FP32 inverse as
  * ara_run_layer (the mean for sigma == 0, 0 for mean == 0); newton_only != 0
  * uses the Halley iteration for every record, as ARA_NEWTON_ONLY does.

@@ -112,12 +112,12 @@ def uniform(seed: int, trial: int, k: int, elt_id: int) -> float:
 
 # ---------------------------------------------------------------- Beta
 def betainc(x: float, a: float, b: float) -> float:
-    """Regularised incomplete Beta I_x(a, b) = B(x; a, b) / B(a, b) (Section 3.4)."""
+    """Regularised incomplete Beta I_x(a, b) = B(x; a, b) / B(a, b) (Section 3.3)."""
     return _load().or_betainc(float(x), float(a), float(b))
 
 
 def betaincinv(p: float, a: float, b: float) -> float:
-    """InvCDF_beta(p; a, b) (Section 3.4): the x with I_x(a, b) = p."""
+    """InvCDF_beta(p; a, b) (Section 3.3): the x with I_x(a, b) = p."""
     return _load().or_betaincinv(float(p), float(a), float(b))
 
 
@@ -155,7 +155,7 @@ def betainc_batch(x, a, b) -> np.ndarray:
 
 
 def beta_params(mu: float, sigma: float, max_l: float):
-    """(kind, alpha, beta) of one XELT record (Section 3.4).
+    """(kind, alpha, beta) of one XELT record (Section 3.3).
 
     kind 0: secondary uncertainty with Beta(alpha, beta); 1: deterministic
     (mu == 0 or sigma == 0); -1: invalid record.

@@ -15,7 +15,7 @@
  *   l = min(max(l - OccR, 0), OccL); accumulate the occurrence losses and
  *   apply the aggregate terms l = min(max(S - AggR, 0), AggL) to the
  *   cumulative sum.  The trial's final aggregate loss is its YLT entry.
- *   Section 3.4: secondary uncertainty is applied to each looked-up loss,
+ *   Section 3.3: secondary uncertainty is applied to each looked-up loss,
  *   after the lookup and before the financial terms: with
  *   sigma_b = sigma / max_l, mu_b = mu / max_l,
  *   sigma_bmax = sqrt(mu_b (1 - mu_b)) (sigma_b clipped just below it),
@@ -36,7 +36,7 @@
  *     seed >> 32), word 0 mapped to ((w >> 9) + 0.5) * 2^-23, which lies in
  *     [2^-24, 1 - 2^-24], is exact in both FP32 and FP64 and has an exact
  *     complement 1 - z on the same grid; with sigma_C = 0 the
- *     five-step combination of Section 3.3 returns z unchanged;
+ *     five-step combination of Section 3.2 returns z unchanged;
  *   - a record with mu = 0 contributes nothing; a record with sigma = 0 has
  *     no secondary uncertainty and contributes mu;
  *   - PML(RP) is the m-th largest year loss, m = ceil(N / RP), and TVaR(RP)
@@ -97,7 +97,7 @@ double or_uniform(uint64_t seed, int64_t trial, int32_t k, int32_t elt_id)
 
 /* ------------------------------------------------------------------ */
 /* Regularised incomplete Beta I_x(a, b) = B(x; a, b) / B(a, b)         */
-/* (Section 3.4) by its continued fraction (Abramowitz & Stegun 26.5.8)*/
+/* (Section 3.3) by its continued fraction (Abramowitz & Stegun 26.5.8)*/
 /* evaluated with the modified Lentz method, using the symmetry         */
 /* I_x(a, b) = 1 - I_{1-x}(b, a) on the side where the fraction        */
 /* converges fast, x > (a + 1) / (a + b + 2).                           */
@@ -183,7 +183,7 @@ static double betaincinv_small_root(double p, double a, double b)
     return x;
 }
 
-/* InvCDF_beta(p; a, b) of Section 3.4: the x in (0, 1) with I_x(a, b) = p.
+/* InvCDF_beta(p; a, b) of Section 3.3: the x in (0, 1) with I_x(a, b) = p.
  * The root is computed as the smaller of x and 1 - x, so that both ends
  * keep full relative precision: when I_{1/2}(a, b) < p the root lies above
  * 1/2 and 1 - x solves I_{1-x}(b, a) = 1 - p. */
@@ -204,7 +204,7 @@ double or_betaincinv_complement(double p, double a, double b)
     return betaincinv_small_root(1.0 - p, b, a);
 }
 
-/* Beta shape parameters of one XELT record (Section 3.4).  Returns 0 when
+/* Beta shape parameters of one XELT record (Section 3.3).  Returns 0 when
  * the record carries secondary uncertainty (alpha, beta set), 1 when it is
  * deterministic (sigma == 0 or mu == 0), -1 when it is invalid
  * (mu_b outside (0, 1) with mu > 0, or a negative/non-finite value). */

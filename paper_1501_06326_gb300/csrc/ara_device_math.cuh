@@ -2,7 +2,7 @@
 // inverse of the regularised incomplete Beta function, and the financial
 // terms.  Everything here runs per (trial, event, ELT) pair on the GPU.
 //
-// Inverse Beta (Section 3.4: Loss = max_l * InvCDF_beta(z; alpha, beta)).
+// Inverse Beta (Section 3.3: Loss = max_l * InvCDF_beta(z; alpha, beta)).
 // The root x of I_x(a, b) = z is found in FP32 as the smaller of x and 1 - x
 // (the side is chosen with the per-record value I_{1/2}(a, b)), so both ends
 // keep relative precision.  Writing (A, B, P) for the oriented problem and r

@@ -1,5 +1,5 @@
 """Pins of the oracle's ARA loop (Algorithm 1, Section 2.2, with secondary
-uncertainty inserted after the lookup as Section 3.4 states) and of its
+uncertainty inserted after the lookup as Section 3.3 states) and of its
 PML/TVaR (Section 2.3).
 
 Hand-summed year losses of tiny YETs (tests/golden/tiny_ara_cases.json),

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Beta machinery (Section 3.4: Beta parameters from the
+"""Pins of the oracle's Beta machinery (Section 3.3: Beta parameters from the
 XELT record, the sigma clip, and Loss = max_l * InvCDF_beta(z; alpha, beta)).
 
 Closed forms of the Beta quantile, integer-shape binomial sums of the
