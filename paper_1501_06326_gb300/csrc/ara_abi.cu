@@ -149,6 +149,16 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Small parameter arrays to the host: a plain copy from host memory (no
+// device synchronisation), cudaMemcpy from device memory.
+cudaError_t copy_params_to_host(void* dst, const void* src, size_t bytes) {
+  if (!is_device_ptr(src)) {
+    std::memcpy(dst, src, bytes);
+    return cudaSuccess;
+  }
+  return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+}
+
 cudaMemcpyKind kind_to_device(const void* src) {
   return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 }
@@ -259,9 +269,9 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
   std::vector<int32_t> ids(n_elts);
   std::vector<int64_t> offs(static_cast<size_t>(n_elts) + 1);
   std::vector<ara_elt_terms> tm(n_elts, ara_elt_terms{0.0f, INFINITY, 1.0f});
-  ARA_CUDA(c, cudaMemcpy(ids.data(), elt_ids, sizeof(int32_t) * n_elts, cudaMemcpyDefault));
-  ARA_CUDA(c, cudaMemcpy(offs.data(), rec_offsets, sizeof(int64_t) * (n_elts + 1), cudaMemcpyDefault));
-  if (terms) ARA_CUDA(c, cudaMemcpy(tm.data(), terms, sizeof(ara_elt_terms) * n_elts, cudaMemcpyDefault));
+  ARA_CUDA(c, copy_params_to_host(ids.data(), elt_ids, sizeof(int32_t) * n_elts));
+  ARA_CUDA(c, copy_params_to_host(offs.data(), rec_offsets, sizeof(int64_t) * (n_elts + 1)));
+  if (terms) ARA_CUDA(c, copy_params_to_host(tm.data(), terms, sizeof(ara_elt_terms) * n_elts));
   if (offs[0] != 0) return fail(c, ARA_EINVAL, "ara_load_elts: rec_offsets[0] must be 0");
   for (int32_t i = 0; i < n_elts; ++i) {
     if (ids[i] < 0) return fail(c, ARA_EINVAL, "ara_load_elts: pool id %d is negative", ids[i]);
@@ -650,7 +660,7 @@ int ara_pml_tvar(ara_ctx* c, const double* ylt, int64_t n, const double* rps, in
   if (!ylt || n < 1 || !rps || n_rp < 1 || !pml_out || !tvar_out)
     return fail(c, ARA_EINVAL, "ara_pml_tvar: bad arguments");
   std::vector<double> h_rps(n_rp);
-  ARA_CUDA(c, cudaMemcpy(h_rps.data(), rps, sizeof(double) * n_rp, cudaMemcpyDefault));
+  ARA_CUDA(c, copy_params_to_host(h_rps.data(), rps, sizeof(double) * n_rp));
   for (double r : h_rps)
     if (!(r >= 1.0) || !std::isfinite(r)) return fail(c, ARA_EINVAL, "ara_pml_tvar: return periods must be >= 1");
   const double* d_ylt = ylt;

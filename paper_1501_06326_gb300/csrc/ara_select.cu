@@ -21,7 +21,8 @@ namespace ara {
 namespace {
 
 constexpr int kSelBlocks = 152;  // fixed grid: deterministic reduction order
-constexpr int kSelThreads = 256;
+constexpr int kSelThreads = 1024;
+constexpr int kSelUnroll = 4;  // loads in flight per thread
 constexpr int kSelGroup = 4;     // return periods selected together (one pass over the YLT serves all)
 
 __device__ __forceinline__ unsigned long long key_of(double v) {
@@ -47,6 +48,7 @@ struct SelScratch {
   unsigned int hist[kSelGroup][256];
   double part_sum[kSelBlocks][kSelGroup];
   unsigned long long part_cnt[kSelBlocks][kSelGroup];
+  unsigned int done;  // blocks of the current pass that have published their part
 };
 
 struct SelMs {
@@ -63,9 +65,25 @@ __global__ void k_sel_init(SelScratch* sc, SelMs ms, int g) {
     st.bad = 0;
   }
   for (int i = threadIdx.x; i < kSelGroup * 256; i += blockDim.x) (&sc->hist[0][0])[i] = 0;
+  if (threadIdx.x == 0) sc->done = 0;
 }
 
-// One MSB-first digit pass for every return period of the group.
+// True in the block that is the last of the grid to arrive (after each block
+// published its part with a fence); that block then sees every part.
+__device__ __forceinline__ bool last_block_arrives(SelScratch* sc) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&sc->done, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+// One MSB-first digit pass for every return period of the group: histogram of
+// the digit among the keys that match each period's prefix (warp-aggregated
+// shared-memory counts, then one global add per digit and block); the last
+// block to finish picks each period's digit and clears the histogram.
 __global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, int shift) {
   __shared__ unsigned int sh[kSelGroup][256];
   for (int i = threadIdx.x; i < kSelGroup * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
@@ -78,14 +96,37 @@ __global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, 
   __syncthreads();
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   bool nan = false;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
-    const double v = ylt[i];
-    nan |= (v != v);
-    const unsigned long long k = key_of(v);
-    const unsigned int d = static_cast<unsigned int>((k >> shift) & 255u);
+  // whole warps take part in every round (the match below needs all lanes)
+  const int64_t span = stride * kSelUnroll;
+  const int64_t n_round = ((n + span - 1) / span) * span;
+  for (int64_t i0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i0 < n_round; i0 += span) {
+    double v[kSelUnroll];
 #pragma unroll
-    for (int r = 0; r < kSelGroup; ++r)
-      if (r < g && (k & mask[r]) == prefix[r]) atomicAdd(&sh[r][d], 1u);
+    for (int u = 0; u < kSelUnroll; ++u) {
+      const int64_t i = i0 + u * stride;
+      v[u] = (i < n) ? ylt[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kSelUnroll; ++u) {
+      const bool in = i0 + u * stride < n;
+      nan |= (v[u] != v[u]);
+      const unsigned long long k = key_of(v[u]);
+      const unsigned int d = static_cast<unsigned int>((k >> shift) & 255u);
+#pragma unroll
+      for (int r = 0; r < kSelGroup; ++r) {
+        if (r >= g) break;
+        const bool hit = in && (k & mask[r]) == prefix[r];
+        const unsigned int hm = __ballot_sync(0xffffffffu, hit);
+        if (hm == 0u) continue;
+        if (__popc(hm) == 1) {  // one key: no aggregation needed
+          if (hit) atomicAdd(&sh[r][d], 1u);
+          continue;
+        }
+        const unsigned int peers = __match_any_sync(0xffffffffu, hit ? d : 256u + (threadIdx.x & 31));
+        if (hit && (threadIdx.x & 31) == static_cast<unsigned int>(__ffs(peers) - 1))
+          atomicAdd(&sh[r][d], static_cast<unsigned int>(__popc(peers)));
+      }
+    }
   }
   if (nan) atomicOr(&sc->st[0].bad, 1u);
   __syncthreads();
@@ -93,28 +134,41 @@ __global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, 
     const unsigned int c = (&sh[0][0])[i];
     if (c) atomicAdd(&(&sc->hist[0][0])[i], c);
   }
-}
-
-__global__ void k_sel_pick(SelScratch* sc, int g, int shift) {
-  if (threadIdx.x < g) {
-    SelState& st = sc->st[threadIdx.x];
-    const unsigned int* h = sc->hist[threadIdx.x];
-    unsigned long long above = 0;
-    int d = 255;
-    for (; d > 0; --d) {
-      if (above + h[d] >= st.want) break;
-      above += h[d];
+  if (!last_block_arrives(sc)) return;
+  // ---- pick: per period, the digit holding the wanted rank (a suffix scan of
+  // the counts from digit 255 down, thread t holding digit 255 - t)
+  __shared__ unsigned int s_warp[kSelThreads / 32];
+  for (int r = 0; r < g; ++r) {
+    const unsigned int c = (threadIdx.x < 256) ? __ldcg(&sc->hist[r][255 - threadIdx.x]) : 0u;
+    unsigned int incl = c;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+      const unsigned int o = __shfl_up_sync(0xffffffffu, incl, dd);
+      if ((threadIdx.x & 31) >= static_cast<unsigned int>(dd)) incl += o;
     }
-    st.want -= above;
-    st.prefix |= static_cast<unsigned long long>(d) << shift;
-    st.mask |= 255ull << shift;
+    if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    unsigned int before = 0;
+    for (int w = 0; w < static_cast<int>(threadIdx.x >> 5); ++w) before += s_warp[w];
+    incl += before;  // counts of digits 255 .. 255 - t
+    const unsigned long long want = __ldcg(&sc->st[r].want);
+    // the first t (highest digit) whose running count reaches want; digit 0 if none does
+    const bool reach = threadIdx.x < 256 && static_cast<unsigned long long>(incl) >= want &&
+                       (threadIdx.x == 0 || static_cast<unsigned long long>(incl - c) < want);
+    if (reach || (threadIdx.x == 255 && static_cast<unsigned long long>(incl) < want)) {
+      SelState& st = sc->st[r];
+      st.want = want - (incl - c);
+      st.prefix |= static_cast<unsigned long long>(255 - threadIdx.x) << shift;
+      st.mask |= 255ull << shift;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int i = threadIdx.x; i < kSelGroup * 256; i += blockDim.x) (&sc->hist[0][0])[i] = 0;
+  if (threadIdx.x == 0) sc->done = 0;
 }
 
 // Sum and count of the values whose key exceeds each selected key.
-__global__ void k_sel_tail(const double* ylt, int64_t n, SelScratch* sc, int g) {
+__global__ void k_sel_tail(const double* ylt, int64_t n, SelScratch* sc, int g, double* pml, double* tvar) {
   __shared__ double s_sum[kSelThreads / 32][kSelGroup];
   __shared__ unsigned long long s_cnt[kSelThreads / 32][kSelGroup];
   unsigned long long kth[kSelGroup];
@@ -128,15 +182,23 @@ __global__ void k_sel_tail(const double* ylt, int64_t n, SelScratch* sc, int g) 
     sum[r] = 0.0;
     cnt[r] = 0;
   }
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
-    const double v = ylt[i];
-    const unsigned long long k = key_of(v);
+  for (int64_t i0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i0 < n; i0 += stride * kSelUnroll) {
+    double v[kSelUnroll];
 #pragma unroll
-    for (int r = 0; r < kSelGroup; ++r)
-      if (k > kth[r]) {
-        sum[r] += v;
-        ++cnt[r];
-      }
+    for (int u = 0; u < kSelUnroll; ++u) {
+      const int64_t i = i0 + u * stride;
+      v[u] = (i < n) ? ylt[i] : -INFINITY;
+    }
+#pragma unroll
+    for (int u = 0; u < kSelUnroll; ++u) {
+      const unsigned long long k = key_of(v[u]);
+#pragma unroll
+      for (int r = 0; r < kSelGroup; ++r)
+        if (i0 + u * stride < n && k > kth[r]) {
+          sum[r] += v[u];
+          ++cnt[r];
+        }
+    }
   }
 #pragma unroll
   for (int r = 0; r < kSelGroup; ++r) {
@@ -161,22 +223,34 @@ __global__ void k_sel_tail(const double* ylt, int64_t n, SelScratch* sc, int g) 
     sc->part_sum[blockIdx.x][r] = t;
     sc->part_cnt[blockIdx.x][r] = c;
   }
-}
-
-__global__ void k_sel_finish(const SelScratch* sc, int g, int n_parts, double* pml, double* tvar) {
-  if (threadIdx.x < g) {
-    const int r = threadIdx.x;
-    double s = 0.0;
-    unsigned long long c = 0;
-    for (int i = 0; i < n_parts; ++i) {
-      s += sc->part_sum[i][r];
-      c += sc->part_cnt[i][r];
+  if (!last_block_arrives(sc)) return;
+  // ---- finish (the last block): one thread per part, then a tree of fixed
+  // shape over the parts, so the sum is deterministic
+  __shared__ double s_ps[kSelBlocks];
+  __shared__ unsigned long long s_pc[kSelBlocks];
+  for (int r = 0; r < g; ++r) {
+    const unsigned int i = threadIdx.x;
+    if (i < kSelBlocks) {
+      s_ps[i] = (i < gridDim.x) ? __ldcg(&sc->part_sum[i][r]) : 0.0;
+      s_pc[i] = (i < gridDim.x) ? __ldcg(&sc->part_cnt[i][r]) : 0ull;
     }
-    const double v = value_of(sc->st[r].prefix);
-    const unsigned long long m = sc->st[r].m;
-    pml[r] = v;
-    tvar[r] = (s + static_cast<double>(m - c) * v) / static_cast<double>(m);
+    __syncthreads();
+    for (unsigned int half = 128; half > 0; half >>= 1) {  // 256 >= kSelBlocks leaves
+      if (i < half && i + half < kSelBlocks) {
+        s_ps[i] += s_ps[i + half];
+        s_pc[i] += s_pc[i + half];
+      }
+      __syncthreads();
+    }
+    if (i == 0) {
+      const double v = value_of(sc->st[r].prefix);
+      const unsigned long long m = sc->st[r].m;
+      pml[r] = v;
+      tvar[r] = (s_ps[0] + static_cast<double>(m - s_pc[0]) * v) / static_cast<double>(m);
+    }
+    __syncthreads();
   }
+  if (threadIdx.x == 0) sc->done = 0;
 }
 
 }  // namespace
@@ -198,13 +272,9 @@ cudaError_t pml_tvar_device(const double* ylt, int64_t n, const double* rps_host
       ms.m[r] = static_cast<unsigned long long>(m);
     }
     k_sel_init<<<1, 256, 0, s>>>(sc, ms, g);
-    for (int shift = 56; shift >= 0; shift -= 8) {
-      k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, shift);
-      k_sel_pick<<<1, 256, 0, s>>>(sc, g, shift);
-    }
-    k_sel_tail<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g);
-    k_sel_finish<<<1, 32, 0, s>>>(sc, g, grid, pml + r0, tvar + r0);
-    if (n_launch) *n_launch += 19;
+    for (int shift = 56; shift >= 0; shift -= 8) k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, shift);
+    k_sel_tail<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, pml + r0, tvar + r0);
+    if (n_launch) *n_launch += 10;
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
