@@ -153,8 +153,8 @@ ARA_API int ara_load_yet(ara_ctx *ctx, int64_t n_trials, const int64_t *offsets,
  * (no secondary uncertainty).  `terms` (n_elts entries, NULL: identity) are
  * the ELT financial terms.  Loading a pool id that is already resident
  * replaces it.  The Beta shapes of every record are derived here (Section
- * 3.4), once per record, together with a 32-node quantile table of each
- * record's Beta built in FP64 (512 bytes per record).  At most 2^23 - 1
+ * 3.3), once per record, together with a 32-node quantile table of each
+ * record's Beta built in FP64 (512 bytes per record).  At most 2^22 - 1
  * records per ELT.
  * Errors: ARA_EINVAL (unsorted or duplicate ids, negative or non-finite
  * values, exposure <= mean), ARA_ENOMEM, ARA_ECUDA. */
@@ -181,6 +181,29 @@ ARA_API int ara_run_layer(ara_ctx *ctx, const ara_layer *layer, uint64_t seed, i
  * an order-free hash of the hit list), used to check event indexing. */
 ARA_API int ara_run_layer_diag(ara_ctx *ctx, const ara_layer *layer, uint64_t seed, int64_t trial_begin,
                        int64_t trial_end, double *ylt_out, const ara_diag *diag);
+
+/* Several layers over the same trials in one pass (a batch): the YET of the
+ * trial range is read once for all the layers, and the loss after ELT terms
+ * of each (event occurrence, ELT) is computed once for every layer of the
+ * batch that holds the ELT.  Algorithm 1 runs per layer over a portfolio's
+ * layers (Section 2.1 (iii)); each layer's year losses are those of
+ * ara_run_layer with the same seed, up to FP32 rounding of the per-event sums
+ * (the uniforms depend on the trial, event index and ELT pool id only).
+ * layers: n_layers (1..ARA_MAX_BATCH_LAYERS) layers, each as for
+ * ara_run_layer, all with the same flags; their ELTs together (the union)
+ * number at most ARA_MAX_BATCH_ELTS.
+ * ylt_out: n_layers * (trial_end - trial_begin) doubles, layer-major (layer l's
+ * year losses start at l * (trial_end - trial_begin)); host or device memory.
+ * Each trial's sum of occurrence losses is accumulated per layer as a 64-bit
+ * fixed-point integer (a power-of-two scale per layer, chosen from the layer's
+ * largest possible occurrence loss and the longest trial of the YET), so the
+ * result does not depend on the order of the additions.
+ * Errors: ARA_EINVAL (bad layers, mixed flags, union too large, bad range),
+ * ARA_ENOTLOADED, ARA_ENOMEM, ARA_ECUDA. */
+#define ARA_MAX_BATCH_LAYERS 32
+#define ARA_MAX_BATCH_ELTS 64
+ARA_API int ara_run_layers(ara_ctx *ctx, int32_t n_layers, const ara_layer *layers, uint64_t seed,
+                   int64_t trial_begin, int64_t trial_end, double *ylt_out);
 
 /* PML and TVaR of a YLT (Section 2.3) at n_rp return periods (each >= 1):
  * with m = ceil(n / RP), PML is the m-th largest year loss and TVaR the mean

@@ -169,7 +169,7 @@ def beta_params(mu: float, sigma: float, max_l: float):
 # ---------------------------------------------------------------- ARA
 def run_layer(yet, pool, layer_terms, seed: int = 0, primary_only: bool = False,
               trials=None, threads: int = 0):
-    """Algorithm 1 with secondary uncertainty over one layer (Sections 2.2, 3.4).
+    """Algorithm 1 with secondary uncertainty over one layer (Sections 2.2, 3.3).
 
     ``pool`` holds exactly the layer's ELTs (an ``ELTPool``); ``layer_terms``
     is (OccR, OccL, AggR, AggL).  Returns a dict with ``ylt`` (year loss per

@@ -3,7 +3,7 @@
 Argument marshalling only: every step of the ARA hot path runs in the CUDA
 kernels of ``libara.so``.  The module-level functions mirror the C entry
 points one to one (``ara_create``, ``ara_load_yet``, ``ara_load_elts``,
-``ara_run_layer``, ``ara_run_layer_diag``, ``ara_pml_tvar``, ``ara_sort_ylt``,
+``ara_run_layer``, ``ara_run_layer_diag``, ``ara_run_layers``, ``ara_pml_tvar``, ``ara_sort_ylt``,
 ``ara_get_stats``, ``ara_last_error``, ``ara_destroy``); ``Ara`` wraps them
 with error checking.  Arrays may be numpy arrays (host memory) or torch
 tensors (host, pinned or CUDA): only their data pointers cross the boundary.
@@ -27,6 +27,8 @@ ARA_OK, ARA_EINVAL, ARA_ENOMEM, ARA_ENOTLOADED, ARA_ECUDA, ARA_ETIMEOUT = 0, -1,
 ARA_PRIMARY_ONLY = 1
 ARA_NEWTON_ONLY = 2
 ARA_MAX_LAYER_ELTS = 32
+ARA_MAX_BATCH_LAYERS = 32
+ARA_MAX_BATCH_ELTS = 64
 _ERR_NAMES = {
     ARA_EINVAL: "ARA_EINVAL", ARA_ENOMEM: "ARA_ENOMEM", ARA_ENOTLOADED: "ARA_ENOTLOADED",
     ARA_ECUDA: "ARA_ECUDA", ARA_ETIMEOUT: "ARA_ETIMEOUT",
@@ -37,7 +39,7 @@ EXPORTED = (
     "ara_create", "ara_set_stream", "ara_load_yet", "ara_load_elts", "ara_run_layer",
     "ara_run_layer_diag", "ara_pml_tvar", "ara_sort_ylt", "ara_debug_uniforms",
     "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
-    "ara_pml_tvar_noalloc",
+    "ara_pml_tvar_noalloc", "ara_run_layers",
 )
 ARA_NOALLOC_MAX_RP = 64
 
@@ -121,6 +123,7 @@ def load_library(path: str = LIB_PATH):
     lib.ara_load_elts.argtypes = [P, i32, P, P, P, P, P, P, P]
     lib.ara_run_layer.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P]
     lib.ara_run_layer_diag.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P, ctypes.POINTER(Diag)]
+    lib.ara_run_layers.argtypes = [P, i32, ctypes.POINTER(Layer), u64, i64, i64, P]
     lib.ara_pml_tvar.argtypes = [P, P, i64, P, i32, P, P]
     lib.ara_sort_ylt.argtypes = [P, P, i64, P]
     lib.ara_debug_uniforms.argtypes = [P, u64, i64, P, P, P, P]
@@ -200,6 +203,12 @@ def ara_run_layer(h, layer: Layer, seed, trial_begin, trial_end, ylt_out):
 def ara_run_layer_diag(h, layer: Layer, seed, trial_begin, trial_end, ylt_out, diag: Diag):
     return load_library().ara_run_layer_diag(h, ctypes.byref(layer), int(seed), int(trial_begin),
                                              int(trial_end), _ptr(ylt_out, np.float64), ctypes.byref(diag))
+
+
+def ara_run_layers(h, n_layers, layers, seed, trial_begin, trial_end, ylt_out):
+    """``layers``: a ctypes array of ``Layer``; ``ylt_out``: n_layers x (trial_end - trial_begin), layer-major."""
+    return load_library().ara_run_layers(h, int(n_layers), layers, int(seed), int(trial_begin), int(trial_end),
+                                         _ptr(ylt_out, np.float64))
 
 
 def ara_pml_tvar(h, ylt, n, return_periods, n_rp, pml_out, tvar_out):
@@ -314,6 +323,14 @@ class Ara:
         else:
             d = Diag(_ptr(hits_out, np.int64), _ptr(hash_out, np.uint64))
             self._check(ara_run_layer_diag(self._h, lay, seed, trial_begin, trial_end, ylt_out, d))
+
+    def run_layers(self, layers, seed: int, trial_begin: int, trial_end: int, ylt_out,
+                   primary_only: bool = False, newton_only: bool = False) -> None:
+        """Several layers in one pass.  ``layers``: a sequence of (elt_ids, layer_terms);
+        ``ylt_out``: (n_layers, trial_end - trial_begin) float64, C order."""
+        made = [self.make_layer(ids, terms, primary_only, newton_only) for ids, terms in layers]
+        arr = (Layer * len(made))(*made)
+        self._check(ara_run_layers(self._h, len(made), arr, seed, trial_begin, trial_end, ylt_out))
 
     def pml_tvar(self, ylt, return_periods, pml_out=None, tvar_out=None):
         rps = np.ascontiguousarray(return_periods, dtype=np.float64)

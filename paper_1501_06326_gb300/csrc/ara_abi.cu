@@ -28,6 +28,7 @@ struct Elt {
   DevBuf tabf;    // float4 [n_fine * kTabFineStride] fine quantile tables
   int64_t n = 0;
   int64_t n_fine = 0;
+  float max_loss = 0.0f;  // largest loss a record can produce (max(exposure, mean))
   int32_t max_event = -1;
   ara_elt_terms terms{0.0f, INFINITY, 1.0f};
 };
@@ -44,6 +45,7 @@ struct ara_ctx {
   DevBuf yet_off, yet_ids;
   std::vector<int64_t> h_off;
   int64_t n_trials = 0;
+  int64_t max_trial_events = 0;
   int64_t n_events = 0;
   int32_t catalogue = 0;
   bool yet_loaded = false;
@@ -253,8 +255,11 @@ int ara_load_yet(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int
   if (h_flags & ara::kLongTrial) return fail(c, ARA_EINVAL, "ara_load_yet: a trial has 2^22 or more events");
   if (h_flags & ara::kBadEventId)
     return fail(c, ARA_EINVAL, "ara_load_yet: an event id lies outside [0, %d)", catalogue_size);
+  int64_t longest = 0;  // bounds a trial's sum in the batched layers' fixed point
+  for (int64_t t = 0; t < n_trials; ++t) longest = std::max(longest, c->h_off[t + 1] - c->h_off[t]);
   c->n_trials = n_trials;
   c->n_events = n_events;
+  c->max_trial_events = longest;
   c->catalogue = catalogue_size;
   c->yet_loaded = true;
   return ARA_OK;
@@ -303,7 +308,7 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
       (rc = reserve(c, c->elt_tabf_stage, sizeof(float4) * ara::kTabFineStride * (fine_off[n_elts] + 1))) ||
       (rc = reserve(c, c->elt_work, sizeof(uint32_t) * (work_off[n_elts] + R + 8) +
                                         sizeof(ara::FineJob) * static_cast<size_t>(n_elts))) ||
-      (rc = reserve(c, c->elt_flags, sizeof(uint32_t) * 3 * n_elts)))
+      (rc = reserve(c, c->elt_flags, sizeof(uint32_t) * 4 * n_elts)))
     return rc;
   int32_t* d_ev = static_cast<int32_t*>(c->elt_stage.ptr);
   float* d_mu = reinterpret_cast<float*>(d_ev + R);
@@ -322,19 +327,21 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     ARA_CUDA(c, cudaMemcpyAsync(d_sg, sigma, sizeof(float) * R, kind_to_device(sigma), c->stream));
     ARA_CUDA(c, cudaMemcpyAsync(d_ex, exposure, sizeof(float) * R, kind_to_device(exposure), c->stream));
   }
-  // per ELT: flags word, the largest event id (0xFFFFFFFF = none), candidates for fine tables
-  std::vector<uint32_t> init(3 * static_cast<size_t>(n_elts));
+  // per ELT: flags word, the largest event id (0xFFFFFFFF = none), candidates for fine
+  // tables, the largest loss (FP32 bits)
+  std::vector<uint32_t> init(4 * static_cast<size_t>(n_elts));
   for (int32_t i = 0; i < n_elts; ++i) {
-    init[3 * i] = 0u;
-    init[3 * i + 1] = 0xFFFFFFFFu;
-    init[3 * i + 2] = 0u;
+    init[4 * i] = 0u;
+    init[4 * i + 1] = 0xFFFFFFFFu;
+    init[4 * i + 2] = 0u;
+    init[4 * i + 3] = 0u;
   }
   ARA_CUDA(c, cudaMemcpyAsync(d_flags, init.data(), sizeof(uint32_t) * init.size(), cudaMemcpyHostToDevice, c->stream));
   for (int32_t i = 0; i < n_elts; ++i) {
     const int64_t o = offs[i], n = offs[i + 1] - offs[i];
-    uint32_t* f = d_flags + 3 * i;
+    uint32_t* f = d_flags + 4 * i;
     ARA_CUDA(c, ara::launch_prepare_records(d_ev + o, d_mu + o, d_sg + o, d_ex + o, n, d_recs + o, d_shapes + o, f,
-                                            reinterpret_cast<int32_t*>(f + 1), c->stream));
+                                            reinterpret_cast<int32_t*>(f + 1), f + 3, c->stream));
     c->launches += 1;
   }
   // coarse tables of every record in one launch, then each ELT's fine tables
@@ -347,7 +354,7 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     int launched = 0;
     uint32_t* w = d_work + work_off[i];
     ARA_CUDA(c, ara::scan_exclusive_u32(d_need + o, w, n, w + n + 1, c->stream, &launched));
-    ARA_CUDA(c, cudaMemcpyAsync(d_flags + 3 * i + 2, w + n, sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream));
+    ARA_CUDA(c, cudaMemcpyAsync(d_flags + 4 * i + 2, w + n, sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream));
     c->launches += launched;
     jobs.push_back(ara::FineJob{o, n, w, fine_off[i], ara::fine_table_cap(n), 0});
   }
@@ -361,11 +368,11 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
                                             fine_off[n_elts], d_tabf, c->stream));
     c->launches += 1;
   }
-  std::vector<uint32_t> hf(3 * static_cast<size_t>(n_elts));
+  std::vector<uint32_t> hf(4 * static_cast<size_t>(n_elts));
   ARA_CUDA(c, cudaMemcpyAsync(hf.data(), d_flags, sizeof(uint32_t) * hf.size(), cudaMemcpyDeviceToHost, c->stream));
   ARA_CUDA(c, cudaStreamSynchronize(c->stream));
   for (int32_t i = 0; i < n_elts; ++i) {
-    const uint32_t f = hf[3 * i];
+    const uint32_t f = hf[4 * i];
     const char* why = nullptr;
     if (f & ara::kBadOrder) why = "event ids are not strictly increasing";
     else if (f & ara::kBadEventId) why = "an event id is negative";
@@ -376,7 +383,7 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
   // ---- commit: each ELT keeps (or grows) its own buffers; the pool only changes once all checks passed
   for (int32_t i = 0; i < n_elts; ++i) {
     const int64_t o = offs[i], n = offs[i + 1] - offs[i];
-    const int64_t n_fine = std::min<int64_t>(hf[3 * i + 2], ara::fine_table_cap(n));
+    const int64_t n_fine = std::min<int64_t>(hf[4 * i + 2], ara::fine_table_cap(n));
     Elt& el = c->pool[ids[i]];
     if ((rc = reserve(c, el.events, sizeof(int32_t) * (n + 4))) ||
         (rc = reserve(c, el.recs, sizeof(ara::Pair) * (n > 0 ? n : 1))) ||
@@ -392,7 +399,8 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     el.n = n;
     el.n_fine = n_fine;
     el.terms = tm[i];
-    el.max_event = static_cast<int32_t>(hf[3 * i + 1]);
+    el.max_event = static_cast<int32_t>(hf[4 * i + 1]);
+    std::memcpy(&el.max_loss, &hf[4 * i + 3], sizeof(float));
     if (n > 0) {
       ARA_CUDA(c, cudaMemcpyAsync(el.events.ptr, d_ev + o, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
       ARA_CUDA(c, cudaMemcpyAsync(el.recs.ptr, d_recs + o, sizeof(ara::Pair) * n, cudaMemcpyDeviceToDevice, c->stream));
@@ -407,38 +415,173 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
   return ARA_OK;
 }
 
-static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out,
-                          const ara_diag* diag) {
-  int rc = bind(c);
-  if (rc) return rc;
-  if (!L || !ylt_out) return fail(c, ARA_EINVAL, "ara_run_layer: layer and ylt_out are required");
-  if (!c->yet_loaded) return fail(c, ARA_ENOTLOADED, "ara_run_layer: no YET loaded");
+// ---------------------------------------------------------------- layer passes
+// What a pass over a trial range needs before its losses kernel: the index of
+// the ELTs it covers (a layer, or the union of a batch) and the gather launch.
+struct PassPlan {
+  ara::LayerEltRefs refs{};
+  ara::LayerIndex ix{};
+  ara::GatherParams g{};
+  int64_t n_out = 0, n_tiles = 0, e0 = 0;
+  int grid = 0;
+  size_t smem = 0;
+  int filt_words = 0;
+};
+
+static int check_trial_range(ara_ctx* c, int64_t t0, int64_t t1, const char* who) {
+  if (!c->yet_loaded) return fail(c, ARA_ENOTLOADED, "%s: no YET loaded", who);
   if (t0 < 0 || t1 > c->n_trials || t0 >= t1)
-    return fail(c, ARA_EINVAL, "ara_run_layer: trial range [%lld, %lld) outside [0, %lld)", (long long)t0,
-                (long long)t1, (long long)c->n_trials);
+    return fail(c, ARA_EINVAL, "%s: trial range [%lld, %lld) outside [0, %lld)", who, (long long)t0, (long long)t1,
+                (long long)c->n_trials);
+  return ARA_OK;
+}
+
+// A layer's ELT list (1..ARA_MAX_LAYER_ELTS distinct ids) and terms; `ids`
+// receives the ids in canonical (ascending) order, so that no result depends
+// on the order in which the caller lists a layer's ELTs.
+static int check_layer(ara_ctx* c, const ara_layer* L, const char* who, std::vector<int32_t>* ids) {
   if (L->n_elts < 1 || L->n_elts > ARA_MAX_LAYER_ELTS || !L->elt_ids)
-    return fail(c, ARA_EINVAL, "ara_run_layer: a layer needs 1..%d ELTs", ARA_MAX_LAYER_ELTS);
+    return fail(c, ARA_EINVAL, "%s: a layer needs 1..%d ELTs", who, ARA_MAX_LAYER_ELTS);
   if (!(L->occ_retention >= 0.0) || !(L->agg_retention >= 0.0) || !(L->occ_limit >= 0.0) ||
       !(L->agg_limit >= 0.0) || !std::isfinite(L->occ_retention) || !std::isfinite(L->agg_retention))
-    return fail(c, ARA_EINVAL, "ara_run_layer: retentions must be finite and >= 0, limits >= 0");
-  std::vector<int32_t> ids(L->elt_ids, L->elt_ids + L->n_elts);
-  std::sort(ids.begin(), ids.end());  // canonical order: the layer's result does not depend on ELT order
-  for (size_t i = 1; i < ids.size(); ++i)
-    if (ids[i] == ids[i - 1]) return fail(c, ARA_EINVAL, "ara_run_layer: pool id %d repeated in the layer", ids[i]);
-  ara::LayerEltRefs refs{};
-  refs.n_elts = L->n_elts;
-  refs.rec_begin[0] = 0;
-  ara::LossParams p{};
-  for (int i = 0; i < L->n_elts; ++i) {
+    return fail(c, ARA_EINVAL, "%s: retentions must be finite and >= 0, limits >= 0", who);
+  ids->assign(L->elt_ids, L->elt_ids + L->n_elts);
+  std::sort(ids->begin(), ids->end());
+  for (size_t i = 1; i < ids->size(); ++i)
+    if ((*ids)[i] == (*ids)[i - 1]) return fail(c, ARA_EINVAL, "%s: pool id %d repeated in a layer", who, (*ids)[i]);
+  return ARA_OK;
+}
+
+// Index buffers for the ELTs `ids` (ascending pool ids, at most
+// kMaxIndexElts) and the gather over [t0, t1).
+static int plan_pass(ara_ctx* c, const std::vector<int32_t>& ids, int64_t t0, int64_t t1, const char* who,
+                     PassPlan* pl) {
+  int rc;
+  pl->refs = ara::LayerEltRefs{};
+  pl->refs.n_elts = static_cast<int32_t>(ids.size());
+  pl->refs.rec_begin[0] = 0;
+  for (size_t i = 0; i < ids.size(); ++i) {
     auto it = c->pool.find(ids[i]);
-    if (it == c->pool.end()) return fail(c, ARA_ENOTLOADED, "ara_run_layer: ELT %d is not loaded", ids[i]);
+    if (it == c->pool.end()) return fail(c, ARA_ENOTLOADED, "%s: ELT %d is not loaded", who, ids[i]);
     const Elt& el = it->second;
     if (el.max_event >= c->catalogue)
-      return fail(c, ARA_EINVAL, "ara_run_layer: ELT %d holds event id %d outside the catalogue of %d", ids[i],
+      return fail(c, ARA_EINVAL, "%s: ELT %d holds event id %d outside the catalogue of %d", who, ids[i],
                   el.max_event, c->catalogue);
-    refs.events[i] = static_cast<const int32_t*>(el.events.ptr);
-    refs.recs[i] = static_cast<const ara::Pair*>(el.recs.ptr);
-    refs.rec_begin[i + 1] = refs.rec_begin[i] + el.n;
+    pl->refs.events[i] = static_cast<const int32_t*>(el.events.ptr);
+    pl->refs.recs[i] = static_cast<const ara::Pair*>(el.recs.ptr);
+    pl->refs.rec_begin[i + 1] = pl->refs.rec_begin[i] + el.n;
+  }
+  const int64_t n_recs = pl->refs.rec_begin[ids.size()];
+  if (n_recs >= (int64_t(1) << 31) - 1) return fail(c, ARA_EINVAL, "%s: the ELTs hold too many records", who);
+  // ---- index
+  const int64_t n_words = (static_cast<int64_t>(c->catalogue) + 31) / 32;
+  const size_t tmp_words = std::max(ara::scan_tmp_words(n_words), ara::scan_tmp_words(n_recs));
+  if ((rc = reserve(c, c->bits, sizeof(uint32_t) * n_words)) ||
+      (rc = reserve(c, c->word_cnt, sizeof(uint32_t) * (n_words + 1))) ||
+      (rc = reserve(c, c->word_pairs, sizeof(uint32_t) * (n_words + 1))) ||
+      (rc = reserve(c, c->rankdir, sizeof(uint2) * n_words)) ||
+      (rc = reserve(c, c->mask, sizeof(unsigned long long) * (n_recs + 1))) ||
+      (rc = reserve(c, c->slot_cnt, sizeof(uint32_t) * (n_recs + 2))) ||
+      (rc = reserve(c, c->pairs, sizeof(ara::Pair) * (n_recs + 1))) ||
+      (rc = reserve(c, c->pairs_hot, sizeof(ara::PairHot) * (n_recs + 1))) ||
+      (rc = reserve(c, c->scan_tmp, sizeof(uint32_t) * (tmp_words + 8))))
+    return rc;
+  ara::LayerIndex& ix = pl->ix;
+  ix.bits = static_cast<uint32_t*>(c->bits.ptr);
+  ix.word_cnt = static_cast<uint32_t*>(c->word_cnt.ptr);
+  ix.word_pairs = static_cast<uint32_t*>(c->word_pairs.ptr);
+  ix.rankdir = static_cast<uint2*>(c->rankdir.ptr);
+  ix.mask = static_cast<unsigned long long*>(c->mask.ptr);
+  ix.slot_cnt = static_cast<uint32_t*>(c->slot_cnt.ptr);
+  ix.pairs = static_cast<ara::Pair*>(c->pairs.ptr);
+  ix.hot = static_cast<ara::PairHot*>(c->pairs_hot.ptr);
+  ix.scan_tmp = static_cast<uint32_t*>(c->scan_tmp.ptr);
+  ix.n_words = n_words;
+  ix.n_recs = n_recs;
+  // ---- gather
+  pl->filt_words = ara::gather_filter_words(n_words, c->max_smem);
+  pl->smem = ara::gather_smem_bytes(pl->filt_words);
+  if (pl->smem > static_cast<size_t>(c->max_smem))
+    return fail(c, ARA_ECUDA, "%s: kernel needs %zu bytes of shared memory, device allows %d", who, pl->smem,
+                c->max_smem);
+  pl->n_out = t1 - t0;
+  pl->n_tiles = (pl->n_out + ara::kWarpTrials - 1) / ara::kWarpTrials;
+  pl->e0 = c->h_off[t0];
+  const int64_t e1 = c->h_off[t1];
+  if ((rc = reserve(c, c->ev_buf, sizeof(uint2) * (e1 - pl->e0 + 1))) ||
+      (rc = reserve(c, c->tile_cnt, sizeof(uint32_t) * (pl->n_tiles + 1))) ||
+      (rc = reserve(c, c->def_acc, sizeof(double) * (pl->n_out + 1))))
+    return rc;
+  ara::GatherParams& g = pl->g;
+  g.off = static_cast<const int64_t*>(c->yet_off.ptr);
+  g.ids = static_cast<const int32_t*>(c->yet_ids.ptr);
+  g.t_begin = t0;
+  g.t_end = t1;
+  g.n_tiles = pl->n_tiles;
+  g.e0 = pl->e0;
+  g.rankdir = ix.rankdir;
+  g.n_words = n_words;
+  g.slot_start = ix.slot_cnt;
+  g.filt_words = pl->filt_words;
+  g.ev_buf = static_cast<uint2*>(c->ev_buf.ptr);
+  g.tile_cnt = static_cast<uint32_t*>(c->tile_cnt.ptr);
+  g.queue = static_cast<unsigned long long*>(c->counters.ptr) + 4;
+  const int64_t warps_per_sm = ara::kGatherThreads / 32;
+  pl->grid = static_cast<int>(std::min<int64_t>(c->num_sms, (pl->n_tiles + warps_per_sm - 1) / warps_per_sm));
+  return ARA_OK;
+}
+
+// Index build and gather on the context stream (with their timing events).
+static int launch_index_and_gather(ara_ctx* c, const PassPlan& pl, const char* who, int* launched) {
+  cudaEvent_t ia, ib, ka, kb;
+  if (!timed_pair(c, 1, &ia, &ib) || !timed_pair(c, 0, &ka, &kb))
+    return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
+  ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 8 * sizeof(unsigned long long), c->stream));
+  ARA_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
+  ARA_CUDA(c, cudaEventRecord(ia, c->stream));
+  ARA_CUDA(c, ara::build_layer_index(pl.refs, const_cast<ara::LayerIndex&>(pl.ix), c->stream, launched));
+  ARA_CUDA(c, cudaEventRecord(ib, c->stream));
+  ARA_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
+  ARA_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+  ARA_CUDA(c, cudaEventRecord(ka, c->stream));
+  ARA_CUDA(c, ara::launch_gather(pl.g, pl.grid, pl.smem, c->stream));
+  ARA_CUDA(c, cudaEventRecord(kb, c->stream));
+  *launched += 1;
+  return ARA_OK;
+}
+
+static void fill_philox_keys(uint64_t seed, uint32_t (&rk)[20]) {
+  const uint32_t lo = static_cast<uint32_t>(seed & 0xFFFFFFFFull), hi = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {  // Weyl key schedule of Philox4x32
+    rk[2 * r] = lo + static_cast<uint32_t>(r) * 0x9E3779B9u;
+    rk[2 * r + 1] = hi + static_cast<uint32_t>(r) * 0xBB67AE85u;
+  }
+}
+
+static void record_pass_stats(ara_ctx* c, const PassPlan& pl, int64_t t0, int64_t t1, int64_t elts) {
+  c->stats = ara_stats{};
+  c->stats.n_events = c->h_off[t1] - c->h_off[t0];
+  c->stats.n_evals = c->stats.n_events * elts;
+  c->stats.grid = pl.grid;
+  c->stats.block = ara::kGatherThreads;
+  c->stats.smem_bytes = static_cast<int32_t>(pl.smem);
+  c->stats.filter_bits = pl.filt_words * 32;
+  c->stats.kernel_ms = -1.0f;  // device times are read lazily by ara_get_stats
+}
+
+static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out,
+                          const ara_diag* diag) {
+  static const char* who = "ara_run_layer";
+  int rc = bind(c);
+  if (rc) return rc;
+  if (!L || !ylt_out) return fail(c, ARA_EINVAL, "%s: layer and ylt_out are required", who);
+  std::vector<int32_t> ids;
+  if ((rc = check_trial_range(c, t0, t1, who)) || (rc = check_layer(c, L, who, &ids))) return rc;
+  PassPlan pl;
+  if ((rc = plan_pass(c, ids, t0, t1, who, &pl))) return rc;
+  ara::LossParams p{};
+  for (size_t i = 0; i < ids.size(); ++i) {
+    const Elt& el = c->pool.find(ids[i])->second;
     p.elt_id[i] = ids[i];
     p.tab[i] = static_cast<const float4*>(el.tab.ptr);
     p.tabf[i] = static_cast<const float4*>(el.tabf.ptr);
@@ -446,35 +589,8 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
     p.t_lim[i] = el.terms.limit;
     p.t_share[i] = el.terms.share;
   }
-  const int64_t n_recs = refs.rec_begin[L->n_elts];
-  if (n_recs >= (int64_t(1) << 31) - 1) return fail(c, ARA_EINVAL, "ara_run_layer: layer holds too many records");
-  // ---- per-layer index
-  const int64_t n_words = (static_cast<int64_t>(c->catalogue) + 31) / 32;
-  const size_t tmp_words = std::max(ara::scan_tmp_words(n_words), ara::scan_tmp_words(n_recs));
-  if ((rc = reserve(c, c->bits, sizeof(uint32_t) * n_words)) ||
-      (rc = reserve(c, c->word_cnt, sizeof(uint32_t) * (n_words + 1))) ||
-      (rc = reserve(c, c->word_pairs, sizeof(uint32_t) * (n_words + 1))) ||
-      (rc = reserve(c, c->rankdir, sizeof(uint2) * n_words)) ||
-      (rc = reserve(c, c->mask, sizeof(uint32_t) * (n_recs + 1))) ||
-      (rc = reserve(c, c->slot_cnt, sizeof(uint32_t) * (n_recs + 2))) ||
-      (rc = reserve(c, c->pairs, sizeof(ara::Pair) * (n_recs + 1))) ||
-      (rc = reserve(c, c->pairs_hot, sizeof(ara::PairHot) * (n_recs + 1))) ||
-      (rc = reserve(c, c->scan_tmp, sizeof(uint32_t) * (tmp_words + 8))))
-    return rc;
-  ara::LayerIndex ix{};
-  ix.bits = static_cast<uint32_t*>(c->bits.ptr);
-  ix.word_cnt = static_cast<uint32_t*>(c->word_cnt.ptr);
-  ix.word_pairs = static_cast<uint32_t*>(c->word_pairs.ptr);
-  ix.rankdir = static_cast<uint2*>(c->rankdir.ptr);
-  ix.mask = static_cast<uint32_t*>(c->mask.ptr);
-  ix.slot_cnt = static_cast<uint32_t*>(c->slot_cnt.ptr);
-  ix.pairs = static_cast<ara::Pair*>(c->pairs.ptr);
-  ix.hot = static_cast<ara::PairHot*>(c->pairs_hot.ptr);
-  ix.scan_tmp = static_cast<uint32_t*>(c->scan_tmp.ptr);
-  ix.n_words = n_words;
-  ix.n_recs = n_recs;
   // ---- outputs
-  const int64_t n_out = t1 - t0;
+  const int64_t n_out = pl.n_out;
   const bool ylt_dev = is_device_ptr(ylt_out);
   double* d_ylt = ylt_out;
   if (!ylt_dev) {
@@ -490,52 +606,16 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
     if (diag->hits) d_hits = hits_dev ? diag->hits : static_cast<int64_t*>(c->diag_tmp.ptr);
     if (diag->hit_hash) d_hash = hash_dev ? diag->hit_hash : reinterpret_cast<uint64_t*>(static_cast<int64_t*>(c->diag_tmp.ptr) + n_out);
   }
-  // ---- launch
-  cudaEvent_t ia, ib, ka, kb;
-  if (!timed_pair(c, 1, &ia, &ib) || !timed_pair(c, 0, &ka, &kb))
-    return fail(c, ARA_ECUDA, "ara_run_layer: cannot create timing events");
-  int launched = 0;
-  ARA_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
-  ARA_CUDA(c, cudaEventRecord(ia, c->stream));
-  ARA_CUDA(c, ara::build_layer_index(refs, ix, c->stream, &launched));
-  ARA_CUDA(c, cudaEventRecord(ib, c->stream));
-  ARA_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
-  // ---- layer kernels: gather (YET -> hit-event records), then losses
-  const int filt_words = ara::gather_filter_words(n_words, c->max_smem);
-  const size_t smem = ara::gather_smem_bytes(filt_words);
-  if (smem > static_cast<size_t>(c->max_smem))
-    return fail(c, ARA_ECUDA, "ara_run_layer: kernel needs %zu bytes of shared memory, device allows %d", smem,
-                c->max_smem);
-  const int64_t n_tiles = (n_out + ara::kWarpTrials - 1) / ara::kWarpTrials;
-  const int64_t e0 = c->h_off[t0], e1 = c->h_off[t1];
-  if ((rc = reserve(c, c->ev_buf, sizeof(uint2) * (e1 - e0 + 1))) ||
-      (rc = reserve(c, c->tile_cnt, sizeof(uint32_t) * (n_tiles + 1))) ||
-      (rc = reserve(c, c->def_acc, sizeof(double) * (n_out + 1))))
-    return rc;
-  unsigned long long* counters = static_cast<unsigned long long*>(c->counters.ptr);
-  ara::GatherParams g{};
-  g.off = static_cast<const int64_t*>(c->yet_off.ptr);
-  g.ids = static_cast<const int32_t*>(c->yet_ids.ptr);
-  g.t_begin = t0;
-  g.t_end = t1;
-  g.n_tiles = n_tiles;
-  g.e0 = e0;
-  g.rankdir = ix.rankdir;
-  g.n_words = n_words;
-  g.slot_start = ix.slot_cnt;
-  g.filt_words = filt_words;
-  g.ev_buf = static_cast<uint2*>(c->ev_buf.ptr);
-  g.tile_cnt = static_cast<uint32_t*>(c->tile_cnt.ptr);
-  g.queue = counters + 4;
-  p.off = g.off;
+  // ---- losses parameters
+  p.off = pl.g.off;
   p.t_begin = t0;
   p.t_end = t1;
-  p.n_tiles = n_tiles;
-  p.e0 = e0;
-  p.ev_buf = g.ev_buf;
-  p.tile_cnt = g.tile_cnt;
-  p.pairs = ix.pairs;
-  p.hot = ix.hot;
+  p.n_tiles = pl.n_tiles;
+  p.e0 = pl.e0;
+  p.ev_buf = pl.g.ev_buf;
+  p.tile_cnt = pl.g.tile_cnt;
+  p.pairs = pl.ix.pairs;
+  p.hot = pl.ix.hot;
   p.n_elts = L->n_elts;
   p.occ_r = static_cast<float>(L->occ_retention);
   p.occ_l = static_cast<float>(L->occ_limit);
@@ -543,34 +623,27 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   p.agg_l = L->agg_limit;
   p.seed_lo = static_cast<uint32_t>(seed & 0xFFFFFFFFull);
   p.seed_hi = static_cast<uint32_t>(seed >> 32);
-  for (int r = 0; r < 10; ++r) {  // Weyl key schedule of Philox4x32
-    p.rk[2 * r] = p.seed_lo + static_cast<uint32_t>(r) * 0x9E3779B9u;
-    p.rk[2 * r + 1] = p.seed_hi + static_cast<uint32_t>(r) * 0xBB67AE85u;
-  }
+  fill_philox_keys(seed, p.rk);
   p.primary_only = (L->flags & ARA_PRIMARY_ONLY) ? 1 : 0;
   p.newton_only = (L->flags & ARA_NEWTON_ONLY) ? 1 : 0;
   p.ylt = d_ylt;
   p.def_acc = static_cast<double*>(c->def_acc.ptr);
   p.diag_hits = d_hits;
   p.diag_hash = d_hash;
-  p.counters = counters;
-  ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 8 * sizeof(unsigned long long), c->stream));
-  const int64_t warps_per_sm = ara::kGatherThreads / 32;
-  const int grid = static_cast<int>(std::min<int64_t>(c->num_sms, (n_tiles + warps_per_sm - 1) / warps_per_sm));
+  p.counters = static_cast<unsigned long long*>(c->counters.ptr);
   const int64_t loss_warps = ara::kLossThreads / 32;
   const int loss_grid = static_cast<int>(std::min<int64_t>(c->num_sms * ara::kLossBlocksPerSm,
-                                                           (n_tiles + loss_warps - 1) / loss_warps));
+                                                           (pl.n_tiles + loss_warps - 1) / loss_warps));
+  // ---- launch
+  int launched = 0;
+  if ((rc = launch_index_and_gather(c, pl, who, &launched))) return rc;
   cudaEvent_t la, lb;
-  if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "ara_run_layer: cannot create timing events");
-  ARA_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
-  ARA_CUDA(c, cudaEventRecord(ka, c->stream));
-  ARA_CUDA(c, ara::launch_gather(g, grid, smem, c->stream));
-  ARA_CUDA(c, cudaEventRecord(kb, c->stream));
+  if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
   ARA_CUDA(c, cudaEventRecord(la, c->stream));
   ARA_CUDA(c, ara::launch_losses(p, loss_grid, c->stream));
   ARA_CUDA(c, cudaEventRecord(lb, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
-  launched += 2;
+  launched += 1;
   c->launches += launched;
   if (!ylt_dev)
     ARA_CUDA(c, cudaMemcpyAsync(ylt_out, d_ylt, sizeof(double) * n_out, cudaMemcpyDeviceToHost, c->stream));
@@ -579,20 +652,129 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   if (d_hash && !hash_dev)
     ARA_CUDA(c, cudaMemcpyAsync(diag->hit_hash, d_hash, sizeof(uint64_t) * n_out, cudaMemcpyDeviceToHost, c->stream));
   if (!ylt_dev || (d_hits && !hits_dev) || (d_hash && !hash_dev)) ARA_CUDA(c, cudaStreamSynchronize(c->stream));
-  // ---- stats (device times are read lazily by ara_get_stats)
-  c->stats = ara_stats{};
-  c->stats.n_events = c->h_off[t1] - c->h_off[t0];
-  c->stats.n_evals = c->stats.n_events * L->n_elts;
-  c->stats.grid = grid;
-  c->stats.block = ara::kGatherThreads;
-  c->stats.smem_bytes = static_cast<int32_t>(smem);
-  c->stats.filter_bits = filt_words * 32;
-  c->stats.kernel_ms = -1.0f;
+  record_pass_stats(c, pl, t0, t1, L->n_elts);
+  return ARA_OK;
+}
+
+// Fixed-point exponent of a batched layer: a trial's sum of occurrence losses
+// is counted as O * 2^e in 64 bits.  O is at most O_max (the layer's occurrence
+// limit, or its largest possible event loss above the retention), a trial has
+// at most n_max events, so e = 61 - ceil(log2(n_max + 1)) - ceil(log2(O_max))
+// keeps every sum below 2^61.
+static int batch_scale_exp(double o_max, int64_t n_max) {
+  if (!(o_max > 0.0) || !std::isfinite(o_max)) return 0;
+  const int e = 61 - static_cast<int>(std::ceil(std::log2(static_cast<double>(n_max) + 1.0))) -
+                static_cast<int>(std::ceil(std::log2(o_max)));
+  return std::max(-1000, std::min(1000, e));
+}
+
+static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers, uint64_t seed, int64_t t0,
+                           int64_t t1, double* ylt_out) {
+  static const char* who = "ara_run_layers";
+  int rc = bind(c);
+  if (rc) return rc;
+  if (n_layers < 1 || n_layers > ARA_MAX_BATCH_LAYERS || !layers || !ylt_out)
+    return fail(c, ARA_EINVAL, "%s: need 1..%d layers and ylt_out", who, ARA_MAX_BATCH_LAYERS);
+  if ((rc = check_trial_range(c, t0, t1, who))) return rc;
+  std::vector<std::vector<int32_t>> lids(n_layers);
+  std::vector<int32_t> uni;
+  for (int32_t l = 0; l < n_layers; ++l) {
+    if ((rc = check_layer(c, &layers[l], who, &lids[l]))) return rc;
+    if (layers[l].flags != layers[0].flags) return fail(c, ARA_EINVAL, "%s: the layers' flags differ", who);
+    uni.insert(uni.end(), lids[l].begin(), lids[l].end());
+  }
+  std::sort(uni.begin(), uni.end());
+  uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+  if (uni.size() > static_cast<size_t>(ARA_MAX_BATCH_ELTS))
+    return fail(c, ARA_EINVAL, "%s: the layers cover %zu ELTs (at most %d)", who, uni.size(), ARA_MAX_BATCH_ELTS);
+  PassPlan pl;
+  if ((rc = plan_pass(c, uni, t0, t1, who, &pl))) return rc;
+  ara::BatchParams p{};
+  std::vector<float> gmax(n_layers, 0.0f);
+  for (size_t i = 0; i < uni.size(); ++i) {
+    const Elt& el = c->pool.find(uni[i])->second;
+    p.elt_id[i] = uni[i];
+    p.tab[i] = static_cast<const float4*>(el.tab.ptr);
+    p.tabf[i] = static_cast<const float4*>(el.tabf.ptr);
+    p.t_ret[i] = el.terms.retention;
+    p.t_lim[i] = el.terms.limit;
+    p.t_share[i] = el.terms.share;
+  }
+  for (int32_t l = 0; l < n_layers; ++l) {
+    const ara_layer& L = layers[l];
+    double g_max = 0.0;  // the layer's largest possible event loss after ELT terms
+    for (int32_t id : lids[l]) {
+      const size_t pos = std::lower_bound(uni.begin(), uni.end(), id) - uni.begin();
+      p.layers_of[pos] |= 1ull << l;
+      const Elt& el = c->pool.find(id)->second;
+      const double lj = std::min(static_cast<double>(el.terms.limit),
+                                 std::max(0.0, static_cast<double>(el.max_loss) - el.terms.retention));
+      g_max += static_cast<double>(el.terms.share) * lj;
+    }
+    const double o_max = std::min(L.occ_limit, std::max(0.0, g_max - L.occ_retention));
+    p.occ_r[l] = static_cast<float>(L.occ_retention);
+    p.occ_l[l] = static_cast<float>(L.occ_limit);
+    p.agg_r[l] = L.agg_retention;
+    p.agg_l[l] = L.agg_limit;
+    p.scale_exp[l] = batch_scale_exp(o_max, c->max_trial_events);
+    p.inv_scale[l] = std::ldexp(1.0, -p.scale_exp[l]);
+  }
+  // ---- outputs
+  const int64_t n_out = pl.n_out;
+  const bool ylt_dev = is_device_ptr(ylt_out);
+  double* d_ylt = ylt_out;
+  if (!ylt_dev) {
+    if ((rc = reserve(c, c->ylt_tmp, sizeof(double) * n_out * n_layers))) return rc;
+    d_ylt = static_cast<double*>(c->ylt_tmp.ptr);
+  }
+  p.off = pl.g.off;
+  p.t_begin = t0;
+  p.t_end = t1;
+  p.n_tiles = pl.n_tiles;
+  p.e0 = pl.e0;
+  p.ev_buf = pl.g.ev_buf;
+  p.tile_cnt = pl.g.tile_cnt;
+  p.pairs = pl.ix.pairs;
+  p.hot = pl.ix.hot;
+  p.n_elts = static_cast<int32_t>(uni.size());
+  p.n_layers = n_layers;
+  fill_philox_keys(seed, p.rk);
+  p.primary_only = (layers[0].flags & ARA_PRIMARY_ONLY) ? 1 : 0;
+  p.newton_only = (layers[0].flags & ARA_NEWTON_ONLY) ? 1 : 0;
+  p.ylt = d_ylt;
+  p.n_out = n_out;
+  p.counters = static_cast<unsigned long long*>(c->counters.ptr);
+  const int64_t warps = ara::kBatchThreads / 32;
+  const int grid = static_cast<int>(std::min<int64_t>(c->num_sms * ara::kBatchBlocksPerSm,
+                                                      (pl.n_tiles + warps - 1) / warps));
+  int launched = 0;
+  if ((rc = launch_index_and_gather(c, pl, who, &launched))) return rc;
+  cudaEvent_t la, lb;
+  if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
+  ARA_CUDA(c, cudaEventRecord(la, c->stream));
+  ARA_CUDA(c, ara::launch_losses_batch(p, grid, c->stream));
+  ARA_CUDA(c, cudaEventRecord(lb, c->stream));
+  ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
+  launched += 1;
+  c->launches += launched;
+  if (!ylt_dev) {
+    ARA_CUDA(c, cudaMemcpyAsync(ylt_out, d_ylt, sizeof(double) * n_out * n_layers, cudaMemcpyDeviceToHost,
+                                c->stream));
+    ARA_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  int64_t elts = 0;
+  for (int32_t l = 0; l < n_layers; ++l) elts += static_cast<int64_t>(lids[l].size());
+  record_pass_stats(c, pl, t0, t1, elts);
   return ARA_OK;
 }
 
 int ara_run_layer(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out) {
   return run_layer_impl(c, L, seed, t0, t1, ylt_out, nullptr);
+}
+
+int ara_run_layers(ara_ctx* c, int32_t n_layers, const ara_layer* layers, uint64_t seed, int64_t t0, int64_t t1,
+                   double* ylt_out) {
+  return run_layers_impl(c, n_layers, layers, seed, t0, t1, ylt_out);
 }
 
 int ara_run_layer_diag(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out,
@@ -784,7 +966,8 @@ int ara_debug_record_losses(ara_ctx* c, int64_t n, const float* mean, const floa
   for (int64_t i = 0; i < n; ++i) ev[i] = static_cast<int32_t>(i);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_ev, ev.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, 2 * sizeof(uint32_t), c->stream);
-  if (e == cudaSuccess) e = ara::launch_prepare_records(d_ev, d_mu, d_sg, d_ex, n, d_p, d_sh, flags, max_ev, c->stream);
+  if (e == cudaSuccess)
+    e = ara::launch_prepare_records(d_ev, d_mu, d_sg, d_ex, n, d_p, d_sh, flags, max_ev, nullptr, c->stream);
   int launched = 2;
   if (e == cudaSuccess) e = ara::launch_build_tables(d_p, d_sh, n, d_tab, d_tabf, d_work, c->stream, &launched);
   if (e == cudaSuccess) e = ara::launch_debug_losses(d_p, d_tab, d_tabf, d_z, n, newton_only, d_o, d_it, c->stream);

@@ -51,8 +51,8 @@ struct __align__(16) Pair {
   float max_l;    // exposure (maximum loss)
   float mu;       // mean loss
   float p_half;   // I_{1/2}(a, b)
-  uint32_t meta;  // bits 0-4 layer position, 5-6 kind, 7: fine table, 8: table exact, 9-31 record index
-                  // (the fine-table slot when bit 7 is set)
+  uint32_t meta;  // bits 0-5 position in the layer (or batch), 6-7 kind, 8: fine table, 9: table exact,
+                  // 10-31 record index (the fine-table slot when bit 8 is set)
 };
 static_assert(sizeof(Pair) == 32, "Pair must be one 32-byte sector");
 
@@ -65,13 +65,15 @@ struct __align__(16) PairHot {
   uint32_t node;  // first node of the record's quantile table (coarse or fine table of its ELT)
 };
 
-constexpr uint32_t kMaxEltRecords = 1u << 23;  // record index field of meta
+constexpr uint32_t kMaxEltRecords = 1u << 22;  // record index field of meta
+constexpr uint32_t kMetaPosMask = 63u;          // positions 0..63
+constexpr uint32_t kMetaKindShift = 6, kMetaFineBit = 8, kMetaExactBit = 9, kMetaRecShift = 10;
 
-__host__ __device__ inline uint32_t pair_pos(uint32_t meta) { return meta & 31u; }
-__host__ __device__ inline uint32_t pair_kind(uint32_t meta) { return (meta >> 5) & 3u; }
-__host__ __device__ inline bool pair_fine(uint32_t meta) { return (meta >> 7) & 1u; }
-__host__ __device__ inline bool pair_tab_exact(uint32_t meta) { return (meta >> 8) & 1u; }
-__host__ __device__ inline uint32_t pair_rec(uint32_t meta) { return meta >> 9; }
+__host__ __device__ inline uint32_t pair_pos(uint32_t meta) { return meta & kMetaPosMask; }
+__host__ __device__ inline uint32_t pair_kind(uint32_t meta) { return (meta >> kMetaKindShift) & 3u; }
+__host__ __device__ inline bool pair_fine(uint32_t meta) { return (meta >> kMetaFineBit) & 1u; }
+__host__ __device__ inline bool pair_tab_exact(uint32_t meta) { return (meta >> kMetaExactBit) & 1u; }
+__host__ __device__ inline uint32_t pair_rec(uint32_t meta) { return meta >> kMetaRecShift; }
 
 // ------------------------------------------------------------------ tables
 constexpr int kTabNodes = 32;

@@ -26,10 +26,12 @@ cudaError_t launch_check_ids(const int32_t* ids, int64_t n, int32_t catalogue, u
 
 // Prepare the Pair records of one ELT from (mean, sigma, exposure) in FP64:
 // Beta shapes, x0/y0, C, I_{1/2}(a, b), kind.  Also checks order and values
-// and reduces the largest event id into *max_event (atomicMax).
+// and reduces the largest event id into *max_event and the largest loss a
+// record can produce (max(exposure, mean) over records with a loss, as FP32
+// bits) into *max_loss (both atomicMax; max_loss may be null).
 cudaError_t launch_prepare_records(const int32_t* events, const float* mean, const float* sigma,
                                    const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
-                                   int32_t* max_event, cudaStream_t s);
+                                   int32_t* max_event, uint32_t* max_loss, cudaStream_t s);
 
 // Quantile tables of prepared records, built in FP64: kTabNodes float4 per
 // record in `tab`; then, for the first fine_table_cap(n) records (in record
@@ -75,11 +77,13 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uin
                                int* n_launch = nullptr);
 
 // --------------------------------------------------------------- layer index
+constexpr int kMaxIndexElts = 64;  // ELT positions of one index (a layer, or the union of a batch of layers)
+
 struct LayerEltRefs {
   int32_t n_elts;
-  const int32_t* events[32];  // sorted event ids of the layer's ELT at position p
-  const Pair* recs[32];       // prepared records (meta carries the record index)
-  int64_t rec_begin[33];      // prefix sums of record counts over positions
+  const int32_t* events[kMaxIndexElts];  // sorted event ids of the ELT at position p
+  const Pair* recs[kMaxIndexElts];       // prepared records (meta carries the record index)
+  int64_t rec_begin[kMaxIndexElts + 1];  // prefix sums of record counts over positions
 };
 
 struct LayerIndex {
@@ -88,7 +92,7 @@ struct LayerIndex {
   uint32_t* word_pairs;  // [n_words + 1] scratch: pairs per word, then exclusive scan
   uint2* rankdir;        // [n_words] {bits, base}: base = pairs before the word, or (1 << 31) | slots
                          // before the word when the word holds an event with several ELT records
-  uint32_t* mask;        // [n_recs] per slot: bitmask of layer positions
+  unsigned long long* mask;  // [n_recs] per slot: bitmask of layer positions
   uint32_t* slot_cnt;    // [n_recs + 1] scratch -> slot_start
   Pair* pairs;           // [n_recs]
   PairHot* hot;          // [n_recs] the table-path part of each pair
@@ -110,6 +114,12 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
 constexpr int kGatherThreads = 1024;  // 32 warps per CTA, one CTA per SM
 constexpr int kLossThreads = 256;
 constexpr int kLossBlocksPerSm = 3;  // 24 warps per SM at up to 85 registers: no spills in the loss loop
+// Hit-event record written by k_gather: x = (trial in tile << 28) |
+// ((ELT pairs - 1) << 22) | event index in the trial; y = first pair.
+constexpr uint32_t kRecTrialShift = 28;
+constexpr uint32_t kRecCntShift = 22;
+constexpr uint32_t kRecCntMask = 63u;
+constexpr uint32_t kRecKMask = (1u << 22) - 1u;
 constexpr int kWarpTrials = 8;        // trials per tile (< 32)
 constexpr int kMaxTrialEvents = 1 << 22;
 
@@ -152,6 +162,41 @@ struct LossParams {
   uint64_t* diag_hash;
   unsigned long long* counters;  // [0] tile queue, [1] pairs, [2] non-converged, [3] Halley events
 };
+
+// Batched layers (one pass for several layers over the union of their ELTs):
+// k_gather as above over the union's index, then k_losses_batch.
+constexpr int kBatchLayers = 32;  // ARA_MAX_BATCH_LAYERS
+constexpr int kBatchThreads = 128;
+constexpr int kBatchBlocksPerSm = 6;
+
+struct BatchParams {
+  const int64_t* off;
+  int64_t t_begin, t_end, n_tiles;
+  int64_t e0;
+  const uint2* ev_buf;
+  const uint32_t* tile_cnt;
+  const Pair* pairs;
+  const PairHot* hot;
+  int32_t n_elts;  // union positions
+  int32_t n_layers;
+  int32_t elt_id[kMaxIndexElts];
+  const float4* tab[kMaxIndexElts];
+  const float4* tabf[kMaxIndexElts];
+  float t_ret[kMaxIndexElts], t_lim[kMaxIndexElts], t_share[kMaxIndexElts];
+  unsigned long long layers_of[kMaxIndexElts];  // per union position: bitmask of the layers holding it
+  float occ_r[kBatchLayers], occ_l[kBatchLayers];
+  double agg_r[kBatchLayers], agg_l[kBatchLayers];
+  int32_t scale_exp[kBatchLayers];     // fixed point: a layer's occurrence loss O is counted as O * 2^scale_exp
+  double inv_scale[kBatchLayers];      // 2^-scale_exp
+  uint32_t rk[20];                     // Philox round keys of the seed
+  int32_t primary_only;
+  int32_t newton_only;
+  double* ylt;                         // layer-major, stride n_out
+  int64_t n_out;
+  unsigned long long* counters;        // [0] tile queue, [1] pairs, [2] non-converged
+};
+
+cudaError_t launch_losses_batch(const BatchParams& p, int grid, cudaStream_t s);
 
 size_t gather_smem_bytes(int filt_words);
 int gather_filter_words(int64_t n_words, int max_smem);

@@ -141,10 +141,11 @@ __device__ double beta_cf_f64(double a, double b, double x) {
 // alpha = mu_b ((sigma_bmax / sigma_b)^2 - 1), beta = (1 - mu_b)(...).
 __global__ void k_prepare_records(const int32_t* events, const float* mean, const float* sigma,
                                   const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
-                                  int32_t* max_event) {
+                                  int32_t* max_event, uint32_t* max_loss) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   uint32_t f = 0;
   int32_t emax = -1;
+  float lmax = 0.0f;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
     const int32_t e = events[i];
     emax = max(emax, e);
@@ -192,23 +193,29 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
       p.c = static_cast<float>(c);
       p.p_half = static_cast<float>(ph);
     }
-    p.meta = (kind << 5) | (static_cast<uint32_t>(i) << 9);
+    p.meta = (kind << kMetaKindShift) | (static_cast<uint32_t>(i) << kMetaRecShift);
+    if (kind != kKindZero) lmax = fmaxf(lmax, fmaxf(p.max_l, p.mu));
     out[i] = p;
     if (shapes) shapes[i] = make_double2(sa, sb_);
   }
   if (f) atomicOr(flags, f);
   // block max of event ids, then one atomic per warp
-  for (int d = 16; d > 0; d >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, d));
+  for (int d = 16; d > 0; d >>= 1) {
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, d));
+    lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, d));
+  }
   if ((threadIdx.x & 31) == 0 && emax >= 0) atomicMax(max_event, emax);
+  // non-negative floats order as their bit patterns
+  if ((threadIdx.x & 31) == 0 && max_loss && lmax > 0.0f) atomicMax(max_loss, __float_as_uint(lmax));
 }
 
 cudaError_t launch_prepare_records(const int32_t* events, const float* mean, const float* sigma,
                                    const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
-                                   int32_t* max_event, cudaStream_t s) {
+                                   int32_t* max_event, uint32_t* max_loss, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int64_t blocks = (n + 127) / 128;
   k_prepare_records<<<static_cast<int>(blocks < 65535 ? blocks : 65535), 128, 0, s>>>(
-      events, mean, sigma, exposure, n, out, shapes, flags, max_event);
+      events, mean, sigma, exposure, n, out, shapes, flags, max_event, max_loss);
   return cudaGetLastError();
 }
 
@@ -384,7 +391,7 @@ __global__ void __launch_bounds__(256, 4) k_build_tables(Pair* recs, const doubl
                                          : (isfinite(node.x) && isfinite(node.z) && isfinite(node.w));
   const bool all_ok = __all_sync(0xffffffffu, ok);
   if (lane == 0) {
-    if (all_ok) recs[rec].meta = pr.meta | (1u << 8);
+    if (all_ok) recs[rec].meta = pr.meta | (1u << kMetaExactBit);
     need[rec] = all_ok ? 0u : 1u;
   }
 }
@@ -447,7 +454,9 @@ __global__ void __launch_bounds__(kTabFineStride) k_build_fine(Pair* recs, const
   }
   if (j < kTabFineNodes) tabf[gb * kTabFineStride + j] = node;
   const bool all_ok = __syncthreads_and(ok) != 0;
-  if (j == 0) recs[rec].meta = (pr.meta & 0x7Fu) | (1u << 7) | (all_ok ? (1u << 8) : 0u) | (ls << 9);
+  if (j == 0)
+    recs[rec].meta = (pr.meta & ((1u << kMetaFineBit) - 1u)) | (1u << kMetaFineBit) |
+                     (all_ok ? (1u << kMetaExactBit) : 0u) | (ls << kMetaRecShift);
 }
 
 size_t build_tables_work_words(int64_t n) {
@@ -668,23 +677,25 @@ __device__ __forceinline__ uint32_t rank_of(const uint32_t* bits, const uint32_t
   return slot_base[e >> 5] + __popc(bits[e >> 5] & (bit - 1u));
 }
 
-__global__ void k_mark_positions(LayerEltRefs r, const uint32_t* bits, const uint32_t* slot_base, uint32_t* mask) {
+__global__ void k_mark_positions(LayerEltRefs r, const uint32_t* bits, const uint32_t* slot_base,
+                                 unsigned long long* mask) {
   const int64_t n = r.rec_begin[r.n_elts];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
     const int p = find_pos(r, i);
     const int32_t e = r.events[p][i - r.rec_begin[p]];
-    atomicOr(&mask[rank_of(bits, slot_base, e)], 1u << p);
+    atomicOr(&mask[rank_of(bits, slot_base, e)], 1ull << p);
   }
 }
 
-__global__ void k_slot_counts(const uint32_t* mask, int64_t n, uint32_t* cnt) {
+__global__ void k_slot_counts(const unsigned long long* mask, int64_t n, uint32_t* cnt) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride)
-    cnt[i] = __popc(mask[i]);
+    cnt[i] = __popcll(mask[i]);
 }
 
-__global__ void k_fill_pairs(LayerEltRefs r, const uint32_t* bits, const uint32_t* slot_base, const uint32_t* mask,
+__global__ void k_fill_pairs(LayerEltRefs r, const uint32_t* bits, const uint32_t* slot_base,
+                             const unsigned long long* mask,
                              const uint32_t* slot_start, Pair* pairs, PairHot* hot) {
   const int64_t n = r.rec_begin[r.n_elts];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -693,9 +704,9 @@ __global__ void k_fill_pairs(LayerEltRefs r, const uint32_t* bits, const uint32_
     const int64_t j = i - r.rec_begin[p];
     const int32_t e = r.events[p][j];
     const uint32_t slot = rank_of(bits, slot_base, e);
-    const uint32_t within = __popc(mask[slot] & ((1u << p) - 1u));
+    const uint32_t within = __popcll(mask[slot] & ((1ull << p) - 1ull));
     Pair q = r.recs[p][j];
-    q.meta = (q.meta & ~31u) | static_cast<uint32_t>(p);
+    q.meta = (q.meta & ~kMetaPosMask) | static_cast<uint32_t>(p);
     const uint32_t at = slot_start[slot] + within;
     pairs[at] = q;
     PairHot hq;
@@ -719,7 +730,8 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
   cudaError_t err;
   if ((err = cudaMemsetAsync(ix.bits, 0, sizeof(uint32_t) * ix.n_words, s)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(ix.word_pairs, 0, sizeof(uint32_t) * (ix.n_words + 1), s)) != cudaSuccess) return err;
-  if ((err = cudaMemsetAsync(ix.mask, 0, sizeof(uint32_t) * (n_recs > 0 ? n_recs : 1), s)) != cudaSuccess)
+  if ((err = cudaMemsetAsync(ix.mask, 0, sizeof(unsigned long long) * (n_recs > 0 ? n_recs : 1), s)) !=
+      cudaSuccess)
     return err;
   int launched = 0;
   if (n_recs > 0) {

@@ -52,9 +52,6 @@ namespace {
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
-constexpr uint32_t kRecTrialShift = 27;
-constexpr uint32_t kRecCntShift = 22;
-constexpr uint32_t kRecKMask = (1u << 22) - 1u;
 
 struct GatherWarp {
   int32_t off[16];  // trial offsets relative to the tile's first event; INT32_MAX past the tile's end
@@ -354,7 +351,7 @@ __device__ __noinline__ void resolve_deferred(const LossParams& p, LossWarp& ws,
   if (lane < static_cast<uint32_t>(nd)) {
     const uint32_t key = ws.d_key[lane];
     const uint32_t k = key & kRecKMask;
-    const uint32_t cnt = ((key >> kRecCntShift) & 31u) + 1u;
+    const uint32_t cnt = ((key >> kRecCntShift) & kRecCntMask) + 1u;
     const int64_t t = p.t_begin + ws.d_o[lane];
     float G = 0.0f;
     for (uint32_t j = 0; j < cnt; ++j) G += pair_slow(p, p.pairs[ws.d_ps[lane] + j], t, k, nc);
@@ -468,7 +465,7 @@ __device__ __forceinline__ int2 process_multi(const LossParams& p, const EltShar
   for (int i0 = 0; i0 < nq;) {
     const int ie = i0 + static_cast<int>(q);
     const uint2 r = (ie < nq) ? ws.mq[ie] : make_uint2(0u, 0u);
-    const uint32_t cnt = (ie < nq) ? ((r.x >> kRecCntShift) & 31u) + 1u : 0u;
+    const uint32_t cnt = (ie < nq) ? ((r.x >> kRecCntShift) & kRecCntMask) + 1u : 0u;
     const uint32_t incl = warp_inclusive_scan(cnt);
     const uint32_t pre = incl - cnt;
     const bool take = cnt != 0 && incl <= 32u;
@@ -587,7 +584,7 @@ __global__ void __launch_bounds__(kLossThreads, kLossBlocksPerSm) k_losses(const
     uint2 r0 = (lane < n) ? __ldcs(recs + lane) : make_uint2(0u, 0u);
     uint2 r1 = (32 + lane < n) ? __ldcs(recs + 32 + lane) : make_uint2(0u, 0u);
     PairHot h0{0.0f, 0.0f, kKindZero << 5, 0u};
-    if (lane < n && ((r0.x >> kRecCntShift) & 31u) == 0u) h0 = p.hot[r0.y];
+    if (lane < n && ((r0.x >> kRecCntShift) & kRecCntMask) == 0u) h0 = p.hot[r0.y];
     for (uint32_t base = 0;;) {
 #pragma unroll 1
       for (; base < n && nq <= kQueue - 32; base += 32) {
@@ -596,8 +593,8 @@ __global__ void __launch_bounds__(kLossThreads, kLossBlocksPerSm) k_losses(const
         const bool valid = base + lane < n;
         r0 = r1;
         if (base + 64 + lane < n) r1 = __ldcs(recs + base + 64 + lane);
-        if (base + 32 + lane < n && ((r0.x >> kRecCntShift) & 31u) == 0u) h0 = p.hot[r0.y];
-        const uint32_t cnt = ((r.x >> kRecCntShift) & 31u) + 1u;
+        if (base + 32 + lane < n && ((r0.x >> kRecCntShift) & kRecCntMask) == 0u) h0 = p.hot[r0.y];
+        const uint32_t cnt = ((r.x >> kRecCntShift) & kRecCntMask) + 1u;
         const uint32_t tl = r.x >> kRecTrialShift, k = r.x & kRecKMask;
         const bool single = valid && cnt == 1u;
         bool slow = false;

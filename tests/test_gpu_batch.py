@@ -1,0 +1,166 @@
+"""GPU parity of batched layers (ara_run_layers: several layers in one pass
+over the YET) against the FP64 oracle run layer by layer, and against the
+single-layer path.  Same tolerances as the single-layer parity tests: each
+year loss within 1e-5 of max(|Y|, gross loss) of its layer's oracle run.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1501_06326_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+YLT_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1501_06326_gb300 import ara
+
+    e = ara.Ara(0)
+    yield e
+    e.close()
+
+
+def check_ylt(ylt, ref, tol=YLT_TOL):
+    scale = np.maximum(np.abs(ref["ylt"]), ref["gross"])
+    err = np.abs(ylt - ref["ylt"])
+    bad = err > tol * scale
+    worst = float(np.max(err / np.where(scale > 0, scale, 1.0))) if err.size else 0.0
+    assert not bad.any(), f"{bad.sum()} trials out of tolerance, worst {worst:.3e}"
+    return worst
+
+
+def _batch_case(n_trials, catalogue, mean_events, n_elts, entries, n_layers, max_elts, seed, recipe="plain"):
+    yet = synth.make_yet(n_trials, mean_events, catalogue, seed)
+    pool = synth.make_elt_pool(n_elts, entries, catalogue, seed + 1, recipe=recipe)
+    layer_ids = synth.draw_layers(n_layers, pool.elt_ids, max_elts, seed + 2)
+    layers = []
+    for ids in layer_ids:
+        sub = pool.subset([int(np.flatnonzero(pool.elt_ids == i)[0]) for i in ids])
+        layers.append((ids, oracle.calibrate_layer_terms(yet, sub), sub))
+    return yet, pool, layers
+
+
+def _run_batch(eng, yet, pool, layers, seed, t0=0, t1=None, **kw):
+    t1 = yet.n_trials if t1 is None else t1
+    eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
+    eng.load_pool(pool)
+    out = np.zeros((len(layers), t1 - t0))
+    eng.run_layers([(ids, terms) for ids, terms, _ in layers], seed, t0, t1, out, **kw)
+    return out
+
+
+@pytest.fixture(scope="module")
+def small_batch():
+    # 1,000 trials x Poisson(100) over a catalogue of 10,000; a pool of 12 ELTs x 1,000
+    # records; 6 layers of 1..8 ELTs (overlapping), terms per layer
+    return _batch_case(1000, 10_000, 100.0, 12, 1000, 6, 8, 4242)
+
+
+def test_batch_matches_oracle_layer_by_layer(eng, small_batch):
+    yet, pool, layers = small_batch
+    for seed in (0, 77):
+        out = _run_batch(eng, yet, pool, layers, seed)
+        for l, (ids, terms, sub) in enumerate(layers):
+            ref = oracle.run_layer(yet, sub, terms, seed=seed)
+            check_ylt(out[l], ref)
+
+
+def test_batch_matches_the_single_layer_path(eng, small_batch):
+    # the two paths differ only in the FP32 rounding of multi-ELT event sums and in
+    # how a trial's sum is carried, so they agree well inside the oracle tolerance
+    # (scaled, as there, by the trial's gross loss: terms are 1-Lipschitz)
+    yet, pool, layers = small_batch
+    out = _run_batch(eng, yet, pool, layers, 5)
+    for l, (ids, terms, sub) in enumerate(layers):
+        single = np.zeros(yet.n_trials)
+        eng.run_layer(ids, terms, 5, 0, yet.n_trials, single)
+        gross = oracle.run_layer(yet, sub, terms, seed=5)["gross"]
+        scale = np.maximum(np.abs(single), gross)
+        assert np.all(np.abs(out[l] - single) <= 1e-6 * scale + 1e-300)
+
+
+def test_batch_is_deterministic_and_order_free(eng, small_batch):
+    yet, pool, layers = small_batch
+    a = _run_batch(eng, yet, pool, layers, 3)
+    b = _run_batch(eng, yet, pool, layers, 3)
+    assert np.array_equal(a, b)
+    # listing the layers in another order permutes the outputs exactly
+    perm = [3, 0, 5, 1, 4, 2]
+    c = _run_batch(eng, yet, pool, [layers[i] for i in perm], 3)
+    assert np.array_equal(c, a[perm])
+
+
+def test_batch_subrange_primary_only_and_halley(eng, small_batch):
+    yet, pool, layers = small_batch
+    t0, t1 = 137, 911
+    out = _run_batch(eng, yet, pool, layers, 9, t0, t1, primary_only=True)
+    for l, (ids, terms, sub) in enumerate(layers):
+        ref = oracle.run_layer(yet, sub, terms, seed=9, primary_only=True, trials=np.arange(t0, t1))
+        check_ylt(out[l], ref)
+    out = _run_batch(eng, yet, pool, layers, 9, 0, 300, newton_only=True)
+    for l, (ids, terms, sub) in enumerate(layers):
+        ref = oracle.run_layer(yet, sub, terms, seed=9, trials=np.arange(0, 300))
+        check_ylt(out[l], ref)
+
+
+def test_batch_of_one_layer_and_of_full_layers(eng):
+    # one layer; then 32 layers, all 32 ELTs each (the batch limits), over a small YET
+    yet, pool, layers = _batch_case(300, 5000, 60.0, 32, 400, 1, 32, 777)
+    out = _run_batch(eng, yet, pool, layers, 1)
+    check_ylt(out[0], oracle.run_layer(yet, layers[0][2], layers[0][1], seed=1))
+    ids = pool.elt_ids
+    terms = oracle.calibrate_layer_terms(yet, pool)
+    full = [(ids, terms, pool)] * 32
+    out = _run_batch(eng, yet, pool, full, 1)
+    ref = oracle.run_layer(yet, pool, terms, seed=1)
+    for l in range(32):
+        check_ylt(out[l], ref)
+
+
+def test_paper_shaped_batch_sampled(eng):
+    # the paper-1m YET (first 2,000 trials), a pool of 64 ELTs x 10,000 records,
+    # 16 layers of 1..32 ELTs: the shapes of the batched workload
+    spec = synth.WORKLOADS["paper-1m"]
+    yet = synth.make_yet(2000, spec["mean_events"], spec["catalogue"], spec["seed"])
+    pool = synth.make_elt_pool(64, spec["entries"], spec["catalogue"], spec["seed"] + 7)
+    layer_ids = synth.draw_layers(16, pool.elt_ids, 32, spec["seed"] + 8)
+    layers = []
+    for ids in layer_ids:
+        sub = pool.subset([int(np.flatnonzero(pool.elt_ids == i)[0]) for i in ids])
+        layers.append((ids, oracle.calibrate_layer_terms(yet, sub), sub))
+    out = _run_batch(eng, yet, pool, layers, 0)
+    for l, (ids, terms, sub) in enumerate(layers):
+        check_ylt(out[l], oracle.run_layer(yet, sub, terms, seed=0))
+
+
+def test_batch_errors(eng, small_batch):
+    from paper_1501_06326_gb300 import ara
+
+    yet, pool, layers = small_batch
+    eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
+    eng.load_pool(pool)
+    out = np.zeros((40, 10))
+    spec = [(l[0], l[1]) for l in layers]
+    with pytest.raises(ara.AraError) as e:  # too many layers
+        eng.run_layers(spec * 7, 0, 0, 10, out)
+    assert e.value.code == ara.ARA_EINVAL
+    with pytest.raises(ara.AraError) as e:  # an ELT that is not loaded
+        eng.run_layers(spec + [([999], spec[0][1])], 0, 0, 10, out)
+    assert e.value.code == ara.ARA_ENOTLOADED
+    with pytest.raises(ara.AraError) as e:  # bad range
+        eng.run_layers(spec, 0, 5, 5, out)
+    assert e.value.code == ara.ARA_EINVAL
+    big = synth.make_elt_pool(70, 20, yet.catalogue_size, 5)
+    big.elt_ids = big.elt_ids + 1000
+    eng.load_pool(big)
+    wide = [(big.elt_ids[:32], spec[0][1]), (big.elt_ids[32:64], spec[0][1]), (big.elt_ids[64:], spec[0][1])]
+    with pytest.raises(ara.AraError) as e:  # union of 70 ELTs
+        eng.run_layers(wide, 0, 0, 10, out)
+    assert e.value.code == ara.ARA_EINVAL
