@@ -348,6 +348,11 @@ def run_gpu(args):
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
                "sample": f"first {min(args.cpu_trials, n_trials)} trials of the workload ({ev} evals, {dt:.1f} s)"}
 
+    # ---- batched layers (several layers in one pass over the YET) against one pass per layer
+    batched = None
+    if ws == 1 and not args.no_batched:
+        batched = _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -372,6 +377,8 @@ def run_gpu(args):
         }
         if global_pml is not None:
             line["global_pml_tvar"] = {"pml": list(global_pml[0]), "tvar": list(global_pml[1])}
+        if batched is not None:
+            line["batched"] = batched
         print(json.dumps(line))
     eng.close()
     if ws > 1:
@@ -379,6 +386,49 @@ def run_gpu(args):
 
         dist.destroy_process_group()
     return 0
+
+
+def _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args):
+    """The batched workload: 16 layers of 1..32 ELTs from a pool of 64, over the same
+    YET, as one ara_run_layers pass and as 16 ara_run_layer passes (device buffers,
+    CUDA events on the engine's stream)."""
+    spec = synth.WORKLOADS["batched-16"]
+    with open(os.path.join(ROOT, "tests", "golden", "workload_terms.json")) as fh:
+        spec_layers = json.load(fh)["batched-16"]["layers"]
+    pool = synth.make_elt_pool(spec["n_elts"], spec["entries"], spec["catalogue"], spec["elt_seed"],
+                               recipe=spec["recipe"])
+    eng.load_pool(pool)
+    layers = [(np.asarray(l["elt_ids"], np.int32), l["layer_terms"]) for l in spec_layers]
+    out = torch.empty((len(layers), n_trials), dtype=torch.float64, device=dev)
+
+    def batch_step():
+        eng.run_layers(layers, seed, 0, n_trials, out)
+
+    def plain_step():
+        for l, (ids, terms) in enumerate(layers):
+            eng.run_layer(ids, terms, seed, 0, n_trials, out[l])
+
+    def timed(fn, steps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / steps
+
+    steps = max(2, min(args.steps, 5))
+    ms_batch = timed(batch_step, steps)
+    ms_plain = timed(plain_step, steps)
+    evals = n_events * sum(len(ids) for ids, _ in layers)
+    return {"workload": f"batched-16: the {n_trials:,}-trial YET, 16 layers of 1..32 ELTs from a pool of "
+                        f"{spec['n_elts']} x {spec['entries']:,} records",
+            "layers": len(layers), "steps": steps, "ms_batched": ms_batch, "ms_plain": ms_plain,
+            "layers_per_s": len(layers) / (ms_batch * 1e-3), "plain_layers_per_s": len(layers) / (ms_plain * 1e-3),
+            "speedup": ms_plain / ms_batch, "evals_per_s": evals / (ms_batch * 1e-3)}
 
 
 def main(argv=None):
@@ -395,6 +445,7 @@ def main(argv=None):
                     help="truncate the YET (profiling of a smaller case); the default is the full workload")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-layers comparison")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -23,10 +23,8 @@ namespace {
 constexpr int kBatchQueue = 64;  // multi-ELT events queued per warp
 
 struct BatchWarp {
-  unsigned long long acc[kBatchLayers][kWarpTrials];  // per layer and trial: sum of occurrence losses (fixed point)
-  float gbuf[kBatchLayers][32];                       // per layer and lane: a multi-ELT event's loss sum
-  uint2 mq[kBatchQueue];                              // queued multi-ELT events (records)
-  int32_t tr_beg[kWarpTrials + 1];                    // first record of each trial of the tile
+  unsigned long long acc[kBatchLayers][32];  // per layer and lane: the lane's sum of occurrence losses (fixed point)
+  uint2 mq[kBatchQueue];                     // queued multi-ELT events (records)
 };
 
 struct BatchShared {
@@ -87,46 +85,125 @@ __device__ __forceinline__ float pair_loss_batch(const BatchParams& p, const Bat
   return bs.share[pos] * clamp_terms_f(loss, bs.ret[pos], bs.lim[pos]);
 }
 
-__device__ __forceinline__ void add_occurrence(BatchWarp& ws, const BatchShared& bs, int layer, uint32_t tl,
+// Adds a layer's occurrence loss (from the event's loss sum G over the
+// layer's ELTs) to a lane's fixed-point sum.
+__device__ __forceinline__ void add_occurrence(BatchWarp& ws, const BatchShared& bs, int layer, uint32_t lane,
                                                float G) {
   const float O = clamp_terms_f(G, bs.occ_r[layer], bs.occ_l[layer]);
-  if (O > 0.0f) atomicAdd(&ws.acc[layer][tl], fixed_of(O, bs.sexp[layer]));
+  if (O > 0.0f) ws.acc[layer][lane] += fixed_of(O, bs.sexp[layer]);
 }
 
-// The queued multi-ELT events, one per lane: the event's pair losses (each
-// once) are summed per layer in the pairs' (canonical) order, then each
-// layer's occurrence loss is added.
-__device__ __noinline__ void batch_multi(const BatchParams& p, const BatchShared& bs, BatchWarp& ws, int nq,
-                                         int64_t ta, unsigned long long* nc) {
+// A multi-ELT event with more pairs than a window holds, by one lane: for each
+// layer it touches, its pair losses over the layer's ELTs summed in the pairs'
+// order (each pair's loss recomputed per layer: such events are rare).
+__device__ __noinline__ void batch_long_event(const BatchParams& p, const BatchShared& bs, BatchWarp& ws, uint2 r,
+                                              int64_t trial, unsigned long long* nc) {
   const uint32_t lane = lane_id();
-  for (int i0 = 0; i0 < nq; i0 += 32) {
-    const int i = i0 + static_cast<int>(lane);
-    if (i < nq) {
-      const uint2 r = ws.mq[i];
-      const uint32_t cnt = ((r.x >> kRecCntShift) & kRecCntMask) + 1u;
-      const uint32_t tl = r.x >> kRecTrialShift, k = r.x & kRecKMask;
-      unsigned long long touched = 0ull;
-      for (uint32_t j = 0; j < cnt; ++j) touched |= bs.layers_of[pair_pos(p.hot[r.y + j].meta)];
-      for (unsigned long long m = touched; m; m &= m - 1ull) ws.gbuf[__ffsll(m) - 1][lane] = 0.0f;
-      for (uint32_t j = 0; j < cnt; ++j) {
-        const float L = pair_loss_batch(p, bs, r.y + j, ta + tl, k, nc);
-        for (unsigned long long m = bs.layers_of[pair_pos(p.hot[r.y + j].meta)]; m; m &= m - 1ull)
-          ws.gbuf[__ffsll(m) - 1][lane] += L;
-      }
-      for (unsigned long long m = touched; m; m &= m - 1ull) {
-        const int l = __ffsll(m) - 1;
-        add_occurrence(ws, bs, l, tl, ws.gbuf[l][lane]);
-      }
+  const uint32_t cnt = ((r.x >> kRecCntShift) & kRecCntMask) + 1u;
+  const uint32_t k = r.x & kRecKMask;
+  unsigned long long touched = 0ull;
+  for (uint32_t j = 0; j < cnt; ++j) touched |= bs.layers_of[pair_pos(p.hot[r.y + j].meta)];
+  for (unsigned long long m = touched; m; m &= m - 1ull) {
+    const int l = __ffsll(m) - 1;
+    float G = 0.0f;
+    for (uint32_t j = 0; j < cnt; ++j)
+      if ((bs.layers_of[pair_pos(p.hot[r.y + j].meta)] >> l) & 1ull) G += pair_loss_batch(p, bs, r.y + j, trial, k, nc);
+    add_occurrence(ws, bs, l, lane, G);
+  }
+}
+
+// The queued multi-ELT events of one trial, in windows of at most 32 pairs
+// (one per lane): each pair's loss once, then for each layer the window's
+// events touch, a segmented sum over each event's pairs of that layer (in the
+// pairs' order) and the occurrence terms at the event's last lane.
+__device__ __noinline__ uint32_t batch_multi(const BatchParams& p, const BatchShared& bs, BatchWarp& ws, int nq,
+                                             int64_t trial, unsigned long long* nc) {
+  const uint32_t q = lane_id();
+  const uint32_t upto = 0xffffffffu >> (31u - q);  // lanes 0..q
+  uint32_t n_pairs = 0;
+  for (int i0 = 0; i0 < nq;) {
+    const int ie = i0 + static_cast<int>(q);
+    const uint2 r = (ie < nq) ? ws.mq[ie] : make_uint2(0u, 0u);
+    const uint32_t cnt = (ie < nq) ? ((r.x >> kRecCntShift) & kRecCntMask) + 1u : 0u;
+    if (__shfl_sync(0xffffffffu, cnt, 0) > 32u) {  // a long event first in line: by lane 0
+      if (q == 0) batch_long_event(p, bs, ws, r, trial, nc);
+      n_pairs += __shfl_sync(0xffffffffu, cnt, 0);
+      __syncwarp();
+      ++i0;
+      continue;
     }
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+      if (q >= static_cast<uint32_t>(d)) incl += o;
+    }
+    const uint32_t pre = incl - cnt;
+    const bool take = cnt != 0 && incl <= 32u;
+    const int n_take = __popc(__ballot_sync(0xffffffffu, take));
+    const uint32_t np = __shfl_sync(0xffffffffu, incl, n_take - 1);
+    const uint32_t starts = __reduce_or_sync(0xffffffffu, take ? (1u << pre) : 0u);
+    const uint32_t ev = static_cast<uint32_t>(__popc(starts & upto)) - 1u;  // lane q's event
+    const uint32_t ex = __shfl_sync(0xffffffffu, r.x, ev);
+    const uint32_t ey = __shfl_sync(0xffffffffu, r.y, ev);
+    const uint32_t epre = __shfl_sync(0xffffffffu, pre, ev);
+    const uint32_t ecnt = __shfl_sync(0xffffffffu, cnt, ev);
+    float L = 0.0f;
+    unsigned long long lm = 0ull;
+    if (q < np) {
+      L = pair_loss_batch(p, bs, ey + (q - epre), trial, ex & kRecKMask, nc);
+      lm = bs.layers_of[pair_pos(p.hot[ey + (q - epre)].meta)];
+    }
+    n_pairs += np;
+    const bool end = q < np && q == epre + ecnt - 1u;
+    unsigned long long touched = lm;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) touched |= __shfl_xor_sync(0xffffffffu, touched, d);
+    for (unsigned long long m = touched; m; m &= m - 1ull) {
+      const int l = __ffsll(m) - 1;
+      float v = ((lm >> l) & 1ull) ? L : 0.0f;
+#pragma unroll
+      for (uint32_t d = 1; d < 32; d <<= 1) {
+        const float o = __shfl_up_sync(0xffffffffu, v, d);
+        if (q >= epre + d) v += o;
+      }
+      if (end) add_occurrence(ws, bs, l, q, v);
+    }
+    i0 += n_take;
   }
   __syncwarp();
+  return n_pairs;
+}
+
+// First record in [0, n) whose trial is >= key (n if none), by the whole warp:
+// each round probes 32 evenly spaced records and keeps the gap between the
+// last probe below key and the first at or above it.
+__device__ __forceinline__ int32_t first_record_of(const uint2* recs, int32_t n, uint32_t key, uint32_t lane) {
+  int32_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (lo < hi) {
+    const int32_t step = (hi - lo + 31) / 32;
+    const int32_t pos = lo + static_cast<int32_t>(lane) * step;
+    const bool ge = pos < hi && (__ldg(&recs[pos].x) >> kRecTrialShift) >= key;
+    const uint32_t b = __ballot_sync(0xffffffffu, ge);
+    if (b == 0u) {
+      const int32_t probes = (hi - lo + step - 1) / step;  // positions lo + j step < hi
+      lo += (probes - 1) * step + 1;
+    } else {
+      const int32_t f = __ffs(b) - 1;
+      hi = lo + f * step;
+      if (f > 0) lo += (f - 1) * step + 1;
+    }
+  }
+  return lo;
 }
 
 }  // namespace
 
-// One warp per tile of kWarpTrials trials; its lanes are spread over the
-// tile's trials (four per trial), so that atomic additions to one trial's
-// sums come from at most four lanes at a time.
+// One warp per (tile, trial) item: the trial's hit-event records, one per lane
+// per round (records two rounds ahead and single-ELT hot pairs one round ahead
+// in flight); every lane keeps its own fixed-point sum per layer, so nothing is
+// shared between lanes until the item's end, where the lanes' sums of each
+// layer are added and the layer's aggregate terms give the year loss.
 __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_batch(const BatchParams p) {
   __shared__ BatchWarp bw[kBatchThreads / 32];
   __shared__ BatchShared bs;
@@ -149,53 +226,70 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
   }
   __syncthreads();
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const uint32_t my_t = lane & (kWarpTrials - 1), my_sub = lane / kWarpTrials;
-  constexpr uint32_t kLanesPerTrial = 32 / kWarpTrials;
+  const int64_t n_items = p.n_tiles * kWarpTrials;
   unsigned long long nc = 0ull;
   uint32_t n_pairs = 0;
 
+  // items are claimed one ahead, so that the claim's latency overlaps an item's work
+  unsigned long long next = 0ull;
+  if (lane == 0) next = atomicAdd(&p.counters[0], 1ull);
   for (;;) {
-    int64_t tile = 0;
-    if (lane == 0) tile = static_cast<int64_t>(atomicAdd(&p.counters[0], 1ull));
-    tile = __shfl_sync(0xffffffffu, tile, 0);
-    if (tile >= p.n_tiles) break;
+    const int64_t item = static_cast<int64_t>(__shfl_sync(0xffffffffu, next, 0));
+    if (item >= n_items) break;
+    if (lane == 0) next = atomicAdd(&p.counters[0], 1ull);
+    const int64_t tile = item / kWarpTrials;
+    const uint32_t tl = static_cast<uint32_t>(item % kWarpTrials);
     const int64_t ta = p.t_begin + tile * kWarpTrials;
-    const int64_t tb = (ta + kWarpTrials < p.t_end) ? ta + kWarpTrials : p.t_end;
-    const int ntr = static_cast<int>(tb - ta);
+    const int64_t trial = ta + tl;
+    if (trial >= p.t_end) continue;
     const uint2* recs = p.ev_buf + (__ldg(&p.off[ta]) - p.e0);
+    // the trial's records [beg, end) of the tile (records are in trial order)
     const int32_t n = static_cast<int32_t>(__ldg(&p.tile_cnt[tile]));
-    for (int i = lane; i < p.n_layers * kWarpTrials; i += 32) ws.acc[i / kWarpTrials][i % kWarpTrials] = 0ull;
-    // each trial's records (sorted by trial): the first record with trial >= t
-    if (lane <= static_cast<uint32_t>(kWarpTrials)) {
-      int32_t lo = 0, hi = n;
-      while (lo < hi) {
-        const int32_t mid = (lo + hi) >> 1;
-        if ((__ldg(&recs[mid].x) >> kRecTrialShift) < lane) lo = mid + 1; else hi = mid;
-      }
-      ws.tr_beg[lane] = lo;
-    }
-    __syncwarp();
-    const int32_t beg = ws.tr_beg[my_t], end = ws.tr_beg[my_t + 1];
+    const int32_t beg = first_record_of(recs, n, tl, lane);
+    const int32_t end = first_record_of(recs, n, tl + 1, lane);
+    for (int l = 0; l < p.n_layers; ++l) ws.acc[l][lane] = 0ull;
     int nq = 0;
-    for (int32_t idx = beg + static_cast<int32_t>(my_sub);; idx += kLanesPerTrial) {
-      const bool active = static_cast<int>(my_t) < ntr && idx < end;
-      if (!__any_sync(0xffffffffu, active)) break;
-      const uint2 r = active ? __ldcs(&recs[idx]) : make_uint2(0u, 0u);
+    uint2 r0 = (beg + static_cast<int32_t>(lane) < end) ? __ldcs(recs + beg + lane) : make_uint2(0u, 0u);
+    uint2 r1 = (beg + 32 + static_cast<int32_t>(lane) < end) ? __ldcs(recs + beg + 32 + lane) : make_uint2(0u, 0u);
+    PairHot h0{0.0f, 0.0f, kKindZero << kMetaKindShift, 0u};
+    if (beg + static_cast<int32_t>(lane) < end && ((r0.x >> kRecCntShift) & kRecCntMask) == 0u) h0 = p.hot[r0.y];
+    for (int32_t base = beg; base < end; base += 32) {
+      const uint2 r = r0;
+      const PairHot h = h0;
+      const bool valid = base + static_cast<int32_t>(lane) < end;
+      r0 = r1;
+      if (base + 64 + static_cast<int32_t>(lane) < end) r1 = __ldcs(recs + base + 64 + lane);
+      if (base + 32 + static_cast<int32_t>(lane) < end && ((r0.x >> kRecCntShift) & kRecCntMask) == 0u)
+        h0 = p.hot[r0.y];
       const uint32_t cnt = ((r.x >> kRecCntShift) & kRecCntMask) + 1u;
-      const bool single = active && cnt == 1u;
-      if (single) {
+      if (valid && cnt == 1u) {
         const uint32_t k = r.x & kRecKMask;
-        const float L = pair_loss_batch(p, bs, r.y, ta + my_t, k, &nc);
-        for (unsigned long long m = bs.layers_of[pair_pos(p.hot[r.y].meta)]; m; m &= m - 1ull)
-          add_occurrence(ws, bs, __ffsll(m) - 1, my_t, L);
+        const uint32_t kind = pair_kind(h.meta);
+        const uint32_t pos = pair_pos(h.meta);
+        float loss = h.mu;
+        if (kind == kKindZero) {
+          loss = 0.0f;
+        } else if (!p.primary_only && kind == kKindBeta) {
+          if (p.newton_only || !pair_tab_exact(h.meta)) {
+            loss = -1.0f;  // marks the Halley path below
+          } else {
+            const float z = philox_uniform_rk(p.rk, trial, k, bs.elt_id[pos]);
+            const bool fine = pair_fine(h.meta);
+            loss = h.max_l * tab_quantile((fine ? bs.tabf[pos] : bs.tab[pos]) + h.node, z, fine);
+          }
+        }
+        const float L = (loss < 0.0f) ? pair_loss_slow(p, p.pairs[r.y], trial, k, &nc)
+                                      : bs.share[pos] * clamp_terms_f(loss, bs.ret[pos], bs.lim[pos]);
+        for (unsigned long long m = bs.layers_of[pos]; m; m &= m - 1ull) add_occurrence(ws, bs, __ffsll(m) - 1, lane, L);
+        ++n_pairs;
       }
-      const bool multi = active && cnt > 1u;
-      n_pairs += single ? 1u : (multi ? cnt : 0u);
+      const bool multi = valid && cnt > 1u;
       const uint32_t mmask = __ballot_sync(0xffffffffu, multi);
       if (mmask) {
         if (nq + __popc(mmask) > kBatchQueue) {
           __syncwarp();
-          batch_multi(p, bs, ws, nq, ta, &nc);
+          const uint32_t np = batch_multi(p, bs, ws, nq, trial, &nc);
+          if (lane == 0) n_pairs += np;
           nq = 0;
         }
         if (multi) ws.mq[nq + __popc(mmask & lt_mask)] = r;
@@ -203,13 +297,17 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
         __syncwarp();
       }
     }
-    if (nq > 0) batch_multi(p, bs, ws, nq, ta, &nc);
+    if (nq > 0) {
+      const uint32_t np = batch_multi(p, bs, ws, nq, trial, &nc);
+      if (lane == 0) n_pairs += np;
+    }
     __syncwarp();
-    // ---- year losses: aggregate terms of each layer's sum
-    for (int i = lane; i < p.n_layers * ntr; i += 32) {
-      const int l = i / ntr, t = i % ntr;
-      const double S = __ull2double_rn(ws.acc[l][t]) * p.inv_scale[l];
-      p.ylt[static_cast<int64_t>(l) * p.n_out + (ta + t - p.t_begin)] = clamp_terms_d(S, p.agg_r[l], p.agg_l[l]);
+    // ---- the trial's year loss for each layer: the lanes' sums, then the aggregate terms
+    for (int l = lane; l < p.n_layers; l += 32) {
+      unsigned long long S = 0ull;
+      for (int j = 0; j < 32; ++j) S += ws.acc[l][j];
+      const double s = __ull2double_rn(S) * p.inv_scale[l];
+      p.ylt[static_cast<int64_t>(l) * p.n_out + (trial - p.t_begin)] = clamp_terms_d(s, p.agg_r[l], p.agg_l[l]);
     }
     __syncwarp();
   }

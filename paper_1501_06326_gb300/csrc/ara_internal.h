@@ -167,7 +167,7 @@ struct LossParams {
 // k_gather as above over the union's index, then k_losses_batch.
 constexpr int kBatchLayers = 32;  // ARA_MAX_BATCH_LAYERS
 constexpr int kBatchThreads = 128;
-constexpr int kBatchBlocksPerSm = 6;
+constexpr int kBatchBlocksPerSm = 4;
 
 struct BatchParams {
   const int64_t* off;

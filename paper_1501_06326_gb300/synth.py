@@ -249,7 +249,19 @@ WORKLOADS = {
         n_trials=1_000_000, mean_events=1000.0, catalogue=2_000_000, n_elts=15, entries=10_000,
         recipe="stress", seed=20150127, elt_seed=20150129, return_periods=(100.0, 250.0),
     ),
+    # several layers over one YET (a portfolio's layers, Section 2.1 (iii)): the paper-1m
+    # YET, a pool of 64 ELTs, 16 layers of 1..32 ELTs each (draw_layers)
+    "batched-16": dict(
+        n_trials=1_000_000, mean_events=1000.0, catalogue=2_000_000, n_elts=64, entries=10_000,
+        recipe="plain", seed=20150127, elt_seed=20150130, layer_seed=20150131, n_layers=16,
+        max_layer_elts=32, return_periods=(100.0, 250.0),
+    ),
 }
+
+
+def workload_layers(spec, pool) -> list:
+    """The layers (sorted pool-id arrays) of a batched workload."""
+    return draw_layers(spec["n_layers"], pool.elt_ids, spec["max_layer_elts"], spec["layer_seed"])
 
 
 def workload(name: str, n_trials: Optional[int] = None):

@@ -20,6 +20,7 @@ import oracle  # noqa: E402
 from paper_1501_06326_gb300 import synth  # noqa: E402
 
 SAMPLE = {"plain-1k": 1000, "paper-1m": 20000, "stress-1m": 20000}
+BATCHED = {"batched-16": 20000}
 
 
 def main() -> None:
@@ -29,6 +30,16 @@ def main() -> None:
         terms = oracle.calibrate_layer_terms(yet, pool)
         out[name] = {"sample_trials": n, "layer_terms": list(terms), "elt_ids": pool.elt_ids.tolist()}
         print(name, terms)
+    for name, n in BATCHED.items():
+        # each layer's terms from its own ELTs, as for a single layer
+        yet, pool, spec = synth.workload(name, n_trials=n)
+        layers = []
+        for ids in synth.workload_layers(spec, pool):
+            sub = pool.subset([int(i) for i in ids])  # pool ids are the positions 0..n-1
+            terms = oracle.calibrate_layer_terms(yet, sub)
+            layers.append({"elt_ids": [int(i) for i in ids], "layer_terms": list(terms)})
+        out[name] = {"sample_trials": n, "layers": layers}
+        print(name, len(layers), "layers")
     with open(os.path.join(HERE, "workload_terms.json"), "w") as fh:
         json.dump(out, fh, indent=2)
 

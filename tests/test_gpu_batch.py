@@ -164,3 +164,26 @@ def test_batch_errors(eng, small_batch):
     with pytest.raises(ara.AraError) as e:  # union of 70 ELTs
         eng.run_layers(wide, 0, 0, 10, out)
     assert e.value.code == ara.ARA_EINVAL
+
+
+def test_batch_with_empty_and_long_trials(eng):
+    # empty trials (also at tile starts and ends), a trial longer than a gather step,
+    # a partial last tile: the per-trial record ranges of each tile
+    rng = np.random.default_rng(11)
+    C = 2003
+    lens = [0, 0, 3, 0, 4097, 0, 0, 0, 0, 1, 0, 250] + list(rng.integers(0, 40, 203)) + [0, 0]
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    offsets[1:] = np.cumsum(lens)
+    yet = synth.YET(offsets, rng.integers(0, C, offsets[-1]).astype(np.int32), C)
+    pool = synth.make_elt_pool(6, 300, C, 31)
+    layer_ids = [np.array([0, 1, 2], np.int32), np.array([2, 3, 4, 5], np.int32), np.array([5], np.int32)]
+    layers = []
+    for ids in layer_ids:
+        sub = pool.subset([int(i) for i in ids])
+        layers.append((ids, (100.0, 5e5, 1e3, 5e6), sub))
+    out = _run_batch(eng, yet, pool, layers, 2)
+    for l, (ids, terms, sub) in enumerate(layers):
+        check_ylt(out[l], oracle.run_layer(yet, sub, terms, seed=2))
+    out = _run_batch(eng, yet, pool, layers, 2, 3, 200)
+    for l, (ids, terms, sub) in enumerate(layers):
+        check_ylt(out[l], oracle.run_layer(yet, sub, terms, seed=2, trials=np.arange(3, 200)))
