@@ -249,52 +249,115 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
     const int32_t end = first_record_of(recs, n, tl + 1, lane);
     for (int l = 0; l < p.n_layers; ++l) ws.acc[l][lane] = 0ull;
     int nq = 0;
-    uint2 r0 = (beg + static_cast<int32_t>(lane) < end) ? __ldcs(recs + beg + lane) : make_uint2(0u, 0u);
-    uint2 r1 = (beg + 32 + static_cast<int32_t>(lane) < end) ? __ldcs(recs + beg + 32 + lane) : make_uint2(0u, 0u);
-    PairHot h0{0.0f, 0.0f, kKindZero << kMetaKindShift, 0u};
-    if (beg + static_cast<int32_t>(lane) < end && ((r0.x >> kRecCntShift) & kRecCntMask) == 0u) h0 = p.hot[r0.y];
-    for (int32_t base = beg; base < end; base += 32) {
-      const uint2 r = r0;
-      const PairHot h = h0;
-      const bool valid = base + static_cast<int32_t>(lane) < end;
-      r0 = r1;
-      if (base + 64 + static_cast<int32_t>(lane) < end) r1 = __ldcs(recs + base + 64 + lane);
-      if (base + 32 + static_cast<int32_t>(lane) < end && ((r0.x >> kRecCntShift) & kRecCntMask) == 0u)
-        h0 = p.hot[r0.y];
-      const uint32_t cnt = ((r.x >> kRecCntShift) & kRecCntMask) + 1u;
-      if (valid && cnt == 1u) {
-        const uint32_t k = r.x & kRecKMask;
-        const uint32_t kind = pair_kind(h.meta);
-        const uint32_t pos = pair_pos(h.meta);
-        float loss = h.mu;
-        if (kind == kKindZero) {
-          loss = 0.0f;
-        } else if (!p.primary_only && kind == kKindBeta) {
-          if (p.newton_only || !pair_tab_exact(h.meta)) {
-            loss = -1.0f;  // marks the Halley path below
-          } else {
-            const float z = philox_uniform_rk(p.rk, trial, k, bs.elt_id[pos]);
-            const bool fine = pair_fine(h.meta);
-            loss = h.max_l * tab_quantile((fine ? bs.tabf[pos] : bs.tab[pos]) + h.node, z, fine);
+    // 64 records per round, two per lane (lane and 32 + lane), so that two table
+    // reads are in flight per lane; the next round's records and single-ELT hot
+    // pairs are loaded one round ahead
+    uint2 rn[2];
+    PairHot hn[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int32_t at = beg + 32 * j + static_cast<int32_t>(lane);
+      rn[j] = (at < end) ? __ldcs(recs + at) : make_uint2(0u, 0u);
+      hn[j] = PairHot{0.0f, 0.0f, kKindZero << kMetaKindShift, 0u};
+      if (at < end && ((rn[j].x >> kRecCntShift) & kRecCntMask) == 0u) hn[j] = p.hot[rn[j].y];
+    }
+    for (int32_t base = beg; base < end; base += 64) {
+      uint2 r[2];
+      PairHot h[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        r[j] = rn[j];
+        h[j] = hn[j];
+        const int32_t at = base + 64 + 32 * j + static_cast<int32_t>(lane);
+        if (at < end) rn[j] = __ldcs(recs + at);
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int32_t at = base + 64 + 32 * j + static_cast<int32_t>(lane);
+        if (at < end && ((rn[j].x >> kRecCntShift) & kRecCntMask) == 0u) hn[j] = p.hot[rn[j].y];
+      }
+      // ---- single-ELT events: uniform, table position, then both table reads, then the losses
+      int mode[2];  // 0: none, 1: loss known (no loss / mean), 2: table, 3: Halley
+      float val[2], sfrac[2];
+      const float4* node[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const bool valid = base + 32 * j + static_cast<int32_t>(lane) < end;
+        const uint32_t cnt = ((r[j].x >> kRecCntShift) & kRecCntMask) + 1u;
+        mode[j] = 0;
+        val[j] = 0.0f;
+        sfrac[j] = 0.0f;
+        node[j] = nullptr;
+        if (valid && cnt == 1u) {
+          const uint32_t kind = pair_kind(h[j].meta);
+          const uint32_t pos = pair_pos(h[j].meta);
+          mode[j] = 1;
+          val[j] = h[j].mu;
+          if (kind == kKindZero) {
+            val[j] = 0.0f;
+          } else if (!p.primary_only && kind == kKindBeta) {
+            if (p.newton_only || !pair_tab_exact(h[j].meta)) {
+              mode[j] = 3;
+            } else {
+              mode[j] = 2;
+              const float z = philox_uniform_rk(p.rk, trial, r[j].x & kRecKMask, bs.elt_id[pos]);
+              const bool fine = pair_fine(h[j].meta);
+              const int nseg = fine ? kTabFineNodes - 1 : kTabNodes - 1;
+              float u = (normcdfinvf(z) + kTabT1f) * (fine ? kTabInvH * kTabRefine : kTabInvH);
+              u = fminf(fmaxf(u, 0.0f), static_cast<float>(nseg));
+              int i = static_cast<int>(u);
+              if (i > nseg - 1) i = nseg - 1;
+              sfrac[j] = u - static_cast<float>(i);
+              node[j] = (fine ? bs.tabf[pos] : bs.tab[pos]) + h[j].node + i;
+            }
           }
         }
-        const float L = (loss < 0.0f) ? pair_loss_slow(p, p.pairs[r.y], trial, k, &nc)
-                                      : bs.share[pos] * clamp_terms_f(loss, bs.ret[pos], bs.lim[pos]);
+      }
+      float4 n0[2];
+      float2 n1[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (mode[j] == 2) {
+          n0[j] = __ldg(node[j]);
+          n1[j] = __ldg(reinterpret_cast<const float2*>(node[j] + 1) + 1);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (mode[j] == 0) continue;
+        const uint32_t pos = pair_pos(h[j].meta);
+        float L;
+        if (mode[j] == 3) {
+          L = pair_loss_slow(p, p.pairs[r[j].y], trial, r[j].x & kRecKMask, &nc);
+        } else {
+          float loss = val[j];
+          if (mode[j] == 2)
+            loss = (n0[j].x > 0.0f)
+                       ? h[j].max_l * (n0[j].x * expf(tab_increment(sfrac[j], n0[j].y, n0[j].z, n0[j].w, n1[j].x,
+                                                                     n1[j].y)))
+                       : 0.0f;
+          L = bs.share[pos] * clamp_terms_f(loss, bs.ret[pos], bs.lim[pos]);
+        }
         for (unsigned long long m = bs.layers_of[pos]; m; m &= m - 1ull) add_occurrence(ws, bs, __ffsll(m) - 1, lane, L);
         ++n_pairs;
       }
-      const bool multi = valid && cnt > 1u;
-      const uint32_t mmask = __ballot_sync(0xffffffffu, multi);
-      if (mmask) {
-        if (nq + __popc(mmask) > kBatchQueue) {
+      // ---- multi-ELT events: queued
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const bool valid = base + 32 * j + static_cast<int32_t>(lane) < end;
+        const bool multi = valid && ((r[j].x >> kRecCntShift) & kRecCntMask) != 0u;
+        const uint32_t mmask = __ballot_sync(0xffffffffu, multi);
+        if (mmask) {
+          if (nq + __popc(mmask) > kBatchQueue) {
+            __syncwarp();
+            const uint32_t np = batch_multi(p, bs, ws, nq, trial, &nc);
+            if (lane == 0) n_pairs += np;
+            nq = 0;
+          }
+          if (multi) ws.mq[nq + __popc(mmask & lt_mask)] = r[j];
+          nq += __popc(mmask);
           __syncwarp();
-          const uint32_t np = batch_multi(p, bs, ws, nq, trial, &nc);
-          if (lane == 0) n_pairs += np;
-          nq = 0;
         }
-        if (multi) ws.mq[nq + __popc(mmask & lt_mask)] = r;
-        nq += __popc(mmask);
-        __syncwarp();
       }
     }
     if (nq > 0) {
