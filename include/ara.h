@@ -50,6 +50,7 @@ extern "C" {
 #define ARA_ENOTLOADED (-3) /* the YET or a referenced ELT is not loaded */
 #define ARA_ECUDA (-4)      /* a CUDA runtime call failed */
 #define ARA_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define ARA_EAGAIN (-6)     /* a served request has not finished yet */
 
 /* Largest number of ELTs in one layer.  The paper's layers cover 3 to 30
  * ELTs (Section 2.1 (iii)). */
@@ -204,6 +205,36 @@ ARA_API int ara_run_layer_diag(ara_ctx *ctx, const ara_layer *layer, uint64_t se
 #define ARA_MAX_BATCH_ELTS 64
 ARA_API int ara_run_layers(ara_ctx *ctx, int32_t n_layers, const ara_layer *layers, uint64_t seed,
                    int64_t trial_begin, int64_t trial_end, double *ylt_out);
+
+/* Serving: layer requests against the resident YET and ELT pool, run in
+ * batches (continuous batching into ara_run_layers).  The paper has no serving
+ * system; a portfolio's layers (Section 2.1 (iii)) are its natural requests.
+ *
+ * ara_submit queues one request: a layer (as for ara_run_layer), its seed, the
+ * trial prefix [0, trial_end) to simulate, and n_rp (1..ARA_SERVE_MAX_RP)
+ * return periods (host memory, each >= 1) for PML/TVaR of the prefix's YLT.
+ * The layer's ELTs must be loaded.  *ticket receives the request's handle.
+ * Errors: ARA_EINVAL, ARA_ENOTLOADED, ARA_ENOMEM (the request alone would not
+ * fit the context's HBM budget).
+ *
+ * ara_serve_step runs one batch: from the queue, in arrival order, every
+ * request that fits next to the first (same seed and flags, at most
+ * ARA_MAX_BATCH_LAYERS layers with at most ARA_MAX_BATCH_ELTS ELTs together,
+ * the batch's year losses within the HBM budget), over the longest prefix of
+ * the batch, then each request's PML/TVaR over its own prefix.  It returns when
+ * the batch's results are on the host; *n_done (may be NULL) receives the
+ * number of requests finished (0 when the queue is empty).  A request's result
+ * does not depend on the batch it ran in.  Errors: ARA_ENOMEM, ARA_ECUDA.
+ *
+ * ara_poll returns ARA_EAGAIN while the request is queued; once finished, it
+ * copies its PML and TVaR (n_rp doubles each, host memory) and releases the
+ * ticket, returning the request's own status (ARA_OK, or the error its batch
+ * met).  Errors: ARA_EINVAL (unknown ticket). */
+#define ARA_SERVE_MAX_RP 16
+ARA_API int ara_submit(ara_ctx *ctx, const ara_layer *layer, uint64_t seed, int64_t trial_end,
+               const double *return_periods, int32_t n_rp, int64_t *ticket);
+ARA_API int ara_serve_step(ara_ctx *ctx, int32_t *n_done);
+ARA_API int ara_poll(ara_ctx *ctx, int64_t ticket, double *pml_out, double *tvar_out);
 
 /* PML and TVaR of a YLT (Section 2.3) at n_rp return periods (each >= 1):
  * with m = ceil(n / RP), PML is the m-th largest year loss and TVaR the mean

@@ -23,15 +23,16 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libara.so")
 
-ARA_OK, ARA_EINVAL, ARA_ENOMEM, ARA_ENOTLOADED, ARA_ECUDA, ARA_ETIMEOUT = 0, -1, -2, -3, -4, -5
+ARA_OK, ARA_EINVAL, ARA_ENOMEM, ARA_ENOTLOADED, ARA_ECUDA, ARA_ETIMEOUT, ARA_EAGAIN = 0, -1, -2, -3, -4, -5, -6
 ARA_PRIMARY_ONLY = 1
 ARA_NEWTON_ONLY = 2
 ARA_MAX_LAYER_ELTS = 32
 ARA_MAX_BATCH_LAYERS = 32
 ARA_MAX_BATCH_ELTS = 64
+ARA_SERVE_MAX_RP = 16
 _ERR_NAMES = {
     ARA_EINVAL: "ARA_EINVAL", ARA_ENOMEM: "ARA_ENOMEM", ARA_ENOTLOADED: "ARA_ENOTLOADED",
-    ARA_ECUDA: "ARA_ECUDA", ARA_ETIMEOUT: "ARA_ETIMEOUT",
+    ARA_ECUDA: "ARA_ECUDA", ARA_ETIMEOUT: "ARA_ETIMEOUT", ARA_EAGAIN: "ARA_EAGAIN",
 }
 
 # Every function the header declares (checked by the tests against the .so).
@@ -39,7 +40,7 @@ EXPORTED = (
     "ara_create", "ara_set_stream", "ara_load_yet", "ara_load_elts", "ara_run_layer",
     "ara_run_layer_diag", "ara_pml_tvar", "ara_sort_ylt", "ara_debug_uniforms",
     "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
-    "ara_pml_tvar_noalloc", "ara_run_layers",
+    "ara_pml_tvar_noalloc", "ara_run_layers", "ara_submit", "ara_serve_step", "ara_poll",
 )
 ARA_NOALLOC_MAX_RP = 64
 
@@ -124,6 +125,9 @@ def load_library(path: str = LIB_PATH):
     lib.ara_run_layer.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P]
     lib.ara_run_layer_diag.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P, ctypes.POINTER(Diag)]
     lib.ara_run_layers.argtypes = [P, i32, ctypes.POINTER(Layer), u64, i64, i64, P]
+    lib.ara_submit.argtypes = [P, ctypes.POINTER(Layer), u64, i64, P, i32, P]
+    lib.ara_serve_step.argtypes = [P, P]
+    lib.ara_poll.argtypes = [P, i64, P, P]
     lib.ara_pml_tvar.argtypes = [P, P, i64, P, i32, P, P]
     lib.ara_sort_ylt.argtypes = [P, P, i64, P]
     lib.ara_debug_uniforms.argtypes = [P, u64, i64, P, P, P, P]
@@ -209,6 +213,19 @@ def ara_run_layers(h, n_layers, layers, seed, trial_begin, trial_end, ylt_out):
     """``layers``: a ctypes array of ``Layer``; ``ylt_out``: n_layers x (trial_end - trial_begin), layer-major."""
     return load_library().ara_run_layers(h, int(n_layers), layers, int(seed), int(trial_begin), int(trial_end),
                                          _ptr(ylt_out, np.float64))
+
+
+def ara_submit(h, layer: Layer, seed, trial_end, return_periods, n_rp, ticket_out):
+    return load_library().ara_submit(h, ctypes.byref(layer), int(seed), int(trial_end),
+                                     _ptr(return_periods, np.float64), int(n_rp), _ptr(ticket_out, np.int64))
+
+
+def ara_serve_step(h, n_done_out):
+    return load_library().ara_serve_step(h, _ptr(n_done_out, np.int32))
+
+
+def ara_poll(h, ticket, pml_out, tvar_out):
+    return load_library().ara_poll(h, int(ticket), _ptr(pml_out, np.float64), _ptr(tvar_out, np.float64))
 
 
 def ara_pml_tvar(h, ylt, n, return_periods, n_rp, pml_out, tvar_out):
@@ -331,6 +348,30 @@ class Ara:
         made = [self.make_layer(ids, terms, primary_only, newton_only) for ids, terms in layers]
         arr = (Layer * len(made))(*made)
         self._check(ara_run_layers(self._h, len(made), arr, seed, trial_begin, trial_end, ylt_out))
+
+    def submit(self, elt_ids, layer_terms, seed: int, trial_end: int, return_periods,
+               primary_only: bool = False) -> int:
+        """Queue a serving request; returns its ticket."""
+        lay = self.make_layer(elt_ids, layer_terms, primary_only)
+        rps = np.ascontiguousarray(return_periods, dtype=np.float64)
+        tk = np.zeros(1, np.int64)
+        self._check(ara_submit(self._h, lay, seed, trial_end, rps, rps.shape[0], tk))
+        return int(tk[0])
+
+    def serve_step(self) -> int:
+        """Run one batch of queued requests; returns how many finished."""
+        n = np.zeros(1, np.int32)
+        self._check(ara_serve_step(self._h, n))
+        return int(n[0])
+
+    def poll(self, ticket: int, n_rp: int):
+        """(pml, tvar) of a finished request, or None while it is queued."""
+        pml, tvar = np.zeros(n_rp), np.zeros(n_rp)
+        rc = ara_poll(self._h, ticket, pml, tvar)
+        if rc == ARA_EAGAIN:
+            return None
+        self._check(rc)
+        return pml, tvar
 
     def pml_tvar(self, ylt, return_periods, pml_out=None, tvar_out=None):
         rps = np.ascontiguousarray(return_periods, dtype=np.float64)

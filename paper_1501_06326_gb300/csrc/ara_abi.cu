@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <string>
 #include <vector>
@@ -31,6 +32,17 @@ struct Elt {
   float max_loss = 0.0f;  // largest loss a record can produce (max(exposure, mean))
   int32_t max_event = -1;
   ara_elt_terms terms{0.0f, INFINITY, 1.0f};
+};
+
+// A request of the serving loop (ara_submit).
+struct ServeReq {
+  std::vector<int32_t> elt_ids;
+  ara_layer layer{};  // elt_ids points into the vector above
+  uint64_t seed = 0;
+  int64_t t_end = 0;
+  std::vector<double> rps, pml, tvar;
+  bool done = false;
+  int status = ARA_OK;
 };
 
 }  // namespace
@@ -77,6 +89,11 @@ struct ara_ctx {
   int64_t launches = 0;
   int num_sms = 0;
   int max_smem = 0;
+  // serving
+  std::deque<int64_t> serve_queue;      // tickets in arrival order
+  std::map<int64_t, ServeReq> serve_reqs;
+  int64_t next_ticket = 1;
+  DevBuf serve_ylt, serve_out;          // a batch's year losses; its PML/TVaR
 };
 
 namespace {
@@ -835,6 +852,127 @@ int ara_get_timing(ara_ctx* c, ara_timing* out, int reset) {
   return ARA_OK;
 }
 
+// ---------------------------------------------------------------- serving
+int ara_submit(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t_end, const double* rps, int32_t n_rp,
+               int64_t* ticket) {
+  static const char* who = "ara_submit";
+  int rc = bind(c);
+  if (rc) return rc;
+  if (!L || !rps || !ticket || n_rp < 1 || n_rp > ARA_SERVE_MAX_RP)
+    return fail(c, ARA_EINVAL, "%s: need a layer, 1..%d return periods and a ticket", who, ARA_SERVE_MAX_RP);
+  std::vector<int32_t> ids;
+  if ((rc = check_trial_range(c, 0, t_end, who)) || (rc = check_layer(c, L, who, &ids))) return rc;
+  for (int32_t id : ids)
+    if (c->pool.find(id) == c->pool.end()) return fail(c, ARA_ENOTLOADED, "%s: ELT %d is not loaded", who, id);
+  for (int32_t i = 0; i < n_rp; ++i)
+    if (!(rps[i] >= 1.0) || !std::isfinite(rps[i])) return fail(c, ARA_EINVAL, "%s: return periods must be >= 1", who);
+  if (c->budget && sizeof(double) * static_cast<size_t>(t_end) > c->budget)
+    return fail(c, ARA_ENOMEM, "%s: the request's year losses exceed the HBM budget", who);
+  const int64_t tk = c->next_ticket++;
+  ServeReq& r = c->serve_reqs[tk];
+  r.elt_ids = ids;
+  r.layer = *L;
+  r.layer.elt_ids = r.elt_ids.data();
+  r.layer.n_elts = static_cast<int32_t>(r.elt_ids.size());
+  r.seed = seed;
+  r.t_end = t_end;
+  r.rps.assign(rps, rps + n_rp);
+  c->serve_queue.push_back(tk);
+  *ticket = tk;
+  return ARA_OK;
+}
+
+int ara_serve_step(ara_ctx* c, int32_t* n_done) {
+  static const char* who = "ara_serve_step";
+  int rc = bind(c);
+  if (rc) return rc;
+  if (n_done) *n_done = 0;
+  if (c->serve_queue.empty()) return ARA_OK;
+  // ---- the batch: in arrival order, every request that fits next to the first
+  const ServeReq& first = c->serve_reqs[c->serve_queue.front()];
+  const size_t room = c->budget ? c->budget - std::min(c->budget, c->used - c->serve_ylt.bytes) : SIZE_MAX;
+  std::vector<int64_t> batch;
+  std::vector<int32_t> uni;
+  int64_t t_max = 0;
+  for (int64_t tk : c->serve_queue) {
+    const ServeReq& r = c->serve_reqs[tk];
+    if (batch.size() == static_cast<size_t>(ARA_MAX_BATCH_LAYERS)) break;
+    if (r.seed != first.seed || r.layer.flags != first.layer.flags) continue;
+    std::vector<int32_t> u2 = uni;
+    u2.insert(u2.end(), r.elt_ids.begin(), r.elt_ids.end());
+    std::sort(u2.begin(), u2.end());
+    u2.erase(std::unique(u2.begin(), u2.end()), u2.end());
+    if (u2.size() > static_cast<size_t>(ARA_MAX_BATCH_ELTS)) continue;
+    const int64_t t2 = std::max(t_max, r.t_end);
+    if (sizeof(double) * static_cast<size_t>(t2) * (batch.size() + 1) > room && !batch.empty()) continue;
+    batch.push_back(tk);
+    uni.swap(u2);
+    t_max = t2;
+  }
+  // ---- the layers over [0, t_max), then each request's PML/TVaR over its own prefix
+  const int32_t nb = static_cast<int32_t>(batch.size());
+  std::vector<ara_layer> layers(nb);
+  int32_t n_rp_total = 0;
+  for (int32_t i = 0; i < nb; ++i) {
+    layers[i] = c->serve_reqs[batch[i]].layer;
+    n_rp_total += static_cast<int32_t>(c->serve_reqs[batch[i]].rps.size());
+  }
+  int status = reserve(c, c->serve_ylt, sizeof(double) * static_cast<size_t>(t_max) * nb);
+  if (!status) status = reserve(c, c->serve_out, 2 * sizeof(double) * n_rp_total);
+  if (!status) status = reserve(c, c->sel, ara::select_scratch_bytes(t_max));
+  double* d_ylt = static_cast<double*>(c->serve_ylt.ptr);
+  double* d_out = static_cast<double*>(c->serve_out.ptr);
+  if (!status) status = run_layers_impl(c, nb, layers.data(), first.seed, 0, t_max, d_ylt);
+  std::vector<double> h_out(2 * static_cast<size_t>(n_rp_total));
+  if (!status) {
+    int32_t at = 0, launched = 0;
+    cudaError_t e = cudaSuccess;
+    for (int32_t i = 0; i < nb && e == cudaSuccess; ++i) {
+      const ServeReq& r = c->serve_reqs[batch[i]];
+      const int32_t m = static_cast<int32_t>(r.rps.size());
+      e = ara::pml_tvar_device(d_ylt + static_cast<int64_t>(i) * t_max, r.t_end, r.rps.data(), m, d_out + at,
+                               d_out + n_rp_total + at, c->sel.ptr, c->stream, &launched);
+      at += m;
+    }
+    c->launches += launched;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h_out.data(), d_out, sizeof(double) * h_out.size(), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) status = fail(c, ARA_ECUDA, "%s: %s", who, cudaGetErrorString(e));
+  }
+  // ---- the batch's requests are finished (with the batch's status)
+  int32_t at = 0;
+  for (int32_t i = 0; i < nb; ++i) {
+    ServeReq& r = c->serve_reqs[batch[i]];
+    const int32_t m = static_cast<int32_t>(r.rps.size());
+    r.done = true;
+    r.status = status;
+    if (!status) {
+      r.pml.assign(h_out.begin() + at, h_out.begin() + at + m);
+      r.tvar.assign(h_out.begin() + n_rp_total + at, h_out.begin() + n_rp_total + at + m);
+    }
+    at += m;
+  }
+  for (int64_t tk : batch) c->serve_queue.erase(std::find(c->serve_queue.begin(), c->serve_queue.end(), tk));
+  if (n_done) *n_done = nb;
+  return status;
+}
+
+int ara_poll(ara_ctx* c, int64_t ticket, double* pml_out, double* tvar_out) {
+  int rc = bind(c);
+  if (rc) return rc;
+  auto it = c->serve_reqs.find(ticket);
+  if (it == c->serve_reqs.end()) return fail(c, ARA_EINVAL, "ara_poll: unknown ticket %lld", (long long)ticket);
+  if (!it->second.done) return ARA_EAGAIN;
+  const int status = it->second.status;
+  if (status == ARA_OK) {
+    if (pml_out) std::copy(it->second.pml.begin(), it->second.pml.end(), pml_out);
+    if (tvar_out) std::copy(it->second.tvar.begin(), it->second.tvar.end(), tvar_out);
+  }
+  c->serve_reqs.erase(it);
+  return status;
+}
+
 int ara_pml_tvar(ara_ctx* c, const double* ylt, int64_t n, const double* rps, int32_t n_rp, double* pml_out,
                  double* tvar_out) {
   int rc = bind(c);
@@ -1005,7 +1143,7 @@ void ara_destroy(ara_ctx* c) {
                     &c->yet_ids,    &c->bits,           &c->word_cnt,      &c->word_pairs,     &c->rankdir,
                     &c->mask,       &c->slot_cnt,       &c->pairs,         &c->pairs_hot,     &c->scan_tmp,       &c->flags,
                     &c->counters,   &c->ylt_tmp,        &c->diag_tmp,      &c->sel,            &c->in_tmp,
-                    &c->out_tmp};
+                    &c->out_tmp,    &c->serve_ylt,      &c->serve_out};
   for (DevBuf* b : bufs) release(c, *b);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);

@@ -25,6 +25,8 @@ constexpr int kBatchQueue = 64;  // multi-ELT events queued per warp
 struct BatchWarp {
   unsigned long long acc[kBatchLayers][32];  // per layer and lane: the lane's sum of occurrence losses (fixed point)
   uint2 mq[kBatchQueue];                     // queued multi-ELT events (records)
+  float wl[32];                              // a window's pair losses
+  unsigned long long wm[32];                 // a window's pairs: layers holding the pair's ELT
 };
 
 struct BatchShared {
@@ -114,8 +116,11 @@ __device__ __noinline__ void batch_long_event(const BatchParams& p, const BatchS
 
 // The queued multi-ELT events of one trial, in windows of at most 32 pairs
 // (one per lane): each pair's loss once, then for each layer the window's
-// events touch, a segmented sum over each event's pairs of that layer (in the
-// pairs' order) and the occurrence terms at the event's last lane.
+// events touch, each event's last lane sums the event's pair losses of that
+// layer from left to right (the pairs' canonical order) and applies the
+// occurrence terms.  A left-to-right sum does not change when pairs of other
+// layers' ELTs are present, so an event's per-layer losses are the same in
+// any batch.
 __device__ __noinline__ uint32_t batch_multi(const BatchParams& p, const BatchShared& bs, BatchWarp& ws, int nq,
                                              int64_t trial, unsigned long long* nc) {
   const uint32_t q = lane_id();
@@ -154,21 +159,24 @@ __device__ __noinline__ uint32_t batch_multi(const BatchParams& p, const BatchSh
       L = pair_loss_batch(p, bs, ey + (q - epre), trial, ex & kRecKMask, nc);
       lm = bs.layers_of[pair_pos(p.hot[ey + (q - epre)].meta)];
     }
+    ws.wl[q] = L;
+    ws.wm[q] = lm;
     n_pairs += np;
     const bool end = q < np && q == epre + ecnt - 1u;
     unsigned long long touched = lm;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) touched |= __shfl_xor_sync(0xffffffffu, touched, d);
+    __syncwarp();
     for (unsigned long long m = touched; m; m &= m - 1ull) {
       const int l = __ffsll(m) - 1;
-      float v = ((lm >> l) & 1ull) ? L : 0.0f;
-#pragma unroll
-      for (uint32_t d = 1; d < 32; d <<= 1) {
-        const float o = __shfl_up_sync(0xffffffffu, v, d);
-        if (q >= epre + d) v += o;
+      if (end) {
+        float G = 0.0f;
+        for (uint32_t j = epre; j <= q; ++j)
+          if ((ws.wm[j] >> l) & 1ull) G += ws.wl[j];
+        add_occurrence(ws, bs, l, q, G);
       }
-      if (end) add_occurrence(ws, bs, l, q, v);
     }
+    __syncwarp();
     i0 += n_take;
   }
   __syncwarp();
