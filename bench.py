@@ -352,6 +352,9 @@ def run_gpu(args):
     batched = None
     if ws == 1 and not args.no_batched:
         batched = _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args)
+    serving = None
+    if ws == 1 and not args.no_serving and n_trials == synth.WORKLOADS["serving"]["n_trials"]:
+        serving = _serving_leg(eng, synth, offsets, args)
 
     if rank == 0:
         line = {
@@ -379,6 +382,8 @@ def run_gpu(args):
             line["global_pml_tvar"] = {"pml": list(global_pml[0]), "tvar": list(global_pml[1])}
         if batched is not None:
             line["batched"] = batched
+        if serving is not None:
+            line["serving"] = serving
         print(json.dumps(line))
     eng.close()
     if ws > 1:
@@ -431,6 +436,55 @@ def _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args)
             "speedup": ms_plain / ms_batch, "evals_per_s": evals / (ms_batch * 1e-3)}
 
 
+def _serving_leg(eng, synth, offsets, args):
+    """The serving workload: requests with Poisson arrivals at several rates, served by
+    ara_submit / ara_serve_step / ara_poll.  Time is virtual: each serve step advances
+    the clock by its measured wall time (GPU work and host overhead), and a request's
+    latency is its finish minus its arrival, so the sweep runs as fast as the server."""
+    spec = synth.WORKLOADS["serving"]
+    pool = synth.make_elt_pool(spec["n_elts"], spec["entries"], spec["catalogue"], spec["elt_seed"],
+                               recipe=spec["recipe"])
+    eng.load_pool(pool)
+    occ_r, occ_l, agg_r, agg_l = _terms()
+    reqs = synth.serving_requests(spec, args.serve_requests, spec["request_seed"])
+    rps = np.array(RETURN_PERIODS)
+    results = []
+    for rate in args.serve_rates:
+        rng = np.random.default_rng([spec["request_seed"], int(rate)])
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+        clock, i, busy, n_batches = 0.0, 0, 0.0, 0
+        pending, lat, evals = {}, [], 0
+        while i < len(reqs) or pending:
+            if not pending:
+                clock = max(clock, arrivals[i])
+            while i < len(reqs) and arrivals[i] <= clock:
+                ids, t_end = reqs[i]
+                f = len(ids) / 15.0  # percentile terms of the 15-ELT layer, aggregate terms scaled to |J|
+                tk = eng.submit(ids, (occ_r, occ_l, agg_r * f, agg_l * f), 0, t_end, rps)
+                pending[tk] = (arrivals[i], int(offsets[t_end]) * len(ids))
+                i += 1
+            t0 = time.perf_counter()
+            eng.serve_step()
+            dt = time.perf_counter() - t0
+            clock += dt
+            busy += dt
+            n_batches += 1
+            for tk in list(pending):
+                if eng.poll(tk, len(rps)) is not None:
+                    arr, ev = pending.pop(tk)
+                    lat.append(clock - arr)
+                    evals += ev
+        lat_ms = 1e3 * np.asarray(lat)
+        results.append({"rate_per_s": rate, "p50_ms": float(np.percentile(lat_ms, 50)),
+                        "p99_ms": float(np.percentile(lat_ms, 99)), "batches": n_batches,
+                        "requests_per_batch": len(reqs) / n_batches, "evals_per_s": evals / busy})
+    return {"workload": f"serving: the paper-1m YET, a pool of {spec['n_elts']} ELTs x {spec['entries']:,} records, "
+                        f"{len(reqs)} requests of |J| ~ U{{1..15}} over trial prefixes log-uniform in [1e4, 1e6], "
+                        "RP 100/250; terms: the paper-1m percentile terms, aggregate terms scaled by |J|/15",
+            "time": "virtual: Poisson arrivals, each serve step advances the clock by its wall time",
+            "rates": results}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -446,6 +500,10 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-layers comparison")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency sweep")
+    ap.add_argument("--serve-requests", type=int, default=400, help="requests per rate of the serving sweep")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 800.0, 3200.0],
+                    help="request arrival rates (per second) of the serving sweep")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
     if args.impl == "reference":

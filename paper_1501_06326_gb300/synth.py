@@ -256,7 +256,29 @@ WORKLOADS = {
         recipe="plain", seed=20150127, elt_seed=20150130, layer_seed=20150131, n_layers=16,
         max_layer_elts=32, return_periods=(100.0, 250.0),
     ),
+    # layer requests served against a resident YET and pool: the paper-1m YET, a pool of 200
+    # ELTs, |J| ~ U{1..15}, trial prefixes log-uniform in [1e4, 1e6]
+    "serving": dict(
+        n_trials=1_000_000, mean_events=1000.0, catalogue=2_000_000, n_elts=200, entries=10_000,
+        recipe="plain", seed=20150127, elt_seed=20150132, request_seed=20150133, max_layer_elts=15,
+        min_prefix=10_000, max_prefix=1_000_000, return_periods=(100.0, 250.0),
+    ),
 }
+
+
+def serving_requests(spec, n: int, seed: int):
+    """Requests of a serving workload: per request the sorted pool ids of its layer
+    (|J| ~ U{1..max_layer_elts} from the pool) and its trial prefix (log-uniform in
+    [min_prefix, max_prefix]); inter-arrival gaps are drawn by the caller."""
+    rng = _rng(seed, _S_LAYERS)
+    out = []
+    for _ in range(n):
+        k = int(rng.integers(1, spec["max_layer_elts"] + 1))
+        ids = np.sort(rng.choice(spec["n_elts"], size=k, replace=False)).astype(np.int32)
+        lo, hi = math.log(spec["min_prefix"]), math.log(spec["max_prefix"])
+        t_end = int(round(math.exp(rng.uniform(lo, hi))))
+        out.append((ids, min(max(t_end, 1), spec["n_trials"])))
+    return out
 
 
 def workload_layers(spec, pool) -> list:
