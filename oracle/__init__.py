@@ -60,7 +60,7 @@ def _load():
             lib.or_beta_params.restype = ctypes.c_int
             lib.or_run_layer.argtypes = [
                 i64, P, P, i32,  # yet
-                i32, P, P, P, P, P, P, P,  # elts
+                i32, P, P, P, P, P, P, P, P,  # elts (ids, offsets, events, mean, sigma, sigma_c, exposure, terms)
                 dbl, dbl, dbl, dbl,  # layer terms
                 u64, ctypes.c_int,  # seed, primary_only
                 i64, P,  # trial list
@@ -68,11 +68,19 @@ def _load():
             ]
             lib.or_run_layer.restype = ctypes.c_int
             lib.or_event_losses.argtypes = [
-                P, P, i32, i32, P, P, P, P, P, P, P, u64, ctypes.c_int, i64, i64, P, i64
+                P, P, i32, i32, P, P, P, P, P, P, P, P, u64, ctypes.c_int, i64, i64, P, i64
             ]
             lib.or_event_losses.restype = i64
             lib.or_uniform_batch.argtypes = [u64, i64, P, P, P, P]
             lib.or_uniform_batch.restype = None
+            lib.or_combined_normal_batch.argtypes = [u64, i64, P, P, P, dbl, dbl, P, P]
+            lib.or_combined_normal_batch.restype = None
+            lib.or_normcdfinv_batch.argtypes = [i64, P, P]
+            lib.or_normcdfinv_batch.restype = None
+            lib.or_normcdf.argtypes = [dbl]
+            lib.or_normcdf.restype = dbl
+            lib.or_uniform_event.argtypes = [u64, i64, i32]
+            lib.or_uniform_event.restype = dbl
             lib.or_betaincinv_batch.argtypes = [i64, P, P, P, P]
             lib.or_betaincinv_batch.restype = None
             lib.or_betainc_batch.argtypes = [i64, P, P, P, P]
@@ -167,6 +175,47 @@ def beta_params(mu: float, sigma: float, max_l: float):
 
 
 # ---------------------------------------------------------------- ARA
+def _elt_arrays(pool):
+    """The pool's arrays in the oracle's argument order (sigma_c: None when the
+    records carry no correlated standard deviation)."""
+    sc = getattr(pool, "sigma_c", None)
+    return [
+        _c(pool.elt_ids, np.int32), _c(pool.rec_offsets, np.int64), _c(pool.event_ids, np.int32),
+        _c(pool.mean, np.float32), _c(pool.sigma, np.float32), None if sc is None else _c(sc, np.float32),
+        _c(pool.exposure, np.float32), _c(pool.terms, np.float32),
+    ]
+
+
+def uniform_event(seed: int, trial: int, k: int) -> float:
+    """The event-occurrence uniform z_(E) (Section 3.1 (ii)): shared by all ELTs."""
+    return _load().or_uniform_event(int(seed), int(trial), int(k))
+
+
+def normcdf(v: float) -> float:
+    """Standard normal CDF (Section 3.2 step v)."""
+    return _load().or_normcdf(float(v))
+
+
+def normcdfinv_batch(p) -> np.ndarray:
+    """Standard normal quantile (Section 3.2 step ii)."""
+    p = _c(p, np.float64)
+    out = np.zeros(p.shape[0], np.float64)
+    _load().or_normcdfinv_batch(p.shape[0], _p(p), _p(out))
+    return out
+
+
+def combined_normal_batch(seed: int, trials, ks, elts, sigma_i: float, sigma_c: float):
+    """(v, z) of the five steps of Section 3.2 for each (trial, k, ELT pool id)."""
+    t = _c(trials, np.int64)
+    k = _c(ks, np.int32)
+    e = _c(elts, np.int32)
+    v = np.zeros(t.shape[0], np.float64)
+    z = np.zeros(t.shape[0], np.float64)
+    _load().or_combined_normal_batch(int(seed), t.shape[0], _p(t), _p(k), _p(e), float(sigma_i), float(sigma_c),
+                                     _p(v), _p(z))
+    return v, z
+
+
 def run_layer(yet, pool, layer_terms, seed: int = 0, primary_only: bool = False,
               trials=None, threads: int = 0):
     """Algorithm 1 with secondary uncertainty over one layer (Sections 2.2, 3.3).
@@ -186,15 +235,11 @@ def run_layer(yet, pool, layer_terms, seed: int = 0, primary_only: bool = False,
     gross = np.zeros(n, np.float64)
     hits = np.zeros(n, np.int64)
     hh = np.zeros(n, np.uint64)
-    arrs = [
-        _c(pool.elt_ids, np.int32), _c(pool.rec_offsets, np.int64), _c(pool.event_ids, np.int32),
-        _c(pool.mean, np.float32), _c(pool.sigma, np.float32), _c(pool.exposure, np.float32),
-        _c(pool.terms, np.float32),
-    ]
+    arrs = _elt_arrays(pool)
     occ_r, occ_l, agg_r, agg_l = (float(v) for v in layer_terms)
     rc = lib.or_run_layer(
         yet.n_trials, _p(offs), _p(ids), int(yet.catalogue_size),
-        pool.n_elts, *[_p(a) for a in arrs],
+        pool.n_elts, *[_p(a) if a is not None else None for a in arrs],
         occ_r, occ_l, agg_r, agg_l, int(seed), int(bool(primary_only)),
         0 if tl is None else n, _p(tl) if tl is not None else None,
         _p(ylt), _p(gross), _p(hits), _p(hh), int(threads),
@@ -212,13 +257,9 @@ def event_losses(yet, pool, seed=0, primary_only=True, t_begin=0, t_end=None):
     ids = _c(yet.event_ids, np.int32)
     cap = int(offs[t_end] - offs[t_begin]) + 1
     out = np.zeros(cap, np.float64)
-    arrs = [
-        _c(pool.elt_ids, np.int32), _c(pool.rec_offsets, np.int64), _c(pool.event_ids, np.int32),
-        _c(pool.mean, np.float32), _c(pool.sigma, np.float32), _c(pool.exposure, np.float32),
-        _c(pool.terms, np.float32),
-    ]
+    arrs = _elt_arrays(pool)
     n = lib.or_event_losses(
-        _p(offs), _p(ids), int(yet.catalogue_size), pool.n_elts, *[_p(a) for a in arrs],
+        _p(offs), _p(ids), int(yet.catalogue_size), pool.n_elts, *[_p(a) if a is not None else None for a in arrs],
         int(seed), int(bool(primary_only)), int(t_begin), int(t_end), _p(out), cap,
     )
     if n < 0:

@@ -37,6 +37,12 @@
  *     [2^-24, 1 - 2^-24], is exact in both FP32 and FP64 and has an exact
  *     complement 1 - z on the same grid; with sigma_C = 0 the
  *     five-step combination of Section 3.2 returns z unchanged;
+ *   - records may carry a correlated standard deviation sigma_C (Section
+ *     3.1): the Beta then uses sigma = sigma_I + sigma_C (Section 3.2 step
+ *     i), and its uniform combines z_(Prog,E) with the event-occurrence
+ *     uniform z_(E), one draw per (trial, event index) shared by every ELT,
+ *     taken from the same Philox stream with the ELT word 0xFFFFFFFF; the
+ *     transform of step ii, written as the CDF integral, is the quantile;
  *   - a record with mu = 0 contributes nothing; a record with sigma = 0 has
  *     no secondary uncertainty and contributes mu;
  *   - PML(RP) is the m-th largest year loss, m = ceil(N / RP), and TVaR(RP)
@@ -93,6 +99,61 @@ double or_uniform(uint64_t seed, int64_t trial, int32_t k, int32_t elt_id)
     key[1] = (uint32_t)(seed >> 32);
     or_philox4x32_10(ctr, key, w);
     return ((double)(w[0] >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+/* The event-occurrence uniform z_(E) of Section 3.1 (ii), shared by all  */
+/* ELTs (and layers) for one occurrence: the same stream with the ELT      */
+/* word of the counter set to 0xFFFFFFFF, which no pool id takes.          */
+double or_uniform_event(uint64_t seed, int64_t trial, int32_t k)
+{
+    return or_uniform(seed, trial, k, (int32_t)-1);
+}
+
+/* ------------------------------------------------------------------ */
+/* Standard normal CDF and quantile (Section 3.2 steps ii and v; the   */
+/* transform written as the CDF integral is read as the quantile).     */
+/* ------------------------------------------------------------------ */
+double or_normcdf(double v)
+{
+    return 0.5 * erfc(-v / sqrt(2.0));
+}
+
+/* The v with Phi(v) = p, by bisection on Phi (each halving keeps the root */
+/* bracketed) down to adjacent doubles; the upper half by symmetry.        */
+double or_normcdfinv(double p)
+{
+    double lo = -40.0, hi = 0.0;
+    int it;
+    if (!(p > 0.0)) return -INFINITY;
+    if (!(p < 1.0)) return INFINITY;
+    if (p > 0.5) return -or_normcdfinv(1.0 - p);
+    for (it = 0; it < 2000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        if (or_normcdf(mid) < p) lo = mid; else hi = mid;
+    }
+    return (p - or_normcdf(lo) <= or_normcdf(hi) - p) ? lo : hi;
+}
+
+/* Section 3.2: the uniform fed to the Beta quantile from z_(Prog,E) = zp  */
+/* and z_(E) = ze: sigma = sI + sC, v_P = Phi^-1(zp), v_E = Phi^-1(ze),    */
+/* LC = v_P sI / sigma + v_E sC / sigma, v = LC / sqrt((sI/sigma)^2 +      */
+/* (sC/sigma)^2), z = Phi(v).  The two extreme cases the model names are   */
+/* exact: sC = 0 gives zp, sI = 0 gives ze.  Returns v; *z and *zc receive  */
+/* Phi(v) and 1 - Phi(v), each computed directly.                           */
+double or_combined_normal(double zp, double ze, double s_i, double s_c, double *z, double *zc)
+{
+    double s, vp, ve, lc, v;
+    if (s_c == 0.0) { *z = zp; *zc = 1.0 - zp; return or_normcdfinv(zp); }
+    if (s_i == 0.0) { *z = ze; *zc = 1.0 - ze; return or_normcdfinv(ze); }
+    s = s_i + s_c;
+    vp = or_normcdfinv(zp);
+    ve = or_normcdfinv(ze);
+    lc = vp * (s_i / s) + ve * (s_c / s);
+    v = lc / sqrt((s_i / s) * (s_i / s) + (s_c / s) * (s_c / s));
+    *z = or_normcdf(v);
+    *zc = or_normcdf(-v);
+    return v;
 }
 
 /* ------------------------------------------------------------------ */
@@ -226,16 +287,23 @@ int or_beta_params(double mu, double sigma, double max_l, double *alpha, double 
     return 0;
 }
 
-/* One record's loss with or without secondary uncertainty. */
-static double record_loss(double mu, double sigma, double max_l, int primary_only,
+/* One record's loss with or without secondary uncertainty.  sigma_c is the */
+/* record's correlated standard deviation (Section 3.1): the Beta uses      */
+/* sigma = sigma_I + sigma_C (Section 3.2 step i), and its uniform is the   */
+/* combination of z_(Prog,E) and z_(E).                                      */
+static double record_loss(double mu, double sigma, double sigma_c, double max_l, int primary_only,
                           uint64_t seed, int64_t trial, int32_t k, int32_t elt_id)
 {
-    double a, b;
+    double a, b, zp, z, zc;
     int kind;
     if (primary_only) return mu;
-    kind = or_beta_params(mu, sigma, max_l, &a, &b);
+    kind = or_beta_params(mu, sigma + sigma_c, max_l, &a, &b);
     if (kind != 0) return mu; /* mu == 0 or sigma == 0 (invalid records are rejected at load) */
-    return max_l * or_betaincinv(or_uniform(seed, trial, k, elt_id), a, b);
+    zp = or_uniform(seed, trial, k, elt_id);
+    if (sigma_c == 0.0) return max_l * or_betaincinv(zp, a, b);
+    or_combined_normal(zp, or_uniform_event(seed, trial, k), sigma, sigma_c, &z, &zc);
+    /* the root on the side where it keeps its relative precision */
+    return max_l * ((z <= 0.5) ? or_betaincinv(z, a, b) : 1.0 - or_betaincinv_complement(zc, a, b));
 }
 
 static double clamp_terms(double l, double retention, double limit)
@@ -269,6 +337,7 @@ static uint64_t mix64(uint64_t v)
 int or_run_layer(int64_t n_trials, const int64_t *offsets, const int32_t *ids, int32_t catalogue,
                  int32_t n_elts, const int32_t *elt_pool_ids, const int64_t *rec_offsets,
                  const int32_t *rec_events, const float *rec_mean, const float *rec_sigma,
+                 const float *rec_sigma_c /* or NULL: all zero */,
                  const float *rec_exposure, const float *elt_terms /* [n_elts*3] or NULL */,
                  double occ_ret, double occ_lim, double agg_ret, double agg_lim,
                  uint64_t seed, int primary_only,
@@ -313,8 +382,9 @@ int or_run_layer(int64_t n_trials, const int64_t *offsets, const int32_t *ids, i
                     if (r < 0) continue;                          /* no record: zero loss */
                     ++hits;
                     hh += mix64(((uint64_t)(uint32_t)k << 32) | (uint32_t)elt_pool_ids[jj]);
-                    l_E = record_loss(rec_mean[r], rec_sigma[r], rec_exposure[r], primary_only,
-                                      seed, t, k, elt_pool_ids[jj]);  /* secondary uncertainty */
+                    l_E = record_loss(rec_mean[r], rec_sigma[r], rec_sigma_c ? rec_sigma_c[r] : 0.0f,
+                                      rec_exposure[r], primary_only, seed, t, k,
+                                      elt_pool_ids[jj]);               /* secondary uncertainty */
                     G_sum += l_E;
                     if (elt_terms)                                 /* ELT financial terms */
                         l_E = (double)elt_terms[3 * jj + 2] *
@@ -342,7 +412,7 @@ int or_run_layer(int64_t n_trials, const int64_t *offsets, const int32_t *ids, i
 int64_t or_event_losses(const int64_t *offsets, const int32_t *ids, int32_t catalogue,
                         int32_t n_elts, const int32_t *elt_pool_ids, const int64_t *rec_offsets,
                         const int32_t *rec_events, const float *rec_mean, const float *rec_sigma,
-                        const float *rec_exposure, const float *elt_terms,
+                        const float *rec_sigma_c, const float *rec_exposure, const float *elt_terms,
                         uint64_t seed, int primary_only, int64_t t_begin, int64_t t_end,
                         double *out, int64_t cap)
 {
@@ -363,8 +433,8 @@ int64_t or_event_losses(const int64_t *offsets, const int32_t *ids, int32_t cata
                 int32_t r = row_of[(int64_t)jj * catalogue + ids[pos]];
                 double l_E;
                 if (r < 0) continue;
-                l_E = record_loss(rec_mean[r], rec_sigma[r], rec_exposure[r], primary_only, seed, t, k,
-                                  elt_pool_ids[jj]);
+                l_E = record_loss(rec_mean[r], rec_sigma[r], rec_sigma_c ? rec_sigma_c[r] : 0.0f, rec_exposure[r],
+                                  primary_only, seed, t, k, elt_pool_ids[jj]);
                 if (elt_terms)
                     l_E = (double)elt_terms[3 * jj + 2] * clamp_terms(l_E, elt_terms[3 * jj + 0], elt_terms[3 * jj + 1]);
                 l_T += l_E;
@@ -433,6 +503,24 @@ void or_uniform_batch(uint64_t seed, int64_t n, const int64_t *trials, const int
 {
     int64_t i;
     for (i = 0; i < n; ++i) out[i] = or_uniform(seed, trials[i], ks[i], elts[i]);
+}
+
+void or_combined_normal_batch(uint64_t seed, int64_t n, const int64_t *trials, const int32_t *ks,
+                              const int32_t *elts, double s_i, double s_c, double *v_out, double *z_out)
+{
+    int64_t i;
+    for (i = 0; i < n; ++i) {
+        double z, zc;
+        v_out[i] = or_combined_normal(or_uniform(seed, trials[i], ks[i], elts[i]),
+                                      or_uniform_event(seed, trials[i], ks[i]), s_i, s_c, &z, &zc);
+        if (z_out) z_out[i] = z;
+    }
+}
+
+void or_normcdfinv_batch(int64_t n, const double *p, double *out)
+{
+    int64_t i;
+    for (i = 0; i < n; ++i) out[i] = or_normcdfinv(p[i]);
 }
 
 void or_betaincinv_batch(int64_t n, const double *p, const double *a, const double *b, double *out)

@@ -41,7 +41,7 @@ import numpy as np
 _CHUNK = 1 << 24
 
 # stream ids within one workload seed
-_S_COUNTS, _S_IDS, _S_ELT, _S_LAYERS = 1, 2, 3, 4
+_S_COUNTS, _S_IDS, _S_ELT, _S_LAYERS, _S_CORR = 1, 2, 3, 4, 5
 
 
 @dataclasses.dataclass
@@ -78,6 +78,7 @@ class ELTPool:
     sigma: np.ndarray  # float32 [R]
     exposure: np.ndarray  # float32 [R]
     terms: np.ndarray  # float32 [n, 3]: retention, limit, share
+    sigma_c: Optional[np.ndarray] = None  # float32 [R]: correlated standard deviation (None: all zero)
 
     @property
     def n_elts(self) -> int:
@@ -86,13 +87,15 @@ class ELTPool:
     def subset(self, positions) -> "ELTPool":
         """The ELTs at the given pool positions, as a new pool (copies)."""
         positions = list(positions)
-        ev, mu, sg, ex, offs = [], [], [], [], [0]
+        ev, mu, sg, ex, sc, offs = [], [], [], [], [], [0]
         for p in positions:
             lo, hi = int(self.rec_offsets[p]), int(self.rec_offsets[p + 1])
             ev.append(self.event_ids[lo:hi])
             mu.append(self.mean[lo:hi])
             sg.append(self.sigma[lo:hi])
             ex.append(self.exposure[lo:hi])
+            if self.sigma_c is not None:
+                sc.append(self.sigma_c[lo:hi])
             offs.append(offs[-1] + hi - lo)
         cat = lambda xs, dt: (np.concatenate(xs) if xs else np.zeros(0, dt)).astype(dt)
         return ELTPool(
@@ -103,6 +106,7 @@ class ELTPool:
             sigma=cat(sg, np.float32),
             exposure=cat(ex, np.float32),
             terms=self.terms[positions].copy(),
+            sigma_c=None if self.sigma_c is None else cat(sc, np.float32),
         )
 
 
@@ -177,6 +181,7 @@ def make_elt_pool(
     first_id: int = 0,
     shape_floor: float = 0.05,
     stress_range=(0.2, 50.0),
+    correlated: float = 0.0,
 ) -> ELTPool:
     """A pool of ``n_elts`` ELTs with ``entries`` distinct events each.
 
@@ -186,6 +191,10 @@ def make_elt_pool(
     and sigma follow from the Beta moments.  Pool ids are
     ``first_id .. first_id + n_elts - 1``; terms are the identity
     (retention 0, limit +inf, share 1).
+    ``correlated > 0`` splits each record's sigma into an independent and a
+    correlated part (Section 3.1): sigma_C = sigma * u, sigma_I = sigma - sigma_C
+    with u ~ U(0, correlated) per record, so sigma_I + sigma_C (and the Beta
+    shapes) are those of the recipe.
     """
     if entries > catalogue_size:
         raise ValueError("an ELT cannot hold more distinct events than the catalogue")
@@ -214,14 +223,21 @@ def make_elt_pool(
     offs = np.zeros(n_elts + 1, dtype=np.int64)
     offs[1:] = np.cumsum([len(e) for e in ev_l])
     terms = np.tile(np.array([0.0, np.inf, 1.0], dtype=np.float32), (n_elts, 1))
+    sigma = np.concatenate(sg_l) if sg_l else np.zeros(0, np.float32)
+    sigma_c = None
+    if correlated > 0.0:
+        u = _rng(seed, _S_CORR).uniform(0.0, correlated, size=sigma.shape[0])
+        sigma_c = (sigma.astype(np.float64) * u).astype(np.float32)
+        sigma = (sigma.astype(np.float64) - sigma_c).astype(np.float32)
     return ELTPool(
         elt_ids=np.arange(first_id, first_id + n_elts, dtype=np.int32),
         rec_offsets=offs,
         event_ids=np.concatenate(ev_l) if ev_l else np.zeros(0, np.int32),
         mean=np.concatenate(mu_l) if mu_l else np.zeros(0, np.float32),
-        sigma=np.concatenate(sg_l) if sg_l else np.zeros(0, np.float32),
+        sigma=sigma,
         exposure=np.concatenate(ex_l) if ex_l else np.zeros(0, np.float32),
         terms=terms,
+        sigma_c=sigma_c,
     )
 
 

@@ -1,0 +1,98 @@
+"""Pins of the oracle's two-sigma secondary uncertainty (Section 3.1 inputs,
+Section 3.2 five-step combination): the normal CDF and quantile, the two
+extreme cases the model names (sigma_C = 0: z = z_(Prog,E); sigma_I = 0:
+z = z_(E), shared by all ELTs of an occurrence), and the distribution of the
+combined normal (Monte Carlo)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1501_06326_gb300 import synth
+
+
+def test_normal_cdf_closed_values():
+    assert oracle.normcdf(0.0) == 0.5
+    assert abs(oracle.normcdf(1.959963984540054) - 0.975) < 1e-15
+    assert abs(oracle.normcdf(-1.0) - 0.15865525393145707) < 1e-16
+    for v in (-5.0, -1.3, 0.7, 4.2):
+        assert abs(oracle.normcdf(v) + oracle.normcdf(-v) - 1.0) < 1e-15
+
+
+def test_normal_quantile_round_trip_and_library_pin():
+    # the lower half round-trips to FP64 resolution (above 1/2, 1 - Phi(v) is not
+    # representable near 1, which is why the oracle carries the complement Phi(-v))
+    v = np.linspace(-5.3, 0.0, 201)
+    p = np.array([oracle.normcdf(x) for x in v])
+    back = oracle.normcdfinv_batch(p)
+    assert np.max(np.abs(back - v)) < 1e-12
+    # on the uniform grid 1 - p is exact, and the quantile is odd about 1/2
+    g = (np.arange(0, 1 << 23, 4099) + 0.5) / 2.0**23
+    assert np.array_equal(oracle.normcdfinv_batch(1.0 - g), -oracle.normcdfinv_batch(g))
+    special = pytest.importorskip("scipy.special")
+    z = (np.arange(1, 2000) + 0.5) / 2000.0
+    assert np.allclose(oracle.normcdfinv_batch(z), special.ndtri(z), rtol=1e-13, atol=1e-13)
+
+
+def _tiny(corr_split):
+    yet = synth.make_yet(300, 40.0, 2000, 91)
+    pool = synth.make_elt_pool(2, 600, 2000, 92, correlated=0.5)
+    if corr_split == "independent":
+        pool.sigma_c = np.zeros_like(pool.sigma_c)
+    return yet, pool
+
+
+def test_sigma_c_zero_is_the_independent_model():
+    yet, pool = _tiny("independent")
+    terms = (0.0, math.inf, 0.0, math.inf)
+    plain = synth.ELTPool(pool.elt_ids, pool.rec_offsets, pool.event_ids, pool.mean, pool.sigma, pool.exposure,
+                          pool.terms)
+    a = oracle.run_layer(yet, pool, terms, seed=4)
+    b = oracle.run_layer(yet, plain, terms, seed=4)
+    assert np.array_equal(a["ylt"], b["ylt"])
+
+
+def test_sigma_i_zero_makes_the_elts_of_an_occurrence_share_their_uniform():
+    # two ELTs with identical records and sigma_I = 0: every occurrence draws the
+    # same z_(E) for both, so each event's loss is exactly twice one ELT's
+    yet = synth.make_yet(300, 40.0, 2000, 93)
+    one = synth.make_elt_pool(1, 600, 2000, 94)
+    sc = one.sigma.copy()
+    zero = np.zeros_like(sc)
+    cat = lambda a: np.concatenate([a, a])
+    two = synth.ELTPool(np.array([0, 1], np.int32), np.array([0, 600, 1200], np.int64), cat(one.event_ids),
+                        cat(one.mean), cat(zero), cat(one.exposure), np.tile(one.terms, (2, 1)), cat(sc))
+    single = synth.ELTPool(one.elt_ids, one.rec_offsets, one.event_ids, one.mean, zero, one.exposure, one.terms, sc)
+    terms = (0.0, math.inf, 0.0, math.inf)
+    y2 = oracle.run_layer(yet, two, terms, seed=8)["ylt"]
+    y1 = oracle.run_layer(yet, single, terms, seed=8)["ylt"]
+    assert np.array_equal(y2, 2.0 * y1)
+    # with sigma_C = 0 instead, the two ELTs draw independently
+    indep = synth.ELTPool(two.elt_ids, two.rec_offsets, two.event_ids, two.mean, cat(sc), two.exposure, two.terms)
+    assert not np.array_equal(oracle.run_layer(yet, indep, terms, seed=8)["ylt"], 2.0 * y1)
+
+
+@pytest.mark.parametrize("s_i,s_c", [(1.0, 1.0), (0.6, 0.8), (0.3, 0.05)])
+def test_combined_normal_distribution(s_i, s_c):
+    n = 200_000
+    rng = np.random.default_rng(5)
+    t = rng.integers(0, 1 << 40, n)
+    k = rng.integers(0, 5000, n).astype(np.int32)
+    v1, z1 = oracle.combined_normal_batch(11, t, k, np.full(n, 3, np.int32), s_i, s_c)
+    v2, _ = oracle.combined_normal_batch(11, t, k, np.full(n, 7, np.int32), s_i, s_c)
+    se = 1.0 / math.sqrt(n)
+    assert abs(v1.mean()) < 5 * se and abs(v1.var() - 1.0) < 10 * se
+    rho = s_c * s_c / (s_i * s_i + s_c * s_c)  # shared z_(E), independent z_(Prog,E)
+    assert abs(np.corrcoef(v1, v2)[0, 1] - rho) < 5 * se
+    # z = Phi(v) is uniform (Kolmogorov-Smirnov distance)
+    zs = np.sort(z1)
+    ks = np.max(np.abs(zs - (np.arange(1, n + 1) - 0.5) / n))
+    assert ks < 1.63 / math.sqrt(n)
+
+
+def test_event_uniform_is_a_separate_stream():
+    zs = [oracle.uniform_event(2, t, k) for t in range(40) for k in range(5)]
+    zp = [oracle.uniform(2, t, k, 0) for t in range(40) for k in range(5)]
+    assert len(set(zs)) == len(zs) and not set(zs) & set(zp)
