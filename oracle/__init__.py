@@ -87,6 +87,8 @@ def _load():
             lib.or_betainc_batch.restype = None
             lib.or_betaincinv_complement.argtypes = [dbl, dbl, dbl]
             lib.or_betaincinv_complement.restype = dbl
+            lib.or_betaincinv_upper.argtypes = [dbl, dbl, dbl]
+            lib.or_betaincinv_upper.restype = dbl
             lib.or_sort_desc.argtypes = [P, i64, P]
             lib.or_sort_desc.restype = ctypes.c_int
             lib.or_pml_tvar.argtypes = [P, i64, P, i32, P, P]
@@ -132,6 +134,11 @@ def betaincinv(p: float, a: float, b: float) -> float:
 def betaincinv_complement(p: float, a: float, b: float) -> float:
     """1 - InvCDF_beta(p; a, b), accurate when the root is close to 1."""
     return _load().or_betaincinv_complement(float(p), float(a), float(b))
+
+
+def betaincinv_upper(q: float, a: float, b: float) -> float:
+    """InvCDF_beta(1 - q; a, b) from the upper-tail probability q."""
+    return _load().or_betaincinv_upper(float(q), float(a), float(b))
 
 
 def uniform_batch(seed: int, trials, ks, elts) -> np.ndarray:

@@ -265,6 +265,18 @@ double or_betaincinv_complement(double p, double a, double b)
     return betaincinv_small_root(1.0 - p, b, a);
 }
 
+/* InvCDF_beta(1 - q; a, b): the x with 1 - I_x(a, b) = q, from the upper-  */
+/* tail probability q itself (so that a q far below 1 keeps its precision). */
+/* When the root lies above 1/2 (q <= I_{1/2}(b, a)) its complement y = 1 - x */
+/* is the small root of I_y(b, a) = q.                                       */
+double or_betaincinv_upper(double q, double a, double b)
+{
+    if (!(q > 0.0)) return 1.0;
+    if (!(q < 1.0)) return 0.0;
+    if (q <= or_betainc(0.5, b, a)) return 1.0 - betaincinv_small_root(q, b, a);
+    return betaincinv_small_root(1.0 - q, a, b);
+}
+
 /* Beta shape parameters of one XELT record (Section 3.3).  Returns 0 when
  * the record carries secondary uncertainty (alpha, beta set), 1 when it is
  * deterministic (sigma == 0 or mu == 0), -1 when it is invalid
@@ -302,8 +314,8 @@ static double record_loss(double mu, double sigma, double sigma_c, double max_l,
     zp = or_uniform(seed, trial, k, elt_id);
     if (sigma_c == 0.0) return max_l * or_betaincinv(zp, a, b);
     or_combined_normal(zp, or_uniform_event(seed, trial, k), sigma, sigma_c, &z, &zc);
-    /* the root on the side where it keeps its relative precision */
-    return max_l * ((z <= 0.5) ? or_betaincinv(z, a, b) : 1.0 - or_betaincinv_complement(zc, a, b));
+    /* z above 1/2 is solved from 1 - z = Phi(-v), which keeps its precision */
+    return max_l * ((z <= 0.5) ? or_betaincinv(z, a, b) : or_betaincinv_upper(zc, a, b));
 }
 
 static double clamp_terms(double l, double retention, double limit)

@@ -96,3 +96,42 @@ def test_event_uniform_is_a_separate_stream():
     zs = [oracle.uniform_event(2, t, k) for t in range(40) for k in range(5)]
     zp = [oracle.uniform(2, t, k, 0) for t in range(40) for k in range(5)]
     assert len(set(zs)) == len(zs) and not set(zs) & set(zp)
+
+
+Q_GRID = (0.9, 0.5, 0.1, 1e-3, 1e-7, 1e-12)
+
+
+@pytest.mark.parametrize("q", Q_GRID)
+def test_upper_tail_quantile_closed_forms(q):
+    # 1 - I_x(a, 1) = 1 - x^a = q  =>  x = (1 - q)^(1/a)
+    for a in (0.3, 1.0, 7.5):
+        assert abs(oracle.betaincinv_upper(q, a, 1.0) - math.exp(math.log1p(-q) / a)) <= 1e-12
+    # 1 - I_x(1, b) = (1 - x)^b = q  =>  x = 1 - q^(1/b)
+    for b in (0.3, 1.0, 7.5):
+        assert abs(oracle.betaincinv_upper(q, 1.0, b) + math.expm1(math.log(q) / b)) <= 1e-12
+    # arcsine law: I_x(1/2, 1/2) = (2 / pi) asin(sqrt(x))  =>  x = cos^2(pi q / 2)
+    assert abs(oracle.betaincinv_upper(q, 0.5, 0.5) - math.cos(math.pi * q / 2.0) ** 2) <= 1e-12
+
+
+@pytest.mark.parametrize("s_i,s_c", [(300.0, 100.0), (200.0, 200.0), (0.0, 400.0), (50.0, 350.0)])
+def test_correlated_record_loss_against_library_routines(s_i, s_c):
+    # one record (mean 1000, exposure 4000, sigma = s_i + s_c) hit once per trial:
+    # each year loss is max_l InvCDF_beta(Phi(v)), v the combined normal of the
+    # record's and the occurrence's uniforms (Section 3.2), here from SciPy's
+    # normal and Beta inverses (the upper half by the complemented inverse)
+    special = pytest.importorskip("scipy.special")
+    n, seed = 3000, 17
+    yet = synth.YET(np.arange(n + 1, dtype=np.int64), np.zeros(n, np.int32), 4)
+    pool = synth.ELTPool(np.array([5], np.int32), np.array([0, 1], np.int64), np.array([0], np.int32),
+                         np.array([1000.0], np.float32), np.array([s_i], np.float32), np.array([4000.0], np.float32),
+                         np.array([[0.0, np.inf, 1.0]], np.float32), np.array([s_c], np.float32))
+    got = oracle.run_layer(yet, pool, (0.0, math.inf, 0.0, math.inf), seed=seed)["ylt"]
+    t = np.arange(n, dtype=np.int64)
+    k = np.zeros(n, np.int32)
+    vp = special.ndtri(oracle.uniform_batch(seed, t, k, np.full(n, 5, np.int32)))
+    ve = special.ndtri(oracle.uniform_batch(seed, t, k, np.full(n, -1, np.int32)))
+    v = (s_i * vp + s_c * ve) / math.hypot(s_i, s_c)
+    _, a, b = oracle.beta_params(1000.0, s_i + s_c, 4000.0)
+    x = np.where(v <= 0.0, special.betaincinv(a, b, special.ndtr(v)), special.betainccinv(a, b, special.ndtr(-v)))
+    assert np.sum(v > 0.0) > n // 3 and np.sum(v < 0.0) > n // 3
+    assert np.allclose(got, 4000.0 * x, rtol=1e-9, atol=0.0)
