@@ -348,6 +348,28 @@ def run_gpu(args):
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
                "sample": f"first {min(args.cpu_trials, n_trials)} trials of the workload ({ev} evals, {dt:.1f} s)"}
 
+    # ---- two-part secondary uncertainty (correlated sigma) on the same layer; the plain
+    # layer pass is timed here too, on the same stream, for the comparison
+    correlated = None
+    if ws == 1 and not args.no_correlated:
+        eng.load_pool(pool)
+
+        def plain_layer():
+            eng.run_layer(pool.elt_ids, terms, seed, 0, n_trials, ylt)
+
+        for _ in range(3):
+            plain_layer()
+        torch.cuda.synchronize(dev)
+        steps_c = max(2, min(args.steps, 10))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps_c):
+            plain_layer()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        correlated = _correlated_leg(eng, synth, torch, dev, stream, spec, terms, n_trials, n_events, seed,
+                                     a.elapsed_time(b) / steps_c, args)
+
     # ---- batched layers (several layers in one pass over the YET) against one pass per layer
     batched = None
     if ws == 1 and not args.no_batched:
@@ -380,6 +402,8 @@ def run_gpu(args):
         }
         if global_pml is not None:
             line["global_pml_tvar"] = {"pml": list(global_pml[0]), "tvar": list(global_pml[1])}
+        if correlated is not None:
+            line["correlated"] = correlated
         if batched is not None:
             line["batched"] = batched
         if serving is not None:
@@ -434,6 +458,40 @@ def _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args)
             "layers": len(layers), "steps": steps, "ms_batched": ms_batch, "ms_plain": ms_plain,
             "layers_per_s": len(layers) / (ms_batch * 1e-3), "plain_layers_per_s": len(layers) / (ms_plain * 1e-3),
             "speedup": ms_plain / ms_batch, "evals_per_s": evals / (ms_batch * 1e-3)}
+
+
+def _correlated_leg(eng, synth, torch, dev, stream, spec, terms, n_trials, n_events, seed, ms_plain, args):
+    """The paper-1m layer with each record's sigma split into an independent and a
+    correlated part (sigma_C = sigma u, u ~ U(0, 0.5); the Beta shapes are those of
+    the main workload), loaded with ara_load_xelts: layer passes (index, gather,
+    losses) timed with CUDA events against the same passes on the plain pool."""
+    pool = synth.make_elt_pool(spec["n_elts"], spec["entries"], spec["catalogue"], spec["seed"],
+                               recipe=spec["recipe"], correlated=0.5)
+    eng.load_pool(pool)
+    out = torch.empty(n_trials, dtype=torch.float64, device=dev)
+
+    def layer():
+        eng.run_layer(pool.elt_ids, terms, seed, 0, n_trials, out)
+
+    for _ in range(3):
+        layer()
+    torch.cuda.synchronize(dev)
+    eng.timing(reset=True)
+    steps = max(2, min(args.steps, 10))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        layer()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    tm = eng.timing(reset=True)
+    calls = max(tm["layer_calls"], 1)
+    evals = n_events * pool.n_elts
+    return {"workload": f"{WORKLOAD} with sigma = sigma_I + sigma_C, sigma_C = sigma u, u ~ U(0, 0.5) per record",
+            "steps": steps, "ms_layer": ms, "ms_layer_plain": ms_plain, "evals_per_s": evals / (ms * 1e-3),
+            "gather_ms": tm["gather_ms"] / calls, "losses_ms": tm["losses_ms"] / calls,
+            "newton_pairs": eng.stats()["n_newton"]}
 
 
 def _serving_leg(eng, synth, offsets, args):
@@ -500,6 +558,7 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-layers comparison")
+    ap.add_argument("--no-correlated", action="store_true", help="skip the correlated-sigma layer")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency sweep")
     ap.add_argument("--serve-requests", type=int, default=400, help="requests per rate of the serving sweep")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 800.0, 3200.0],

@@ -163,6 +163,23 @@ ARA_API int ara_load_elts(ara_ctx *ctx, int32_t n_elts, const int32_t *elt_ids, 
                   const int32_t *event_ids, const float *mean, const float *sigma,
                   const float *exposure, const ara_elt_terms *terms);
 
+/* ara_load_elts with the two-part secondary uncertainty of Sections 3.1 and
+ * 3.2: each record's standard deviation is split into an independent part
+ * sigma_i and a correlated part sigma_c (both >= 0, finite).  The Beta of
+ * Section 3.3 takes sigma = sigma_i + sigma_c.  A record with sigma_c == 0
+ * draws its uniform z_(Prog,E) as in ara_load_elts; one with sigma_c > 0 uses
+ * z = Phi(v), v = (sigma_i Phi^-1(z_(Prog,E)) + sigma_c Phi^-1(z_(E))) /
+ * sqrt(sigma_i^2 + sigma_c^2), where z_(E) is the occurrence's uniform, shared
+ * by every ELT and layer: word 0 of the Philox block of ara_run_layer with the
+ * ELT word of the counter set to 0xFFFFFFFF (no pool id takes that value).
+ * sigma_i == 0 makes every ELT of an occurrence use z = z_(E).  Such ELTs keep
+ * 8 more bytes per record (the two weights).  sigma_c must not be NULL when
+ * there are records; the other arguments, ownership and errors are those of
+ * ara_load_elts. */
+ARA_API int ara_load_xelts(ara_ctx *ctx, int32_t n_elts, const int32_t *elt_ids, const int64_t *rec_offsets,
+                   const int32_t *event_ids, const float *mean, const float *sigma_i, const float *sigma_c,
+                   const float *exposure, const ara_elt_terms *terms);
+
 /* Run one layer over trials [trial_begin, trial_end) (Algorithm 1 with the
  * secondary uncertainty of Section 3.3) and write one year loss per trial to
  * ylt_out (FP64, trial_end - trial_begin entries).  The uniform of trial t,

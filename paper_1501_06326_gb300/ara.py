@@ -40,7 +40,7 @@ EXPORTED = (
     "ara_create", "ara_set_stream", "ara_load_yet", "ara_load_elts", "ara_run_layer",
     "ara_run_layer_diag", "ara_pml_tvar", "ara_sort_ylt", "ara_debug_uniforms",
     "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
-    "ara_pml_tvar_noalloc", "ara_run_layers", "ara_submit", "ara_serve_step", "ara_poll",
+    "ara_pml_tvar_noalloc", "ara_run_layers", "ara_submit", "ara_serve_step", "ara_poll", "ara_load_xelts",
 )
 ARA_NOALLOC_MAX_RP = 64
 
@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH):
     lib.ara_set_stream.argtypes = [P, P]
     lib.ara_load_yet.argtypes = [P, i64, P, P, i32]
     lib.ara_load_elts.argtypes = [P, i32, P, P, P, P, P, P, P]
+    lib.ara_load_xelts.argtypes = [P, i32, P, P, P, P, P, P, P, P]
     lib.ara_run_layer.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P]
     lib.ara_run_layer_diag.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P, ctypes.POINTER(Diag)]
     lib.ara_run_layers.argtypes = [P, i32, ctypes.POINTER(Layer), u64, i64, i64, P]
@@ -196,6 +197,14 @@ def ara_load_elts(h, n_elts, elt_ids, rec_offsets, event_ids, mean, sigma, expos
     return load_library().ara_load_elts(
         h, int(n_elts), _ptr(elt_ids, np.int32), _ptr(rec_offsets, np.int64), _ptr(event_ids, np.int32),
         _ptr(mean, np.float32), _ptr(sigma, np.float32), _ptr(exposure, np.float32), _ptr(terms, np.float32),
+    )
+
+
+def ara_load_xelts(h, n_elts, elt_ids, rec_offsets, event_ids, mean, sigma_i, sigma_c, exposure, terms=None):
+    return load_library().ara_load_xelts(
+        h, int(n_elts), _ptr(elt_ids, np.int32), _ptr(rec_offsets, np.int64), _ptr(event_ids, np.int32),
+        _ptr(mean, np.float32), _ptr(sigma_i, np.float32), _ptr(sigma_c, np.float32), _ptr(exposure, np.float32),
+        _ptr(terms, np.float32),
     )
 
 
@@ -318,10 +327,21 @@ class Ara:
         self._check(ara_load_elts(self._h, _len(elt_ids), elt_ids, rec_offsets, event_ids, mean, sigma, exposure,
                                   terms))
 
+    def load_xelts(self, elt_ids, rec_offsets, event_ids, mean, sigma_i, sigma_c, exposure, terms=None) -> None:
+        if terms is not None and isinstance(terms, np.ndarray):
+            terms = np.ascontiguousarray(terms, dtype=np.float32)
+        self._check(ara_load_xelts(self._h, _len(elt_ids), elt_ids, rec_offsets, event_ids, mean, sigma_i, sigma_c,
+                                   exposure, terms))
+
     def load_pool(self, pool) -> None:
-        """Load an ``ELTPool`` (see ``synth``)."""
-        self.load_elts(pool.elt_ids, pool.rec_offsets, pool.event_ids, pool.mean, pool.sigma, pool.exposure,
-                       pool.terms)
+        """Load an ``ELTPool`` (see ``synth``); a pool with a correlated part
+        ``sigma_c`` goes through ``ara_load_xelts``."""
+        if getattr(pool, "sigma_c", None) is not None:
+            self.load_xelts(pool.elt_ids, pool.rec_offsets, pool.event_ids, pool.mean, pool.sigma, pool.sigma_c,
+                            pool.exposure, pool.terms)
+        else:
+            self.load_elts(pool.elt_ids, pool.rec_offsets, pool.event_ids, pool.mean, pool.sigma, pool.exposure,
+                           pool.terms)
 
     @staticmethod
     def make_layer(elt_ids: Sequence[int], layer_terms, primary_only: bool = False, newton_only: bool = False):

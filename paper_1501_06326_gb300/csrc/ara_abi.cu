@@ -27,6 +27,8 @@ struct Elt {
   DevBuf recs;    // ara::Pair [n]
   DevBuf tab;     // float4 [n * kTabNodes] coarse quantile tables
   DevBuf tabf;    // float4 [n_fine * kTabFineStride] fine quantile tables
+  DevBuf wts;     // float2 [n] (w_I, w_C) per record, when the ELT holds correlated records
+  bool correlated = false;
   int64_t n = 0;
   int64_t n_fine = 0;
   float max_loss = 0.0f;  // largest loss a record can produce (max(exposure, mean))
@@ -64,7 +66,7 @@ struct ara_ctx {
   // ELT pool
   std::map<int32_t, Elt> pool;
   // per-layer index (grown on demand)
-  DevBuf bits, word_cnt, word_pairs, rankdir, mask, slot_cnt, pairs, pairs_hot, scan_tmp;
+  DevBuf bits, word_cnt, word_pairs, rankdir, mask, slot_cnt, pairs, pairs_hot, pairs_w, scan_tmp;
   DevBuf ev_buf, tile_cnt;  // hit-event records of the layer kernels
   DevBuf def_acc;           // per-trial FP64 sums of deferred occurrence losses
   DevBuf elt_stage, elt_recs_stage, elt_tab_stage, elt_flags;  // ELT load staging (grow-only)
@@ -282,35 +284,36 @@ int ara_load_yet(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int
   return ARA_OK;
 }
 
-int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int64_t* rec_offsets,
-                  const int32_t* event_ids, const float* mean, const float* sigma, const float* exposure,
-                  const ara_elt_terms* terms) {
+// ara_load_elts and ara_load_xelts; sigma_c == NULL: no correlated part.
+static int load_elts_impl(ara_ctx* c, const char* who, int32_t n_elts, const int32_t* elt_ids,
+                          const int64_t* rec_offsets, const int32_t* event_ids, const float* mean, const float* sigma,
+                          const float* sigma_c, const float* exposure, const ara_elt_terms* terms) {
   int rc = bind(c);
   if (rc) return rc;
-  if (n_elts < 1 || !elt_ids || !rec_offsets) return fail(c, ARA_EINVAL, "ara_load_elts: bad arguments");
+  if (n_elts < 1 || !elt_ids || !rec_offsets) return fail(c, ARA_EINVAL, "%s: bad arguments", who);
   std::vector<int32_t> ids(n_elts);
   std::vector<int64_t> offs(static_cast<size_t>(n_elts) + 1);
   std::vector<ara_elt_terms> tm(n_elts, ara_elt_terms{0.0f, INFINITY, 1.0f});
   ARA_CUDA(c, copy_params_to_host(ids.data(), elt_ids, sizeof(int32_t) * n_elts));
   ARA_CUDA(c, copy_params_to_host(offs.data(), rec_offsets, sizeof(int64_t) * (n_elts + 1)));
   if (terms) ARA_CUDA(c, copy_params_to_host(tm.data(), terms, sizeof(ara_elt_terms) * n_elts));
-  if (offs[0] != 0) return fail(c, ARA_EINVAL, "ara_load_elts: rec_offsets[0] must be 0");
+  if (offs[0] != 0) return fail(c, ARA_EINVAL, "%s: rec_offsets[0] must be 0", who);
   for (int32_t i = 0; i < n_elts; ++i) {
-    if (ids[i] < 0) return fail(c, ARA_EINVAL, "ara_load_elts: pool id %d is negative", ids[i]);
-    if (offs[i + 1] < offs[i]) return fail(c, ARA_EINVAL, "ara_load_elts: rec_offsets decrease at %d", i);
+    if (ids[i] < 0) return fail(c, ARA_EINVAL, "%s: pool id %d is negative", who, ids[i]);
+    if (offs[i + 1] < offs[i]) return fail(c, ARA_EINVAL, "%s: rec_offsets decrease at %d", who, i);
     if (offs[i + 1] - offs[i] >= static_cast<int64_t>(ara::kMaxEltRecords))
-      return fail(c, ARA_EINVAL, "ara_load_elts: ELT %d has %lld records (at most %u)", ids[i],
+      return fail(c, ARA_EINVAL, "%s: ELT %d has %lld records (at most %u)", who, ids[i],
                   (long long)(offs[i + 1] - offs[i]), ara::kMaxEltRecords - 1);
     const ara_elt_terms& t = tm[i];
     if (!(t.retention >= 0.0f) || !(t.limit >= 0.0f) || !(t.share >= 0.0f) || std::isnan(t.limit) ||
         !std::isfinite(t.retention) || !std::isfinite(t.share))
-      return fail(c, ARA_EINVAL, "ara_load_elts: ELT %d has invalid financial terms", ids[i]);
+      return fail(c, ARA_EINVAL, "%s: ELT %d has invalid financial terms", who, ids[i]);
     for (int32_t j = 0; j < i; ++j)
-      if (ids[j] == ids[i]) return fail(c, ARA_EINVAL, "ara_load_elts: pool id %d appears twice", ids[i]);
+      if (ids[j] == ids[i]) return fail(c, ARA_EINVAL, "%s: pool id %d appears twice", who, ids[i]);
   }
   const int64_t R = offs[n_elts];
   if (R > 0 && (!event_ids || !mean || !sigma || !exposure))
-    return fail(c, ARA_EINVAL, "ara_load_elts: record arrays are NULL");
+    return fail(c, ARA_EINVAL, "%s: record arrays are NULL", who);
   // ---- stage: inputs, prepared records and tables of all ELTs (grow-only context buffers)
   std::vector<int64_t> fine_off(static_cast<size_t>(n_elts) + 1, 0), work_off(static_cast<size_t>(n_elts) + 1, 0);
   for (int32_t i = 0; i < n_elts; ++i) {
@@ -318,7 +321,8 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     fine_off[i + 1] = fine_off[i] + ara::fine_table_cap(n);
     work_off[i + 1] = work_off[i] + static_cast<int64_t>(ara::build_tables_work_words(n));
   }
-  const size_t in_bytes = static_cast<size_t>(R) * (sizeof(int32_t) + 3 * sizeof(float) + sizeof(double2)) + 64;
+  const size_t in_bytes =
+      static_cast<size_t>(R) * (sizeof(int32_t) + 4 * sizeof(float) + sizeof(double2) + sizeof(float2)) + 64;
   if ((rc = reserve(c, c->elt_stage, in_bytes)) ||
       (rc = reserve(c, c->elt_recs_stage, sizeof(ara::Pair) * (R + 1))) ||
       (rc = reserve(c, c->elt_tab_stage, sizeof(float4) * ara::kTabNodes * (R + 1))) ||
@@ -331,7 +335,9 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
   float* d_mu = reinterpret_cast<float*>(d_ev + R);
   float* d_sg = d_mu + R;
   float* d_ex = d_sg + R;
-  double2* d_shapes = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(d_ex + R) + 15) & ~uintptr_t(15));
+  float* d_sc = d_ex + R;
+  double2* d_shapes = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(d_sc + R) + 15) & ~uintptr_t(15));
+  float2* d_w = reinterpret_cast<float2*>(d_shapes + R);
   ara::Pair* d_recs = static_cast<ara::Pair*>(c->elt_recs_stage.ptr);
   float4* d_tab = static_cast<float4*>(c->elt_tab_stage.ptr);
   float4* d_tabf = static_cast<float4*>(c->elt_tabf_stage.ptr);
@@ -343,6 +349,7 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     ARA_CUDA(c, cudaMemcpyAsync(d_mu, mean, sizeof(float) * R, kind_to_device(mean), c->stream));
     ARA_CUDA(c, cudaMemcpyAsync(d_sg, sigma, sizeof(float) * R, kind_to_device(sigma), c->stream));
     ARA_CUDA(c, cudaMemcpyAsync(d_ex, exposure, sizeof(float) * R, kind_to_device(exposure), c->stream));
+    if (sigma_c) ARA_CUDA(c, cudaMemcpyAsync(d_sc, sigma_c, sizeof(float) * R, kind_to_device(sigma_c), c->stream));
   }
   // per ELT: flags word, the largest event id (0xFFFFFFFF = none), candidates for fine
   // tables, the largest loss (FP32 bits)
@@ -358,7 +365,8 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     const int64_t o = offs[i], n = offs[i + 1] - offs[i];
     uint32_t* f = d_flags + 4 * i;
     ARA_CUDA(c, ara::launch_prepare_records(d_ev + o, d_mu + o, d_sg + o, d_ex + o, n, d_recs + o, d_shapes + o, f,
-                                            reinterpret_cast<int32_t*>(f + 1), f + 3, c->stream));
+                                            reinterpret_cast<int32_t*>(f + 1), f + 3, c->stream,
+                                            sigma_c ? d_sc + o : nullptr, sigma_c ? d_w + o : nullptr));
     c->launches += 1;
   }
   // coarse tables of every record in one launch, then each ELT's fine tables
@@ -393,26 +401,31 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     const char* why = nullptr;
     if (f & ara::kBadOrder) why = "event ids are not strictly increasing";
     else if (f & ara::kBadEventId) why = "an event id is negative";
-    else if (f & ara::kBadValue) why = "a mean, sigma or exposure is negative or not finite";
+    else if (f & ara::kBadValue) why = "a mean, sigma, sigma_c or exposure is negative or not finite";
     else if (f & ara::kBadExposure) why = "a record with mean > 0 and sigma > 0 has exposure <= mean";
-    if (why) return fail(c, ARA_EINVAL, "ara_load_elts: ELT %d: %s", ids[i], why);
+    if (why) return fail(c, ARA_EINVAL, "%s: ELT %d: %s", who, ids[i], why);
   }
   // ---- commit: each ELT keeps (or grows) its own buffers; the pool only changes once all checks passed
   for (int32_t i = 0; i < n_elts; ++i) {
     const int64_t o = offs[i], n = offs[i + 1] - offs[i];
     const int64_t n_fine = std::min<int64_t>(hf[4 * i + 2], ara::fine_table_cap(n));
+    const bool corr = (hf[4 * i] & ara::kHasCorrelated) != 0u;
     Elt& el = c->pool[ids[i]];
     if ((rc = reserve(c, el.events, sizeof(int32_t) * (n + 4))) ||
         (rc = reserve(c, el.recs, sizeof(ara::Pair) * (n > 0 ? n : 1))) ||
         (rc = reserve(c, el.tab, sizeof(float4) * ara::kTabNodes * (n > 0 ? n : 1))) ||
-        (rc = reserve(c, el.tabf, sizeof(float4) * ara::kTabFineStride * (n_fine > 0 ? n_fine : 1)))) {
+        (rc = reserve(c, el.tabf, sizeof(float4) * ara::kTabFineStride * (n_fine > 0 ? n_fine : 1))) ||
+        (corr && (rc = reserve(c, el.wts, sizeof(float2) * n)))) {
       release(c, el.events);
       release(c, el.recs);
       release(c, el.tab);
       release(c, el.tabf);
+      release(c, el.wts);
       c->pool.erase(ids[i]);
       return rc;
     }
+    if (!corr) release(c, el.wts);
+    el.correlated = corr;
     el.n = n;
     el.n_fine = n_fine;
     el.terms = tm[i];
@@ -423,6 +436,8 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
       ARA_CUDA(c, cudaMemcpyAsync(el.recs.ptr, d_recs + o, sizeof(ara::Pair) * n, cudaMemcpyDeviceToDevice, c->stream));
       ARA_CUDA(c, cudaMemcpyAsync(el.tab.ptr, d_tab + o * ara::kTabNodes, sizeof(float4) * ara::kTabNodes * n,
                                   cudaMemcpyDeviceToDevice, c->stream));
+      if (corr)
+        ARA_CUDA(c, cudaMemcpyAsync(el.wts.ptr, d_w + o, sizeof(float2) * n, cudaMemcpyDeviceToDevice, c->stream));
     }
     if (n_fine > 0) {
       ARA_CUDA(c, cudaMemcpyAsync(el.tabf.ptr, d_tabf + fine_off[i] * ara::kTabFineStride,
@@ -430,6 +445,27 @@ int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int6
     }
   }
   return ARA_OK;
+}
+
+int ara_load_elts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int64_t* rec_offsets,
+                  const int32_t* event_ids, const float* mean, const float* sigma, const float* exposure,
+                  const ara_elt_terms* terms) {
+  return load_elts_impl(c, "ara_load_elts", n_elts, elt_ids, rec_offsets, event_ids, mean, sigma, nullptr, exposure,
+                        terms);
+}
+
+int ara_load_xelts(ara_ctx* c, int32_t n_elts, const int32_t* elt_ids, const int64_t* rec_offsets,
+                   const int32_t* event_ids, const float* mean, const float* sigma_i, const float* sigma_c,
+                   const float* exposure, const ara_elt_terms* terms) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (!sigma_c && n_elts >= 1 && rec_offsets) {
+    int64_t R = 0;
+    ARA_CUDA(c, copy_params_to_host(&R, rec_offsets + n_elts, sizeof(int64_t)));
+    if (R > 0) return fail(c, ARA_EINVAL, "ara_load_xelts: sigma_c is NULL");
+  }
+  return load_elts_impl(c, "ara_load_xelts", n_elts, elt_ids, rec_offsets, event_ids, mean, sigma_i, sigma_c,
+                        exposure, terms);
 }
 
 // ---------------------------------------------------------------- layer passes
@@ -477,6 +513,7 @@ static int plan_pass(ara_ctx* c, const std::vector<int32_t>& ids, int64_t t0, in
   pl->refs = ara::LayerEltRefs{};
   pl->refs.n_elts = static_cast<int32_t>(ids.size());
   pl->refs.rec_begin[0] = 0;
+  bool any_corr = false;
   for (size_t i = 0; i < ids.size(); ++i) {
     auto it = c->pool.find(ids[i]);
     if (it == c->pool.end()) return fail(c, ARA_ENOTLOADED, "%s: ELT %d is not loaded", who, ids[i]);
@@ -486,6 +523,8 @@ static int plan_pass(ara_ctx* c, const std::vector<int32_t>& ids, int64_t t0, in
                   el.max_event, c->catalogue);
     pl->refs.events[i] = static_cast<const int32_t*>(el.events.ptr);
     pl->refs.recs[i] = static_cast<const ara::Pair*>(el.recs.ptr);
+    pl->refs.wts[i] = el.correlated ? static_cast<const float2*>(el.wts.ptr) : nullptr;
+    any_corr = any_corr || el.correlated;
     pl->refs.rec_begin[i + 1] = pl->refs.rec_begin[i] + el.n;
   }
   const int64_t n_recs = pl->refs.rec_begin[ids.size()];
@@ -501,6 +540,7 @@ static int plan_pass(ara_ctx* c, const std::vector<int32_t>& ids, int64_t t0, in
       (rc = reserve(c, c->slot_cnt, sizeof(uint32_t) * (n_recs + 2))) ||
       (rc = reserve(c, c->pairs, sizeof(ara::Pair) * (n_recs + 1))) ||
       (rc = reserve(c, c->pairs_hot, sizeof(ara::PairHot) * (n_recs + 1))) ||
+      (any_corr && (rc = reserve(c, c->pairs_w, sizeof(float2) * (n_recs + 1)))) ||
       (rc = reserve(c, c->scan_tmp, sizeof(uint32_t) * (tmp_words + 8))))
     return rc;
   ara::LayerIndex& ix = pl->ix;
@@ -512,6 +552,7 @@ static int plan_pass(ara_ctx* c, const std::vector<int32_t>& ids, int64_t t0, in
   ix.slot_cnt = static_cast<uint32_t*>(c->slot_cnt.ptr);
   ix.pairs = static_cast<ara::Pair*>(c->pairs.ptr);
   ix.hot = static_cast<ara::PairHot*>(c->pairs_hot.ptr);
+  ix.pw = any_corr ? static_cast<float2*>(c->pairs_w.ptr) : nullptr;
   ix.scan_tmp = static_cast<uint32_t*>(c->scan_tmp.ptr);
   ix.n_words = n_words;
   ix.n_recs = n_recs;
@@ -633,6 +674,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   p.tile_cnt = pl.g.tile_cnt;
   p.pairs = pl.ix.pairs;
   p.hot = pl.ix.hot;
+  p.pw = pl.ix.pw;
   p.n_elts = L->n_elts;
   p.occ_r = static_cast<float>(L->occ_retention);
   p.occ_l = static_cast<float>(L->occ_limit);
@@ -753,6 +795,7 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
   p.tile_cnt = pl.g.tile_cnt;
   p.pairs = pl.ix.pairs;
   p.hot = pl.ix.hot;
+  p.pw = pl.ix.pw;
   p.n_elts = static_cast<int32_t>(uni.size());
   p.n_layers = n_layers;
   fill_philox_keys(seed, p.rk);
@@ -1137,11 +1180,12 @@ void ara_destroy(ara_ctx* c) {
     release(c, kv.second.recs);
     release(c, kv.second.tab);
     release(c, kv.second.tabf);
+    release(c, kv.second.wts);
   }
   DevBuf* bufs[] = {&c->elt_stage,  &c->elt_recs_stage, &c->elt_tab_stage, &c->elt_tabf_stage, &c->elt_work,
                     &c->elt_flags,  &c->ev_buf,         &c->tile_cnt,      &c->def_acc,        &c->yet_off,
                     &c->yet_ids,    &c->bits,           &c->word_cnt,      &c->word_pairs,     &c->rankdir,
-                    &c->mask,       &c->slot_cnt,       &c->pairs,         &c->pairs_hot,     &c->scan_tmp,       &c->flags,
+                    &c->mask,       &c->slot_cnt,       &c->pairs,         &c->pairs_hot,     &c->pairs_w,          &c->scan_tmp,       &c->flags,
                     &c->counters,   &c->ylt_tmp,        &c->diag_tmp,      &c->sel,            &c->in_tmp,
                     &c->out_tmp,    &c->serve_ylt,      &c->serve_out};
   for (DevBuf* b : bufs) release(c, *b);

@@ -54,17 +54,39 @@ __device__ __forceinline__ unsigned long long fixed_of(float O, int e) {
   return (m + (1ull << (-s - 1))) >> (-s);
 }
 
-// Loss after ELT terms of one pair; the Halley iteration when the record's
-// table is not exact (or when the layers ask for it).
-__device__ __noinline__ float pair_loss_slow(const BatchParams& p, const Pair& pr, int64_t trial, uint32_t k,
-                                             unsigned long long* nc) {
+// The table argument t = Phi^-1(z) of pair `pi` (a record of kind Beta or
+// BetaC) in occurrence (trial, k); false when t lies beyond the tables' range
+// (only a combined normal can).
+__device__ __forceinline__ bool batch_pair_normal(const BatchParams& p, uint32_t kind, uint32_t elt, uint32_t pi,
+                                                  int64_t trial, uint32_t k, float* t) {
+  if (kind == kKindBetaC) {
+    *t = correlated_normal(p.rk, trial, k, elt, p.pw[pi]);
+    return fabsf(*t) <= kTabT1f;
+  }
+  *t = normcdfinvf(philox_uniform_rk(p.rk, trial, k, elt));
+  return true;
+}
+
+// Loss after ELT terms of pair `pi` by the Halley iteration: when the record's
+// table is not exact, when a combined normal lies beyond the tables' range, or
+// when the layers ask for it.
+__device__ __noinline__ float pair_loss_slow(const BatchParams& p, const Pair& pr, uint32_t pi, int64_t trial,
+                                             uint32_t k, unsigned long long* nc) {
   const uint32_t pos = pair_pos(pr.meta);
-  const float z = philox_uniform_rk(p.rk, trial, k, static_cast<uint32_t>(p.elt_id[pos]));
+  const uint32_t elt = static_cast<uint32_t>(p.elt_id[pos]);
   const bool fine = pair_fine(pr.meta);
   const float4* tab = fine ? p.tabf[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabFineStride
                            : p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes;
   BetaSolveStats st;
-  const float x = pair_quantile_newton(pr, z, p.newton_only ? -1.0f : tab_quantile(tab, z, fine), &st);
+  float x;
+  if (pair_kind(pr.meta) == kKindBetaC) {
+    const float t = correlated_normal(p.rk, trial, k, elt, p.pw[pi]);
+    x = pair_quantile_newton_zc(pr, normcdff(t), normcdff(-t), p.newton_only ? -1.0f : tab_quantile_t(tab, t, fine),
+                                &st);
+  } else {
+    const float z = philox_uniform_rk(p.rk, trial, k, elt);
+    x = pair_quantile_newton(pr, z, p.newton_only ? -1.0f : tab_quantile(tab, z, fine), &st);
+  }
   if (!st.converged) ++*nc;
   return p.t_share[pos] * clamp_terms_f(pr.max_l * x, p.t_ret[pos], p.t_lim[pos]);
 }
@@ -77,12 +99,15 @@ __device__ __forceinline__ float pair_loss_batch(const BatchParams& p, const Bat
   float loss = h.mu;
   if (kind == kKindZero) {
     loss = 0.0f;
-  } else if (!p.primary_only && kind == kKindBeta) {
-    if (p.newton_only || !pair_tab_exact(h.meta)) return pair_loss_slow(p, p.pairs[pair_index], trial, k, nc);
-    const float z = philox_uniform_rk(p.rk, trial, k, bs.elt_id[pos]);
+  } else if (!p.primary_only && kind_is_beta(kind)) {
+    if (p.newton_only || !pair_tab_exact(h.meta))
+      return pair_loss_slow(p, p.pairs[pair_index], pair_index, trial, k, nc);
+    float t;
+    if (!batch_pair_normal(p, kind, bs.elt_id[pos], pair_index, trial, k, &t))
+      return pair_loss_slow(p, p.pairs[pair_index], pair_index, trial, k, nc);
     const bool fine = pair_fine(h.meta);
     const float4* tb = (fine ? bs.tabf[pos] : bs.tab[pos]) + h.node;
-    loss = h.max_l * tab_quantile(tb, z, fine);
+    loss = h.max_l * tab_quantile_t(tb, t, fine);
   }
   return bs.share[pos] * clamp_terms_f(loss, bs.ret[pos], bs.lim[pos]);
 }
@@ -303,15 +328,16 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
           val[j] = h[j].mu;
           if (kind == kKindZero) {
             val[j] = 0.0f;
-          } else if (!p.primary_only && kind == kKindBeta) {
-            if (p.newton_only || !pair_tab_exact(h[j].meta)) {
+          } else if (!p.primary_only && kind_is_beta(kind)) {
+            float t = 0.0f;
+            if (p.newton_only || !pair_tab_exact(h[j].meta) ||
+                !batch_pair_normal(p, kind, bs.elt_id[pos], r[j].y, trial, r[j].x & kRecKMask, &t)) {
               mode[j] = 3;
             } else {
               mode[j] = 2;
-              const float z = philox_uniform_rk(p.rk, trial, r[j].x & kRecKMask, bs.elt_id[pos]);
               const bool fine = pair_fine(h[j].meta);
               const int nseg = fine ? kTabFineNodes - 1 : kTabNodes - 1;
-              float u = (normcdfinvf(z) + kTabT1f) * (fine ? kTabInvH * kTabRefine : kTabInvH);
+              float u = (t + kTabT1f) * (fine ? kTabInvH * kTabRefine : kTabInvH);
               u = fminf(fmaxf(u, 0.0f), static_cast<float>(nseg));
               int i = static_cast<int>(u);
               if (i > nseg - 1) i = nseg - 1;
@@ -336,7 +362,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
         const uint32_t pos = pair_pos(h[j].meta);
         float L;
         if (mode[j] == 3) {
-          L = pair_loss_slow(p, p.pairs[r[j].y], trial, r[j].x & kRecKMask, &nc);
+          L = pair_loss_slow(p, p.pairs[r[j].y], r[j].y, trial, r[j].x & kRecKMask, &nc);
         } else {
           float loss = val[j];
           if (mode[j] == 2)

@@ -39,9 +39,10 @@ namespace ara {
 // ------------------------------------------------------------------ records
 // One (event, ELT) pair of a layer, 32 bytes (one L2 sector).
 enum : uint32_t {
-  kKindBeta = 0u,  // Beta secondary uncertainty
-  kKindMean = 1u,  // sigma == 0: the loss is the mean
-  kKindZero = 2u,  // mean == 0: no loss
+  kKindBeta = 0u,   // Beta secondary uncertainty, uniform z_(Prog,E)
+  kKindBetaC = 1u,  // Beta secondary uncertainty with a correlated sigma_C > 0 (Section 3.2 uniform)
+  kKindMean = 2u,   // sigma == 0: the loss is the mean
+  kKindZero = 3u,   // mean == 0: no loss
 };
 
 struct __align__(16) Pair {
@@ -74,6 +75,8 @@ __host__ __device__ inline uint32_t pair_kind(uint32_t meta) { return (meta >> k
 __host__ __device__ inline bool pair_fine(uint32_t meta) { return (meta >> kMetaFineBit) & 1u; }
 __host__ __device__ inline bool pair_tab_exact(uint32_t meta) { return (meta >> kMetaExactBit) & 1u; }
 __host__ __device__ inline uint32_t pair_rec(uint32_t meta) { return meta >> kMetaRecShift; }
+// Beta and BetaC are the two kinds below kKindMean.
+__host__ __device__ inline bool kind_is_beta(uint32_t kind) { return kind < kKindMean; }
 
 // ------------------------------------------------------------------ tables
 constexpr int kTabNodes = 32;
@@ -123,6 +126,24 @@ __device__ __forceinline__ float philox_uniform_rk(const uint32_t (&rk)[20], int
   const uint64_t t = static_cast<uint64_t>(trial);
   const uint32_t w = philox4x32_10_w0(make_uint4(static_cast<uint32_t>(t), k, elt, static_cast<uint32_t>(t >> 32)), rk);
   return (static_cast<float>(w >> 9) + 0.5f) * 1.1920928955078125e-07f;  // 2^-23
+}
+
+// The event-occurrence uniform z_(E) (Section 3.1 (ii)): one per (trial,
+// event index), shared by every ELT; the same stream with the ELT word
+// 0xFFFFFFFF, which no pool id takes.
+__device__ __forceinline__ float philox_uniform_event_rk(const uint32_t (&rk)[20], int64_t trial, uint32_t k) {
+  return philox_uniform_rk(rk, trial, k, 0xFFFFFFFFu);
+}
+
+// Section 3.2 for a record with a correlated sigma: the normal variable
+// v = (sigma_I Phi^-1(z_(Prog,E)) + sigma_C Phi^-1(z_(E))) / sqrt(sigma_I^2 +
+// sigma_C^2), with w = (sigma_I, sigma_C) / sqrt(sigma_I^2 + sigma_C^2).  Its
+// uniform is z = Phi(v); a record's table is a function of t = Phi^-1(z) = v.
+__device__ __forceinline__ float correlated_normal(const uint32_t (&rk)[20], int64_t trial, uint32_t k, uint32_t elt,
+                                                   float2 w) {
+  const float zp = philox_uniform_rk(rk, trial, k, elt);
+  const float ze = philox_uniform_event_rk(rk, trial, k);
+  return w.x * normcdfinvf(zp) + w.y * normcdfinvf(ze);
 }
 
 // Uniform of (trial, event index k, ELT pool id): word 0 of the block with
@@ -212,10 +233,10 @@ __device__ __forceinline__ float tab_increment(float s, float dw, float d0, floa
   return fmaf(dw, g0, fmaf(d0, h1, fmaf(d1, g1, fmaf(e0, h2, e1 * g2))));
 }
 
-// x = InvCDF_beta(z) from a record's table (nodes are float4 {x_i, w_{i+1} - w_i,
-// h w'_i, h^2 w''_i}); `fine` selects the 8x refined grid.
-__device__ __forceinline__ float tab_quantile(const float4* __restrict__ tab, float z, bool fine) {
-  const float t = normcdfinvf(z);
+// x = InvCDF_beta(Phi(t)) from a record's table (nodes are float4 {x_i,
+// w_{i+1} - w_i, h w'_i, h^2 w''_i} on a grid in t); `fine` selects the 8x
+// refined grid.  t outside the grid's range [-T1, T1] is clamped to it.
+__device__ __forceinline__ float tab_quantile_t(const float4* __restrict__ tab, float t, bool fine) {
   const int nseg = fine ? kTabFineNodes - 1 : kTabNodes - 1;
   float u = (t + kTabT1f) * (fine ? kTabInvH * kTabRefine : kTabInvH);
   u = fminf(fmaxf(u, 0.0f), static_cast<float>(nseg));
@@ -226,6 +247,11 @@ __device__ __forceinline__ float tab_quantile(const float4* __restrict__ tab, fl
   if (!(n0.x > 0.0f)) return 0.0f;  // below the FP32 range
   const float2 n1 = __ldg(reinterpret_cast<const float2*>(tab + i + 1) + 1);
   return n0.x * expf(tab_increment(s, n0.y, n0.z, n0.w, n1.x, n1.y));
+}
+
+// x = InvCDF_beta(z) from a record's table.
+__device__ __forceinline__ float tab_quantile(const float4* __restrict__ tab, float z, bool fine) {
+  return tab_quantile_t(tab, normcdfinvf(z), fine);
 }
 
 struct BetaSolveStats {
@@ -318,6 +344,20 @@ __device__ __forceinline__ float beta_solve_oriented(float A, float B, float x0,
   return r;
 }
 
+// InvCDF_beta(z; a, b) from z and its complement zc = 1 - z, each computed
+// directly (so that neither loses the precision of a value near 0).
+__device__ __forceinline__ float pair_quantile_newton_zc(const Pair& p, float z, float zc, float x_start,
+                                                         BetaSolveStats* st) {
+  const bool m0x = signbit(p.m0);
+  const float m0 = fabsf(p.m0);
+  const float x0 = m0x ? m0 : 1.0f - m0;
+  const float y0 = m0x ? 1.0f - m0 : m0;
+  const float lnz = logf(z), ln1mz = logf(zc);
+  if (z <= p.p_half) return beta_solve_oriented(p.a, p.b, x0, y0, p.c, lnz, ln1mz, x_start, st);
+  const float y_start = (x_start > 0.0f && x_start < 1.0f) ? 1.0f - x_start : -1.0f;
+  return 1.0f - beta_solve_oriented(p.b, p.a, y0, x0, p.c, ln1mz, lnz, y_start, st);
+}
+
 // InvCDF_beta(z; a, b) of a Beta record by the FP32 Halley iteration; x_start
 // in (0, 1) seeds it (otherwise the analytic start point is used).
 __device__ __forceinline__ float pair_quantile_newton(const Pair& p, float z, float x_start, BetaSolveStats* st) {
@@ -344,7 +384,7 @@ __device__ __forceinline__ float pair_loss(const Pair& p, float z, bool primary_
   st->cf_terms = 0;
   st->converged = true;
   if (kind == kKindZero) return 0.0f;
-  if (primary_only || kind == kKindMean) return p.mu;
+  if (primary_only || !kind_is_beta(kind)) return p.mu;
   if (tab != nullptr && !newton_only) {
     const float x = tab_quantile(tab, z, pair_fine(p.meta));
     if (pair_tab_exact(p.meta)) return p.max_l * x;

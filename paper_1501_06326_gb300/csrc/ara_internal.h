@@ -18,6 +18,7 @@ enum : uint32_t {
   kBadValue = 8u,      // negative / non-finite mean, sigma or exposure
   kBadExposure = 16u,  // exposure <= mean for a record with mean > 0 and sigma > 0
   kLongTrial = 32u,    // a trial with 2^22 or more events
+  kHasCorrelated = 64u,  // not an error: an ELT holds a record with sigma_C > 0
 };
 
 cudaError_t launch_check_offsets(const int64_t* off, int64_t n_trials, int64_t n_events, uint32_t* flags,
@@ -31,7 +32,8 @@ cudaError_t launch_check_ids(const int32_t* ids, int64_t n, int32_t catalogue, u
 // bits) into *max_loss (both atomicMax; max_loss may be null).
 cudaError_t launch_prepare_records(const int32_t* events, const float* mean, const float* sigma,
                                    const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
-                                   int32_t* max_event, uint32_t* max_loss, cudaStream_t s);
+                                   int32_t* max_event, uint32_t* max_loss, cudaStream_t s,
+                                   const float* sigma_c = nullptr, float2* weights = nullptr);
 
 // Quantile tables of prepared records, built in FP64: kTabNodes float4 per
 // record in `tab`; then, for the first fine_table_cap(n) records (in record
@@ -83,6 +85,7 @@ struct LayerEltRefs {
   int32_t n_elts;
   const int32_t* events[kMaxIndexElts];  // sorted event ids of the ELT at position p
   const Pair* recs[kMaxIndexElts];       // prepared records (meta carries the record index)
+  const float2* wts[kMaxIndexElts];      // per record (w_I, w_C) of a correlated sigma
   int64_t rec_begin[kMaxIndexElts + 1];  // prefix sums of record counts over positions
 };
 
@@ -96,6 +99,7 @@ struct LayerIndex {
   uint32_t* slot_cnt;    // [n_recs + 1] scratch -> slot_start
   Pair* pairs;           // [n_recs]
   PairHot* hot;          // [n_recs] the table-path part of each pair
+  float2* pw;            // [n_recs] (w_I, w_C) of each pair's record (pairs of kind kKindBetaC)
   uint32_t* scan_tmp;
   int64_t n_words;
   int64_t n_recs;
@@ -110,7 +114,6 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
 //             event buffer (the region of a tile starts at its first event);
 //   k_losses  reads the records of a tile and computes the pair losses, event
 //             losses, trial sums and year losses.
-// Event record: x = (trial in tile << 27) | ((pairs - 1) << 22) | k, y = first pair.
 constexpr int kGatherThreads = 1024;  // 32 warps per CTA, one CTA per SM
 constexpr int kLossThreads = 256;
 constexpr int kLossBlocksPerSm = 3;  // 24 warps per SM at up to 85 registers: no spills in the loss loop
@@ -145,6 +148,7 @@ struct LossParams {
   const uint32_t* tile_cnt;
   const Pair* pairs;
   const PairHot* hot;
+  const float2* pw;
   int32_t n_elts;
   int32_t elt_id[32];
   const float4* tab[32];   // coarse quantile tables of the layer's ELTs (by position)
@@ -177,6 +181,7 @@ struct BatchParams {
   const uint32_t* tile_cnt;
   const Pair* pairs;
   const PairHot* hot;
+  const float2* pw;
   int32_t n_elts;  // union positions
   int32_t n_layers;
   int32_t elt_id[kMaxIndexElts];

@@ -138,10 +138,14 @@ __device__ double beta_cf_f64(double a, double b, double x) {
 
 // Section 3.3 per record: sigma_b = sigma / max_l, mu_b = mu / max_l,
 // sigma_bmax = sqrt(mu_b (1 - mu_b)), sigma_b clipped to (1 - 1e-6) sigma_bmax,
-// alpha = mu_b ((sigma_bmax / sigma_b)^2 - 1), beta = (1 - mu_b)(...).
+// alpha = mu_b ((sigma_bmax / sigma_b)^2 - 1), beta = (1 - mu_b)(...).  With a
+// correlated part sigma_C (Section 3.1), sigma = sigma_I + sigma_C
+// (Section 3.2 step i) and a record with sigma_C > 0 is of kind kKindBetaC,
+// with weights (sigma_I, sigma_C) / sqrt(sigma_I^2 + sigma_C^2) for the
+// combination of its two normal variables.
 __global__ void k_prepare_records(const int32_t* events, const float* mean, const float* sigma,
                                   const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
-                                  int32_t* max_event, uint32_t* max_loss) {
+                                  int32_t* max_event, uint32_t* max_loss, const float* sigma_c, float2* weights) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   uint32_t f = 0;
   int32_t emax = -1;
@@ -151,14 +155,17 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
     emax = max(emax, e);
     if (e < 0) f |= kBadEventId;
     if (i > 0 && events[i - 1] >= e) f |= kBadOrder;
-    const double mu = mean[i], sg = sigma[i], ex = exposure[i];
+    const double mu = mean[i], si = sigma[i], ex = exposure[i];
+    const double sc = sigma_c ? static_cast<double>(sigma_c[i]) : 0.0;
+    const double sg = si + sc;
     Pair p;
     p.a = p.b = p.m0 = p.c = p.p_half = 0.0f;
     p.max_l = static_cast<float>(ex);
     p.mu = static_cast<float>(mu);
     uint32_t kind = kKindBeta;
     double sa = 0.0, sb_ = 0.0;
-    if (!(mu >= 0.0) || !(sg >= 0.0) || !isfinite(mu) || !isfinite(sg) || !isfinite(ex)) {
+    float2 w = make_float2(1.0f, 0.0f);
+    if (!(mu >= 0.0) || !(si >= 0.0) || !(sc >= 0.0) || !isfinite(mu) || !isfinite(sg) || !isfinite(ex)) {
       f |= kBadValue;
       kind = kKindZero;
     } else if (mu == 0.0) {
@@ -192,11 +199,18 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
       p.m0 = (x0 <= y0) ? -static_cast<float>(x0) : static_cast<float>(y0);
       p.c = static_cast<float>(c);
       p.p_half = static_cast<float>(ph);
+      if (sc > 0.0) {
+        kind = kKindBetaC;
+        f |= kHasCorrelated;
+        const double nrm = sqrt(si * si + sc * sc);
+        w = make_float2(static_cast<float>(si / nrm), static_cast<float>(sc / nrm));
+      }
     }
     p.meta = (kind << kMetaKindShift) | (static_cast<uint32_t>(i) << kMetaRecShift);
     if (kind != kKindZero) lmax = fmaxf(lmax, fmaxf(p.max_l, p.mu));
     out[i] = p;
     if (shapes) shapes[i] = make_double2(sa, sb_);
+    if (weights) weights[i] = w;
   }
   if (f) atomicOr(flags, f);
   // block max of event ids, then one atomic per warp
@@ -211,11 +225,12 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
 
 cudaError_t launch_prepare_records(const int32_t* events, const float* mean, const float* sigma,
                                    const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
-                                   int32_t* max_event, uint32_t* max_loss, cudaStream_t s) {
+                                   int32_t* max_event, uint32_t* max_loss, cudaStream_t s, const float* sigma_c,
+                                   float2* weights) {
   if (n == 0) return cudaSuccess;
   const int64_t blocks = (n + 127) / 128;
   k_prepare_records<<<static_cast<int>(blocks < 65535 ? blocks : 65535), 128, 0, s>>>(
-      events, mean, sigma, exposure, n, out, shapes, flags, max_event, max_loss);
+      events, mean, sigma, exposure, n, out, shapes, flags, max_event, max_loss, sigma_c, weights);
   return cudaGetLastError();
 }
 
@@ -371,7 +386,7 @@ __global__ void __launch_bounds__(256, 4) k_build_tables(Pair* recs, const doubl
   if (rec >= n) return;
   const Pair pr = recs[rec];
   float4* out = tab + rec * kTabNodes;
-  if (pair_kind(pr.meta) != kKindBeta) {
+  if (!kind_is_beta(pair_kind(pr.meta))) {
     out[lane] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (lane == 0) need[rec] = 0u;
     return;
@@ -696,7 +711,7 @@ __global__ void k_slot_counts(const unsigned long long* mask, int64_t n, uint32_
 
 __global__ void k_fill_pairs(LayerEltRefs r, const uint32_t* bits, const uint32_t* slot_base,
                              const unsigned long long* mask,
-                             const uint32_t* slot_start, Pair* pairs, PairHot* hot) {
+                             const uint32_t* slot_start, Pair* pairs, PairHot* hot, float2* pw) {
   const int64_t n = r.rec_begin[r.n_elts];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
@@ -715,6 +730,7 @@ __global__ void k_fill_pairs(LayerEltRefs r, const uint32_t* bits, const uint32_
     hq.meta = q.meta;
     hq.node = pair_rec(q.meta) * (pair_fine(q.meta) ? kTabFineStride : kTabNodes);
     hot[at] = hq;
+    if (pw && r.wts[p]) pw[at] = r.wts[p][j];
   }
 }
 
@@ -758,7 +774,8 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if ((err = scan_exclusive_u32(ix.slot_cnt, ix.slot_cnt, n_recs, ix.scan_tmp, s, &launched)) != cudaSuccess)
       return err;
-    k_fill_pairs<<<grid_for(n_recs, 256), 256, 0, s>>>(refs, ix.bits, ix.word_cnt, ix.mask, ix.slot_cnt, ix.pairs, ix.hot);
+    k_fill_pairs<<<grid_for(n_recs, 256), 256, 0, s>>>(refs, ix.bits, ix.word_cnt, ix.mask, ix.slot_cnt, ix.pairs, ix.hot,
+                                                        ix.pw);
     launched += 3;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   } else {

@@ -302,37 +302,61 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float hi2, float lo
   lo = e - (hi - s);
 }
 
-// Loss after ELT terms of one pair, for the table path; returns false when the
-// pair needs the Halley iteration.
-__device__ __forceinline__ bool pair_fast(const LossParams& p, const Pair& pr, int64_t trial, uint32_t k, float* out) {
+// The table argument t = Phi^-1(z) of pair `pi` of an ELT record of kind
+// `kind` (Beta or BetaC) in occurrence (trial, k); false when t lies beyond
+// the tables' range (only a combined normal can).
+__device__ __forceinline__ bool pair_normal(const LossParams& p, uint32_t kind, uint32_t elt, uint32_t pi,
+                                            int64_t trial, uint32_t k, float* t) {
+  if (kind == kKindBetaC) {
+    *t = correlated_normal(p.rk, trial, k, elt, p.pw[pi]);
+    return fabsf(*t) <= kTabT1f;
+  }
+  *t = normcdfinvf(philox_uniform_rk(p.rk, trial, k, elt));
+  return true;
+}
+
+// Loss after ELT terms of pair `pi`, for the table path; returns false when
+// the pair needs the Halley iteration.
+__device__ __forceinline__ bool pair_fast(const LossParams& p, const Pair& pr, uint32_t pi, int64_t trial, uint32_t k,
+                                          float* out) {
   const uint32_t kind = pair_kind(pr.meta);
   const uint32_t pos = pair_pos(pr.meta);
   float loss = pr.mu;
   if (kind == kKindZero) {
     loss = 0.0f;
-  } else if (!p.primary_only && kind == kKindBeta) {
+  } else if (!p.primary_only && kind_is_beta(kind)) {
     if (p.newton_only || !pair_tab_exact(pr.meta)) return false;
-    const float z = philox_uniform_rk(p.rk, trial, k, static_cast<uint32_t>(p.elt_id[pos]));
+    float t;
+    if (!pair_normal(p, kind, static_cast<uint32_t>(p.elt_id[pos]), pi, trial, k, &t)) return false;
     const bool fine = pair_fine(pr.meta);
     const float4* tb = fine ? p.tabf[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabFineStride
                             : p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes;
-    loss = pr.max_l * tab_quantile(tb, z, fine);
+    loss = pr.max_l * tab_quantile_t(tb, t, fine);
   }
   *out = p.t_share[pos] * clamp_terms_f(loss, p.t_ret[pos], p.t_lim[pos]);
   return true;
 }
 
-__device__ __noinline__ float pair_slow(const LossParams& p, const Pair& pr, int64_t trial, uint32_t k,
+__device__ __noinline__ float pair_slow(const LossParams& p, const Pair& pr, uint32_t pi, int64_t trial, uint32_t k,
                                         unsigned long long* nc) {
   const uint32_t pos = pair_pos(pr.meta);
   float v;
-  if (pair_fast(p, pr, trial, k, &v)) return v;
-  const float z = philox_uniform_rk(p.rk, trial, k, static_cast<uint32_t>(p.elt_id[pos]));
+  if (pair_fast(p, pr, pi, trial, k, &v)) return v;
+  const uint32_t elt = static_cast<uint32_t>(p.elt_id[pos]);
   const bool fine = pair_fine(pr.meta);
   const float4* tab = fine ? p.tabf[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabFineStride
                            : p.tab[pos] + static_cast<size_t>(pair_rec(pr.meta)) * kTabNodes;
   BetaSolveStats st;
-  const float x = pair_quantile_newton(pr, z, p.newton_only ? -1.0f : tab_quantile(tab, z, fine), &st);
+  float x;
+  if (pair_kind(pr.meta) == kKindBetaC) {
+    // z = Phi(v) and 1 - z = Phi(-v), each directly
+    const float t = correlated_normal(p.rk, trial, k, elt, p.pw[pi]);
+    x = pair_quantile_newton_zc(pr, normcdff(t), normcdff(-t), p.newton_only ? -1.0f : tab_quantile_t(tab, t, fine),
+                                &st);
+  } else {
+    const float z = philox_uniform_rk(p.rk, trial, k, elt);
+    x = pair_quantile_newton(pr, z, p.newton_only ? -1.0f : tab_quantile(tab, z, fine), &st);
+  }
   if (!st.converged) ++*nc;
   return p.t_share[pos] * clamp_terms_f(pr.max_l * x, p.t_ret[pos], p.t_lim[pos]);
 }
@@ -354,7 +378,7 @@ __device__ __noinline__ void resolve_deferred(const LossParams& p, LossWarp& ws,
     const uint32_t cnt = ((key >> kRecCntShift) & kRecCntMask) + 1u;
     const int64_t t = p.t_begin + ws.d_o[lane];
     float G = 0.0f;
-    for (uint32_t j = 0; j < cnt; ++j) G += pair_slow(p, p.pairs[ws.d_ps[lane] + j], t, k, nc);
+    for (uint32_t j = 0; j < cnt; ++j) G += pair_slow(p, p.pairs[ws.d_ps[lane] + j], ws.d_ps[lane] + j, t, k, nc);
     O = clamp_terms_f(G, p.occ_r, p.occ_l);
   }
   const uint32_t nc_w = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(nc_l));
@@ -434,19 +458,20 @@ struct EltShared {
 
 // Loss after ELT terms of one pair from its hot record, for the table path;
 // returns false when the pair needs the Halley iteration.
-__device__ __forceinline__ bool pair_fast_hot(const LossParams& p, const EltShared& es, const PairHot& h,
+__device__ __forceinline__ bool pair_fast_hot(const LossParams& p, const EltShared& es, const PairHot& h, uint32_t pi,
                                               int64_t trial, uint32_t k, float* out) {
   const uint32_t kind = pair_kind(h.meta);
   const uint32_t pos = pair_pos(h.meta);
   float loss = h.mu;
   if (kind == kKindZero) {
     loss = 0.0f;
-  } else if (!p.primary_only && kind == kKindBeta) {
+  } else if (!p.primary_only && kind_is_beta(kind)) {
     if (p.newton_only || !pair_tab_exact(h.meta)) return false;
-    const float z = philox_uniform_rk(p.rk, trial, k, es.elt_id[pos]);
+    float t;
+    if (!pair_normal(p, kind, es.elt_id[pos], pi, trial, k, &t)) return false;
     const bool fine = pair_fine(h.meta);
     const float4* tb = (fine ? es.tabf[pos] : es.tab[pos]) + h.node;
-    loss = h.max_l * tab_quantile(tb, z, fine);
+    loss = h.max_l * tab_quantile_t(tb, t, fine);
   }
   *out = es.share[pos] * clamp_terms_f(loss, es.ret[pos], es.lim[pos]);
   return true;
@@ -482,8 +507,9 @@ __device__ __forceinline__ int2 process_multi(const LossParams& p, const EltShar
     float L = 0.0f;
     bool slow = false;
     if (q < np) {
-      const PairHot h = p.hot[ey + (q - epre)];
-      slow = !pair_fast_hot(p, es, h, ta + etl, ek, &L);
+      const uint32_t pi = ey + (q - epre);
+      const PairHot h = p.hot[pi];
+      slow = !pair_fast_hot(p, es, h, pi, ta + etl, ek, &L);
       if (diag) {
         const uint32_t elt = es.elt_id[pair_pos(h.meta)];
         atomicAdd(&ws.hits[etl], 1ull);
@@ -583,7 +609,7 @@ __global__ void __launch_bounds__(kLossThreads, kLossBlocksPerSm) k_losses(const
     // pipeline: r1 = records of the next round, r0/h0 = this round's record and hot pair
     uint2 r0 = (lane < n) ? __ldcs(recs + lane) : make_uint2(0u, 0u);
     uint2 r1 = (32 + lane < n) ? __ldcs(recs + 32 + lane) : make_uint2(0u, 0u);
-    PairHot h0{0.0f, 0.0f, kKindZero << 5, 0u};
+    PairHot h0{0.0f, 0.0f, kKindZero << kMetaKindShift, 0u};
     if (lane < n && ((r0.x >> kRecCntShift) & kRecCntMask) == 0u) h0 = p.hot[r0.y];
     for (uint32_t base = 0;;) {
 #pragma unroll 1
@@ -600,7 +626,7 @@ __global__ void __launch_bounds__(kLossThreads, kLossBlocksPerSm) k_losses(const
         bool slow = false;
         if (single) {
           float L;
-          slow = !pair_fast_hot(p, es, h, ta + tl, k, &L);
+          slow = !pair_fast_hot(p, es, h, r.y, ta + tl, k, &L);
           if (!slow) acc_add(ws, tl, clamp_terms_f(L, p.occ_r, p.occ_l));
           if (diag) {
             const uint32_t elt = es.elt_id[pair_pos(h.meta)];
