@@ -71,6 +71,11 @@ def _load():
                 P, P, i32, i32, P, P, P, P, P, P, P, P, u64, ctypes.c_int, i64, i64, P, i64
             ]
             lib.or_event_losses.restype = i64
+            lib.or_run_layer_events.argtypes = [
+                P, P, i32, i32, P, P, P, P, P, P, P, P, dbl, dbl, dbl, dbl, u64, ctypes.c_int, i64, i64,
+                P, P, P, P, P, i64, P,
+            ]
+            lib.or_run_layer_events.restype = i64
             lib.or_uniform_batch.argtypes = [u64, i64, P, P, P, P]
             lib.or_uniform_batch.restype = None
             lib.or_combined_normal_batch.argtypes = [u64, i64, P, P, P, dbl, dbl, P, P]
@@ -272,6 +277,33 @@ def event_losses(yet, pool, seed=0, primary_only=True, t_begin=0, t_end=None):
     if n < 0:
         raise ValueError(f"oracle event_losses failed with code {n}")
     return out[:n]
+
+
+def run_layer_events(yet, pool, layer_terms, seed=0, primary_only=False, t_begin=0, t_end=None):
+    """Per-event output of a layer over trials [t_begin, t_end): one row per event
+    occurrence held by at least one of the layer's ELTs, in (trial, k) order, as a
+    dict of arrays ``trial, k, event, occ`` (O_k after occurrence terms) and ``inc``
+    (A_k - A_{k-1}), plus ``max_occ`` per trial."""
+    lib = _load()
+    t_end = yet.n_trials if t_end is None else int(t_end)
+    offs = _c(yet.offsets, np.int64)
+    ids = _c(yet.event_ids, np.int32)
+    cap = int(offs[t_end] - offs[t_begin]) + 1
+    rows = {"trial": np.zeros(cap, np.int64), "k": np.zeros(cap, np.int32), "event": np.zeros(cap, np.int32),
+            "occ": np.zeros(cap, np.float64), "inc": np.zeros(cap, np.float64)}
+    max_occ = np.zeros(max(t_end - t_begin, 1), np.float64)
+    occ_r, occ_l, agg_r, agg_l = (float(v) for v in layer_terms)
+    arrs = _elt_arrays(pool)
+    n = lib.or_run_layer_events(
+        _p(offs), _p(ids), int(yet.catalogue_size), pool.n_elts, *[_p(a) if a is not None else None for a in arrs],
+        occ_r, occ_l, agg_r, agg_l, int(seed), int(bool(primary_only)), int(t_begin), int(t_end),
+        _p(rows["trial"]), _p(rows["k"]), _p(rows["event"]), _p(rows["occ"]), _p(rows["inc"]), cap, _p(max_occ),
+    )
+    if n < 0:
+        raise ValueError(f"oracle run_layer_events failed with code {n}")
+    out = {k: v[:n] for k, v in rows.items()}
+    out["max_occ"] = max_occ[: t_end - t_begin]
+    return out
 
 
 # ---------------------------------------------------------------- PML / TVaR

@@ -417,6 +417,70 @@ int or_run_layer(int64_t n_trials, const int64_t *offsets, const int32_t *ids, i
     return 0;
 }
 
+/* Per-event output of one layer: the Algorithm 1 loop over trials        */
+/* t_begin .. t_end-1 in order, emitting one row per event occurrence that  */
+/* at least one of the layer's ELTs holds a record for, in (trial, event    */
+/* index) order: the trial, the event index k, the event id, the event's     */
+/* occurrence loss O_k (after the occurrence terms) and the increment        */
+/* inc_k = A_k - A_{k-1} of the loss after aggregate terms (A before the     */
+/* first event is 0), so that a trial's increments add up to its year loss. */
+/* max_occ (optional) receives each trial's largest O_k, 0 without rows.    */
+/* Returns the number of rows, or -1 when cap is too small (-2: no memory). */
+int64_t or_run_layer_events(const int64_t *offsets, const int32_t *ids, int32_t catalogue,
+                            int32_t n_elts, const int32_t *elt_pool_ids, const int64_t *rec_offsets,
+                            const int32_t *rec_events, const float *rec_mean, const float *rec_sigma,
+                            const float *rec_sigma_c, const float *rec_exposure, const float *elt_terms,
+                            double occ_ret, double occ_lim, double agg_ret, double agg_lim,
+                            uint64_t seed, int primary_only, int64_t t_begin, int64_t t_end,
+                            int64_t *row_trial, int32_t *row_k, int32_t *row_event, double *row_occ,
+                            double *row_inc, int64_t cap, double *max_occ)
+{
+    int32_t *row_of;
+    int64_t j, e, t, n = 0;
+    row_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)catalogue * (size_t)(n_elts > 0 ? n_elts : 1));
+    if (!row_of) return -2;
+    for (j = 0; j < (int64_t)catalogue * n_elts; ++j) row_of[j] = -1;
+    for (j = 0; j < n_elts; ++j)
+        for (e = rec_offsets[j]; e < rec_offsets[j + 1]; ++e) row_of[j * (int64_t)catalogue + rec_events[e]] = (int32_t)e;
+    for (t = t_begin; t < t_end; ++t) {
+        double S = 0.0, A = 0.0, O_max = 0.0;
+        int64_t pos;
+        for (pos = offsets[t]; pos < offsets[t + 1]; ++pos) {
+            int32_t k = (int32_t)(pos - offsets[t]);
+            double l_T = 0.0, O, A_new;
+            int held = 0;
+            int32_t jj;
+            for (jj = 0; jj < n_elts; ++jj) {
+                int32_t r = row_of[(int64_t)jj * catalogue + ids[pos]];
+                double l_E;
+                if (r < 0) continue;
+                held = 1;
+                l_E = record_loss(rec_mean[r], rec_sigma[r], rec_sigma_c ? rec_sigma_c[r] : 0.0f, rec_exposure[r],
+                                  primary_only, seed, t, k, elt_pool_ids[jj]);
+                if (elt_terms)
+                    l_E = (double)elt_terms[3 * jj + 2] * clamp_terms(l_E, elt_terms[3 * jj + 0], elt_terms[3 * jj + 1]);
+                l_T += l_E;
+            }
+            if (!held) continue;
+            O = clamp_terms(l_T, occ_ret, occ_lim);
+            S += O;
+            A_new = clamp_terms(S, agg_ret, agg_lim);
+            if (n >= cap) { free(row_of); return -1; }
+            row_trial[n] = t;
+            row_k[n] = k;
+            row_event[n] = ids[pos];
+            row_occ[n] = O;
+            row_inc[n] = A_new - A;
+            ++n;
+            A = A_new;
+            if (O > O_max) O_max = O;
+        }
+        if (max_occ) max_occ[t - t_begin] = O_max;
+    }
+    free(row_of);
+    return n;
+}
+
 /* Per-occurrence combined event losses l_T (after ELT terms, before the
  * occurrence terms) of the listed trials, for the percentile calibration of
  * layer terms.  Writes the nonzero values into out (capacity cap) and
