@@ -350,7 +350,7 @@ def run_gpu(args):
 
     # ---- two-part secondary uncertainty (correlated sigma) on the same layer; the plain
     # layer pass is timed here too, on the same stream, for the comparison
-    correlated = None
+    correlated = events = None
     if ws == 1 and not args.no_correlated:
         eng.load_pool(pool)
 
@@ -367,8 +367,12 @@ def run_gpu(args):
             plain_layer()
         b.record(stream)
         torch.cuda.synchronize(dev)
+        ms_plain_layer = a.elapsed_time(b) / steps_c
         correlated = _correlated_leg(eng, synth, torch, dev, stream, spec, terms, n_trials, n_events, seed,
-                                     a.elapsed_time(b) / steps_c, args)
+                                     ms_plain_layer, args)
+        eng.load_pool(pool)
+        if not args.no_events:
+            events = _events_leg(eng, torch, dev, stream, pool, terms, n_trials, seed, ms_plain_layer, args)
 
     # ---- batched layers (several layers in one pass over the YET) against one pass per layer
     batched = None
@@ -404,6 +408,8 @@ def run_gpu(args):
             line["global_pml_tvar"] = {"pml": list(global_pml[0]), "tvar": list(global_pml[1])}
         if correlated is not None:
             line["correlated"] = correlated
+        if events is not None:
+            line["events"] = events
         if batched is not None:
             line["batched"] = batched
         if serving is not None:
@@ -494,6 +500,35 @@ def _correlated_leg(eng, synth, torch, dev, stream, spec, terms, n_trials, n_eve
             "newton_pairs": eng.stats()["n_newton"]}
 
 
+def _events_leg(eng, torch, dev, stream, pool, terms, n_trials, seed, ms_plain, args):
+    """The paper-1m layer with its per-event output (ara_run_layer_events): one row
+    per hit event (trial, k, event id, O_k, inc_k: 32 bytes) and each trial's largest
+    O_k, all in device memory; timed with CUDA events against the plain layer pass."""
+    ylt = torch.empty(n_trials, dtype=torch.float64, device=dev)
+    n_rows = eng.run_layer_events(pool.elt_ids, terms, seed, 0, n_trials, ylt)
+    rows = [torch.empty(n_rows, dtype=dt, device=dev)
+            for dt in (torch.int64, torch.int32, torch.int32, torch.float64, torch.float64)]
+    max_occ = torch.empty(n_trials, dtype=torch.float64, device=dev)
+
+    def step():
+        eng.run_layer_events(pool.elt_ids, terms, seed, 0, n_trials, ylt, *rows, max_occ)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    steps = max(2, min(args.steps, 10))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    return {"workload": f"{WORKLOAD} layer with per-event rows (YELT) and per-trial max occurrence loss (OEP input)",
+            "steps": steps, "rows": n_rows, "row_bytes": 32 * n_rows, "ms_layer_events": ms,
+            "ms_layer_plain": ms_plain, "rows_per_s": n_rows / (ms * 1e-3)}
+
+
 def _serving_leg(eng, synth, offsets, args):
     """The serving workload: requests with Poisson arrivals at several rates, served by
     ara_submit / ara_serve_step / ara_poll.  Time is virtual: each serve step advances
@@ -558,7 +593,9 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-layers comparison")
-    ap.add_argument("--no-correlated", action="store_true", help="skip the correlated-sigma layer")
+    ap.add_argument("--no-correlated", action="store_true",
+                    help="skip the correlated-sigma layer and the per-event output legs")
+    ap.add_argument("--no-events", action="store_true", help="skip the per-event output leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency sweep")
     ap.add_argument("--serve-requests", type=int, default=400, help="requests per rate of the serving sweep")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 800.0, 3200.0],

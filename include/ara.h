@@ -99,6 +99,23 @@ typedef struct {
     uint64_t *hit_hash; /* sum over hits of fmix64((k << 32) | elt_id), k = event index in the trial */
 } ara_diag;
 
+/* Per-event output of ara_run_layer_events() (the Year Event Loss Table).
+ * One row per event occurrence of the trial range that at least one of the
+ * layer's ELTs holds a record for, in (trial, event index) order.  Every
+ * pointer may be NULL (not written) and may be host or device memory; row
+ * arrays hold `capacity` entries and only the first min(capacity, n_rows)
+ * rows are written. */
+typedef struct {
+    int64_t capacity;     /* rows the arrays below hold */
+    int64_t *trial;       /* trial index */
+    int32_t *event_index; /* k: position of the event in the trial, from 0 */
+    int32_t *event_id;    /* the event's id in the catalogue */
+    double *occ_loss;     /* O_k: the event's loss after ELT and occurrence terms */
+    double *agg_inc;      /* inc_k = A_k - A_(k-1), A the loss after aggregate terms */
+    double *max_occ;      /* trial_end - trial_begin entries: each trial's largest O_k (0 without rows) */
+    int64_t n_rows;       /* out: rows of the trial range (may exceed capacity) */
+} ara_event_rows;
+
 /* Counters of the last ara_run_layer* call (read back with ara_get_stats). */
 typedef struct {
     int64_t n_events;        /* YET entries scanned */
@@ -199,6 +216,24 @@ ARA_API int ara_run_layer(ara_ctx *ctx, const ara_layer *layer, uint64_t seed, i
  * an order-free hash of the hit list), used to check event indexing. */
 ARA_API int ara_run_layer_diag(ara_ctx *ctx, const ara_layer *layer, uint64_t seed, int64_t trial_begin,
                        int64_t trial_end, double *ylt_out, const ara_diag *diag);
+
+/* ara_run_layer plus its per-event output (Algorithm 1, Section 2.2, read
+ * per event): for each held event occurrence, O_k is the combined loss of the
+ * layer's ELTs after the occurrence terms; S_k is the sum of O_1..O_k in
+ * event order (FP64), A_k = min(max(S_k - AggR, 0), AggL) the loss after the
+ * aggregate terms, and inc_k = A_k - A_(k-1) with A_0 = 0, so that a trial's
+ * increments add up to its year loss.  max_occ holds each trial's largest
+ * O_k, the input of occurrence exceedance: ara_pml_tvar over max_occ gives the
+ * OEP loss and its tail mean at the return periods (the year losses give the
+ * aggregate ones).  O_k is the FP32 value the year loss sums; ylt_out is
+ * written as by ara_run_layer.  rows->n_rows receives the row count.  Limit:
+ * the trial range holds fewer than 2^32 YET entries.  Extra device memory: 4
+ * bytes per YET entry of the range, and the rows when the arrays are host
+ * memory.
+ * Errors: those of ara_run_layer; ARA_EINVAL for a NULL rows or a negative
+ * capacity. */
+ARA_API int ara_run_layer_events(ara_ctx *ctx, const ara_layer *layer, uint64_t seed, int64_t trial_begin,
+                         int64_t trial_end, double *ylt_out, ara_event_rows *rows);
 
 /* Several layers over the same trials in one pass (a batch): the YET of the
  * trial range is read once for all the layers, and the loss after ELT terms

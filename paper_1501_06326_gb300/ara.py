@@ -41,6 +41,7 @@ EXPORTED = (
     "ara_run_layer_diag", "ara_pml_tvar", "ara_sort_ylt", "ara_debug_uniforms",
     "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
     "ara_pml_tvar_noalloc", "ara_run_layers", "ara_submit", "ara_serve_step", "ara_poll", "ara_load_xelts",
+    "ara_run_layer_events",
 )
 ARA_NOALLOC_MAX_RP = 64
 
@@ -69,6 +70,19 @@ class Layer(ctypes.Structure):
 
 class Diag(ctypes.Structure):
     _fields_ = [("hits", ctypes.c_void_p), ("hit_hash", ctypes.c_void_p)]
+
+
+class EventRows(ctypes.Structure):
+    _fields_ = [
+        ("capacity", ctypes.c_int64),
+        ("trial", ctypes.c_void_p),
+        ("event_index", ctypes.c_void_p),
+        ("event_id", ctypes.c_void_p),
+        ("occ_loss", ctypes.c_void_p),
+        ("agg_inc", ctypes.c_void_p),
+        ("max_occ", ctypes.c_void_p),
+        ("n_rows", ctypes.c_int64),
+    ]
 
 
 class Stats(ctypes.Structure):
@@ -126,6 +140,7 @@ def load_library(path: str = LIB_PATH):
     lib.ara_run_layer.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P]
     lib.ara_run_layer_diag.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P, ctypes.POINTER(Diag)]
     lib.ara_run_layers.argtypes = [P, i32, ctypes.POINTER(Layer), u64, i64, i64, P]
+    lib.ara_run_layer_events.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P, ctypes.POINTER(EventRows)]
     lib.ara_submit.argtypes = [P, ctypes.POINTER(Layer), u64, i64, P, i32, P]
     lib.ara_serve_step.argtypes = [P, P]
     lib.ara_poll.argtypes = [P, i64, P, P]
@@ -216,6 +231,11 @@ def ara_run_layer(h, layer: Layer, seed, trial_begin, trial_end, ylt_out):
 def ara_run_layer_diag(h, layer: Layer, seed, trial_begin, trial_end, ylt_out, diag: Diag):
     return load_library().ara_run_layer_diag(h, ctypes.byref(layer), int(seed), int(trial_begin),
                                              int(trial_end), _ptr(ylt_out, np.float64), ctypes.byref(diag))
+
+
+def ara_run_layer_events(h, layer: Layer, seed, trial_begin, trial_end, ylt_out, rows: EventRows):
+    return load_library().ara_run_layer_events(h, ctypes.byref(layer), int(seed), int(trial_begin),
+                                               int(trial_end), _ptr(ylt_out, np.float64), ctypes.byref(rows))
 
 
 def ara_run_layers(h, n_layers, layers, seed, trial_begin, trial_end, ylt_out):
@@ -360,6 +380,23 @@ class Ara:
         else:
             d = Diag(_ptr(hits_out, np.int64), _ptr(hash_out, np.uint64))
             self._check(ara_run_layer_diag(self._h, lay, seed, trial_begin, trial_end, ylt_out, d))
+
+    def run_layer_events(self, elt_ids, layer_terms, seed: int, trial_begin: int, trial_end: int, ylt_out,
+                         trial=None, event_index=None, event_id=None, occ_loss=None, agg_inc=None, max_occ=None,
+                         capacity: Optional[int] = None, primary_only: bool = False,
+                         newton_only: bool = False) -> int:
+        """ara_run_layer plus the per-event rows (any array may be None); returns
+        the number of rows of the trial range (rows beyond ``capacity`` -- by
+        default the length of the given row arrays -- are not written)."""
+        lay = self.make_layer(elt_ids, layer_terms, primary_only, newton_only)
+        arrs = [(trial, np.int64), (event_index, np.int32), (event_id, np.int32), (occ_loss, np.float64),
+                (agg_inc, np.float64)]
+        if capacity is None:
+            lens = [len(a) for a, _ in arrs if a is not None]
+            capacity = min(lens) if lens else 0
+        rows = EventRows(int(capacity), *[_ptr(a, dt) for a, dt in arrs], _ptr(max_occ, np.float64), 0)
+        self._check(ara_run_layer_events(self._h, lay, seed, trial_begin, trial_end, ylt_out, rows))
+        return int(rows.n_rows)
 
     def run_layers(self, layers, seed: int, trial_begin: int, trial_end: int, ylt_out,
                    primary_only: bool = False, newton_only: bool = False) -> None:

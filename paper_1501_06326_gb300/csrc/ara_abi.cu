@@ -76,6 +76,9 @@ struct ara_ctx {
   DevBuf counters;  // 4 x u64
   DevBuf ylt_tmp;   // device YLT when the caller's output is on the host
   DevBuf diag_tmp;  // device diagnostics when the caller's outputs are on the host
+  DevBuf ev_occ;     // per-event output: O_k beside each event buffer record (float)
+  DevBuf row_base;   //   rows before each tile (exclusive scan of tile_cnt) and its scan scratch
+  DevBuf evr_stage;  //   rows and max_occ staged on the device for host arrays
   DevBuf sel;       // select / sort scratch
   DevBuf in_tmp;    // staging of host inputs for pml/sort
   DevBuf out_tmp;   // small device outputs
@@ -627,9 +630,78 @@ static void record_pass_stats(ara_ctx* c, const PassPlan& pl, int64_t t0, int64_
   c->stats.kernel_ms = -1.0f;  // device times are read lazily by ara_get_stats
 }
 
+// The rows of ara_run_layer_events after the losses kernel wrote O_k beside
+// the records: row bases per tile, the row count (read back), then the rows.
+static int emit_event_rows(ara_ctx* c, const PassPlan& pl, const ara::LossParams& p, ara_event_rows* evr,
+                           int* launched) {
+  const int64_t n_tiles = pl.n_tiles, n_out = pl.n_out;
+  int rc;
+  const size_t tmp_words = ara::scan_tmp_words(n_tiles);
+  if ((rc = reserve(c, c->row_base, sizeof(uint32_t) * (n_tiles + 1 + tmp_words + 8)))) return rc;
+  uint32_t* d_base = static_cast<uint32_t*>(c->row_base.ptr);
+  ARA_CUDA(c, ara::scan_exclusive_u32(p.tile_cnt, d_base, n_tiles, d_base + n_tiles + 1, c->stream, launched));
+  uint32_t total = 0;
+  ARA_CUDA(c, cudaMemcpyAsync(&total, d_base + n_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+  ARA_CUDA(c, cudaStreamSynchronize(c->stream));
+  const int64_t n_rows = total;
+  const int64_t n_w = std::min<int64_t>(evr->capacity, n_rows);
+  // device targets: the caller's arrays, or slices of the staging buffer
+  void* user[5] = {evr->trial, evr->event_index, evr->event_id, evr->occ_loss, evr->agg_inc};
+  const size_t esz[5] = {sizeof(int64_t), sizeof(int32_t), sizeof(int32_t), sizeof(double), sizeof(double)};
+  bool staged[5];
+  size_t stage_bytes = 0, at[6];
+  for (int i = 0; i < 5; ++i) {
+    staged[i] = user[i] && n_w > 0 && !is_device_ptr(user[i]);
+    at[i] = stage_bytes;
+    if (staged[i]) stage_bytes += (esz[i] * static_cast<size_t>(n_w) + 15) & ~size_t(15);
+  }
+  const bool max_staged = evr->max_occ && !is_device_ptr(evr->max_occ);
+  at[5] = stage_bytes;
+  if (max_staged) stage_bytes += sizeof(double) * static_cast<size_t>(n_out);
+  if (stage_bytes > 0 && (rc = reserve(c, c->evr_stage, stage_bytes))) return rc;
+  char* stage = static_cast<char*>(c->evr_stage.ptr);
+  void* dev[6];
+  for (int i = 0; i < 5; ++i) dev[i] = staged[i] ? static_cast<void*>(stage + at[i]) : (n_w > 0 ? user[i] : nullptr);
+  dev[5] = max_staged ? static_cast<void*>(stage + at[5]) : static_cast<void*>(evr->max_occ);
+  ara::EventRowsParams q{};
+  q.off = pl.g.off;
+  q.ids = pl.g.ids;
+  q.t_begin = p.t_begin;
+  q.t_end = p.t_end;
+  q.n_tiles = n_tiles;
+  q.e0 = p.e0;
+  q.ev_buf = p.ev_buf;
+  q.occ = p.occ;
+  q.tile_cnt = p.tile_cnt;
+  q.row_base = d_base;
+  q.agg_r = p.agg_r;
+  q.agg_l = p.agg_l;
+  q.cap = n_w;
+  q.row_trial = static_cast<int64_t*>(dev[0]);
+  q.row_k = static_cast<int32_t*>(dev[1]);
+  q.row_event = static_cast<int32_t*>(dev[2]);
+  q.row_occ = static_cast<double*>(dev[3]);
+  q.row_inc = static_cast<double*>(dev[4]);
+  q.max_occ = static_cast<double*>(dev[5]);
+  if (q.max_occ) ARA_CUDA(c, cudaMemsetAsync(q.max_occ, 0, sizeof(double) * n_out, c->stream));
+  const int warps_per_block = ara::kEventRowsThreads / 32;
+  const int grid = static_cast<int>(
+      std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(c->num_sms) * 8,
+                                             (n_tiles + warps_per_block - 1) / warps_per_block)));
+  ARA_CUDA(c, ara::launch_event_rows(q, grid, c->stream));
+  *launched += 1;
+  for (int i = 0; i < 5; ++i)
+    if (staged[i])
+      ARA_CUDA(c, cudaMemcpyAsync(user[i], dev[i], esz[i] * n_w, cudaMemcpyDeviceToHost, c->stream));
+  if (max_staged)
+    ARA_CUDA(c, cudaMemcpyAsync(evr->max_occ, dev[5], sizeof(double) * n_out, cudaMemcpyDeviceToHost, c->stream));
+  evr->n_rows = n_rows;
+  return ARA_OK;
+}
+
 static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out,
-                          const ara_diag* diag) {
-  static const char* who = "ara_run_layer";
+                          const ara_diag* diag, ara_event_rows* evr = nullptr) {
+  const char* who = evr ? "ara_run_layer_events" : "ara_run_layer";
   int rc = bind(c);
   if (rc) return rc;
   if (!L || !ylt_out) return fail(c, ARA_EINVAL, "%s: layer and ylt_out are required", who);
@@ -690,6 +762,14 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   p.diag_hits = d_hits;
   p.diag_hash = d_hash;
   p.counters = static_cast<unsigned long long*>(c->counters.ptr);
+  if (evr) {
+    const int64_t n_ev = c->h_off[t1] - pl.e0;
+    if (n_ev >= (int64_t(1) << 32) - 1)
+      return fail(c, ARA_EINVAL, "%s: the trial range holds %lld YET entries (at most 2^32 - 2)", who,
+                  (long long)n_ev);
+    if ((rc = reserve(c, c->ev_occ, sizeof(float) * (n_ev + 1)))) return rc;
+    p.occ = static_cast<float*>(c->ev_occ.ptr);
+  }
   const int64_t loss_warps = ara::kLossThreads / 32;
   const int loss_grid = static_cast<int>(std::min<int64_t>(c->num_sms * ara::kLossBlocksPerSm,
                                                            (pl.n_tiles + loss_warps - 1) / loss_warps));
@@ -703,6 +783,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   ARA_CUDA(c, cudaEventRecord(lb, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   launched += 1;
+  if (evr && (rc = emit_event_rows(c, pl, p, evr, &launched))) return rc;
   c->launches += launched;
   if (!ylt_dev)
     ARA_CUDA(c, cudaMemcpyAsync(ylt_out, d_ylt, sizeof(double) * n_out, cudaMemcpyDeviceToHost, c->stream));
@@ -710,7 +791,8 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
     ARA_CUDA(c, cudaMemcpyAsync(diag->hits, d_hits, sizeof(int64_t) * n_out, cudaMemcpyDeviceToHost, c->stream));
   if (d_hash && !hash_dev)
     ARA_CUDA(c, cudaMemcpyAsync(diag->hit_hash, d_hash, sizeof(uint64_t) * n_out, cudaMemcpyDeviceToHost, c->stream));
-  if (!ylt_dev || (d_hits && !hits_dev) || (d_hash && !hash_dev)) ARA_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (!ylt_dev || (d_hits && !hits_dev) || (d_hash && !hash_dev) || evr)
+    ARA_CUDA(c, cudaStreamSynchronize(c->stream));
   record_pass_stats(c, pl, t0, t1, L->n_elts);
   return ARA_OK;
 }
@@ -840,6 +922,16 @@ int ara_run_layers(ara_ctx* c, int32_t n_layers, const ara_layer* layers, uint64
 int ara_run_layer_diag(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out,
                        const ara_diag* diag) {
   return run_layer_impl(c, L, seed, t0, t1, ylt_out, diag);
+}
+
+int ara_run_layer_events(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out,
+                         ara_event_rows* rows) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (!rows || rows->capacity < 0)
+    return fail(c, ARA_EINVAL, "ara_run_layer_events: rows is NULL or its capacity is negative");
+  rows->n_rows = 0;
+  return run_layer_impl(c, L, seed, t0, t1, ylt_out, nullptr, rows);
 }
 
 int ara_get_stats(const ara_ctx* cc, ara_stats* out) {
@@ -1187,7 +1279,8 @@ void ara_destroy(ara_ctx* c) {
                     &c->yet_ids,    &c->bits,           &c->word_cnt,      &c->word_pairs,     &c->rankdir,
                     &c->mask,       &c->slot_cnt,       &c->pairs,         &c->pairs_hot,     &c->pairs_w,          &c->scan_tmp,       &c->flags,
                     &c->counters,   &c->ylt_tmp,        &c->diag_tmp,      &c->sel,            &c->in_tmp,
-                    &c->out_tmp,    &c->serve_ylt,      &c->serve_out};
+                    &c->out_tmp,    &c->serve_ylt,      &c->serve_out,      &c->ev_occ,        &c->row_base,
+                    &c->evr_stage};
   for (DevBuf* b : bufs) release(c, *b);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);

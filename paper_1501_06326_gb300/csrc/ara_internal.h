@@ -164,6 +164,7 @@ struct LossParams {
   double* def_acc;  // per trial: deferred occurrence losses of trials still pending at their tile's end
   int64_t* diag_hits;
   uint64_t* diag_hash;
+  float* occ;  // per-event output: [event buffer entries] each hit event's O_k, beside its record (or NULL)
   unsigned long long* counters;  // [0] tile queue, [1] pairs, [2] non-converged, [3] Halley events
 };
 
@@ -207,6 +208,32 @@ size_t gather_smem_bytes(int filt_words);
 int gather_filter_words(int64_t n_words, int max_smem);
 cudaError_t launch_gather(const GatherParams& p, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_losses(const LossParams& p, int grid, cudaStream_t s);
+
+// Per-event output: from the records of each tile and their occurrence losses
+// O_k (k_losses with LossParams::occ), each trial's in-order running sum S_k,
+// A_k = aggregate terms of S_k and inc_k = A_k - A_{k-1}, written as one row
+// per hit event at row_base[tile] + its place in the tile (rows at or beyond
+// `cap` are not written); max_occ[t] = the trial's largest O_k (the caller
+// zeroes it first: trials without rows keep 0).
+struct EventRowsParams {
+  const int64_t* off;
+  const int32_t* ids;  // YET event ids
+  int64_t t_begin, t_end, n_tiles, e0;
+  const uint2* ev_buf;
+  const float* occ;
+  const uint32_t* tile_cnt;
+  const uint32_t* row_base;  // [n_tiles + 1] exclusive scan of tile_cnt
+  double agg_r, agg_l;
+  int64_t cap;
+  int64_t* row_trial;   // each of the five may be NULL
+  int32_t* row_k;
+  int32_t* row_event;
+  double* row_occ;
+  double* row_inc;
+  double* max_occ;      // [t_end - t_begin] or NULL
+};
+cudaError_t launch_event_rows(const EventRowsParams& q, int grid, cudaStream_t s);
+constexpr int kEventRowsThreads = 256;
 
 // --------------------------------------------------------------- PML / TVaR / sort
 // Scratch sizes in bytes for n year losses.

@@ -281,9 +281,11 @@ constexpr uint32_t kDefLast = 2u;  // last deferred event of its trial
 struct LossWarp {
   float2 acc[kWarpTrials][32];  // per trial and lane: double-float sum of the lane's occurrence losses
   uint2 mq[kQueue];             // queued multi-ELT events (event records)
+  uint32_t mqi[kQueue];         //   their places in the tile's records (per-event output)
   uint32_t d_key[32];           // deferred events: record
   uint32_t d_ps[32];            //   first pair
   int64_t d_o[32];              //   trial (output index)
+  int64_t d_idx[32];            //   event buffer entry of the record (per-event output)
   uint32_t d_fl[32];            //   kDefCur | kDefLast
   float d_O[32];                //   occurrence loss, once resolved
   double Sd[kWarpTrials];       // sums of the deferred occurrence losses resolved while the tile is open
@@ -366,7 +368,9 @@ __device__ __noinline__ float pair_slow(const LossParams& p, const Pair& pr, uin
 // deferred losses form their own FP64 sum, in event order, so where the list
 // is flushed does not change any result: entries of the open tile go to its
 // shared sums, older ones to def_acc, and the last one of a trial finishes
-// its year loss.
+// its year loss.  kEmit: also stores each entry's occurrence loss beside its
+// record (per-event output).
+template <bool kEmit>
 __device__ __noinline__ void resolve_deferred(const LossParams& p, LossWarp& ws, int nd) {
   const uint32_t lane = lane_id();
   float O = 0.0f;
@@ -380,6 +384,7 @@ __device__ __noinline__ void resolve_deferred(const LossParams& p, LossWarp& ws,
     float G = 0.0f;
     for (uint32_t j = 0; j < cnt; ++j) G += pair_slow(p, p.pairs[ws.d_ps[lane] + j], ws.d_ps[lane] + j, t, k, nc);
     O = clamp_terms_f(G, p.occ_r, p.occ_l);
+    if constexpr (kEmit) p.occ[ws.d_idx[lane]] = O;
   }
   const uint32_t nc_w = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(nc_l));
   ws.d_O[lane] = O;
@@ -420,13 +425,15 @@ namespace {
 
 // Appends this lane's event to the deferred list when `defer` (warp-wide call;
 // events are listed in lane order), resolving the list first when it is full.
-// Returns the new length of the list.
+// Returns the new length of the list.  `idx` (kEmit) is the record's event
+// buffer entry.
+template <bool kEmit>
 __device__ __forceinline__ int defer_events(const LossParams& p, LossWarp& ws, int nd, bool defer, uint2 r,
-                                            int64_t o) {
+                                            int64_t o, int64_t idx) {
   const uint32_t dmask = __ballot_sync(0xffffffffu, defer);
   if (dmask == 0) return nd;
   if (nd + __popc(dmask) > 32) {
-    resolve_deferred(p, ws, nd);
+    resolve_deferred<kEmit>(p, ws, nd);
     nd = 0;
   }
   if (defer) {
@@ -435,6 +442,7 @@ __device__ __forceinline__ int defer_events(const LossParams& p, LossWarp& ws, i
     ws.d_ps[at] = r.y;
     ws.d_o[at] = o;
     ws.d_fl[at] = kDefCur;
+    if constexpr (kEmit) ws.d_idx[at] = idx;
   }
   __syncwarp();
   return nd + __popc(dmask);
@@ -480,9 +488,11 @@ __device__ __forceinline__ bool pair_fast_hot(const LossParams& p, const EltShar
 // The queued multi-ELT events, in windows of at most 32 pairs (one per lane):
 // losses of the pairs, a segmented sum per event (pairs in layer order), the
 // occurrence terms at each event's last lane.  Returns (deferred list length,
-// pairs processed).
+// pairs processed).  kEmit: the occurrence losses also go beside the records
+// (the tile's records start at event buffer entry rb).
+template <bool kEmit>
 __device__ __forceinline__ int2 process_multi(const LossParams& p, const EltShared& es, LossWarp& ws, int nd, int nq,
-                                              int64_t ta, bool diag) {
+                                              int64_t ta, bool diag, int64_t rb) {
   const uint32_t q = lane_id();
   const uint32_t upto = 0xffffffffu >> (31u - q);  // lanes 0..q
   int n_pairs = 0;
@@ -526,8 +536,15 @@ __device__ __forceinline__ int2 process_multi(const LossParams& p, const EltShar
     const uint32_t smask = __ballot_sync(0xffffffffu, slow);
     const bool end = q < np && q == epre + ecnt - 1u;
     const bool seg_slow = ((smask >> epre) & (0xffffffffu >> (31u - (q - epre)))) != 0u;
-    if (end && !seg_slow) acc_add(ws, etl, clamp_terms_f(L, p.occ_r, p.occ_l));
-    nd = defer_events(p, ws, nd, end && seg_slow, make_uint2(ex, ey), ta + etl - p.t_begin);
+    if (end && !seg_slow) {
+      const float O = clamp_terms_f(L, p.occ_r, p.occ_l);
+      acc_add(ws, etl, O);
+      if constexpr (kEmit) p.occ[rb + ws.mqi[i0 + ev]] = O;
+    }
+    int64_t idx = 0;  // lane q < np holds a pair of queue entry i0 + ev; only event ends read it
+    if constexpr (kEmit)
+      if (end) idx = rb + ws.mqi[i0 + ev];
+    nd = defer_events<kEmit>(p, ws, nd, end && seg_slow, make_uint2(ex, ey), ta + etl - p.t_begin, idx);
     i0 += n_take;
   }
   __syncwarp();
@@ -561,7 +578,9 @@ __device__ __forceinline__ void reduce_scatter_stage(float (&h)[kWarpTrials], fl
 // lane's sum for the event's trial.  Events with several pairs are queued and
 // processed in windows of 32 pairs with a segmented sum.  At the end of the
 // tile one reduce-scatter over the lanes turns the per-lane sums into the
-// trials' sums.
+// trials' sums.  kEmit (per-event output) also stores each hit event's
+// occurrence loss beside its record.
+template <bool kEmit>
 __global__ void __launch_bounds__(kLossThreads, kLossBlocksPerSm) k_losses(const LossParams p) {
   __shared__ LossWarp lw[kLossThreads / 32];
   __shared__ EltShared es;
@@ -595,7 +614,8 @@ __global__ void __launch_bounds__(kLossThreads, kLossBlocksPerSm) k_losses(const
     const int64_t ta = p.t_begin + tile * kWarpTrials;
     const int64_t tb = (ta + kWarpTrials < p.t_end) ? ta + kWarpTrials : p.t_end;
     const int ntr = static_cast<int>(tb - ta);
-    const uint2* recs = p.ev_buf + (__ldg(&p.off[ta]) - p.e0);
+    const int64_t rb = __ldg(&p.off[ta]) - p.e0;  // the tile's first event buffer entry
+    const uint2* recs = p.ev_buf + rb;
     const uint32_t n = __ldg(&p.tile_cnt[tile]);
 #pragma unroll
     for (int t = 0; t < kWarpTrials; ++t) ws.acc[t][lane] = make_float2(0.0f, 0.0f);
@@ -627,7 +647,11 @@ __global__ void __launch_bounds__(kLossThreads, kLossBlocksPerSm) k_losses(const
         if (single) {
           float L;
           slow = !pair_fast_hot(p, es, h, r.y, ta + tl, k, &L);
-          if (!slow) acc_add(ws, tl, clamp_terms_f(L, p.occ_r, p.occ_l));
+          if (!slow) {
+            const float O = clamp_terms_f(L, p.occ_r, p.occ_l);
+            acc_add(ws, tl, O);
+            if constexpr (kEmit) p.occ[rb + base + lane] = O;
+          }
           if (diag) {
             const uint32_t elt = es.elt_id[pair_pos(h.meta)];
             atomicAdd(&ws.hits[tl], 1ull);
@@ -635,16 +659,19 @@ __global__ void __launch_bounds__(kLossThreads, kLossBlocksPerSm) k_losses(const
           }
         }
         n_pairs += __popc(__ballot_sync(0xffffffffu, single));
-        nd = defer_events(p, ws, nd, slow, r, ta + tl - p.t_begin);
+        nd = defer_events<kEmit>(p, ws, nd, slow, r, ta + tl - p.t_begin, rb + base + lane);
         const uint32_t mmask = __ballot_sync(0xffffffffu, valid && cnt > 1u);
         if (mmask) {
-          if (valid && cnt > 1u) ws.mq[nq + __popc(mmask & lt_mask)] = r;
+          if (valid && cnt > 1u) {
+            ws.mq[nq + __popc(mmask & lt_mask)] = r;
+            if constexpr (kEmit) ws.mqi[nq + __popc(mmask & lt_mask)] = base + lane;
+          }
           nq += __popc(mmask);
         }
       }
       __syncwarp();
       if (nq > 0) {
-        const int2 rv = process_multi(p, es, ws, nd, nq, ta, diag);
+        const int2 rv = process_multi<kEmit>(p, es, ws, nd, nq, ta, diag, rb);
         nd = rv.x;
         n_pairs += static_cast<uint32_t>(rv.y);
         nq = 0;
@@ -702,7 +729,7 @@ __global__ void __launch_bounds__(kLossThreads, kLossBlocksPerSm) k_losses(const
     }
     __syncwarp();
   }
-  if (nd > 0) resolve_deferred(p, ws, nd);
+  if (nd > 0) resolve_deferred<kEmit>(p, ws, nd);
   if (lane == 0) {
     const unsigned long long n_nc = ws.n_nc, n_slow = ws.n_slow;
     if (n_pairs) atomicAdd(&p.counters[1], static_cast<unsigned long long>(n_pairs));
@@ -712,7 +739,10 @@ __global__ void __launch_bounds__(kLossThreads, kLossBlocksPerSm) k_losses(const
 }
 
 cudaError_t launch_losses(const LossParams& p, int grid, cudaStream_t s) {
-  k_losses<<<grid, kLossThreads, 0, s>>>(p);
+  if (p.occ)
+    k_losses<true><<<grid, kLossThreads, 0, s>>>(p);
+  else
+    k_losses<false><<<grid, kLossThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 
