@@ -562,7 +562,7 @@ static int plan_pass(ara_ctx* c, const std::vector<int32_t>& ids, int64_t t0, in
   // ---- gather
   pl->filt_words = ara::gather_filter_words(n_words, c->max_smem);
   pl->smem = ara::gather_smem_bytes(pl->filt_words);
-  if (pl->smem > static_cast<size_t>(c->max_smem))
+  if (pl->filt_words < 1 || pl->smem > static_cast<size_t>(c->max_smem))
     return fail(c, ARA_ECUDA, "%s: kernel needs %zu bytes of shared memory, device allows %d", who, pl->smem,
                 c->max_smem);
   pl->n_out = t1 - t0;

@@ -134,7 +134,7 @@ struct GatherParams {
   const uint2* rankdir;
   int64_t n_words;
   const uint32_t* slot_start;
-  int32_t filt_words;  // power of two
+  int32_t filt_words;  // filter words: at least n_words / 2, else a power of two
   uint2* ev_buf;
   uint32_t* tile_cnt;
   unsigned long long* queue;  // tile counter

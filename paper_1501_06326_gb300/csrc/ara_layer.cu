@@ -29,24 +29,24 @@ __device__ __forceinline__ T warp_inclusive_scan(T v) {
 // =============================================================== layer kernels
 //
 // k_gather: one persistent CTA of 32 warps per SM.  The CTA folds the layer's
-// catalogue bitmap into a shared-memory membership filter once; then each warp
-// independently takes tiles of kWarpTrials consecutive trials and streams the
-// tile's YET ids, 128 per step (one int4 per lane, evict-first, the next step
-// in flight).  Each id is tested against the filter; each positive is resolved
-// against the rank directory (8 bytes: the word's bits and its pair base) and,
-// if it is a member, becomes an event record written in YET order to the
-// tile's region of the event buffer.
+// catalogue bitmap into a shared-memory membership filter once (as many words
+// as shared memory holds; word w of the catalogue lands on w mod filt_words);
+// then each warp independently takes tiles of kWarpTrials consecutive trials
+// and streams the tile's YET ids, 256 per step (two int4 per lane, evict-first,
+// two more steps in flight).  Each id is tested against the filter; each
+// positive is resolved against the rank directory (8 bytes: the word's bits
+// and its pair base) and, if it is a member, becomes an event record written
+// in YET order to the tile's region of the event buffer.
 //
-// k_losses: each warp takes tiles and reads their records in windows of up to
-// 32 events whose (event, ELT) pairs number at most 32, one pair per lane:
-// Philox uniform, inverse Beta through the record's quantile table, ELT terms.
-// A segmented warp reduction sums each event's pair losses in layer order
-// (FP32) and applies the occurrence terms; a segmented double-float reduction
-// adds the window's occurrence losses of each trial into the trial's FP64
-// running sum (one FP64 add per trial and window).  Events with a pair whose
-// record's table is not exact are deferred and resolved, 32 at a time, by the
-// FP32 Halley iteration.  The aggregate terms turn each running sum into the
-// trial's year loss.
+// k_losses: each warp takes tiles and reads their records one per lane.  An
+// event with one (event, ELT) pair is finished by its lane: Philox uniform,
+// inverse Beta through the record's quantile table, ELT and occurrence terms,
+// and a double-float add into the lane's sum for the event's trial.  Events
+// with several pairs are queued and processed in windows of 32 pairs with a
+// segmented sum.  Events with a pair whose record's table is not exact are
+// deferred and resolved, 32 at a time, by the FP32 Halley iteration.  At the
+// end of a tile a reduce-scatter over the lanes gives the trials' sums, and
+// the aggregate terms turn each into the trial's year loss.
 
 namespace {
 
@@ -54,8 +54,9 @@ __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
 
 struct GatherWarp {
-  int32_t off[16];  // trial offsets relative to the tile's first event; INT32_MAX past the tile's end
-  uint2 pos[256];   // filter positives of one step: (event id, position in the step)
+  int32_t off[16];      // trial offsets relative to the tile's first event; INT32_MAX past the tile's end
+  uint32_t pos_id[256];  // filter positives of one step: event id
+  uint8_t pos_q[256];    //   and position in the step
 };
 
 }  // namespace
@@ -64,10 +65,22 @@ size_t gather_smem_bytes(int filt_words) {
   return sizeof(uint32_t) * static_cast<size_t>(filt_words) + sizeof(GatherWarp) * (kGatherThreads / 32) + 16;
 }
 
+// k_gather's shared memory stays within the 196 KB carveout (less the 1 KB
+// the driver reserves per block): the L1 that the rest of the SM's 256 KB
+// leaves (60 KB) holds the id stream's loads in flight, and a larger carveout
+// (L1 28 KB) was measured to slow the stream by a quarter, more than a larger
+// filter saves.
+constexpr int kGatherSmemBudget = 196 * 1024 - 1024;
+
 int gather_filter_words(int64_t n_words, int max_smem) {
-  int fw = 1;
-  while (fw < n_words && gather_smem_bytes(fw * 2) <= static_cast<size_t>(max_smem)) fw *= 2;
-  return fw;
+  const int64_t budget = max_smem < kGatherSmemBudget ? max_smem : kGatherSmemBudget;
+  const int64_t room = (budget - static_cast<int64_t>(gather_smem_bytes(0))) / 4;
+  const int64_t fw_max = room & ~int64_t(31);
+  if (fw_max < 32) return 0;
+  if (n_words <= 2 * fw_max) return static_cast<int>(n_words <= fw_max ? (n_words > 0 ? n_words : 1) : fw_max);
+  int64_t fw = 32;
+  while (fw * 2 <= fw_max) fw *= 2;
+  return static_cast<int>(fw);
 }
 
 namespace {
@@ -141,7 +154,11 @@ __device__ __forceinline__ void gather_complete(const GatherParams& p, const Gat
 // One step of 256 YET positions: filter, compact the positives in YET order,
 // finish the previous step's positives, then either put this step's in flight
 // (up to 64) or resolve them at once.
-__device__ __forceinline__ void gather_step(const GatherParams& p, const uint32_t* __restrict__ filt, uint32_t fmask,
+// kSub: the catalogue has at most twice filt_words words, and word w folds
+// onto min(w, w - filt_words) (unsigned); otherwise filt_words is a power of
+// two and w folds onto w & (filt_words - 1).  fsel is filt_words or the mask.
+template <bool kSub>
+__device__ __forceinline__ void gather_step(const GatherParams& p, const uint32_t* __restrict__ filt, uint32_t fsel,
                                             GatherWarp& ws, GatherTile& g, GatherPending& pd, int32_t c0,
                                             uint32_t lane, int4 v0, int4 v1) {
   const uint32_t e[8] = {static_cast<uint32_t>(v0.x), static_cast<uint32_t>(v0.y), static_cast<uint32_t>(v0.z),
@@ -151,7 +168,8 @@ __device__ __forceinline__ void gather_step(const GatherParams& p, const uint32_
   uint32_t m = 0;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    const uint32_t w = filt[(e[j] >> 5) & fmask];
+    const uint32_t wi = e[j] >> 5;
+    const uint32_t w = filt[kSub ? min(wi, wi - fsel) : (wi & fsel)];
     m |= (__funnelshift_r(w, w, e[j]) & 1u) << j;
   }
   const uint32_t q0 = 4u * lane;  // step positions of the lane's ids: q0 + j, q0 + 128 + j
@@ -174,29 +192,37 @@ __device__ __forceinline__ void gather_step(const GatherParams& p, const uint32_
   gather_complete(p, ws, g, pd, lane);
   pd.npos = 0;
   if (npos == 0) return;
+  // 4. this step's positives: staged, then in flight, or resolved at once when there are many
   if (m) {
     uint32_t at = (incl & 0xFFFFu) - cl;
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (m & (1u << j)) ws.pos[at++] = make_uint2(e[j], q0 + j);
+      if (m & (1u << j)) {
+        ws.pos_id[at] = e[j];
+        ws.pos_q[at] = static_cast<uint8_t>(q0 + j);
+        ++at;
+      }
     at = nlo + (incl >> 16) - ch;
 #pragma unroll
     for (int j = 4; j < 8; ++j)
-      if (m & (1u << j)) ws.pos[at++] = make_uint2(e[j], q0 + 124 + j);
+      if (m & (1u << j)) {
+        ws.pos_id[at] = e[j];
+        ws.pos_q[at] = static_cast<uint8_t>(q0 + 124 + j);
+        ++at;
+      }
   }
   __syncwarp();
-  // 4. this step's positives: in flight, or resolved now when there are many
   if (npos <= 64) {
     pd.npos = npos;
     pd.c0 = c0;
-    pd.q0 = lane < npos ? ws.pos[lane] : make_uint2(0u, 0u);
-    pd.q1 = 32 + lane < npos ? ws.pos[32 + lane] : make_uint2(0u, 0u);
+    pd.q0 = lane < npos ? make_uint2(ws.pos_id[lane], ws.pos_q[lane]) : make_uint2(0u, 0u);
+    pd.q1 = 32 + lane < npos ? make_uint2(ws.pos_id[32 + lane], ws.pos_q[32 + lane]) : make_uint2(0u, 0u);
     pd.rd0 = lane < npos ? __ldg(&p.rankdir[pd.q0.x >> 5]) : make_uint2(0u, 0u);
     pd.rd1 = 32 + lane < npos ? __ldg(&p.rankdir[pd.q1.x >> 5]) : make_uint2(0u, 0u);
   } else {
     for (uint32_t r0 = 0; r0 < npos; r0 += 32) {
       const bool valid = r0 + lane < npos;
-      const uint2 q = valid ? ws.pos[r0 + lane] : make_uint2(0u, 0u);
+      const uint2 q = valid ? make_uint2(ws.pos_id[r0 + lane], ws.pos_q[r0 + lane]) : make_uint2(0u, 0u);
       const uint2 rd = valid ? __ldg(&p.rankdir[q.x >> 5]) : make_uint2(0u, 0u);
       gather_resolve(p, ws, g, c0, q, rd, valid, lane);
     }
@@ -206,13 +232,14 @@ __device__ __forceinline__ void gather_step(const GatherParams& p, const uint32_
 
 }  // namespace
 
+template <bool kSub>
 __global__ void __launch_bounds__(kGatherThreads, 1) k_gather(const GatherParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   GatherWarp* gw = reinterpret_cast<GatherWarp*>(smem_raw);
   uint32_t* filt = reinterpret_cast<uint32_t*>(gw + (kGatherThreads / 32));
   const uint32_t lane = lane_id();
   GatherWarp& ws = gw[threadIdx.x >> 5];
-  const uint32_t fmask = static_cast<uint32_t>(p.filt_words) - 1u;
+  const uint32_t fsel = kSub ? static_cast<uint32_t>(p.filt_words) : static_cast<uint32_t>(p.filt_words) - 1u;
 
   for (int w = threadIdx.x; w < p.filt_words; w += blockDim.x) {
     uint32_t v = 0;
@@ -250,13 +277,13 @@ __global__ void __launch_bounds__(kGatherThreads, 1) k_gather(const GatherParams
     gather_load(g, 256, lane, b0, b1);
     for (int32_t c0 = 0; c0 < g.span; c0 += 768) {
       gather_load(g, c0 + 512, lane, c0v, c1v);
-      gather_step(p, filt, fmask, ws, g, pd, c0, lane, a0, a1);
+      gather_step<kSub>(p, filt, fsel, ws, g, pd, c0, lane, a0, a1);
       if (c0 + 256 >= g.span) break;
       gather_load(g, c0 + 768, lane, a0, a1);
-      gather_step(p, filt, fmask, ws, g, pd, c0 + 256, lane, b0, b1);
+      gather_step<kSub>(p, filt, fsel, ws, g, pd, c0 + 256, lane, b0, b1);
       if (c0 + 512 >= g.span) break;
       gather_load(g, c0 + 1024, lane, b0, b1);
-      gather_step(p, filt, fmask, ws, g, pd, c0 + 512, lane, c0v, c1v);
+      gather_step<kSub>(p, filt, fsel, ws, g, pd, c0 + 512, lane, c0v, c1v);
     }
     gather_complete(p, ws, g, pd, lane);
     if (lane == 0) p.tile_cnt[tile] = g.nout;
@@ -265,10 +292,14 @@ __global__ void __launch_bounds__(kGatherThreads, 1) k_gather(const GatherParams
 }
 
 cudaError_t launch_gather(const GatherParams& p, int grid, size_t smem, cudaStream_t s) {
-  cudaError_t err =
-      cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  const bool sub = p.n_words <= 2 * static_cast<int64_t>(p.filt_words);
+  const void* fn = sub ? reinterpret_cast<const void*>(k_gather<true>) : reinterpret_cast<const void*>(k_gather<false>);
+  cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (err != cudaSuccess) return err;
-  k_gather<<<grid, kGatherThreads, smem, s>>>(p);
+  if (sub)
+    k_gather<true><<<grid, kGatherThreads, smem, s>>>(p);
+  else
+    k_gather<false><<<grid, kGatherThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
