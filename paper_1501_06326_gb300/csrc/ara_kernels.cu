@@ -99,7 +99,7 @@ namespace {
 // multiply-adds; every 8 terms the pairs are rescaled by 1/B_n, which is where
 // convergence of A_n / B_n is tested.  FP64 divisions are slow on this GPU, so
 // this costs about a tenth of the modified Lentz method.
-__device__ double beta_cf_f64(double a, double b, double x) {
+__device__ double beta_cf_f64_ref(double a, double b, double x) {
   double A2 = 1.0, B2 = 0.0;  // A_{n-2}, B_{n-2}
   double A1 = 1.0, B1 = 1.0;  // A_{n-1}, B_{n-1}
   double q_prev = 1.0, f_prev = 1.0;
@@ -132,6 +132,107 @@ __device__ double beta_cf_f64(double a, double b, double x) {
     }
   }
   return B1 / A1;
+}
+
+// Double-float arithmetic (an unevaluated sum hi + lo of two FP32 values, 48
+// significand bits): error-free sums (Knuth's TwoSum) and products (by FMA),
+// with the rounding intrinsics so that no step is contracted or reordered.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_of(double v) {
+  const float hi = static_cast<float>(v);
+  return DF{hi, static_cast<float>(v - static_cast<double>(hi))};
+}
+__device__ __forceinline__ double df_val(DF v) { return static_cast<double>(v.hi) + static_cast<double>(v.lo); }
+__device__ __forceinline__ DF df_norm(float s, float e) {  // |s| >= |e|
+  const float h = __fadd_rn(s, e);
+  return DF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  const float s = __fadd_rn(x.hi, y.hi);
+  const float bb = __fsub_rn(s, x.hi);
+  const float err = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+  return df_norm(s, __fadd_rn(err, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ DF df_add_f(DF x, float y) {
+  const float s = __fadd_rn(x.hi, y);
+  const float bb = __fsub_rn(s, x.hi);
+  const float err = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y, bb));
+  return df_norm(s, __fadd_rn(err, x.lo));
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
+  return df_norm(p, e);
+}
+__device__ __forceinline__ DF df_neg(DF x) { return DF{-x.hi, -x.lo}; }
+// x 2^k for an exponent k with 2^k a normal float (exact)
+__device__ __forceinline__ DF df_scale(DF x, int k) {
+  const float f = __int_as_float((127 + k) << 23);
+  return DF{__fmul_rn(x.hi, f), __fmul_rn(x.lo, f)};
+}
+__device__ __forceinline__ int f_exponent(float v) { return ((__float_as_int(v) >> 23) & 255) - 127; }
+
+// The continued fraction of beta_cf_f64_ref in double-float arithmetic, two
+// terms (the odd and the even one of each m) per iteration: FP64 runs at a
+// small fraction of the FP32 rate on this GPU, and 48 bits carry the value to
+// the 1e-13 relative tolerance used here (the table nodes are FP32; their
+// polish and check need the CDF to about 1e-10).  FP32's exponent range is
+// kept by rescaling the four convergents by a power of two each iteration
+// (exact; the ratio is unchanged).  Returns NaN when a value leaves the FP32
+// range or the iteration does not converge, for the FP64 fallback.
+__device__ double beta_cf_df(double a, double b, double x) {
+  const DF X = df_of(x);
+  DF v = df_of(a);          // a + m
+  DF w = df_of(a + b);      // a + b + m
+  DF y = df_of(b - 1.0);    // b - m - 1
+  DF u = df_of(a);          // a + 2m
+  DF A2{1.0f, 0.0f}, B2{0.0f, 0.0f}, A1{1.0f, 0.0f}, B1{1.0f, 0.0f};
+  DF q_prev{1.0f, 0.0f};
+  double f_prev = 1.0;
+  for (int m = 0; m < 20000; ++m) {
+    const DF u1 = df_add_f(u, 1.0f), u2 = df_add_f(u, 2.0f);
+    // odd term n = 2m + 1: p = -(a + m)(a + b + m) x, q = (a + 2m)(a + 2m + 1)
+    const DF qo = df_mul(u, u1);
+    const DF ao = df_mul(q_prev, df_neg(df_mul(df_mul(v, w), X)));
+    DF A0 = df_add(df_mul(qo, A1), df_mul(ao, A2));
+    DF B0 = df_add(df_mul(qo, B1), df_mul(ao, B2));
+    // even term n = 2m + 2: p = (m + 1)(b - m - 1) x, q = (a + 2m + 1)(a + 2m + 2)
+    const DF qe = df_mul(u1, u2);
+    const DF ae = df_mul(qo, df_mul(df_mul(DF{static_cast<float>(m + 1), 0.0f}, y), X));
+    const DF Ae = df_add(df_mul(qe, A0), df_mul(ae, A1));
+    const DF Be = df_add(df_mul(qe, B0), df_mul(ae, B1));
+    A2 = A0;
+    B2 = B0;
+    A1 = Ae;
+    B1 = Be;
+    q_prev = qe;
+    v = df_add_f(v, 1.0f);
+    w = df_add_f(w, 1.0f);
+    y = df_add_f(y, -1.0f);
+    u = u2;
+    const float big = fmaxf(fabsf(A1.hi), fabsf(B1.hi));
+    if (!(big < 3.0e38f) || !(big > 0.0f)) return __longlong_as_double(0x7ff8000000000000ll);
+    const int k = -f_exponent(big);
+    A1 = df_scale(A1, k);
+    A2 = df_scale(A2, k);
+    B1 = df_scale(B1, k);
+    B2 = df_scale(B2, k);
+    if ((m & 3) == 3) {
+      const double f = df_val(A1) / df_val(B1);
+      if (fabs(f - f_prev) <= 1e-13 * fabs(f)) return df_val(B1) / df_val(A1);
+      f_prev = f;
+    }
+  }
+  return __longlong_as_double(0x7ff8000000000000ll);
+}
+
+// The continued fraction of I_x(a, b): double-float, else FP64.
+__device__ double beta_cf_f64(double a, double b, double x) {
+  const double r = beta_cf_df(a, b, x);
+  return isfinite(r) ? r : beta_cf_f64_ref(a, b, x);
 }
 
 }  // namespace
@@ -379,7 +480,7 @@ __device__ bool table_segment_ok(float4 nd, float d1, float e1, double t, double
 // Coarse tables, one warp per record, lane j = node j at t_j = -T1 + j h.  The
 // stored float4 is {x_j, w_{j+1} - w_j, h w'_j, h^2 w''_j}.  need[rec] = 1 for
 // a Beta record whose coarse table is not exact (a candidate for a fine table).
-__global__ void __launch_bounds__(256, 4) k_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab,
+__global__ void __launch_bounds__(256, 2) k_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab,
                                                         uint32_t* need) {
   const int lane = threadIdx.x & 31;
   const int64_t rec = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
