@@ -1066,7 +1066,7 @@ int ara_serve_step(ara_ctx* c, int32_t* n_done) {
       const ServeReq& r = c->serve_reqs[batch[i]];
       const int32_t m = static_cast<int32_t>(r.rps.size());
       e = ara::pml_tvar_device(d_ylt + static_cast<int64_t>(i) * t_max, r.t_end, r.rps.data(), m, d_out + at,
-                               d_out + n_rp_total + at, c->sel.ptr, c->stream, &launched);
+                               d_out + n_rp_total + at, c->sel.ptr, c->sel.bytes, c->stream, &launched);
       at += m;
     }
     c->launches += launched;
@@ -1134,7 +1134,8 @@ int ara_pml_tvar(ara_ctx* c, const double* ylt, int64_t n, const double* rps, in
   if (!timed_pair(c, 2, &pa, &pb)) return fail(c, ARA_ECUDA, "ara_pml_tvar: cannot create timing events");
   int launched = 0;
   ARA_CUDA(c, cudaEventRecord(pa, c->stream));
-  ARA_CUDA(c, ara::pml_tvar_device(d_ylt, n, h_rps.data(), n_rp, d_pml, d_tvar, c->sel.ptr, c->stream, &launched));
+  ARA_CUDA(c, ara::pml_tvar_device(d_ylt, n, h_rps.data(), n_rp, d_pml, d_tvar, c->sel.ptr, c->sel.bytes, c->stream,
+                                   &launched));
   ARA_CUDA(c, cudaEventRecord(pb, c->stream));
   c->launches += launched;
   if (!pml_dev) ARA_CUDA(c, cudaMemcpyAsync(pml_out, d_pml, sizeof(double) * n_rp, cudaMemcpyDeviceToHost, c->stream));

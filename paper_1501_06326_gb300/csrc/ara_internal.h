@@ -237,10 +237,12 @@ constexpr int kEventRowsThreads = 256;
 
 // --------------------------------------------------------------- PML / TVaR / sort
 // Scratch sizes in bytes for n year losses.
+// Scratch of the five-launch select (a select state alone, sizeof the
+// state, runs the ten-launch select).
 size_t select_scratch_bytes(int64_t n);
 // pml/tvar: n_rp device doubles each; rps: host array.
 cudaError_t pml_tvar_device(const double* ylt, int64_t n, const double* rps_host, int32_t n_rp, double* pml,
-                            double* tvar, void* scratch, cudaStream_t s, int* n_launch);
+                            double* tvar, void* scratch, size_t scratch_bytes, cudaStream_t s, int* n_launch);
 size_t sort_scratch_bytes(int64_t n);
 cudaError_t sort_desc_device(const double* ylt, int64_t n, int64_t* order, void* scratch, cudaStream_t s,
                              int* n_launch);

@@ -2,10 +2,14 @@
 //
 // Year losses are mapped to order-preserving 64-bit keys (sign-flipped IEEE
 // bits).  PML(RP) is the m-th largest year loss, m = ceil(n / RP): an MSB-first
-// radix select with 8-bit digits narrows the key prefix in eight histogram
-// passes.  TVaR(RP) is the mean of the m largest: the sum of the values whose
-// key exceeds the m-th key plus the tied remainder times the m-th value, in
-// FP64 with a fixed reduction order (deterministic).  The full trial order
+// radix select with 8-bit digits narrows the key prefix.  With a scratch of
+// select_scratch_bytes(n), two histogram passes fix 16 bits, a third pass
+// compacts the keys of that 16-bit bucket (in a fixed order) and one block
+// finishes the remaining 48 bits on them; with only the select state (the
+// allocation-free entry point) all eight passes run over the YLT.  TVaR(RP)
+// is the mean of the m largest: the sum of the values whose key exceeds the
+// m-th key plus the tied remainder times the m-th value, in FP64 with a fixed
+// reduction order (deterministic).  The full trial order
 // (largest first, ties by index) is an LSD radix sort of the complemented keys
 // with stable per-tile scatter (warp match + per-warp digit offsets).
 #include <cuda_runtime.h>
@@ -55,6 +59,18 @@ struct SelMs {
   unsigned long long m[kSelGroup];
 };
 
+// The fast path's part of the scratch (after SelScratch): each block's digit
+// counts of the second pass, and its sum and count of the values above each
+// period's 16-bit bucket.
+struct SelFast {
+  unsigned int blk_hist[kSelBlocks][kSelGroup][256];
+  double above_sum[kSelBlocks][kSelGroup];
+  unsigned long long above_cnt[kSelBlocks][kSelGroup];
+};
+
+constexpr size_t kSelStateBytes = (sizeof(SelScratch) + 255) & ~size_t(255);
+constexpr size_t kSelFastBytes = (sizeof(SelFast) + 255) & ~size_t(255);
+
 __global__ void k_sel_init(SelScratch* sc, SelMs ms, int g) {
   if (threadIdx.x < g) {
     SelState& st = sc->st[threadIdx.x];
@@ -84,7 +100,8 @@ __device__ __forceinline__ bool last_block_arrives(SelScratch* sc) {
 // the digit among the keys that match each period's prefix (warp-aggregated
 // shared-memory counts, then one global add per digit and block); the last
 // block to finish picks each period's digit and clears the histogram.
-__global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, int shift) {
+// blk_hist (or NULL): each block also stores its own counts there.
+__global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, int shift, unsigned int* blk_hist) {
   __shared__ unsigned int sh[kSelGroup][256];
   for (int i = threadIdx.x; i < kSelGroup * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
   unsigned long long prefix[kSelGroup], mask[kSelGroup];
@@ -133,6 +150,7 @@ __global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, 
   for (int i = threadIdx.x; i < g * 256; i += blockDim.x) {
     const unsigned int c = (&sh[0][0])[i];
     if (c) atomicAdd(&(&sc->hist[0][0])[i], c);
+    if (blk_hist) blk_hist[static_cast<size_t>(blockIdx.x) * kSelGroup * 256 + i] = c;
   }
   if (!last_block_arrives(sc)) return;
   // ---- pick: per period, the digit holding the wanted rank (a suffix scan of
@@ -253,13 +271,244 @@ __global__ void k_sel_tail(const double* ylt, int64_t n, SelScratch* sc, int g, 
   if (threadIdx.x == 0) sc->done = 0;
 }
 
+// The fast path's third pass: with each period's 16-bit prefix fixed, the
+// keys of that bucket are written to cand[r * n ..] in a fixed order (block
+// by block, in the order of the block's elements), each block starting at the
+// number of bucket keys of the blocks before it (from the second pass's
+// per-block counts); each block also publishes the FP64 sum and the count of
+// its values above the bucket.  Same grid and element assignment as
+// k_sel_hist.
+__global__ void k_sel_compact(const double* ylt, int64_t n, const SelScratch* sc, SelFast* sf, int g,
+                              unsigned long long* cand) {
+  __shared__ unsigned int s_wcnt[kSelThreads / 32][kSelGroup];
+  __shared__ unsigned int s_off[kSelGroup];
+  __shared__ double s_sum[kSelThreads / 32][kSelGroup];
+  __shared__ unsigned long long s_cnt[kSelThreads / 32][kSelGroup];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long prefix[kSelGroup], mask[kSelGroup], top[kSelGroup];
+#pragma unroll
+  for (int r = 0; r < kSelGroup; ++r) {
+    prefix[r] = r < g ? sc->st[r].prefix : ~0ull;
+    mask[r] = r < g ? sc->st[r].mask : 0ull;
+    top[r] = r < g ? (prefix[r] | ~mask[r]) : ~0ull;  // the bucket's largest key
+  }
+  if (threadIdx.x < static_cast<unsigned int>(g)) {
+    const int r = threadIdx.x;
+    const unsigned int d = static_cast<unsigned int>(prefix[r] >> 48) & 255u;
+    unsigned int off = 0;
+    for (unsigned int b = 0; b < blockIdx.x; ++b) off += sf->blk_hist[b][r][d];
+    s_off[r] = off;
+  }
+  __syncthreads();
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t span = stride * kSelUnroll;
+  const int64_t n_round = ((n + span - 1) / span) * span;
+  double sum[kSelGroup];
+  unsigned long long cnt[kSelGroup];
+#pragma unroll
+  for (int r = 0; r < kSelGroup; ++r) {
+    sum[r] = 0.0;
+    cnt[r] = 0;
+  }
+  for (int64_t i0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i0 < n_round; i0 += span) {
+#pragma unroll 1
+    for (int u = 0; u < kSelUnroll; ++u) {
+      const bool in = i0 + u * stride < n;
+      const double vu = in ? ylt[i0 + u * stride] : 0.0;
+      const unsigned long long k = key_of(vu);
+      unsigned int bal[kSelGroup];
+#pragma unroll
+      for (int r = 0; r < kSelGroup; ++r) {
+        const bool match = r < g && in && (k & mask[r]) == prefix[r];
+        bal[r] = __ballot_sync(0xffffffffu, match);
+        if (r < g && in && k > top[r]) {
+          sum[r] += vu;
+          ++cnt[r];
+        }
+      }
+      if (lane == 0)
+#pragma unroll
+        for (int r = 0; r < kSelGroup; ++r) s_wcnt[warp][r] = __popc(bal[r]);
+      __syncthreads();
+      unsigned int total[kSelGroup];
+#pragma unroll
+      for (int r = 0; r < kSelGroup; ++r) {
+        // exclusive prefix of the warps' counts: lane w holds warp w's count
+        // (periods r >= g have none)
+        const unsigned int c = s_wcnt[lane][r];
+        unsigned int incl = c;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const unsigned int o = __shfl_up_sync(0xffffffffu, incl, dd);
+          if (lane >= static_cast<unsigned int>(dd)) incl += o;
+        }
+        const unsigned int before = __shfl_sync(0xffffffffu, incl - c, warp);
+        total[r] = __shfl_sync(0xffffffffu, incl, 31);
+        if ((bal[r] >> lane) & 1u)
+          cand[static_cast<size_t>(r) * n + s_off[r] + before + __popc(bal[r] & ((1u << lane) - 1u))] = k;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0)
+#pragma unroll
+        for (int r = 0; r < kSelGroup; ++r)
+          if (r < g) s_off[r] += total[r];
+      __syncthreads();
+    }
+  }
+  // the block's sums above the buckets, in a fixed order
+#pragma unroll
+  for (int r = 0; r < kSelGroup; ++r) {
+    for (int d = 16; d > 0; d >>= 1) {
+      sum[r] += __shfl_down_sync(0xffffffffu, sum[r], d);
+      cnt[r] += __shfl_down_sync(0xffffffffu, cnt[r], d);
+    }
+    if (lane == 0) {
+      s_sum[warp][r] = sum[r];
+      s_cnt[warp][r] = cnt[r];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < static_cast<unsigned int>(g)) {
+    const int r = threadIdx.x;
+    double t = 0.0;
+    unsigned long long c = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) {
+      t += s_sum[w][r];
+      c += s_cnt[w][r];
+    }
+    sf->above_sum[blockIdx.x][r] = t;
+    sf->above_cnt[blockIdx.x][r] = c;
+  }
+}
+
+// The fast path's finish, one block: per period, the remaining six digits of
+// the m-th key over the bucket's keys, then TVaR from the sums above the
+// bucket (the blocks' parts, a tree of fixed shape) and the bucket keys above
+// the m-th key (a fixed assignment of keys to threads and a fixed tree).
+__global__ void __launch_bounds__(kSelThreads) k_sel_finish(int64_t n, SelScratch* sc, const SelFast* sf, int g,
+                                                             int n_blk, const unsigned long long* cand, double* pml,
+                                                             double* tvar) {
+  __shared__ unsigned int s_hist[256];
+  __shared__ unsigned int s_warp[kSelThreads / 32];
+  __shared__ unsigned long long s_prefix, s_mask, s_want;
+  __shared__ unsigned int s_c;
+  __shared__ double s_ps[256];
+  __shared__ unsigned long long s_pc[256];
+  const unsigned int t = threadIdx.x, lane = t & 31;
+  for (int r = 0; r < g; ++r) {
+    if (t == 0) {
+      s_prefix = sc->st[r].prefix;
+      s_mask = sc->st[r].mask;
+      s_want = sc->st[r].want;
+      const unsigned int d = static_cast<unsigned int>(s_prefix >> 48) & 255u;
+      unsigned int c = 0;
+      for (int b = 0; b < n_blk; ++b) c += sf->blk_hist[b][r][d];
+      s_c = c;
+    }
+    __syncthreads();
+    const unsigned int C = s_c;
+    const unsigned long long* ck = cand + static_cast<size_t>(r) * n;
+    for (int shift = 40; shift >= 0; shift -= 8) {
+      if (t < 256) s_hist[t] = 0;
+      __syncthreads();
+      const unsigned long long prefix = s_prefix, mask = s_mask;
+      for (unsigned int j = t; j < C; j += kSelThreads) {
+        const unsigned long long k = ck[j];
+        if ((k & mask) == prefix) atomicAdd(&s_hist[(k >> shift) & 255u], 1u);
+      }
+      __syncthreads();
+      // the digit holding the wanted rank (suffix scan, thread t holding digit 255 - t)
+      const unsigned int c = (t < 256) ? s_hist[255 - t] : 0u;
+      unsigned int incl = c;
+#pragma unroll
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const unsigned int o = __shfl_up_sync(0xffffffffu, incl, dd);
+        if (lane >= static_cast<unsigned int>(dd)) incl += o;
+      }
+      if (lane == 31) s_warp[t >> 5] = incl;
+      __syncthreads();
+      unsigned int before = 0;
+      for (unsigned int w = 0; w < (t >> 5); ++w) before += s_warp[w];
+      incl += before;
+      const unsigned long long want = s_want;
+      const bool reach = t < 256 && static_cast<unsigned long long>(incl) >= want &&
+                         (t == 0 || static_cast<unsigned long long>(incl - c) < want);
+      __syncthreads();
+      if (reach || (t == 255 && static_cast<unsigned long long>(incl) < want)) {
+        s_want = want - (incl - c);
+        s_prefix = prefix | (static_cast<unsigned long long>(255 - t) << shift);
+        s_mask = mask | (255ull << shift);
+      }
+      __syncthreads();
+    }
+    const unsigned long long kth = s_prefix;
+    // bucket keys above the m-th key
+    double sum = 0.0;
+    unsigned long long cnt = 0;
+    for (unsigned int j = t; j < C; j += kSelThreads) {
+      const unsigned long long k = ck[j];
+      if (k > kth) {
+        sum += value_of(k);
+        ++cnt;
+      }
+    }
+    for (int d = 16; d > 0; d >>= 1) {
+      sum += __shfl_down_sync(0xffffffffu, sum, d);
+      cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+    }
+    if (lane == 0) {
+      s_ps[t >> 5] = sum;
+      s_pc[t >> 5] = cnt;
+    }
+    __syncthreads();
+    double bucket_sum = 0.0;
+    unsigned long long bucket_cnt = 0;
+    if (t == 0) {
+      for (int w = 0; w < kSelThreads / 32; ++w) {
+        bucket_sum += s_ps[w];
+        bucket_cnt += s_pc[w];
+      }
+    }
+    __syncthreads();
+    // the blocks' parts above the bucket
+    if (t < 256) {
+      s_ps[t] = (static_cast<int>(t) < n_blk) ? sf->above_sum[t][r] : 0.0;
+      s_pc[t] = (static_cast<int>(t) < n_blk) ? sf->above_cnt[t][r] : 0ull;
+    }
+    __syncthreads();
+    for (unsigned int half = 128; half > 0; half >>= 1) {
+      if (t < half) {
+        s_ps[t] += s_ps[t + half];
+        s_pc[t] += s_pc[t + half];
+      }
+      __syncthreads();
+    }
+    if (t == 0) {
+      const double v = value_of(kth);
+      const unsigned long long m = sc->st[r].m;
+      const double s_all = s_ps[0] + bucket_sum;
+      const unsigned long long c_all = s_pc[0] + bucket_cnt;
+      pml[r] = v;
+      tvar[r] = (s_all + static_cast<double>(m - c_all) * v) / static_cast<double>(m);
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
-size_t select_scratch_bytes(int64_t /*n*/) { return sizeof(SelScratch) + 64; }
+size_t select_scratch_bytes(int64_t n) {
+  return kSelStateBytes + kSelFastBytes + sizeof(unsigned long long) * kSelGroup * static_cast<size_t>(n) + 64;
+}
 
 cudaError_t pml_tvar_device(const double* ylt, int64_t n, const double* rps_host, int32_t n_rp, double* pml,
-                            double* tvar, void* scratch, cudaStream_t s, int* n_launch) {
+                            double* tvar, void* scratch, size_t scratch_bytes, cudaStream_t s, int* n_launch) {
   SelScratch* sc = static_cast<SelScratch*>(scratch);
+  const bool fast = scratch_bytes >= select_scratch_bytes(n);
+  SelFast* sf = fast ? reinterpret_cast<SelFast*>(static_cast<unsigned char*>(scratch) + kSelStateBytes) : nullptr;
+  unsigned long long* cand =
+      fast ? reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(scratch) + kSelStateBytes + kSelFastBytes)
+           : nullptr;
   const int64_t blocks = (n + kSelThreads - 1) / kSelThreads;
   const int grid = static_cast<int>(blocks < kSelBlocks ? blocks : kSelBlocks);
   for (int32_t r0 = 0; r0 < n_rp; r0 += kSelGroup) {
@@ -272,9 +521,18 @@ cudaError_t pml_tvar_device(const double* ylt, int64_t n, const double* rps_host
       ms.m[r] = static_cast<unsigned long long>(m);
     }
     k_sel_init<<<1, 256, 0, s>>>(sc, ms, g);
-    for (int shift = 56; shift >= 0; shift -= 8) k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, shift);
-    k_sel_tail<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, pml + r0, tvar + r0);
-    if (n_launch) *n_launch += 10;
+    if (fast) {
+      k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, 56, nullptr);
+      k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, 48, &sf->blk_hist[0][0][0]);
+      k_sel_compact<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, sf, g, cand);
+      k_sel_finish<<<1, kSelThreads, 0, s>>>(n, sc, sf, g, grid, cand, pml + r0, tvar + r0);
+      if (n_launch) *n_launch += 5;
+    } else {
+      for (int shift = 56; shift >= 0; shift -= 8)
+        k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, shift, nullptr);
+      k_sel_tail<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, pml + r0, tvar + r0);
+      if (n_launch) *n_launch += 10;
+    }
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
@@ -442,7 +700,8 @@ extern "C" ARA_API int ara_pml_tvar_noalloc(const double* ylt, int64_t n, const 
   double* d_pml = pml_dev ? pml_out : d_out;
   double* d_tvar = tvar_dev ? tvar_out : d_out + ARA_NOALLOC_MAX_RP;
   // the select kernels reset their own histogram and state on every call
-  if (ara::pml_tvar_device(ylt, n, return_periods, n_rp, d_pml, d_tvar, state, s, nullptr) != cudaSuccess)
+  if (ara::pml_tvar_device(ylt, n, return_periods, n_rp, d_pml, d_tvar, state, sizeof(ara::SelScratch), s, nullptr) !=
+      cudaSuccess)
     return ARA_ECUDA;
   if (!pml_dev && cudaMemcpyAsync(pml_out, d_pml, sizeof(double) * n_rp, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return ARA_ECUDA;
