@@ -98,6 +98,16 @@ def test_event_rows_halley_path_subrange_and_primary_only(eng, world):
     check_rows(n_rows, ylt, got, ref, oracle.run_layer(yet, sub, terms, seed=4, primary_only=True, trials=trials), t0)
 
 
+def test_event_rows_aggregate_terms_beyond_fp32(eng, world):
+    # an aggregate limit beyond the FP32 range: the running sums in FP64
+    yet, pool, ids, sub, terms = world
+    _load(eng, yet, pool)
+    big = (terms[0], terms[1], terms[2], 1e300)
+    n_rows, ylt, got = _run(eng, ids, big, 3, 0, yet.n_trials)
+    ref = oracle.run_layer_events(yet, sub, big, seed=3)
+    check_rows(n_rows, ylt, got, ref, oracle.run_layer(yet, sub, big, seed=3), 0)
+
+
 def test_event_rows_empty_and_long_trials(eng):
     rng = np.random.default_rng(811)
     C = 2003
