@@ -71,6 +71,7 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 LAYER_SOURCES = ("ara_layer.cu", "ara_device_math.cuh", "ara_internal.h")  # what k_gather and k_losses compile from
 
 
@@ -163,13 +164,13 @@ def _algorithmic_bytes(offsets_span: int, n_events: int, n_trials: int, n_record
 
 
 # ------------------------------------------------------------------ CPU legs (oracle)
-def _oracle_leg(yet, pool, terms, seed, sample_trials: int):
+def _oracle_leg(yet, pool, terms, seed, sample_trials: int, threads: int = 0):
     import oracle
 
     trials = np.arange(sample_trials, dtype=np.int64)
     evals = int(yet.offsets[sample_trials] - yet.offsets[0]) * pool.n_elts
     t = time.perf_counter()
-    oracle.run_layer(yet, pool, terms, seed=seed, trials=trials)
+    oracle.run_layer(yet, pool, terms, seed=seed, trials=trials, threads=threads)
     dt = time.perf_counter() - t
     return evals / dt, dt, evals
 
@@ -301,6 +302,7 @@ def run_gpu(args):
     peak, peak_kind = _peaks()
     achieved = algo / (kernel_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                 "traffic": _profiled_traffic(), "kernel": "k_gather+k_losses", "kernel_ms": kernel_ms,
                 "gather_ms": tm["gather_ms"] / calls, "losses_ms": tm["losses_ms"] / calls,
                 "algorithmic_bytes": algo, "peak_source": f"hbm_gbs of {peak_kind}"}
@@ -345,8 +347,11 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu:
         yet_view = synth.YET(offsets=offsets, event_ids=ids_host.numpy(), catalogue_size=spec["catalogue"])
         v, dt, ev = _oracle_leg(yet_view, pool, terms, seed, min(args.cpu_trials, n_trials))
+        n1 = min(args.cpu_trials // 50, n_trials)
+        v1, dt1, ev1 = _oracle_leg(yet_view, pool, terms, seed, n1, threads=1)
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
-               "sample": f"first {min(args.cpu_trials, n_trials)} trials of the workload ({ev} evals, {dt:.1f} s)"}
+               "sample": f"first {min(args.cpu_trials, n_trials)} trials of the workload ({ev} evals, {dt:.1f} s)",
+               "single_core": {"value": v1, "sample": f"first {n1} trials ({ev1} evals, {dt1:.1f} s, 1 thread)"}}
 
     # ---- two-part secondary uncertainty (correlated sigma) on the same layer; the plain
     # layer pass is timed here too, on the same stream, for the comparison

@@ -369,14 +369,15 @@ int or_run_layer(int64_t n_trials, const int64_t *offsets, const int32_t *ids, i
             row_of[j * (int64_t)catalogue + ev] = (int32_t)e;
         }
     n_eval = trials ? n_list : n_trials;
-#ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#else
-    (void)n_threads;
-#endif
     {
         int64_t i;
-#pragma omp parallel for schedule(dynamic, 16)
+#ifdef _OPENMP
+        /* n_threads > 0: that many threads for this call only */
+        const int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+#else
+        (void)n_threads;
+#endif
         for (i = 0; i < n_eval; ++i) {
             int64_t t = trials ? trials[i] : i;
             int64_t first = offsets[t], last = offsets[t + 1], pos;

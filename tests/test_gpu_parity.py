@@ -97,6 +97,16 @@ def test_inverse_beta_records(eng, recipe, newton_only):
     assert (iters >= 0).all()
     # each loss within 1e-5 of itself or, for losses far below the mean, 1e-6 of the mean
     assert np.all(err <= 1e-5 * want + 1e-6 * mu)
+    # the error by (alpha, beta) bucket (decades of each shape)
+    scaled = err / (want + 0.1 * mu)
+    la, lb = np.floor(np.log10(shapes[:, 0])), np.floor(np.log10(shapes[:, 1]))
+    rows = []
+    for a in np.unique(la):
+        for b in np.unique(lb):
+            sel = (la == a) & (lb == b)
+            if sel.sum() >= 20:
+                rows.append(f"a~1e{int(a)} b~1e{int(b)}: n {sel.sum()} max {scaled[sel].max():.1e}")
+    print("  by (alpha, beta) decade, max err / (loss + mean/10): " + "; ".join(rows))
 
 
 @pytest.mark.parametrize("newton_only", [False, True], ids=["table", "newton"])
@@ -254,6 +264,15 @@ def test_pml_tvar_and_sort(eng, n):
 
 
 # ------------------------------------------------------------------ full size (sampled)
+def _report_plain_relative(ylt, ref, terms):
+    # the plain relative error over trials well above the aggregate retention's kink
+    sel = ref["ylt"] > 1e-3 * terms[3]
+    if sel.any():
+        rel = np.abs(ylt[sel] - ref["ylt"][sel]) / ref["ylt"][sel]
+        print(f"  plain relative error over {sel.sum()} trials with Y > 1e-3 AggL: max {rel.max():.2e}, "
+              f"median {np.median(rel):.2e}")
+
+
 def test_paper_1m_layer_sampled_parity(eng):
     """The 1M-trial x Poisson(1000) x 15-ELT layer in the benchmark's launch
     configuration; the oracle evaluates every 997th trial."""
@@ -276,7 +295,38 @@ def test_paper_1m_layer_sampled_parity(eng):
     assert np.array_equal(hits[sample], ref["hits"]) and np.array_equal(hh[sample], ref["hit_hash"])
     worst = check_ylt(ylt[sample], ref)
     print(f"\npaper-1m sampled worst scaled error {worst:.3e}, pairs {st['n_pairs_hit']}")
+    _report_plain_relative(ylt[sample], ref, terms)
     # PML / TVaR of the full GPU YLT against the oracle's order statistics of the same YLT
     pml, tvar = eng.pml_tvar(ylt, spec["return_periods"])
     rpml, rtvar = oracle.pml_tvar(ylt, spec["return_periods"])
     assert np.array_equal(pml, rpml) and np.allclose(tvar, rtvar, rtol=1e-12)
+
+
+def test_stress_1m_layer_sampled_parity(eng):
+    """The precision-stress layer: the paper-1m YET and 15 ELTs x 10,000 records with
+    Beta shapes log-uniform over [0.2, 50]; the oracle evaluates every 997th trial.
+    Per-trial error statistics, and PML/TVaR of the sampled trials against the
+    oracle's."""
+    import json
+    import os
+
+    yet, pool, spec = synth.workload("stress-1m")
+    with open(os.path.join(os.path.dirname(__file__), "golden", "workload_terms.json")) as fh:
+        terms = json.load(fh)["stress-1m"]["layer_terms"]
+    eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
+    eng.load_pool(pool)
+    ylt = np.zeros(yet.n_trials)
+    eng.run_layer(pool.elt_ids, terms, 0, 0, yet.n_trials, ylt)
+    assert eng.stats()["n_nonconverged"] == 0
+    sample = np.arange(0, yet.n_trials, 997)
+    ref = oracle.run_layer(yet, pool, terms, seed=0, trials=sample)
+    worst = check_ylt(ylt[sample], ref)
+    scale = np.maximum(np.abs(ref["ylt"]), ref["gross"])
+    scaled = np.abs(ylt[sample] - ref["ylt"]) / np.where(scale > 0, scale, 1.0)
+    print(f"\nstress-1m sampled scaled error: max {worst:.3e}, median {np.median(scaled):.3e}")
+    _report_plain_relative(ylt[sample], ref, terms)
+    pml, tvar = eng.pml_tvar(ylt[sample].copy(), spec["return_periods"])
+    rpml, rtvar = oracle.pml_tvar(ref["ylt"], spec["return_periods"])
+    print(f"  PML/TVaR of the sample: rel err {np.max(np.abs(pml - rpml) / rpml):.2e} / "
+          f"{np.max(np.abs(tvar - rtvar) / rtvar):.2e}")
+    assert np.allclose(pml, rpml, rtol=1e-4) and np.allclose(tvar, rtvar, rtol=1e-4)
