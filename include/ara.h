@@ -65,6 +65,13 @@ extern "C" {
 /* Layer flags */
 #define ARA_PRIMARY_ONLY 1u /* no secondary uncertainty: every record's loss is its mean */
 #define ARA_NEWTON_ONLY 2u  /* invert every Beta by the FP32 Halley iteration, not the record's quantile table */
+/* The uniform z_(Prog,E) per event occurrence, shared by the layer's ELTs
+ * (Section 3.1 keys it by the YET entry): every pair of an occurrence draws
+ * word 0 of the Philox block with the ELT word of the counter set to
+ * 0xFFFFFFFE (no pool id takes it) in place of its ELT pool id, which also
+ * stands for the pool id in the hit hash of ara_run_layer_diag.  Without it,
+ * each (trial, event index, ELT pool id) has its own draw. */
+#define ARA_SHARED_Z 4u
 
 typedef struct ara_ctx ara_ctx;
 
@@ -89,7 +96,7 @@ typedef struct {
     double occ_limit;
     double agg_retention;
     double agg_limit;
-    uint32_t flags; /* ARA_PRIMARY_ONLY, ARA_NEWTON_ONLY or 0 */
+    uint32_t flags; /* ARA_PRIMARY_ONLY, ARA_NEWTON_ONLY, ARA_SHARED_Z, or 0 */
 } ara_layer;
 
 /* Optional per-trial diagnostics of ara_run_layer_diag(); any pointer may be

@@ -187,12 +187,19 @@ def beta_params(mu: float, sigma: float, max_l: float):
 
 
 # ---------------------------------------------------------------- ARA
-def _elt_arrays(pool):
+# The ELT word of the Philox counter that every ELT of an occurrence shares
+# when z_(Prog,E) is one draw per YET entry (Section 3.1): 0xFFFFFFFE.
+SHARED_Z_WORD = -2
+
+
+def _elt_arrays(pool, shared_z: bool = False):
     """The pool's arrays in the oracle's argument order (sigma_c: None when the
-    records carry no correlated standard deviation)."""
+    records carry no correlated standard deviation).  ``shared_z``: every ELT
+    keys its uniforms (and the hit hash) by SHARED_Z_WORD instead of its pool id."""
     sc = getattr(pool, "sigma_c", None)
+    ids = np.full(pool.n_elts, SHARED_Z_WORD, np.int32) if shared_z else _c(pool.elt_ids, np.int32)
     return [
-        _c(pool.elt_ids, np.int32), _c(pool.rec_offsets, np.int64), _c(pool.event_ids, np.int32),
+        ids, _c(pool.rec_offsets, np.int64), _c(pool.event_ids, np.int32),
         _c(pool.mean, np.float32), _c(pool.sigma, np.float32), None if sc is None else _c(sc, np.float32),
         _c(pool.exposure, np.float32), _c(pool.terms, np.float32),
     ]
@@ -229,7 +236,7 @@ def combined_normal_batch(seed: int, trials, ks, elts, sigma_i: float, sigma_c: 
 
 
 def run_layer(yet, pool, layer_terms, seed: int = 0, primary_only: bool = False,
-              trials=None, threads: int = 0):
+              trials=None, threads: int = 0, shared_z: bool = False):
     """Algorithm 1 with secondary uncertainty over one layer (Sections 2.2, 3.3).
 
     ``pool`` holds exactly the layer's ELTs (an ``ELTPool``); ``layer_terms``
@@ -247,7 +254,7 @@ def run_layer(yet, pool, layer_terms, seed: int = 0, primary_only: bool = False,
     gross = np.zeros(n, np.float64)
     hits = np.zeros(n, np.int64)
     hh = np.zeros(n, np.uint64)
-    arrs = _elt_arrays(pool)
+    arrs = _elt_arrays(pool, shared_z)
     occ_r, occ_l, agg_r, agg_l = (float(v) for v in layer_terms)
     rc = lib.or_run_layer(
         yet.n_trials, _p(offs), _p(ids), int(yet.catalogue_size),
@@ -279,7 +286,7 @@ def event_losses(yet, pool, seed=0, primary_only=True, t_begin=0, t_end=None):
     return out[:n]
 
 
-def run_layer_events(yet, pool, layer_terms, seed=0, primary_only=False, t_begin=0, t_end=None):
+def run_layer_events(yet, pool, layer_terms, seed=0, primary_only=False, t_begin=0, t_end=None, shared_z=False):
     """Per-event output of a layer over trials [t_begin, t_end): one row per event
     occurrence held by at least one of the layer's ELTs, in (trial, k) order, as a
     dict of arrays ``trial, k, event, occ`` (O_k after occurrence terms) and ``inc``
@@ -293,7 +300,7 @@ def run_layer_events(yet, pool, layer_terms, seed=0, primary_only=False, t_begin
             "occ": np.zeros(cap, np.float64), "inc": np.zeros(cap, np.float64)}
     max_occ = np.zeros(max(t_end - t_begin, 1), np.float64)
     occ_r, occ_l, agg_r, agg_l = (float(v) for v in layer_terms)
-    arrs = _elt_arrays(pool)
+    arrs = _elt_arrays(pool, shared_z)
     n = lib.or_run_layer_events(
         _p(offs), _p(ids), int(yet.catalogue_size), pool.n_elts, *[_p(a) if a is not None else None for a in arrs],
         occ_r, occ_l, agg_r, agg_l, int(seed), int(bool(primary_only)), int(t_begin), int(t_end),

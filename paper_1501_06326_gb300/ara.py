@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(_HERE, "libara.so")
 ARA_OK, ARA_EINVAL, ARA_ENOMEM, ARA_ENOTLOADED, ARA_ECUDA, ARA_ETIMEOUT, ARA_EAGAIN = 0, -1, -2, -3, -4, -5, -6
 ARA_PRIMARY_ONLY = 1
 ARA_NEWTON_ONLY = 2
+ARA_SHARED_Z = 4
 ARA_MAX_LAYER_ELTS = 32
 ARA_MAX_BATCH_LAYERS = 32
 ARA_MAX_BATCH_ELTS = 64
@@ -364,17 +365,20 @@ class Ara:
                            pool.terms)
 
     @staticmethod
-    def make_layer(elt_ids: Sequence[int], layer_terms, primary_only: bool = False, newton_only: bool = False):
+    def make_layer(elt_ids: Sequence[int], layer_terms, primary_only: bool = False, newton_only: bool = False,
+                   shared_z: bool = False):
         ids = (ctypes.c_int32 * len(elt_ids))(*[int(i) for i in elt_ids])
         occ_r, occ_l, agg_r, agg_l = (float(v) for v in layer_terms)
-        flags = (ARA_PRIMARY_ONLY if primary_only else 0) | (ARA_NEWTON_ONLY if newton_only else 0)
+        flags = ((ARA_PRIMARY_ONLY if primary_only else 0) | (ARA_NEWTON_ONLY if newton_only else 0)
+                 | (ARA_SHARED_Z if shared_z else 0))
         lay = Layer(len(elt_ids), ids, occ_r, occ_l, agg_r, agg_l, flags)
         lay._ids = ids  # keep the id array alive with the struct
         return lay
 
     def run_layer(self, elt_ids, layer_terms, seed: int, trial_begin: int, trial_end: int, ylt_out,
-                  primary_only: bool = False, hits_out=None, hash_out=None, newton_only: bool = False) -> None:
-        lay = self.make_layer(elt_ids, layer_terms, primary_only, newton_only)
+                  primary_only: bool = False, hits_out=None, hash_out=None, newton_only: bool = False,
+                  shared_z: bool = False) -> None:
+        lay = self.make_layer(elt_ids, layer_terms, primary_only, newton_only, shared_z)
         if hits_out is None and hash_out is None:
             self._check(ara_run_layer(self._h, lay, seed, trial_begin, trial_end, ylt_out))
         else:
@@ -384,11 +388,11 @@ class Ara:
     def run_layer_events(self, elt_ids, layer_terms, seed: int, trial_begin: int, trial_end: int, ylt_out,
                          trial=None, event_index=None, event_id=None, occ_loss=None, agg_inc=None, max_occ=None,
                          capacity: Optional[int] = None, primary_only: bool = False,
-                         newton_only: bool = False) -> int:
+                         newton_only: bool = False, shared_z: bool = False) -> int:
         """ara_run_layer plus the per-event rows (any array may be None); returns
         the number of rows of the trial range (rows beyond ``capacity`` -- by
         default the length of the given row arrays -- are not written)."""
-        lay = self.make_layer(elt_ids, layer_terms, primary_only, newton_only)
+        lay = self.make_layer(elt_ids, layer_terms, primary_only, newton_only, shared_z)
         arrs = [(trial, np.int64), (event_index, np.int32), (event_id, np.int32), (occ_loss, np.float64),
                 (agg_inc, np.float64)]
         if capacity is None:
@@ -399,17 +403,17 @@ class Ara:
         return int(rows.n_rows)
 
     def run_layers(self, layers, seed: int, trial_begin: int, trial_end: int, ylt_out,
-                   primary_only: bool = False, newton_only: bool = False) -> None:
+                   primary_only: bool = False, newton_only: bool = False, shared_z: bool = False) -> None:
         """Several layers in one pass.  ``layers``: a sequence of (elt_ids, layer_terms);
         ``ylt_out``: (n_layers, trial_end - trial_begin) float64, C order."""
-        made = [self.make_layer(ids, terms, primary_only, newton_only) for ids, terms in layers]
+        made = [self.make_layer(ids, terms, primary_only, newton_only, shared_z) for ids, terms in layers]
         arr = (Layer * len(made))(*made)
         self._check(ara_run_layers(self._h, len(made), arr, seed, trial_begin, trial_end, ylt_out))
 
     def submit(self, elt_ids, layer_terms, seed: int, trial_end: int, return_periods,
-               primary_only: bool = False) -> int:
+               primary_only: bool = False, shared_z: bool = False) -> int:
         """Queue a serving request; returns its ticket."""
-        lay = self.make_layer(elt_ids, layer_terms, primary_only)
+        lay = self.make_layer(elt_ids, layer_terms, primary_only, shared_z=shared_z)
         rps = np.ascontiguousarray(return_periods, dtype=np.float64)
         tk = np.zeros(1, np.int64)
         self._check(ara_submit(self._h, lay, seed, trial_end, rps, rps.shape[0], tk))

@@ -508,6 +508,12 @@ static int check_layer(ara_ctx* c, const ara_layer* L, const char* who, std::vec
   return ARA_OK;
 }
 
+// The ELT word of a pair's Philox counter: its pool id, or the word every
+// ELT of an occurrence shares under ARA_SHARED_Z.
+static int32_t philox_elt_word(int32_t pool_id, uint32_t flags) {
+  return (flags & ARA_SHARED_Z) ? static_cast<int32_t>(0xFFFFFFFEu) : pool_id;
+}
+
 // Index buffers for the ELTs `ids` (ascending pool ids, at most
 // kMaxIndexElts) and the gather over [t0, t1).
 static int plan_pass(ara_ctx* c, const std::vector<int32_t>& ids, int64_t t0, int64_t t1, const char* who,
@@ -712,7 +718,7 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   ara::LossParams p{};
   for (size_t i = 0; i < ids.size(); ++i) {
     const Elt& el = c->pool.find(ids[i])->second;
-    p.elt_id[i] = ids[i];
+    p.elt_id[i] = philox_elt_word(ids[i], L->flags);
     p.tab[i] = static_cast<const float4*>(el.tab.ptr);
     p.tabf[i] = static_cast<const float4*>(el.tabf.ptr);
     p.t_ret[i] = el.terms.retention;
@@ -834,7 +840,7 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
   std::vector<float> gmax(n_layers, 0.0f);
   for (size_t i = 0; i < uni.size(); ++i) {
     const Elt& el = c->pool.find(uni[i])->second;
-    p.elt_id[i] = uni[i];
+    p.elt_id[i] = philox_elt_word(uni[i], layers[0].flags);
     p.tab[i] = static_cast<const float4*>(el.tab.ptr);
     p.tabf[i] = static_cast<const float4*>(el.tabf.ptr);
     p.t_ret[i] = el.terms.retention;

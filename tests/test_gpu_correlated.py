@@ -216,3 +216,52 @@ def test_load_xelts_errors(eng, world):
     with pytest.raises(ara.AraError) as e:
         eng.load_xelts(sub.elt_ids, sub.rec_offsets, sub.event_ids, sub.mean, sub.sigma, None, sub.exposure)
     assert e.value.code == ara.ARA_EINVAL
+
+
+def test_shared_z_single_batched_and_doubling(eng, world):
+    # ARA_SHARED_Z: one z_(Prog,E) per occurrence for every ELT of the layer
+    yet, pool = world
+    _load(eng, yet, pool)
+    ids = LAYERS[2]
+    sub = pool.subset(ids)
+    terms = oracle.calibrate_layer_terms(yet, sub)
+    out = np.zeros(yet.n_trials)
+    hits = np.zeros(yet.n_trials, np.int64)
+    hh = np.zeros(yet.n_trials, np.uint64)
+    eng.run_layer(ids, terms, 6, 0, yet.n_trials, out, shared_z=True, hits_out=hits, hash_out=hh)
+    ref = oracle.run_layer(yet, sub, terms, seed=6, shared_z=True)
+    check_ylt(out, ref)
+    assert np.array_equal(hits, ref["hits"]) and np.array_equal(hh, ref["hit_hash"])
+    layers = [(LAYERS[0], terms), (LAYERS[1], terms), (ids, terms)]
+    outb = np.zeros((3, yet.n_trials))
+    eng.run_layers(layers, 6, 0, yet.n_trials, outb, shared_z=True)
+    for l, (lids, _) in enumerate(layers):
+        check_ylt(outb[l], oracle.run_layer(yet, pool.subset(lids), terms, seed=6, shared_z=True))
+    # two ELTs with identical records: every occurrence's loss doubles
+    one = synth.make_elt_pool(1, 800, yet.catalogue_size, 651)
+    cat = lambda a: np.concatenate([a, a])
+    two = synth.ELTPool(np.array([0, 1], np.int32), np.array([0, 800, 1600], np.int64), cat(one.event_ids),
+                        cat(one.mean), cat(one.sigma), cat(one.exposure), np.tile(one.terms, (2, 1)))
+    ident = (0.0, math.inf, 0.0, math.inf)
+    _load(eng, yet, two)
+    y2, y1 = np.zeros(yet.n_trials), np.zeros(yet.n_trials)
+    eng.run_layer([0, 1], ident, 2, 0, yet.n_trials, y2, shared_z=True)
+    eng.run_layer([0], ident, 2, 0, yet.n_trials, y1, shared_z=True)
+    assert np.allclose(y2, 2.0 * y1, rtol=1e-6, atol=0.0)
+    check_ylt(y2, oracle.run_layer(yet, two, ident, seed=2, shared_z=True))
+
+
+def test_shared_z_event_rows(eng, world):
+    yet, pool = world
+    _load(eng, yet, pool)
+    ids = LAYERS[1]
+    sub = pool.subset(ids)
+    terms = oracle.calibrate_layer_terms(yet, sub)
+    cap = 1 << 20
+    trial, occ = np.zeros(cap, np.int64), np.zeros(cap)
+    ylt = np.zeros(yet.n_trials)
+    n = eng.run_layer_events(ids, terms, 8, 0, yet.n_trials, ylt, trial=trial, occ_loss=occ, shared_z=True)
+    ref = oracle.run_layer_events(yet, sub, terms, seed=8, shared_z=True)
+    assert n == len(ref["trial"]) and np.array_equal(trial[:n], ref["trial"])
+    gross = oracle.run_layer(yet, sub, terms, seed=8, shared_z=True)["gross"]
+    assert np.all(np.abs(occ[:n] - ref["occ"]) <= YLT_TOL * gross[ref["trial"]])

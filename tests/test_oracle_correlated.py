@@ -135,3 +135,27 @@ def test_correlated_record_loss_against_library_routines(s_i, s_c):
     x = np.where(v <= 0.0, special.betaincinv(a, b, special.ndtr(v)), special.betainccinv(a, b, special.ndtr(-v)))
     assert np.sum(v > 0.0) > n // 3 and np.sum(v < 0.0) > n // 3
     assert np.allclose(got, 4000.0 * x, rtol=1e-9, atol=0.0)
+
+
+def test_shared_z_keys_every_elt_by_the_occurrence():
+    # Beta(1,1) records (mu/max = 1/2, sigma^2/max^2 = 1/12) have Loss = max z: with one
+    # event per trial the year loss is max z, and z is the occurrence's shared draw
+    n, seed = 200, 9
+    max_l = 1000.0
+    yet = synth.YET(np.arange(n + 1, dtype=np.int64), np.full(n, 2, np.int32), 4)
+    pool = synth.ELTPool(np.array([3, 8], np.int32), np.array([0, 1, 2], np.int64), np.array([2, 2], np.int32),
+                         np.full(2, 500.0, np.float32), np.full(2, max_l / math.sqrt(12.0), np.float32),
+                         np.full(2, max_l, np.float32), np.tile(np.array([0.0, np.inf, 1.0], np.float32), (2, 1)))
+    terms = (0.0, math.inf, 0.0, math.inf)
+    z = oracle.uniform_batch(seed, np.arange(n, dtype=np.int64), np.zeros(n, np.int32),
+                             np.full(n, oracle.SHARED_Z_WORD, np.int32))
+    one = oracle.run_layer(yet, pool.subset([0]), terms, seed=seed, shared_z=True)["ylt"]
+    assert np.allclose(one, max_l * z, rtol=1e-6, atol=0.0)  # shapes 1 up to the FP32 sigma
+    # both ELTs draw the same z: the year loss doubles exactly; without the flag it does not
+    two = oracle.run_layer(yet, pool, terms, seed=seed, shared_z=True)["ylt"]
+    assert np.array_equal(two, 2.0 * one)
+    indep = oracle.run_layer(yet, pool, terms, seed=seed)["ylt"]
+    assert not np.allclose(indep, two, rtol=1e-3)
+    # the shared word is outside the pool-id range and apart from the occurrence stream of sigma_C
+    assert oracle.SHARED_Z_WORD < 0
+    assert oracle.uniform(seed, 5, 0, oracle.SHARED_Z_WORD) != oracle.uniform_event(seed, 5, 0)
