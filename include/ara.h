@@ -49,7 +49,7 @@ extern "C" {
 #define ARA_ENOMEM (-2)     /* device allocation failed or over the HBM budget */
 #define ARA_ENOTLOADED (-3) /* the YET or a referenced ELT is not loaded */
 #define ARA_ECUDA (-4)      /* a CUDA runtime call failed */
-#define ARA_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define ARA_ETIMEOUT (-5)   /* a bounded wait gave up (ara_wait) */
 #define ARA_EAGAIN (-6)     /* a served request has not finished yet */
 
 /* Largest number of ELTs in one layer.  The paper's layers cover 3 to 30
@@ -288,12 +288,18 @@ ARA_API int ara_run_layers(ara_ctx *ctx, int32_t n_layers, const ara_layer *laye
  * ara_poll returns ARA_EAGAIN while the request is queued; once finished, it
  * copies its PML and TVaR (n_rp doubles each, host memory) and releases the
  * ticket, returning the request's own status (ARA_OK, or the error its batch
- * met).  Errors: ARA_EINVAL (unknown ticket). */
+ * met).  Errors: ARA_EINVAL (unknown ticket).
+ *
+ * ara_wait runs serve steps until the request is finished, then returns as
+ * ara_poll does; it returns ARA_ETIMEOUT, with the request still queued,
+ * when timeout_ns (nanoseconds of host time, 0: no limit) has passed at the
+ * end of a step.  A step that has started runs to its end. */
 #define ARA_SERVE_MAX_RP 16
 ARA_API int ara_submit(ara_ctx *ctx, const ara_layer *layer, uint64_t seed, int64_t trial_end,
                const double *return_periods, int32_t n_rp, int64_t *ticket);
 ARA_API int ara_serve_step(ara_ctx *ctx, int32_t *n_done);
 ARA_API int ara_poll(ara_ctx *ctx, int64_t ticket, double *pml_out, double *tvar_out);
+ARA_API int ara_wait(ara_ctx *ctx, int64_t ticket, double *pml_out, double *tvar_out, uint64_t timeout_ns);
 
 /* PML and TVaR of a YLT (Section 2.3) at n_rp return periods (each >= 1):
  * with m = ceil(n / RP), PML is the m-th largest year loss and TVaR the mean

@@ -42,7 +42,7 @@ EXPORTED = (
     "ara_run_layer_diag", "ara_pml_tvar", "ara_sort_ylt", "ara_debug_uniforms",
     "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
     "ara_pml_tvar_noalloc", "ara_run_layers", "ara_submit", "ara_serve_step", "ara_poll", "ara_load_xelts",
-    "ara_run_layer_events",
+    "ara_run_layer_events", "ara_wait",
 )
 ARA_NOALLOC_MAX_RP = 64
 
@@ -145,6 +145,7 @@ def load_library(path: str = LIB_PATH):
     lib.ara_submit.argtypes = [P, ctypes.POINTER(Layer), u64, i64, P, i32, P]
     lib.ara_serve_step.argtypes = [P, P]
     lib.ara_poll.argtypes = [P, i64, P, P]
+    lib.ara_wait.argtypes = [P, i64, P, P, u64]
     lib.ara_pml_tvar.argtypes = [P, P, i64, P, i32, P, P]
     lib.ara_sort_ylt.argtypes = [P, P, i64, P]
     lib.ara_debug_uniforms.argtypes = [P, u64, i64, P, P, P, P]
@@ -256,6 +257,11 @@ def ara_serve_step(h, n_done_out):
 
 def ara_poll(h, ticket, pml_out, tvar_out):
     return load_library().ara_poll(h, int(ticket), _ptr(pml_out, np.float64), _ptr(tvar_out, np.float64))
+
+
+def ara_wait(h, ticket, pml_out, tvar_out, timeout_ns=0):
+    return load_library().ara_wait(h, int(ticket), _ptr(pml_out, np.float64), _ptr(tvar_out, np.float64),
+                                   int(timeout_ns))
 
 
 def ara_pml_tvar(h, ylt, n, return_periods, n_rp, pml_out, tvar_out):
@@ -432,6 +438,13 @@ class Ara:
         if rc == ARA_EAGAIN:
             return None
         self._check(rc)
+        return pml, tvar
+
+    def wait(self, ticket: int, n_rp: int, timeout_ns: int = 0):
+        """Serve until the request is finished; its (pml, tvar).  Raises AraError
+        (code ARA_ETIMEOUT) when timeout_ns passes first."""
+        pml, tvar = np.zeros(n_rp), np.zeros(n_rp)
+        self._check(ara_wait(self._h, ticket, pml, tvar, timeout_ns))
         return pml, tvar
 
     def pml_tvar(self, ylt, return_periods, pml_out=None, tvar_out=None):

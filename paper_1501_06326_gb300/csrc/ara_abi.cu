@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1112,6 +1113,26 @@ int ara_poll(ara_ctx* c, int64_t ticket, double* pml_out, double* tvar_out) {
   }
   c->serve_reqs.erase(it);
   return status;
+}
+
+int ara_wait(ara_ctx* c, int64_t ticket, double* pml_out, double* tvar_out, uint64_t timeout_ns) {
+  int rc = bind(c);
+  if (rc) return rc;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    rc = ara_poll(c, ticket, pml_out, tvar_out);
+    if (rc != ARA_EAGAIN) return rc;
+    if (timeout_ns) {
+      const auto dt = std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0);
+      if (static_cast<uint64_t>(dt.count()) >= timeout_ns)
+        return fail(c, ARA_ETIMEOUT, "ara_wait: ticket %lld not finished within %llu ns", (long long)ticket,
+                    (unsigned long long)timeout_ns);
+    }
+    int32_t n_done = 0;
+    if ((rc = ara_serve_step(c, &n_done))) return rc;
+    if (n_done == 0 && ara_poll(c, ticket, nullptr, nullptr) == ARA_EAGAIN)
+      return fail(c, ARA_EINVAL, "ara_wait: ticket %lld is queued but no step can run it", (long long)ticket);
+  }
 }
 
 int ara_pml_tvar(ara_ctx* c, const double* ylt, int64_t n, const double* rps, int32_t n_rp, double* pml_out,

@@ -121,3 +121,26 @@ def test_serving_errors(eng, world):
     with pytest.raises(ara.AraError) as e:
         eng.poll(123456789, len(RPS))
     assert e.value.code == ara.ARA_EINVAL
+
+
+def test_wait_serves_until_the_request_is_done(eng, world):
+    from paper_1501_06326_gb300 import ara
+
+    yet, pool, reqs = world
+    _load(eng, yet, pool)
+    # requests of two seeds: waiting for a later one runs the steps before it
+    t_a = [eng.submit(ids, terms, 11, t_end, RPS) for ids, terms, t_end, _ in reqs[:3]]
+    t_b = eng.submit(reqs[3][0], reqs[3][1], 12, reqs[3][2], RPS)
+    pml, tvar = eng.wait(t_b, len(RPS))
+    ids, terms, t_end, sub = reqs[3]
+    ref = oracle.run_layer(yet, sub, terms, seed=12, trials=np.arange(t_end))
+    rpml, rtvar = oracle.pml_tvar(ref["ylt"], RPS)
+    assert np.allclose(pml, rpml, rtol=PML_TOL) and np.allclose(tvar, rtvar, rtol=PML_TOL)
+    for t in t_a:  # finished by the steps that ran before t_b's
+        assert eng.poll(t, len(RPS)) is not None
+    # a timeout that has passed before the first step: the request stays queued
+    t_c = eng.submit(ids, terms, 13, t_end, RPS)
+    with pytest.raises(ara.AraError) as e:
+        eng.wait(t_c, len(RPS), timeout_ns=1)
+    assert e.value.code == ara.ARA_ETIMEOUT
+    assert eng.wait(t_c, len(RPS)) is not None
