@@ -381,7 +381,7 @@ __global__ void k_sel_compact(const double* ylt, int64_t n, const SelScratch* sc
   }
 }
 
-// The fast path's finish, one block: per period, the remaining six digits of
+// The fast path's finish, one block per period: the remaining six digits of
 // the m-th key over the bucket's keys, then TVaR from the sums above the
 // bucket (the blocks' parts, a tree of fixed shape) and the bucket keys above
 // the m-th key (a fixed assignment of keys to threads and a fixed tree).
@@ -395,7 +395,8 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_finish(int64_t n, SelScratc
   __shared__ double s_ps[256];
   __shared__ unsigned long long s_pc[256];
   const unsigned int t = threadIdx.x, lane = t & 31;
-  for (int r = 0; r < g; ++r) {
+  {
+    const int r = blockIdx.x;
     if (t == 0) {
       s_prefix = sc->st[r].prefix;
       s_mask = sc->st[r].mask;
@@ -525,7 +526,7 @@ cudaError_t pml_tvar_device(const double* ylt, int64_t n, const double* rps_host
       k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, 56, nullptr);
       k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, 48, &sf->blk_hist[0][0][0]);
       k_sel_compact<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, sf, g, cand);
-      k_sel_finish<<<1, kSelThreads, 0, s>>>(n, sc, sf, g, grid, cand, pml + r0, tvar + r0);
+      k_sel_finish<<<g, kSelThreads, 0, s>>>(n, sc, sf, g, grid, cand, pml + r0, tvar + r0);
       if (n_launch) *n_launch += 5;
     } else {
       for (int shift = 56; shift >= 0; shift -= 8)
