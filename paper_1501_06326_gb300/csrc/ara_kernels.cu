@@ -317,15 +317,14 @@ __device__ void beta_inc_pair_f64(double x, double a, double b, double lnB, doub
   }
   const double front = exp(a * log(x) + b * log1p(-x) - lnB);
   if (front_out) *front_out = front;
-  if (x < (a + 1.0) / (a + b + 2.0)) {
-    const double v = front * beta_cf_f64(a, b, x) / a;
-    *I = v;
-    *Ic = 1.0 - v;
-  } else {
-    const double v = front * beta_cf_f64(b, a, 1.0 - x) / b;
-    *Ic = v;
-    *I = 1.0 - v;
-  }
+  // the fraction on the side where it converges fast: the side is chosen per
+  // lane and the fraction called once, so that the lanes of a warp do not
+  // run it twice
+  const bool lower = x < (a + 1.0) / (a + b + 2.0);
+  const double p = lower ? a : b, q = lower ? b : a, y = lower ? x : 1.0 - x;
+  const double v = front * beta_cf_f64(p, q, y) / p;
+  *I = lower ? v : 1.0 - v;
+  *Ic = lower ? 1.0 - v : v;
 }
 
 // Root r of I_r(A, B) = p (p <= 1/2) by bracketed Newton in FP64 from `guess`.
@@ -391,16 +390,15 @@ __device__ float4 table_node(const Pair& pr, double a, double b, double lnB, dou
   BetaSolveStats st;
   const float zf = (t <= 0.0) ? static_cast<float>(zl) : static_cast<float>(1.0 - zl);
   const float seed = pair_quantile_newton(pr, fminf(fmaxf(zf, 5.9604645e-08f), 0.99999994f), -1.0f, &st);
-  double w, lny;
-  if (t <= 0.0) {
-    const double x = beta_polish_f64(zl, a, b, lnB, static_cast<double>(seed));
-    w = log(x);
-    lny = log1p(-x);
-  } else {
-    const double y = beta_polish_f64(zl, b, a, lnB, 1.0 - static_cast<double>(seed));
-    w = log1p(-y);
-    lny = log(y);
-  }
+  // the root x (t <= 0) or y = 1 - x (t > 0): the shapes are swapped per lane
+  // and the polish called once (ln B is symmetric), so that the two halves of
+  // the warp do not run it in turn
+  const bool lo = t <= 0.0;
+  const double r = beta_polish_f64(zl, lo ? a : b, lo ? b : a, lnB,
+                                   lo ? static_cast<double>(seed) : 1.0 - static_cast<double>(seed));
+  const double l_r = log(r), l_1mr = log1p(-r);
+  const double w = lo ? l_r : l_1mr;
+  const double lny = lo ? l_1mr : l_r;
   const double lpdf = (a - 1.0) * w + (b - 1.0) * lny - lnB;
   const double lphi = -0.5 * t * t - 0.91893853320467274178;
   const double D = exp(lphi - w - lpdf);
