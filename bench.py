@@ -356,7 +356,7 @@ def run_gpu(args):
     # ---- two-part secondary uncertainty (correlated sigma) on the same layer; the plain
     # layer pass is timed here too, on the same stream, for the comparison
     correlated = events = None
-    if ws == 1 and not args.no_correlated:
+    if ws == 1 and not (args.no_correlated and args.no_events):
         eng.load_pool(pool)
 
         def plain_layer():
@@ -373,9 +373,10 @@ def run_gpu(args):
         b.record(stream)
         torch.cuda.synchronize(dev)
         ms_plain_layer = a.elapsed_time(b) / steps_c
-        correlated = _correlated_leg(eng, synth, torch, dev, stream, spec, terms, n_trials, n_events, seed,
-                                     ms_plain_layer, args)
-        eng.load_pool(pool)
+        if not args.no_correlated:
+            correlated = _correlated_leg(eng, synth, torch, dev, stream, spec, terms, n_trials, n_events, seed,
+                                         ms_plain_layer, args)
+            eng.load_pool(pool)
         if not args.no_events:
             events = _events_leg(eng, torch, dev, stream, pool, terms, n_trials, seed, ms_plain_layer, args)
 

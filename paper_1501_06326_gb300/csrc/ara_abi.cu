@@ -67,7 +67,7 @@ struct ara_ctx {
   // ELT pool
   std::map<int32_t, Elt> pool;
   // per-layer index (grown on demand)
-  DevBuf bits, word_cnt, word_pairs, rankdir, mask, slot_cnt, pairs, pairs_hot, pairs_w, scan_tmp;
+  DevBuf bits, word_cnt, word_pairs, rankdir, mask, slot_cnt, pairs, pairs_hot, pairs_w, pairs_ev, scan_tmp;
   DevBuf ev_buf, tile_cnt;  // hit-event records of the layer kernels
   DevBuf def_acc;           // per-trial FP64 sums of deferred occurrence losses
   DevBuf elt_stage, elt_recs_stage, elt_tab_stage, elt_flags;  // ELT load staging (grow-only)
@@ -551,6 +551,7 @@ static int plan_pass(ara_ctx* c, const std::vector<int32_t>& ids, int64_t t0, in
       (rc = reserve(c, c->pairs, sizeof(ara::Pair) * (n_recs + 1))) ||
       (rc = reserve(c, c->pairs_hot, sizeof(ara::PairHot) * (n_recs + 1))) ||
       (any_corr && (rc = reserve(c, c->pairs_w, sizeof(float2) * (n_recs + 1)))) ||
+      (rc = reserve(c, c->pairs_ev, sizeof(int32_t) * (n_recs + 1))) ||
       (rc = reserve(c, c->scan_tmp, sizeof(uint32_t) * (tmp_words + 8))))
     return rc;
   ara::LayerIndex& ix = pl->ix;
@@ -563,6 +564,7 @@ static int plan_pass(ara_ctx* c, const std::vector<int32_t>& ids, int64_t t0, in
   ix.pairs = static_cast<ara::Pair*>(c->pairs.ptr);
   ix.hot = static_cast<ara::PairHot*>(c->pairs_hot.ptr);
   ix.pw = any_corr ? static_cast<float2*>(c->pairs_w.ptr) : nullptr;
+  ix.pev = static_cast<int32_t*>(c->pairs_ev.ptr);
   ix.scan_tmp = static_cast<uint32_t*>(c->scan_tmp.ptr);
   ix.n_words = n_words;
   ix.n_recs = n_recs;
@@ -672,7 +674,7 @@ static int emit_event_rows(ara_ctx* c, const PassPlan& pl, const ara::LossParams
   dev[5] = max_staged ? static_cast<void*>(stage + at[5]) : static_cast<void*>(evr->max_occ);
   ara::EventRowsParams q{};
   q.off = pl.g.off;
-  q.ids = pl.g.ids;
+  q.pair_event = pl.ix.pev;
   q.t_begin = p.t_begin;
   q.t_end = p.t_end;
   q.n_tiles = n_tiles;
@@ -691,11 +693,7 @@ static int emit_event_rows(ara_ctx* c, const PassPlan& pl, const ara::LossParams
   q.row_inc = static_cast<double*>(dev[4]);
   q.max_occ = static_cast<double*>(dev[5]);
   if (q.max_occ) ARA_CUDA(c, cudaMemsetAsync(q.max_occ, 0, sizeof(double) * n_out, c->stream));
-  const int warps_per_block = ara::kEventRowsThreads / 32;
-  const int grid = static_cast<int>(
-      std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(c->num_sms) * 8,
-                                             (n_tiles + warps_per_block - 1) / warps_per_block)));
-  ARA_CUDA(c, ara::launch_event_rows(q, grid, c->stream));
+  ARA_CUDA(c, ara::launch_event_rows(q, c->num_sms, c->stream));
   *launched += 1;
   for (int i = 0; i < 5; ++i)
     if (staged[i])
@@ -1305,7 +1303,7 @@ void ara_destroy(ara_ctx* c) {
   DevBuf* bufs[] = {&c->elt_stage,  &c->elt_recs_stage, &c->elt_tab_stage, &c->elt_tabf_stage, &c->elt_work,
                     &c->elt_flags,  &c->ev_buf,         &c->tile_cnt,      &c->def_acc,        &c->yet_off,
                     &c->yet_ids,    &c->bits,           &c->word_cnt,      &c->word_pairs,     &c->rankdir,
-                    &c->mask,       &c->slot_cnt,       &c->pairs,         &c->pairs_hot,     &c->pairs_w,          &c->scan_tmp,       &c->flags,
+                    &c->mask,       &c->slot_cnt,       &c->pairs,         &c->pairs_hot,     &c->pairs_w,          &c->pairs_ev,         &c->scan_tmp,       &c->flags,
                     &c->counters,   &c->ylt_tmp,        &c->diag_tmp,      &c->sel,            &c->in_tmp,
                     &c->out_tmp,    &c->serve_ylt,      &c->serve_out,      &c->ev_occ,        &c->row_base,
                     &c->evr_stage};

@@ -100,6 +100,7 @@ struct LayerIndex {
   Pair* pairs;           // [n_recs]
   PairHot* hot;          // [n_recs] the table-path part of each pair
   float2* pw;            // [n_recs] (w_I, w_C) of each pair's record (pairs of kind kKindBetaC)
+  int32_t* pev;          // [n_recs] each pair's event id (the per-event output reads it)
   uint32_t* scan_tmp;
   int64_t n_words;
   int64_t n_recs;
@@ -217,12 +218,12 @@ cudaError_t launch_losses(const LossParams& p, int grid, cudaStream_t s);
 // zeroes it first: trials without rows keep 0).
 struct EventRowsParams {
   const int64_t* off;
-  const int32_t* ids;  // YET event ids
   int64_t t_begin, t_end, n_tiles, e0;
   const uint2* ev_buf;
   const float* occ;
   const uint32_t* tile_cnt;
   const uint32_t* row_base;  // [n_tiles + 1] exclusive scan of tile_cnt
+  const int32_t* pair_event;  // [pairs] each pair's event id (a record's event: that of its first pair)
   double agg_r, agg_l;
   int64_t cap;
   int64_t* row_trial;   // each of the five may be NULL
@@ -232,7 +233,8 @@ struct EventRowsParams {
   double* row_inc;
   double* max_occ;      // [t_end - t_begin] or NULL
 };
-cudaError_t launch_event_rows(const EventRowsParams& q, int grid, cudaStream_t s);
+// One wave of resident blocks over num_sms SMs.
+cudaError_t launch_event_rows(const EventRowsParams& q, int num_sms, cudaStream_t s);
 constexpr int kEventRowsThreads = 256;
 
 // --------------------------------------------------------------- PML / TVaR / sort

@@ -770,7 +770,7 @@ __global__ void k_slot_counts(const unsigned long long* mask, int64_t n, uint32_
 
 __global__ void k_fill_pairs(LayerEltRefs r, const uint32_t* bits, const uint32_t* slot_base,
                              const unsigned long long* mask,
-                             const uint32_t* slot_start, Pair* pairs, PairHot* hot, float2* pw) {
+                             const uint32_t* slot_start, Pair* pairs, PairHot* hot, float2* pw, int32_t* pev) {
   const int64_t n = r.rec_begin[r.n_elts];
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
@@ -790,6 +790,7 @@ __global__ void k_fill_pairs(LayerEltRefs r, const uint32_t* bits, const uint32_
     hq.node = pair_rec(q.meta) * (pair_fine(q.meta) ? kTabFineStride : kTabNodes);
     hot[at] = hq;
     if (pw && r.wts[p]) pw[at] = r.wts[p][j];
+    if (pev) pev[at] = e;
   }
 }
 
@@ -834,7 +835,7 @@ cudaError_t build_layer_index(const LayerEltRefs& refs, LayerIndex& ix, cudaStre
     if ((err = scan_exclusive_u32(ix.slot_cnt, ix.slot_cnt, n_recs, ix.scan_tmp, s, &launched)) != cudaSuccess)
       return err;
     k_fill_pairs<<<grid_for(n_recs, 256), 256, 0, s>>>(refs, ix.bits, ix.word_cnt, ix.mask, ix.slot_cnt, ix.pairs, ix.hot,
-                                                        ix.pw);
+                                                        ix.pw, ix.pev);
     launched += 3;
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   } else {
