@@ -170,6 +170,24 @@ ARA_API int ara_set_stream(ara_ctx *ctx, void *cuda_stream);
 ARA_API int ara_load_yet(ara_ctx *ctx, int64_t n_trials, const int64_t *offsets, const int32_t *event_ids,
                  int32_t catalogue_size);
 
+/* ara_load_yet without waiting for the upload: the offsets are read and the
+ * sizes checked during the call (the call first waits for the work already on
+ * the context's stream); the offsets and ids are then copied to the device
+ * and checked on an internal stream, beside later work on the context's
+ * stream, so that an ELT load (its table build) overlaps the copy.  offsets
+ * and event_ids stay owned by the caller and must stay valid and unchanged
+ * until the upload is finished: by ara_finish_yet or by the next call that
+ * uses the YET (ara_run_layer*, ara_submit, ara_serve, ...), which waits for
+ * it.  Errors in the offsets or ids are returned by that call (ARA_EINVAL,
+ * with no YET loaded); errors in the arguments by this one.  A second upload
+ * replaces one still in flight. */
+ARA_API int ara_load_yet_async(ara_ctx *ctx, int64_t n_trials, const int64_t *offsets, const int32_t *event_ids,
+                               int32_t catalogue_size);
+
+/* Waits for an ara_load_yet_async upload and returns its result (ARA_OK when
+ * none is in flight). */
+ARA_API int ara_finish_yet(ara_ctx *ctx);
+
 /* Load ELTs into the resident pool (Sections 2.1 (ii), 3.1): ELT i has pool id
  * elt_ids[i] (>= 0) and records rec_offsets[i] .. rec_offsets[i+1] of
  * (event_ids, mean, sigma, exposure), with strictly increasing event ids.

@@ -42,7 +42,7 @@ EXPORTED = (
     "ara_run_layer_diag", "ara_pml_tvar", "ara_sort_ylt", "ara_debug_uniforms",
     "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
     "ara_pml_tvar_noalloc", "ara_run_layers", "ara_submit", "ara_serve_step", "ara_poll", "ara_load_xelts",
-    "ara_run_layer_events", "ara_wait",
+    "ara_run_layer_events", "ara_wait", "ara_load_yet_async", "ara_finish_yet",
 )
 ARA_NOALLOC_MAX_RP = 64
 
@@ -136,6 +136,8 @@ def load_library(path: str = LIB_PATH):
     lib.ara_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.c_size_t, P]
     lib.ara_set_stream.argtypes = [P, P]
     lib.ara_load_yet.argtypes = [P, i64, P, P, i32]
+    lib.ara_load_yet_async.argtypes = [P, i64, P, P, i32]
+    lib.ara_finish_yet.argtypes = [P]
     lib.ara_load_elts.argtypes = [P, i32, P, P, P, P, P, P, P]
     lib.ara_load_xelts.argtypes = [P, i32, P, P, P, P, P, P, P, P]
     lib.ara_run_layer.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P]
@@ -208,6 +210,15 @@ def ara_set_stream(h, cuda_stream: int):
 def ara_load_yet(h, n_trials, offsets, event_ids, catalogue_size):
     return load_library().ara_load_yet(h, int(n_trials), _ptr(offsets, np.int64), _ptr(event_ids, np.int32),
                                        int(catalogue_size))
+
+
+def ara_load_yet_async(h, n_trials, offsets, event_ids, catalogue_size):
+    return load_library().ara_load_yet_async(h, int(n_trials), _ptr(offsets, np.int64), _ptr(event_ids, np.int32),
+                                             int(catalogue_size))
+
+
+def ara_finish_yet(h):
+    return load_library().ara_finish_yet(h)
 
 
 def ara_load_elts(h, n_elts, elt_ids, rec_offsets, event_ids, mean, sigma, exposure, terms=None):
@@ -318,12 +329,14 @@ class Ara:
         if rc != ARA_OK:
             raise AraError(rc, f"ara_create(device={device}) failed")
         self._h = h
+        self._yet_refs = None  # the arrays of an upload in flight (load_yet_async)
 
     # -- lifecycle
     def close(self) -> None:
         if getattr(self, "_h", None):
             ara_destroy(self._h)
             self._h = None
+        self._yet_refs = None
 
     def __enter__(self):
         return self
@@ -346,7 +359,20 @@ class Ara:
         self._check(ara_set_stream(self._h, cuda_stream))
 
     def load_yet(self, offsets, event_ids, catalogue_size: int) -> None:
-        self._check(ara_load_yet(self._h, _len(offsets) - 1, offsets, event_ids, catalogue_size))
+        # the call waits for an upload in flight before its arrays are let go
+        rc = ara_load_yet(self._h, _len(offsets) - 1, offsets, event_ids, catalogue_size)
+        self._yet_refs = None
+        self._check(rc)
+
+    def load_yet_async(self, offsets, event_ids, catalogue_size: int) -> None:
+        """``ara_load_yet_async``: returns while the ids are copied; the arrays
+        are kept referenced until the next YET load or ``close``."""
+        rc = ara_load_yet_async(self._h, _len(offsets) - 1, offsets, event_ids, catalogue_size)
+        self._yet_refs = (offsets, event_ids)
+        self._check(rc)
+
+    def finish_yet(self) -> None:
+        self._check(ara_finish_yet(self._h))
 
     def load_elts(self, elt_ids, rec_offsets, event_ids, mean, sigma, exposure, terms=None) -> None:
         if terms is not None and isinstance(terms, np.ndarray):

@@ -64,6 +64,16 @@ struct ara_ctx {
   int64_t n_events = 0;
   int32_t catalogue = 0;
   bool yet_loaded = false;
+  // YET upload in flight (ara_load_yet_async): copied and checked on copy_stream;
+  // the first call that uses the YET waits for yet_ready and reads the flags
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t yet_ready = nullptr;
+  DevBuf yet_flags;                  // uint32 check flags of the upload
+  uint32_t* h_yet_flags = nullptr;   // pinned copy of them
+  bool yet_pending = false;
+  const char* yet_who = "ara_load_yet";
+  int64_t p_trials = 0, p_events = 0, p_longest = 0;
+  int32_t p_catalogue = 0;
   // ELT pool
   std::map<int32_t, Elt> pool;
   // per-layer index (grown on demand)
@@ -184,6 +194,17 @@ cudaError_t copy_params_to_host(void* dst, const void* src, size_t bytes) {
   return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
 }
 
+// Pinned (or registered) host memory that kernels can read at the same address.
+bool is_mapped_host_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
 cudaMemcpyKind kind_to_device(const void* src) {
   return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 }
@@ -241,51 +262,109 @@ int ara_set_stream(ara_ctx* c, void* cuda_stream) {
   return ARA_OK;
 }
 
-int ara_load_yet(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int32_t* event_ids,
-                 int32_t catalogue_size) {
+}  // extern "C"
+
+namespace {
+
+// Waits for the YET upload in flight, if any, and makes it the loaded YET when
+// its checks passed.
+int yet_finish(ara_ctx* c) {
+  if (!c->yet_pending) return ARA_OK;
+  c->yet_pending = false;
+  ARA_CUDA(c, cudaEventSynchronize(c->yet_ready));
+  const uint32_t f = *c->h_yet_flags;
+  if (f & ara::kBadOffsets) return fail(c, ARA_EINVAL, "%s: offsets are not non-decreasing", c->yet_who);
+  if (f & ara::kLongTrial) return fail(c, ARA_EINVAL, "%s: a trial has 2^22 or more events", c->yet_who);
+  if (f & ara::kBadEventId)
+    return fail(c, ARA_EINVAL, "%s: an event id lies outside [0, %d)", c->yet_who, c->p_catalogue);
+  c->n_trials = c->p_trials;
+  c->n_events = c->p_events;
+  c->max_trial_events = c->p_longest;
+  c->catalogue = c->p_catalogue;
+  c->yet_loaded = true;
+  return ARA_OK;
+}
+
+// Starts loading a YET: the offsets are read on the host during the call; the
+// offsets and ids are copied to the device and checked on copy_stream, which
+// runs beside later work on the context's stream until yet_finish.
+int yet_begin(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int32_t* event_ids,
+              int32_t catalogue_size, const char* who) {
   int rc = bind(c);
   if (rc) return rc;
   if (n_trials < 1 || !offsets || catalogue_size < 1)
-    return fail(c, ARA_EINVAL, "ara_load_yet: need n_trials >= 1, offsets and catalogue_size >= 1");
+    return fail(c, ARA_EINVAL, "%s: need n_trials >= 1, offsets and catalogue_size >= 1", who);
+  // an upload still in flight is replaced: wait for it, whatever its checks say
+  if (c->yet_pending) {
+    c->yet_pending = false;
+    ARA_CUDA(c, cudaEventSynchronize(c->yet_ready));
+  }
   c->yet_loaded = false;
-  // offsets: keep a host copy (sizes and ranges are planned on the host)
+  if (!c->copy_stream) {
+    ARA_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    ARA_CUDA(c, cudaEventCreateWithFlags(&c->yet_ready, cudaEventDisableTiming));
+    ARA_CUDA(c, cudaMallocHost(&c->h_yet_flags, sizeof(uint32_t)));
+    if ((rc = reserve(c, c->yet_flags, 16))) return rc;
+  }
+  // offsets: keep a host copy (sizes and ranges are planned on the host); this
+  // also waits for the work before the call, which may still read the old YET
   c->h_off.resize(static_cast<size_t>(n_trials) + 1);
   ARA_CUDA(c, cudaMemcpyAsync(c->h_off.data(), offsets, sizeof(int64_t) * (n_trials + 1), cudaMemcpyDefault,
                               c->stream));
   ARA_CUDA(c, cudaStreamSynchronize(c->stream));
   const int64_t n_events = c->h_off[n_trials];
-  if (c->h_off[0] != 0 || n_events < 0) return fail(c, ARA_EINVAL, "ara_load_yet: offsets[0] must be 0 and offsets[n] >= 0");
-  if (n_events > 0 && !event_ids) return fail(c, ARA_EINVAL, "ara_load_yet: event_ids is NULL");
+  if (c->h_off[0] != 0 || n_events < 0) return fail(c, ARA_EINVAL, "%s: offsets[0] must be 0 and offsets[n] >= 0", who);
+  if (n_events > 0 && !event_ids) return fail(c, ARA_EINVAL, "%s: event_ids is NULL", who);
   if ((rc = reserve(c, c->yet_off, sizeof(int64_t) * (n_trials + 1)))) return rc;
   // ids: padded by 4 entries so that 16-byte loads near the end stay inside the buffer
   if ((rc = reserve(c, c->yet_ids, sizeof(int32_t) * (n_events + 4)))) return rc;
-  ARA_CUDA(c, cudaMemcpyAsync(c->yet_off.ptr, c->h_off.data(), sizeof(int64_t) * (n_trials + 1),
-                              cudaMemcpyHostToDevice, c->stream));
-  if (n_events > 0)
-    ARA_CUDA(c, cudaMemcpyAsync(c->yet_ids.ptr, event_ids, sizeof(int32_t) * n_events, kind_to_device(event_ids),
-                                c->stream));
-  ARA_CUDA(c, cudaMemsetAsync(static_cast<int32_t*>(c->yet_ids.ptr) + n_events, 0, sizeof(int32_t) * 4, c->stream));
-  uint32_t* flags = static_cast<uint32_t*>(c->flags.ptr);
-  ARA_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(uint32_t), c->stream));
-  ARA_CUDA(c, ara::launch_check_offsets(static_cast<const int64_t*>(c->yet_off.ptr), n_trials, n_events, flags,
-                                        c->stream));
-  ARA_CUDA(c, ara::launch_check_ids(static_cast<const int32_t*>(c->yet_ids.ptr), n_events, catalogue_size, flags,
-                                    c->stream));
-  uint32_t h_flags = 0;
-  ARA_CUDA(c, cudaMemcpyAsync(&h_flags, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
-  ARA_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (h_flags & ara::kBadOffsets) return fail(c, ARA_EINVAL, "ara_load_yet: offsets are not non-decreasing");
-  if (h_flags & ara::kLongTrial) return fail(c, ARA_EINVAL, "ara_load_yet: a trial has 2^22 or more events");
-  if (h_flags & ara::kBadEventId)
-    return fail(c, ARA_EINVAL, "ara_load_yet: an event id lies outside [0, %d)", catalogue_size);
+  cudaStream_t cs = c->copy_stream;
+  uint32_t* flags = static_cast<uint32_t*>(c->yet_flags.ptr);
+  ARA_CUDA(c, cudaMemsetAsync(flags, 0, sizeof(uint32_t), cs));
+  ARA_CUDA(c, cudaMemcpyAsync(c->yet_off.ptr, offsets, sizeof(int64_t) * (n_trials + 1), kind_to_device(offsets), cs));
+  ARA_CUDA(c, cudaMemsetAsync(static_cast<int32_t*>(c->yet_ids.ptr) + n_events, 0, sizeof(int32_t) * 4, cs));
+  ARA_CUDA(c, ara::launch_check_offsets(static_cast<const int64_t*>(c->yet_off.ptr), n_trials, n_events, flags, cs));
+  int32_t* d_ids = static_cast<int32_t*>(c->yet_ids.ptr);
+  if (n_events > 0 && is_mapped_host_ptr(event_ids)) {
+    // pinned host ids: a kernel reads them over the host link and checks them on
+    // the way, so that the copy engine serves the other streams' copies meanwhile
+    ARA_CUDA(c, ara::launch_upload_ids(event_ids, d_ids, n_events, catalogue_size, flags, cs));
+  } else if (n_events > 0) {
+    ARA_CUDA(c, cudaMemcpyAsync(d_ids, event_ids, sizeof(int32_t) * n_events, kind_to_device(event_ids), cs));
+    ARA_CUDA(c, ara::launch_check_ids(d_ids, n_events, catalogue_size, flags, cs));
+  }
+  c->launches += 1 + (n_events > 0 ? 1 : 0);
+  ARA_CUDA(c, cudaMemcpyAsync(c->h_yet_flags, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, cs));
+  ARA_CUDA(c, cudaEventRecord(c->yet_ready, cs));
   int64_t longest = 0;  // bounds a trial's sum in the batched layers' fixed point
   for (int64_t t = 0; t < n_trials; ++t) longest = std::max(longest, c->h_off[t + 1] - c->h_off[t]);
-  c->n_trials = n_trials;
-  c->n_events = n_events;
-  c->max_trial_events = longest;
-  c->catalogue = catalogue_size;
-  c->yet_loaded = true;
+  c->p_trials = n_trials;
+  c->p_events = n_events;
+  c->p_longest = longest;
+  c->p_catalogue = catalogue_size;
+  c->yet_who = who;
+  c->yet_pending = true;
   return ARA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ara_load_yet(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int32_t* event_ids,
+                 int32_t catalogue_size) {
+  const int rc = yet_begin(c, n_trials, offsets, event_ids, catalogue_size, "ara_load_yet");
+  return rc ? rc : yet_finish(c);
+}
+
+int ara_load_yet_async(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int32_t* event_ids,
+                       int32_t catalogue_size) {
+  return yet_begin(c, n_trials, offsets, event_ids, catalogue_size, "ara_load_yet_async");
+}
+
+int ara_finish_yet(ara_ctx* c) {
+  const int rc = bind(c);
+  return rc ? rc : yet_finish(c);
 }
 
 // ara_load_elts and ara_load_xelts; sigma_c == NULL: no correlated part.
@@ -486,6 +565,8 @@ struct PassPlan {
 };
 
 static int check_trial_range(ara_ctx* c, int64_t t0, int64_t t1, const char* who) {
+  const int rc = yet_finish(c);
+  if (rc) return rc;
   if (!c->yet_loaded) return fail(c, ARA_ENOTLOADED, "%s: no YET loaded", who);
   if (t0 < 0 || t1 > c->n_trials || t0 >= t1)
     return fail(c, ARA_EINVAL, "%s: trial range [%lld, %lld) outside [0, %lld)", who, (long long)t0, (long long)t1,
@@ -1293,6 +1374,7 @@ void ara_destroy(ara_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   for (auto& kv : c->pool) {
     release(c, kv.second.events);
     release(c, kv.second.recs);
@@ -1306,11 +1388,14 @@ void ara_destroy(ara_ctx* c) {
                     &c->mask,       &c->slot_cnt,       &c->pairs,         &c->pairs_hot,     &c->pairs_w,          &c->pairs_ev,         &c->scan_tmp,       &c->flags,
                     &c->counters,   &c->ylt_tmp,        &c->diag_tmp,      &c->sel,            &c->in_tmp,
                     &c->out_tmp,    &c->serve_ylt,      &c->serve_out,      &c->ev_occ,        &c->row_base,
-                    &c->evr_stage};
+                    &c->evr_stage,  &c->yet_flags};
   for (DevBuf* b : bufs) release(c, *b);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->ev_pool) cudaEventDestroy(e);
+  if (c->yet_ready) cudaEventDestroy(c->yet_ready);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->h_yet_flags) cudaFreeHost(c->h_yet_flags);
   cudaGetLastError();
   delete c;
 }

@@ -24,6 +24,11 @@ enum : uint32_t {
 cudaError_t launch_check_offsets(const int64_t* off, int64_t n_trials, int64_t n_events, uint32_t* flags,
                                  cudaStream_t s);
 cudaError_t launch_check_ids(const int32_t* ids, int64_t n, int32_t catalogue, uint32_t* flags, cudaStream_t s);
+// Copies n ids from pinned host memory that kernels can read at the same
+// address (src) into device memory (dst) on a few SMs, checking each against
+// [0, catalogue) as it passes: the copy engine stays free for other streams.
+cudaError_t launch_upload_ids(const int32_t* src, int32_t* dst, int64_t n, int32_t catalogue, uint32_t* flags,
+                              cudaStream_t s);
 
 // Prepare the Pair records of one ELT from (mean, sigma, exposure) in FP64:
 // Beta shapes, x0/y0, C, I_{1/2}(a, b), kind.  Also checks order and values

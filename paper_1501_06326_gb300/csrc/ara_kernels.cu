@@ -72,6 +72,60 @@ __global__ void k_check_ids(const int32_t* ids, int64_t n, int32_t catalogue, ui
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kBadEventId);
 }
 
+// The YET upload from pinned host memory: each thread moves int4 groups of
+// ids (four groups in flight) when the source is 16-byte aligned, single ids
+// otherwise, and flags any id outside [0, catalogue).  A few blocks keep
+// enough reads in flight to fill the host link.
+constexpr int kUploadBlocks = 32;
+constexpr int kUploadThreads = 512;
+
+__device__ __forceinline__ bool id_bad(int32_t e, uint32_t cat) { return static_cast<uint32_t>(e) >= cat; }
+
+__global__ void __launch_bounds__(kUploadThreads) k_upload_ids(const int32_t* __restrict__ src,
+                                                               int32_t* __restrict__ dst, int64_t n,
+                                                               int32_t catalogue, uint32_t* flags) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const uint32_t cat = static_cast<uint32_t>(catalogue);
+  bool bad = false;
+  int64_t k0 = 0;  // first id of the single-id tail
+  if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+    const int4* s4 = reinterpret_cast<const int4*>(src);
+    int4* d4 = reinterpret_cast<int4*>(dst);
+    const int64_t n4 = n >> 2;
+    int64_t i = tid;
+    for (; i + 3 * stride < n4; i += 4 * stride) {
+      int4 v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = s4[i + j * stride];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        d4[i + j * stride] = v[j];
+        bad |= id_bad(v[j].x, cat) | id_bad(v[j].y, cat) | id_bad(v[j].z, cat) | id_bad(v[j].w, cat);
+      }
+    }
+    for (; i < n4; i += stride) {
+      const int4 v = s4[i];
+      d4[i] = v;
+      bad |= id_bad(v.x, cat) | id_bad(v.y, cat) | id_bad(v.z, cat) | id_bad(v.w, cat);
+    }
+    k0 = 4 * n4;
+  }
+  for (int64_t k = k0 + tid; k < n; k += stride) {
+    const int32_t e = src[k];
+    dst[k] = e;
+    bad |= id_bad(e, cat);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kBadEventId);
+}
+
+cudaError_t launch_upload_ids(const int32_t* src, int32_t* dst, int64_t n, int32_t catalogue, uint32_t* flags,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_upload_ids<<<kUploadBlocks, kUploadThreads, 0, s>>>(src, dst, n, catalogue, flags);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_offsets(const int64_t* off, int64_t n_trials, int64_t n_events, uint32_t* flags,
                                  cudaStream_t s) {
   const int64_t blocks = (n_trials + 255) / 256;

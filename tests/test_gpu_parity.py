@@ -248,6 +248,75 @@ def test_layer_errors_are_reported(eng, plain_1k):
         eng.load_pool(neg)
 
 
+def test_async_yet_load(eng, plain_1k):
+    """ara_load_yet_async: the upload runs beside an ELT load, the next layer call
+    waits for it; results identical to the synchronous load; errors in the ids
+    surface at that call and leave no YET loaded."""
+    import torch
+
+    from paper_1501_06326_gb300 import ara
+
+    yet, pool, spec, terms = plain_1k
+    eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
+    eng.load_pool(pool)
+    want = np.zeros(yet.n_trials)
+    eng.run_layer(pool.elt_ids, terms, 3, 0, yet.n_trials, want)
+    off_h = torch.from_numpy(yet.offsets).pin_memory()
+    ids_h = torch.from_numpy(yet.event_ids).pin_memory()
+    # host (pinned) source, an ELT load while the upload runs
+    eng.load_yet_async(off_h, ids_h, yet.catalogue_size)
+    eng.load_pool(pool)
+    got = np.zeros(yet.n_trials)
+    eng.run_layer(pool.elt_ids, terms, 3, 0, yet.n_trials, got)
+    assert np.array_equal(got, want)
+    eng.finish_yet()  # nothing in flight
+    # device source; a second upload replaces the first while it is in flight
+    other = synth.make_yet(50, 5.0, yet.catalogue_size, 77)
+    eng.load_yet_async(other.offsets, other.event_ids, other.catalogue_size)
+    eng.load_yet_async(torch.from_numpy(yet.offsets).cuda(), torch.from_numpy(yet.event_ids).cuda(),
+                       yet.catalogue_size)
+    eng.finish_yet()
+    got[:] = 0.0
+    eng.run_layer(pool.elt_ids, terms, 3, 0, yet.n_trials, got)
+    assert np.array_equal(got, want)
+    # a bad id: the upload call succeeds, the next call that needs the YET fails
+    bad_ids = yet.event_ids.copy()
+    bad_ids[7] = -1
+    eng.load_yet_async(yet.offsets, bad_ids, yet.catalogue_size)
+    with pytest.raises(ara.AraError) as e:
+        eng.run_layer(pool.elt_ids, terms, 3, 0, 10, got)
+    assert e.value.code == ara.ARA_EINVAL and "ara_load_yet_async" in str(e.value)
+    with pytest.raises(ara.AraError) as e:
+        eng.run_layer(pool.elt_ids, terms, 3, 0, 10, got)
+    assert e.value.code == ara.ARA_ENOTLOADED
+    # pinned ids start 4 bytes past a 16-byte boundary: the upload kernel's single-id path
+    buf = torch.empty(yet.event_ids.size + 1, dtype=torch.int32).pin_memory()
+    buf[1:] = torch.from_numpy(yet.event_ids)
+    eng.load_yet_async(off_h, buf[1:], yet.catalogue_size)
+    got[:] = 0.0
+    eng.run_layer(pool.elt_ids, terms, 3, 0, yet.n_trials, got)
+    assert np.array_equal(got, want)
+    # a bad id in pinned memory, found by the upload kernel (aligned and not)
+    for view, bad in ((torch.from_numpy(bad_ids).pin_memory(), -1), (buf[1:], yet.catalogue_size)):
+        view[7] = bad
+        eng.load_yet_async(off_h, view, yet.catalogue_size)
+        with pytest.raises(ara.AraError) as e:
+            eng.finish_yet()
+        assert e.value.code == ara.ARA_EINVAL and "outside" in str(e.value)
+    # bad offsets are found by the upload's checks too
+    bad_off = yet.offsets.copy()
+    bad_off[5] = bad_off[4] - 1
+    eng.load_yet_async(bad_off, yet.event_ids, yet.catalogue_size)
+    with pytest.raises(ara.AraError) as e:
+        eng.finish_yet()
+    assert e.value.code == ara.ARA_EINVAL
+    # argument errors are reported by the call itself
+    with pytest.raises(ara.AraError) as e:
+        eng.load_yet_async(yet.offsets, yet.event_ids, 0)
+    assert e.value.code == ara.ARA_EINVAL
+    eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
+
+
 # ------------------------------------------------------------------ PML / TVaR / sort
 @pytest.mark.parametrize("n", [1, 999, 100_000, 1_000_003])
 def test_pml_tvar_and_sort(eng, n):
