@@ -337,12 +337,25 @@ def run_gpu(args):
             t = torch.tensor([e2e_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_ms = float(t.item())
+        # its parts alone (wall time): the YET upload, the ELT load with its table build
+        def wall(fn, reps=2):
+            barrier()
+            t = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            barrier()
+            return (time.perf_counter() - t) * 1e3 / reps
+
+        upload_ms = wall(lambda: (eng.load_yet_async(offsets_host, ids_host, spec["catalogue"]), eng.finish_yet()))
+        elt_ms = wall(lambda: eng.load_elts(pool.elt_ids, pool.rec_offsets, pool.event_ids, pool.mean, pool.sigma,
+                                            pool.exposure, terms_arr))
         pool_bytes = (pool.elt_ids.nbytes + pool.rec_offsets.nbytes + pool.event_ids.nbytes + pool.mean.nbytes
                       + pool.sigma.nbytes + pool.exposure.nbytes + pool.terms.nbytes)
         h2d = offsets.nbytes + 4 * n_events + pool_bytes + 8 * n_trials  # ylt host -> device staging for PML
         d2h = 8 * n_trials + 16 * len(rps)
         e2e = {"value": ws * evals_per_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
+               "yet_upload_ms": upload_ms, "elt_load_ms": elt_ms,
                "step": "ara_load_yet_async (pinned host YET) beside ara_load_elts (host ELTs, table build), "
                        "ara_run_layer (host YLT), ara_pml_tvar"}
 
