@@ -895,8 +895,11 @@ static int batch_scale_exp(double o_max, int64_t n_max) {
   return std::max(-1000, std::min(1000, e));
 }
 
+// layer_t_end (NULL: t1 for every layer): layer l's trials end at
+// min(layer_t_end[l], t1); its year losses of later trials are 0 and cost no
+// loss computations (the serving loop's requests over their own prefixes).
 static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers, uint64_t seed, int64_t t0,
-                           int64_t t1, double* ylt_out) {
+                           int64_t t1, double* ylt_out, const int64_t* layer_t_end = nullptr) {
   static const char* who = "ara_run_layers";
   int rc = bind(c);
   if (rc) return rc;
@@ -945,6 +948,7 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
     p.agg_l[l] = L.agg_limit;
     p.scale_exp[l] = batch_scale_exp(o_max, c->max_trial_events);
     p.inv_scale[l] = std::ldexp(1.0, -p.scale_exp[l]);
+    p.layer_t_end[l] = layer_t_end ? std::min(layer_t_end[l], t1) : t1;
   }
   // ---- outputs
   const int64_t n_out = pl.n_out;
@@ -1133,9 +1137,11 @@ int ara_serve_step(ara_ctx* c, int32_t* n_done) {
   // ---- the layers over [0, t_max), then each request's PML/TVaR over its own prefix
   const int32_t nb = static_cast<int32_t>(batch.size());
   std::vector<ara_layer> layers(nb);
+  std::vector<int64_t> t_ends(nb);
   int32_t n_rp_total = 0;
   for (int32_t i = 0; i < nb; ++i) {
     layers[i] = c->serve_reqs[batch[i]].layer;
+    t_ends[i] = c->serve_reqs[batch[i]].t_end;
     n_rp_total += static_cast<int32_t>(c->serve_reqs[batch[i]].rps.size());
   }
   int status = reserve(c, c->serve_ylt, sizeof(double) * static_cast<size_t>(t_max) * nb);
@@ -1143,7 +1149,8 @@ int ara_serve_step(ara_ctx* c, int32_t* n_done) {
   if (!status) status = reserve(c, c->sel, ara::select_scratch_bytes(t_max));
   double* d_ylt = static_cast<double*>(c->serve_ylt.ptr);
   double* d_out = static_cast<double*>(c->serve_out.ptr);
-  if (!status) status = run_layers_impl(c, nb, layers.data(), first.seed, 0, t_max, d_ylt);
+  // each request's layer over its own prefix only; the pass spans the longest
+  if (!status) status = run_layers_impl(c, nb, layers.data(), first.seed, 0, t_max, d_ylt, t_ends.data());
   std::vector<double> h_out(2 * static_cast<size_t>(n_rp_total));
   if (!status) {
     int32_t at = 0, launched = 0;

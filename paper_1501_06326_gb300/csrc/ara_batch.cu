@@ -37,6 +37,7 @@ struct BatchShared {
   unsigned long long layers_of[kMaxIndexElts];
   float occ_r[kBatchLayers], occ_l[kBatchLayers];
   int32_t sexp[kBatchLayers];
+  int64_t t_end[kBatchLayers];
 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
@@ -124,13 +125,13 @@ __device__ __forceinline__ void add_occurrence(BatchWarp& ws, const BatchShared&
 // layer it touches, its pair losses over the layer's ELTs summed in the pairs'
 // order (each pair's loss recomputed per layer: such events are rare).
 __device__ __noinline__ void batch_long_event(const BatchParams& p, const BatchShared& bs, BatchWarp& ws, uint2 r,
-                                              int64_t trial, unsigned long long* nc) {
+                                              int64_t trial, unsigned long long act, unsigned long long* nc) {
   const uint32_t lane = lane_id();
   const uint32_t cnt = ((r.x >> kRecCntShift) & kRecCntMask) + 1u;
   const uint32_t k = r.x & kRecKMask;
   unsigned long long touched = 0ull;
   for (uint32_t j = 0; j < cnt; ++j) touched |= bs.layers_of[pair_pos(p.hot[r.y + j].meta)];
-  for (unsigned long long m = touched; m; m &= m - 1ull) {
+  for (unsigned long long m = touched & act; m; m &= m - 1ull) {
     const int l = __ffsll(m) - 1;
     float G = 0.0f;
     for (uint32_t j = 0; j < cnt; ++j)
@@ -145,9 +146,10 @@ __device__ __noinline__ void batch_long_event(const BatchParams& p, const BatchS
 // layer from left to right (the pairs' canonical order) and applies the
 // occurrence terms.  A left-to-right sum does not change when pairs of other
 // layers' ELTs are present, so an event's per-layer losses are the same in
-// any batch.
+// any batch.  Only the layers in `act` (those whose trials reach this one)
+// are served; a pair of none of them is not computed.
 __device__ __noinline__ uint32_t batch_multi(const BatchParams& p, const BatchShared& bs, BatchWarp& ws, int nq,
-                                             int64_t trial, unsigned long long* nc) {
+                                             int64_t trial, unsigned long long act, unsigned long long* nc) {
   const uint32_t q = lane_id();
   const uint32_t upto = 0xffffffffu >> (31u - q);  // lanes 0..q
   uint32_t n_pairs = 0;
@@ -156,7 +158,7 @@ __device__ __noinline__ uint32_t batch_multi(const BatchParams& p, const BatchSh
     const uint2 r = (ie < nq) ? ws.mq[ie] : make_uint2(0u, 0u);
     const uint32_t cnt = (ie < nq) ? ((r.x >> kRecCntShift) & kRecCntMask) + 1u : 0u;
     if (__shfl_sync(0xffffffffu, cnt, 0) > 32u) {  // a long event first in line: by lane 0
-      if (q == 0) batch_long_event(p, bs, ws, r, trial, nc);
+      if (q == 0) batch_long_event(p, bs, ws, r, trial, act, nc);
       n_pairs += __shfl_sync(0xffffffffu, cnt, 0);
       __syncwarp();
       ++i0;
@@ -181,8 +183,8 @@ __device__ __noinline__ uint32_t batch_multi(const BatchParams& p, const BatchSh
     float L = 0.0f;
     unsigned long long lm = 0ull;
     if (q < np) {
-      L = pair_loss_batch(p, bs, ey + (q - epre), trial, ex & kRecKMask, nc);
-      lm = bs.layers_of[pair_pos(p.hot[ey + (q - epre)].meta)];
+      lm = bs.layers_of[pair_pos(p.hot[ey + (q - epre)].meta)] & act;
+      if (lm) L = pair_loss_batch(p, bs, ey + (q - epre), trial, ex & kRecKMask, nc);
     }
     ws.wl[q] = L;
     ws.wm[q] = lm;
@@ -256,6 +258,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
     bs.occ_r[i] = p.occ_r[i];
     bs.occ_l[i] = p.occ_l[i];
     bs.sexp[i] = p.scale_exp[i];
+    bs.t_end[i] = i < p.n_layers ? p.layer_t_end[i] : 0;
   }
   __syncthreads();
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -275,9 +278,14 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
     const int64_t ta = p.t_begin + tile * kWarpTrials;
     const int64_t trial = ta + tl;
     if (trial >= p.t_end) continue;
+    // the layers whose trials reach this one (all of them unless a layer ends early)
+    static_assert(kBatchLayers <= 32, "one lane per layer");
+    const unsigned long long act =
+        __ballot_sync(0xffffffffu, lane < static_cast<uint32_t>(p.n_layers) && trial < bs.t_end[lane]);
     const uint2* recs = p.ev_buf + (__ldg(&p.off[ta]) - p.e0);
-    // the trial's records [beg, end) of the tile (records are in trial order)
-    const int32_t n = static_cast<int32_t>(__ldg(&p.tile_cnt[tile]));
+    // the trial's records [beg, end) of the tile (records are in trial order); none
+    // when no layer reaches the trial
+    const int32_t n = act ? static_cast<int32_t>(__ldg(&p.tile_cnt[tile])) : 0;
     const int32_t beg = first_record_of(recs, n, tl, lane);
     const int32_t end = first_record_of(recs, n, tl + 1, lane);
     for (int l = 0; l < p.n_layers; ++l) ws.acc[l][lane] = 0ull;
@@ -321,7 +329,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
         val[j] = 0.0f;
         sfrac[j] = 0.0f;
         node[j] = nullptr;
-        if (valid && cnt == 1u) {
+        if (valid && cnt == 1u && (bs.layers_of[pair_pos(h[j].meta)] & act)) {
           const uint32_t kind = pair_kind(h[j].meta);
           const uint32_t pos = pair_pos(h[j].meta);
           mode[j] = 1;
@@ -372,7 +380,8 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
                        : 0.0f;
           L = bs.share[pos] * clamp_terms_f(loss, bs.ret[pos], bs.lim[pos]);
         }
-        for (unsigned long long m = bs.layers_of[pos]; m; m &= m - 1ull) add_occurrence(ws, bs, __ffsll(m) - 1, lane, L);
+        for (unsigned long long m = bs.layers_of[pos] & act; m; m &= m - 1ull)
+          add_occurrence(ws, bs, __ffsll(m) - 1, lane, L);
         ++n_pairs;
       }
       // ---- multi-ELT events: queued
@@ -384,7 +393,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
         if (mmask) {
           if (nq + __popc(mmask) > kBatchQueue) {
             __syncwarp();
-            const uint32_t np = batch_multi(p, bs, ws, nq, trial, &nc);
+            const uint32_t np = batch_multi(p, bs, ws, nq, trial, act, &nc);
             if (lane == 0) n_pairs += np;
             nq = 0;
           }
@@ -395,7 +404,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
       }
     }
     if (nq > 0) {
-      const uint32_t np = batch_multi(p, bs, ws, nq, trial, &nc);
+      const uint32_t np = batch_multi(p, bs, ws, nq, trial, act, &nc);
       if (lane == 0) n_pairs += np;
     }
     __syncwarp();

@@ -206,6 +206,7 @@ struct BatchParams {
   double* ylt;                         // layer-major, stride n_out
   int64_t n_out;
   unsigned long long* counters;        // [0] tile queue, [1] pairs, [2] non-converged
+  int64_t layer_t_end[kBatchLayers];   // layer l's trials end here (<= t_end): later trials get no losses (year loss 0)
 };
 
 cudaError_t launch_losses_batch(const BatchParams& p, int grid, cudaStream_t s);
