@@ -976,15 +976,29 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
   p.ylt = d_ylt;
   p.n_out = n_out;
   p.counters = static_cast<unsigned long long*>(c->counters.ptr);
+  // expected hit records per trial: each union ELT's records over the catalogue, times the
+  // events per trial, weighted by the share of the pass's trials its layers reach
+  double recs_per_trial = 0.0;
+  for (size_t i = 0; i < uni.size(); ++i) {
+    double reach = 0.0;
+    for (int32_t l = 0; l < n_layers; ++l)
+      if ((p.layers_of[i] >> l) & 1ull)
+        reach = std::max(reach, static_cast<double>(p.layer_t_end[l] - t0) / static_cast<double>(t1 - t0));
+    recs_per_trial += reach * static_cast<double>(c->pool.find(uni[i])->second.n);
+  }
+  recs_per_trial *= static_cast<double>(c->n_events) / (static_cast<double>(c->n_trials) * c->catalogue);
+  // one warp per trial once a trial's records fill a warp's rounds; else one warp per tile
+  const bool per_trial = recs_per_trial >= 192.0;
   const int64_t warps = ara::kBatchThreads / 32;
-  const int grid = static_cast<int>(std::min<int64_t>(c->num_sms * ara::kBatchBlocksPerSm,
-                                                      (pl.n_tiles + warps - 1) / warps));
+  const int64_t items = per_trial ? pl.n_tiles * ara::kWarpTrials : pl.n_tiles;
+  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->num_sms * ara::kBatchBlocksPerSm,
+                                                                           (items + warps - 1) / warps)));
   int launched = 0;
   if ((rc = launch_index_and_gather(c, pl, who, &launched))) return rc;
   cudaEvent_t la, lb;
   if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
   ARA_CUDA(c, cudaEventRecord(la, c->stream));
-  ARA_CUDA(c, ara::launch_losses_batch(p, grid, c->stream));
+  ARA_CUDA(c, ara::launch_losses_batch(p, per_trial, grid, c->stream));
   ARA_CUDA(c, cudaEventRecord(lb, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   launched += 1;

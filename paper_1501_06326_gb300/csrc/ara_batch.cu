@@ -6,10 +6,10 @@
 // computed once and serves every layer of the batch that holds the ELT.  Per
 // layer, the event's losses over the layer's ELTs are summed (Algorithm 1),
 // the occurrence terms applied, and the occurrence loss is added to the
-// layer's sum for the trial: a 64-bit fixed-point integer in shared memory, so
-// that the sum is exact for the FP32 occurrence losses and independent of the
-// order of the (atomic) additions.  The aggregate terms of each layer then give
-// its year losses.
+// layer's sum for the trial: a 64-bit fixed-point integer, so that the sum is
+// exact for the FP32 occurrence losses and independent of the order of the
+// (atomic) additions.  The aggregate terms of each layer then give its year
+// losses.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -23,7 +23,9 @@ namespace {
 constexpr int kBatchQueue = 64;  // multi-ELT events queued per warp
 
 struct BatchWarp {
-  unsigned long long acc[kBatchLayers][32];  // per layer and lane: the lane's sum of occurrence losses (fixed point)
+  unsigned long long acc[kBatchLayers][32];  // per layer and lane: the lane's sum for its current trial (fixed point)
+  unsigned long long (*tacc)[kWarpTrials];  // per layer and trial of the tile: the trial's sum (tiles only)
+  uint32_t act[kWarpTrials];                 // per trial of the tile: the layers whose trials reach it
   uint2 mq[kBatchQueue];                     // queued multi-ELT events (records)
   float wl[32];                              // a window's pair losses
   unsigned long long wm[32];                 // a window's pairs: layers holding the pair's ELT
@@ -114,42 +116,72 @@ __device__ __forceinline__ float pair_loss_batch(const BatchParams& p, const Bat
 }
 
 // Adds a layer's occurrence loss (from the event's loss sum G over the
-// layer's ELTs) to a lane's fixed-point sum.
+// layer's ELTs) to the lane's fixed-point sum for its current trial.
 __device__ __forceinline__ void add_occurrence(BatchWarp& ws, const BatchShared& bs, int layer, uint32_t lane,
-                                               float G) {
+                                               float G, uint32_t* dirty) {
   const float O = clamp_terms_f(G, bs.occ_r[layer], bs.occ_l[layer]);
-  if (O > 0.0f) ws.acc[layer][lane] += fixed_of(O, bs.sexp[layer]);
+  if (O > 0.0f) {
+    ws.acc[layer][lane] += fixed_of(O, bs.sexp[layer]);
+    *dirty |= 1u << layer;
+  }
+}
+
+// The same, straight into the trial's sum of the tile (events whose lane is
+// not tracking their trial: the multi-ELT ones).
+__device__ __forceinline__ void add_occurrence_trial(BatchWarp& ws, const BatchShared& bs, int layer, uint32_t tl,
+                                                     float G) {
+  const float O = clamp_terms_f(G, bs.occ_r[layer], bs.occ_l[layer]);
+  if (O > 0.0f) atomicAdd(&ws.tacc[layer][tl], fixed_of(O, bs.sexp[layer]));
+}
+
+// Moves the lane's sums of the layers in `dirty` into the tile's sums of
+// trial tl.
+__device__ __forceinline__ void flush_lane(BatchWarp& ws, uint32_t lane, uint32_t tl, uint32_t dirty) {
+  for (uint32_t m = dirty; m; m &= m - 1u) {
+    const int l = __ffs(m) - 1;
+    atomicAdd(&ws.tacc[l][tl], ws.acc[l][lane]);
+    ws.acc[l][lane] = 0ull;
+  }
 }
 
 // A multi-ELT event with more pairs than a window holds, by one lane: for each
 // layer it touches, its pair losses over the layer's ELTs summed in the pairs'
 // order (each pair's loss recomputed per layer: such events are rare).
+template <bool kPerTrial>
 __device__ __noinline__ void batch_long_event(const BatchParams& p, const BatchShared& bs, BatchWarp& ws, uint2 r,
-                                              int64_t trial, unsigned long long act, unsigned long long* nc) {
-  const uint32_t lane = lane_id();
+                                              int64_t ta, unsigned long long* nc) {
   const uint32_t cnt = ((r.x >> kRecCntShift) & kRecCntMask) + 1u;
   const uint32_t k = r.x & kRecKMask;
+  const uint32_t tl = r.x >> kRecTrialShift;
   unsigned long long touched = 0ull;
   for (uint32_t j = 0; j < cnt; ++j) touched |= bs.layers_of[pair_pos(p.hot[r.y + j].meta)];
-  for (unsigned long long m = touched & act; m; m &= m - 1ull) {
+  for (unsigned long long m = touched & ws.act[tl]; m; m &= m - 1ull) {
     const int l = __ffsll(m) - 1;
     float G = 0.0f;
     for (uint32_t j = 0; j < cnt; ++j)
-      if ((bs.layers_of[pair_pos(p.hot[r.y + j].meta)] >> l) & 1ull) G += pair_loss_batch(p, bs, r.y + j, trial, k, nc);
-    add_occurrence(ws, bs, l, lane, G);
+      if ((bs.layers_of[pair_pos(p.hot[r.y + j].meta)] >> l) & 1ull) G += pair_loss_batch(p, bs, r.y + j, ta + tl, k, nc);
+    if (kPerTrial) {
+      uint32_t unused = 0u;
+      add_occurrence(ws, bs, l, lane_id(), G, &unused);
+    } else {
+      add_occurrence_trial(ws, bs, l, tl, G);
+    }
   }
 }
 
-// The queued multi-ELT events of one trial, in windows of at most 32 pairs
+// The queued multi-ELT events of a tile, in windows of at most 32 pairs
 // (one per lane): each pair's loss once, then for each layer the window's
 // events touch, each event's last lane sums the event's pair losses of that
-// layer from left to right (the pairs' canonical order) and applies the
-// occurrence terms.  A left-to-right sum does not change when pairs of other
-// layers' ELTs are present, so an event's per-layer losses are the same in
-// any batch.  Only the layers in `act` (those whose trials reach this one)
-// are served; a pair of none of them is not computed.
+// layer from left to right (the pairs' canonical order), applies the
+// occurrence terms and adds the result to its trial's sum.  A left-to-right
+// sum does not change when pairs of other layers' ELTs are present, so an
+// event's per-layer losses are the same in any batch.  Only the layers that
+// reach the event's trial are served; a pair of none of them is not computed.
+// kPerTrial: all events are of one trial, and the end lanes add into their own
+// sums (no contention); else into the trial's sum of the tile.
+template <bool kPerTrial>
 __device__ __noinline__ uint32_t batch_multi(const BatchParams& p, const BatchShared& bs, BatchWarp& ws, int nq,
-                                             int64_t trial, unsigned long long act, unsigned long long* nc) {
+                                             int64_t ta, unsigned long long* nc) {
   const uint32_t q = lane_id();
   const uint32_t upto = 0xffffffffu >> (31u - q);  // lanes 0..q
   uint32_t n_pairs = 0;
@@ -158,7 +190,7 @@ __device__ __noinline__ uint32_t batch_multi(const BatchParams& p, const BatchSh
     const uint2 r = (ie < nq) ? ws.mq[ie] : make_uint2(0u, 0u);
     const uint32_t cnt = (ie < nq) ? ((r.x >> kRecCntShift) & kRecCntMask) + 1u : 0u;
     if (__shfl_sync(0xffffffffu, cnt, 0) > 32u) {  // a long event first in line: by lane 0
-      if (q == 0) batch_long_event(p, bs, ws, r, trial, act, nc);
+      if (q == 0) batch_long_event<kPerTrial>(p, bs, ws, r, ta, nc);
       n_pairs += __shfl_sync(0xffffffffu, cnt, 0);
       __syncwarp();
       ++i0;
@@ -180,11 +212,12 @@ __device__ __noinline__ uint32_t batch_multi(const BatchParams& p, const BatchSh
     const uint32_t ey = __shfl_sync(0xffffffffu, r.y, ev);
     const uint32_t epre = __shfl_sync(0xffffffffu, pre, ev);
     const uint32_t ecnt = __shfl_sync(0xffffffffu, cnt, ev);
+    const uint32_t etl = ex >> kRecTrialShift;
     float L = 0.0f;
     unsigned long long lm = 0ull;
     if (q < np) {
-      lm = bs.layers_of[pair_pos(p.hot[ey + (q - epre)].meta)] & act;
-      if (lm) L = pair_loss_batch(p, bs, ey + (q - epre), trial, ex & kRecKMask, nc);
+      lm = bs.layers_of[pair_pos(p.hot[ey + (q - epre)].meta)] & ws.act[etl];
+      if (lm) L = pair_loss_batch(p, bs, ey + (q - epre), ta + etl, ex & kRecKMask, nc);
     }
     ws.wl[q] = L;
     ws.wm[q] = lm;
@@ -200,7 +233,12 @@ __device__ __noinline__ uint32_t batch_multi(const BatchParams& p, const BatchSh
         float G = 0.0f;
         for (uint32_t j = epre; j <= q; ++j)
           if ((ws.wm[j] >> l) & 1ull) G += ws.wl[j];
-        add_occurrence(ws, bs, l, q, G);
+        if (kPerTrial) {
+          uint32_t unused = 0u;
+          add_occurrence(ws, bs, l, q, G, &unused);
+        } else {
+          add_occurrence_trial(ws, bs, l, etl, G);
+        }
       }
     }
     __syncwarp();
@@ -234,16 +272,30 @@ __device__ __forceinline__ int32_t first_record_of(const uint2* recs, int32_t n,
 
 }  // namespace
 
-// One warp per (tile, trial) item: the trial's hit-event records, one per lane
-// per round (records two rounds ahead and single-ELT hot pairs one round ahead
-// in flight); every lane keeps its own fixed-point sum per layer, so nothing is
-// shared between lanes until the item's end, where the lanes' sums of each
-// layer are added and the layer's aggregate terms give the year loss.
+// One warp per item, the item's hit-event records two per lane per round
+// (records two rounds ahead and single-ELT hot pairs one round ahead in
+// flight); every lane keeps its own fixed-point sum per layer.
+// kPerTrial = false: an item is a tile of kWarpTrials trials.  A lane's
+//   records come in trial order, so its sums are for its current trial and
+//   move into the tile's per-trial sums (shared-memory atomics) when the
+//   trial changes.  Few records per trial fill the lanes this way.
+// kPerTrial = true: an item is one trial of a tile (its records found by a
+//   warp search), and the lanes' sums are added once at the item's end.
+//   Many records per trial (many ELTs in the batch) keep the lanes busy, and
+//   the lanes do not contend for the same sums.
+// Multi-ELT events add into the per-trial sums directly.  At the item's end
+// the aggregate terms of each layer give the year losses.  Both kinds add the
+// same fixed-point numbers, so they give the same results.
+template <bool kPerTrial>
 __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_batch(const BatchParams p) {
   __shared__ BatchWarp bw[kBatchThreads / 32];
   __shared__ BatchShared bs;
+  // (one-trial items need none: a placeholder keeps the block within the shared-memory
+  // carveout that leaves L1 its room)
+  __shared__ unsigned long long tacc_all[kPerTrial ? 1 : kBatchThreads / 32][kPerTrial ? 1 : kBatchLayers][kWarpTrials];
   const uint32_t lane = lane_id();
   BatchWarp& ws = bw[threadIdx.x >> 5];
+  if (lane == 0) ws.tacc = tacc_all[kPerTrial ? 0 : threadIdx.x >> 5];
   for (int i = threadIdx.x; i < kMaxIndexElts; i += blockDim.x) {
     const bool in = i < p.n_elts;
     bs.tab[i] = in ? p.tab[i] : nullptr;
@@ -261,10 +313,13 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
     bs.t_end[i] = i < p.n_layers ? p.layer_t_end[i] : 0;
   }
   __syncthreads();
+  static_assert(kBatchLayers <= 32, "one lane per layer");
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const int64_t n_items = p.n_tiles * kWarpTrials;
+  const int nl = p.n_layers;
   unsigned long long nc = 0ull;
   uint32_t n_pairs = 0;
+  for (int l = 0; l < nl; ++l) ws.acc[l][lane] = 0ull;
+  const int64_t n_items = kPerTrial ? p.n_tiles * kWarpTrials : p.n_tiles;
 
   // items are claimed one ahead, so that the claim's latency overlaps an item's work
   unsigned long long next = 0ull;
@@ -273,22 +328,36 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
     const int64_t item = static_cast<int64_t>(__shfl_sync(0xffffffffu, next, 0));
     if (item >= n_items) break;
     if (lane == 0) next = atomicAdd(&p.counters[0], 1ull);
-    const int64_t tile = item / kWarpTrials;
-    const uint32_t tl = static_cast<uint32_t>(item % kWarpTrials);
+    const int64_t tile = kPerTrial ? item / kWarpTrials : item;
+    const uint32_t tl0 = kPerTrial ? static_cast<uint32_t>(item % kWarpTrials) : 0u;  // the item's first trial
     const int64_t ta = p.t_begin + tile * kWarpTrials;
-    const int64_t trial = ta + tl;
-    if (trial >= p.t_end) continue;
-    // the layers whose trials reach this one (all of them unless a layer ends early)
-    static_assert(kBatchLayers <= 32, "one lane per layer");
-    const unsigned long long act =
-        __ballot_sync(0xffffffffu, lane < static_cast<uint32_t>(p.n_layers) && trial < bs.t_end[lane]);
+    const int ntr = static_cast<int>((ta + kWarpTrials < p.t_end) ? kWarpTrials : p.t_end - ta);
+    if (kPerTrial && static_cast<int>(tl0) >= ntr) continue;
+    const int t_lo = static_cast<int>(tl0);  // the item's (first) trial in the tile
+    // per trial of the item, the layers whose trials reach it (all of them unless a layer ends early)
+    uint32_t any = 0u;
+#pragma unroll
+    for (int t = 0; t < kWarpTrials; ++t) {
+      if (kPerTrial && t != t_lo) continue;
+      const uint32_t a =
+          __ballot_sync(0xffffffffu, t < ntr && lane < static_cast<uint32_t>(nl) && ta + t < bs.t_end[lane]);
+      if (lane == 0) ws.act[t] = a;
+      any |= a;
+    }
+    if (!kPerTrial)
+      for (int i = static_cast<int>(lane); i < nl * kWarpTrials; i += 32) ws.tacc[i / kWarpTrials][i % kWarpTrials] = 0ull;
+    __syncwarp();
     const uint2* recs = p.ev_buf + (__ldg(&p.off[ta]) - p.e0);
-    // the trial's records [beg, end) of the tile (records are in trial order); none
-    // when no layer reaches the trial
-    const int32_t n = act ? static_cast<int32_t>(__ldg(&p.tile_cnt[tile])) : 0;
-    const int32_t beg = first_record_of(recs, n, tl, lane);
-    const int32_t end = first_record_of(recs, n, tl + 1, lane);
-    for (int l = 0; l < p.n_layers; ++l) ws.acc[l][lane] = 0ull;
+    const int32_t n_tile = any ? static_cast<int32_t>(__ldg(&p.tile_cnt[tile])) : 0;
+    // the item's records [beg, n) of the tile (records are in trial order)
+    const int32_t beg = kPerTrial ? first_record_of(recs, n_tile, tl0, lane) : 0;
+    const int32_t n = kPerTrial ? first_record_of(recs, n_tile, tl0 + 1, lane) : n_tile;
+    if (kPerTrial) {  // each lane clears its own sums (conflict-free)
+      __syncwarp();
+      for (int l = 0; l < nl; ++l) ws.acc[l][lane] = 0ull;
+    }
+    uint32_t cur = tl0, dirty = 0u;  // the lane's current trial, and the layers its sums hold
+    const uint32_t act0 = ws.act[t_lo];  // the item's layers (one trial)
     int nq = 0;
     // 64 records per round, two per lane (lane and 32 + lane), so that two table
     // reads are in flight per lane; the next round's records and single-ELT hot
@@ -298,11 +367,11 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
       const int32_t at = beg + 32 * j + static_cast<int32_t>(lane);
-      rn[j] = (at < end) ? __ldcs(recs + at) : make_uint2(0u, 0u);
+      rn[j] = (at < n) ? __ldcs(recs + at) : make_uint2(0u, 0u);
       hn[j] = PairHot{0.0f, 0.0f, kKindZero << kMetaKindShift, 0u};
-      if (at < end && ((rn[j].x >> kRecCntShift) & kRecCntMask) == 0u) hn[j] = p.hot[rn[j].y];
+      if (at < n && ((rn[j].x >> kRecCntShift) & kRecCntMask) == 0u) hn[j] = p.hot[rn[j].y];
     }
-    for (int32_t base = beg; base < end; base += 64) {
+    for (int32_t base = beg; base < n; base += 64) {
       uint2 r[2];
       PairHot h[2];
 #pragma unroll
@@ -310,26 +379,31 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
         r[j] = rn[j];
         h[j] = hn[j];
         const int32_t at = base + 64 + 32 * j + static_cast<int32_t>(lane);
-        if (at < end) rn[j] = __ldcs(recs + at);
+        if (at < n) rn[j] = __ldcs(recs + at);
       }
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int32_t at = base + 64 + 32 * j + static_cast<int32_t>(lane);
-        if (at < end && ((rn[j].x >> kRecCntShift) & kRecCntMask) == 0u) hn[j] = p.hot[rn[j].y];
+        if (at < n && ((rn[j].x >> kRecCntShift) & kRecCntMask) == 0u) hn[j] = p.hot[rn[j].y];
       }
       // ---- single-ELT events: uniform, table position, then both table reads, then the losses
       int mode[2];  // 0: none, 1: loss known (no loss / mean), 2: table, 3: Halley
       float val[2], sfrac[2];
       const float4* node[2];
+      uint32_t lmask[2];  // the layers the event serves
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const bool valid = base + 32 * j + static_cast<int32_t>(lane) < end;
+        const bool valid = base + 32 * j + static_cast<int32_t>(lane) < n;
         const uint32_t cnt = ((r[j].x >> kRecCntShift) & kRecCntMask) + 1u;
+        const uint32_t tl = kPerTrial ? tl0 : r[j].x >> kRecTrialShift;
         mode[j] = 0;
         val[j] = 0.0f;
         sfrac[j] = 0.0f;
         node[j] = nullptr;
-        if (valid && cnt == 1u && (bs.layers_of[pair_pos(h[j].meta)] & act)) {
+        lmask[j] = (valid && cnt == 1u)
+                       ? static_cast<uint32_t>(bs.layers_of[pair_pos(h[j].meta)]) & (kPerTrial ? act0 : ws.act[tl])
+                       : 0u;
+        if (lmask[j]) {
           const uint32_t kind = pair_kind(h[j].meta);
           const uint32_t pos = pair_pos(h[j].meta);
           mode[j] = 1;
@@ -339,7 +413,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
           } else if (!p.primary_only && kind_is_beta(kind)) {
             float t = 0.0f;
             if (p.newton_only || !pair_tab_exact(h[j].meta) ||
-                !batch_pair_normal(p, kind, bs.elt_id[pos], r[j].y, trial, r[j].x & kRecKMask, &t)) {
+                !batch_pair_normal(p, kind, bs.elt_id[pos], r[j].y, ta + tl, r[j].x & kRecKMask, &t)) {
               mode[j] = 3;
             } else {
               mode[j] = 2;
@@ -368,9 +442,10 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
       for (int j = 0; j < 2; ++j) {
         if (mode[j] == 0) continue;
         const uint32_t pos = pair_pos(h[j].meta);
+        const uint32_t tl = kPerTrial ? tl0 : r[j].x >> kRecTrialShift;
         float L;
         if (mode[j] == 3) {
-          L = pair_loss_slow(p, p.pairs[r[j].y], r[j].y, trial, r[j].x & kRecKMask, &nc);
+          L = pair_loss_slow(p, p.pairs[r[j].y], r[j].y, ta + tl, r[j].x & kRecKMask, &nc);
         } else {
           float loss = val[j];
           if (mode[j] == 2)
@@ -380,20 +455,26 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
                        : 0.0f;
           L = bs.share[pos] * clamp_terms_f(loss, bs.ret[pos], bs.lim[pos]);
         }
-        for (unsigned long long m = bs.layers_of[pos] & act; m; m &= m - 1ull)
-          add_occurrence(ws, bs, __ffsll(m) - 1, lane, L);
+        if constexpr (!kPerTrial) {
+          if (tl != cur) {  // the lane's records have moved on to a later trial
+            flush_lane(ws, lane, cur, dirty);
+            dirty = 0u;
+            cur = tl;
+          }
+        }
+        for (uint32_t m = lmask[j]; m; m &= m - 1u) add_occurrence(ws, bs, __ffs(m) - 1, lane, L, &dirty);
         ++n_pairs;
       }
       // ---- multi-ELT events: queued
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const bool valid = base + 32 * j + static_cast<int32_t>(lane) < end;
+        const bool valid = base + 32 * j + static_cast<int32_t>(lane) < n;
         const bool multi = valid && ((r[j].x >> kRecCntShift) & kRecCntMask) != 0u;
         const uint32_t mmask = __ballot_sync(0xffffffffu, multi);
         if (mmask) {
           if (nq + __popc(mmask) > kBatchQueue) {
             __syncwarp();
-            const uint32_t np = batch_multi(p, bs, ws, nq, trial, act, &nc);
+            const uint32_t np = batch_multi<kPerTrial>(p, bs, ws, nq, ta, &nc);
             if (lane == 0) n_pairs += np;
             nq = 0;
           }
@@ -404,16 +485,26 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
       }
     }
     if (nq > 0) {
-      const uint32_t np = batch_multi(p, bs, ws, nq, trial, act, &nc);
+      const uint32_t np = batch_multi<kPerTrial>(p, bs, ws, nq, ta, &nc);
       if (lane == 0) n_pairs += np;
     }
-    __syncwarp();
-    // ---- the trial's year loss for each layer: the lanes' sums, then the aggregate terms
-    for (int l = lane; l < p.n_layers; l += 32) {
-      unsigned long long S = 0ull;
-      for (int j = 0; j < 32; ++j) S += ws.acc[l][j];
-      const double s = __ull2double_rn(S) * p.inv_scale[l];
-      p.ylt[static_cast<int64_t>(l) * p.n_out + (trial - p.t_begin)] = clamp_terms_d(s, p.agg_r[l], p.agg_l[l]);
+    // ---- the year losses of the item's trials for each layer: the aggregate terms of the trials' sums
+    if constexpr (kPerTrial) {
+      __syncwarp();
+      for (int l = static_cast<int>(lane); l < nl; l += 32) {  // the lanes' sums, one lane per layer
+        unsigned long long S = 0ull;
+        for (int j = 0; j < 32; ++j) S += ws.acc[l][j];
+        const double sd = __ull2double_rn(S) * p.inv_scale[l];
+        p.ylt[static_cast<int64_t>(l) * p.n_out + (ta + t_lo - p.t_begin)] = clamp_terms_d(sd, p.agg_r[l], p.agg_l[l]);
+      }
+    } else {
+      flush_lane(ws, lane, cur, dirty);
+      __syncwarp();
+      for (int i = static_cast<int>(lane); i < nl * ntr; i += 32) {
+        const int l = i / ntr, t = i - l * ntr;
+        const double sd = __ull2double_rn(ws.tacc[l][t]) * p.inv_scale[l];
+        p.ylt[static_cast<int64_t>(l) * p.n_out + (ta + t - p.t_begin)] = clamp_terms_d(sd, p.agg_r[l], p.agg_l[l]);
+      }
     }
     __syncwarp();
   }
@@ -425,8 +516,11 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
   }
 }
 
-cudaError_t launch_losses_batch(const BatchParams& p, int grid, cudaStream_t s) {
-  k_losses_batch<<<grid, kBatchThreads, 0, s>>>(p);
+cudaError_t launch_losses_batch(const BatchParams& p, bool per_trial, int grid, cudaStream_t s) {
+  if (per_trial)
+    k_losses_batch<true><<<grid, kBatchThreads, 0, s>>>(p);
+  else
+    k_losses_batch<false><<<grid, kBatchThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 

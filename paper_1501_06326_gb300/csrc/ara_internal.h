@@ -209,7 +209,9 @@ struct BatchParams {
   int64_t layer_t_end[kBatchLayers];   // layer l's trials end here (<= t_end): later trials get no losses (year loss 0)
 };
 
-cudaError_t launch_losses_batch(const BatchParams& p, int grid, cudaStream_t s);
+// per_trial: one warp per trial (many hit records per trial), else one warp
+// per tile of kWarpTrials trials; the results are the same.
+cudaError_t launch_losses_batch(const BatchParams& p, bool per_trial, int grid, cudaStream_t s);
 
 size_t gather_smem_bytes(int filt_words);
 int gather_filter_words(int64_t n_words, int max_smem);
