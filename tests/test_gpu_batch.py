@@ -140,6 +140,22 @@ def test_paper_shaped_batch_sampled(eng):
         check_ylt(out[l], oracle.run_layer(yet, sub, terms, seed=0))
 
 
+def test_trial_items_and_tile_items_agree(eng):
+    # the 16-layer batch has about 320 hit records per trial (one-trial work items);
+    # each layer alone has at most about 160 (tiles of 8 trials): the same
+    # fixed-point sums, so each layer's year losses are identical bit for bit
+    spec = synth.WORKLOADS["paper-1m"]
+    yet = synth.make_yet(1200, spec["mean_events"], spec["catalogue"], spec["seed"])
+    pool = synth.make_elt_pool(64, spec["entries"], spec["catalogue"], spec["seed"] + 7)
+    layer_ids = synth.draw_layers(16, pool.elt_ids, 32, spec["seed"] + 8)
+    layers = [(ids, (50.0, 5e6, 1e4, 5e7), None) for ids in layer_ids]
+    both = _run_batch(eng, yet, pool, layers, 5)
+    for l, layer in enumerate(layers):
+        alone = _run_batch(eng, yet, pool, [layer], 5)
+        assert np.array_equal(alone[0], both[l])
+    assert np.count_nonzero(both) > both.size // 2
+
+
 def test_batch_errors(eng, small_batch):
     from paper_1501_06326_gb300 import ara
 
