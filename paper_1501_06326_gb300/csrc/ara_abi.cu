@@ -306,14 +306,13 @@ int yet_begin(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int32_
     ARA_CUDA(c, cudaMallocHost(&c->h_yet_flags, sizeof(uint32_t)));
     if ((rc = reserve(c, c->yet_flags, 16))) return rc;
   }
-  // offsets: keep a host copy (sizes and ranges are planned on the host); this
-  // also waits for the work before the call, which may still read the old YET
-  c->h_off.resize(static_cast<size_t>(n_trials) + 1);
-  ARA_CUDA(c, cudaMemcpyAsync(c->h_off.data(), offsets, sizeof(int64_t) * (n_trials + 1), cudaMemcpyDefault,
-                              c->stream));
+  // the work before the call may still read the old YET
   ARA_CUDA(c, cudaStreamSynchronize(c->stream));
-  const int64_t n_events = c->h_off[n_trials];
-  if (c->h_off[0] != 0 || n_events < 0) return fail(c, ARA_EINVAL, "%s: offsets[0] must be 0 and offsets[n] >= 0", who);
+  // the sizes first; the host copy of all offsets is taken while the upload runs
+  int64_t first = 0, n_events = 0;
+  ARA_CUDA(c, copy_params_to_host(&first, offsets, sizeof(int64_t)));
+  ARA_CUDA(c, copy_params_to_host(&n_events, offsets + n_trials, sizeof(int64_t)));
+  if (first != 0 || n_events < 0) return fail(c, ARA_EINVAL, "%s: offsets[0] must be 0 and offsets[n] >= 0", who);
   if (n_events > 0 && !event_ids) return fail(c, ARA_EINVAL, "%s: event_ids is NULL", who);
   if ((rc = reserve(c, c->yet_off, sizeof(int64_t) * (n_trials + 1)))) return rc;
   // ids: padded by 4 entries so that 16-byte loads near the end stay inside the buffer
@@ -336,6 +335,9 @@ int yet_begin(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int32_
   c->launches += 1 + (n_events > 0 ? 1 : 0);
   ARA_CUDA(c, cudaMemcpyAsync(c->h_yet_flags, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, cs));
   ARA_CUDA(c, cudaEventRecord(c->yet_ready, cs));
+  // offsets: keep a host copy (sizes and ranges are planned on the host)
+  c->h_off.resize(static_cast<size_t>(n_trials) + 1);
+  ARA_CUDA(c, copy_params_to_host(c->h_off.data(), offsets, sizeof(int64_t) * (n_trials + 1)));
   int64_t longest = 0;  // bounds a trial's sum in the batched layers' fixed point
   for (int64_t t = 0; t < n_trials; ++t) longest = std::max(longest, c->h_off[t + 1] - c->h_off[t]);
   c->p_trials = n_trials;
