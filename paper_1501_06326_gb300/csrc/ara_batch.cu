@@ -6,10 +6,10 @@
 // computed once and serves every layer of the batch that holds the ELT.  Per
 // layer, the event's losses over the layer's ELTs are summed (Algorithm 1),
 // the occurrence terms applied, and the occurrence loss is added to the
-// layer's sum for the trial: a 64-bit fixed-point integer, so that the sum is
-// exact for the FP32 occurrence losses and independent of the order of the
-// (atomic) additions.  The aggregate terms of each layer then give its year
-// losses.
+// layer's sum for the trial: a 64-bit fixed-point integer (each loss rounded
+// to the layer's unit, 2^-61 of its largest possible trial sum), so that the
+// sum is exact in those units and independent of the order of the (atomic)
+// additions.  The aggregate terms of each layer then give its year losses.
 #include <cuda_runtime.h>
 
 #include <cstdint>
