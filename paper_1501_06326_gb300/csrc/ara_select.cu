@@ -292,14 +292,30 @@ __global__ void k_sel_compact(const double* ylt, int64_t n, const SelScratch* sc
     mask[r] = r < g ? sc->st[r].mask : 0ull;
     top[r] = r < g ? (prefix[r] | ~mask[r]) : ~0ull;  // the bucket's largest key
   }
-  if (threadIdx.x < static_cast<unsigned int>(g)) {
-    const int r = threadIdx.x;
-    const unsigned int d = static_cast<unsigned int>(prefix[r] >> 48) & 255u;
-    unsigned int off = 0;
-    for (unsigned int b = 0; b < blockIdx.x; ++b) off += sf->blk_hist[b][r][d];
-    s_off[r] = off;
+  {
+    // this block's first candidate per period: the bucket counts of the blocks
+    // before it, summed by the whole block (one earlier block per thread)
+    unsigned int part[kSelGroup];
+#pragma unroll
+    for (int r = 0; r < kSelGroup; ++r) part[r] = 0u;
+    for (unsigned int b = threadIdx.x; b < blockIdx.x; b += blockDim.x) {
+#pragma unroll
+      for (int r = 0; r < kSelGroup; ++r)
+        if (r < g) part[r] += sf->blk_hist[b][r][static_cast<unsigned int>(prefix[r] >> 48) & 255u];
+    }
+#pragma unroll
+    for (int r = 0; r < kSelGroup; ++r) {
+      const unsigned int w = __reduce_add_sync(0xffffffffu, part[r]);
+      if (lane == 0) s_wcnt[warp][r] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < static_cast<unsigned int>(g)) {
+      unsigned int off = 0;
+      for (int w = 0; w < kSelThreads / 32; ++w) off += s_wcnt[w][threadIdx.x];
+      s_off[threadIdx.x] = off;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t span = stride * kSelUnroll;
   const int64_t n_round = ((n + span - 1) / span) * span;
