@@ -314,6 +314,14 @@ def test_async_yet_load(eng, plain_1k):
     with pytest.raises(ara.AraError) as e:
         eng.load_yet_async(yet.offsets, yet.event_ids, 0)
     assert e.value.code == ara.ARA_EINVAL
+    # a served request after an upload in flight: the submit waits for it, and the
+    # result is the one after the synchronous load
+    rps = np.array([10.0, 50.0])
+    eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
+    sync_res = eng.wait(eng.submit(pool.elt_ids, terms, 3, yet.n_trials, rps), len(rps))
+    eng.load_yet_async(off_h, ids_h, yet.catalogue_size)
+    async_res = eng.wait(eng.submit(pool.elt_ids, terms, 3, yet.n_trials, rps), len(rps))
+    assert np.array_equal(sync_res[0], async_res[0]) and np.array_equal(sync_res[1], async_res[1])
     eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
 
 
