@@ -407,7 +407,7 @@ static int load_elts_impl(ara_ctx* c, const char* who, int32_t n_elts, const int
     work_off[i + 1] = work_off[i] + static_cast<int64_t>(ara::build_tables_work_words(n));
   }
   const size_t in_bytes =
-      static_cast<size_t>(R) * (sizeof(int32_t) + 4 * sizeof(float) + sizeof(double2) + sizeof(float2)) + 64;
+      static_cast<size_t>(R) * (sizeof(int32_t) + 4 * sizeof(float) + sizeof(ara::BetaShape) + sizeof(float2)) + 64;
   if ((rc = reserve(c, c->elt_stage, in_bytes)) ||
       (rc = reserve(c, c->elt_recs_stage, sizeof(ara::Pair) * (R + 1))) ||
       (rc = reserve(c, c->elt_tab_stage, sizeof(float4) * ara::kTabNodes * (R + 1))) ||
@@ -421,7 +421,8 @@ static int load_elts_impl(ara_ctx* c, const char* who, int32_t n_elts, const int
   float* d_sg = d_mu + R;
   float* d_ex = d_sg + R;
   float* d_sc = d_ex + R;
-  double2* d_shapes = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(d_sc + R) + 15) & ~uintptr_t(15));
+  ara::BetaShape* d_shapes =
+      reinterpret_cast<ara::BetaShape*>((reinterpret_cast<uintptr_t>(d_sc + R) + 15) & ~uintptr_t(15));
   float2* d_w = reinterpret_cast<float2*>(d_shapes + R);
   ara::Pair* d_recs = static_cast<ara::Pair*>(c->elt_recs_stage.ptr);
   float4* d_tab = static_cast<float4*>(c->elt_tab_stage.ptr);
@@ -1342,7 +1343,7 @@ int ara_debug_record_losses(ara_ctx* c, int64_t n, const float* mean, const floa
   if (n >= static_cast<int64_t>(ara::kMaxEltRecords))
     return fail(c, ARA_EINVAL, "ara_debug_record_losses: at most %u records per call", ara::kMaxEltRecords - 1);
   const size_t bytes = static_cast<size_t>(n) * (sizeof(ara::Pair) + 6 * sizeof(float) + sizeof(int32_t) +
-                                                 sizeof(double2) + sizeof(float4) * ara::kTabNodes) +
+                                                 sizeof(ara::BetaShape) + sizeof(float4) * ara::kTabNodes) +
                        sizeof(float4) * ara::kTabFineStride * (ara::fine_table_cap(n) + 1) +
                        sizeof(uint32_t) * ara::build_tables_work_words(n) + 256;
   if ((rc = reserve(c, tmp, bytes))) return rc;
@@ -1354,7 +1355,8 @@ int ara_debug_record_losses(ara_ctx* c, int64_t n, const float* mean, const floa
   float* d_o = d_z + n;
   int32_t* d_ev = reinterpret_cast<int32_t*>(d_o + n);
   int32_t* d_it = d_ev + n;
-  double2* d_sh = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(d_it + n) + 15) & ~uintptr_t(15));
+  ara::BetaShape* d_sh =
+      reinterpret_cast<ara::BetaShape*>((reinterpret_cast<uintptr_t>(d_it + n) + 15) & ~uintptr_t(15));
   float4* d_tab = reinterpret_cast<float4*>(d_sh + n);
   float4* d_tabf = d_tab + n * ara::kTabNodes;
   uint32_t* d_work = reinterpret_cast<uint32_t*>(d_tabf + ara::kTabFineStride * (ara::fine_table_cap(n) + 1));

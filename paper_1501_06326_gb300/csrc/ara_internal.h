@@ -21,6 +21,12 @@ enum : uint32_t {
   kHasCorrelated = 64u,  // not an error: an ELT holds a record with sigma_C > 0
 };
 
+// A record's Beta shapes in FP64 and ln B(a, b), computed once when the
+// record is prepared (the table builds read them on every node).
+struct __align__(16) BetaShape {
+  double a, b, lnB, pad;
+};
+
 cudaError_t launch_check_offsets(const int64_t* off, int64_t n_trials, int64_t n_events, uint32_t* flags,
                                  cudaStream_t s);
 cudaError_t launch_check_ids(const int32_t* ids, int64_t n, int32_t catalogue, uint32_t* flags, cudaStream_t s);
@@ -36,7 +42,7 @@ cudaError_t launch_upload_ids(const int32_t* src, int32_t* dst, int64_t n, int32
 // record can produce (max(exposure, mean) over records with a loss, as FP32
 // bits) into *max_loss (both atomicMax; max_loss may be null).
 cudaError_t launch_prepare_records(const int32_t* events, const float* mean, const float* sigma,
-                                   const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
+                                   const float* exposure, int64_t n, Pair* out, BetaShape* shapes, uint32_t* flags,
                                    int32_t* max_event, uint32_t* max_loss, cudaStream_t s,
                                    const float* sigma_c = nullptr, float2* weights = nullptr);
 
@@ -48,14 +54,14 @@ cudaError_t launch_prepare_records(const int32_t* events, const float* mean, con
 // candidates for fine tables (min(work[n], cap) slots are used).
 size_t build_tables_work_words(int64_t n);
 uint32_t fine_table_cap(int64_t n);
-cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, float4* tabf,
+cudaError_t launch_build_tables(Pair* recs, const BetaShape* shapes, int64_t n, float4* tab, float4* tabf,
                                 uint32_t* work, cudaStream_t s, int* n_launch);
 // The two halves of launch_build_tables: coarse tables of n records (need[rec]
 // = 1 marks a candidate for a fine table; one launch may span several ELTs),
 // then the fine tables of one ELT (`work`: build_tables_work_words(n) words).
-cudaError_t launch_build_coarse(Pair* recs, const double2* shapes, int64_t n, float4* tab, uint32_t* need,
+cudaError_t launch_build_coarse(Pair* recs, const BetaShape* shapes, int64_t n, float4* tab, uint32_t* need,
                                 cudaStream_t s);
-cudaError_t launch_build_fine(Pair* recs, const double2* shapes, int64_t n, const uint32_t* need, float4* tabf,
+cudaError_t launch_build_fine(Pair* recs, const BetaShape* shapes, int64_t n, const uint32_t* need, float4* tabf,
                               uint32_t* work, cudaStream_t s, int* n_launch);
 // Fine tables of several ELTs in one launch: job i covers records
 // [rec_begin, rec_begin + n) whose candidates were scanned into `slot` (n + 1
@@ -67,7 +73,7 @@ struct FineJob {
   int64_t slot_begin;
   uint32_t cap, pad;
 };
-cudaError_t launch_build_fine_jobs(Pair* recs, const double2* shapes, const FineJob* jobs, int n_jobs,
+cudaError_t launch_build_fine_jobs(Pair* recs, const BetaShape* shapes, const FineJob* jobs, int n_jobs,
                                    int64_t total_slots, float4* tabf, cudaStream_t s);
 
 // Check kernels (device functions of the hot path on given inputs).

@@ -259,7 +259,7 @@ __device__ double beta_cf_f64(double a, double b, double x) {
 // with weights (sigma_I, sigma_C) / sqrt(sigma_I^2 + sigma_C^2) for the
 // combination of its two normal variables.
 __global__ void k_prepare_records(const int32_t* events, const float* mean, const float* sigma,
-                                  const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
+                                  const float* exposure, int64_t n, Pair* out, BetaShape* shapes, uint32_t* flags,
                                   int32_t* max_event, uint32_t* max_loss, const float* sigma_c, float2* weights) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   uint32_t f = 0;
@@ -278,7 +278,7 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
     p.max_l = static_cast<float>(ex);
     p.mu = static_cast<float>(mu);
     uint32_t kind = kKindBeta;
-    double sa = 0.0, sb_ = 0.0;
+    double sa = 0.0, sb_ = 0.0, slnb = 0.0;
     float2 w = make_float2(1.0f, 0.0f);
     if (!(mu >= 0.0) || !(si >= 0.0) || !(sc >= 0.0) || !isfinite(mu) || !isfinite(sg) || !isfinite(ex)) {
       f |= kBadValue;
@@ -311,6 +311,7 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
       p.b = static_cast<float>(b);
       sa = a;
       sb_ = b;
+      slnb = lnB;
       p.m0 = (x0 <= y0) ? -static_cast<float>(x0) : static_cast<float>(y0);
       p.c = static_cast<float>(c);
       p.p_half = static_cast<float>(ph);
@@ -324,7 +325,7 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
     p.meta = (kind << kMetaKindShift) | (static_cast<uint32_t>(i) << kMetaRecShift);
     if (kind != kKindZero) lmax = fmaxf(lmax, fmaxf(p.max_l, p.mu));
     out[i] = p;
-    if (shapes) shapes[i] = make_double2(sa, sb_);
+    if (shapes) shapes[i] = BetaShape{sa, sb_, slnb, 0.0};
     if (weights) weights[i] = w;
   }
   if (f) atomicOr(flags, f);
@@ -339,7 +340,7 @@ __global__ void k_prepare_records(const int32_t* events, const float* mean, cons
 }
 
 cudaError_t launch_prepare_records(const int32_t* events, const float* mean, const float* sigma,
-                                   const float* exposure, int64_t n, Pair* out, double2* shapes, uint32_t* flags,
+                                   const float* exposure, int64_t n, Pair* out, BetaShape* shapes, uint32_t* flags,
                                    int32_t* max_event, uint32_t* max_loss, cudaStream_t s, const float* sigma_c,
                                    float2* weights) {
   if (n == 0) return cudaSuccess;
@@ -492,7 +493,7 @@ __device__ bool table_segment_ok(float4 nd, float d1, float e1, double t, double
 // Coarse tables, one warp per record, lane j = node j at t_j = -T1 + j h.  The
 // stored float4 is {x_j, w_{j+1} - w_j, h w'_j, h^2 w''_j}.  need[rec] = 1 for
 // a Beta record whose coarse table is not exact (a candidate for a fine table).
-__global__ void __launch_bounds__(256, 2) k_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab,
+__global__ void __launch_bounds__(256, 2) k_build_tables(Pair* recs, const BetaShape* shapes, int64_t n, float4* tab,
                                                         uint32_t* need) {
   const int lane = threadIdx.x & 31;
   const int64_t rec = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -504,8 +505,7 @@ __global__ void __launch_bounds__(256, 2) k_build_tables(Pair* recs, const doubl
     if (lane == 0) need[rec] = 0u;
     return;
   }
-  const double a = shapes[rec].x, b = shapes[rec].y;
-  const double lnB = lgamma(a) + lgamma(b) - lgamma(a + b);
+  const double a = shapes[rec].a, b = shapes[rec].b, lnB = shapes[rec].lnB;
   const double h = 2.0 * kTabT1 / (kTabNodes - 1);
   const double t = -kTabT1 + h * lane;
   double w;
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(256, 2) k_build_tables(Pair* recs, const doubl
 // t_j = -T1 + j h / kTabRefine.  The record's meta then addresses its fine
 // table (by the ELT-local slot); it is table-exact if the fine table passes
 // the check.
-__global__ void __launch_bounds__(kTabFineStride) k_build_fine(Pair* recs, const double2* shapes,
+__global__ void __launch_bounds__(kTabFineStride) k_build_fine(Pair* recs, const BetaShape* shapes,
                                                               const FineJob* jobs, int n_jobs, float4* tabf) {
   __shared__ double s_w[kTabFineStride];
   __shared__ float4 s_node[kTabFineStride];
@@ -562,8 +562,7 @@ __global__ void __launch_bounds__(kTabFineStride) k_build_fine(Pair* recs, const
   if (rec < 0) return;
   const uint32_t ls = s_ls;
   const Pair pr = recs[rec];
-  const double a = shapes[rec].x, b = shapes[rec].y;
-  const double lnB = lgamma(a) + lgamma(b) - lgamma(a + b);
+  const double a = shapes[rec].a, b = shapes[rec].b, lnB = shapes[rec].lnB;
   const double h = 2.0 * kTabT1 / (kTabFineNodes - 1);
   const int j = threadIdx.x;
   const double t = -kTabT1 + h * (j < kTabFineNodes ? j : kTabFineNodes - 1);
@@ -597,7 +596,7 @@ uint32_t fine_table_cap(int64_t n) {
   return static_cast<uint32_t>(cap < n ? cap : n);
 }
 
-cudaError_t launch_build_coarse(Pair* recs, const double2* shapes, int64_t n, float4* tab, uint32_t* need,
+cudaError_t launch_build_coarse(Pair* recs, const BetaShape* shapes, int64_t n, float4* tab, uint32_t* need,
                                 cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int64_t blocks = (n + 7) / 8;  // 8 warps (records) per block
@@ -606,7 +605,7 @@ cudaError_t launch_build_coarse(Pair* recs, const double2* shapes, int64_t n, fl
   return cudaGetLastError();
 }
 
-cudaError_t launch_build_fine_jobs(Pair* recs, const double2* shapes, const FineJob* jobs, int n_jobs,
+cudaError_t launch_build_fine_jobs(Pair* recs, const BetaShape* shapes, const FineJob* jobs, int n_jobs,
                                    int64_t total_slots, float4* tabf, cudaStream_t s) {
   if (n_jobs == 0 || total_slots == 0) return cudaSuccess;
   k_build_fine<<<static_cast<int>(total_slots), kTabFineStride, 0, s>>>(recs, shapes, jobs, n_jobs, tabf);
@@ -615,7 +614,7 @@ cudaError_t launch_build_fine_jobs(Pair* recs, const double2* shapes, const Fine
 
 // One ELT: its scan, then its fine tables (a one-job launch; the job record
 // sits after the scan's scratch in `work`).
-cudaError_t launch_build_fine(Pair* recs, const double2* shapes, int64_t n, const uint32_t* need, float4* tabf,
+cudaError_t launch_build_fine(Pair* recs, const BetaShape* shapes, int64_t n, const uint32_t* need, float4* tabf,
                               uint32_t* work, cudaStream_t s, int* n_launch) {
   if (n == 0) return cudaSuccess;
   int launched = 0;
@@ -631,7 +630,7 @@ cudaError_t launch_build_fine(Pair* recs, const double2* shapes, int64_t n, cons
   return cudaSuccess;
 }
 
-cudaError_t launch_build_tables(Pair* recs, const double2* shapes, int64_t n, float4* tab, float4* tabf,
+cudaError_t launch_build_tables(Pair* recs, const BetaShape* shapes, int64_t n, float4* tab, float4* tabf,
                                 uint32_t* work, cudaStream_t s, int* n_launch) {
   if (n == 0) return cudaSuccess;
   cudaError_t err = launch_build_coarse(recs, shapes, n, tab, work, s);
