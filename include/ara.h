@@ -174,11 +174,13 @@ ARA_API int ara_load_yet(ara_ctx *ctx, int64_t n_trials, const int64_t *offsets,
  * sizes checked during the call (the call first waits for the work already on
  * the context's stream); the offsets and ids are then copied to the device
  * and checked on an internal stream, beside later work on the context's
- * stream, so that an ELT load (its table build) overlaps the copy.  offsets
- * and event_ids stay owned by the caller and must stay valid and unchanged
- * until the upload is finished: by ara_finish_yet or by the next call that
- * uses the YET (ara_run_layer*, ara_submit, ara_serve, ...), which waits for
- * it.  Errors in the offsets or ids are returned by that call (ARA_EINVAL,
+ * stream, so that an ELT load (its table build) overlaps the copy.  Ids in
+ * pinned host memory are read by a kernel over the host link, which leaves
+ * the copy engine to the other streams' copies; other ids are copied by the
+ * copy engine.  offsets and event_ids stay owned by the caller and must stay
+ * valid and unchanged until the upload is finished: by ara_finish_yet or by
+ * the next call that uses the YET (ara_run_layer*, ara_submit,
+ * ara_serve_step, ...), which waits for it.  Errors in the offsets or ids are returned by that call (ARA_EINVAL,
  * with no YET loaded); errors in the arguments by this one.  A second upload
  * replaces one still in flight. */
 ARA_API int ara_load_yet_async(ara_ctx *ctx, int64_t n_trials, const int64_t *offsets, const int32_t *event_ids,
