@@ -335,9 +335,14 @@ int yet_begin(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int32_
   c->launches += 1 + (n_events > 0 ? 1 : 0);
   ARA_CUDA(c, cudaMemcpyAsync(c->h_yet_flags, flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, cs));
   ARA_CUDA(c, cudaEventRecord(c->yet_ready, cs));
-  // offsets: keep a host copy (sizes and ranges are planned on the host)
+  // offsets: keep a host copy (sizes and ranges are planned on the host); on an
+  // error the upload just started is waited for, so that nothing is left in flight
   c->h_off.resize(static_cast<size_t>(n_trials) + 1);
-  ARA_CUDA(c, copy_params_to_host(c->h_off.data(), offsets, sizeof(int64_t) * (n_trials + 1)));
+  const cudaError_t he = copy_params_to_host(c->h_off.data(), offsets, sizeof(int64_t) * (n_trials + 1));
+  if (he != cudaSuccess) {
+    cudaEventSynchronize(c->yet_ready);
+    return fail(c, ARA_ECUDA, "%s: copy of the offsets: %s", who, cudaGetErrorString(he));
+  }
   int64_t longest = 0;  // bounds a trial's sum in the batched layers' fixed point
   for (int64_t t = 0; t < n_trials; ++t) longest = std::max(longest, c->h_off[t + 1] - c->h_off[t]);
   c->p_trials = n_trials;
