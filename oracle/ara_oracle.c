@@ -346,6 +346,120 @@ static uint64_t mix64(uint64_t v)
     return v;
 }
 
+/* The layer's records as a direct-access table, row_of[j * C + e] = the  */
+/* record of event e in the layer's j-th ELT, or -1 (Section 4.2 keeps the  */
+/* ELTs as direct-access tables too).  NULL on a bad event id or no memory. */
+static int32_t *direct_access_rows(int32_t catalogue, int32_t n_elts, const int64_t *rec_offsets,
+                                   const int32_t *rec_events, int *status)
+{
+    int32_t *row_of;
+    int64_t j, e;
+    row_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)catalogue * (size_t)(n_elts > 0 ? n_elts : 1));
+    if (!row_of) { *status = -2; return NULL; }
+    for (j = 0; j < (int64_t)catalogue * n_elts; ++j) row_of[j] = -1;
+    for (j = 0; j < n_elts; ++j)
+        for (e = rec_offsets[j]; e < rec_offsets[j + 1]; ++e) {
+            int32_t ev = rec_events[e];
+            if (ev < 0 || ev >= catalogue) { free(row_of); *status = -3; return NULL; }
+            row_of[j * (int64_t)catalogue + ev] = (int32_t)e;
+        }
+    *status = 0;
+    return row_of;
+}
+
+/* What one trial's year loss depends on: the layer (its ELT records and   */
+/* terms) and the draw (seed, primary-only switch).                         */
+typedef struct {
+    int32_t catalogue, n_elts;
+    const int32_t *row_of, *elt_pool_ids;
+    const float *mean, *sigma, *sigma_c, *exposure, *elt_terms;
+    double occ_ret, occ_lim, agg_ret, agg_lim;
+    uint64_t seed;
+    int primary_only;
+} layer_def;
+
+/* Per-trial by-products: the gross loss (sum of the sampled record losses  */
+/* before any terms), the number of (event occurrence, ELT record) pairs   */
+/* and an order-free hash of them.                                          */
+typedef struct {
+    double gross;
+    int64_t hits;
+    uint64_t hash;
+} trial_extras;
+
+/* The loss of event occurrence k (event id ev) of trial t combined over    */
+/* the layer's ELTs, before the occurrence terms.  Section 2.2: each ELT's   */
+/* loss for the event, after that ELT's financial terms, summed over the     */
+/* ELTs of the layer; an ELT without a record for the event contributes     */
+/* nothing.  Section 3.3: the loss of a record is the secondary-uncertainty */
+/* draw, taken before the financial terms act on it.                         */
+static double combined_event_loss(const layer_def *L, int64_t t, int32_t k, int32_t ev, trial_extras *x)
+{
+    double combined = 0.0;
+    int32_t j;
+    for (j = 0; j < L->n_elts; ++j) {
+        int32_t r = L->row_of[(int64_t)j * L->catalogue + ev];
+        double sampled;
+        if (r < 0) continue;
+        sampled = record_loss(L->mean[r], L->sigma[r], L->sigma_c ? L->sigma_c[r] : 0.0f, L->exposure[r],
+                              L->primary_only, L->seed, t, k, L->elt_pool_ids[j]);
+        x->gross += sampled;
+        x->hits += 1;
+        x->hash += mix64(((uint64_t)(uint32_t)k << 32) | (uint32_t)L->elt_pool_ids[j]);
+        combined += L->elt_terms
+                        ? (double)L->elt_terms[3 * j + 2] *
+                              clamp_terms(sampled, L->elt_terms[3 * j + 0], L->elt_terms[3 * j + 1])
+                        : sampled;
+    }
+    return combined;
+}
+
+/* The year loss of trial t (Section 2.2 and the YLT of Section 2.3): the    */
+/* occurrence terms act on each event's combined loss; the aggregate terms   */
+/* act on the running total of the occurrence losses, taken in the trial's  */
+/* event (time) order; the value after the last event is the year loss, 0   */
+/* for a trial without events.                                               */
+static double trial_year_loss(const layer_def *L, const int64_t *offsets, const int32_t *ids, int64_t t,
+                              trial_extras *x)
+{
+    double running = 0.0, after_aggregate = 0.0;
+    int64_t pos;
+    x->gross = 0.0;
+    x->hits = 0;
+    x->hash = 0;
+    for (pos = offsets[t]; pos < offsets[t + 1]; ++pos) {
+        int32_t k = (int32_t)(pos - offsets[t]);
+        double occurrence = clamp_terms(combined_event_loss(L, t, k, ids[pos], x), L->occ_ret, L->occ_lim);
+        running += occurrence;
+        after_aggregate = clamp_terms(running, L->agg_ret, L->agg_lim);
+    }
+    return after_aggregate;
+}
+
+static void set_layer_def(layer_def *L, const int32_t *row_of, int32_t catalogue, int32_t n_elts,
+                          const int32_t *elt_pool_ids, const float *mean, const float *sigma, const float *sigma_c,
+                          const float *exposure, const float *elt_terms, double occ_ret, double occ_lim,
+                          double agg_ret, double agg_lim, uint64_t seed, int primary_only)
+{
+    L->row_of = row_of;
+    L->catalogue = catalogue;
+    L->n_elts = n_elts;
+    L->elt_pool_ids = elt_pool_ids;
+    L->mean = mean;
+    L->sigma = sigma;
+    L->sigma_c = sigma_c;
+    L->exposure = exposure;
+    L->elt_terms = elt_terms;
+    L->occ_ret = occ_ret;
+    L->occ_lim = occ_lim;
+    L->agg_ret = agg_ret;
+    L->agg_lim = agg_lim;
+    L->seed = seed;
+    L->primary_only = primary_only;
+}
+
+/* The YLT of one layer over a list of trials (all trials when `trials` is */
+/* NULL), with the per-trial by-products above (each output optional).     */
 int or_run_layer(int64_t n_trials, const int64_t *offsets, const int32_t *ids, int32_t catalogue,
                  int32_t n_elts, const int32_t *elt_pool_ids, const int64_t *rec_offsets,
                  const int32_t *rec_events, const float *rec_mean, const float *rec_sigma,
@@ -356,18 +470,15 @@ int or_run_layer(int64_t n_trials, const int64_t *offsets, const int32_t *ids, i
                  int64_t n_list, const int64_t *trials,
                  double *ylt, double *gross, int64_t *n_hits, uint64_t *hit_hash, int n_threads)
 {
-    int32_t *row_of; /* direct-access table: row_of[j * C + e] = record index or -1 */
-    int64_t j, e, n_eval;
+    layer_def L;
+    int status;
+    int32_t *row_of;
+    int64_t n_eval;
     if (catalogue <= 0 || n_elts < 0) return -1;
-    row_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)catalogue * (size_t)(n_elts > 0 ? n_elts : 1));
-    if (!row_of) return -2;
-    for (j = 0; j < (int64_t)catalogue * n_elts; ++j) row_of[j] = -1;
-    for (j = 0; j < n_elts; ++j)
-        for (e = rec_offsets[j]; e < rec_offsets[j + 1]; ++e) {
-            int32_t ev = rec_events[e];
-            if (ev < 0 || ev >= catalogue) { free(row_of); return -3; }
-            row_of[j * (int64_t)catalogue + ev] = (int32_t)e;
-        }
+    row_of = direct_access_rows(catalogue, n_elts, rec_offsets, rec_events, &status);
+    if (!row_of) return status;
+    set_layer_def(&L, row_of, catalogue, n_elts, elt_pool_ids, rec_mean, rec_sigma, rec_sigma_c, rec_exposure,
+                  elt_terms, occ_ret, occ_lim, agg_ret, agg_lim, seed, primary_only);
     n_eval = trials ? n_list : n_trials;
     {
         int64_t i;
@@ -379,39 +490,12 @@ int or_run_layer(int64_t n_trials, const int64_t *offsets, const int32_t *ids, i
         (void)n_threads;
 #endif
         for (i = 0; i < n_eval; ++i) {
-            int64_t t = trials ? trials[i] : i;
-            int64_t first = offsets[t], last = offsets[t + 1], pos;
-            double S = 0.0, A = 0.0, G_sum = 0.0;
-            int64_t hits = 0;
-            uint64_t hh = 0;
-            for (pos = first; pos < last; ++pos) {               /* each Event E in T */
-                int32_t k = (int32_t)(pos - first);
-                int32_t ev = ids[pos];
-                double l_T = 0.0, O;
-                int32_t jj;
-                for (jj = 0; jj < n_elts; ++jj) {                 /* each ELT covered by L */
-                    int32_t r = row_of[(int64_t)jj * catalogue + ev]; /* lookup E in the ELT */
-                    double l_E;
-                    if (r < 0) continue;                          /* no record: zero loss */
-                    ++hits;
-                    hh += mix64(((uint64_t)(uint32_t)k << 32) | (uint32_t)elt_pool_ids[jj]);
-                    l_E = record_loss(rec_mean[r], rec_sigma[r], rec_sigma_c ? rec_sigma_c[r] : 0.0f,
-                                      rec_exposure[r], primary_only, seed, t, k,
-                                      elt_pool_ids[jj]);               /* secondary uncertainty */
-                    G_sum += l_E;
-                    if (elt_terms)                                 /* ELT financial terms */
-                        l_E = (double)elt_terms[3 * jj + 2] *
-                              clamp_terms(l_E, elt_terms[3 * jj + 0], elt_terms[3 * jj + 1]);
-                    l_T += l_E;                                    /* sum over ELTs */
-                }
-                O = clamp_terms(l_T, occ_ret, occ_lim);            /* occurrence terms */
-                S += O;                                            /* cumulative occurrence loss */
-                A = clamp_terms(S, agg_ret, agg_lim);              /* aggregate terms */
-            }
-            ylt[i] = A;                                            /* populate the YLT */
-            if (gross) gross[i] = G_sum;
-            if (n_hits) n_hits[i] = hits;
-            if (hit_hash) hit_hash[i] = hh;
+            trial_extras x;
+            double y = trial_year_loss(&L, offsets, ids, trials ? trials[i] : i, &x);
+            ylt[i] = y;
+            if (gross) gross[i] = x.gross;
+            if (n_hits) n_hits[i] = x.hits;
+            if (hit_hash) hit_hash[i] = x.hash;
         }
     }
     free(row_of);
@@ -436,45 +520,35 @@ int64_t or_run_layer_events(const int64_t *offsets, const int32_t *ids, int32_t 
                             int64_t *row_trial, int32_t *row_k, int32_t *row_event, double *row_occ,
                             double *row_inc, int64_t cap, double *max_occ)
 {
+    layer_def L;
+    int status;
     int32_t *row_of;
-    int64_t j, e, t, n = 0;
-    row_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)catalogue * (size_t)(n_elts > 0 ? n_elts : 1));
-    if (!row_of) return -2;
-    for (j = 0; j < (int64_t)catalogue * n_elts; ++j) row_of[j] = -1;
-    for (j = 0; j < n_elts; ++j)
-        for (e = rec_offsets[j]; e < rec_offsets[j + 1]; ++e) row_of[j * (int64_t)catalogue + rec_events[e]] = (int32_t)e;
+    int64_t t, n = 0;
+    if (catalogue <= 0 || n_elts < 0) return -3;
+    row_of = direct_access_rows(catalogue, n_elts, rec_offsets, rec_events, &status);
+    if (!row_of) return status == -2 ? -2 : -3;
+    set_layer_def(&L, row_of, catalogue, n_elts, elt_pool_ids, rec_mean, rec_sigma, rec_sigma_c, rec_exposure,
+                  elt_terms, occ_ret, occ_lim, agg_ret, agg_lim, seed, primary_only);
     for (t = t_begin; t < t_end; ++t) {
-        double S = 0.0, A = 0.0, O_max = 0.0;
+        double running = 0.0, before = 0.0, O_max = 0.0;
         int64_t pos;
         for (pos = offsets[t]; pos < offsets[t + 1]; ++pos) {
             int32_t k = (int32_t)(pos - offsets[t]);
-            double l_T = 0.0, O, A_new;
-            int held = 0;
-            int32_t jj;
-            for (jj = 0; jj < n_elts; ++jj) {
-                int32_t r = row_of[(int64_t)jj * catalogue + ids[pos]];
-                double l_E;
-                if (r < 0) continue;
-                held = 1;
-                l_E = record_loss(rec_mean[r], rec_sigma[r], rec_sigma_c ? rec_sigma_c[r] : 0.0f, rec_exposure[r],
-                                  primary_only, seed, t, k, elt_pool_ids[jj]);
-                if (elt_terms)
-                    l_E = (double)elt_terms[3 * jj + 2] * clamp_terms(l_E, elt_terms[3 * jj + 0], elt_terms[3 * jj + 1]);
-                l_T += l_E;
-            }
-            if (!held) continue;
-            O = clamp_terms(l_T, occ_ret, occ_lim);
-            S += O;
-            A_new = clamp_terms(S, agg_ret, agg_lim);
+            trial_extras x = {0.0, 0, 0};
+            double occurrence = clamp_terms(combined_event_loss(&L, t, k, ids[pos], &x), occ_ret, occ_lim);
+            double after;
+            if (x.hits == 0) continue; /* no ELT of the layer holds the event: no row */
+            running += occurrence;
+            after = clamp_terms(running, agg_ret, agg_lim);
             if (n >= cap) { free(row_of); return -1; }
             row_trial[n] = t;
             row_k[n] = k;
             row_event[n] = ids[pos];
-            row_occ[n] = O;
-            row_inc[n] = A_new - A;
+            row_occ[n] = occurrence;
+            row_inc[n] = after - before;
             ++n;
-            A = A_new;
-            if (O > O_max) O_max = O;
+            before = after;
+            if (occurrence > O_max) O_max = occurrence;
         }
         if (max_occ) max_occ[t - t_begin] = O_max;
     }
@@ -493,32 +567,23 @@ int64_t or_event_losses(const int64_t *offsets, const int32_t *ids, int32_t cata
                         uint64_t seed, int primary_only, int64_t t_begin, int64_t t_end,
                         double *out, int64_t cap)
 {
+    layer_def L;
+    int status;
     int32_t *row_of;
-    int64_t j, e, t, n = 0;
-    row_of = (int32_t *)malloc(sizeof(int32_t) * (size_t)catalogue * (size_t)(n_elts > 0 ? n_elts : 1));
-    if (!row_of) return -2;
-    for (j = 0; j < (int64_t)catalogue * n_elts; ++j) row_of[j] = -1;
-    for (j = 0; j < n_elts; ++j)
-        for (e = rec_offsets[j]; e < rec_offsets[j + 1]; ++e) row_of[j * (int64_t)catalogue + rec_events[e]] = (int32_t)e;
+    int64_t t, n = 0;
+    if (catalogue <= 0 || n_elts < 0) return -3;
+    row_of = direct_access_rows(catalogue, n_elts, rec_offsets, rec_events, &status);
+    if (!row_of) return status == -2 ? -2 : -3;
+    set_layer_def(&L, row_of, catalogue, n_elts, elt_pool_ids, rec_mean, rec_sigma, rec_sigma_c, rec_exposure,
+                  elt_terms, 0.0, 0.0, 0.0, 0.0, seed, primary_only);
     for (t = t_begin; t < t_end; ++t) {
         int64_t pos;
         for (pos = offsets[t]; pos < offsets[t + 1]; ++pos) {
-            int32_t k = (int32_t)(pos - offsets[t]);
-            double l_T = 0.0;
-            int32_t jj;
-            for (jj = 0; jj < n_elts; ++jj) {
-                int32_t r = row_of[(int64_t)jj * catalogue + ids[pos]];
-                double l_E;
-                if (r < 0) continue;
-                l_E = record_loss(rec_mean[r], rec_sigma[r], rec_sigma_c ? rec_sigma_c[r] : 0.0f, rec_exposure[r],
-                                  primary_only, seed, t, k, elt_pool_ids[jj]);
-                if (elt_terms)
-                    l_E = (double)elt_terms[3 * jj + 2] * clamp_terms(l_E, elt_terms[3 * jj + 0], elt_terms[3 * jj + 1]);
-                l_T += l_E;
-            }
-            if (l_T != 0.0) {
+            trial_extras x = {0.0, 0, 0};
+            double combined = combined_event_loss(&L, t, (int32_t)(pos - offsets[t]), ids[pos], &x);
+            if (combined != 0.0) {
                 if (n >= cap) { free(row_of); return -1; }
-                out[n++] = l_T;
+                out[n++] = combined;
             }
         }
     }

@@ -87,6 +87,58 @@ def test_secondary_uncertainty_closed_forms(rec):
     assert np.allclose(r["ylt"], want, rtol=2e-6, atol=0)
 
 
+def _su_under_terms_closed_form(c, z5, z8):
+    """The year loss that tests/golden/tiny_ara_cases.json's su_under_terms
+    states as a closed form of the two uniforms."""
+    (r5, r8) = c["records"]
+    occ_r, occ_l = c["layer_terms"][0], c["layer_terms"][1]
+
+    def elt(rec, z):
+        ret, lim, share = rec["terms"]
+        loss = rec["max"] * (z if rec["quantile"] == "z" else np.sqrt(z))
+        return share * np.minimum(np.maximum(loss - ret, 0.0), lim)
+
+    return np.minimum(np.maximum(elt(r5, z5) + elt(r8, z8) - occ_r, 0.0), occ_l)
+
+
+def test_secondary_uncertainty_sits_before_elt_terms():
+    """Section 3.3: the Beta loss is drawn for the looked-up record, and the
+    ELT financial terms (Section 2.2) act on the drawn loss, then the sum
+    over ELTs, then the occurrence terms."""
+    c = golden()["su_under_terms"]
+    for h in c["hand_checks"]:
+        got = _su_under_terms_closed_form(c, np.array(h["z"][0]), np.array(h["z"][1]))
+        assert abs(float(got) - h["year_loss"]) <= 1e-9
+    n = 400
+    offsets = np.arange(n + 1, dtype=np.int64)
+    yet = synth.YET(offsets=offsets, event_ids=np.full(n, 2, np.int32), catalogue_size=4)
+    recs = c["records"]
+    pool = synth.ELTPool(
+        elt_ids=np.array([r["pool_id"] for r in recs], np.int32), rec_offsets=np.array([0, 1, 2], np.int64),
+        event_ids=np.array([2, 2], np.int32), mean=np.array([r["mu"] for r in recs], np.float32),
+        sigma=np.array([r["max"] * math.sqrt(r["sigma_sq_over_max_sq"]) for r in recs], np.float32),
+        exposure=np.array([r["max"] for r in recs], np.float32),
+        terms=np.array([r["terms"] for r in recs], np.float32),
+    )
+    lt = [_f(v) for v in c["layer_terms"]]
+    seed = 31
+    r = oracle.run_layer(yet, pool, lt, seed=seed)
+    tr = np.arange(n)
+    z5 = oracle.uniform_batch(seed, tr, np.zeros(n, np.int32), np.full(n, recs[0]["pool_id"], np.int32))
+    z8 = oracle.uniform_batch(seed, tr, np.zeros(n, np.int32), np.full(n, recs[1]["pool_id"], np.int32))
+    want = _su_under_terms_closed_form(c, z5, z8)
+    # the records' float32 rounding moves the shapes by ~1e-7 relative; the
+    # terms are 1-Lipschitz, so the year loss moves by at most that share of
+    # the two maxima
+    assert np.allclose(r["ylt"], want, rtol=0, atol=2e-6 * (recs[0]["max"] + recs[1]["max"]))
+    # the case exercises every regime of both ELTs' terms and of the occurrence terms
+    l5 = recs[0]["max"] * z5
+    assert (l5 < 200).any() and ((l5 > 200) & (l5 < 700)).any() and (l5 > 700).any()
+    l8 = recs[1]["max"] * np.sqrt(z8)
+    assert (l8 < 50).any() and ((l8 > 50) & (l8 < 200)).any() and (l8 > 200).any()
+    assert (want == 0).any() and ((want > 0) & (want < 400)).any()
+
+
 def _small(n_trials=150, seed_shift=0):
     spec = synth.WORKLOADS["plain-1k"]
     yet = synth.make_yet(n_trials, spec["mean_events"], spec["catalogue"], spec["seed"] + seed_shift)
