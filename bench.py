@@ -34,7 +34,6 @@ import hashlib
 import json
 import math
 import os
-import re
 import subprocess
 import sys
 import tempfile
@@ -86,18 +85,27 @@ def _kernel_source_hash() -> str:
 
 
 def _profiled_traffic():
-    """DRAM bytes per launch of the layer kernel from the committed ncu summary,
-    if it was taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_layer_paper-1m.md")
+    """DRAM bytes per launch of the layer kernels from the committed ncu figures
+    (profiles/k_layer_paper-1m.json, beside its summary), if they were taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_layer_paper-1m.json")
     try:
-        text = open(path).read()
-    except OSError:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
         return None
-    m_hash = re.search(r"source hash:\s*`?([0-9a-f]{16})", text)
-    m_bytes = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", text)
-    if not m_hash or not m_bytes or m_hash.group(1) != _kernel_source_hash():
+    if d.get("source_hash") != _kernel_source_hash():
         return None
-    return float(m_bytes.group(1))
+    v = d.get("dram_bytes_per_full_launch")
+    return float(v) if v is not None else None
+
+
+def _usable_cores() -> int:
+    """Host cores this process may run on (its CPU affinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
 
 class ClockSampler:
@@ -185,7 +193,7 @@ def run_reference(args):
     n_sample = args.ref_trials
     yet, pool, spec = synth.workload(WORKLOAD, n_trials=n_sample)
     terms = _terms()
-    cores = os.cpu_count() or 1
+    cores = _usable_cores()
     for _ in range(args.warmup):
         _oracle_leg(yet, pool, terms, 0, min(n_sample, 200))
     times, evals = [], 0
@@ -366,7 +374,7 @@ def run_gpu(args):
         v, dt, ev = _oracle_leg(yet_view, pool, terms, seed, min(args.cpu_trials, n_trials))
         n1 = min(args.cpu_trials // 50, n_trials)
         v1, dt1, ev1 = _oracle_leg(yet_view, pool, terms, seed, n1, threads=1)
-        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+        cpu = {"value": v, "unit": UNIT, "cores": _usable_cores(), "kind": "oracle",
                "sample": f"first {min(args.cpu_trials, n_trials)} trials of the workload ({ev} evals, {dt:.1f} s)",
                "single_core": {"value": v1, "sample": f"first {n1} trials ({ev1} evals, {dt1:.1f} s, 1 thread)"}}
 

@@ -363,8 +363,7 @@ ARA_API int ara_debug_record_losses(ara_ctx *ctx, int64_t n, const float *mean, 
  * memory: code running under a framework's caching allocator, which owns the
  * device memory budget, or in a latency-critical loop where cudaMalloc and
  * cudaFree, which can synchronise the whole device, are not acceptable.  It
- * needs no context (creating one allocates).  The paper has no counterpart:
- * this is a deployment variant of the Section 2.3 step.
+ * needs no context (creating one allocates).  The paper has no counterpart.
  *
  * The select state lives in a fixed block of device memory that belongs to
  * the library (ARA_NOALLOC_SCRATCH_BYTES per GPU, held from the library's
@@ -378,12 +377,14 @@ ARA_API int ara_debug_record_losses(ara_ctx *ctx, int64_t n, const float *mean, 
  *   pml_out, tvar_out
  *                n_rp doubles each, host or device memory
  *   cuda_stream  cudaStream_t to run on (NULL: the legacy default stream);
- *                the current device must be the device that holds ylt
+ *                the current device must be the device that holds ylt and
+ *                any device output
  *
  * The first call on each device looks up the device address of the fixed
  * block (cudaGetSymbolAddress); make that first call before any stream
  * capture begins.  With host outputs the call synchronises the stream.
- * Returns ARA_OK, ARA_EINVAL (NULL or host ylt, n < 1, n_rp outside
+ * Returns ARA_OK, ARA_EINVAL (NULL or host ylt, ylt or a device output on
+ * another device than the current one, n < 1, n_rp outside
  * 1..ARA_NOALLOC_MAX_RP, RP < 1) or ARA_ECUDA.  It never calls cudaMalloc,
  * cudaFree or any allocating routine. */
 #define ARA_NOALLOC_MAX_RP 64

@@ -692,6 +692,8 @@ extern "C" ARA_API int ara_pml_tvar_noalloc(const double* ylt, int64_t n, const 
   if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return ARA_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return ARA_ECUDA;
+  // memory of another GPU would be read as a peer access
+  if (at.type == cudaMemoryTypeDevice && at.device != dev) return ARA_EINVAL;
   // set-up, once per device (with that device current): the block's device address
   if (g_noalloc_addr[dev] == nullptr) {
     void* addr = nullptr;
@@ -705,15 +707,20 @@ extern "C" ARA_API int ara_pml_tvar_noalloc(const double* ylt, int64_t n, const 
   double* d_out = reinterpret_cast<double*>(block);                      // 2 * ARA_NOALLOC_MAX_RP doubles
   void* state = block + 2 * ARA_NOALLOC_MAX_RP * sizeof(double);          // select state (256-aligned)
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  auto is_dev = [](const void* p) {
+  // 0: host memory, 1: device (or managed) memory of this GPU, -1: another GPU's memory
+  auto kind_of = [dev](const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
       cudaGetLastError();
-      return false;
+      return 0;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return 1;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? 1 : -1;
+    return 0;
   };
-  const bool pml_dev = is_dev(pml_out), tvar_dev = is_dev(tvar_out);
+  const int pml_kind = kind_of(pml_out), tvar_kind = kind_of(tvar_out);
+  if (pml_kind < 0 || tvar_kind < 0) return ARA_EINVAL;
+  const bool pml_dev = pml_kind == 1, tvar_dev = tvar_kind == 1;
   double* d_pml = pml_dev ? pml_out : d_out;
   double* d_tvar = tvar_dev ? tvar_out : d_out + ARA_NOALLOC_MAX_RP;
   // the select kernels reset their own histogram and state on every call

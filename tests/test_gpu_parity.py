@@ -340,25 +340,40 @@ def test_pml_tvar_and_sort(eng, n):
     assert np.array_equal(order, np.lexsort((np.arange(n), -y)))
 
 
-# ------------------------------------------------------------------ full size (sampled)
-def _report_plain_relative(ylt, ref, terms):
-    # the plain relative error over trials well above the aggregate retention's kink
-    sel = ref["ylt"] > 1e-3 * terms[3]
-    if sel.any():
-        rel = np.abs(ylt[sel] - ref["ylt"][sel]) / ref["ylt"][sel]
-        print(f"  plain relative error over {sel.sum()} trials with Y > 1e-3 AggL: max {rel.max():.2e}, "
-              f"median {np.median(rel):.2e}")
+# ------------------------------------------------------------------ full size (every trial)
+# The plain relative error |dY| / Y is asserted where the year loss is at
+# least this share of the trial's gross loss.  Below it Y is a small
+# difference S - AggR (the aggregate retention takes most of the running
+# sum), and a relative error of the FP32 pair losses in S appears in Y
+# multiplied by S / Y: there the bound is the scaled one, relative to
+# max(|Y|, gross).
+PLAIN_REL_FLOOR = 0.05
 
 
-def test_paper_1m_layer_sampled_parity(eng):
+def _plain_relative(ylt, ref, label):
+    sel = ref["ylt"] >= PLAIN_REL_FLOOR * ref["gross"]
+    sel &= ref["ylt"] > 0
+    rel = np.abs(ylt[sel] - ref["ylt"][sel]) / ref["ylt"][sel]
+    worst = float(rel.max()) if rel.size else 0.0
+    print(f"  {label}: plain relative error over {sel.sum()} trials with Y >= {PLAIN_REL_FLOOR} gross: "
+          f"max {worst:.2e}, median {np.median(rel) if rel.size else 0.0:.2e}")
+    assert worst <= YLT_TOL, f"plain relative error {worst:.3e} above {YLT_TOL}"
+    # reported beside it: the trials below the floor that are above 1e-3 of the aggregate limit
+    return worst
+
+
+def _full_size_parity(eng, name):
     """The 1M-trial x Poisson(1000) x 15-ELT layer in the benchmark's launch
-    configuration; the oracle evaluates every 997th trial."""
+    configuration against the oracle over every trial: hit lists bit-exact,
+    each year loss within the scaled bound, the plain relative bound above
+    the floor, and PML/TVaR at the workload's return periods from the GPU's
+    YLT against those from the oracle's own YLT (Section 2.3)."""
     import json
     import os
 
-    yet, pool, spec = synth.workload("paper-1m")
+    yet, pool, spec = synth.workload(name)
     with open(os.path.join(os.path.dirname(__file__), "golden", "workload_terms.json")) as fh:
-        terms = json.load(fh)["paper-1m"]["layer_terms"]
+        terms = json.load(fh)[name]["layer_terms"]
     eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
     eng.load_pool(pool)
     ylt = np.zeros(yet.n_trials)
@@ -367,43 +382,38 @@ def test_paper_1m_layer_sampled_parity(eng):
     eng.run_layer(pool.elt_ids, terms, 0, 0, yet.n_trials, ylt, hits_out=hits, hash_out=hh)
     st = eng.stats()
     assert st["n_nonconverged"] == 0
-    sample = np.arange(0, yet.n_trials, 997)
-    ref = oracle.run_layer(yet, pool, terms, seed=0, trials=sample)
-    assert np.array_equal(hits[sample], ref["hits"]) and np.array_equal(hh[sample], ref["hit_hash"])
-    worst = check_ylt(ylt[sample], ref)
-    print(f"\npaper-1m sampled worst scaled error {worst:.3e}, pairs {st['n_pairs_hit']}")
-    _report_plain_relative(ylt[sample], ref, terms)
-    # PML / TVaR of the full GPU YLT against the oracle's order statistics of the same YLT
-    pml, tvar = eng.pml_tvar(ylt, spec["return_periods"])
-    rpml, rtvar = oracle.pml_tvar(ylt, spec["return_periods"])
-    assert np.array_equal(pml, rpml) and np.allclose(tvar, rtvar, rtol=1e-12)
-
-
-def test_stress_1m_layer_sampled_parity(eng):
-    """The precision-stress layer: the paper-1m YET and 15 ELTs x 10,000 records with
-    Beta shapes log-uniform over [0.2, 50]; the oracle evaluates every 997th trial.
-    Per-trial error statistics, and PML/TVaR of the sampled trials against the
-    oracle's."""
-    import json
-    import os
-
-    yet, pool, spec = synth.workload("stress-1m")
-    with open(os.path.join(os.path.dirname(__file__), "golden", "workload_terms.json")) as fh:
-        terms = json.load(fh)["stress-1m"]["layer_terms"]
-    eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
-    eng.load_pool(pool)
-    ylt = np.zeros(yet.n_trials)
-    eng.run_layer(pool.elt_ids, terms, 0, 0, yet.n_trials, ylt)
-    assert eng.stats()["n_nonconverged"] == 0
-    sample = np.arange(0, yet.n_trials, 997)
-    ref = oracle.run_layer(yet, pool, terms, seed=0, trials=sample)
-    worst = check_ylt(ylt[sample], ref)
+    ref = oracle.run_layer(yet, pool, terms, seed=0)
+    assert np.array_equal(hits, ref["hits"]) and np.array_equal(hh, ref["hit_hash"])
+    worst = check_ylt(ylt, ref)
     scale = np.maximum(np.abs(ref["ylt"]), ref["gross"])
-    scaled = np.abs(ylt[sample] - ref["ylt"]) / np.where(scale > 0, scale, 1.0)
-    print(f"\nstress-1m sampled scaled error: max {worst:.3e}, median {np.median(scaled):.3e}")
-    _report_plain_relative(ylt[sample], ref, terms)
-    pml, tvar = eng.pml_tvar(ylt[sample].copy(), spec["return_periods"])
-    rpml, rtvar = oracle.pml_tvar(ref["ylt"], spec["return_periods"])
-    print(f"  PML/TVaR of the sample: rel err {np.max(np.abs(pml - rpml) / rpml):.2e} / "
-          f"{np.max(np.abs(tvar - rtvar) / rtvar):.2e}")
-    assert np.allclose(pml, rpml, rtol=1e-4) and np.allclose(tvar, rtvar, rtol=1e-4)
+    scaled = np.abs(ylt - ref["ylt"]) / np.where(scale > 0, scale, 1.0)
+    print(f"\n{name}: {yet.n_trials} trials, {st['n_pairs_hit']} pairs; scaled error max {worst:.3e}, "
+          f"median {np.median(scaled):.3e}")
+    _plain_relative(ylt, ref, name)
+    kink = ref["ylt"] > 1e-3 * terms[3]
+    rel_k = np.abs(ylt[kink] - ref["ylt"][kink]) / ref["ylt"][kink]
+    print(f"  plain relative error over the {kink.sum()} trials with Y > 1e-3 AggL: max {rel_k.max():.2e}, "
+          f"median {np.median(rel_k):.2e}")
+    rps = spec["return_periods"]
+    pml, tvar = eng.pml_tvar(ylt, rps)
+    rpml, rtvar = oracle.pml_tvar(ref["ylt"], rps)
+    e_pml = np.abs(pml - rpml) / rpml
+    e_tvar = np.abs(tvar - rtvar) / rtvar
+    print(f"  PML {pml} vs {rpml}: rel {e_pml.max():.2e}; TVaR rel {e_tvar.max():.2e}")
+    assert np.all(e_pml <= PML_TOL) and np.all(e_tvar <= PML_TOL)
+    # order statistics and tail means are 1-Lipschitz in the sup norm
+    dmax = float(np.abs(ylt - ref["ylt"]).max())
+    assert np.all(np.abs(pml - rpml) <= dmax + 1e-9 * rpml) and np.all(np.abs(tvar - rtvar) <= dmax + 1e-9 * rtvar)
+    # the GPU select over the GPU's own YLT is exact against a host sort of it
+    gpml, gtvar = oracle.pml_tvar(ylt, rps)
+    assert np.array_equal(pml, gpml) and np.allclose(tvar, gtvar, rtol=1e-12)
+
+
+def test_paper_1m_layer_full_parity(eng):
+    _full_size_parity(eng, "paper-1m")
+
+
+def test_stress_1m_layer_full_parity(eng):
+    """The precision-stress layer: the paper-1m YET and 15 ELTs x 10,000 records
+    with Beta shapes log-uniform over [0.2, 50]."""
+    _full_size_parity(eng, "stress-1m")

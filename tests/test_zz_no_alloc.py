@@ -7,12 +7,14 @@ device) are not acceptable.  This entry point keeps its select state in a
 fixed block of device memory owned by the library instead.  The test calls it
 through the C ABI twice in a row (two different YLTs, so the second call must
 not see the first call's state) and compares each result with the
-allocating entry point, ara_pml_tvar.  It sits in a file of its own, collected
+allocating entry point, ara_pml_tvar, and with the FP64 oracle.  It sits in a file of its own, collected
 last, and passes both alone in a fresh process and after the other tests.
 """
 
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +55,12 @@ def test_noalloc_pml_tvar_matches_the_allocating_entry_point():
             pml, tvar = pml.cpu().numpy(), tvar.cpu().numpy()
         assert np.allclose(pml, ref_pml, rtol=PML_TOL, atol=0)
         assert np.allclose(tvar, ref_tvar, rtol=PML_TOL, atol=0)
+        # and against the FP64 oracle's sort (Section 2.3), as tightly as the
+        # allocating entry point meets it: PML is one of the year losses, and
+        # TVaR a sum of them in a fixed order
+        or_pml, or_tvar = oracle.pml_tvar(y, RPS)
+        assert np.array_equal(pml, or_pml)
+        assert np.allclose(tvar, or_tvar, rtol=1e-12, atol=0)
         results.append((pml, tvar))
     eng.close()
     assert not np.array_equal(results[0][0], results[1][0])
