@@ -285,41 +285,67 @@ ARA_API int ara_run_layer_events(ara_ctx *ctx, const ara_layer *layer, uint64_t 
 ARA_API int ara_run_layers(ara_ctx *ctx, int32_t n_layers, const ara_layer *layers, uint64_t seed,
                    int64_t trial_begin, int64_t trial_end, double *ylt_out);
 
-/* Serving: layer requests against the resident YET and ELT pool, run in
- * batches (continuous batching into ara_run_layers).  The paper has no serving
- * system; a portfolio's layers (Section 2.1 (iii)) are its natural requests.
+/* Serving: layer requests against the resident YET and ELT pool, with
+ * continuous batching.  The paper has no serving system; a portfolio's
+ * layers (Section 2.1 (iii)) are its natural requests, and the chunked,
+ * asynchronous hand-off of trials follows the hybrid offload of Section 4.
  *
  * ara_submit queues one request: a layer (as for ara_run_layer), its seed, the
  * trial prefix [0, trial_end) to simulate, and n_rp (1..ARA_SERVE_MAX_RP)
  * return periods (host memory, each >= 1) for PML/TVaR of the prefix's YLT.
  * The layer's ELTs must be loaded.  *ticket receives the request's handle.
- * Errors: ARA_EINVAL, ARA_ENOTLOADED, ARA_ENOMEM (the request alone would not
- * fit the context's HBM budget).
+ * Errors: ARA_EINVAL, ARA_ENOTLOADED, ARA_ENOMEM (the request's year losses,
+ * 8 * trial_end bytes, exceed the serving arena, which the HBM budget bounds:
+ * it would never be admitted).
  *
- * ara_serve_step runs one batch: from the queue, in arrival order, every
- * request that fits next to the first (same seed and flags, at most
- * ARA_MAX_BATCH_LAYERS layers with at most ARA_MAX_BATCH_ELTS ELTs together,
- * the batch's year losses within the HBM budget), over the longest prefix of
- * the batch, then each request's PML/TVaR over its own prefix.  It returns when
- * the batch's results are on the host; *n_done (may be NULL) receives the
- * number of requests finished (0 when the queue is empty).  A request's result
- * does not depend on the batch it ran in.  Errors: ARA_ENOMEM, ARA_ECUDA.
+ * The prefix is cut into chunks of trials (ara_serve_info.chunk_trials).
+ * ara_serve_step does not wait for the device.  It (1) finishes the requests
+ * whose work the device has completed; (2) admits queued requests, in arrival
+ * order, whose year losses fit the serving arena (one that does not fit yet
+ * stays queued and a later, smaller one may go first); (3) when fewer than two
+ * rounds are in flight, launches one round on the context's stream: batched
+ * passes over one chunk each (one seed and flags per pass, at most
+ * ARA_MAX_BATCH_LAYERS requests with at most ARA_MAX_BATCH_ELTS ELTs
+ * together), and, behind each request's last chunk, its PML/TVaR over its own
+ * prefix.  Requests submitted while a round runs join the next round, so a
+ * short request overtakes a long one admitted before it.  *n_done (may be
+ * NULL) receives the number of requests finished in this call.  A request's
+ * result does not depend on the requests it shared rounds with.
+ * Errors: ARA_ENOMEM (the serving workspace), ARA_ECUDA.  The YET cannot be
+ * replaced while requests are queued or running, nor an ELT that a running
+ * request uses (ARA_EINVAL).
  *
- * ara_poll returns ARA_EAGAIN while the request is queued; once finished, it
- * copies its PML and TVaR (n_rp doubles each, host memory) and releases the
- * ticket, returning the request's own status (ARA_OK, or the error its batch
- * met).  Errors: ARA_EINVAL (unknown ticket).
+ * ara_poll returns ARA_EAGAIN while the request is not finished; once
+ * finished, it copies its PML and TVaR (n_rp doubles each, host memory) and
+ * releases the ticket, returning the request's own status (ARA_OK, or the
+ * error its pass met).  Errors: ARA_EINVAL (unknown ticket).
  *
- * ara_wait runs serve steps until the request is finished, then returns as
- * ara_poll does; it returns ARA_ETIMEOUT, with the request still queued,
+ * ara_wait runs serve steps, and waits on the host for the oldest round when a
+ * step finishes nothing, until the request is finished; then it returns as
+ * ara_poll does.  It returns ARA_ETIMEOUT, with the request still pending,
  * when timeout_ns (nanoseconds of host time, 0: no limit) has passed at the
- * end of a step.  A step that has started runs to its end. */
+ * end of a step or a wait.
+ *
+ * ara_serve_stats reports the queue: requests queued (not admitted), active
+ * (admitted, not finished), rounds in flight, and totals since the context
+ * was created. */
+typedef struct {
+    int64_t queued;            /* submitted, not yet admitted */
+    int64_t active;            /* admitted, not finished */
+    int64_t rounds_in_flight;  /* launched, not yet retired */
+    int64_t rounds_launched;   /* totals since the context was created */
+    int64_t passes_launched;
+    int64_t requests_finished;
+    int64_t chunk_trials;      /* trials per chunk */
+    int64_t arena_bytes;       /* device memory for the year losses of admitted requests */
+} ara_serve_info;
 #define ARA_SERVE_MAX_RP 16
 ARA_API int ara_submit(ara_ctx *ctx, const ara_layer *layer, uint64_t seed, int64_t trial_end,
                const double *return_periods, int32_t n_rp, int64_t *ticket);
 ARA_API int ara_serve_step(ara_ctx *ctx, int32_t *n_done);
 ARA_API int ara_poll(ara_ctx *ctx, int64_t ticket, double *pml_out, double *tvar_out);
 ARA_API int ara_wait(ara_ctx *ctx, int64_t ticket, double *pml_out, double *tvar_out, uint64_t timeout_ns);
+ARA_API int ara_serve_stats(ara_ctx *ctx, ara_serve_info *out);
 
 /* PML and TVaR of a YLT (Section 2.3) at n_rp return periods (each >= 1):
  * with m = ceil(n / RP), PML is the m-th largest year loss and TVaR the mean

@@ -42,7 +42,7 @@ EXPORTED = (
     "ara_run_layer_diag", "ara_pml_tvar", "ara_sort_ylt", "ara_debug_uniforms",
     "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
     "ara_pml_tvar_noalloc", "ara_run_layers", "ara_submit", "ara_serve_step", "ara_poll", "ara_load_xelts",
-    "ara_run_layer_events", "ara_wait", "ara_load_yet_async", "ara_finish_yet",
+    "ara_run_layer_events", "ara_wait", "ara_load_yet_async", "ara_finish_yet", "ara_serve_stats",
 )
 ARA_NOALLOC_MAX_RP = 64
 
@@ -105,6 +105,22 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServeInfo(ctypes.Structure):
+    _fields_ = [
+        ("queued", ctypes.c_int64),
+        ("active", ctypes.c_int64),
+        ("rounds_in_flight", ctypes.c_int64),
+        ("rounds_launched", ctypes.c_int64),
+        ("passes_launched", ctypes.c_int64),
+        ("requests_finished", ctypes.c_int64),
+        ("chunk_trials", ctypes.c_int64),
+        ("arena_bytes", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class Timing(ctypes.Structure):
     _fields_ = [
         ("layer_calls", ctypes.c_int64),
@@ -148,6 +164,7 @@ def load_library(path: str = LIB_PATH):
     lib.ara_serve_step.argtypes = [P, P]
     lib.ara_poll.argtypes = [P, i64, P, P]
     lib.ara_wait.argtypes = [P, i64, P, P, u64]
+    lib.ara_serve_stats.argtypes = [P, ctypes.POINTER(ServeInfo)]
     lib.ara_pml_tvar.argtypes = [P, P, i64, P, i32, P, P]
     lib.ara_sort_ylt.argtypes = [P, P, i64, P]
     lib.ara_debug_uniforms.argtypes = [P, u64, i64, P, P, P, P]
@@ -264,6 +281,10 @@ def ara_submit(h, layer: Layer, seed, trial_end, return_periods, n_rp, ticket_ou
 
 def ara_serve_step(h, n_done_out):
     return load_library().ara_serve_step(h, _ptr(n_done_out, np.int32))
+
+
+def ara_serve_stats(h, out):
+    return load_library().ara_serve_stats(h, ctypes.byref(out))
 
 
 def ara_poll(h, ticket, pml_out, tvar_out):
@@ -452,10 +473,18 @@ class Ara:
         return int(tk[0])
 
     def serve_step(self) -> int:
-        """Run one batch of queued requests; returns how many finished."""
+        """Finish what the device has completed, admit queued requests and launch
+        the next round without waiting for it; returns how many requests
+        finished in this call."""
         n = np.zeros(1, np.int32)
         self._check(ara_serve_step(self._h, n))
         return int(n[0])
+
+    def serve_stats(self) -> dict:
+        """Queue state and totals of the serving loop (ara_serve_stats)."""
+        info = ServeInfo()
+        self._check(ara_serve_stats(self._h, info))
+        return info.as_dict()
 
     def poll(self, ticket: int, n_rp: int):
         """(pml, tvar) of a finished request, or None while it is queued."""

@@ -46,6 +46,17 @@ struct ServeReq {
   std::vector<double> rps, pml, tvar;
   bool done = false;
   int status = ARA_OK;
+  // once admitted: its year losses in the serving arena, its result slot, its chunk cursor
+  size_t ylt_off = 0, ylt_bytes = 0;
+  int32_t slot = -1;
+  int64_t next_chunk = 0, n_chunks = 0;
+};
+
+// A launched serving round: the event recorded after its work and the
+// requests whose results it completes.
+struct ServeRound {
+  cudaEvent_t ev = nullptr;
+  std::vector<int64_t> finishing;
 };
 
 }  // namespace
@@ -105,17 +116,31 @@ struct ara_ctx {
   int64_t launches = 0;
   int num_sms = 0;
   int max_smem = 0;
-  // serving
-  std::deque<int64_t> serve_queue;      // tickets in arrival order
+  bool no_timing = false;   // serving passes record no timing events
+  // serving (continuous batching)
+  std::deque<int64_t> serve_queue;      // submitted, not yet admitted, in arrival order
+  std::vector<int64_t> serve_active;    // admitted and not finished, in admission order
   std::map<int64_t, ServeReq> serve_reqs;
+  std::deque<ServeRound> serve_rounds;  // launched and not retired, in launch order
+  std::vector<cudaEvent_t> serve_ev_free;
   int64_t next_ticket = 1;
-  DevBuf serve_ylt, serve_out;          // a batch's year losses; its PML/TVaR
+  bool serve_ready = false;
+  DevBuf serve_arena;                   // year losses of the admitted requests
+  std::map<size_t, size_t> arena_free;  // free blocks of the arena: offset -> bytes
+  DevBuf serve_out;                     // device result slots (PML, TVaR)
+  double* serve_host = nullptr;         // pinned host result slots
+  std::vector<int32_t> serve_slots_free;
+  int64_t serve_rounds_launched = 0, serve_passes = 0, serve_finished = 0;
 };
 
 namespace {
 
 // Two events for one timed launch group (reused after a reset).
 bool timed_pair(ara_ctx* c, int kind, cudaEvent_t* a, cudaEvent_t* b) {
+  if (c->no_timing) {
+    *a = *b = nullptr;
+    return true;
+  }
   const size_t need = 2 * (c->timed.size() + 1);
   while (c->ev_pool.size() < need) {
     cudaEvent_t e;
@@ -127,6 +152,9 @@ bool timed_pair(ara_ctx* c, int kind, cudaEvent_t* a, cudaEvent_t* b) {
   c->timed.push_back({kind, *a, *b});
   return true;
 }
+
+// Records a timing event (a null event, from a pass without timing, is skipped).
+cudaError_t record_ev(cudaEvent_t e, cudaStream_t s) { return e ? cudaEventRecord(e, s) : cudaSuccess; }
 
 int fail(ara_ctx* c, int code, const char* fmt, ...) {
   char buf[512];
@@ -294,6 +322,11 @@ int yet_begin(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int32_
   if (rc) return rc;
   if (n_trials < 1 || !offsets || catalogue_size < 1)
     return fail(c, ARA_EINVAL, "%s: need n_trials >= 1, offsets and catalogue_size >= 1", who);
+  if (!c->serve_queue.empty() || !c->serve_active.empty() || !c->serve_rounds.empty())
+    return fail(c, ARA_EINVAL, "%s: served requests are queued or running on the loaded YET", who);
+  // the serving workspace and arena follow the YET's size
+  c->serve_ready = false;
+  release(c, c->serve_arena);
   // an upload still in flight is replaced: wait for it, whatever its checks say
   if (c->yet_pending) {
     c->yet_pending = false;
@@ -400,6 +433,11 @@ static int load_elts_impl(ara_ctx* c, const char* who, int32_t n_elts, const int
       return fail(c, ARA_EINVAL, "%s: ELT %d has invalid financial terms", who, ids[i]);
     for (int32_t j = 0; j < i; ++j)
       if (ids[j] == ids[i]) return fail(c, ARA_EINVAL, "%s: pool id %d appears twice", who, ids[i]);
+    for (int64_t tk : c->serve_active) {
+      const std::vector<int32_t>& used = c->serve_reqs[tk].elt_ids;
+      if (std::find(used.begin(), used.end(), ids[i]) != used.end())
+        return fail(c, ARA_EINVAL, "%s: ELT %d is used by a served request that has not finished", who, ids[i]);
+    }
   }
   const int64_t R = offs[n_elts];
   if (R > 0 && (!event_ids || !mean || !sigma || !exposure))
@@ -697,14 +735,14 @@ static int launch_index_and_gather(ara_ctx* c, const PassPlan& pl, const char* w
     return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
   ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 8 * sizeof(unsigned long long), c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
-  ARA_CUDA(c, cudaEventRecord(ia, c->stream));
+  ARA_CUDA(c, record_ev(ia, c->stream));
   ARA_CUDA(c, ara::build_layer_index(pl.refs, const_cast<ara::LayerIndex&>(pl.ix), c->stream, launched));
-  ARA_CUDA(c, cudaEventRecord(ib, c->stream));
+  ARA_CUDA(c, record_ev(ib, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
-  ARA_CUDA(c, cudaEventRecord(ka, c->stream));
+  ARA_CUDA(c, record_ev(ka, c->stream));
   ARA_CUDA(c, ara::launch_gather(pl.g, pl.grid, pl.smem, c->stream));
-  ARA_CUDA(c, cudaEventRecord(kb, c->stream));
+  ARA_CUDA(c, record_ev(kb, c->stream));
   *launched += 1;
   return ARA_OK;
 }
@@ -872,9 +910,9 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
   if ((rc = launch_index_and_gather(c, pl, who, &launched))) return rc;
   cudaEvent_t la, lb;
   if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
-  ARA_CUDA(c, cudaEventRecord(la, c->stream));
+  ARA_CUDA(c, record_ev(la, c->stream));
   ARA_CUDA(c, ara::launch_losses(p, loss_grid, c->stream));
-  ARA_CUDA(c, cudaEventRecord(lb, c->stream));
+  ARA_CUDA(c, record_ev(lb, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   launched += 1;
   if (evr && (rc = emit_event_rows(c, pl, p, evr, &launched))) return rc;
@@ -904,14 +942,18 @@ static int batch_scale_exp(double o_max, int64_t n_max) {
 }
 
 // layer_t_end (NULL: t1 for every layer): layer l's trials end at
-// min(layer_t_end[l], t1); its year losses of later trials are 0 and cost no
-// loss computations (the serving loop's requests over their own prefixes).
+// min(layer_t_end[l], t1); later trials cost no loss computations and get no
+// output (the serving loop's requests over their own prefixes).  ylt_l (NULL:
+// ylt_out, layer-major): per layer, a device array that receives the year
+// losses of trials [t0, layer end) from index 0; the call then neither copies
+// nor synchronises.
 static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers, uint64_t seed, int64_t t0,
-                           int64_t t1, double* ylt_out, const int64_t* layer_t_end = nullptr) {
+                           int64_t t1, double* ylt_out, const int64_t* layer_t_end = nullptr,
+                           double* const* ylt_l = nullptr) {
   static const char* who = "ara_run_layers";
   int rc = bind(c);
   if (rc) return rc;
-  if (n_layers < 1 || n_layers > ARA_MAX_BATCH_LAYERS || !layers || !ylt_out)
+  if (n_layers < 1 || n_layers > ARA_MAX_BATCH_LAYERS || !layers || (!ylt_out && !ylt_l))
     return fail(c, ARA_EINVAL, "%s: need 1..%d layers and ylt_out", who, ARA_MAX_BATCH_LAYERS);
   if ((rc = check_trial_range(c, t0, t1, who))) return rc;
   std::vector<std::vector<int32_t>> lids(n_layers);
@@ -960,12 +1002,13 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
   }
   // ---- outputs
   const int64_t n_out = pl.n_out;
-  const bool ylt_dev = is_device_ptr(ylt_out);
+  const bool ylt_dev = ylt_l || is_device_ptr(ylt_out);
   double* d_ylt = ylt_out;
   if (!ylt_dev) {
     if ((rc = reserve(c, c->ylt_tmp, sizeof(double) * n_out * n_layers))) return rc;
     d_ylt = static_cast<double*>(c->ylt_tmp.ptr);
   }
+  for (int32_t l = 0; l < n_layers; ++l) p.ylt_l[l] = ylt_l ? ylt_l[l] : d_ylt + static_cast<int64_t>(l) * n_out;
   p.off = pl.g.off;
   p.t_begin = t0;
   p.t_end = t1;
@@ -981,8 +1024,6 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
   fill_philox_keys(seed, p.rk);
   p.primary_only = (layers[0].flags & ARA_PRIMARY_ONLY) ? 1 : 0;
   p.newton_only = (layers[0].flags & ARA_NEWTON_ONLY) ? 1 : 0;
-  p.ylt = d_ylt;
-  p.n_out = n_out;
   p.counters = static_cast<unsigned long long*>(c->counters.ptr);
   // expected hit records per trial: each union ELT's records over the catalogue, times the
   // events per trial, weighted by the share of the pass's trials its layers reach
@@ -1005,9 +1046,9 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
   if ((rc = launch_index_and_gather(c, pl, who, &launched))) return rc;
   cudaEvent_t la, lb;
   if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
-  ARA_CUDA(c, cudaEventRecord(la, c->stream));
+  ARA_CUDA(c, record_ev(la, c->stream));
   ARA_CUDA(c, ara::launch_losses_batch(p, per_trial, grid, c->stream));
-  ARA_CUDA(c, cudaEventRecord(lb, c->stream));
+  ARA_CUDA(c, record_ev(lb, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   launched += 1;
   c->launches += launched;
@@ -1099,7 +1140,317 @@ int ara_get_timing(ara_ctx* c, ara_timing* out, int reset) {
   return ARA_OK;
 }
 
+}  // extern "C"
+
 // ---------------------------------------------------------------- serving
+// Continuous batching.  A request's trial prefix is cut into chunks of
+// kServeChunk trials; an admitted request has a cursor, its next chunk.
+// ara_serve_step retires the rounds the device has finished (cudaEventQuery,
+// no waiting), admits queued requests whose year losses fit the serving
+// arena, and launches one round: at most kServePassesPerRound batched passes
+// (ara_run_layers over one chunk), each for up to ARA_MAX_BATCH_LAYERS
+// admitted requests that are at the same chunk, with one seed and flags and
+// at most ARA_MAX_BATCH_ELTS ELTs together, every layer writing its chunk
+// into its own request's year losses.  Behind a request's last chunk the
+// round queues its PML/TVaR select and the copy of the results to pinned
+// host memory.  The step returns with the round in flight: requests
+// submitted meanwhile join the next round, and at most kServeMaxInFlight
+// rounds are in flight.
+namespace {
+
+constexpr int64_t kServeChunk = 131072;        // trials per chunk
+constexpr size_t kServeMaxInFlight = 2;        // rounds launched and not retired
+constexpr int kServePassesPerRound = 8;
+constexpr int32_t kServeSlots = 1024;          // result slots: admitted requests at most
+constexpr int64_t kServeArenaRequests = 96;    // default arena: year losses of this many whole-YET requests
+constexpr size_t kArenaAlign = 256;
+
+size_t arena_round(size_t bytes) { return (bytes + kArenaAlign - 1) & ~(kArenaAlign - 1); }
+
+bool arena_alloc(ara_ctx* c, size_t bytes, size_t* off) {
+  bytes = arena_round(bytes);
+  for (auto it = c->arena_free.begin(); it != c->arena_free.end(); ++it) {
+    if (it->second < bytes) continue;
+    *off = it->first;
+    const size_t rest = it->second - bytes, at = it->first + bytes;
+    c->arena_free.erase(it);
+    if (rest) c->arena_free[at] = rest;
+    return true;
+  }
+  return false;
+}
+
+void arena_release(ara_ctx* c, size_t off, size_t bytes) {
+  bytes = arena_round(bytes);
+  auto next = c->arena_free.lower_bound(off);
+  if (next != c->arena_free.end() && off + bytes == next->first) {
+    bytes += next->second;
+    next = c->arena_free.erase(next);
+  }
+  if (next != c->arena_free.begin()) {
+    auto prev = std::prev(next);
+    if (prev->first + prev->second == off) {
+      prev->second += bytes;
+      return;
+    }
+  }
+  c->arena_free[off] = bytes;
+}
+
+// Device buffers the serving passes use besides the arena, with the sizes they
+// need: the event buffer of the largest chunk, the tile counts and deferred
+// sums of a chunk, the layer index of the pool's ARA_MAX_BATCH_ELTS largest
+// ELTs, the select scratch for the whole YET and the result slots.  The
+// serving loop reserves them before it sizes the arena, so that no pass grows
+// a buffer while rounds are in flight.
+std::vector<std::pair<DevBuf*, size_t>> serve_workspace(ara_ctx* c) {
+  int64_t max_ev = 0;
+  for (int64_t t0 = 0; t0 < c->n_trials; t0 += kServeChunk) {
+    const int64_t t1 = std::min(t0 + kServeChunk, c->n_trials);
+    max_ev = std::max(max_ev, c->h_off[t1] - c->h_off[t0]);
+  }
+  std::vector<int64_t> sizes;
+  bool any_corr = false;
+  for (const auto& kv : c->pool) {
+    sizes.push_back(kv.second.n);
+    any_corr = any_corr || kv.second.correlated;
+  }
+  std::sort(sizes.rbegin(), sizes.rend());
+  int64_t n_recs = 0;
+  for (size_t i = 0; i < sizes.size() && i < static_cast<size_t>(ARA_MAX_BATCH_ELTS); ++i) n_recs += sizes[i];
+  const int64_t n_words = (static_cast<int64_t>(c->catalogue) + 31) / 32;
+  const size_t tmp_words = std::max(ara::scan_tmp_words(n_words), ara::scan_tmp_words(n_recs));
+  const size_t chunk_tiles = static_cast<size_t>(kServeChunk / ara::kWarpTrials + 2);
+  std::vector<std::pair<DevBuf*, size_t>> w = {
+      {&c->ev_buf, sizeof(uint2) * static_cast<size_t>(max_ev + 1)},
+      {&c->tile_cnt, sizeof(uint32_t) * chunk_tiles},
+      {&c->def_acc, sizeof(double) * static_cast<size_t>(kServeChunk + 1)},
+      {&c->bits, sizeof(uint32_t) * n_words},
+      {&c->word_cnt, sizeof(uint32_t) * (n_words + 1)},
+      {&c->word_pairs, sizeof(uint32_t) * (n_words + 1)},
+      {&c->rankdir, sizeof(uint2) * n_words},
+      {&c->mask, sizeof(unsigned long long) * (n_recs + 1)},
+      {&c->slot_cnt, sizeof(uint32_t) * (n_recs + 2)},
+      {&c->pairs, sizeof(ara::Pair) * (n_recs + 1)},
+      {&c->pairs_hot, sizeof(ara::PairHot) * (n_recs + 1)},
+      {&c->pairs_ev, sizeof(int32_t) * (n_recs + 1)},
+      {&c->scan_tmp, sizeof(uint32_t) * (tmp_words + 8)},
+      {&c->sel, ara::select_scratch_bytes(c->n_trials)},
+      {&c->serve_out, 2 * sizeof(double) * ARA_SERVE_MAX_RP * kServeSlots},
+  };
+  if (any_corr) w.push_back({&c->pairs_w, sizeof(float2) * (n_recs + 1)});
+  return w;
+}
+
+// The arena's size: once prepared, its size; before, what the budget leaves
+// once the workspace is reserved, or room for kServeArenaRequests whole-YET
+// requests without a budget.
+size_t serve_arena_bytes(ara_ctx* c) {
+  if (c->serve_ready) return c->serve_arena.bytes;
+  if (!c->budget) return arena_round(sizeof(double) * static_cast<size_t>(c->n_trials)) * kServeArenaRequests;
+  size_t missing = 0;
+  for (const auto& w : serve_workspace(c)) missing += w.second > w.first->bytes ? w.second - w.first->bytes : 0;
+  const size_t arena_now = c->serve_arena.bytes;  // released and re-reserved by the preparation
+  const size_t used = c->used - arena_now + missing;
+  return (c->budget > used ? c->budget - used : 0) & ~(kArenaAlign - 1);
+}
+
+// First use (and after a new YET): the workspace, the arena, the result slots.
+int serve_prepare(ara_ctx* c, const char* who) {
+  if (c->serve_ready) return ARA_OK;
+  const size_t arena = serve_arena_bytes(c);
+  release(c, c->serve_arena);
+  int rc;
+  for (const auto& w : serve_workspace(c))
+    if ((rc = reserve(c, *w.first, w.second))) return rc;
+  if (!c->serve_host) {
+    void* h = nullptr;
+    if (cudaHostAlloc(&h, 2 * sizeof(double) * ARA_SERVE_MAX_RP * kServeSlots, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, ARA_ENOMEM, "%s: cannot allocate pinned result slots", who);
+    }
+    c->serve_host = static_cast<double*>(h);
+  }
+  if (arena < kArenaAlign) return fail(c, ARA_ENOMEM, "%s: the HBM budget leaves no room for year losses", who);
+  if ((rc = reserve(c, c->serve_arena, arena))) return rc;
+  c->arena_free.clear();
+  c->arena_free[0] = c->serve_arena.bytes;
+  c->serve_slots_free.clear();
+  for (int32_t i = kServeSlots - 1; i >= 0; --i) c->serve_slots_free.push_back(i);
+  c->serve_ready = true;
+  return ARA_OK;
+}
+
+// Finishes the requests of the rounds the device has completed, oldest first;
+// with `block`, waits for the oldest round first.  *n_done counts them.
+int serve_retire(ara_ctx* c, bool block, int32_t* n_done) {
+  while (!c->serve_rounds.empty()) {
+    ServeRound& r = c->serve_rounds.front();
+    const cudaError_t e = block ? cudaEventSynchronize(r.ev) : cudaEventQuery(r.ev);
+    if (e == cudaErrorNotReady) {
+      cudaGetLastError();
+      break;
+    }
+    int status = ARA_OK;
+    if (e != cudaSuccess) status = fail(c, ARA_ECUDA, "ara_serve_step: %s", cudaGetErrorString(e));
+    for (int64_t tk : r.finishing) {
+      ServeReq& q = c->serve_reqs[tk];
+      const size_t m = q.rps.size();
+      q.done = true;
+      q.status = status;
+      if (!status) {
+        const double* h = c->serve_host + static_cast<size_t>(q.slot) * 2 * ARA_SERVE_MAX_RP;
+        q.pml.assign(h, h + m);
+        q.tvar.assign(h + ARA_SERVE_MAX_RP, h + ARA_SERVE_MAX_RP + m);
+      }
+      arena_release(c, q.ylt_off, q.ylt_bytes);
+      c->serve_slots_free.push_back(q.slot);
+      c->serve_active.erase(std::find(c->serve_active.begin(), c->serve_active.end(), tk));
+      ++c->serve_finished;
+      if (n_done) ++*n_done;
+    }
+    c->serve_ev_free.push_back(r.ev);
+    c->serve_rounds.pop_front();
+    block = false;
+    if (status) return status;
+  }
+  return ARA_OK;
+}
+
+// Queued requests, in arrival order, whose year losses fit the arena (a
+// request that does not fit yet stays queued; a later, smaller one may go).
+void serve_admit(ara_ctx* c) {
+  for (auto it = c->serve_queue.begin(); it != c->serve_queue.end() && !c->serve_slots_free.empty();) {
+    ServeReq& q = c->serve_reqs[*it];
+    size_t off = 0;
+    if (!arena_alloc(c, sizeof(double) * static_cast<size_t>(q.t_end), &off)) {
+      ++it;
+      continue;
+    }
+    q.ylt_off = off;
+    q.ylt_bytes = sizeof(double) * static_cast<size_t>(q.t_end);
+    q.slot = c->serve_slots_free.back();
+    c->serve_slots_free.pop_back();
+    q.next_chunk = 0;
+    q.n_chunks = (q.t_end + kServeChunk - 1) / kServeChunk;
+    c->serve_active.push_back(*it);
+    it = c->serve_queue.erase(it);
+  }
+}
+
+// Fails the requests of a pass that could not be launched.
+void serve_fail_requests(ara_ctx* c, const std::vector<int64_t>& tks, int status) {
+  for (int64_t tk : tks) {
+    ServeReq& q = c->serve_reqs[tk];
+    q.done = true;
+    q.status = status;
+    arena_release(c, q.ylt_off, q.ylt_bytes);
+    c->serve_slots_free.push_back(q.slot);
+    c->serve_active.erase(std::find(c->serve_active.begin(), c->serve_active.end(), tk));
+    ++c->serve_finished;
+  }
+}
+
+int serve_launch_round(ara_ctx* c, const char* who, int32_t* n_failed) {
+  std::vector<int64_t> cand;
+  for (int64_t tk : c->serve_active) {
+    const ServeReq& q = c->serve_reqs[tk];
+    if (q.next_chunk < q.n_chunks) cand.push_back(tk);
+  }
+  if (cand.empty()) return ARA_OK;
+  ServeRound round;
+  if (!c->serve_ev_free.empty()) {
+    round.ev = c->serve_ev_free.back();
+    c->serve_ev_free.pop_back();
+  } else if (cudaEventCreateWithFlags(&round.ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, ARA_ECUDA, "%s: cannot create an event", who);
+  }
+  double* arena = static_cast<double*>(c->serve_arena.ptr);
+  double* d_out = static_cast<double*>(c->serve_out.ptr);
+  std::vector<bool> used(cand.size(), false);
+  int passes = 0, status = ARA_OK;
+  c->no_timing = true;
+  for (size_t i = 0; i < cand.size() && passes < kServePassesPerRound; ++i) {
+    if (used[i]) continue;
+    const ServeReq& a = c->serve_reqs[cand[i]];
+    std::vector<int64_t> members{cand[i]};
+    used[i] = true;
+    std::vector<int32_t> uni = a.elt_ids;
+    for (size_t j = i + 1; j < cand.size() && members.size() < static_cast<size_t>(ARA_MAX_BATCH_LAYERS); ++j) {
+      if (used[j]) continue;
+      const ServeReq& b = c->serve_reqs[cand[j]];
+      if (b.next_chunk != a.next_chunk || b.seed != a.seed || b.layer.flags != a.layer.flags) continue;
+      std::vector<int32_t> u2 = uni;
+      u2.insert(u2.end(), b.elt_ids.begin(), b.elt_ids.end());
+      std::sort(u2.begin(), u2.end());
+      u2.erase(std::unique(u2.begin(), u2.end()), u2.end());
+      if (u2.size() > static_cast<size_t>(ARA_MAX_BATCH_ELTS)) continue;
+      members.push_back(cand[j]);
+      used[j] = true;
+      uni.swap(u2);
+    }
+    const int64_t t0 = a.next_chunk * kServeChunk;
+    int64_t t1 = t0;
+    const int32_t nm = static_cast<int32_t>(members.size());
+    std::vector<ara_layer> layers(nm);
+    std::vector<int64_t> t_ends(nm);
+    std::vector<double*> outs(nm);
+    for (int32_t m = 0; m < nm; ++m) {
+      const ServeReq& q = c->serve_reqs[members[m]];
+      layers[m] = q.layer;
+      t_ends[m] = q.t_end;
+      t1 = std::max(t1, std::min(q.t_end, t0 + kServeChunk));
+      outs[m] = arena + q.ylt_off / sizeof(double) + t0;
+    }
+    int rc = run_layers_impl(c, nm, layers.data(), a.seed, t0, t1, nullptr, t_ends.data(), outs.data());
+    for (int32_t m = 0; m < nm && !rc; ++m) {
+      ServeReq& q = c->serve_reqs[members[m]];
+      if (++q.next_chunk < q.n_chunks) continue;
+      // the request's last chunk: its PML/TVaR over its whole prefix, then the results to the host
+      double* slot = d_out + static_cast<size_t>(q.slot) * 2 * ARA_SERVE_MAX_RP;
+      int launched = 0;
+      cudaError_t e = ara::pml_tvar_device(arena + q.ylt_off / sizeof(double), q.t_end, q.rps.data(),
+                                           static_cast<int32_t>(q.rps.size()), slot, slot + ARA_SERVE_MAX_RP,
+                                           c->sel.ptr, c->sel.bytes, c->stream, &launched);
+      c->launches += launched;
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->serve_host + static_cast<size_t>(q.slot) * 2 * ARA_SERVE_MAX_RP, slot,
+                            2 * sizeof(double) * ARA_SERVE_MAX_RP, cudaMemcpyDeviceToHost, c->stream);
+      if (e != cudaSuccess) rc = fail(c, ARA_ECUDA, "%s: %s", who, cudaGetErrorString(e));
+      else round.finishing.push_back(members[m]);
+    }
+    if (rc) {
+      // the pass's requests end with its error; the others of the round go on
+      std::vector<int64_t> failed;
+      for (int64_t tk : members)
+        if (std::find(round.finishing.begin(), round.finishing.end(), tk) == round.finishing.end())
+          failed.push_back(tk);
+      serve_fail_requests(c, failed, rc);
+      if (n_failed) *n_failed += static_cast<int32_t>(failed.size());
+      status = rc;
+      break;
+    }
+    ++passes;
+  }
+  c->no_timing = false;
+  const cudaError_t e = cudaEventRecord(round.ev, c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->serve_ev_free.push_back(round.ev);
+    serve_fail_requests(c, round.finishing, ARA_ECUDA);
+    return fail(c, ARA_ECUDA, "%s: %s", who, cudaGetErrorString(e));
+  }
+  c->serve_rounds.push_back(std::move(round));
+  ++c->serve_rounds_launched;
+  c->serve_passes += passes;
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
 int ara_submit(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t_end, const double* rps, int32_t n_rp,
                int64_t* ticket) {
   static const char* who = "ara_submit";
@@ -1113,8 +1464,10 @@ int ara_submit(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t_end, con
     if (c->pool.find(id) == c->pool.end()) return fail(c, ARA_ENOTLOADED, "%s: ELT %d is not loaded", who, id);
   for (int32_t i = 0; i < n_rp; ++i)
     if (!(rps[i] >= 1.0) || !std::isfinite(rps[i])) return fail(c, ARA_EINVAL, "%s: return periods must be >= 1", who);
-  if (c->budget && sizeof(double) * static_cast<size_t>(t_end) > c->budget)
-    return fail(c, ARA_ENOMEM, "%s: the request's year losses exceed the HBM budget", who);
+  const size_t arena = serve_arena_bytes(c);
+  if (arena_round(sizeof(double) * static_cast<size_t>(t_end)) > arena)
+    return fail(c, ARA_ENOMEM, "%s: the request's year losses (%lld bytes) exceed the serving arena (%zu bytes)",
+                who, (long long)(sizeof(double) * t_end), arena);
   const int64_t tk = c->next_ticket++;
   ServeReq& r = c->serve_reqs[tk];
   r.elt_ids = ids;
@@ -1133,79 +1486,33 @@ int ara_serve_step(ara_ctx* c, int32_t* n_done) {
   static const char* who = "ara_serve_step";
   int rc = bind(c);
   if (rc) return rc;
-  if (n_done) *n_done = 0;
-  if (c->serve_queue.empty()) return ARA_OK;
-  // ---- the batch: in arrival order, every request that fits next to the first
-  const ServeReq& first = c->serve_reqs[c->serve_queue.front()];
-  const size_t room = c->budget ? c->budget - std::min(c->budget, c->used - c->serve_ylt.bytes) : SIZE_MAX;
-  std::vector<int64_t> batch;
-  std::vector<int32_t> uni;
-  int64_t t_max = 0;
-  for (int64_t tk : c->serve_queue) {
-    const ServeReq& r = c->serve_reqs[tk];
-    if (batch.size() == static_cast<size_t>(ARA_MAX_BATCH_LAYERS)) break;
-    if (r.seed != first.seed || r.layer.flags != first.layer.flags) continue;
-    std::vector<int32_t> u2 = uni;
-    u2.insert(u2.end(), r.elt_ids.begin(), r.elt_ids.end());
-    std::sort(u2.begin(), u2.end());
-    u2.erase(std::unique(u2.begin(), u2.end()), u2.end());
-    if (u2.size() > static_cast<size_t>(ARA_MAX_BATCH_ELTS)) continue;
-    const int64_t t2 = std::max(t_max, r.t_end);
-    if (sizeof(double) * static_cast<size_t>(t2) * (batch.size() + 1) > room && !batch.empty()) continue;
-    batch.push_back(tk);
-    uni.swap(u2);
-    t_max = t2;
-  }
-  // ---- the layers over [0, t_max), then each request's PML/TVaR over its own prefix
-  const int32_t nb = static_cast<int32_t>(batch.size());
-  std::vector<ara_layer> layers(nb);
-  std::vector<int64_t> t_ends(nb);
-  int32_t n_rp_total = 0;
-  for (int32_t i = 0; i < nb; ++i) {
-    layers[i] = c->serve_reqs[batch[i]].layer;
-    t_ends[i] = c->serve_reqs[batch[i]].t_end;
-    n_rp_total += static_cast<int32_t>(c->serve_reqs[batch[i]].rps.size());
-  }
-  int status = reserve(c, c->serve_ylt, sizeof(double) * static_cast<size_t>(t_max) * nb);
-  if (!status) status = reserve(c, c->serve_out, 2 * sizeof(double) * n_rp_total);
-  if (!status) status = reserve(c, c->sel, ara::select_scratch_bytes(t_max));
-  double* d_ylt = static_cast<double*>(c->serve_ylt.ptr);
-  double* d_out = static_cast<double*>(c->serve_out.ptr);
-  // each request's layer over its own prefix only; the pass spans the longest
-  if (!status) status = run_layers_impl(c, nb, layers.data(), first.seed, 0, t_max, d_ylt, t_ends.data());
-  std::vector<double> h_out(2 * static_cast<size_t>(n_rp_total));
-  if (!status) {
-    int32_t at = 0, launched = 0;
-    cudaError_t e = cudaSuccess;
-    for (int32_t i = 0; i < nb && e == cudaSuccess; ++i) {
-      const ServeReq& r = c->serve_reqs[batch[i]];
-      const int32_t m = static_cast<int32_t>(r.rps.size());
-      e = ara::pml_tvar_device(d_ylt + static_cast<int64_t>(i) * t_max, r.t_end, r.rps.data(), m, d_out + at,
-                               d_out + n_rp_total + at, c->sel.ptr, c->sel.bytes, c->stream, &launched);
-      at += m;
+  int32_t n = 0;
+  rc = serve_retire(c, false, &n);
+  if (!rc && (!c->serve_queue.empty() || !c->serve_active.empty()) && c->serve_rounds.size() < kServeMaxInFlight) {
+    rc = serve_prepare(c, who);
+    if (!rc) {
+      serve_admit(c);
+      rc = serve_launch_round(c, who, &n);
     }
-    c->launches += launched;
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(h_out.data(), d_out, sizeof(double) * h_out.size(), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) status = fail(c, ARA_ECUDA, "%s: %s", who, cudaGetErrorString(e));
   }
-  // ---- the batch's requests are finished (with the batch's status)
-  int32_t at = 0;
-  for (int32_t i = 0; i < nb; ++i) {
-    ServeReq& r = c->serve_reqs[batch[i]];
-    const int32_t m = static_cast<int32_t>(r.rps.size());
-    r.done = true;
-    r.status = status;
-    if (!status) {
-      r.pml.assign(h_out.begin() + at, h_out.begin() + at + m);
-      r.tvar.assign(h_out.begin() + n_rp_total + at, h_out.begin() + n_rp_total + at + m);
-    }
-    at += m;
-  }
-  for (int64_t tk : batch) c->serve_queue.erase(std::find(c->serve_queue.begin(), c->serve_queue.end(), tk));
-  if (n_done) *n_done = nb;
-  return status;
+  if (n_done) *n_done = n;
+  return rc;
+}
+
+int ara_serve_stats(ara_ctx* c, ara_serve_info* out) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (!out) return fail(c, ARA_EINVAL, "ara_serve_stats: out is NULL");
+  *out = ara_serve_info{};
+  out->queued = static_cast<int64_t>(c->serve_queue.size());
+  out->active = static_cast<int64_t>(c->serve_active.size());
+  out->rounds_in_flight = static_cast<int64_t>(c->serve_rounds.size());
+  out->rounds_launched = c->serve_rounds_launched;
+  out->passes_launched = c->serve_passes;
+  out->requests_finished = c->serve_finished;
+  out->chunk_trials = kServeChunk;
+  out->arena_bytes = static_cast<int64_t>(serve_arena_bytes(c));
+  return ARA_OK;
 }
 
 int ara_poll(ara_ctx* c, int64_t ticket, double* pml_out, double* tvar_out) {
@@ -1238,8 +1545,13 @@ int ara_wait(ara_ctx* c, int64_t ticket, double* pml_out, double* tvar_out, uint
     }
     int32_t n_done = 0;
     if ((rc = ara_serve_step(c, &n_done))) return rc;
-    if (n_done == 0 && ara_poll(c, ticket, nullptr, nullptr) == ARA_EAGAIN)
+    if (n_done > 0) continue;
+    // nothing finished in this step: wait on the host for the oldest round in flight
+    if (!c->serve_rounds.empty()) {
+      if ((rc = serve_retire(c, true, nullptr))) return rc;
+    } else if (ara_poll(c, ticket, nullptr, nullptr) == ARA_EAGAIN) {
       return fail(c, ARA_EINVAL, "ara_wait: ticket %lld is queued but no step can run it", (long long)ticket);
+    }
   }
 }
 
@@ -1417,12 +1729,15 @@ void ara_destroy(ara_ctx* c) {
                     &c->yet_ids,    &c->bits,           &c->word_cnt,      &c->word_pairs,     &c->rankdir,
                     &c->mask,       &c->slot_cnt,       &c->pairs,         &c->pairs_hot,     &c->pairs_w,          &c->pairs_ev,         &c->scan_tmp,       &c->flags,
                     &c->counters,   &c->ylt_tmp,        &c->diag_tmp,      &c->sel,            &c->in_tmp,
-                    &c->out_tmp,    &c->serve_ylt,      &c->serve_out,      &c->ev_occ,        &c->row_base,
+                    &c->out_tmp,    &c->serve_arena,    &c->serve_out,      &c->ev_occ,        &c->row_base,
                     &c->evr_stage,  &c->yet_flags};
   for (DevBuf* b : bufs) release(c, *b);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->ev_pool) cudaEventDestroy(e);
+  for (auto& r : c->serve_rounds) cudaEventDestroy(r.ev);
+  for (auto& e : c->serve_ev_free) cudaEventDestroy(e);
+  if (c->serve_host) cudaFreeHost(c->serve_host);
   if (c->yet_ready) cudaEventDestroy(c->yet_ready);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->h_yet_flags) cudaFreeHost(c->h_yet_flags);

@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
         unsigned long long S = 0ull;
         for (int j = 0; j < 32; ++j) S += ws.acc[l][j];
         const double sd = __ull2double_rn(S) * p.inv_scale[l];
-        p.ylt[static_cast<int64_t>(l) * p.n_out + (ta + t_lo - p.t_begin)] = clamp_terms_d(sd, p.agg_r[l], p.agg_l[l]);
+        if (ta + t_lo < p.layer_t_end[l]) p.ylt_l[l][ta + t_lo - p.t_begin] = clamp_terms_d(sd, p.agg_r[l], p.agg_l[l]);
       }
     } else {
       flush_lane(ws, lane, cur, dirty);
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
       for (int i = static_cast<int>(lane); i < nl * ntr; i += 32) {
         const int l = i / ntr, t = i - l * ntr;
         const double sd = __ull2double_rn(ws.tacc[l][t]) * p.inv_scale[l];
-        p.ylt[static_cast<int64_t>(l) * p.n_out + (ta + t - p.t_begin)] = clamp_terms_d(sd, p.agg_r[l], p.agg_l[l]);
+        if (ta + t < p.layer_t_end[l]) p.ylt_l[l][ta + t - p.t_begin] = clamp_terms_d(sd, p.agg_r[l], p.agg_l[l]);
       }
     }
     __syncwarp();

@@ -209,10 +209,9 @@ struct BatchParams {
   uint32_t rk[20];                     // Philox round keys of the seed
   int32_t primary_only;
   int32_t newton_only;
-  double* ylt;                         // layer-major, stride n_out
-  int64_t n_out;
+  double* ylt_l[kBatchLayers];         // layer l's year losses of trials [t_begin, layer_t_end[l]) (indexed from t_begin)
   unsigned long long* counters;        // [0] tile queue, [1] pairs, [2] non-converged
-  int64_t layer_t_end[kBatchLayers];   // layer l's trials end here (<= t_end): later trials get no losses (year loss 0)
+  int64_t layer_t_end[kBatchLayers];   // layer l's trials end here (<= t_end): later trials get no losses, no output
 };
 
 // per_trial: one warp per trial (many hit records per trial), else one warp

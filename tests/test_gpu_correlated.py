@@ -111,10 +111,8 @@ def test_correlated_batched_layers_and_serving(eng, world):
         check_ylt(out[l], oracle.run_layer(yet, sub, terms, seed=9))
     rps = (10.0, 50.0)
     tk = [eng.submit(ids, terms, 9, 700, rps) for ids, terms, _ in layers[:3]]
-    while eng.serve_step():
-        pass
     for t, (ids, terms, sub) in zip(tk, layers[:3]):
-        pml, tvar = eng.poll(t, len(rps))
+        pml, tvar = eng.wait(t, len(rps))
         ref_pml, ref_tvar = oracle.pml_tvar(oracle.run_layer(yet, sub, terms, seed=9, trials=np.arange(700))["ylt"], rps)
         assert np.allclose(pml, ref_pml, rtol=1e-4) and np.allclose(tvar, ref_tvar, rtol=1e-4)
 

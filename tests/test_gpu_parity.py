@@ -382,6 +382,10 @@ def _full_size_parity(eng, name):
     eng.run_layer(pool.elt_ids, terms, 0, 0, yet.n_trials, ylt, hits_out=hits, hash_out=hh)
     st = eng.stats()
     assert st["n_nonconverged"] == 0
+    # the call without hit lists (the benchmark's) gives the same bits
+    plain = np.zeros(yet.n_trials)
+    eng.run_layer(pool.elt_ids, terms, 0, 0, yet.n_trials, plain)
+    assert np.array_equal(plain, ylt)
     ref = oracle.run_layer(yet, pool, terms, seed=0)
     assert np.array_equal(hits, ref["hits"]) and np.array_equal(hh, ref["hit_hash"])
     worst = check_ylt(ylt, ref)

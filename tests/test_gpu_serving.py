@@ -1,7 +1,12 @@
-"""GPU tests of the serving loop (ara_submit / ara_serve_step / ara_poll):
-each request's PML/TVaR against the FP64 oracle on its own trial prefix
-(1e-4 relative), results identical alone and in a mix of requests, and the
-batch-forming rules."""
+"""GPU tests of the serving loop (ara_submit / ara_serve_step / ara_poll /
+ara_wait): continuous batching of layer requests over trial chunks.
+
+Each request's PML/TVaR against the FP64 oracle on its own trial prefix (1e-4
+relative); results bit-identical alone and in a mix of requests; a short
+request submitted while a long one is in flight finishes first; the rules that
+form a round's passes; admission by the HBM budget (a request that does not
+fit yet waits, one that can never fit is refused at submit); errors.
+"""
 
 import numpy as np
 import pytest
@@ -43,6 +48,14 @@ def world():
     return yet, pool, reqs
 
 
+@pytest.fixture(scope="module")
+def long_world():
+    # 600,000 trials x Poisson(20) over 50,000 events: a whole-YET request spans several chunks
+    yet = synth.make_yet(600_000, 20.0, 50_000, 611)
+    pool = synth.make_elt_pool(6, 3000, 50_000, 612)
+    return yet, pool
+
+
 def _load(eng, yet, pool):
     eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
     eng.load_pool(pool)
@@ -50,57 +63,125 @@ def _load(eng, yet, pool):
 
 def _serve_all(eng, reqs, seed=0):
     tickets = [eng.submit(ids, terms, seed, t_end, RPS) for ids, terms, t_end, _ in reqs]
-    steps = 0
-    while True:
-        n = eng.serve_step()
-        if n == 0:
-            break
-        steps += 1
-    return [eng.poll(tk, len(RPS)) for tk in tickets], steps
+    return [eng.wait(tk, len(RPS)) for tk in tickets]
 
 
 def test_served_requests_match_the_oracle(eng, world):
     yet, pool, reqs = world
     _load(eng, yet, pool)
-    got, steps = _serve_all(eng, reqs, seed=3)
-    assert steps >= 1
+    got = _serve_all(eng, reqs, seed=3)
     for (ids, terms, t_end, sub), res in zip(reqs, got):
-        assert res is not None
         ref = oracle.run_layer(yet, sub, terms, seed=3, trials=np.arange(t_end))
         pml, tvar = oracle.pml_tvar(ref["ylt"], RPS)
         assert np.allclose(res[0], pml, rtol=PML_TOL, atol=1e-9)
         assert np.allclose(res[1], tvar, rtol=PML_TOL, atol=1e-9)
+    st = eng.serve_stats()
+    assert st["queued"] == 0 and st["active"] == 0 and st["rounds_in_flight"] == 0
 
 
 def test_results_identical_alone_and_in_a_mix(eng, world):
     yet, pool, reqs = world
     _load(eng, yet, pool)
-    mixed, _ = _serve_all(eng, reqs, seed=7)
+    mixed = _serve_all(eng, reqs, seed=7)
     for req, res in zip(reqs, mixed):
-        alone, _ = _serve_all(eng, [req], seed=7)
+        alone = _serve_all(eng, [req], seed=7)
         assert np.array_equal(alone[0][0], res[0]) and np.array_equal(alone[0][1], res[1])
 
 
-def test_batches_follow_the_rules(eng, world):
+def test_a_short_request_overtakes_a_long_one_in_flight(eng, long_world):
+    """A whole-YET request is launched; a 10,000-trial request submitted while its
+    first round is on the device joins the next round and finishes first.  Both
+    results are bit-identical to each request served alone."""
+    yet, pool = long_world
+    _load(eng, yet, pool)
+    chunk = eng.serve_stats()["chunk_trials"]
+    assert yet.n_trials > 3 * chunk
+    long_ids, short_ids = pool.elt_ids[:4], pool.elt_ids[2:5]
+    terms = (2e5, 5e6, 1e6, 1e9)
+    t_long = eng.submit(long_ids, terms, 5, yet.n_trials, RPS)
+    assert eng.serve_step() == 0  # launches the long request's first round and returns
+    assert eng.serve_stats()["rounds_in_flight"] >= 1
+    t_short = eng.submit(short_ids, terms, 5, 10_000, RPS)
+    order, res = [], {}
+    while len(order) < 2:
+        eng.serve_step()
+        for tk in (t_long, t_short):
+            if tk not in res:
+                r = eng.poll(tk, len(RPS))
+                if r is not None:
+                    res[tk] = r
+                    order.append(tk)
+    assert order == [t_short, t_long]
+    alone_long = _serve_all(eng, [(long_ids, terms, yet.n_trials, None)], seed=5)[0]
+    alone_short = _serve_all(eng, [(short_ids, terms, 10_000, None)], seed=5)[0]
+    for a, b in ((alone_long, res[t_long]), (alone_short, res[t_short])):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # the short request against the oracle
+    sub = pool.subset([int(i) for i in short_ids])
+    ref = oracle.run_layer(yet, sub, terms, seed=5, trials=np.arange(10_000))
+    pml, tvar = oracle.pml_tvar(ref["ylt"], RPS)
+    assert np.allclose(res[t_short][0], pml, rtol=PML_TOL) and np.allclose(res[t_short][1], tvar, rtol=PML_TOL)
+
+
+def test_rounds_follow_the_rules(eng, world):
     yet, pool, reqs = world
     _load(eng, yet, pool)
     ids, terms, t_end, _ = reqs[0]
-    # at most ARA_MAX_BATCH_LAYERS requests per batch
+    # 40 requests at the same chunk, one seed: passes of at most 32 layers, one round
+    s0 = eng.serve_stats()
     tk = [eng.submit(ids, terms, 0, t_end, RPS) for _ in range(40)]
-    assert eng.serve_step() == 32
-    assert eng.serve_step() == 8
-    assert eng.serve_step() == 0
-    first = [eng.poll(t, len(RPS)) for t in tk]
-    assert all(np.array_equal(first[0][0], r[0]) for r in first)
-    # one seed per batch: requests of another seed wait for a later batch
+    res = [eng.wait(t, len(RPS)) for t in tk]
+    s1 = eng.serve_stats()
+    assert s1["passes_launched"] - s0["passes_launched"] == 2
+    assert s1["rounds_launched"] - s0["rounds_launched"] == 1
+    assert all(np.array_equal(res[0][0], r[0]) and np.array_equal(res[0][1], r[1]) for r in res)
+    # one seed per pass: two seeds share the round in two passes
     a = [eng.submit(ids, terms, 1, t_end, RPS) for _ in range(3)]
     b = [eng.submit(ids, terms, 2, t_end, RPS) for _ in range(3)]
     assert eng.poll(a[0], len(RPS)) is None
-    assert eng.serve_step() == 3
-    assert eng.poll(b[0], len(RPS)) is None
-    assert eng.serve_step() == 3
     for t in a + b:
-        assert eng.poll(t, len(RPS)) is not None
+        eng.wait(t, len(RPS))
+    s2 = eng.serve_stats()
+    assert s2["passes_launched"] - s1["passes_launched"] == 2
+    assert s2["rounds_launched"] - s1["rounds_launched"] == 1
+
+
+def test_admission_follows_the_hbm_budget(world):
+    """Under a budget whose arena holds one large request but not two, a second
+    large request waits for the first to finish (it is not failed) and the small
+    requests behind it go first; every result is bit-identical to serving it
+    alone without a budget; a request that could never fit is refused at submit
+    with ARA_ENOMEM."""
+    from paper_1501_06326_gb300 import ara
+
+    yet, pool, reqs = world
+    free_ctx = ara.Ara(0)
+    _load(free_ctx, yet, pool)
+    probe = ara.Ara(0, 1 << 40)  # a budget that binds nothing: arena = budget - used - workspace
+    _load(probe, yet, pool)
+    fixed = (1 << 40) - probe.serve_stats()["arena_bytes"]
+    probe.close()
+    big, small = 1000, 100
+    arena = 8 * big + 8 * big // 2  # one big request (8 KB), not two
+    eng = ara.Ara(0, fixed + arena)
+    _load(eng, yet, pool)
+    assert 8 * big <= eng.serve_stats()["arena_bytes"] < 16 * big
+    ids, terms, _, _ = reqs[1]
+    tk = [eng.submit(ids, terms, 4, t, RPS) for t in (big, big, small, small)]
+    eng.serve_step()
+    st = eng.serve_stats()
+    assert st["active"] == 3 and st["queued"] == 1  # the second big request waits
+    res = [eng.wait(t, len(RPS)) for t in tk]
+    for t_end, r in zip((big, big, small, small), res):
+        alone = free_ctx.wait(free_ctx.submit(ids, terms, 4, t_end, RPS), len(RPS))
+        assert np.array_equal(alone[0], r[0]) and np.array_equal(alone[1], r[1])
+    bad = ara.Ara(0, fixed + 4096)
+    _load(bad, yet, pool)
+    with pytest.raises(ara.AraError) as e:
+        bad.submit(ids, terms, 4, big, RPS)
+    assert e.value.code == ara.ARA_ENOMEM
+    for e_ in (eng, bad, free_ctx):
+        e_.close()
 
 
 def test_serving_errors(eng, world):
@@ -121,6 +202,13 @@ def test_serving_errors(eng, world):
     with pytest.raises(ara.AraError) as e:
         eng.poll(123456789, len(RPS))
     assert e.value.code == ara.ARA_EINVAL
+    # the YET cannot be replaced under queued requests
+    tk = eng.submit(ids, terms, 0, t_end, RPS)
+    with pytest.raises(ara.AraError) as e:
+        eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
+    assert e.value.code == ara.ARA_EINVAL
+    eng.wait(tk, len(RPS))
+    eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
 
 
 def test_wait_serves_until_the_request_is_done(eng, world):
@@ -128,7 +216,6 @@ def test_wait_serves_until_the_request_is_done(eng, world):
 
     yet, pool, reqs = world
     _load(eng, yet, pool)
-    # requests of two seeds: waiting for a later one runs the steps before it
     t_a = [eng.submit(ids, terms, 11, t_end, RPS) for ids, terms, t_end, _ in reqs[:3]]
     t_b = eng.submit(reqs[3][0], reqs[3][1], 12, reqs[3][2], RPS)
     pml, tvar = eng.wait(t_b, len(RPS))
@@ -136,9 +223,9 @@ def test_wait_serves_until_the_request_is_done(eng, world):
     ref = oracle.run_layer(yet, sub, terms, seed=12, trials=np.arange(t_end))
     rpml, rtvar = oracle.pml_tvar(ref["ylt"], RPS)
     assert np.allclose(pml, rpml, rtol=PML_TOL) and np.allclose(tvar, rtvar, rtol=PML_TOL)
-    for t in t_a:  # finished by the steps that ran before t_b's
-        assert eng.poll(t, len(RPS)) is not None
-    # a timeout that has passed before the first step: the request stays queued
+    for t in t_a:  # they shared t_b's round
+        assert eng.wait(t, len(RPS)) is not None
+    # a timeout that has passed before the first step: the request stays pending
     t_c = eng.submit(ids, terms, 13, t_end, RPS)
     with pytest.raises(ara.AraError) as e:
         eng.wait(t_c, len(RPS), timeout_ns=1)
