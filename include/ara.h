@@ -72,6 +72,14 @@ extern "C" {
  * stands for the pool id in the hit hash of ara_run_layer_diag.  Without it,
  * each (trial, event index, ELT pool id) has its own draw. */
 #define ARA_SHARED_Z 4u
+/* ara_run_layers: pick the losses kernel's configuration (work item of one
+ * trial or of a tile of trials; CTAs per SM) by measurement.  The first pass
+ * of a batch shape (layers, ELTs of the union, trials, hit records per trial)
+ * runs every candidate once, timed with CUDA events, and keeps the fastest
+ * for later passes of that shape; all candidates give the same bits.  Without
+ * the flag a pass uses the cached choice for its shape if there is one, else
+ * the default rule. */
+#define ARA_AUTOTUNE 16u
 
 typedef struct ara_ctx ara_ctx;
 
@@ -136,6 +144,11 @@ typedef struct {
     int32_t block;           /* threads per CTA */
     int32_t smem_bytes;      /* dynamic shared memory per CTA */
     int32_t filter_bits;     /* shared-memory membership filter size in bits */
+    /* ara_run_layers: the losses kernel's configuration (the last pass) */
+    int32_t batch_per_trial;     /* 1: one warp per trial, 0: one warp per tile of trials */
+    int32_t batch_blocks_per_sm; /* resident CTAs per SM of the persistent grid */
+    int32_t batch_tuned;         /* 1: chosen by the autotuner (measured), 0: by the default rule */
+    int32_t reserved;
 } ara_stats;
 
 /* Device time accumulated over the ara_run_layer* and ara_pml_tvar calls
@@ -382,6 +395,32 @@ ARA_API int ara_debug_uniforms(ara_ctx *ctx, uint64_t seed, int64_t n, const int
 ARA_API int ara_debug_record_losses(ara_ctx *ctx, int64_t n, const float *mean, const float *sigma,
                                     const float *exposure, const float *z, int32_t newton_only, float *out,
                                     int32_t *iters_out);
+
+/* Trial shards across GPUs (Section 5 treats trials as independent): a rank
+ * that holds the YLT of trials [trial_offset, trial_offset + n) needs to send
+ * only its m largest year losses for the PML and TVaR of the whole YLT at
+ * return periods of at least N_total / m.
+ *
+ * ara_top_m writes the m largest year losses of ylt (host or device, n >= 1
+ * doubles) in descending order, ties by trial index, to values_out, and their
+ * global trial indices (trial_offset + local index) to trials_out (m entries
+ * each, host or device memory).  When m > n the last m - n entries are
+ * (-INFINITY, -1).  Runs the device radix sort of the YLT.
+ * Errors: ARA_EINVAL (n < 1 or >= 2^31, m < 1, trial_offset < 0), ARA_ENOMEM,
+ * ARA_ECUDA.
+ *
+ * ara_merge_top (host memory only, no context, no GPU) takes the ranks'
+ * lists concatenated (count entries; -INFINITY entries are ignored), orders
+ * them by year loss, largest first, ties by global trial index, and writes
+ * for each of the n_rp return periods (each >= 1) PML = the m-th value and
+ * TVaR = the mean of the first m (m = ceil(n_total / RP), at least 1 and at
+ * most n_total), the TVaR sum compensated (Neumaier) in that order: the
+ * definitions of ara_pml_tvar over the whole YLT.
+ * Errors: ARA_EINVAL (bad arguments, or fewer than m finite values). */
+ARA_API int ara_top_m(ara_ctx *ctx, const double *ylt, int64_t n, int64_t m, int64_t trial_offset,
+                      double *values_out, int64_t *trials_out);
+ARA_API int ara_merge_top(const double *values, const int64_t *trials, int64_t count, int64_t n_total,
+                          const double *return_periods, int32_t n_rp, double *pml_out, double *tvar_out);
 
 /* PML and TVaR without any device allocation.
  *

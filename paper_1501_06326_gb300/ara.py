@@ -27,6 +27,7 @@ ARA_OK, ARA_EINVAL, ARA_ENOMEM, ARA_ENOTLOADED, ARA_ECUDA, ARA_ETIMEOUT, ARA_EAG
 ARA_PRIMARY_ONLY = 1
 ARA_NEWTON_ONLY = 2
 ARA_SHARED_Z = 4
+ARA_AUTOTUNE = 16
 ARA_MAX_LAYER_ELTS = 32
 ARA_MAX_BATCH_LAYERS = 32
 ARA_MAX_BATCH_ELTS = 64
@@ -43,6 +44,7 @@ EXPORTED = (
     "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
     "ara_pml_tvar_noalloc", "ara_run_layers", "ara_submit", "ara_serve_step", "ara_poll", "ara_load_xelts",
     "ara_run_layer_events", "ara_wait", "ara_load_yet_async", "ara_finish_yet", "ara_serve_stats",
+    "ara_top_m", "ara_merge_top",
 )
 ARA_NOALLOC_MAX_RP = 64
 
@@ -99,6 +101,10 @@ class Stats(ctypes.Structure):
         ("block", ctypes.c_int32),
         ("smem_bytes", ctypes.c_int32),
         ("filter_bits", ctypes.c_int32),
+        ("batch_per_trial", ctypes.c_int32),
+        ("batch_blocks_per_sm", ctypes.c_int32),
+        ("batch_tuned", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -165,6 +171,8 @@ def load_library(path: str = LIB_PATH):
     lib.ara_poll.argtypes = [P, i64, P, P]
     lib.ara_wait.argtypes = [P, i64, P, P, u64]
     lib.ara_serve_stats.argtypes = [P, ctypes.POINTER(ServeInfo)]
+    lib.ara_top_m.argtypes = [P, P, i64, i64, i64, P, P]
+    lib.ara_merge_top.argtypes = [P, P, i64, i64, P, i32, P, P]
     lib.ara_pml_tvar.argtypes = [P, P, i64, P, i32, P, P]
     lib.ara_sort_ylt.argtypes = [P, P, i64, P]
     lib.ara_debug_uniforms.argtypes = [P, u64, i64, P, P, P, P]
@@ -285,6 +293,30 @@ def ara_serve_step(h, n_done_out):
 
 def ara_serve_stats(h, out):
     return load_library().ara_serve_stats(h, ctypes.byref(out))
+
+
+def ara_top_m(h, ylt, n, m, trial_offset, values_out, trials_out):
+    return load_library().ara_top_m(h, _ptr(ylt, np.float64), n, m, trial_offset, _ptr(values_out, np.float64),
+                                    _ptr(trials_out, np.int64))
+
+
+def ara_merge_top(values, trials, count, n_total, rps, n_rp, pml_out, tvar_out):
+    return load_library().ara_merge_top(_ptr(values, np.float64), _ptr(trials, np.int64), count, n_total,
+                                        _ptr(rps, np.float64), n_rp, _ptr(pml_out, np.float64),
+                                        _ptr(tvar_out, np.float64))
+
+
+def merge_top(values, trials, n_total: int, return_periods):
+    """PML and TVaR of a trial-sharded YLT from the ranks' ara_top_m lists
+    (concatenated host arrays): ara_merge_top, which needs no GPU."""
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    t = np.ascontiguousarray(trials, dtype=np.int64)
+    rps = np.ascontiguousarray(return_periods, dtype=np.float64)
+    pml, tvar = np.zeros(rps.shape[0]), np.zeros(rps.shape[0])
+    rc = ara_merge_top(v, t, v.shape[0], int(n_total), rps, rps.shape[0], pml, tvar)
+    if rc != ARA_OK:
+        raise AraError(rc, "ara_merge_top: bad arguments or fewer than m finite values")
+    return pml, tvar
 
 
 def ara_poll(h, ticket, pml_out, tvar_out):
@@ -419,11 +451,11 @@ class Ara:
 
     @staticmethod
     def make_layer(elt_ids: Sequence[int], layer_terms, primary_only: bool = False, newton_only: bool = False,
-                   shared_z: bool = False):
+                   shared_z: bool = False, autotune: bool = False):
         ids = (ctypes.c_int32 * len(elt_ids))(*[int(i) for i in elt_ids])
         occ_r, occ_l, agg_r, agg_l = (float(v) for v in layer_terms)
         flags = ((ARA_PRIMARY_ONLY if primary_only else 0) | (ARA_NEWTON_ONLY if newton_only else 0)
-                 | (ARA_SHARED_Z if shared_z else 0))
+                 | (ARA_SHARED_Z if shared_z else 0) | (ARA_AUTOTUNE if autotune else 0))
         lay = Layer(len(elt_ids), ids, occ_r, occ_l, agg_r, agg_l, flags)
         lay._ids = ids  # keep the id array alive with the struct
         return lay
@@ -456,10 +488,12 @@ class Ara:
         return int(rows.n_rows)
 
     def run_layers(self, layers, seed: int, trial_begin: int, trial_end: int, ylt_out,
-                   primary_only: bool = False, newton_only: bool = False, shared_z: bool = False) -> None:
+                   primary_only: bool = False, newton_only: bool = False, shared_z: bool = False,
+                   autotune: bool = False) -> None:
         """Several layers in one pass.  ``layers``: a sequence of (elt_ids, layer_terms);
-        ``ylt_out``: (n_layers, trial_end - trial_begin) float64, C order."""
-        made = [self.make_layer(ids, terms, primary_only, newton_only, shared_z) for ids, terms in layers]
+        ``ylt_out``: (n_layers, trial_end - trial_begin) float64, C order.  ``autotune``:
+        ARA_AUTOTUNE (measure the losses kernel's configurations on a new shape)."""
+        made = [self.make_layer(ids, terms, primary_only, newton_only, shared_z, autotune) for ids, terms in layers]
         arr = (Layer * len(made))(*made)
         self._check(ara_run_layers(self._h, len(made), arr, seed, trial_begin, trial_end, ylt_out))
 
@@ -479,6 +513,14 @@ class Ara:
         n = np.zeros(1, np.int32)
         self._check(ara_serve_step(self._h, n))
         return int(n[0])
+
+    def top_m(self, ylt, m: int, trial_offset: int = 0, values_out=None, trials_out=None):
+        """The m largest year losses (descending, ties by trial) and their global
+        trial indices (ara_top_m); host arrays unless outputs are given."""
+        vals = np.zeros(m) if values_out is None else values_out
+        trials = np.zeros(m, np.int64) if trials_out is None else trials_out
+        self._check(ara_top_m(self._h, ylt, _len(ylt), int(m), int(trial_offset), vals, trials))
+        return vals, trials
 
     def serve_stats(self) -> dict:
         """Queue state and totals of the serving loop (ara_serve_stats)."""

@@ -117,6 +117,10 @@ struct ara_ctx {
   int num_sms = 0;
   int max_smem = 0;
   bool no_timing = false;   // serving passes record no timing events
+  // the batched losses kernel's configuration per batch shape, chosen by measurement (ARA_AUTOTUNE)
+  std::map<std::vector<int64_t>, std::pair<int, int>> tune_cache;  // shape -> (per_trial, blocks per SM)
+  int32_t last_per_trial = 0, last_blocks = 0, last_tuned = 0;
+  cudaEvent_t tune_ev[2] = {nullptr, nullptr};
   // serving (continuous batching)
   std::deque<int64_t> serve_queue;      // submitted, not yet admitted, in arrival order
   std::vector<int64_t> serve_active;    // admitted and not finished, in admission order
@@ -1036,21 +1040,61 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
     recs_per_trial += reach * static_cast<double>(c->pool.find(uni[i])->second.n);
   }
   recs_per_trial *= static_cast<double>(c->n_events) / (static_cast<double>(c->n_trials) * c->catalogue);
-  // one warp per trial once a trial's records fill a warp's rounds; else one warp per tile
-  const bool per_trial = recs_per_trial >= 192.0;
+  // The losses kernel's configuration: the work item (one warp per trial, or per
+  // tile of trials) and the CTAs per SM.  Default rule: one warp per trial once a
+  // trial's records fill a warp's rounds, and all the CTAs an SM holds.  Every
+  // configuration adds the same fixed-point numbers, so none changes a result.
+  const std::vector<int64_t> shape = {n_layers, static_cast<int64_t>(uni.size()), t1 - t0,
+                                      static_cast<int64_t>(std::lround(4.0 * std::log2(recs_per_trial + 1.0)))};
+  int per_trial = recs_per_trial >= 192.0 ? 1 : 0, blocks = ara::kBatchBlocksPerSm;
+  const auto cached = c->tune_cache.find(shape);
+  const bool tune = cached == c->tune_cache.end() && (layers[0].flags & ARA_AUTOTUNE);
+  if (cached != c->tune_cache.end()) {
+    per_trial = cached->second.first;
+    blocks = cached->second.second;
+  }
   const int64_t warps = ara::kBatchThreads / 32;
-  const int64_t items = per_trial ? pl.n_tiles * ara::kWarpTrials : pl.n_tiles;
-  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(c->num_sms * ara::kBatchBlocksPerSm,
-                                                                           (items + warps - 1) / warps)));
+  auto grid_of = [&](int pt, int b) {
+    const int64_t items = pt ? pl.n_tiles * ara::kWarpTrials : pl.n_tiles;
+    return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(c->num_sms) * b,
+                                                                   (items + warps - 1) / warps)));
+  };
   int launched = 0;
   if ((rc = launch_index_and_gather(c, pl, who, &launched))) return rc;
+  if (tune) {
+    // every candidate once on this pass's records, timed on the stream; the fastest is kept
+    float best = 0.0f;
+    for (auto& e : c->tune_ev)
+      if (!e) ARA_CUDA(c, cudaEventCreate(&e));
+    for (int pt = 0; pt < 2; ++pt)
+      for (int b = 2; b <= ara::kBatchBlocksPerSm; ++b) {
+        ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 4 * sizeof(unsigned long long), c->stream));
+        ARA_CUDA(c, cudaEventRecord(c->tune_ev[0], c->stream));
+        ARA_CUDA(c, ara::launch_losses_batch(p, pt != 0, grid_of(pt, b), c->stream));
+        ARA_CUDA(c, cudaEventRecord(c->tune_ev[1], c->stream));
+        ARA_CUDA(c, cudaEventSynchronize(c->tune_ev[1]));
+        float ms = 0.0f;
+        ARA_CUDA(c, cudaEventElapsedTime(&ms, c->tune_ev[0], c->tune_ev[1]));
+        launched += 1;
+        if (best == 0.0f || ms < best) {
+          best = ms;
+          per_trial = pt;
+          blocks = b;
+        }
+      }
+    c->tune_cache[shape] = {per_trial, blocks};
+    ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 4 * sizeof(unsigned long long), c->stream));
+  }
   cudaEvent_t la, lb;
   if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
   ARA_CUDA(c, record_ev(la, c->stream));
-  ARA_CUDA(c, ara::launch_losses_batch(p, per_trial, grid, c->stream));
+  ARA_CUDA(c, ara::launch_losses_batch(p, per_trial != 0, grid_of(per_trial, blocks), c->stream));
   ARA_CUDA(c, record_ev(lb, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   launched += 1;
+  c->last_per_trial = per_trial;
+  c->last_blocks = blocks;
+  c->last_tuned = cached != c->tune_cache.end() || tune ? 1 : 0;
   c->launches += launched;
   if (!ylt_dev) {
     ARA_CUDA(c, cudaMemcpyAsync(ylt_out, d_ylt, sizeof(double) * n_out * n_layers, cudaMemcpyDeviceToHost,
@@ -1060,6 +1104,9 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
   int64_t elts = 0;
   for (int32_t l = 0; l < n_layers; ++l) elts += static_cast<int64_t>(lids[l].size());
   record_pass_stats(c, pl, t0, t1, elts);
+  c->stats.batch_per_trial = c->last_per_trial;
+  c->stats.batch_blocks_per_sm = c->last_blocks;
+  c->stats.batch_tuned = c->last_tuned;
   return ARA_OK;
 }
 
@@ -1592,6 +1639,74 @@ int ara_pml_tvar(ara_ctx* c, const double* ylt, int64_t n, const double* rps, in
   return ARA_OK;
 }
 
+int ara_top_m(ara_ctx* c, const double* ylt, int64_t n, int64_t m, int64_t trial_offset, double* values_out,
+              int64_t* trials_out) {
+  static const char* who = "ara_top_m";
+  int rc = bind(c);
+  if (rc) return rc;
+  if (!ylt || n < 1 || m < 1 || trial_offset < 0 || !values_out || !trials_out)
+    return fail(c, ARA_EINVAL, "%s: bad arguments", who);
+  if (n >= (int64_t(1) << 31)) return fail(c, ARA_EINVAL, "%s: at most 2^31 - 1 trials", who);
+  const double* d_ylt = ylt;
+  if (!is_device_ptr(ylt)) {
+    if ((rc = reserve(c, c->in_tmp, sizeof(double) * n))) return rc;
+    ARA_CUDA(c, cudaMemcpyAsync(c->in_tmp.ptr, ylt, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    d_ylt = static_cast<const double*>(c->in_tmp.ptr);
+  }
+  const bool vals_dev = is_device_ptr(values_out), trials_dev = is_device_ptr(trials_out);
+  // scratch: the sort's, then the order of all n, then staged outputs for host arrays
+  const size_t sort_bytes = (ara::sort_scratch_bytes(n) + 255) & ~size_t(255);
+  const size_t order_bytes = (sizeof(int64_t) * static_cast<size_t>(n) + 255) & ~size_t(255);
+  const size_t stage_bytes = (vals_dev && trials_dev) ? 0 : 2 * sizeof(int64_t) * static_cast<size_t>(m);
+  if ((rc = reserve(c, c->sel, sort_bytes + order_bytes + stage_bytes))) return rc;
+  char* base = static_cast<char*>(c->sel.ptr);
+  int64_t* d_order = reinterpret_cast<int64_t*>(base + sort_bytes);
+  double* d_vals = vals_dev ? values_out : reinterpret_cast<double*>(base + sort_bytes + order_bytes);
+  int64_t* d_trials = trials_dev ? trials_out : reinterpret_cast<int64_t*>(base + sort_bytes + order_bytes) + m;
+  int launched = 0;
+  ARA_CUDA(c, ara::sort_desc_device(d_ylt, n, d_order, c->sel.ptr, c->stream, &launched));
+  ARA_CUDA(c, ara::top_gather_device(d_ylt, d_order, std::min(m, n), m, trial_offset, d_vals, d_trials, c->stream));
+  c->launches += launched + 1;
+  if (!vals_dev)
+    ARA_CUDA(c, cudaMemcpyAsync(values_out, d_vals, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream));
+  if (!trials_dev)
+    ARA_CUDA(c, cudaMemcpyAsync(trials_out, d_trials, sizeof(int64_t) * m, cudaMemcpyDeviceToHost, c->stream));
+  if (!vals_dev || !trials_dev || !is_device_ptr(ylt)) ARA_CUDA(c, cudaStreamSynchronize(c->stream));
+  return ARA_OK;
+}
+
+int ara_merge_top(const double* values, const int64_t* trials, int64_t count, int64_t n_total, const double* rps,
+                  int32_t n_rp, double* pml_out, double* tvar_out) {
+  if (!values || !trials || count < 1 || n_total < 1 || !rps || n_rp < 1 || !pml_out || !tvar_out)
+    return ARA_EINVAL;
+  for (int32_t r = 0; r < n_rp; ++r)
+    if (!(rps[r] >= 1.0) || !std::isfinite(rps[r])) return ARA_EINVAL;
+  // the finite entries, by year loss (largest first), ties by global trial index
+  std::vector<int64_t> idx;
+  idx.reserve(static_cast<size_t>(count));
+  for (int64_t i = 0; i < count; ++i)
+    if (std::isfinite(values[i])) idx.push_back(i);
+  std::sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+    return values[a] > values[b] || (values[a] == values[b] && trials[a] < trials[b]);
+  });
+  for (int32_t r = 0; r < n_rp; ++r) {
+    const double mf = std::ceil(static_cast<double>(n_total) / rps[r]);
+    const int64_t m = std::min<int64_t>(std::max<int64_t>(static_cast<int64_t>(mf), 1), n_total);
+    if (m > static_cast<int64_t>(idx.size())) return ARA_EINVAL;  // a rank sent fewer than m values
+    // TVaR: Neumaier's compensated sum in FP64, in the merged order (the same bits on every host)
+    double sum = 0.0, comp = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+      const double v = values[idx[i]];
+      const double t = sum + v;
+      comp += (std::fabs(sum) >= std::fabs(v)) ? (sum - t) + v : (v - t) + sum;
+      sum = t;
+    }
+    pml_out[r] = values[idx[m - 1]];
+    tvar_out[r] = (sum + comp) / static_cast<double>(m);
+  }
+  return ARA_OK;
+}
+
 int ara_sort_ylt(ara_ctx* c, const double* ylt, int64_t n, int64_t* order_out) {
   int rc = bind(c);
   if (rc) return rc;
@@ -1736,6 +1851,8 @@ void ara_destroy(ara_ctx* c) {
     if (e) cudaEventDestroy(e);
   for (auto& e : c->ev_pool) cudaEventDestroy(e);
   for (auto& r : c->serve_rounds) cudaEventDestroy(r.ev);
+  for (auto& e : c->tune_ev)
+    if (e) cudaEventDestroy(e);
   for (auto& e : c->serve_ev_free) cudaEventDestroy(e);
   if (c->serve_host) cudaFreeHost(c->serve_host);
   if (c->yet_ready) cudaEventDestroy(c->yet_ready);

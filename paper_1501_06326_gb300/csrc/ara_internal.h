@@ -259,6 +259,10 @@ size_t select_scratch_bytes(int64_t n);
 cudaError_t pml_tvar_device(const double* ylt, int64_t n, const double* rps_host, int32_t n_rp, double* pml,
                             double* tvar, void* scratch, size_t scratch_bytes, cudaStream_t s, int* n_launch);
 size_t sort_scratch_bytes(int64_t n);
+// vals/trials[i] = ylt[order[i]], trial_offset + order[i] for i < m_valid;
+// (-inf, -1) for m_valid <= i < m.
+cudaError_t top_gather_device(const double* ylt, const int64_t* order, int64_t m_valid, int64_t m, int64_t trial_offset,
+                              double* vals, int64_t* trials, cudaStream_t s);
 cudaError_t sort_desc_device(const double* ylt, int64_t n, int64_t* order, void* scratch, cudaStream_t s,
                              int* n_launch);
 

@@ -658,6 +658,36 @@ cudaError_t sort_desc_device(const double* ylt, int64_t n, int64_t* order, void*
   return cudaSuccess;  // 8 swaps: the result is back in idx_a == order
 }
 
+namespace {
+
+// The first m_valid entries of a descending order: values and global trial
+// indices (trial_offset + local index); entries m_valid..m-1 are padding
+// (-inf, -1).
+__global__ void k_top_gather(const double* ylt, const int64_t* order, int64_t m_valid, int64_t m,
+                             int64_t trial_offset, double* vals, int64_t* trials) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < m; i += stride) {
+    if (i < m_valid) {
+      const int64_t t = order[i];
+      vals[i] = ylt[t];
+      trials[i] = trial_offset + t;
+    } else {
+      vals[i] = -__longlong_as_double(0x7FF0000000000000ll);
+      trials[i] = -1;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t top_gather_device(const double* ylt, const int64_t* order, int64_t m_valid, int64_t m, int64_t trial_offset,
+                              double* vals, int64_t* trials, cudaStream_t s) {
+  const int64_t blocks = (m + 255) / 256;
+  k_top_gather<<<static_cast<int>(blocks < 1024 ? (blocks > 0 ? blocks : 1) : 1024), 256, 0, s>>>(
+      ylt, order, m_valid, m, trial_offset, vals, trials);
+  return cudaGetLastError();
+}
+
 }  // namespace ara
 
 // =============================================================== allocation-free PML / TVaR

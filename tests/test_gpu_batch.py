@@ -203,3 +203,22 @@ def test_batch_with_empty_and_long_trials(eng):
     out = _run_batch(eng, yet, pool, layers, 2, 3, 200)
     for l, (ids, terms, sub) in enumerate(layers):
         check_ylt(out[l], oracle.run_layer(yet, sub, terms, seed=2, trials=np.arange(3, 200)))
+
+
+def test_autotuner_keeps_the_results_and_caches_its_choice(eng, small_batch):
+    """ARA_AUTOTUNE measures the losses kernel's configurations on the first pass
+    of a batch shape and keeps the fastest; every configuration gives the same
+    bits, so the tuned pass equals the default one, and a later pass of the same
+    shape (without the flag) reuses the choice."""
+    yet, pool, layers = small_batch
+    t1 = yet.n_trials - 3  # a shape of its own: nothing cached for it yet
+    base = _run_batch(eng, yet, pool, layers, 5, t1=t1)
+    assert eng.stats()["batch_tuned"] == 0
+    tuned = _run_batch(eng, yet, pool, layers, 5, t1=t1, autotune=True)
+    st = eng.stats()
+    assert st["batch_tuned"] == 1 and st["batch_per_trial"] in (0, 1) and 2 <= st["batch_blocks_per_sm"] <= 4
+    again = _run_batch(eng, yet, pool, layers, 5, t1=t1)
+    st2 = eng.stats()
+    assert st2["batch_tuned"] == 1
+    assert (st2["batch_per_trial"], st2["batch_blocks_per_sm"]) == (st["batch_per_trial"], st["batch_blocks_per_sm"])
+    assert np.array_equal(base, tuned) and np.array_equal(base, again)

@@ -340,6 +340,28 @@ def test_pml_tvar_and_sort(eng, n):
     assert np.array_equal(order, np.lexsort((np.arange(n), -y)))
 
 
+@pytest.mark.parametrize("n,m", [(1, 3), (999, 10), (100_000, 1000), (100_000, 100_007)])
+def test_top_m_against_a_host_sort(eng, n, m):
+    """ara_top_m: the m largest year losses, descending, ties by trial index, with
+    global trial indices; padding (-inf, -1) past n; host and device outputs."""
+    import torch
+
+    rng = np.random.default_rng(n + m)
+    y = np.round(rng.lognormal(8, 2, n), 1)  # ties
+    y[rng.random(n) < 0.4] = 0.0
+    off = 12_345
+    vals, trials = eng.top_m(y, m, off)
+    order = oracle.sort_desc(y)[:m]
+    k = order.size
+    assert np.array_equal(vals[:k], y[order]) and np.array_equal(trials[:k], off + order)
+    assert np.isneginf(vals[k:]).all() and (trials[k:] == -1).all()
+    dv = torch.zeros(m, dtype=torch.float64, device="cuda")
+    dt = torch.zeros(m, dtype=torch.int64, device="cuda")
+    eng.top_m(torch.from_numpy(y).cuda(), m, off, dv, dt)
+    torch.cuda.synchronize()
+    assert np.array_equal(dv.cpu().numpy(), vals) and np.array_equal(dt.cpu().numpy(), trials)
+
+
 # ------------------------------------------------------------------ full size (every trial)
 # The plain relative error |dY| / Y is asserted where the year loss is at
 # least this share of the trial's gross loss.  Below it Y is a small

@@ -1,6 +1,12 @@
-"""Multi-rank PML/TVaR merge (trial shards, one all-gather of top-m values),
-run as world_size-2 gloo ranks on CPU and checked against the oracle on the
-concatenated YLT."""
+"""Multi-rank PML/TVaR over trial shards: each rank sends its m largest year
+losses with their global trial indices, one all-gather, and the C-ABI merge
+(ara_merge_top, host code, no GPU) gives the PML/TVaR of the whole YLT.
+
+Run as world_size-2 gloo ranks on CPU.  A rank's top m comes from the
+oracle's sort here (on the GPU it is ara_top_m, tested in test_gpu_parity.py);
+the merged result is checked against the oracle on the concatenated YLT
+(Section 2.3).
+"""
 
 import os
 import socket
@@ -9,7 +15,6 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_1501_06326_gb300.shard import global_pml_tvar, local_top
 
 RPS = (2.0, 100.0, 250.0)
 
@@ -24,14 +29,25 @@ def _free_port():
 
 def _shard(rank, n):
     rng = np.random.default_rng(100 + rank)
-    y = np.round(rng.lognormal(6, 2, n), 1)
+    y = np.round(rng.lognormal(6, 2, n), 1)  # ties within and across shards
     y[rng.random(n) < 0.3] = 0.0
     return y
+
+
+def _local_top(y, m, offset):
+    order = oracle.sort_desc(y)[:m]
+    vals = np.full(m, -np.inf)
+    trials = np.full(m, -1, np.int64)
+    vals[: order.size] = y[order]
+    trials[: order.size] = offset + order
+    return vals, trials
 
 
 def _worker(rank, world, port, n, q):
     import torch
     import torch.distributed as dist
+
+    from paper_1501_06326_gb300 import ara
 
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -39,10 +55,12 @@ def _worker(rank, world, port, n, q):
     try:
         y = _shard(rank, n)
         m = int(np.ceil(world * n / min(RPS)))
-        top = torch.from_numpy(local_top(y, m))
-        gathered = [torch.empty_like(top) for _ in range(world)]
-        dist.all_gather(gathered, top)
-        pml, tvar = global_pml_tvar([g.numpy() for g in gathered], world * n, RPS)
+        vals, trials = _local_top(y, m, rank * n)
+        gv = [torch.empty(m, dtype=torch.float64) for _ in range(world)]
+        gt = [torch.empty(m, dtype=torch.int64) for _ in range(world)]
+        dist.all_gather(gv, torch.from_numpy(vals))
+        dist.all_gather(gt, torch.from_numpy(trials))
+        pml, tvar = ara.merge_top(torch.cat(gv).numpy(), torch.cat(gt).numpy(), world * n, RPS)
         q.put((rank, pml, tvar))
     finally:
         dist.destroy_process_group()
@@ -69,8 +87,29 @@ def test_two_rank_merge_matches_oracle():
         assert np.allclose(tvar, rtvar, rtol=1e-14, atol=0)
 
 
-def test_local_top_pads_short_shards():
-    t = local_top(np.array([3.0, 1.0]), 4)
-    assert t[0] == 3.0 and t[1] == 1.0 and np.isneginf(t[2:]).all()
-    with pytest.raises(ValueError):
-        global_pml_tvar([t], 6, (1.0,))
+@pytest.mark.parametrize("world", [1, 3, 8])
+def test_merge_of_uneven_shards_matches_oracle(world):
+    from paper_1501_06326_gb300 import ara
+
+    rng = np.random.default_rng(world)
+    sizes = rng.integers(1, 3000, world)
+    shards = [np.round(rng.lognormal(5, 1.5, s), 0) for s in sizes]  # many ties
+    n_total = int(sizes.sum())
+    rps = np.array([1.0, 3.0, 100.0, 1e6])
+    m = int(np.ceil(n_total / rps.min()))
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    tops = [_local_top(y, m, o) for y, o in zip(shards, offs)]
+    pml, tvar = ara.merge_top(np.concatenate([t[0] for t in tops]), np.concatenate([t[1] for t in tops]),
+                              n_total, rps)
+    rpml, rtvar = oracle.pml_tvar(np.concatenate(shards), rps)
+    assert np.array_equal(pml, rpml)
+    assert np.allclose(tvar, rtvar, rtol=1e-14, atol=0)
+
+
+def test_merge_rejects_too_few_values():
+    from paper_1501_06326_gb300 import ara
+
+    with pytest.raises(ara.AraError):
+        ara.merge_top(np.array([3.0, 1.0, -np.inf]), np.array([0, 1, -1]), 6, [1.0])
+    with pytest.raises(ara.AraError):
+        ara.merge_top(np.array([3.0]), np.array([0]), 1, [0.5])
