@@ -23,8 +23,9 @@ of the same workload.
 
 Launch: ``python bench.py [--gpus N --steps K --warmup W]``; for N > 1 under
 torchrun (one process per GPU, weak scaling: every rank runs its own
-1M-trial shard with its own seed; the exact global PML/TVaR comes from one
-all-gather of each rank's top m = ceil(N_total / RP) year losses).
+1M-trial shard with its own seed; the exact global PML/TVaR comes from each
+rank's top m = ceil(N_total / RP) year losses (ara_top_m), one all-gather of
+them, and the C-ABI merge ara_merge_top).
 """
 
 from __future__ import annotations
@@ -289,19 +290,23 @@ def run_gpu(args):
         ms_max = float(t.item())
     value = ws * evals_per_step / (ms_max * 1e-3)
 
-    # ---- global PML/TVaR across ranks: all-gather of each rank's top m year losses
+    # ---- global PML/TVaR across ranks: each rank's top m year losses (ara_top_m on the
+    # device), one all-gather of them over NCCL, and the merge (ara_merge_top)
     global_pml = None
     if ws > 1:
         import torch.distributed as dist
 
-        from paper_1501_06326_gb300.shard import global_pml_tvar, local_top
-
         total = ws * n_trials
         m_max = int(math.ceil(total / min(RETURN_PERIODS)))
-        top = torch.from_numpy(local_top(ylt.cpu().numpy(), m_max)).to(dev)
-        gathered = [torch.empty_like(top) for _ in range(ws)]
-        dist.all_gather(gathered, top)
-        global_pml = global_pml_tvar([g.cpu().numpy() for g in gathered], total, RETURN_PERIODS)
+        top_v = torch.empty(m_max, dtype=torch.float64, device=dev)
+        top_t = torch.empty(m_max, dtype=torch.int64, device=dev)
+        eng.top_m(ylt, m_max, rank * n_trials, top_v, top_t)
+        torch.cuda.synchronize(dev)
+        gv = [torch.empty_like(top_v) for _ in range(ws)]
+        gt = [torch.empty_like(top_t) for _ in range(ws)]
+        dist.all_gather(gv, top_v)
+        dist.all_gather(gt, top_t)
+        global_pml = ara.merge_top(torch.cat(gv).cpu().numpy(), torch.cat(gt).cpu().numpy(), total, RETURN_PERIODS)
 
     # ---- roofline of the layer kernels (gather + losses: the whole per-layer hot
     # path between the index build and PML/TVaR) against the layer's algorithmic bytes
@@ -380,8 +385,8 @@ def run_gpu(args):
 
     # ---- two-part secondary uncertainty (correlated sigma) on the same layer; the plain
     # layer pass is timed here too, on the same stream, for the comparison
-    correlated = events = None
-    if ws == 1 and not (args.no_correlated and args.no_events):
+    correlated = events = stress = None
+    if ws == 1 and not (args.no_correlated and args.no_events and args.no_stress):
         eng.load_pool(pool)
 
         def plain_layer():
@@ -404,6 +409,9 @@ def run_gpu(args):
             eng.load_pool(pool)
         if not args.no_events:
             events = _events_leg(eng, torch, dev, stream, pool, terms, n_trials, seed, ms_plain_layer, args)
+        if not args.no_stress and n_trials == spec["n_trials"]:
+            stress = _stress_leg(eng, synth, torch, dev, stream, n_trials, n_events, ms_plain_layer, args)
+            eng.load_pool(pool)
 
     # ---- batched layers (several layers in one pass over the YET) against one pass per layer
     batched = None
@@ -441,6 +449,8 @@ def run_gpu(args):
             line["correlated"] = correlated
         if events is not None:
             line["events"] = events
+        if stress is not None:
+            line["stress"] = stress
         if batched is not None:
             line["batched"] = batched
         if serving is not None:
@@ -452,6 +462,48 @@ def run_gpu(args):
 
         dist.destroy_process_group()
     return 0
+
+
+def _stress_leg(eng, synth, torch, dev, stream, n_trials, n_events, ms_plain, args):
+    """The precision-stress workload: the paper-1m YET and 15 ELTs x 10,000 records
+    whose Beta shapes are log-uniform over [0.2, 50] (heavy-tailed small shapes
+    included), timed with CUDA events like the plain layer, with the count of
+    pairs that ran the FP32 Halley iteration.  Its errors against the FP64 oracle
+    over all 1M trials are measured by the parity tests, not here."""
+    spec = synth.WORKLOADS["stress-1m"]
+    pool = synth.make_elt_pool(spec["n_elts"], spec["entries"], spec["catalogue"], spec["elt_seed"],
+                               recipe=spec["recipe"])
+    with open(os.path.join(ROOT, "tests", "golden", "workload_terms.json")) as fh:
+        terms = json.load(fh)["stress-1m"]["layer_terms"]
+    eng.load_pool(pool)
+    out = torch.empty(n_trials, dtype=torch.float64, device=dev)
+
+    def layer():
+        eng.run_layer(pool.elt_ids, terms, 0, 0, n_trials, out)
+
+    for _ in range(3):
+        layer()
+    torch.cuda.synchronize(dev)
+    eng.timing(reset=True)
+    steps = max(2, min(args.steps, 10))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        layer()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    tm = eng.timing(reset=True)
+    calls = max(tm["layer_calls"], 1)
+    st = eng.stats()
+    return {"workload": "stress-1m: the paper-1m YET, 15 ELTs x 10,000 records, Beta shapes log-uniform in "
+                        "[0.2, 50], percentile terms",
+            "steps": steps, "ms_layer": ms, "ms_layer_plain": ms_plain,
+            "evals_per_s": n_events * pool.n_elts / (ms * 1e-3),
+            "gather_ms": tm["gather_ms"] / calls, "losses_ms": tm["losses_ms"] / calls,
+            "pairs": st["n_pairs_hit"], "halley_pairs": st["n_newton"], "nonconverged": st["n_nonconverged"],
+            "errors": "against the FP64 oracle over all 1M trials: tests/test_gpu_parity.py "
+                      "test_stress_1m_layer_full_parity"}
 
 
 def _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args):
@@ -470,6 +522,10 @@ def _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args)
     def batch_step():
         eng.run_layers(layers, seed, 0, n_trials, out)
 
+    # the default rule's configuration first, then the autotuner's (its first pass measures
+    # the candidates and caches the fastest for this shape; later passes reuse it)
+    ms_default = None
+
     def plain_step():
         for l, (ids, terms) in enumerate(layers):
             eng.run_layer(ids, terms, seed, 0, n_trials, out[l])
@@ -487,14 +543,22 @@ def _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args)
         return a.elapsed_time(b) / steps
 
     steps = max(2, min(args.steps, 5))
+    ms_default = timed(batch_step, steps)
+    st_default = eng.stats()
+    eng.run_layers(layers, seed, 0, n_trials, out, autotune=True)
     ms_batch = timed(batch_step, steps)
+    st = eng.stats()
     ms_plain = timed(plain_step, steps)
     evals = n_events * sum(len(ids) for ids, _ in layers)
     return {"workload": f"batched-16: the {n_trials:,}-trial YET, 16 layers of 1..32 ELTs from a pool of "
                         f"{spec['n_elts']} x {spec['entries']:,} records",
             "layers": len(layers), "steps": steps, "ms_batched": ms_batch, "ms_plain": ms_plain,
             "layers_per_s": len(layers) / (ms_batch * 1e-3), "plain_layers_per_s": len(layers) / (ms_plain * 1e-3),
-            "speedup": ms_plain / ms_batch, "evals_per_s": evals / (ms_batch * 1e-3)}
+            "speedup": ms_plain / ms_batch, "evals_per_s": evals / (ms_batch * 1e-3),
+            "autotuned": {"per_trial_items": bool(st["batch_per_trial"]), "blocks_per_sm": st["batch_blocks_per_sm"],
+                          "tuned": bool(st["batch_tuned"])},
+            "default_rule": {"per_trial_items": bool(st_default["batch_per_trial"]),
+                             "blocks_per_sm": st_default["batch_blocks_per_sm"], "ms_batched": ms_default}}
 
 
 def _correlated_leg(eng, synth, torch, dev, stream, spec, terms, n_trials, n_events, seed, ms_plain, args):
@@ -562,51 +626,61 @@ def _events_leg(eng, torch, dev, stream, pool, terms, n_trials, seed, ms_plain, 
 
 def _serving_leg(eng, synth, offsets, args):
     """The serving workload: requests with Poisson arrivals at several rates, served by
-    ara_submit / ara_serve_step / ara_poll.  Time is virtual: each serve step advances
-    the clock by its measured wall time (GPU work and host overhead), and a request's
-    latency is its finish minus its arrival, so the sweep runs as fast as the server."""
+    the continuous-batching loop (ara_submit / ara_serve_step / ara_poll) in real time.
+    The host loop submits each request when its arrival time has passed, calls
+    ara_serve_step (which launches rounds without waiting for them) and polls the
+    pending tickets after a step that finished some; a request's latency is the
+    wall time from its arrival to the poll that returns its PML/TVaR."""
     spec = synth.WORKLOADS["serving"]
     pool = synth.make_elt_pool(spec["n_elts"], spec["entries"], spec["catalogue"], spec["elt_seed"],
                                recipe=spec["recipe"])
     eng.load_pool(pool)
-    occ_r, occ_l, agg_r, agg_l = _terms()
+    with open(os.path.join(ROOT, "tests", "golden", "serving_terms.json")) as fh:
+        st = json.load(fh)
     reqs = synth.serving_requests(spec, args.serve_requests, spec["request_seed"])
+    terms = st["layer_terms"][: len(reqs)]
+    if len(terms) < len(reqs):
+        raise RuntimeError("serving_terms.json holds fewer requests than asked for")
     rps = np.array(RETURN_PERIODS)
     results = []
     for rate in args.serve_rates:
         rng = np.random.default_rng([spec["request_seed"], int(rate)])
         arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
-        clock, i, busy, n_batches = 0.0, 0, 0.0, 0
+        s0 = eng.serve_stats()
         pending, lat, evals = {}, [], 0
+        i, max_pending = 0, 0
+        t0 = time.perf_counter()
         while i < len(reqs) or pending:
-            if not pending:
-                clock = max(clock, arrivals[i])
-            while i < len(reqs) and arrivals[i] <= clock:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and arrivals[i] <= now:
                 ids, t_end = reqs[i]
-                f = len(ids) / 15.0  # percentile terms of the 15-ELT layer, aggregate terms scaled to |J|
-                tk = eng.submit(ids, (occ_r, occ_l, agg_r * f, agg_l * f), 0, t_end, rps)
+                tk = eng.submit(ids, terms[i], 0, t_end, rps)
                 pending[tk] = (arrivals[i], int(offsets[t_end]) * len(ids))
                 i += 1
-            t0 = time.perf_counter()
-            eng.serve_step()
-            dt = time.perf_counter() - t0
-            clock += dt
-            busy += dt
-            n_batches += 1
-            for tk in list(pending):
-                if eng.poll(tk, len(rps)) is not None:
-                    arr, ev = pending.pop(tk)
-                    lat.append(clock - arr)
-                    evals += ev
+            max_pending = max(max_pending, len(pending))
+            if eng.serve_step() > 0:
+                done_at = time.perf_counter() - t0
+                for tk in list(pending):
+                    if eng.poll(tk, len(rps)) is not None:
+                        arr, ev = pending.pop(tk)
+                        lat.append(done_at - arr)
+                        evals += ev
+            elif not pending and i < len(reqs):
+                time.sleep(max(0.0, min(arrivals[i] - (time.perf_counter() - t0), 0.002)))
+        wall = time.perf_counter() - t0
+        s1 = eng.serve_stats()
         lat_ms = 1e3 * np.asarray(lat)
-        results.append({"rate_per_s": rate, "p50_ms": float(np.percentile(lat_ms, 50)),
-                        "p99_ms": float(np.percentile(lat_ms, 99)), "batches": n_batches,
-                        "requests_per_batch": len(reqs) / n_batches, "evals_per_s": evals / busy})
+        passes = s1["passes_launched"] - s0["passes_launched"]
+        results.append({"rate_per_s": rate, "requests": len(lat), "p50_ms": float(np.percentile(lat_ms, 50)),
+                        "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(lat_ms.max()),
+                        "wall_s": wall, "evals_per_s": evals / wall,
+                        "rounds": s1["rounds_launched"] - s0["rounds_launched"], "passes": passes,
+                        "max_pending": max_pending})
     return {"workload": f"serving: the paper-1m YET, a pool of {spec['n_elts']} ELTs x {spec['entries']:,} records, "
-                        f"{len(reqs)} requests of |J| ~ U{{1..15}} over trial prefixes log-uniform in [1e4, 1e6], "
-                        "RP 100/250; terms: the paper-1m percentile terms, aggregate terms scaled by |J|/15",
-            "time": "virtual: Poisson arrivals, each serve step advances the clock by its wall time",
-            "rates": results}
+                        f"{len(reqs)} requests per rate of |J| ~ U{{1..15}} over trial prefixes log-uniform in "
+                        "[1e4, 1e6], RP 100/250, percentile terms per request (tests/golden/serving_terms.json)",
+            "time": "real: Poisson arrivals in wall time; latency = arrival to the poll that returns the result",
+            "chunk_trials": eng.serve_stats()["chunk_trials"], "rates": results}
 
 
 def main(argv=None):
@@ -628,7 +702,8 @@ def main(argv=None):
                     help="skip the correlated-sigma layer and the per-event output legs")
     ap.add_argument("--no-events", action="store_true", help="skip the per-event output leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency sweep")
-    ap.add_argument("--serve-requests", type=int, default=400, help="requests per rate of the serving sweep")
+    ap.add_argument("--no-stress", action="store_true", help="skip the precision-stress layer")
+    ap.add_argument("--serve-requests", type=int, default=10_000, help="requests per rate of the serving sweep")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 800.0, 3200.0],
                     help="request arrival rates (per second) of the serving sweep")
     args = ap.parse_args(argv)
