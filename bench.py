@@ -166,6 +166,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def _memory_nodes(ptr: int, nbytes: int, gpu: int):
+    """NUMA nodes of the pages of a host buffer (move_pages on sampled pages) and
+    the NUMA node of the GPU's PCI device, or None where the host does not say."""
+    import ctypes
+    import platform
+
+    out = {"buffer_nodes": None, "gpu_node": None}
+    nr = {"aarch64": 239, "x86_64": 279}.get(platform.machine())
+    try:
+        if nr is not None:
+            libc = ctypes.CDLL(None, use_errno=True)
+            page = os.sysconf("SC_PAGE_SIZE")
+            k = 16
+            addrs = (ctypes.c_void_p * k)(*[(ptr + i * (nbytes // k)) // page * page for i in range(k)])
+            status = (ctypes.c_int * k)()
+            if libc.syscall(nr, 0, k, addrs, None, status, 0) == 0:
+                # negative entries are error codes (a page not present), not nodes
+                out["buffer_nodes"] = sorted(set(int(v) for v in status if v >= 0))
+        bus = subprocess.run(["nvidia-smi", "-i", str(gpu), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=20).stdout.strip().lower()
+        if bus:
+            dev = bus[-12:] if len(bus) >= 12 else bus
+            with open(f"/sys/bus/pci/devices/{dev}/numa_node") as fh:
+                out["gpu_node"] = int(fh.read().strip())
+    except (OSError, ValueError, subprocess.SubprocessError):
+        pass
+    return out
+
+
 def _algorithmic_bytes(offsets_span: int, n_events: int, n_trials: int, n_records: int) -> int:
     """Bytes the method must move per layer: YET ids (4 B / occurrence), trial
     offsets (8 B / trial), each record of the layer once (16 B: mean, sigma,
@@ -368,7 +397,9 @@ def run_gpu(args):
         d2h = 8 * n_trials + 16 * len(rps)
         e2e = {"value": ws * evals_per_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
-               "yet_upload_ms": upload_ms, "elt_load_ms": elt_ms,
+               "yet_upload_ms": upload_ms, "yet_upload_gbs": 4 * n_events / (upload_ms * 1e-3) / 1e9,
+               "memory_nodes": _memory_nodes(ids_host.data_ptr(), 4 * n_events, local),
+               "elt_load_ms": elt_ms,
                "step": "ara_load_yet_async (pinned host YET) beside ara_load_elts (host ELTs, table build), "
                        "ara_run_layer (host YLT), ara_pml_tvar"}
 
