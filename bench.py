@@ -573,7 +573,19 @@ def _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args)
         torch.cuda.synchronize(dev)
         return a.elapsed_time(b) / steps
 
+    from paper_1501_06326_gb300 import ara
+
     steps = max(2, min(args.steps, 5))
+    # each work item pinned (all CTAs an SM holds), then the default rule, then the autotuner
+    items = {"tile": ara.ARA_BATCH_ITEM_TILE, "trial": ara.ARA_BATCH_ITEM_TRIAL, "dense": ara.ARA_BATCH_ITEM_DENSE}
+    names = {v: k for k, v in items.items()}
+    ms_items = {}
+    try:
+        for name, item in items.items():
+            eng.set_batch_config(item, 0)
+            ms_items[name] = timed(batch_step, steps)
+    finally:
+        eng.set_batch_config(ara.ARA_BATCH_AUTO)
     ms_default = timed(batch_step, steps)
     st_default = eng.stats()
     eng.run_layers(layers, seed, 0, n_trials, out, autotune=True)
@@ -586,9 +598,10 @@ def _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args)
             "layers": len(layers), "steps": steps, "ms_batched": ms_batch, "ms_plain": ms_plain,
             "layers_per_s": len(layers) / (ms_batch * 1e-3), "plain_layers_per_s": len(layers) / (ms_plain * 1e-3),
             "speedup": ms_plain / ms_batch, "evals_per_s": evals / (ms_batch * 1e-3),
-            "autotuned": {"per_trial_items": bool(st["batch_per_trial"]), "blocks_per_sm": st["batch_blocks_per_sm"],
+            "ms_batched_by_item": ms_items,
+            "autotuned": {"item": names[st["batch_item"]], "blocks_per_sm": st["batch_blocks_per_sm"],
                           "tuned": bool(st["batch_tuned"])},
-            "default_rule": {"per_trial_items": bool(st_default["batch_per_trial"]),
+            "default_rule": {"item": names[st_default["batch_item"]],
                              "blocks_per_sm": st_default["batch_blocks_per_sm"], "ms_batched": ms_default}}
 
 

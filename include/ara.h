@@ -72,8 +72,8 @@ extern "C" {
  * stands for the pool id in the hit hash of ara_run_layer_diag.  Without it,
  * each (trial, event index, ELT pool id) has its own draw. */
 #define ARA_SHARED_Z 4u
-/* ara_run_layers: pick the losses kernel's configuration (work item of one
- * trial or of a tile of trials; CTAs per SM) by measurement.  The first pass
+/* ara_run_layers: pick the losses kernel's configuration (its work item, see
+ * ara_set_batch_config; CTAs per SM) by measurement.  The first pass
  * of a batch shape (layers, ELTs of the union, trials, hit records per trial)
  * runs every candidate once, timed with CUDA events, and keeps the fastest
  * for later passes of that shape; all candidates give the same bits.  Without
@@ -145,7 +145,7 @@ typedef struct {
     int32_t smem_bytes;      /* dynamic shared memory per CTA */
     int32_t filter_bits;     /* shared-memory membership filter size in bits */
     /* ara_run_layers: the losses kernel's configuration (the last pass) */
-    int32_t batch_per_trial;     /* 1: one warp per trial, 0: one warp per tile of trials */
+    int32_t batch_item;          /* the work item: an ARA_BATCH_ITEM_* value */
     int32_t batch_blocks_per_sm; /* resident CTAs per SM of the persistent grid */
     int32_t batch_tuned;         /* 1: chosen by the autotuner (measured), 0: by the default rule */
     int32_t reserved;
@@ -297,6 +297,26 @@ ARA_API int ara_run_layer_events(ara_ctx *ctx, const ara_layer *layer, uint64_t 
 #define ARA_MAX_BATCH_ELTS 64
 ARA_API int ara_run_layers(ara_ctx *ctx, int32_t n_layers, const ara_layer *layers, uint64_t seed,
                    int64_t trial_begin, int64_t trial_end, double *ylt_out);
+
+/* The losses kernel of ara_run_layers (and of the serving loop's passes) has
+ * three work items, which add the same fixed-point numbers and so give the
+ * same bits:
+ *   ARA_BATCH_ITEM_TILE   one warp per tile of 8 trials, a lane per hit record;
+ *   ARA_BATCH_ITEM_TRIAL  one warp per trial, a lane per hit record;
+ *   ARA_BATCH_ITEM_DENSE  one warp per tile of 8 trials, a lane per (event, ELT)
+ *                         pair: each pair's loss once, then each record's
+ *                         per-layer occurrence losses.
+ * ara_set_batch_config pins the work item and the CTAs per SM of the
+ * persistent grid (blocks_per_sm 0: as many as an SM holds; a larger number is
+ * cut to that) for later passes; item ARA_BATCH_AUTO returns to the cached
+ * autotuner choice for the pass's shape, else the default rule (the dense item
+ * with as many CTAs as an SM holds).
+ * Errors: ARA_EINVAL (unknown item, blocks_per_sm outside 0..16). */
+#define ARA_BATCH_AUTO (-1)
+#define ARA_BATCH_ITEM_TILE 0
+#define ARA_BATCH_ITEM_TRIAL 1
+#define ARA_BATCH_ITEM_DENSE 2
+ARA_API int ara_set_batch_config(ara_ctx *ctx, int32_t item, int32_t blocks_per_sm);
 
 /* Serving: layer requests against the resident YET and ELT pool, with
  * continuous batching.  The paper has no serving system; a portfolio's

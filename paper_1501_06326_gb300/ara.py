@@ -32,6 +32,7 @@ ARA_MAX_LAYER_ELTS = 32
 ARA_MAX_BATCH_LAYERS = 32
 ARA_MAX_BATCH_ELTS = 64
 ARA_SERVE_MAX_RP = 16
+ARA_BATCH_AUTO, ARA_BATCH_ITEM_TILE, ARA_BATCH_ITEM_TRIAL, ARA_BATCH_ITEM_DENSE = -1, 0, 1, 2
 _ERR_NAMES = {
     ARA_EINVAL: "ARA_EINVAL", ARA_ENOMEM: "ARA_ENOMEM", ARA_ENOTLOADED: "ARA_ENOTLOADED",
     ARA_ECUDA: "ARA_ECUDA", ARA_ETIMEOUT: "ARA_ETIMEOUT", ARA_EAGAIN: "ARA_EAGAIN",
@@ -44,7 +45,7 @@ EXPORTED = (
     "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
     "ara_pml_tvar_noalloc", "ara_run_layers", "ara_submit", "ara_serve_step", "ara_poll", "ara_load_xelts",
     "ara_run_layer_events", "ara_wait", "ara_load_yet_async", "ara_finish_yet", "ara_serve_stats",
-    "ara_top_m", "ara_merge_top",
+    "ara_top_m", "ara_merge_top", "ara_set_batch_config",
 )
 ARA_NOALLOC_MAX_RP = 64
 
@@ -101,7 +102,7 @@ class Stats(ctypes.Structure):
         ("block", ctypes.c_int32),
         ("smem_bytes", ctypes.c_int32),
         ("filter_bits", ctypes.c_int32),
-        ("batch_per_trial", ctypes.c_int32),
+        ("batch_item", ctypes.c_int32),
         ("batch_blocks_per_sm", ctypes.c_int32),
         ("batch_tuned", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
@@ -165,6 +166,7 @@ def load_library(path: str = LIB_PATH):
     lib.ara_run_layer.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P]
     lib.ara_run_layer_diag.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P, ctypes.POINTER(Diag)]
     lib.ara_run_layers.argtypes = [P, i32, ctypes.POINTER(Layer), u64, i64, i64, P]
+    lib.ara_set_batch_config.argtypes = [P, i32, i32]
     lib.ara_run_layer_events.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P, ctypes.POINTER(EventRows)]
     lib.ara_submit.argtypes = [P, ctypes.POINTER(Layer), u64, i64, P, i32, P]
     lib.ara_serve_step.argtypes = [P, P]
@@ -289,6 +291,10 @@ def ara_submit(h, layer: Layer, seed, trial_end, return_periods, n_rp, ticket_ou
 
 def ara_serve_step(h, n_done_out):
     return load_library().ara_serve_step(h, _ptr(n_done_out, np.int32))
+
+
+def ara_set_batch_config(h, item, blocks_per_sm):
+    return load_library().ara_set_batch_config(h, item, blocks_per_sm)
 
 
 def ara_serve_stats(h, out):
@@ -496,6 +502,12 @@ class Ara:
         made = [self.make_layer(ids, terms, primary_only, newton_only, shared_z, autotune) for ids, terms in layers]
         arr = (Layer * len(made))(*made)
         self._check(ara_run_layers(self._h, len(made), arr, seed, trial_begin, trial_end, ylt_out))
+
+    def set_batch_config(self, item: int = ARA_BATCH_AUTO, blocks_per_sm: int = 0) -> None:
+        """Pin the batched losses kernel's work item (ARA_BATCH_ITEM_*) and CTAs per
+        SM (0: as many as an SM holds); ARA_BATCH_AUTO returns to the autotuner's
+        cached choice or the default rule."""
+        self._check(ara_set_batch_config(self._h, int(item), int(blocks_per_sm)))
 
     def submit(self, elt_ids, layer_terms, seed: int, trial_end: int, return_periods,
                primary_only: bool = False, shared_z: bool = False) -> int:

@@ -118,8 +118,9 @@ struct ara_ctx {
   int max_smem = 0;
   bool no_timing = false;   // serving passes record no timing events
   // the batched losses kernel's configuration per batch shape, chosen by measurement (ARA_AUTOTUNE)
-  std::map<std::vector<int64_t>, std::pair<int, int>> tune_cache;  // shape -> (per_trial, blocks per SM)
-  int32_t last_per_trial = 0, last_blocks = 0, last_tuned = 0;
+  std::map<std::vector<int64_t>, std::pair<int, int>> tune_cache;  // shape -> (work item, blocks per SM)
+  int32_t last_item = 0, last_blocks = 0, last_tuned = 0;
+  int32_t force_item = ARA_BATCH_AUTO, force_blocks = 0;  // ara_set_batch_config
   cudaEvent_t tune_ev[2] = {nullptr, nullptr};
   // serving (continuous batching)
   std::deque<int64_t> serve_queue;      // submitted, not yet admitted, in arrival order
@@ -937,12 +938,14 @@ static int run_layer_impl(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t
 // is counted as O * 2^e in 64 bits.  O is at most O_max (the layer's occurrence
 // limit, or its largest possible event loss above the retention), a trial has
 // at most n_max events, so e = 61 - ceil(log2(n_max + 1)) - ceil(log2(O_max))
-// keeps every sum below 2^61.
+// keeps every sum below 2^61.  e is kept within FP32's normal exponents (2^e
+// is then an FP32 number); only an O_max below 2^-80 or above 2^150 meets the
+// bounds.
 static int batch_scale_exp(double o_max, int64_t n_max) {
   if (!(o_max > 0.0) || !std::isfinite(o_max)) return 0;
   const int e = 61 - static_cast<int>(std::ceil(std::log2(static_cast<double>(n_max) + 1.0))) -
                 static_cast<int>(std::ceil(std::log2(o_max)));
-  return std::max(-1000, std::min(1000, e));
+  return std::max(-126, std::min(127, e));
 }
 
 // layer_t_end (NULL: t1 for every layer): layer l's trials end at
@@ -1000,8 +1003,9 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
     p.occ_l[l] = static_cast<float>(L.occ_limit);
     p.agg_r[l] = L.agg_retention;
     p.agg_l[l] = L.agg_limit;
-    p.scale_exp[l] = batch_scale_exp(o_max, c->max_trial_events);
-    p.inv_scale[l] = std::ldexp(1.0, -p.scale_exp[l]);
+    const int e = batch_scale_exp(o_max, c->max_trial_events);
+    p.scale[l] = std::ldexp(1.0f, e);
+    p.inv_scale[l] = std::ldexp(1.0, -e);
     p.layer_t_end[l] = layer_t_end ? std::min(layer_t_end[l], t1) : t1;
   }
   // ---- outputs
@@ -1040,22 +1044,28 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
     recs_per_trial += reach * static_cast<double>(c->pool.find(uni[i])->second.n);
   }
   recs_per_trial *= static_cast<double>(c->n_events) / (static_cast<double>(c->n_trials) * c->catalogue);
-  // The losses kernel's configuration: the work item (one warp per trial, or per
-  // tile of trials) and the CTAs per SM.  Default rule: one warp per trial once a
-  // trial's records fill a warp's rounds, and all the CTAs an SM holds.  Every
-  // configuration adds the same fixed-point numbers, so none changes a result.
+  // The losses kernel's configuration: the work item and the CTAs per SM.  Default
+  // rule: the dense item with all the CTAs an SM holds.  Every configuration adds
+  // the same fixed-point numbers, so none changes a result.
   const std::vector<int64_t> shape = {n_layers, static_cast<int64_t>(uni.size()), t1 - t0,
                                       static_cast<int64_t>(std::lround(4.0 * std::log2(recs_per_trial + 1.0)))};
-  int per_trial = recs_per_trial >= 192.0 ? 1 : 0, blocks = ara::kBatchBlocksPerSm;
+  const int dense_max = ara::losses_dense_blocks_per_sm(n_layers);
+  if (dense_max < 1) return fail(c, ARA_ECUDA, "%s: the dense losses kernel fits no SM", who);
+  auto max_blocks = [&](int it) { return it == ara::kItemDense ? dense_max : ara::kBatchBlocksPerSm; };
+  int item = ara::kItemDense, blocks = dense_max;
   const auto cached = c->tune_cache.find(shape);
-  const bool tune = cached == c->tune_cache.end() && (layers[0].flags & ARA_AUTOTUNE);
-  if (cached != c->tune_cache.end()) {
-    per_trial = cached->second.first;
+  const bool forced = c->force_item != ARA_BATCH_AUTO;
+  const bool tune = !forced && cached == c->tune_cache.end() && (layers[0].flags & ARA_AUTOTUNE);
+  if (forced) {
+    item = c->force_item;
+    blocks = c->force_blocks > 0 ? std::min(c->force_blocks, max_blocks(item)) : max_blocks(item);
+  } else if (cached != c->tune_cache.end()) {
+    item = cached->second.first;
     blocks = cached->second.second;
   }
   const int64_t warps = ara::kBatchThreads / 32;
-  auto grid_of = [&](int pt, int b) {
-    const int64_t items = pt ? pl.n_tiles * ara::kWarpTrials : pl.n_tiles;
+  auto grid_of = [&](int it, int b) {
+    const int64_t items = it == ara::kItemTrial ? pl.n_tiles * ara::kWarpTrials : pl.n_tiles;
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(c->num_sms) * b,
                                                                    (items + warps - 1) / warps)));
   };
@@ -1066,11 +1076,11 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
     float best = 0.0f;
     for (auto& e : c->tune_ev)
       if (!e) ARA_CUDA(c, cudaEventCreate(&e));
-    for (int pt = 0; pt < 2; ++pt)
-      for (int b = 2; b <= ara::kBatchBlocksPerSm; ++b) {
+    for (int it : {ara::kItemTile, ara::kItemTrial, ara::kItemDense})
+      for (int b = 2; b <= max_blocks(it); ++b) {
         ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 4 * sizeof(unsigned long long), c->stream));
         ARA_CUDA(c, cudaEventRecord(c->tune_ev[0], c->stream));
-        ARA_CUDA(c, ara::launch_losses_batch(p, pt != 0, grid_of(pt, b), c->stream));
+        ARA_CUDA(c, ara::launch_losses_batch(p, it, grid_of(it, b), c->stream));
         ARA_CUDA(c, cudaEventRecord(c->tune_ev[1], c->stream));
         ARA_CUDA(c, cudaEventSynchronize(c->tune_ev[1]));
         float ms = 0.0f;
@@ -1078,23 +1088,23 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
         launched += 1;
         if (best == 0.0f || ms < best) {
           best = ms;
-          per_trial = pt;
+          item = it;
           blocks = b;
         }
       }
-    c->tune_cache[shape] = {per_trial, blocks};
+    c->tune_cache[shape] = {item, blocks};
     ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 4 * sizeof(unsigned long long), c->stream));
   }
   cudaEvent_t la, lb;
   if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
   ARA_CUDA(c, record_ev(la, c->stream));
-  ARA_CUDA(c, ara::launch_losses_batch(p, per_trial != 0, grid_of(per_trial, blocks), c->stream));
+  ARA_CUDA(c, ara::launch_losses_batch(p, item, grid_of(item, blocks), c->stream));
   ARA_CUDA(c, record_ev(lb, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
   launched += 1;
-  c->last_per_trial = per_trial;
+  c->last_item = item;
   c->last_blocks = blocks;
-  c->last_tuned = cached != c->tune_cache.end() || tune ? 1 : 0;
+  c->last_tuned = !forced && (cached != c->tune_cache.end() || tune) ? 1 : 0;
   c->launches += launched;
   if (!ylt_dev) {
     ARA_CUDA(c, cudaMemcpyAsync(ylt_out, d_ylt, sizeof(double) * n_out * n_layers, cudaMemcpyDeviceToHost,
@@ -1104,7 +1114,7 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
   int64_t elts = 0;
   for (int32_t l = 0; l < n_layers; ++l) elts += static_cast<int64_t>(lids[l].size());
   record_pass_stats(c, pl, t0, t1, elts);
-  c->stats.batch_per_trial = c->last_per_trial;
+  c->stats.batch_item = c->last_item;
   c->stats.batch_blocks_per_sm = c->last_blocks;
   c->stats.batch_tuned = c->last_tuned;
   return ARA_OK;
@@ -1117,6 +1127,23 @@ int ara_run_layer(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int
 int ara_run_layers(ara_ctx* c, int32_t n_layers, const ara_layer* layers, uint64_t seed, int64_t t0, int64_t t1,
                    double* ylt_out) {
   return run_layers_impl(c, n_layers, layers, seed, t0, t1, ylt_out);
+}
+
+static_assert(ARA_BATCH_ITEM_TILE == ara::kItemTile && ARA_BATCH_ITEM_TRIAL == ara::kItemTrial &&
+                  ARA_BATCH_ITEM_DENSE == ara::kItemDense,
+              "work items of the ABI and the kernels");
+
+int ara_set_batch_config(ara_ctx* c, int32_t item, int32_t blocks_per_sm) {
+  int rc = bind(c);
+  if (rc) return rc;
+  if (item != ARA_BATCH_AUTO && item != ARA_BATCH_ITEM_TILE && item != ARA_BATCH_ITEM_TRIAL &&
+      item != ARA_BATCH_ITEM_DENSE)
+    return fail(c, ARA_EINVAL, "ara_set_batch_config: unknown work item %d", item);
+  if (blocks_per_sm < 0 || blocks_per_sm > 16)
+    return fail(c, ARA_EINVAL, "ara_set_batch_config: blocks_per_sm %d outside 0..16", blocks_per_sm);
+  c->force_item = item;
+  c->force_blocks = blocks_per_sm;
+  return ARA_OK;
 }
 
 int ara_run_layer_diag(ara_ctx* c, const ara_layer* L, uint64_t seed, int64_t t0, int64_t t1, double* ylt_out,

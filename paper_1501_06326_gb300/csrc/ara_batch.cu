@@ -7,9 +7,12 @@
 // layer, the event's losses over the layer's ELTs are summed (Algorithm 1),
 // the occurrence terms applied, and the occurrence loss is added to the
 // layer's sum for the trial: a 64-bit fixed-point integer (each loss rounded
-// to the layer's unit, 2^-61 of its largest possible trial sum), so that the
-// sum is exact in those units and independent of the order of the (atomic)
-// additions.  The aggregate terms of each layer then give its year losses.
+// to the layer's unit, about 2^-61 of its largest possible trial sum), so that
+// the sum is exact in those units and independent of the order of the
+// (atomic) additions.  The aggregate terms of each layer then give its year
+// losses.  Three kernels do this with different work items (a lane per record
+// over a tile or over one trial, or a lane per pair over a tile); they add the
+// same fixed-point numbers and give the same results.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -38,23 +41,17 @@ struct BatchShared {
   float ret[kMaxIndexElts], lim[kMaxIndexElts], share[kMaxIndexElts];
   unsigned long long layers_of[kMaxIndexElts];
   float occ_r[kBatchLayers], occ_l[kBatchLayers];
-  int32_t sexp[kBatchLayers];
+  float scale[kBatchLayers];
   int64_t t_end[kBatchLayers];
 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 
-// O * 2^e as an unsigned 64-bit integer, rounded to nearest (O >= 0 finite,
-// O * 2^e < 2^62): the FP32 significand shifted into place.
-__device__ __forceinline__ unsigned long long fixed_of(float O, int e) {
-  const uint32_t u = __float_as_uint(O);
-  const int x = static_cast<int>((u >> 23) & 255u);
-  if (x == 0) return 0ull;  // zero (subnormal losses are below any scale in use)
-  const unsigned long long m = static_cast<unsigned long long>((u & 0x7FFFFFu) | 0x800000u);
-  const int s = x - 150 + e;  // O = m 2^(x - 150)
-  if (s >= 0) return m << s;
-  if (s <= -64) return 0ull;
-  return (m + (1ull << (-s - 1))) >> (-s);
+// O in a layer's fixed-point units: O * scale rounded to the nearest integer
+// (ties to even).  O >= 0 is finite and scale a power of two, so the product is
+// exact (or below one unit) and O * scale < 2^62 by the choice of scale.
+__device__ __forceinline__ unsigned long long fixed_units(float O, float scale) {
+  return __float2ull_rn(O * scale);
 }
 
 // The table argument t = Phi^-1(z) of pair `pi` (a record of kind Beta or
@@ -121,7 +118,7 @@ __device__ __forceinline__ void add_occurrence(BatchWarp& ws, const BatchShared&
                                                float G, uint32_t* dirty) {
   const float O = clamp_terms_f(G, bs.occ_r[layer], bs.occ_l[layer]);
   if (O > 0.0f) {
-    ws.acc[layer][lane] += fixed_of(O, bs.sexp[layer]);
+    ws.acc[layer][lane] += fixed_units(O, bs.scale[layer]);
     *dirty |= 1u << layer;
   }
 }
@@ -131,7 +128,7 @@ __device__ __forceinline__ void add_occurrence(BatchWarp& ws, const BatchShared&
 __device__ __forceinline__ void add_occurrence_trial(BatchWarp& ws, const BatchShared& bs, int layer, uint32_t tl,
                                                      float G) {
   const float O = clamp_terms_f(G, bs.occ_r[layer], bs.occ_l[layer]);
-  if (O > 0.0f) atomicAdd(&ws.tacc[layer][tl], fixed_of(O, bs.sexp[layer]));
+  if (O > 0.0f) atomicAdd(&ws.tacc[layer][tl], fixed_units(O, bs.scale[layer]));
 }
 
 // Moves the lane's sums of the layers in `dirty` into the tile's sums of
@@ -309,7 +306,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
   for (int i = threadIdx.x; i < kBatchLayers; i += blockDim.x) {
     bs.occ_r[i] = p.occ_r[i];
     bs.occ_l[i] = p.occ_l[i];
-    bs.sexp[i] = p.scale_exp[i];
+    bs.scale[i] = p.scale[i];
     bs.t_end[i] = i < p.n_layers ? p.layer_t_end[i] : 0;
   }
   __syncthreads();
@@ -516,11 +513,396 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSm) k_losses_bat
   }
 }
 
-cudaError_t launch_losses_batch(const BatchParams& p, bool per_trial, int grid, cudaStream_t s) {
-  if (per_trial)
-    k_losses_batch<true><<<grid, kBatchThreads, 0, s>>>(p);
-  else
-    k_losses_batch<false><<<grid, kBatchThreads, 0, s>>>(p);
+namespace {
+
+// ------------------------------------------------------------------ dense kernel
+// One warp per tile, one lane per (event occurrence, ELT) pair.  The tile's
+// records stream through a per-warp record ring; each record's pairs take
+// consecutive slots of a pair ring.  A compute round takes the next 64 pending
+// pairs (two per lane, whatever their records), computes each pair's loss
+// after ELT terms once, and stores it with the layers it serves.  Records
+// whose pairs are all computed are combined up to 64 at a time, with the lanes
+// turned into layers: lane (s, l) holds layer l's fixed-point sum for the
+// current trial in registers and takes the group's records i = s mod S (S
+// record slots: 32 over the layers rounded up to a power of two) that serve
+// layer l, found by bit-matrix transposes of the records' layer masks.  For
+// each (single-ELT records first, then the others), it sums the record's pair
+// losses over the layer's ELTs from left to right (the pairs' order), applies
+// the occurrence terms and adds the result.
+// When a trial's records are all combined, the slots' sums give its year
+// losses.  The fill keeps a round's 64 pairs pending; a record has at most 64
+// pairs, so after a combine at most 63 computed pairs and 63 pending ones are
+// live, and the next record always fits the rings.
+constexpr int kDenseRecs = 128;   // record ring (slots: sequence number mod kDenseRecs)
+constexpr int kDensePairs = 256;  // pair ring (slots: pair sequence number mod kDensePairs)
+constexpr int kDenseBlocksPerSm = 6;
+static_assert(kDensePairs >= 63 + 64 + 64 && kDenseRecs >= 64 + 32, "ring sizes");
+static_assert(kDenseRecs <= 256, "record slots are stored in bytes");
+
+struct DenseWarp {
+  uint2 rec[kDenseRecs];        // the ring's records
+  uint32_t pre[kDenseRecs];     // each record's first pair (sequence number in the tile)
+  float loss[kDensePairs];      // each pair's loss after ELT terms
+  uint32_t lmask[kDensePairs];  // each pair's layers: those holding its ELT that reach its trial
+  uint8_t owner[kDensePairs];   // each pair's record slot
+  uint32_t act[kWarpTrials];    // per trial of the tile: the layers whose trials reach it
+  float g_l0[64];               // a combine group's records: first pair's loss,
+  uint32_t g_pre[64];           //   first pair (sequence number),
+  uint32_t g_cnt[64];           //   pair count
+};
+
+struct DenseShared {
+  const float4* tab[kMaxIndexElts];
+  const float4* tabf[kMaxIndexElts];
+  uint32_t elt_id[kMaxIndexElts];
+  float ret[kMaxIndexElts], lim[kMaxIndexElts], share[kMaxIndexElts];
+  uint32_t layers_of[kMaxIndexElts];
+  float4 occ[kBatchLayers];  // (occurrence retention, occurrence limit, fixed-point scale, 0)
+  double agg_r[kBatchLayers], agg_l[kBatchLayers], inv_scale[kBatchLayers];
+  double* ylt[kBatchLayers];
+  int64_t t_end[kBatchLayers];
+};
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, uint32_t lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= static_cast<uint32_t>(d)) v += o;
+  }
+  return v;
+}
+
+__device__ __forceinline__ uint2 shfl_u2(uint2 v, uint32_t src) {
+  return make_uint2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// Loss after ELT terms by the Halley iteration, with its non-convergence as
+// the second value (0 or 1).
+__device__ __noinline__ float2 dense_pair_slow(const BatchParams& p, uint32_t pi, int64_t trial, uint32_t k) {
+  unsigned long long nc = 0ull;
+  const float L = pair_loss_slow(p, p.pairs[pi], pi, trial, k, &nc);
+  return make_float2(L, static_cast<float>(nc));
+}
+
+// Lane l receives column l of the 32 x 32 bit matrix whose row i is lane i's
+// x: bit i of the result is bit l of lane i's x (the off-diagonal blocks of
+// halves, quarters, ... exchanged between lanes).
+__device__ __forceinline__ uint32_t bit_transpose32(uint32_t x, uint32_t lane) {
+  const uint32_t hi[5] = {0xFFFF0000u, 0xFF00FF00u, 0xF0F0F0F0u, 0xCCCCCCCCu, 0xAAAAAAAAu};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const uint32_t j = 16u >> k;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+    x = (lane & j) ? ((x & hi[k]) | ((y & hi[k]) >> j)) : ((x & ~hi[k]) | ((y & ~hi[k]) << j));
+  }
+  return x;
+}
+
+// Year losses of one trial: the slots' sums of each layer added (lanes l of
+// slot 0 receive them) through the aggregate terms; the sums are cleared.
+__device__ __forceinline__ void dense_finish_trial(const DenseShared& ds, unsigned long long& acc, uint32_t lane,
+                                                   int nlp, int nl, int64_t trial, int64_t t_begin) {
+  for (int d = nlp; d < 32; d <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+  if (lane < static_cast<uint32_t>(nl) && trial < ds.t_end[lane])
+    ds.ylt[lane][trial - t_begin] =
+        clamp_terms_d(__ull2double_rn(acc) * ds.inv_scale[lane], ds.agg_r[lane], ds.agg_l[lane]);
+  acc = 0ull;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kBatchThreads, kDenseBlocksPerSm)
+    k_losses_dense(const __grid_constant__ BatchParams p) {
+  __shared__ DenseWarp dwarp[kBatchThreads / 32];
+  __shared__ DenseShared ds;
+  const uint32_t lane = lane_id();
+  DenseWarp& ws = dwarp[threadIdx.x >> 5];
+  const int nl = p.n_layers;
+  for (int i = threadIdx.x; i < kMaxIndexElts; i += blockDim.x) {
+    const bool in = i < p.n_elts;
+    ds.tab[i] = in ? p.tab[i] : nullptr;
+    ds.tabf[i] = in ? p.tabf[i] : nullptr;
+    ds.elt_id[i] = in ? static_cast<uint32_t>(p.elt_id[i]) : 0u;
+    ds.ret[i] = in ? p.t_ret[i] : 0.0f;
+    ds.lim[i] = in ? p.t_lim[i] : 0.0f;
+    ds.share[i] = in ? p.t_share[i] : 0.0f;
+    ds.layers_of[i] = in ? static_cast<uint32_t>(p.layers_of[i]) : 0u;
+  }
+  for (int i = threadIdx.x; i < kBatchLayers; i += blockDim.x) {
+    const bool in = i < nl;
+    ds.occ[i] = make_float4(p.occ_r[i], p.occ_l[i], p.scale[i], 0.0f);
+    ds.agg_r[i] = p.agg_r[i];
+    ds.agg_l[i] = p.agg_l[i];
+    ds.inv_scale[i] = p.inv_scale[i];
+    ds.ylt[i] = in ? p.ylt_l[i] : nullptr;
+    ds.t_end[i] = in ? p.layer_t_end[i] : 0;
+  }
+  __syncthreads();
+  static_assert(kBatchLayers <= 32, "one lane per layer; 32-bit layer masks");
+  // the lane's layer l and record slot s; its records in a group: i = s mod S
+  int nlp = 1;
+  while (nlp < nl) nlp <<= 1;
+  const uint32_t my_l = lane & static_cast<uint32_t>(nlp - 1);
+  const uint32_t n_slots = 32u / static_cast<uint32_t>(nlp);
+  uint32_t my_pattern = 0u;
+  for (uint32_t i = lane / static_cast<uint32_t>(nlp); i < 32u; i += n_slots) my_pattern |= 1u << i;
+  if (my_l >= static_cast<uint32_t>(nl)) my_pattern = 0u;
+  unsigned long long acc = 0ull;       // the layer's sum over the slot's records of the current trial
+  const uint2 zero2 = make_uint2(0u, 0u);
+  unsigned long long nc = 0ull;
+  uint32_t n_pairs = 0;
+
+  unsigned long long next = 0ull;  // tiles are claimed one ahead
+  if (lane == 0) next = atomicAdd(&p.counters[0], 1ull);
+  for (;;) {
+    const int64_t tile = static_cast<int64_t>(__shfl_sync(0xffffffffu, next, 0));
+    if (tile >= p.n_tiles) break;
+    if (lane == 0) next = atomicAdd(&p.counters[0], 1ull);
+    const int64_t ta = p.t_begin + tile * kWarpTrials;
+    const int ntr = static_cast<int>((ta + kWarpTrials < p.t_end) ? kWarpTrials : p.t_end - ta);
+    uint32_t any = 0u;
+#pragma unroll
+    for (int t = 0; t < kWarpTrials; ++t) {
+      const uint32_t a =
+          __ballot_sync(0xffffffffu, t < ntr && lane < static_cast<uint32_t>(nl) && ta + t < ds.t_end[lane]);
+      if (lane == 0) ws.act[t] = a;
+      any |= a;
+    }
+    __syncwarp();
+    const uint2* recs = p.ev_buf + (__ldg(&p.off[ta]) - p.e0);
+    const int32_t n = any ? static_cast<int32_t>(__ldg(&p.tile_cnt[tile])) : 0;
+    // lane i holds records rec_next + i (rc) and rec_next + 32 + i (rx)
+    int32_t rec_next = 0;
+    uint2 rc = (static_cast<int32_t>(lane) < n) ? __ldcs(recs + lane) : zero2;
+    uint2 rx = (32 + static_cast<int32_t>(lane) < n) ? __ldcs(recs + 32 + lane) : zero2;
+    uint32_t p_fill = 0u, p_done = 0u;  // pairs appended, pairs computed
+    uint32_t r_fill = 0u, r_done = 0u;  // records appended, records combined
+    int cur = 0;  // the trial whose records are being combined
+    for (;;) {
+      // ---- fill: whole records, 32 at a time, until a round's 64 pairs are pending
+      while (p_fill - p_done < 64u && rec_next < n) {
+        const bool valid = rec_next + static_cast<int32_t>(lane) < n;
+        const uint32_t cnt = valid ? ((rc.x >> kRecCntShift) & kRecCntMask) + 1u : 0u;
+        const uint32_t incl = warp_incl_scan(cnt, lane);
+        const uint32_t live = (r_done < r_fill) ? ws.pre[r_done % kDenseRecs] : p_fill;  // oldest live pair
+        const bool fits = valid && r_fill - r_done + lane < static_cast<uint32_t>(kDenseRecs) &&
+                          p_fill + incl - live <= static_cast<uint32_t>(kDensePairs);
+        const uint32_t n_take = __popc(__ballot_sync(0xffffffffu, fits));  // a prefix of the lanes
+        if (n_take == 0u) {  // cannot happen (see above); drop the tile's remaining records rather than spin
+          if (lane == 0) atomicOr(&p.counters[3], 1ull);
+          rec_next = n;
+          break;
+        }
+        if (fits) {
+          const uint32_t slot = (r_fill + lane) % kDenseRecs;
+          const uint32_t pre = p_fill + incl - cnt;
+          ws.rec[slot] = rc;
+          ws.pre[slot] = pre;
+          for (uint32_t j = 0; j < cnt; ++j) ws.owner[(pre + j) % kDensePairs] = static_cast<uint8_t>(slot);
+        }
+        p_fill += __shfl_sync(0xffffffffu, incl, n_take - 1u);
+        r_fill += n_take;
+        rec_next += static_cast<int32_t>(n_take);
+        // slide the window of records by n_take
+        const uint32_t src = lane + n_take;
+        const uint2 a = shfl_u2(rc, src & 31u), b = shfl_u2(rx, src & 31u);
+        rc = src < 32u ? a : b;
+        const int32_t at = rec_next + 32 + static_cast<int32_t>(lane);
+        rx = src < 32u ? b : (at < n ? __ldcs(recs + at) : zero2);
+        __syncwarp();
+      }
+      // ---- compute: up to 64 pending pairs, two per lane
+      if (p_done < p_fill) {
+        const uint32_t np = min(64u, p_fill - p_done);
+        uint32_t q[2], pi[2], kk[2], tl[2], mk[2];
+        PairHot h[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const uint32_t i = 32u * j + lane;
+          q[j] = (p_done + i) % kDensePairs;
+          pi[j] = 0u;
+          kk[j] = 0u;
+          tl[j] = 0u;
+          h[j] = PairHot{0.0f, 0.0f, kKindZero << kMetaKindShift, 0u};
+          if (i < np) {
+            const uint32_t o = ws.owner[q[j]];
+            const uint2 r = ws.rec[o];
+            pi[j] = r.y + (p_done + i - ws.pre[o]);
+            tl[j] = r.x >> kRecTrialShift;
+            kk[j] = r.x & kRecKMask;
+            h[j] = p.hot[pi[j]];
+          }
+        }
+        int mode[2];  // 0: no layer, 1: loss known (no loss / mean), 2: table, 3: Halley
+        float val[2], sfrac[2];
+        const float4* node[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const uint32_t pos = pair_pos(h[j].meta);
+          mk[j] = (32u * j + lane < np) ? ds.layers_of[pos] & ws.act[tl[j]] : 0u;
+          mode[j] = 0;
+          val[j] = 0.0f;
+          sfrac[j] = 0.0f;
+          node[j] = nullptr;
+          if (mk[j]) {
+            const uint32_t kind = pair_kind(h[j].meta);
+            mode[j] = 1;
+            val[j] = h[j].mu;
+            if (kind == kKindZero) {
+              val[j] = 0.0f;
+            } else if (!p.primary_only && kind_is_beta(kind)) {
+              float t = 0.0f;
+              if (p.newton_only || !pair_tab_exact(h[j].meta) ||
+                  !batch_pair_normal(p, kind, ds.elt_id[pos], pi[j], ta + tl[j], kk[j], &t)) {
+                mode[j] = 3;
+              } else {
+                mode[j] = 2;
+                const bool fine = pair_fine(h[j].meta);
+                const int nseg = fine ? kTabFineNodes - 1 : kTabNodes - 1;
+                float u = (t + kTabT1f) * (fine ? kTabInvH * kTabRefine : kTabInvH);
+                u = fminf(fmaxf(u, 0.0f), static_cast<float>(nseg));
+                int ix = static_cast<int>(u);
+                if (ix > nseg - 1) ix = nseg - 1;
+                sfrac[j] = u - static_cast<float>(ix);
+                node[j] = (fine ? ds.tabf[pos] : ds.tab[pos]) + h[j].node + ix;
+              }
+            }
+          }
+        }
+        float4 n0[2];
+        float2 n1[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          if (mode[j] == 2) {
+            n0[j] = __ldg(node[j]);
+            n1[j] = __ldg(reinterpret_cast<const float2*>(node[j] + 1) + 1);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          float L = 0.0f;
+          if (mode[j] == 3) {
+            const float2 r = dense_pair_slow(p, pi[j], ta + tl[j], kk[j]);
+            L = r.x;
+            nc += static_cast<unsigned long long>(r.y);
+          } else if (mode[j] != 0) {
+            const uint32_t pos = pair_pos(h[j].meta);
+            float loss = val[j];
+            if (mode[j] == 2)
+              loss = (n0[j].x > 0.0f)
+                         ? h[j].max_l * (n0[j].x * expf(tab_increment(sfrac[j], n0[j].y, n0[j].z, n0[j].w, n1[j].x,
+                                                                       n1[j].y)))
+                         : 0.0f;
+            L = ds.share[pos] * clamp_terms_f(loss, ds.ret[pos], ds.lim[pos]);
+          }
+          if (32u * j + lane < np) {
+            ws.loss[q[j]] = L;
+            ws.lmask[q[j]] = mk[j];
+          }
+          n_pairs += mk[j] != 0u;
+        }
+        p_done += np;
+        __syncwarp();
+      }
+      // ---- combine: complete records of the current trial, up to 64 at a time (two per lane)
+      for (;;) {
+        uint32_t cnt[2], m[2], multi[2], col[2];
+        int rt[2];
+        bool have[2];
+        uint32_t n_ok = 0u;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t gi = 32u * h + lane;  // the record's place in the group
+          const uint32_t R = r_done + gi;
+          have[h] = R < r_fill;
+          const uint32_t slot = R % kDenseRecs;
+          const uint2 r = have[h] ? ws.rec[slot] : zero2;
+          const uint32_t pre = have[h] ? ws.pre[slot] : 0u;
+          cnt[h] = ((r.x >> kRecCntShift) & kRecCntMask) + 1u;
+          rt[h] = static_cast<int>(r.x >> kRecTrialShift);
+          // a prefix of the group (records are in trial order; <= rather than == keeps the
+          // loop finite whatever the order)
+          const bool ok = have[h] && pre + cnt[h] <= p_done && rt[h] <= cur;
+          n_ok += __popc(__ballot_sync(0xffffffffu, ok));
+          multi[h] = __ballot_sync(0xffffffffu, ok && cnt[h] > 1u);
+          m[h] = 0u;  // the layers the record serves
+          if (ok) {
+            const uint32_t q0 = pre % kDensePairs;
+            m[h] = ws.lmask[q0];
+            for (uint32_t j = 1; j < cnt[h]; ++j) m[h] |= ws.lmask[(pre + j) % kDensePairs];
+            ws.g_l0[gi] = ws.loss[q0];
+            ws.g_pre[gi] = pre;
+            ws.g_cnt[gi] = cnt[h];
+          }
+          col[h] = __shfl_sync(0xffffffffu, bit_transpose32(m[h], lane), my_l) & my_pattern;
+        }
+        __syncwarp();
+        // lane (s, l): the group's records of slot s that serve layer l
+        unsigned long long one = static_cast<unsigned long long>(col[0] & ~multi[0]) |
+                                 (static_cast<unsigned long long>(col[1] & ~multi[1]) << 32);
+        unsigned long long many = static_cast<unsigned long long>(col[0] & multi[0]) |
+                                  (static_cast<unsigned long long>(col[1] & multi[1]) << 32);
+        const float4 oc = ds.occ[my_l];  // the layer's occurrence terms and fixed-point scale
+        for (; one; one &= one - 1ull) {  // single-ELT records: the loss of their one pair
+          const float O = clamp_terms_f(ws.g_l0[__ffsll(one) - 1], oc.x, oc.y);
+          acc += fixed_units(O, oc.z);
+        }
+        for (; many; many &= many - 1ull) {  // the others: their pairs over the layer's ELTs, left to right
+          const int i = __ffsll(many) - 1;
+          const uint32_t c = ws.g_cnt[i], pr = ws.g_pre[i];
+          float G = 0.0f;
+          for (uint32_t j = 0; j < c; ++j) {
+            const uint32_t qq = (pr + j) % kDensePairs;
+            if ((ws.lmask[qq] >> my_l) & 1u) G += ws.loss[qq];
+          }
+          acc += fixed_units(clamp_terms_f(G, oc.x, oc.y), oc.z);
+        }
+        __syncwarp();  // the group's staging is rewritten by the next group
+        r_done += n_ok;
+        if (n_ok == 64u) continue;
+        // the first record not combined: of a later trial (the current one is done), or not complete
+        const bool hi = n_ok >= 32u;
+        const bool stop_have = __shfl_sync(0xffffffffu, (hi ? have[1] : have[0]) ? 1 : 0, n_ok & 31u) != 0;
+        const int stop_t = __shfl_sync(0xffffffffu, hi ? rt[1] : rt[0], n_ok & 31u);
+        if (stop_have && stop_t > cur) {
+          for (; cur < stop_t; ++cur) dense_finish_trial(ds, acc, lane, nlp, nl, ta + cur, p.t_begin);
+          continue;
+        }
+        break;
+      }
+      if (rec_next >= n && r_done == r_fill) break;
+    }
+    for (; cur < ntr; ++cur) dense_finish_trial(ds, acc, lane, nlp, nl, ta + cur, p.t_begin);
+    __syncwarp();
+  }
+  n_pairs = __reduce_add_sync(0xffffffffu, n_pairs);
+  for (int d = 16; d > 0; d >>= 1) nc += __shfl_xor_sync(0xffffffffu, nc, d);
+  if (lane == 0) {
+    if (n_pairs) atomicAdd(&p.counters[1], static_cast<unsigned long long>(n_pairs));
+    if (nc) atomicAdd(&p.counters[2], nc);
+  }
+}
+
+int losses_dense_blocks_per_sm(int /*n_layers*/) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_losses_dense, kBatchThreads, 0) != cudaSuccess) return 0;
+  return b;
+}
+
+cudaError_t launch_losses_batch(const BatchParams& p, int item, int grid, cudaStream_t s) {
+  switch (item) {
+    case kItemTile:
+      k_losses_batch<false><<<grid, kBatchThreads, 0, s>>>(p);
+      break;
+    case kItemTrial:
+      k_losses_batch<true><<<grid, kBatchThreads, 0, s>>>(p);
+      break;
+    case kItemDense:
+      k_losses_dense<<<grid, kBatchThreads, 0, s>>>(p);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

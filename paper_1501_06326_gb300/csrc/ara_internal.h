@@ -204,19 +204,27 @@ struct BatchParams {
   unsigned long long layers_of[kMaxIndexElts];  // per union position: bitmask of the layers holding it
   float occ_r[kBatchLayers], occ_l[kBatchLayers];
   double agg_r[kBatchLayers], agg_l[kBatchLayers];
-  int32_t scale_exp[kBatchLayers];     // fixed point: a layer's occurrence loss O is counted as O * 2^scale_exp
-  double inv_scale[kBatchLayers];      // 2^-scale_exp
+  float scale[kBatchLayers];           // fixed point: a layer's occurrence loss O counts as round(O * scale)
+                                       // units, scale = 2^e with -126 <= e <= 127 (an FP32 power of two)
+  double inv_scale[kBatchLayers];      // 1 / scale
   uint32_t rk[20];                     // Philox round keys of the seed
   int32_t primary_only;
   int32_t newton_only;
   double* ylt_l[kBatchLayers];         // layer l's year losses of trials [t_begin, layer_t_end[l]) (indexed from t_begin)
-  unsigned long long* counters;        // [0] tile queue, [1] pairs, [2] non-converged
+  unsigned long long* counters;        // [0] tile queue, [1] pairs, [2] non-converged, [3] ring overflow (0)
   int64_t layer_t_end[kBatchLayers];   // layer l's trials end here (<= t_end): later trials get no losses, no output
 };
 
-// per_trial: one warp per trial (many hit records per trial), else one warp
-// per tile of kWarpTrials trials; the results are the same.
-cudaError_t launch_losses_batch(const BatchParams& p, bool per_trial, int grid, cudaStream_t s);
+// The losses kernel's work items; all three add the same fixed-point numbers,
+// so they give the same results.
+enum BatchItem : int {
+  kItemTile = 0,   // one warp per tile of kWarpTrials trials, a lane per record
+  kItemTrial = 1,  // one warp per trial of a tile, a lane per record
+  kItemDense = 2,  // one warp per tile, a lane per pair (records streamed through per-warp rings)
+};
+cudaError_t launch_losses_batch(const BatchParams& p, int item, int grid, cudaStream_t s);
+// CTAs of the dense kernel that one SM holds for n_layers layers (0 on error).
+int losses_dense_blocks_per_sm(int n_layers);
 
 size_t gather_smem_bytes(int filt_words);
 int gather_filter_words(int64_t n_words, int max_smem);

@@ -140,10 +140,10 @@ def test_paper_shaped_batch_sampled(eng):
         check_ylt(out[l], oracle.run_layer(yet, sub, terms, seed=0))
 
 
-def test_trial_items_and_tile_items_agree(eng):
-    # the 16-layer batch has about 320 hit records per trial (one-trial work items);
-    # each layer alone has at most about 160 (tiles of 8 trials): the same
-    # fixed-point sums, so each layer's year losses are identical bit for bit
+def test_a_layer_alone_and_in_a_batch_agree(eng):
+    # each layer of a 16-layer batch (about 320 hit records per trial) against the
+    # layer alone (at most about 160): the same fixed-point sums, so each layer's
+    # year losses are identical bit for bit
     spec = synth.WORKLOADS["paper-1m"]
     yet = synth.make_yet(1200, spec["mean_events"], spec["catalogue"], spec["seed"])
     pool = synth.make_elt_pool(64, spec["entries"], spec["catalogue"], spec["seed"] + 7)
@@ -216,9 +216,102 @@ def test_autotuner_keeps_the_results_and_caches_its_choice(eng, small_batch):
     assert eng.stats()["batch_tuned"] == 0
     tuned = _run_batch(eng, yet, pool, layers, 5, t1=t1, autotune=True)
     st = eng.stats()
-    assert st["batch_tuned"] == 1 and st["batch_per_trial"] in (0, 1) and 2 <= st["batch_blocks_per_sm"] <= 4
+    assert st["batch_tuned"] == 1 and st["batch_item"] in (0, 1, 2) and 2 <= st["batch_blocks_per_sm"] <= 16
     again = _run_batch(eng, yet, pool, layers, 5, t1=t1)
     st2 = eng.stats()
     assert st2["batch_tuned"] == 1
-    assert (st2["batch_per_trial"], st2["batch_blocks_per_sm"]) == (st["batch_per_trial"], st["batch_blocks_per_sm"])
+    assert (st2["batch_item"], st2["batch_blocks_per_sm"]) == (st["batch_item"], st["batch_blocks_per_sm"])
     assert np.array_equal(base, tuned) and np.array_equal(base, again)
+
+
+def _run_items(eng, yet, pool, layers, seed, t0=0, t1=None, blocks=(0,), **kw):
+    """The pass under each work item (and CTAs per SM) pinned by ara_set_batch_config."""
+    from paper_1501_06326_gb300 import ara
+
+    outs = {}
+    try:
+        for item in (ara.ARA_BATCH_ITEM_TILE, ara.ARA_BATCH_ITEM_TRIAL, ara.ARA_BATCH_ITEM_DENSE):
+            for b in blocks:
+                eng.set_batch_config(item, b)
+                outs[(item, b)] = _run_batch(eng, yet, pool, layers, seed, t0, t1, **kw)
+                st = eng.stats()
+                assert st["batch_item"] == item and st["batch_tuned"] == 0
+                assert b == 0 or st["batch_blocks_per_sm"] == b
+    finally:
+        eng.set_batch_config(ara.ARA_BATCH_AUTO)
+    return outs
+
+
+def _assert_same_bits(outs):
+    ref = next(iter(outs.values()))
+    for key, out in outs.items():
+        assert np.array_equal(out, ref), f"work item / blocks {key} differs"
+    return ref
+
+
+def test_work_items_give_the_same_bits(eng):
+    """The three losses kernels (a lane per record over a tile or over one trial,
+    a lane per pair over a tile) add the same fixed-point numbers: identical
+    bits on the paper-shaped 16-layer batch, at 2 CTAs per SM and at the most
+    an SM holds; the dense kernel's result against the oracle."""
+    spec = synth.WORKLOADS["paper-1m"]
+    yet = synth.make_yet(600, spec["mean_events"], spec["catalogue"], spec["seed"] + 3)
+    pool = synth.make_elt_pool(64, spec["entries"], spec["catalogue"], spec["seed"] + 7)
+    layer_ids = synth.draw_layers(16, pool.elt_ids, 32, spec["seed"] + 8)
+    layers = []
+    for ids in layer_ids:
+        sub = pool.subset([int(np.flatnonzero(pool.elt_ids == i)[0]) for i in ids])
+        layers.append((ids, oracle.calibrate_layer_terms(yet, sub), sub))
+    out = _assert_same_bits(_run_items(eng, yet, pool, layers, 4, blocks=(0, 2)))
+    for l in (0, 7, 15):
+        check_ylt(out[l], oracle.run_layer(yet, layers[l][2], layers[l][1], seed=4))
+    # a subrange whose first tile is partial, and the Halley path for every pair
+    _assert_same_bits(_run_items(eng, yet, pool, layers, 4, 13, 470))
+    out = _assert_same_bits(_run_items(eng, yet, pool, layers[:4], 4, 0, 100, newton_only=True))
+    for l in range(4):
+        check_ylt(out[l], oracle.run_layer(yet, layers[l][2], layers[l][1], seed=4, trials=np.arange(100)))
+
+
+def test_work_items_on_events_with_64_pairs(eng):
+    """Every ELT of a 64-ELT pool holds every event of a 300-event catalogue, so
+    each hit event has one pair per ELT (64, the most a record holds): long
+    records cross the dense kernel's compute rounds and fill its pair ring.
+    32 layers of up to 32 ELTs; all work items agree, and match the oracle."""
+    C = 300
+    yet = synth.make_yet(160, 40.0, C, 91)
+    pool = synth.make_elt_pool(64, C, C, 92)
+    layer_ids = synth.draw_layers(32, pool.elt_ids, 32, 93)
+    layers = []
+    for ids in layer_ids:
+        sub = pool.subset([int(np.flatnonzero(pool.elt_ids == i)[0]) for i in ids])
+        layers.append((ids, oracle.calibrate_layer_terms(yet, sub), sub))
+    out = _assert_same_bits(_run_items(eng, yet, pool, layers, 6))
+    for l in (0, 13, 31):
+        check_ylt(out[l], oracle.run_layer(yet, layers[l][2], layers[l][1], seed=6))
+
+
+def test_work_items_on_empty_and_long_trials(eng):
+    """Empty trials (at tile starts and ends), a 4,097-event trial, a partial last
+    tile, and a subrange: all work items agree."""
+    rng = np.random.default_rng(12)
+    C = 2003
+    lens = [0, 0, 3, 0, 4097, 0, 0, 0, 0, 1, 0, 250] + list(rng.integers(0, 40, 203)) + [0, 0]
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    offsets[1:] = np.cumsum(lens)
+    yet = synth.YET(offsets, rng.integers(0, C, offsets[-1]).astype(np.int32), C)
+    pool = synth.make_elt_pool(6, 300, C, 32)
+    layers = [(np.array(ids, np.int32), (100.0, 5e5, 1e3, 5e6), None)
+              for ids in ([0, 1, 2], [2, 3, 4, 5], [5], [0, 5])]
+    _assert_same_bits(_run_items(eng, yet, pool, layers, 2))
+    _assert_same_bits(_run_items(eng, yet, pool, layers, 2, 3, 200))
+    _assert_same_bits(_run_items(eng, yet, pool, layers, 2, 4, 5))
+
+
+def test_batch_config_errors(eng):
+    from paper_1501_06326_gb300 import ara
+
+    for item, blocks in ((3, 0), (-2, 0), (ara.ARA_BATCH_ITEM_DENSE, -1), (ara.ARA_BATCH_ITEM_TILE, 17)):
+        with pytest.raises(ara.AraError) as e:
+            eng.set_batch_config(item, blocks)
+        assert e.value.code == ara.ARA_EINVAL
+    eng.set_batch_config(ara.ARA_BATCH_AUTO)
