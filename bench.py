@@ -85,10 +85,10 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic():
-    """DRAM bytes per launch of the layer kernels from the committed ncu figures
-    (profiles/k_layer_paper-1m.json, beside its summary), if they were taken on
-    the current kernel sources (else None)."""
+def _profiled_layer(key):
+    """A per-launch figure of the layer kernels from the committed ncu capture
+    (profiles/k_layer_paper-1m.json, beside its summary), if it was taken on the
+    current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "k_layer_paper-1m.json")
     try:
         with open(path) as fh:
@@ -97,8 +97,13 @@ def _profiled_traffic():
         return None
     if d.get("source_hash") != _kernel_source_hash():
         return None
-    v = d.get("dram_bytes_per_full_launch")
+    v = d.get(key)
     return float(v) if v is not None else None
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the layer kernels (ncu), or None."""
+    return _profiled_layer("dram_bytes_per_full_launch")
 
 
 def _usable_cores() -> int:
@@ -368,9 +373,12 @@ def run_gpu(args):
         e2e_step()
         barrier()
         n_e2e = max(2, min(args.steps, 5))
+        step_ms = []
         t0 = time.perf_counter()
         for _ in range(n_e2e):
+            t_s = time.perf_counter()
             e2e_step()
+            step_ms.append((time.perf_counter() - t_s) * 1e3)
         barrier()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
         if ws > 1:
@@ -396,7 +404,7 @@ def run_gpu(args):
         h2d = offsets.nbytes + 4 * n_events + pool_bytes + 8 * n_trials  # ylt host -> device staging for PML
         d2h = 8 * n_trials + 16 * len(rps)
         e2e = {"value": ws * evals_per_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "ms_steps": step_ms,
                "yet_upload_ms": upload_ms, "yet_upload_gbs": 4 * n_events / (upload_ms * 1e-3) / 1e9,
                "memory_nodes": _memory_nodes(ids_host.data_ptr(), 4 * n_events, local),
                "elt_load_ms": elt_ms,
@@ -452,6 +460,17 @@ def run_gpu(args):
     if ws == 1 and not args.no_serving and n_trials == synth.WORKLOADS["serving"]["n_trials"]:
         serving = _serving_leg(eng, synth, offsets, args)
 
+    # ---- the second bound: warp instructions issued (ncu count per launch) against the SMs'
+    # issue rate (4 warp instructions per SM per cycle at the sampled SM clock)
+    clk = clocks.summary()
+    inst = _profiled_layer("warp_instructions_per_full_launch")
+    if inst is not None and clk.get("sm_mhz"):
+        n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        issue_peak = n_sms * 4 * clk["sm_mhz"] * 1e6
+        roofline["issue"] = {"warp_instructions": inst, "achieved": inst / (kernel_ms * 1e-3), "peak": issue_peak,
+                             "unit": "warp instructions/s", "frac": inst / (kernel_ms * 1e-3) / issue_peak,
+                             "peak_source": f"{n_sms} SMs x 4 issue slots x {clk['sm_mhz']:.0f} MHz (sampled)"}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -467,7 +486,7 @@ def run_gpu(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": tm["kernel_launches"] // max(args.steps, 1),
-            "clocks": clocks.summary(),
+            "clocks": clk,
             "stats": {"index_ms": tm["index_ms"] / max(tm["layer_calls"], 1),
                       "pml_ms": tm["pml_ms"] / max(tm["pml_calls"], 1), "pairs_hit": st["n_pairs_hit"],
                       "nonconverged": st["n_nonconverged"], "newton_pairs": st["n_newton"],
@@ -748,7 +767,7 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency sweep")
     ap.add_argument("--no-stress", action="store_true", help="skip the precision-stress layer")
     ap.add_argument("--serve-requests", type=int, default=10_000, help="requests per rate of the serving sweep")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 800.0, 3200.0],
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 800.0, 1600.0, 3200.0],
                     help="request arrival rates (per second) of the serving sweep")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps
