@@ -1451,10 +1451,24 @@ int serve_launch_round(ara_ctx* c, const char* who, int32_t* n_failed) {
     std::vector<int64_t> members{cand[i]};
     used[i] = true;
     std::vector<int32_t> uni = a.elt_ids;
-    for (size_t j = i + 1; j < cand.size() && members.size() < static_cast<size_t>(ARA_MAX_BATCH_LAYERS); ++j) {
+    // the pass's other members: requests at the same chunk with the same seed and flags,
+    // those whose trials end closest to the first member's within the chunk first (a pass
+    // streams its chunk up to its longest member's end), then in arrival order
+    const int64_t c_begin = a.next_chunk * kServeChunk;
+    auto len_in_chunk = [&](const ServeReq& q) { return std::min(q.t_end, c_begin + kServeChunk) - c_begin; };
+    std::vector<std::pair<int64_t, size_t>> order;
+    for (size_t j = i + 1; j < cand.size(); ++j) {
       if (used[j]) continue;
       const ServeReq& b = c->serve_reqs[cand[j]];
       if (b.next_chunk != a.next_chunk || b.seed != a.seed || b.layer.flags != a.layer.flags) continue;
+      order.emplace_back(std::llabs(len_in_chunk(b) - len_in_chunk(a)), j);
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<int64_t, size_t>& x, const std::pair<int64_t, size_t>& y) { return x.first < y.first; });
+    for (const auto& o : order) {
+      if (members.size() >= static_cast<size_t>(ARA_MAX_BATCH_LAYERS)) break;
+      const size_t j = o.second;
+      const ServeReq& b = c->serve_reqs[cand[j]];
       std::vector<int32_t> u2 = uni;
       u2.insert(u2.end(), b.elt_ids.begin(), b.elt_ids.end());
       std::sort(u2.begin(), u2.end());
