@@ -133,6 +133,9 @@ struct ara_ctx {
   DevBuf serve_arena;                   // year losses of the admitted requests
   std::map<size_t, size_t> arena_free;  // free blocks of the arena: offset -> bytes
   DevBuf serve_out;                     // device result slots (PML, TVaR)
+  DevBuf serve_sel;                     // select scratch of the requests' PML/TVaR
+  cudaStream_t serve_side = nullptr;    // the requests' PML/TVaR and result copies, beside the passes
+  cudaEvent_t serve_join = nullptr;     // the passes' stream up to a point, for the side stream to wait on
   double* serve_host = nullptr;         // pinned host result slots
   std::vector<int32_t> serve_slots_free;
   int64_t serve_rounds_launched = 0, serve_passes = 0, serve_finished = 0;
@@ -1309,7 +1312,7 @@ std::vector<std::pair<DevBuf*, size_t>> serve_workspace(ara_ctx* c) {
       {&c->pairs_hot, sizeof(ara::PairHot) * (n_recs + 1)},
       {&c->pairs_ev, sizeof(int32_t) * (n_recs + 1)},
       {&c->scan_tmp, sizeof(uint32_t) * (tmp_words + 8)},
-      {&c->sel, ara::select_scratch_bytes(c->n_trials)},
+      {&c->serve_sel, ara::select_scratch_bytes(c->n_trials)},
       {&c->serve_out, 2 * sizeof(double) * ARA_SERVE_MAX_RP * kServeSlots},
   };
   if (any_corr) w.push_back({&c->pairs_w, sizeof(float2) * (n_recs + 1)});
@@ -1337,6 +1340,11 @@ int serve_prepare(ara_ctx* c, const char* who) {
   int rc;
   for (const auto& w : serve_workspace(c))
     if ((rc = reserve(c, *w.first, w.second))) return rc;
+  if (!c->serve_side && (cudaStreamCreateWithFlags(&c->serve_side, cudaStreamNonBlocking) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&c->serve_join, cudaEventDisableTiming) != cudaSuccess)) {
+    cudaGetLastError();
+    return fail(c, ARA_ECUDA, "%s: cannot create the serving side stream", who);
+  }
   if (!c->serve_host) {
     void* h = nullptr;
     if (cudaHostAlloc(&h, 2 * sizeof(double) * ARA_SERVE_MAX_RP * kServeSlots, cudaHostAllocDefault) != cudaSuccess) {
@@ -1492,19 +1500,28 @@ int serve_launch_round(ara_ctx* c, const char* who, int32_t* n_failed) {
       outs[m] = arena + q.ylt_off / sizeof(double) + t0;
     }
     int rc = run_layers_impl(c, nm, layers.data(), a.seed, t0, t1, nullptr, t_ends.data(), outs.data());
+    bool joined = false;
     for (int32_t m = 0; m < nm && !rc; ++m) {
       ServeReq& q = c->serve_reqs[members[m]];
       if (++q.next_chunk < q.n_chunks) continue;
-      // the request's last chunk: its PML/TVaR over its whole prefix, then the results to the host
+      // the request's last chunk: its PML/TVaR over its whole prefix, then the results to the host,
+      // on the side stream once the pass is done (they overlap the round's later passes)
+      cudaError_t e = cudaSuccess;
+      if (!joined) {
+        e = cudaEventRecord(c->serve_join, c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->serve_side, c->serve_join, 0);
+        joined = true;
+      }
       double* slot = d_out + static_cast<size_t>(q.slot) * 2 * ARA_SERVE_MAX_RP;
       int launched = 0;
-      cudaError_t e = ara::pml_tvar_device(arena + q.ylt_off / sizeof(double), q.t_end, q.rps.data(),
-                                           static_cast<int32_t>(q.rps.size()), slot, slot + ARA_SERVE_MAX_RP,
-                                           c->sel.ptr, c->sel.bytes, c->stream, &launched);
+      if (e == cudaSuccess)
+        e = ara::pml_tvar_device(arena + q.ylt_off / sizeof(double), q.t_end, q.rps.data(),
+                                 static_cast<int32_t>(q.rps.size()), slot, slot + ARA_SERVE_MAX_RP, c->serve_sel.ptr,
+                                 c->serve_sel.bytes, c->serve_side, &launched);
       c->launches += launched;
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->serve_host + static_cast<size_t>(q.slot) * 2 * ARA_SERVE_MAX_RP, slot,
-                            2 * sizeof(double) * ARA_SERVE_MAX_RP, cudaMemcpyDeviceToHost, c->stream);
+                            2 * sizeof(double) * ARA_SERVE_MAX_RP, cudaMemcpyDeviceToHost, c->serve_side);
       if (e != cudaSuccess) rc = fail(c, ARA_ECUDA, "%s: %s", who, cudaGetErrorString(e));
       else round.finishing.push_back(members[m]);
     }
@@ -1522,7 +1539,10 @@ int serve_launch_round(ara_ctx* c, const char* who, int32_t* n_failed) {
     ++passes;
   }
   c->no_timing = false;
-  const cudaError_t e = cudaEventRecord(round.ev, c->stream);
+  // the round is done when both streams are: the side stream waits for the passes, then records
+  cudaError_t e = cudaEventRecord(c->serve_join, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->serve_side, c->serve_join, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(round.ev, c->serve_side);
   if (e != cudaSuccess) {
     cudaGetLastError();
     c->serve_ev_free.push_back(round.ev);
@@ -1873,6 +1893,7 @@ void ara_destroy(ara_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  if (c->serve_side) cudaStreamSynchronize(c->serve_side);
   for (auto& kv : c->pool) {
     release(c, kv.second.events);
     release(c, kv.second.recs);
@@ -1885,7 +1906,7 @@ void ara_destroy(ara_ctx* c) {
                     &c->yet_ids,    &c->bits,           &c->word_cnt,      &c->word_pairs,     &c->rankdir,
                     &c->mask,       &c->slot_cnt,       &c->pairs,         &c->pairs_hot,     &c->pairs_w,          &c->pairs_ev,         &c->scan_tmp,       &c->flags,
                     &c->counters,   &c->ylt_tmp,        &c->diag_tmp,      &c->sel,            &c->in_tmp,
-                    &c->out_tmp,    &c->serve_arena,    &c->serve_out,      &c->ev_occ,        &c->row_base,
+                    &c->out_tmp,    &c->serve_arena,    &c->serve_out,      &c->serve_sel,      &c->ev_occ,        &c->row_base,
                     &c->evr_stage,  &c->yet_flags};
   for (DevBuf* b : bufs) release(c, *b);
   for (auto& e : c->ev)
@@ -1895,6 +1916,8 @@ void ara_destroy(ara_ctx* c) {
   for (auto& e : c->tune_ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : c->serve_ev_free) cudaEventDestroy(e);
+  if (c->serve_join) cudaEventDestroy(c->serve_join);
+  if (c->serve_side) cudaStreamDestroy(c->serve_side);
   if (c->serve_host) cudaFreeHost(c->serve_host);
   if (c->yet_ready) cudaEventDestroy(c->yet_ready);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
