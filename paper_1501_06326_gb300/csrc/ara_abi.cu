@@ -1224,8 +1224,9 @@ int ara_get_timing(ara_ctx* c, ara_timing* out, int reset) {
 // kServeChunk trials; an admitted request has a cursor, its next chunk.
 // ara_serve_step retires the rounds the device has finished (cudaEventQuery,
 // no waiting), admits queued requests whose year losses fit the serving
-// arena, and launches one round: at most kServePassesPerRound batched passes
-// (ara_run_layers over one chunk), each for up to ARA_MAX_BATCH_LAYERS
+// arena, and launches one round: batched passes (ara_run_layers over one
+// chunk), kServePassesShort at most while kServeShortBacklog or fewer requests
+// have chunks to run, else kServePassesPerRound, each for up to ARA_MAX_BATCH_LAYERS
 // admitted requests that are at the same chunk, with one seed and flags and
 // at most ARA_MAX_BATCH_ELTS ELTs together, every layer writing its chunk
 // into its own request's year losses.  Behind a request's last chunk the
@@ -1237,7 +1238,9 @@ namespace {
 
 constexpr int64_t kServeChunk = 131072;        // trials per chunk
 constexpr size_t kServeMaxInFlight = 2;        // rounds launched and not retired
-constexpr int kServePassesPerRound = 8;
+constexpr int kServePassesPerRound = 16;       // a round's passes under a long backlog
+constexpr int kServePassesShort = 4;           // ... and under a short one
+constexpr size_t kServeShortBacklog = 128;     // requests with chunks to run, at most, for a short backlog
 constexpr int32_t kServeSlots = 1024;          // result slots: admitted requests at most
 constexpr int64_t kServeArenaRequests = 96;    // default arena: year losses of this many whole-YET requests
 constexpr size_t kArenaAlign = 256;
@@ -1453,7 +1456,10 @@ int serve_launch_round(ara_ctx* c, const char* who, int32_t* n_failed) {
   std::vector<bool> used(cand.size(), false);
   int passes = 0, status = ARA_OK;
   c->no_timing = true;
-  for (size_t i = 0; i < cand.size() && passes < kServePassesPerRound; ++i) {
+  // short rounds while the backlog is short (a request that arrives waits for less), long ones
+  // under a long backlog (fewer rounds to launch and retire)
+  const int max_passes = cand.size() > kServeShortBacklog ? kServePassesPerRound : kServePassesShort;
+  for (size_t i = 0; i < cand.size() && passes < max_passes; ++i) {
     if (used[i]) continue;
     const ServeReq& a = c->serve_reqs[cand[i]];
     std::vector<int64_t> members{cand[i]};
