@@ -231,3 +231,29 @@ def test_wait_serves_until_the_request_is_done(eng, world):
         eng.wait(t_c, len(RPS), timeout_ns=1)
     assert e.value.code == ara.ARA_ETIMEOUT
     assert eng.wait(t_c, len(RPS)) is not None
+
+
+def test_direct_selects_while_rounds_are_in_flight(eng, world):
+    """ara_pml_tvar on the same context while serving rounds are in flight: the
+    requests' selects run on their own stream with their own scratch, so the
+    served results equal those of serving alone, and the direct calls match
+    the oracle."""
+    yet, pool, reqs = world
+    _load(eng, yet, pool)
+    alone = _serve_all(eng, reqs[:6], seed=21)
+    tickets = [eng.submit(ids, terms, 21, t_end, RPS) for ids, terms, t_end, _ in reqs[:6]]
+    rng = np.random.default_rng(22)
+    done = {}
+    while len(done) < len(tickets):
+        eng.serve_step()
+        y = np.round(rng.lognormal(5.0, 2.0, int(rng.integers(10, 20_000))), 2)
+        pml, tvar = eng.pml_tvar(y, RPS)
+        rpml, rtvar = oracle.pml_tvar(y, RPS)
+        assert np.array_equal(pml, rpml) and np.allclose(tvar, rtvar, rtol=1e-12, atol=0)
+        for tk in tickets:
+            if tk not in done:
+                r = eng.poll(tk, len(RPS))
+                if r is not None:
+                    done[tk] = r
+    for a, tk in zip(alone, tickets):
+        assert np.array_equal(a[0], done[tk][0]) and np.array_equal(a[1], done[tk][1])
