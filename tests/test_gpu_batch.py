@@ -275,10 +275,20 @@ def test_work_items_give_the_same_bits(eng):
 def test_work_items_on_events_with_64_pairs(eng):
     """Every ELT of a 64-ELT pool holds every event of a 300-event catalogue, so
     each hit event has one pair per ELT (64, the most a record holds): long
-    records cross the dense kernel's compute rounds and fill its pair ring.
-    32 layers of up to 32 ELTs; all work items agree, and match the oracle."""
+    records cross the dense kernel's compute rounds and fill its pair ring; one
+    trial has 4,097 such events.  32 layers of up to 32 ELTs; all work items
+    agree, and match the oracle."""
     C = 300
-    yet = synth.make_yet(160, 40.0, C, 91)
+    base = synth.make_yet(160, 40.0, C, 91)
+    # and a 4,097-event trial (262,208 pairs in one tile) between empty ones
+    rng = np.random.default_rng(94)
+    lens = np.diff(base.offsets).tolist()
+    lens[17:17] = [0, 4097, 0]
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    offsets[1:] = np.cumsum(lens)
+    ev = np.concatenate([base.event_ids[: base.offsets[17]], rng.integers(0, C, 4097).astype(np.int32),
+                         base.event_ids[base.offsets[17]:]])
+    yet = synth.YET(offsets, ev, C)
     pool = synth.make_elt_pool(64, C, C, 92)
     layer_ids = synth.draw_layers(32, pool.elt_ids, 32, 93)
     layers = []
