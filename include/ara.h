@@ -305,18 +305,41 @@ ARA_API int ara_run_layers(ara_ctx *ctx, int32_t n_layers, const ara_layer *laye
  *   ARA_BATCH_ITEM_TRIAL  one warp per trial, a lane per hit record;
  *   ARA_BATCH_ITEM_DENSE  one warp per tile of 8 trials, a lane per (event, ELT)
  *                         pair: each pair's loss once, then each record's
- *                         per-layer occurrence losses.
+ *                         per-layer occurrence losses;
+ *   ARA_BATCH_ITEM_INDEXED  (once ara_build_yet_index has run) a warp per
+ *                         event of the pass's ELTs, over that event's
+ *                         occurrences in the pass's trials, from the YET's
+ *                         event-major index: the YET is not streamed.
  * ara_set_batch_config pins the work item and the CTAs per SM of the
  * persistent grid (blocks_per_sm 0: as many as an SM holds; a larger number is
  * cut to that) for later passes; item ARA_BATCH_AUTO returns to the cached
- * autotuner choice for the pass's shape, else the default rule (the dense item
- * with as many CTAs as an SM holds).
+ * autotuner choice for the pass's shape, else the default rule (the indexed
+ * item when the YET's index is built, else the dense item, with as many CTAs
+ * as an SM holds).
  * Errors: ARA_EINVAL (unknown item, blocks_per_sm outside 0..16). */
 #define ARA_BATCH_AUTO (-1)
 #define ARA_BATCH_ITEM_TILE 0
 #define ARA_BATCH_ITEM_TRIAL 1
 #define ARA_BATCH_ITEM_DENSE 2
+#define ARA_BATCH_ITEM_INDEXED 3
 ARA_API int ara_set_batch_config(ara_ctx *ctx, int32_t item, int32_t blocks_per_sm);
+
+/* The event-major index of the loaded YET (Section 2.1's lookup taken from the
+ * ELT side): for each catalogue event, its occurrences (trial, event index) in
+ * trial order, built on the device by a stable radix sort of the YET's events
+ * by id.  Once built, batched passes (ara_run_layers and the serving loop)
+ * default to ARA_BATCH_ITEM_INDEXED, which reaches a pass's hit events through
+ * its ELTs' events instead of streaming every trial's events; the year losses
+ * are the same bits as the other work items'.  ara_run_layer (one layer, with
+ * its double-float sums and hit diagnostics) keeps streaming the YET.
+ * The index takes 8 bytes per YET event and 4 per catalogue id, and lasts until
+ * the next YET load; the build needs about 24 bytes per event of scratch
+ * besides.  Errors: ARA_ENOTLOADED; ARA_EINVAL (served requests queued or
+ * running, or 2^32 or more events); ARA_ENOMEM; ARA_ECUDA.
+ * ara_yet_index_info reports whether the index is built, its bytes and the
+ * device time of its build (any pointer may be NULL). */
+ARA_API int ara_build_yet_index(ara_ctx *ctx);
+ARA_API int ara_yet_index_info(const ara_ctx *ctx, int32_t *built, int64_t *bytes, float *build_ms);
 
 /* Serving: layer requests against the resident YET and ELT pool, with
  * continuous batching.  The paper has no serving system; a portfolio's

@@ -32,7 +32,7 @@ ARA_MAX_LAYER_ELTS = 32
 ARA_MAX_BATCH_LAYERS = 32
 ARA_MAX_BATCH_ELTS = 64
 ARA_SERVE_MAX_RP = 16
-ARA_BATCH_AUTO, ARA_BATCH_ITEM_TILE, ARA_BATCH_ITEM_TRIAL, ARA_BATCH_ITEM_DENSE = -1, 0, 1, 2
+ARA_BATCH_AUTO, ARA_BATCH_ITEM_TILE, ARA_BATCH_ITEM_TRIAL, ARA_BATCH_ITEM_DENSE, ARA_BATCH_ITEM_INDEXED = -1, 0, 1, 2, 3
 _ERR_NAMES = {
     ARA_EINVAL: "ARA_EINVAL", ARA_ENOMEM: "ARA_ENOMEM", ARA_ENOTLOADED: "ARA_ENOTLOADED",
     ARA_ECUDA: "ARA_ECUDA", ARA_ETIMEOUT: "ARA_ETIMEOUT", ARA_EAGAIN: "ARA_EAGAIN",
@@ -45,7 +45,7 @@ EXPORTED = (
     "ara_debug_record_losses", "ara_get_stats", "ara_get_timing", "ara_last_error", "ara_destroy",
     "ara_pml_tvar_noalloc", "ara_run_layers", "ara_submit", "ara_serve_step", "ara_poll", "ara_load_xelts",
     "ara_run_layer_events", "ara_wait", "ara_load_yet_async", "ara_finish_yet", "ara_serve_stats",
-    "ara_top_m", "ara_merge_top", "ara_set_batch_config",
+    "ara_top_m", "ara_merge_top", "ara_set_batch_config", "ara_build_yet_index", "ara_yet_index_info",
 )
 ARA_NOALLOC_MAX_RP = 64
 
@@ -167,6 +167,8 @@ def load_library(path: str = LIB_PATH):
     lib.ara_run_layer_diag.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P, ctypes.POINTER(Diag)]
     lib.ara_run_layers.argtypes = [P, i32, ctypes.POINTER(Layer), u64, i64, i64, P]
     lib.ara_set_batch_config.argtypes = [P, i32, i32]
+    lib.ara_build_yet_index.argtypes = [P]
+    lib.ara_yet_index_info.argtypes = [P, P, P, P]
     lib.ara_run_layer_events.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P, ctypes.POINTER(EventRows)]
     lib.ara_submit.argtypes = [P, ctypes.POINTER(Layer), u64, i64, P, i32, P]
     lib.ara_serve_step.argtypes = [P, P]
@@ -295,6 +297,14 @@ def ara_serve_step(h, n_done_out):
 
 def ara_set_batch_config(h, item, blocks_per_sm):
     return load_library().ara_set_batch_config(h, item, blocks_per_sm)
+
+
+def ara_build_yet_index(h):
+    return load_library().ara_build_yet_index(h)
+
+
+def ara_yet_index_info(h, built, nbytes, build_ms):
+    return load_library().ara_yet_index_info(h, built, nbytes, build_ms)
 
 
 def ara_serve_stats(h, out):
@@ -508,6 +518,18 @@ class Ara:
         SM (0: as many as an SM holds); ARA_BATCH_AUTO returns to the autotuner's
         cached choice or the default rule."""
         self._check(ara_set_batch_config(self._h, int(item), int(blocks_per_sm)))
+
+    def build_yet_index(self) -> None:
+        """Build the loaded YET's event-major index (ara_build_yet_index)."""
+        self._check(ara_build_yet_index(self._h))
+
+    def yet_index_info(self) -> dict:
+        """Whether the YET's index is built, its bytes and its build's device time."""
+        built = np.zeros(1, np.int32)
+        nbytes = np.zeros(1, np.int64)
+        ms = np.zeros(1, np.float32)
+        self._check(ara_yet_index_info(self._h, built.ctypes.data, nbytes.ctypes.data, ms.ctypes.data))
+        return {"built": bool(built[0]), "bytes": int(nbytes[0]), "build_ms": float(ms[0])}
 
     def submit(self, elt_ids, layer_terms, seed: int, trial_end: int, return_periods,
                primary_only: bool = False, shared_z: bool = False) -> int:

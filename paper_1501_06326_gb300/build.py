@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libara.so")
-SOURCES = ["ara_abi.cu", "ara_batch.cu", "ara_events.cu", "ara_kernels.cu", "ara_layer.cu", "ara_select.cu"]
+SOURCES = ["ara_abi.cu", "ara_batch.cu", "ara_events.cu", "ara_index.cu", "ara_kernels.cu", "ara_layer.cu",
+           "ara_select.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -90,6 +90,11 @@ struct ara_ctx {
   // per-layer index (grown on demand)
   DevBuf bits, word_cnt, word_pairs, rankdir, mask, slot_cnt, pairs, pairs_hot, pairs_w, pairs_ev, scan_tmp;
   DevBuf ev_buf, tile_cnt;  // hit-event records of the layer kernels
+  // event-major index of the YET (ara_build_yet_index) and the indexed passes' buffers
+  DevBuf yix_occ, yix_off;
+  bool yix_ready = false;
+  float yix_build_ms = 0.0f;
+  DevBuf u_flags, u_scan, u_event, u_first, idx_acc;
   DevBuf def_acc;           // per-trial FP64 sums of deferred occurrence losses
   DevBuf elt_stage, elt_recs_stage, elt_tab_stage, elt_flags;  // ELT load staging (grow-only)
   DevBuf elt_tabf_stage, elt_work;
@@ -341,6 +346,9 @@ int yet_begin(ara_ctx* c, int64_t n_trials, const int64_t* offsets, const int32_
     ARA_CUDA(c, cudaEventSynchronize(c->yet_ready));
   }
   c->yet_loaded = false;
+  c->yix_ready = false;  // the index belongs to the YET being replaced
+  release(c, c->yix_occ);
+  release(c, c->yix_off);
   if (!c->copy_stream) {
     ARA_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
     ARA_CUDA(c, cudaEventCreateWithFlags(&c->yet_ready, cudaEventDisableTiming));
@@ -737,10 +745,9 @@ static int plan_pass(ara_ctx* c, const std::vector<int32_t>& ids, int64_t t0, in
 }
 
 // Index build and gather on the context stream (with their timing events).
-static int launch_index_and_gather(ara_ctx* c, const PassPlan& pl, const char* who, int* launched) {
-  cudaEvent_t ia, ib, ka, kb;
-  if (!timed_pair(c, 1, &ia, &ib) || !timed_pair(c, 0, &ka, &kb))
-    return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
+static int launch_index(ara_ctx* c, const PassPlan& pl, const char* who, int* launched) {
+  cudaEvent_t ia, ib;
+  if (!timed_pair(c, 1, &ia, &ib)) return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
   ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 8 * sizeof(unsigned long long), c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
   ARA_CUDA(c, record_ev(ia, c->stream));
@@ -748,6 +755,14 @@ static int launch_index_and_gather(ara_ctx* c, const PassPlan& pl, const char* w
   ARA_CUDA(c, record_ev(ib, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[2], c->stream));
+  return ARA_OK;
+}
+
+static int launch_index_and_gather(ara_ctx* c, const PassPlan& pl, const char* who, int* launched) {
+  int rc = launch_index(c, pl, who, launched);
+  if (rc) return rc;
+  cudaEvent_t ka, kb;
+  if (!timed_pair(c, 0, &ka, &kb)) return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
   ARA_CUDA(c, record_ev(ka, c->stream));
   ARA_CUDA(c, ara::launch_gather(pl.g, pl.grid, pl.smem, c->stream));
   ARA_CUDA(c, record_ev(kb, c->stream));
@@ -1054,12 +1069,21 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
                                       static_cast<int64_t>(std::lround(4.0 * std::log2(recs_per_trial + 1.0)))};
   const int dense_max = ara::losses_dense_blocks_per_sm(n_layers);
   if (dense_max < 1) return fail(c, ARA_ECUDA, "%s: the dense losses kernel fits no SM", who);
-  auto max_blocks = [&](int it) { return it == ara::kItemDense ? dense_max : ara::kBatchBlocksPerSm; };
-  int item = ara::kItemDense, blocks = dense_max;
-  const auto cached = c->tune_cache.find(shape);
+  const int idx_max = c->yix_ready ? ara::losses_indexed_blocks_per_sm() : 0;
+  if (c->yix_ready && idx_max < 1) return fail(c, ARA_ECUDA, "%s: the indexed losses kernel fits no SM", who);
+  auto max_blocks = [&](int it) {
+    return it == ara::kItemDense ? dense_max : it == ara::kItemIndexed ? idx_max : ara::kBatchBlocksPerSm;
+  };
+  // with the YET's event-major index built, the default is the indexed item (no gather)
+  int item = c->yix_ready ? ara::kItemIndexed : ara::kItemDense, blocks = max_blocks(item);
+  std::vector<int64_t> tshape = shape;
+  tshape.push_back(c->yix_ready ? 1 : 0);
+  const auto cached = c->tune_cache.find(tshape);
   const bool forced = c->force_item != ARA_BATCH_AUTO;
   const bool tune = !forced && cached == c->tune_cache.end() && (layers[0].flags & ARA_AUTOTUNE);
   if (forced) {
+    if (c->force_item == ara::kItemIndexed && !c->yix_ready)
+      return fail(c, ARA_EINVAL, "%s: the indexed work item needs ara_build_yet_index first", who);
     item = c->force_item;
     blocks = c->force_blocks > 0 ? std::min(c->force_blocks, max_blocks(item)) : max_blocks(item);
   } else if (cached != c->tune_cache.end()) {
@@ -1068,43 +1092,86 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
   }
   const int64_t warps = ara::kBatchThreads / 32;
   auto grid_of = [&](int it, int b) {
-    const int64_t items = it == ara::kItemTrial ? pl.n_tiles * ara::kWarpTrials : pl.n_tiles;
+    const int64_t items = it == ara::kItemTrial     ? pl.n_tiles * ara::kWarpTrials
+                          : it == ara::kItemIndexed ? pl.ix.n_recs
+                                                    : pl.n_tiles;
     return static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(c->num_sms) * b,
                                                                    (items + warps - 1) / warps)));
   };
+  // the indexed pass: the union's distinct events, and per-layer fixed-point sums
+  ara::IndexedParams q{};
+  const bool use_index = item == ara::kItemIndexed || (tune && c->yix_ready);
+  if (use_index) {
+    const int64_t n_recs = pl.ix.n_recs;
+    if ((rc = reserve(c, c->u_flags, sizeof(uint32_t) * (n_recs + 1))) ||
+        (rc = reserve(c, c->u_scan, sizeof(uint32_t) * (n_recs + 1))) ||
+        (rc = reserve(c, c->u_event, sizeof(int32_t) * (n_recs + 1))) ||
+        (rc = reserve(c, c->u_first, sizeof(uint32_t) * (n_recs + 1))) ||
+        (rc = reserve(c, c->idx_acc, sizeof(unsigned long long) * n_layers * n_out)))
+      return rc;
+    q.b = p;
+    q.occ = static_cast<const unsigned long long*>(c->yix_occ.ptr);
+    q.ev_off = static_cast<const uint32_t*>(c->yix_off.ptr);
+    q.u_event = static_cast<const int32_t*>(c->u_event.ptr);
+    q.u_first = static_cast<const uint32_t*>(c->u_first.ptr);
+    q.n_u = static_cast<const uint32_t*>(c->u_scan.ptr) + n_recs;
+    q.acc = static_cast<unsigned long long*>(c->idx_acc.ptr);
+  }
+  const size_t acc_bytes = sizeof(unsigned long long) * n_layers * n_out;
+  auto launch_item = [&](int it, int b) -> cudaError_t {
+    if (it != ara::kItemIndexed) return ara::launch_losses_batch(p, it, grid_of(it, b), c->stream);
+    cudaError_t e = cudaMemsetAsync(q.acc, 0, acc_bytes, c->stream);
+    if (e == cudaSuccess) e = ara::launch_losses_indexed(q, grid_of(it, b), c->stream);
+    if (e == cudaSuccess) e = ara::launch_indexed_years(q, c->stream);
+    return e;
+  };
   int launched = 0;
-  if ((rc = launch_index_and_gather(c, pl, who, &launched))) return rc;
+  if (item == ara::kItemIndexed && !tune) {
+    if ((rc = launch_index(c, pl, who, &launched))) return rc;
+  } else if ((rc = launch_index_and_gather(c, pl, who, &launched))) {
+    return rc;
+  }
+  if (use_index) {
+    cudaEvent_t ua, ub;  // the union's events stand where the gather stands in a pass's timing
+    if (!timed_pair(c, 0, &ua, &ub)) return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
+    ARA_CUDA(c, record_ev(ua, c->stream));
+    ARA_CUDA(c, ara::launch_union_events(pl.ix.pev, pl.ix.n_recs, static_cast<uint32_t*>(c->u_flags.ptr),
+                                         static_cast<uint32_t*>(c->u_scan.ptr), pl.ix.scan_tmp,
+                                         static_cast<int32_t*>(c->u_event.ptr), static_cast<uint32_t*>(c->u_first.ptr),
+                                         c->stream, &launched));
+    ARA_CUDA(c, record_ev(ub, c->stream));
+  }
   if (tune) {
     // every candidate once on this pass's records, timed on the stream; the fastest is kept
     float best = 0.0f;
     for (auto& e : c->tune_ev)
       if (!e) ARA_CUDA(c, cudaEventCreate(&e));
-    for (int it : {ara::kItemTile, ara::kItemTrial, ara::kItemDense})
+    for (int it : {ara::kItemTile, ara::kItemTrial, ara::kItemDense, ara::kItemIndexed})
       for (int b = 2; b <= max_blocks(it); ++b) {
         ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 4 * sizeof(unsigned long long), c->stream));
         ARA_CUDA(c, cudaEventRecord(c->tune_ev[0], c->stream));
-        ARA_CUDA(c, ara::launch_losses_batch(p, it, grid_of(it, b), c->stream));
+        ARA_CUDA(c, launch_item(it, b));
         ARA_CUDA(c, cudaEventRecord(c->tune_ev[1], c->stream));
         ARA_CUDA(c, cudaEventSynchronize(c->tune_ev[1]));
         float ms = 0.0f;
         ARA_CUDA(c, cudaEventElapsedTime(&ms, c->tune_ev[0], c->tune_ev[1]));
-        launched += 1;
+        launched += it == ara::kItemIndexed ? 2 : 1;
         if (best == 0.0f || ms < best) {
           best = ms;
           item = it;
           blocks = b;
         }
       }
-    c->tune_cache[shape] = {item, blocks};
+    c->tune_cache[tshape] = {item, blocks};
     ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 4 * sizeof(unsigned long long), c->stream));
   }
   cudaEvent_t la, lb;
   if (!timed_pair(c, 3, &la, &lb)) return fail(c, ARA_ECUDA, "%s: cannot create timing events", who);
   ARA_CUDA(c, record_ev(la, c->stream));
-  ARA_CUDA(c, ara::launch_losses_batch(p, item, grid_of(item, blocks), c->stream));
+  ARA_CUDA(c, launch_item(item, blocks));
   ARA_CUDA(c, record_ev(lb, c->stream));
   ARA_CUDA(c, cudaEventRecord(c->ev[3], c->stream));
-  launched += 1;
+  launched += item == ara::kItemIndexed ? 2 : 1;
   c->last_item = item;
   c->last_blocks = blocks;
   c->last_tuned = !forced && (cached != c->tune_cache.end() || tune) ? 1 : 0;
@@ -1133,14 +1200,72 @@ int ara_run_layers(ara_ctx* c, int32_t n_layers, const ara_layer* layers, uint64
 }
 
 static_assert(ARA_BATCH_ITEM_TILE == ara::kItemTile && ARA_BATCH_ITEM_TRIAL == ara::kItemTrial &&
-                  ARA_BATCH_ITEM_DENSE == ara::kItemDense,
+                  ARA_BATCH_ITEM_DENSE == ara::kItemDense && ARA_BATCH_ITEM_INDEXED == ara::kItemIndexed,
               "work items of the ABI and the kernels");
+
+int ara_build_yet_index(ara_ctx* c) {
+  static const char* who = "ara_build_yet_index";
+  int rc = bind(c);
+  if (rc) return rc;
+  if ((rc = yet_finish(c))) return rc;
+  if (!c->yet_loaded) return fail(c, ARA_ENOTLOADED, "%s: no YET loaded", who);
+  if (c->yix_ready) return ARA_OK;
+  if (!c->serve_queue.empty() || !c->serve_active.empty() || !c->serve_rounds.empty())
+    return fail(c, ARA_EINVAL, "%s: served requests are queued or running", who);
+  if (c->n_events >= (int64_t(1) << 32) - 1)
+    return fail(c, ARA_EINVAL, "%s: the YET holds 2^32 or more events", who);
+  const int64_t n = c->n_events;
+  DevBuf scratch;
+  if ((rc = reserve(c, c->yix_occ, sizeof(unsigned long long) * (n + 1))) ||
+      (rc = reserve(c, c->yix_off, sizeof(uint32_t) * (static_cast<size_t>(c->catalogue) + 2))) ||
+      (rc = reserve(c, scratch, ara::yet_index_scratch_bytes(n)))) {
+    release(c, scratch);
+    release(c, c->yix_occ);
+    release(c, c->yix_off);
+    return rc;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
+  int launched = 0;
+  if (e == cudaSuccess)
+    e = ara::build_yet_index(static_cast<const int64_t*>(c->yet_off.ptr), static_cast<const int32_t*>(c->yet_ids.ptr),
+                             c->n_trials, n, c->catalogue, static_cast<unsigned long long*>(c->yix_occ.ptr),
+                             static_cast<uint32_t*>(c->yix_off.ptr), scratch.ptr, c->stream, &launched);
+  if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  release(c, scratch);
+  c->launches += launched;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release(c, c->yix_occ);
+    release(c, c->yix_off);
+    return fail(c, ARA_ECUDA, "%s: %s", who, cudaGetErrorString(e));
+  }
+  c->yix_ready = true;
+  c->yix_build_ms = ms;
+  c->serve_ready = false;  // the serving arena is sized again around the index
+  return ARA_OK;
+}
+
+int ara_yet_index_info(const ara_ctx* c, int32_t* built, int64_t* bytes, float* build_ms) {
+  if (!c) return ARA_EINVAL;
+  if (built) *built = c->yix_ready ? 1 : 0;
+  if (bytes) *bytes = c->yix_ready ? static_cast<int64_t>(c->yix_occ.bytes + c->yix_off.bytes) : 0;
+  if (build_ms) *build_ms = c->yix_ready ? c->yix_build_ms : 0.0f;
+  return ARA_OK;
+}
 
 int ara_set_batch_config(ara_ctx* c, int32_t item, int32_t blocks_per_sm) {
   int rc = bind(c);
   if (rc) return rc;
   if (item != ARA_BATCH_AUTO && item != ARA_BATCH_ITEM_TILE && item != ARA_BATCH_ITEM_TRIAL &&
-      item != ARA_BATCH_ITEM_DENSE)
+      item != ARA_BATCH_ITEM_DENSE && item != ARA_BATCH_ITEM_INDEXED)
     return fail(c, ARA_EINVAL, "ara_set_batch_config: unknown work item %d", item);
   if (blocks_per_sm < 0 || blocks_per_sm > 16)
     return fail(c, ARA_EINVAL, "ara_set_batch_config: blocks_per_sm %d outside 0..16", blocks_per_sm);
@@ -1316,6 +1441,11 @@ std::vector<std::pair<DevBuf*, size_t>> serve_workspace(ara_ctx* c) {
       {&c->pairs_ev, sizeof(int32_t) * (n_recs + 1)},
       {&c->scan_tmp, sizeof(uint32_t) * (tmp_words + 8)},
       {&c->serve_sel, ara::select_scratch_bytes(c->n_trials)},
+      {&c->u_flags, sizeof(uint32_t) * (n_recs + 1)},
+      {&c->u_scan, sizeof(uint32_t) * (n_recs + 1)},
+      {&c->u_event, sizeof(int32_t) * (n_recs + 1)},
+      {&c->u_first, sizeof(uint32_t) * (n_recs + 1)},
+      {&c->idx_acc, sizeof(unsigned long long) * ARA_MAX_BATCH_LAYERS * static_cast<size_t>(kServeChunk)},
       {&c->serve_out, 2 * sizeof(double) * ARA_SERVE_MAX_RP * kServeSlots},
   };
   if (any_corr) w.push_back({&c->pairs_w, sizeof(float2) * (n_recs + 1)});
@@ -1912,7 +2042,8 @@ void ara_destroy(ara_ctx* c) {
                     &c->yet_ids,    &c->bits,           &c->word_cnt,      &c->word_pairs,     &c->rankdir,
                     &c->mask,       &c->slot_cnt,       &c->pairs,         &c->pairs_hot,     &c->pairs_w,          &c->pairs_ev,         &c->scan_tmp,       &c->flags,
                     &c->counters,   &c->ylt_tmp,        &c->diag_tmp,      &c->sel,            &c->in_tmp,
-                    &c->out_tmp,    &c->serve_arena,    &c->serve_out,      &c->serve_sel,      &c->ev_occ,        &c->row_base,
+                    &c->out_tmp,    &c->serve_arena,    &c->serve_out,      &c->yix_occ,        &c->yix_off,       &c->u_flags,
+                    &c->u_scan,        &c->u_event,        &c->u_first,        &c->idx_acc,      &c->serve_sel,      &c->ev_occ,        &c->row_base,
                     &c->evr_stage,  &c->yet_flags};
   for (DevBuf* b : bufs) release(c, *b);
   for (auto& e : c->ev)

@@ -584,6 +584,30 @@ __device__ __noinline__ float2 dense_pair_slow(const BatchParams& p, uint32_t pi
   return make_float2(L, static_cast<float>(nc));
 }
 
+// The pass's per-ELT and per-layer constants in shared memory (the caller syncs).
+__device__ __forceinline__ void load_dense_shared(const BatchParams& p, DenseShared& ds) {
+  const int nl = p.n_layers;
+  for (int i = threadIdx.x; i < kMaxIndexElts; i += blockDim.x) {
+    const bool in = i < p.n_elts;
+    ds.tab[i] = in ? p.tab[i] : nullptr;
+    ds.tabf[i] = in ? p.tabf[i] : nullptr;
+    ds.elt_id[i] = in ? static_cast<uint32_t>(p.elt_id[i]) : 0u;
+    ds.ret[i] = in ? p.t_ret[i] : 0.0f;
+    ds.lim[i] = in ? p.t_lim[i] : 0.0f;
+    ds.share[i] = in ? p.t_share[i] : 0.0f;
+    ds.layers_of[i] = in ? static_cast<uint32_t>(p.layers_of[i]) : 0u;
+  }
+  for (int i = threadIdx.x; i < kBatchLayers; i += blockDim.x) {
+    const bool in = i < nl;
+    ds.occ[i] = make_float4(p.occ_r[i], p.occ_l[i], p.scale[i], 0.0f);
+    ds.agg_r[i] = p.agg_r[i];
+    ds.agg_l[i] = p.agg_l[i];
+    ds.inv_scale[i] = p.inv_scale[i];
+    ds.ylt[i] = in ? p.ylt_l[i] : nullptr;
+    ds.t_end[i] = in ? p.layer_t_end[i] : 0;
+  }
+}
+
 // Lane l receives column l of the 32 x 32 bit matrix whose row i is lane i's
 // x: bit i of the result is bit l of lane i's x (the off-diagonal blocks of
 // halves, quarters, ... exchanged between lanes).
@@ -618,25 +642,7 @@ __global__ void __launch_bounds__(kBatchThreads, kDenseBlocksPerSm)
   const uint32_t lane = lane_id();
   DenseWarp& ws = dwarp[threadIdx.x >> 5];
   const int nl = p.n_layers;
-  for (int i = threadIdx.x; i < kMaxIndexElts; i += blockDim.x) {
-    const bool in = i < p.n_elts;
-    ds.tab[i] = in ? p.tab[i] : nullptr;
-    ds.tabf[i] = in ? p.tabf[i] : nullptr;
-    ds.elt_id[i] = in ? static_cast<uint32_t>(p.elt_id[i]) : 0u;
-    ds.ret[i] = in ? p.t_ret[i] : 0.0f;
-    ds.lim[i] = in ? p.t_lim[i] : 0.0f;
-    ds.share[i] = in ? p.t_share[i] : 0.0f;
-    ds.layers_of[i] = in ? static_cast<uint32_t>(p.layers_of[i]) : 0u;
-  }
-  for (int i = threadIdx.x; i < kBatchLayers; i += blockDim.x) {
-    const bool in = i < nl;
-    ds.occ[i] = make_float4(p.occ_r[i], p.occ_l[i], p.scale[i], 0.0f);
-    ds.agg_r[i] = p.agg_r[i];
-    ds.agg_l[i] = p.agg_l[i];
-    ds.inv_scale[i] = p.inv_scale[i];
-    ds.ylt[i] = in ? p.ylt_l[i] : nullptr;
-    ds.t_end[i] = in ? p.layer_t_end[i] : 0;
-  }
+  load_dense_shared(p, ds);
   __syncthreads();
   static_assert(kBatchLayers <= 32, "one lane per layer; 32-bit layer masks");
   // the lane's layer l and record slot s; its records in a group: i = s mod S
@@ -905,5 +911,232 @@ cudaError_t launch_losses_batch(const BatchParams& p, int item, int grid, cudaSt
   }
   return cudaGetLastError();
 }
+
+
+// ------------------------------------------------------------------ indexed kernel
+// A warp per distinct event of the pass's ELT union (claimed from a queue),
+// over the event's occurrences in the pass's trials, 32 at a time (a lane
+// each), found by a warp search in the event-major YET index.  Every lane of
+// the warp works on the same event, so the pairs, their layers and their
+// tables are the same across the warp.  For each occurrence and each layer it
+// serves, the event's pair losses over the layer's ELTs are summed from left
+// to right (per-lane running sums in shared memory when the event has several
+// pairs), the occurrence terms applied, and the result added to the trial's
+// fixed-point sum with a 64-bit atomic add: the same numbers as the other
+// work items, so the same bits.  A second kernel turns the sums into year
+// losses.
+namespace {
+
+constexpr int kIdxThreads = 128;
+constexpr int kIdxBlocksPerSm = 7;
+
+struct IdxWarp {
+  float gacc[kBatchLayers][32];      // per layer and lane: the running sum of an occurrence's pair losses
+  uint32_t pmask[kMaxIndexElts];     // the event's pairs: layers holding their ELTs
+};
+
+// First entry in [lo, hi) of the event's occurrences whose trial is >= key
+// (hi if none), by the whole warp: each round probes 32 evenly spaced entries.
+__device__ __forceinline__ uint32_t first_occ_at(const unsigned long long* occ, uint32_t lo, uint32_t hi,
+                                                 int64_t key, uint32_t lane) {
+  while (lo < hi) {
+    const uint32_t step = (hi - lo + 31u) / 32u;
+    const uint32_t pos = lo + lane * step;
+    const bool ge = pos < hi && static_cast<int64_t>(__ldg(occ + pos) >> 32) >= key;
+    const uint32_t b = __ballot_sync(0xffffffffu, ge);
+    if (b == 0u) {
+      const uint32_t probes = (hi - lo + step - 1u) / step;
+      lo += (probes - 1u) * step + 1u;
+    } else {
+      const uint32_t f = static_cast<uint32_t>(__ffs(b) - 1);
+      hi = lo + f * step;
+      if (f > 0u) lo += (f - 1u) * step + 1u;
+    }
+  }
+  return lo;
+}
+
+// Loss after ELT terms of pair pi in occurrence (trial, k): as the other work items compute it.
+__device__ __forceinline__ float indexed_pair_loss(const BatchParams& p, const DenseShared& ds, uint32_t pi,
+                                                   int64_t trial, uint32_t k, unsigned long long* nc) {
+  const PairHot h = p.hot[pi];
+  const uint32_t kind = pair_kind(h.meta);
+  const uint32_t pos = pair_pos(h.meta);
+  float loss = h.mu;
+  if (kind == kKindZero) {
+    loss = 0.0f;
+  } else if (!p.primary_only && kind_is_beta(kind)) {
+    float t;
+    if (p.newton_only || !pair_tab_exact(h.meta) || !batch_pair_normal(p, kind, ds.elt_id[pos], pi, trial, k, &t))
+      return pair_loss_slow(p, p.pairs[pi], pi, trial, k, nc);
+    const bool fine = pair_fine(h.meta);
+    loss = h.max_l * tab_quantile_t((fine ? ds.tabf[pos] : ds.tab[pos]) + h.node, t, fine);
+  }
+  return ds.share[pos] * clamp_terms_f(loss, ds.ret[pos], ds.lim[pos]);
+}
+
+__global__ void k_event_flags(const int32_t* __restrict__ pev, int64_t n, uint32_t* flags) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride)
+    flags[i] = (i == 0 || pev[i] != pev[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_union_events(const int32_t* __restrict__ pev, const uint32_t* __restrict__ flags,
+                               const uint32_t* __restrict__ scan, int64_t n, int32_t* u_event, uint32_t* u_first) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+    if (flags[i]) {
+      u_event[scan[i]] = pev[i];
+      u_first[scan[i]] = static_cast<uint32_t>(i);
+    }
+    if (i == n - 1) u_first[scan[n]] = static_cast<uint32_t>(n);
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kIdxThreads, kIdxBlocksPerSm)
+    k_losses_indexed(const __grid_constant__ IndexedParams q) {
+  const BatchParams& p = q.b;
+  __shared__ IdxWarp iwarp[kIdxThreads / 32];
+  __shared__ DenseShared ds;
+  const uint32_t lane = lane_id();
+  IdxWarp& ws = iwarp[threadIdx.x >> 5];
+  load_dense_shared(p, ds);
+  __syncthreads();
+  const int nl = p.n_layers;
+  const int64_t t0 = p.t_begin, stride = p.t_end - p.t_begin;
+  int64_t t_full = p.t_end;  // below it every layer reaches the trial
+  for (int l = 0; l < nl; ++l) t_full = min(t_full, ds.t_end[l]);
+  const uint32_t all = nl >= 32 ? 0xffffffffu : (1u << nl) - 1u;
+  for (int l = 0; l < nl; ++l) ws.gacc[l][lane] = 0.0f;
+  const uint32_t n_u = *q.n_u;
+  unsigned long long nc = 0ull;
+  uint32_t n_pairs = 0;
+
+  unsigned long long next = 0ull;  // events are claimed one ahead
+  if (lane == 0) next = atomicAdd(&p.counters[0], 1ull);
+  for (;;) {
+    const unsigned long long u = __shfl_sync(0xffffffffu, next, 0);
+    if (u >= n_u) break;
+    if (lane == 0) next = atomicAdd(&p.counters[0], 1ull);
+    const int32_t e = q.u_event[u];
+    const uint32_t ps = q.u_first[u], cnt = q.u_first[u + 1] - ps;
+    const uint32_t lo = first_occ_at(q.occ, q.ev_off[e], q.ev_off[e + 1], t0, lane);
+    const uint32_t hi = first_occ_at(q.occ, lo, q.ev_off[e + 1], p.t_end, lane);
+    if (lo >= hi) continue;
+    for (uint32_t j = lane; j < cnt; j += 32) ws.pmask[j] = ds.layers_of[pair_pos(p.hot[ps + j].meta)];
+    __syncwarp();
+    for (uint32_t r = lo; r < hi; r += 32) {
+      const uint32_t i = r + lane;
+      const bool valid = i < hi;
+      const unsigned long long o = valid ? __ldg(q.occ + i) : 0ull;
+      const int64_t trial = static_cast<int64_t>(o >> 32);
+      const uint32_t k = static_cast<uint32_t>(o);
+      uint32_t act = 0u;  // the layers whose trials reach this one
+      if (valid) {
+        act = all;
+        if (trial >= t_full) {
+          act = 0u;
+          for (int l = 0; l < nl; ++l)
+            if (trial < ds.t_end[l]) act |= 1u << l;
+        }
+      }
+      unsigned long long* acc = q.acc + (trial - t0);
+      if (cnt == 1u) {
+        const uint32_t m = ws.pmask[0] & act;
+        if (m) {
+          const float L = indexed_pair_loss(p, ds, ps, trial, k, &nc);
+          ++n_pairs;
+          for (uint32_t mm = m; mm; mm &= mm - 1u) {
+            const int l = __ffs(mm) - 1;
+            const float4 c = ds.occ[l];
+            const float O = clamp_terms_f(L, c.x, c.y);
+            if (O > 0.0f) atomicAdd(acc + static_cast<int64_t>(l) * stride, fixed_units(O, c.z));
+          }
+        }
+      } else {
+        // the pairs in order: each layer's running sum is the left-to-right sum of its pairs' losses
+        uint32_t touched = 0u;
+        for (uint32_t j = 0; j < cnt; ++j) {
+          const uint32_t m = ws.pmask[j] & act;
+          if (m) {
+            const float L = indexed_pair_loss(p, ds, ps + j, trial, k, &nc);
+            ++n_pairs;
+            touched |= m;
+            for (uint32_t mm = m; mm; mm &= mm - 1u) ws.gacc[__ffs(mm) - 1][lane] += L;
+          }
+        }
+        for (uint32_t mm = touched; mm; mm &= mm - 1u) {
+          const int l = __ffs(mm) - 1;
+          const float G = ws.gacc[l][lane];
+          ws.gacc[l][lane] = 0.0f;
+          const float4 c = ds.occ[l];
+          const float O = clamp_terms_f(G, c.x, c.y);
+          if (O > 0.0f) atomicAdd(acc + static_cast<int64_t>(l) * stride, fixed_units(O, c.z));
+        }
+      }
+    }
+    __syncwarp();  // pmask is rewritten for the next event
+  }
+  n_pairs = __reduce_add_sync(0xffffffffu, n_pairs);
+  for (int d = 16; d > 0; d >>= 1) nc += __shfl_xor_sync(0xffffffffu, nc, d);
+  if (lane == 0) {
+    if (n_pairs) atomicAdd(&p.counters[1], static_cast<unsigned long long>(n_pairs));
+    if (nc) atomicAdd(&p.counters[2], nc);
+  }
+}
+
+namespace {
+
+__global__ void k_indexed_years(const __grid_constant__ IndexedParams q) {
+  const BatchParams& p = q.b;
+  const int64_t stride = p.t_end - p.t_begin;
+  const int64_t n = stride * p.n_layers;
+  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += step) {
+    const int l = static_cast<int>(i / stride);
+    const int64_t tt = i - static_cast<int64_t>(l) * stride;
+    if (p.t_begin + tt < p.layer_t_end[l])
+      p.ylt_l[l][tt] = clamp_terms_d(__ull2double_rn(q.acc[i]) * p.inv_scale[l], p.agg_r[l], p.agg_l[l]);
+  }
+}
+
+int grid_for_n(int64_t n, int threads) {
+  const int64_t b = (n + threads - 1) / threads;
+  return static_cast<int>(b < 1 ? 1 : (b > 65535 ? 65535 : b));
+}
+
+}  // namespace
+
+cudaError_t launch_union_events(const int32_t* pev, int64_t n_recs, uint32_t* flags, uint32_t* scan,
+                                uint32_t* scan_tmp, int32_t* u_event, uint32_t* u_first, cudaStream_t s,
+                                int* n_launch) {
+  if (n_recs == 0) return cudaMemsetAsync(scan, 0, sizeof(uint32_t), s);
+  k_event_flags<<<grid_for_n(n_recs, 256), 256, 0, s>>>(pev, n_recs, flags);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  if ((err = scan_exclusive_u32(flags, scan, n_recs, scan_tmp, s, n_launch)) != cudaSuccess) return err;
+  k_union_events<<<grid_for_n(n_recs, 256), 256, 0, s>>>(pev, flags, scan, n_recs, u_event, u_first);
+  if (n_launch) *n_launch += 2;
+  return cudaGetLastError();
+}
+
+int losses_indexed_blocks_per_sm() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_losses_indexed, kIdxThreads, 0) != cudaSuccess) return 0;
+  return b;
+}
+
+cudaError_t launch_losses_indexed(const IndexedParams& q, int grid, cudaStream_t s) {
+  k_losses_indexed<<<grid, kIdxThreads, 0, s>>>(q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_indexed_years(const IndexedParams& q, cudaStream_t s) {
+  k_indexed_years<<<grid_for_n((q.b.t_end - q.b.t_begin) * q.b.n_layers, 256), 256, 0, s>>>(q);
+  return cudaGetLastError();
+}
+
 
 }  // namespace ara

@@ -1,0 +1,79 @@
+// Event-major index of a resident YET: for each catalogue event, its
+// occurrences (trial, event index in the trial), in trial order.  Built once
+// per YET (ara_build_yet_index); batched passes then reach a layer's hit
+// events through its ELTs' events instead of streaming every trial's events
+// (Section 2.1's lookup, taken from the ELT side).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ara_internal.h"
+
+namespace ara {
+
+namespace {
+
+// key = event id, value = (trial << 32) | event index: one warp per trial
+__global__ void k_yet_pairs(const int64_t* __restrict__ off, const int32_t* __restrict__ ids, int64_t n_trials,
+                            unsigned long long* keys, int64_t* vals) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x / 32);
+  for (int64_t t = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + (threadIdx.x >> 5); t < n_trials;
+       t += warps) {
+    const int64_t a = off[t], b = off[t + 1];
+    for (int64_t i = a + lane; i < b; i += 32) {
+      keys[i] = static_cast<unsigned long long>(static_cast<uint32_t>(ids[i]));
+      vals[i] = (t << 32) | (i - a);
+    }
+  }
+}
+
+__global__ void k_fill_u32(uint32_t* a, int64_t n, uint32_t v) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) a[i] = v;
+}
+
+// ev_off[e] = the first sorted position of event e (an event without
+// occurrences takes the next event's start; events past the last key keep n)
+__global__ void k_event_starts(const unsigned long long* __restrict__ keys, int64_t n, uint32_t* ev_off) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n; i += stride) {
+    const int64_t cur = static_cast<int64_t>(keys[i]);
+    const int64_t prev = i > 0 ? static_cast<int64_t>(keys[i - 1]) : -1;
+    for (int64_t e = prev + 1; e <= cur; ++e) ev_off[e] = static_cast<uint32_t>(i);
+  }
+}
+
+int grid_of(int64_t n, int threads) {
+  const int64_t b = (n + threads - 1) / threads;
+  return static_cast<int>(b < 1 ? 1 : (b > 65535 ? 65535 : b));
+}
+
+}  // namespace
+
+size_t yet_index_scratch_bytes(int64_t n_events) {
+  return sizeof(unsigned long long) * static_cast<size_t>(n_events) + sort_pairs_scratch_bytes(n_events) + 256;
+}
+
+cudaError_t build_yet_index(const int64_t* off, const int32_t* ids, int64_t n_trials, int64_t n_events,
+                            int32_t catalogue, unsigned long long* occ, uint32_t* ev_off, void* scratch,
+                            cudaStream_t s, int* n_launch) {
+  unsigned long long* keys = static_cast<unsigned long long*>(scratch);
+  void* sort_scratch = keys + n_events;
+  k_fill_u32<<<grid_of(static_cast<int64_t>(catalogue) + 1, 256), 256, 0, s>>>(ev_off, static_cast<int64_t>(catalogue) + 1,
+                                                                              static_cast<uint32_t>(n_events));
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess || n_events == 0) return err;
+  k_yet_pairs<<<grid_of(n_trials * 32, 256), 256, 0, s>>>(off, ids, n_trials, keys, reinterpret_cast<int64_t*>(occ));
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  int key_bits = 1;
+  while (key_bits < 31 && (1ll << key_bits) < static_cast<int64_t>(catalogue)) ++key_bits;
+  if ((err = sort_pairs_ascending(keys, reinterpret_cast<int64_t*>(occ), n_events, key_bits, sort_scratch, s,
+                                  n_launch)) != cudaSuccess)
+    return err;
+  k_event_starts<<<grid_of(n_events, 256), 256, 0, s>>>(keys, n_events, ev_off);
+  if (n_launch) *n_launch += 3;
+  return cudaGetLastError();
+}
+
+}  // namespace ara

@@ -16,6 +16,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <utility>
 
 #include "../../include/ara.h"
 #include "ara_internal.h"
@@ -656,6 +657,53 @@ cudaError_t sort_desc_device(const double* ylt, int64_t n, int64_t* order, void*
     io = ti;
   }
   return cudaSuccess;  // 8 swaps: the result is back in idx_a == order
+}
+
+size_t sort_pairs_scratch_bytes(int64_t n) {
+  const int64_t tiles = (n + kSortThreads - 1) / kSortThreads;
+  const int64_t cnt = 256 * tiles;
+  return static_cast<size_t>(n) * (sizeof(unsigned long long) + sizeof(int64_t)) +
+         sizeof(unsigned int) * (2 * static_cast<size_t>(cnt) + 1 + scan_tmp_words(cnt)) + 256;
+}
+
+cudaError_t sort_pairs_ascending(unsigned long long* keys, int64_t* vals, int64_t n, int key_bits, void* scratch,
+                                 cudaStream_t s, int* n_launch) {
+  const int64_t tiles = (n + kSortThreads - 1) / kSortThreads;
+  const int64_t cnt = 256 * tiles;
+  const int passes = (key_bits + 7) / 8;
+  unsigned char* base = static_cast<unsigned char*>(scratch);
+  unsigned long long* keys_b = reinterpret_cast<unsigned long long*>(base);
+  int64_t* vals_b = reinterpret_cast<int64_t*>(keys_b + n);
+  unsigned int* counts = reinterpret_cast<unsigned int*>(vals_b + n);
+  unsigned int* offsets = counts + cnt;
+  unsigned int* tmp = offsets + cnt + 1;
+  cudaError_t err = cudaSuccess;
+  // an odd number of passes ends in the scratch buffers: the data start there, so the result
+  // lands in (keys, vals)
+  unsigned long long *ki = keys, *ko = keys_b;
+  int64_t *ii = vals, *io = vals_b;
+  if (passes & 1) {
+    if ((err = cudaMemcpyAsync(keys_b, keys, sizeof(unsigned long long) * n, cudaMemcpyDeviceToDevice, s)) ||
+        (err = cudaMemcpyAsync(vals_b, vals, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s)))
+      return err;
+    ki = keys_b;
+    ko = keys;
+    ii = vals_b;
+    io = vals;
+  }
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = 8 * pass;
+    k_sort_count<<<static_cast<int>(tiles), kSortThreads, 0, s>>>(ki, n, shift, counts, static_cast<int>(tiles));
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if ((err = scan_exclusive_u32(counts, offsets, cnt, tmp, s, n_launch)) != cudaSuccess) return err;
+    k_sort_scatter<<<static_cast<int>(tiles), kSortThreads, 0, s>>>(ki, ii, n, shift, offsets,
+                                                                   static_cast<int>(tiles), ko, io);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    std::swap(ki, ko);
+    std::swap(ii, io);
+  }
+  if (n_launch) *n_launch += 2 * passes;
+  return cudaSuccess;
 }
 
 namespace {

@@ -47,9 +47,11 @@ def _batch_case(n_trials, catalogue, mean_events, n_elts, entries, n_layers, max
     return yet, pool, layers
 
 
-def _run_batch(eng, yet, pool, layers, seed, t0=0, t1=None, **kw):
+def _run_batch(eng, yet, pool, layers, seed, t0=0, t1=None, index=False, **kw):
     t1 = yet.n_trials if t1 is None else t1
     eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
+    if index:
+        eng.build_yet_index()
     eng.load_pool(pool)
     out = np.zeros((len(layers), t1 - t0))
     eng.run_layers([(ids, terms) for ids, terms, _ in layers], seed, t0, t1, out, **kw)
@@ -225,15 +227,18 @@ def test_autotuner_keeps_the_results_and_caches_its_choice(eng, small_batch):
 
 
 def _run_items(eng, yet, pool, layers, seed, t0=0, t1=None, blocks=(0,), **kw):
-    """The pass under each work item (and CTAs per SM) pinned by ara_set_batch_config."""
+    """The pass under each work item (and CTAs per SM) pinned by ara_set_batch_config;
+    the indexed item after the YET's event-major index is built."""
     from paper_1501_06326_gb300 import ara
 
     outs = {}
     try:
-        for item in (ara.ARA_BATCH_ITEM_TILE, ara.ARA_BATCH_ITEM_TRIAL, ara.ARA_BATCH_ITEM_DENSE):
+        for item in (ara.ARA_BATCH_ITEM_TILE, ara.ARA_BATCH_ITEM_TRIAL, ara.ARA_BATCH_ITEM_DENSE,
+                     ara.ARA_BATCH_ITEM_INDEXED):
             for b in blocks:
                 eng.set_batch_config(item, b)
-                outs[(item, b)] = _run_batch(eng, yet, pool, layers, seed, t0, t1, **kw)
+                outs[(item, b)] = _run_batch(eng, yet, pool, layers, seed, t0, t1,
+                                             index=item == ara.ARA_BATCH_ITEM_INDEXED, **kw)
                 st = eng.stats()
                 assert st["batch_item"] == item and st["batch_tuned"] == 0
                 assert b == 0 or st["batch_blocks_per_sm"] == b
@@ -320,8 +325,38 @@ def test_work_items_on_empty_and_long_trials(eng):
 def test_batch_config_errors(eng):
     from paper_1501_06326_gb300 import ara
 
-    for item, blocks in ((3, 0), (-2, 0), (ara.ARA_BATCH_ITEM_DENSE, -1), (ara.ARA_BATCH_ITEM_TILE, 17)):
+    for item, blocks in ((4, 0), (-2, 0), (ara.ARA_BATCH_ITEM_DENSE, -1), (ara.ARA_BATCH_ITEM_TILE, 17)):
         with pytest.raises(ara.AraError) as e:
             eng.set_batch_config(item, blocks)
         assert e.value.code == ara.ARA_EINVAL
     eng.set_batch_config(ara.ARA_BATCH_AUTO)
+
+
+def test_yet_index_default_and_errors(eng, small_batch):
+    """Without an index the indexed item is refused; once built, batched passes
+    default to it and give the same bits as the dense item; a new YET load drops
+    the index; building needs a YET."""
+    from paper_1501_06326_gb300 import ara
+
+    yet, pool, layers = small_batch
+    fresh = ara.Ara(0)
+    with pytest.raises(ara.AraError) as e:
+        fresh.build_yet_index()
+    assert e.value.code == ara.ARA_ENOTLOADED
+    fresh.close()
+    dense = _run_batch(eng, yet, pool, layers, 8)
+    assert eng.stats()["batch_item"] == ara.ARA_BATCH_ITEM_DENSE
+    eng.set_batch_config(ara.ARA_BATCH_ITEM_INDEXED)
+    try:
+        with pytest.raises(ara.AraError) as e:
+            _run_batch(eng, yet, pool, layers, 8)
+        assert e.value.code == ara.ARA_EINVAL
+    finally:
+        eng.set_batch_config(ara.ARA_BATCH_AUTO)
+    indexed = _run_batch(eng, yet, pool, layers, 8, index=True)
+    assert eng.stats()["batch_item"] == ara.ARA_BATCH_ITEM_INDEXED
+    info = eng.yet_index_info()
+    assert info["built"] and info["bytes"] >= 8 * yet.n_events
+    assert np.array_equal(dense, indexed)
+    eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
+    assert not eng.yet_index_info()["built"]

@@ -257,3 +257,29 @@ def test_direct_selects_while_rounds_are_in_flight(eng, world):
                     done[tk] = r
     for a, tk in zip(alone, tickets):
         assert np.array_equal(a[0], done[tk][0]) and np.array_equal(a[1], done[tk][1])
+
+
+def test_served_through_the_yet_index(world):
+    """Serving with the YET's event-major index built (the passes take the
+    indexed work item) gives each request the bits it gets without it; the
+    index cannot be built while requests are queued."""
+    from paper_1501_06326_gb300 import ara
+
+    yet, pool, reqs = world
+    plain = ara.Ara(0)
+    _load(plain, yet, pool)
+    want = _serve_all(plain, reqs, seed=31)
+    plain.close()
+    e = ara.Ara(0)
+    _load(e, yet, pool)
+    tk = e.submit(reqs[0][0], reqs[0][1], 31, reqs[0][2], RPS)
+    with pytest.raises(ara.AraError) as err:
+        e.build_yet_index()
+    assert err.value.code == ara.ARA_EINVAL
+    e.wait(tk, len(RPS))
+    e.build_yet_index()
+    got = _serve_all(e, reqs, seed=31)
+    assert e.stats()["batch_item"] == ara.ARA_BATCH_ITEM_INDEXED
+    for a, b in zip(want, got):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    e.close()
