@@ -595,14 +595,25 @@ def _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args)
     from paper_1501_06326_gb300 import ara
 
     steps = max(2, min(args.steps, 5))
-    # each work item pinned (all CTAs an SM holds), then the default rule, then the autotuner
-    items = {"tile": ara.ARA_BATCH_ITEM_TILE, "trial": ara.ARA_BATCH_ITEM_TRIAL, "dense": ara.ARA_BATCH_ITEM_DENSE}
+    # each work item pinned (all CTAs an SM holds), then the default rule, without the YET's
+    # event-major index and with it (built once, its device time reported), then the autotuner
+    items = {"tile": ara.ARA_BATCH_ITEM_TILE, "trial": ara.ARA_BATCH_ITEM_TRIAL, "dense": ara.ARA_BATCH_ITEM_DENSE,
+             "indexed": ara.ARA_BATCH_ITEM_INDEXED}
     names = {v: k for k, v in items.items()}
     ms_items = {}
     try:
         for name, item in items.items():
+            if item == ara.ARA_BATCH_ITEM_INDEXED:
+                continue
             eng.set_batch_config(item, 0)
             ms_items[name] = timed(batch_step, steps)
+        eng.set_batch_config(ara.ARA_BATCH_AUTO)
+        ms_no_index = timed(batch_step, steps)
+        st_no_index = eng.stats()
+        eng.build_yet_index()
+        index = eng.yet_index_info()
+        eng.set_batch_config(ara.ARA_BATCH_ITEM_INDEXED, 0)
+        ms_items["indexed"] = timed(batch_step, steps)
     finally:
         eng.set_batch_config(ara.ARA_BATCH_AUTO)
     ms_default = timed(batch_step, steps)
@@ -618,6 +629,10 @@ def _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args)
             "layers_per_s": len(layers) / (ms_batch * 1e-3), "plain_layers_per_s": len(layers) / (ms_plain * 1e-3),
             "speedup": ms_plain / ms_batch, "evals_per_s": evals / (ms_batch * 1e-3),
             "ms_batched_by_item": ms_items,
+            "without_yet_index": {"item": names[st_no_index["batch_item"]], "ms_batched": ms_no_index,
+                                  "speedup": ms_plain / ms_no_index},
+            "yet_index": {"bytes": index["bytes"], "build_ms": index["build_ms"],
+                          "note": "built once per YET (ara_build_yet_index); ara_run_layer (ms_plain) streams the YET"},
             "autotuned": {"item": names[st["batch_item"]], "blocks_per_sm": st["batch_blocks_per_sm"],
                           "tuned": bool(st["batch_tuned"])},
             "default_rule": {"item": names[st_default["batch_item"]],
@@ -698,6 +713,8 @@ def _serving_leg(eng, synth, offsets, args):
     pool = synth.make_elt_pool(spec["n_elts"], spec["entries"], spec["catalogue"], spec["elt_seed"],
                                recipe=spec["recipe"])
     eng.load_pool(pool)
+    eng.build_yet_index()  # (no-op when the batched leg built it on this YET)
+    index = eng.yet_index_info()
     with open(os.path.join(ROOT, "tests", "golden", "serving_terms.json")) as fh:
         st = json.load(fh)
     reqs = synth.serving_requests(spec, args.serve_requests, spec["request_seed"])
@@ -743,6 +760,8 @@ def _serving_leg(eng, synth, offsets, args):
                         f"{len(reqs)} requests per rate of |J| ~ U{{1..15}} over trial prefixes log-uniform in "
                         "[1e4, 1e6], RP 100/250, percentile terms per request (tests/golden/serving_terms.json)",
             "time": "real: Poisson arrivals in wall time; latency = arrival to the poll that returns the result",
+            "passes": "batched passes through the YET's event-major index (built once per YET, before the sweep)",
+            "yet_index": {"bytes": index["bytes"], "build_ms": index["build_ms"]},
             "chunk_trials": eng.serve_stats()["chunk_trials"], "rates": results}
 
 

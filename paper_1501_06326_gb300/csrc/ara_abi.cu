@@ -14,7 +14,7 @@
 #include <vector>
 
 #include "../../include/ara.h"
-#include "ara_internal.h"
+#include "ara_batch.h"
 
 namespace {
 
@@ -1146,7 +1146,8 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
     float best = 0.0f;
     for (auto& e : c->tune_ev)
       if (!e) ARA_CUDA(c, cudaEventCreate(&e));
-    for (int it : {ara::kItemTile, ara::kItemTrial, ara::kItemDense, ara::kItemIndexed})
+    for (int it : {static_cast<int>(ara::kItemTile), static_cast<int>(ara::kItemTrial),
+                   static_cast<int>(ara::kItemDense), ara::kItemIndexed})
       for (int b = 2; b <= max_blocks(it); ++b) {
         ARA_CUDA(c, cudaMemsetAsync(c->counters.ptr, 0, 4 * sizeof(unsigned long long), c->stream));
         ARA_CUDA(c, cudaEventRecord(c->tune_ev[0], c->stream));

@@ -1,0 +1,56 @@
+// Internal interface of the event-major YET index and the batched passes that
+// read it (ara_index.cu, ara_batch.cu, ara_select.cu, ara_abi.cu).  Not part
+// of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ara_internal.h"
+
+namespace ara {
+
+// --------------------------------------------------------------- sort
+// Stable ascending sort of n (key, value) pairs by the low key_bits bits of the
+// keys (8 bits a pass), in place; `scratch` holds sort_pairs_scratch_bytes(n).
+size_t sort_pairs_scratch_bytes(int64_t n);
+cudaError_t sort_pairs_ascending(unsigned long long* keys, int64_t* vals, int64_t n, int key_bits, void* scratch,
+                                 cudaStream_t s, int* n_launch);
+
+// --------------------------------------------------------------- event-major YET index
+// occ[i] = (trial << 32) | event index, grouped by event id and in trial order
+// within an event: event e's occurrences are occ[ev_off[e], ev_off[e + 1]).
+// n_events < 2^32.  `scratch` holds yet_index_scratch_bytes(n_events).
+size_t yet_index_scratch_bytes(int64_t n_events);
+cudaError_t build_yet_index(const int64_t* off, const int32_t* ids, int64_t n_trials, int64_t n_events,
+                            int32_t catalogue, unsigned long long* occ, uint32_t* ev_off, void* scratch,
+                            cudaStream_t s, int* n_launch);
+
+// --------------------------------------------------------------- indexed batched pass
+// The fourth work item of the batched losses (after kItemTile, kItemTrial and
+// kItemDense): a warp per distinct event of the pass's ELT union, over the
+// event's occurrences in [t_begin, t_end) from the index; each (occurrence,
+// layer) adds the same fixed-point number as the other work items, into acc
+// with a 64-bit atomic add.  No k_gather.
+constexpr int kItemIndexed = 3;
+struct IndexedParams {
+  BatchParams b;                  // the pass; counters[0] is the event queue
+  const unsigned long long* occ;  // the index (build_yet_index)
+  const uint32_t* ev_off;
+  const int32_t* u_event;         // [n_u] the union's distinct events, in pair order
+  const uint32_t* u_first;        // [n_u + 1] each one's first pair; u_first[n_u] = the pair count
+  const uint32_t* n_u;            // device: the number of distinct events
+  unsigned long long* acc;        // [n_layers][t_end - t_begin] fixed-point sums (zeroed before)
+};
+// The union's distinct events from the pairs' event ids (pev, in pair order):
+// flags and scan hold n_recs + 1 words, scan_tmp scan_tmp_words(n_recs); the
+// count is left at scan[n_recs].
+cudaError_t launch_union_events(const int32_t* pev, int64_t n_recs, uint32_t* flags, uint32_t* scan,
+                                uint32_t* scan_tmp, int32_t* u_event, uint32_t* u_first, cudaStream_t s,
+                                int* n_launch);
+cudaError_t launch_losses_indexed(const IndexedParams& q, int grid, cudaStream_t s);
+// The year losses from acc: each layer's trials [t_begin, layer_t_end).
+cudaError_t launch_indexed_years(const IndexedParams& q, cudaStream_t s);
+int losses_indexed_blocks_per_sm();
+
+}  // namespace ara

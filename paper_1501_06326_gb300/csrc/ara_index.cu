@@ -7,7 +7,7 @@
 
 #include <cstdint>
 
-#include "ara_internal.h"
+#include "ara_batch.h"
 
 namespace ara {
 

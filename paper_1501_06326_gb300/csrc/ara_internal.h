@@ -221,35 +221,10 @@ enum BatchItem : int {
   kItemTile = 0,   // one warp per tile of kWarpTrials trials, a lane per record
   kItemTrial = 1,  // one warp per trial of a tile, a lane per record
   kItemDense = 2,  // one warp per tile, a lane per pair (records streamed through per-warp rings)
-  kItemIndexed = 3,  // a warp per event of the ELT union, through the event-major YET index (no k_gather)
 };
 cudaError_t launch_losses_batch(const BatchParams& p, int item, int grid, cudaStream_t s);
 // CTAs of the dense kernel that one SM holds for n_layers layers (0 on error).
 int losses_dense_blocks_per_sm(int n_layers);
-
-// A batched pass through the event-major YET index (kItemIndexed): a warp per
-// distinct event of the pass's ELT union, over the event's occurrences in
-// [t_begin, t_end); each (occurrence, layer) adds the same fixed-point number
-// as the other work items, into acc with a 64-bit atomic add.
-struct IndexedParams {
-  BatchParams b;                  // the pass; counters[0] is the event queue
-  const unsigned long long* occ;  // the index (build_yet_index)
-  const uint32_t* ev_off;
-  const int32_t* u_event;         // [n_u] the union's distinct events, in pair order
-  const uint32_t* u_first;        // [n_u + 1] each one's first pair; u_first[n_u] = the pair count
-  const uint32_t* n_u;            // device: the number of distinct events
-  unsigned long long* acc;        // [n_layers][t_end - t_begin] fixed-point sums (zeroed before)
-};
-// The union's distinct events from the pairs' event ids (pev, in pair order):
-// flags and scan hold n_recs + 1 words, scan_tmp scan_tmp_words(n_recs); the
-// count is left at scan[n_recs].
-cudaError_t launch_union_events(const int32_t* pev, int64_t n_recs, uint32_t* flags, uint32_t* scan,
-                                uint32_t* scan_tmp, int32_t* u_event, uint32_t* u_first, cudaStream_t s,
-                                int* n_launch);
-cudaError_t launch_losses_indexed(const IndexedParams& q, int grid, cudaStream_t s);
-// The year losses from acc: each layer's trials [t_begin, layer_t_end).
-cudaError_t launch_indexed_years(const IndexedParams& q, cudaStream_t s);
-int losses_indexed_blocks_per_sm();
 
 size_t gather_smem_bytes(int filt_words);
 int gather_filter_words(int64_t n_words, int max_smem);
@@ -298,19 +273,5 @@ cudaError_t top_gather_device(const double* ylt, const int64_t* order, int64_t m
                               double* vals, int64_t* trials, cudaStream_t s);
 cudaError_t sort_desc_device(const double* ylt, int64_t n, int64_t* order, void* scratch, cudaStream_t s,
                              int* n_launch);
-// Stable ascending sort of n (key, value) pairs by the low key_bits bits of the
-// keys (8 bits a pass), in place; `scratch` holds sort_pairs_scratch_bytes(n).
-size_t sort_pairs_scratch_bytes(int64_t n);
-cudaError_t sort_pairs_ascending(unsigned long long* keys, int64_t* vals, int64_t n, int key_bits, void* scratch,
-                                 cudaStream_t s, int* n_launch);
-
-// --------------------------------------------------------------- event-major YET index
-// occ[i] = (trial << 32) | event index, grouped by event id and in trial order
-// within an event: event e's occurrences are occ[ev_off[e], ev_off[e + 1]).
-// n_events < 2^32.  `scratch` holds yet_index_scratch_bytes(n_events).
-size_t yet_index_scratch_bytes(int64_t n_events);
-cudaError_t build_yet_index(const int64_t* off, const int32_t* ids, int64_t n_trials, int64_t n_events,
-                            int32_t catalogue, unsigned long long* occ, uint32_t* ev_off, void* scratch,
-                            cudaStream_t s, int* n_launch);
 
 }  // namespace ara

@@ -19,7 +19,7 @@
 #include <utility>
 
 #include "../../include/ara.h"
-#include "ara_internal.h"
+#include "ara_batch.h"
 
 namespace ara {
 
