@@ -1116,6 +1116,7 @@ static int run_layers_impl(ara_ctx* c, int32_t n_layers, const ara_layer* layers
     q.u_first = static_cast<const uint32_t*>(c->u_first.ptr);
     q.n_u = static_cast<const uint32_t*>(c->u_scan.ptr) + n_recs;
     q.acc = static_cast<unsigned long long*>(c->idx_acc.ptr);
+    q.yet_trials = c->n_trials;
   }
   const size_t acc_bytes = sizeof(unsigned long long) * n_layers * n_out;
   auto launch_item = [&](int it, int b) -> cudaError_t {

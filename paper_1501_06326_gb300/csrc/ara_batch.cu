@@ -929,10 +929,12 @@ namespace {
 
 constexpr int kIdxThreads = 128;
 constexpr int kIdxBlocksPerSm = 7;
+constexpr int kIdxClaim = 8;  // events a warp claims at a time
 
 struct IdxWarp {
   float gacc[kBatchLayers][32];      // per layer and lane: the running sum of an occurrence's pair losses
   uint32_t pmask[kMaxIndexElts];     // the event's pairs: layers holding their ELTs
+  uint4 meta[kIdxClaim];             // the claimed events: (first pair, pair end, occ begin, occ end)
 };
 
 // First entry in [lo, hi) of the event's occurrences whose trial is >= key
@@ -1014,16 +1016,32 @@ __global__ void __launch_bounds__(kIdxThreads, kIdxBlocksPerSm)
   unsigned long long nc = 0ull;
   uint32_t n_pairs = 0;
 
-  unsigned long long next = 0ull;  // events are claimed one ahead
-  if (lane == 0) next = atomicAdd(&p.counters[0], 1ull);
-  for (;;) {
-    const unsigned long long u = __shfl_sync(0xffffffffu, next, 0);
-    if (u >= n_u) break;
-    if (lane == 0) next = atomicAdd(&p.counters[0], 1ull);
-    const int32_t e = q.u_event[u];
-    const uint32_t ps = q.u_first[u], cnt = q.u_first[u + 1] - ps;
-    const uint32_t lo = first_occ_at(q.occ, q.ev_off[e], q.ev_off[e + 1], t0, lane);
-    const uint32_t hi = first_occ_at(q.occ, lo, q.ev_off[e + 1], p.t_end, lane);
+  // events are claimed kIdxClaim at a time, lane j loading the metadata (pair range, occurrence range)
+  // of the claim's event j; the next claim's loads are issued before this claim's events run
+  const bool from_start = t0 <= 0, to_end = p.t_end >= q.yet_trials;
+  uint4 meta = make_uint4(0u, 0u, 0u, 0u);
+  auto claim = [&]() {
+    unsigned long long b = 0ull;
+    if (lane == 0) b = atomicAdd(&p.counters[0], static_cast<unsigned long long>(kIdxClaim));
+    b = __shfl_sync(0xffffffffu, b, 0);
+    const unsigned long long u = b + lane;
+    if (lane < static_cast<uint32_t>(kIdxClaim) && u < n_u) {
+      const int32_t e = q.u_event[u];
+      meta = make_uint4(q.u_first[u], q.u_first[u + 1], q.ev_off[e], q.ev_off[e + 1]);
+    }
+    return b;
+  };
+  unsigned long long base = claim();
+  while (base < n_u) {
+    if (lane < static_cast<uint32_t>(kIdxClaim)) ws.meta[lane] = meta;
+    __syncwarp();
+    const int n_here = static_cast<int>(min(static_cast<unsigned long long>(kIdxClaim), n_u - base));
+    base = claim();
+    for (int g = 0; g < n_here; ++g) {
+    const uint4 m4 = ws.meta[g];
+    const uint32_t ps = m4.x, cnt = m4.y - m4.x, ea = m4.z, eb = m4.w;
+    const uint32_t lo = from_start ? ea : first_occ_at(q.occ, ea, eb, t0, lane);
+    const uint32_t hi = to_end ? eb : first_occ_at(q.occ, lo, eb, p.t_end, lane);
     if (lo >= hi) continue;
     for (uint32_t j = lane; j < cnt; j += 32) ws.pmask[j] = ds.layers_of[pair_pos(p.hot[ps + j].meta)];
     __syncwarp();
@@ -1078,6 +1096,8 @@ __global__ void __launch_bounds__(kIdxThreads, kIdxBlocksPerSm)
       }
     }
     __syncwarp();  // pmask is rewritten for the next event
+    }
+    __syncwarp();  // meta is rewritten for the next claim
   }
   n_pairs = __reduce_add_sync(0xffffffffu, n_pairs);
   for (int d = 16; d > 0; d >>= 1) nc += __shfl_xor_sync(0xffffffffu, nc, d);

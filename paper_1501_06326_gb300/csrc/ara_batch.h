@@ -41,6 +41,7 @@ struct IndexedParams {
   const uint32_t* u_first;        // [n_u + 1] each one's first pair; u_first[n_u] = the pair count
   const uint32_t* n_u;            // device: the number of distinct events
   unsigned long long* acc;        // [n_layers][t_end - t_begin] fixed-point sums (zeroed before)
+  int64_t yet_trials;             // the YET's trials: a pass from 0 or to the end needs no search there
 };
 // The union's distinct events from the pairs' event ids (pev, in pair order):
 // flags and scan hold n_recs + 1 words, scan_tmp scan_tmp_words(n_recs); the
