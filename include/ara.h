@@ -332,9 +332,11 @@ ARA_API int ara_set_batch_config(ara_ctx *ctx, int32_t item, int32_t blocks_per_
  * its ELTs' events instead of streaming every trial's events; the year losses
  * are the same bits as the other work items'.  ara_run_layer (one layer, with
  * its double-float sums and hit diagnostics) keeps streaming the YET.
- * The index takes 8 bytes per YET event and 4 per catalogue id, and lasts until
- * the next YET load; the build needs about 24 bytes per event of scratch
- * besides.  Errors: ARA_ENOTLOADED; ARA_EINVAL (served requests queued or
+ * With each event's occurrences the index keeps their offsets at every
+ * 131,072 trials (the serving chunk), so that a pass's slices of trials find
+ * their occurrences without a search.  It takes 8 bytes per YET event and
+ * 4 * (ceil(n_trials / 131072) + 1) per catalogue id, and lasts until the next
+ * YET load; the build needs about 24 bytes per event of scratch besides.  Errors: ARA_ENOTLOADED; ARA_EINVAL (served requests queued or
  * running, or 2^32 or more events); ARA_ENOMEM; ARA_ECUDA.
  * ara_yet_index_info reports whether the index is built, its bytes and the
  * device time of its build (any pointer may be NULL). */

@@ -914,9 +914,11 @@ cudaError_t launch_losses_batch(const BatchParams& p, int item, int grid, cudaSt
 
 
 // ------------------------------------------------------------------ indexed kernel
-// A warp per distinct event of the pass's ELT union (claimed from a queue),
-// over the event's occurrences in the pass's trials, 32 at a time (a lane
-// each), found by a warp search in the event-major YET index.  Every lane of
+// A warp per distinct event of the pass's ELT union and trial slice (claimed
+// from the slice's queue, eight events at a time), over the event's
+// occurrences in the slice, 32 at a time (a lane each).  The slice's bounds
+// come from the index's trial grid, with a warp search only where a bound is
+// inside a grid cell (a pass's ends off the grid).  Every lane of
 // the warp works on the same event, so the pairs, their layers and their
 // tables are the same across the warp.  For each occurrence and each layer it
 // serves, the event's pair losses over the layer's ELTs are summed from left
@@ -934,7 +936,9 @@ constexpr int kIdxClaim = 8;  // events a warp claims at a time
 struct IdxWarp {
   float gacc[kBatchLayers][32];      // per layer and lane: the running sum of an occurrence's pair losses
   uint32_t pmask[kMaxIndexElts];     // the event's pairs: layers holding their ELTs
-  uint4 meta[kIdxClaim];             // the claimed events: (first pair, pair end, occ begin, occ end)
+  uint4 meta[2 * kIdxClaim];         // the claimed events: [j] (first pair, pair end, range of the slice's first
+                                     // occurrence), [kIdxClaim + j] (range of its end, -, -)
+  int64_t span[2];                   // the trials of the claim's slice
 };
 
 // First entry in [lo, hi) of the event's occurrences whose trial is >= key
@@ -1016,86 +1020,108 @@ __global__ void __launch_bounds__(kIdxThreads, kIdxBlocksPerSm)
   unsigned long long nc = 0ull;
   uint32_t n_pairs = 0;
 
-  // events are claimed kIdxClaim at a time, lane j loading the metadata (pair range, occurrence range)
-  // of the claim's event j; the next claim's loads are issued before this claim's events run
-  const bool from_start = t0 <= 0, to_end = p.t_end >= q.yet_trials;
+  // the queue's groups: kIdxClaim events over one trial slice, every event of a slice before the next
+  // slice, so that the sums being added to stay within a slice's trials; a warp moves to the next slice
+  // when the slice's queue runs out. For the group's event j, lane j loads its pairs and the grid range
+  // that holds the slice's first occurrence, lane kIdxClaim + j the range that holds the slice's end (a
+  // bound on the grid is its own range); the next group's loads are issued before this group's events run.
+  const int slice_shift = q.slice_shift, grid_shift = q.grid_shift;
+  const int64_t k0 = t0 >> slice_shift;
+  const uint32_t per_slice = (n_u + kIdxClaim - 1) / kIdxClaim;
+  const uint32_t n_slices = static_cast<uint32_t>(indexed_slices(t0, p.t_end, slice_shift));
   uint4 meta = make_uint4(0u, 0u, 0u, 0u);
+  uint32_t sl = 0u;  // the slice of the group claimed last
+  auto slice_lo = [&](uint32_t j) { return max(t0, (k0 + j) << slice_shift); };
+  auto slice_hi = [&](uint32_t j) { return min(p.t_end, (k0 + j + 1) << slice_shift); };
   auto claim = [&]() {
-    unsigned long long b = 0ull;
-    if (lane == 0) b = atomicAdd(&p.counters[0], static_cast<unsigned long long>(kIdxClaim));
-    b = __shfl_sync(0xffffffffu, b, 0);
-    const unsigned long long u = b + lane;
-    if (lane < static_cast<uint32_t>(kIdxClaim) && u < n_u) {
-      const int32_t e = q.u_event[u];
-      meta = make_uint4(q.u_first[u], q.u_first[u + 1], q.ev_off[e], q.ev_off[e + 1]);
+    uint32_t g = 0u;
+    for (; sl < n_slices; ++sl) {
+      if (lane == 0) g = atomicAdd(q.slice_queue + sl, 1u);
+      g = __shfl_sync(0xffffffffu, g, 0);
+      if (g < per_slice) break;
     }
-    return b;
+    const uint32_t j = lane & static_cast<uint32_t>(kIdxClaim - 1), u = g * kIdxClaim + j;
+    if (sl < n_slices && lane < static_cast<uint32_t>(2 * kIdxClaim) && u < n_u) {
+      const uint32_t* row = q.ev_grid + static_cast<int64_t>(q.u_event[u]) * (q.grid_cells + 1);
+      const bool end = lane >= static_cast<uint32_t>(kIdxClaim);
+      const int64_t b = end ? slice_hi(sl) : slice_lo(sl);
+      const int64_t cell = b >= q.yet_trials ? q.grid_cells : b >> grid_shift;
+      const bool on_grid = b >= q.yet_trials || (b & ((int64_t{1} << grid_shift) - 1)) == 0;
+      const uint32_t x = row[cell], y = on_grid ? x : row[cell + 1];
+      meta = end ? make_uint4(x, y, 0u, 0u) : make_uint4(q.u_first[u], q.u_first[u + 1], x, y);
+    }
+    return g;
   };
-  unsigned long long base = claim();
-  while (base < n_u) {
-    if (lane < static_cast<uint32_t>(kIdxClaim)) ws.meta[lane] = meta;
+  uint32_t grp = claim();
+  while (sl < n_slices) {
+    if (lane < static_cast<uint32_t>(2 * kIdxClaim)) ws.meta[lane] = meta;
+    if (lane == 0) {
+      ws.span[0] = slice_lo(sl);
+      ws.span[1] = slice_hi(sl);
+    }
     __syncwarp();
-    const int n_here = static_cast<int>(min(static_cast<unsigned long long>(kIdxClaim), n_u - base));
-    base = claim();
+    const int n_here = static_cast<int>(min(static_cast<uint32_t>(kIdxClaim), n_u - grp * kIdxClaim));
+    grp = claim();
     for (int g = 0; g < n_here; ++g) {
-    const uint4 m4 = ws.meta[g];
-    const uint32_t ps = m4.x, cnt = m4.y - m4.x, ea = m4.z, eb = m4.w;
-    const uint32_t lo = from_start ? ea : first_occ_at(q.occ, ea, eb, t0, lane);
-    const uint32_t hi = to_end ? eb : first_occ_at(q.occ, lo, eb, p.t_end, lane);
-    if (lo >= hi) continue;
-    for (uint32_t j = lane; j < cnt; j += 32) ws.pmask[j] = ds.layers_of[pair_pos(p.hot[ps + j].meta)];
-    __syncwarp();
-    for (uint32_t r = lo; r < hi; r += 32) {
-      const uint32_t i = r + lane;
-      const bool valid = i < hi;
-      const unsigned long long o = valid ? __ldg(q.occ + i) : 0ull;
-      const int64_t trial = static_cast<int64_t>(o >> 32);
-      const uint32_t k = static_cast<uint32_t>(o);
-      uint32_t act = 0u;  // the layers whose trials reach this one
-      if (valid) {
-        act = all;
-        if (trial >= t_full) {
-          act = 0u;
-          for (int l = 0; l < nl; ++l)
-            if (trial < ds.t_end[l]) act |= 1u << l;
+      const uint4 m4 = ws.meta[g], h4 = ws.meta[kIdxClaim + g];
+      const uint32_t ps = m4.x, cnt = m4.y - m4.x;
+      // the slice's occurrences: a search only where a bound is inside a grid cell
+      const uint32_t lo = first_occ_at(q.occ, m4.z, m4.w, ws.span[0], lane);
+      const uint32_t hi = first_occ_at(q.occ, max(lo, h4.x), h4.y, ws.span[1], lane);
+      if (lo >= hi) continue;
+      for (uint32_t j = lane; j < cnt; j += 32) ws.pmask[j] = ds.layers_of[pair_pos(p.hot[ps + j].meta)];
+      __syncwarp();
+      for (uint32_t r = lo; r < hi; r += 32) {
+        const uint32_t i = r + lane;
+        const bool valid = i < hi;
+        const unsigned long long o = valid ? __ldg(q.occ + i) : 0ull;
+        const int64_t trial = static_cast<int64_t>(o >> 32);
+        const uint32_t k = static_cast<uint32_t>(o);
+        uint32_t act = 0u;  // the layers whose trials reach this one
+        if (valid) {
+          act = all;
+          if (trial >= t_full) {
+            act = 0u;
+            for (int l = 0; l < nl; ++l)
+              if (trial < ds.t_end[l]) act |= 1u << l;
+          }
         }
-      }
-      unsigned long long* acc = q.acc + (trial - t0);
-      if (cnt == 1u) {
-        const uint32_t m = ws.pmask[0] & act;
-        if (m) {
-          const float L = indexed_pair_loss(p, ds, ps, trial, k, &nc);
-          ++n_pairs;
-          for (uint32_t mm = m; mm; mm &= mm - 1u) {
+        unsigned long long* acc = q.acc + (trial - t0);
+        if (cnt == 1u) {
+          const uint32_t m = ws.pmask[0] & act;
+          if (m) {
+            const float L = indexed_pair_loss(p, ds, ps, trial, k, &nc);
+            ++n_pairs;
+            for (uint32_t mm = m; mm; mm &= mm - 1u) {
+              const int l = __ffs(mm) - 1;
+              const float4 c = ds.occ[l];
+              const float O = clamp_terms_f(L, c.x, c.y);
+              if (O > 0.0f) atomicAdd(acc + static_cast<int64_t>(l) * stride, fixed_units(O, c.z));
+            }
+          }
+        } else {
+          // the pairs in order: each layer's running sum is the left-to-right sum of its pairs' losses
+          uint32_t touched = 0u;
+          for (uint32_t j = 0; j < cnt; ++j) {
+            const uint32_t m = ws.pmask[j] & act;
+            if (m) {
+              const float L = indexed_pair_loss(p, ds, ps + j, trial, k, &nc);
+              ++n_pairs;
+              touched |= m;
+              for (uint32_t mm = m; mm; mm &= mm - 1u) ws.gacc[__ffs(mm) - 1][lane] += L;
+            }
+          }
+          for (uint32_t mm = touched; mm; mm &= mm - 1u) {
             const int l = __ffs(mm) - 1;
+            const float G = ws.gacc[l][lane];
+            ws.gacc[l][lane] = 0.0f;
             const float4 c = ds.occ[l];
-            const float O = clamp_terms_f(L, c.x, c.y);
+            const float O = clamp_terms_f(G, c.x, c.y);
             if (O > 0.0f) atomicAdd(acc + static_cast<int64_t>(l) * stride, fixed_units(O, c.z));
           }
         }
-      } else {
-        // the pairs in order: each layer's running sum is the left-to-right sum of its pairs' losses
-        uint32_t touched = 0u;
-        for (uint32_t j = 0; j < cnt; ++j) {
-          const uint32_t m = ws.pmask[j] & act;
-          if (m) {
-            const float L = indexed_pair_loss(p, ds, ps + j, trial, k, &nc);
-            ++n_pairs;
-            touched |= m;
-            for (uint32_t mm = m; mm; mm &= mm - 1u) ws.gacc[__ffs(mm) - 1][lane] += L;
-          }
-        }
-        for (uint32_t mm = touched; mm; mm &= mm - 1u) {
-          const int l = __ffs(mm) - 1;
-          const float G = ws.gacc[l][lane];
-          ws.gacc[l][lane] = 0.0f;
-          const float4 c = ds.occ[l];
-          const float O = clamp_terms_f(G, c.x, c.y);
-          if (O > 0.0f) atomicAdd(acc + static_cast<int64_t>(l) * stride, fixed_units(O, c.z));
-        }
       }
-    }
-    __syncwarp();  // pmask is rewritten for the next event
+      __syncwarp();  // pmask is rewritten for the next event
     }
     __syncwarp();  // meta is rewritten for the next claim
   }

@@ -19,12 +19,17 @@ cudaError_t sort_pairs_ascending(unsigned long long* keys, int64_t* vals, int64_
 
 // --------------------------------------------------------------- event-major YET index
 // occ[i] = (trial << 32) | event index, grouped by event id and in trial order
-// within an event: event e's occurrences are occ[ev_off[e], ev_off[e + 1]).
-// n_events < 2^32.  `scratch` holds yet_index_scratch_bytes(n_events).
-size_t yet_index_scratch_bytes(int64_t n_events);
+// within an event.  ev_grid[e * (cells + 1) + k], k = 0..cells, is the first
+// position of event e's occurrences whose trial is at least k << grid_shift
+// (the end of e's occurrences where there is none): e's occurrences are
+// occ[ev_grid[e * (cells + 1)], ev_grid[e * (cells + 1) + cells]), with
+// cells = yet_grid_cells(n_trials, grid_shift).  n_events < 2^32.  `scratch`
+// holds yet_index_scratch_bytes(n_events, catalogue).
+int64_t yet_grid_cells(int64_t n_trials, int grid_shift);
+size_t yet_index_scratch_bytes(int64_t n_events, int32_t catalogue);
 cudaError_t build_yet_index(const int64_t* off, const int32_t* ids, int64_t n_trials, int64_t n_events,
-                            int32_t catalogue, unsigned long long* occ, uint32_t* ev_off, void* scratch,
-                            cudaStream_t s, int* n_launch);
+                            int32_t catalogue, int grid_shift, unsigned long long* occ, uint32_t* ev_grid,
+                            void* scratch, cudaStream_t s, int* n_launch);
 
 // --------------------------------------------------------------- indexed batched pass
 // The fourth work item of the batched losses (after kItemTile, kItemTrial and
@@ -34,15 +39,24 @@ cudaError_t build_yet_index(const int64_t* off, const int32_t* ids, int64_t n_tr
 // with a 64-bit atomic add.  No k_gather.
 constexpr int kItemIndexed = 3;
 struct IndexedParams {
-  BatchParams b;                  // the pass; counters[0] is the event queue
+  BatchParams b;                  // the pass
   const unsigned long long* occ;  // the index (build_yet_index)
-  const uint32_t* ev_off;
+  const uint32_t* ev_grid;
+  int64_t grid_cells;
+  int grid_shift;
+  int slice_shift;                // the pass runs in slices [j << slice_shift, (j + 1) << slice_shift) of the
+                                  // trials (clipped to the pass), every event over one slice before the next;
+                                  // slice_shift >= grid_shift, so inner slice bounds are grid bounds
   const int32_t* u_event;         // [n_u] the union's distinct events, in pair order
   const uint32_t* u_first;        // [n_u + 1] each one's first pair; u_first[n_u] = the pair count
   const uint32_t* n_u;            // device: the number of distinct events
   unsigned long long* acc;        // [n_layers][t_end - t_begin] fixed-point sums (zeroed before)
-  int64_t yet_trials;             // the YET's trials: a pass from 0 or to the end needs no search there
+  int64_t yet_trials;             // the YET's trials
+  uint32_t* slice_queue;          // [indexed_slices(t_begin, t_end, slice_shift)] each slice's queue (zeroed before)
 };
+__host__ __device__ inline int64_t indexed_slices(int64_t t_begin, int64_t t_end, int slice_shift) {
+  return t_end > t_begin ? ((t_end - 1) >> slice_shift) - (t_begin >> slice_shift) + 1 : 0;
+}
 // The union's distinct events from the pairs' event ids (pev, in pair order):
 // flags and scan hold n_recs + 1 words, scan_tmp scan_tmp_words(n_recs); the
 // count is left at scan[n_recs].

@@ -44,6 +44,24 @@ __global__ void k_event_starts(const unsigned long long* __restrict__ keys, int6
   }
 }
 
+// ev_grid[e * (cells + 1) + k] = the first of event e's occurrences with
+// trial >= k << grid_shift, by binary search within e's range
+__global__ void k_event_grid(const unsigned long long* __restrict__ occ, const uint32_t* __restrict__ ev_off,
+                             int64_t n_entries, int64_t cells, int grid_shift, uint32_t* ev_grid) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_entries; i += stride) {
+    const int64_t e = i / (cells + 1), k = i - e * (cells + 1);
+    const int64_t key = k << grid_shift;
+    uint32_t lo = ev_off[e], hi = ev_off[e + 1];
+    while (lo < hi) {
+      const uint32_t mid = lo + (hi - lo) / 2u;
+      if (static_cast<int64_t>(occ[mid] >> 32) < key) lo = mid + 1u;
+      else hi = mid;
+    }
+    ev_grid[i] = lo;
+  }
+}
+
 int grid_of(int64_t n, int threads) {
   const int64_t b = (n + threads - 1) / threads;
   return static_cast<int>(b < 1 ? 1 : (b > 65535 ? 65535 : b));
@@ -51,28 +69,46 @@ int grid_of(int64_t n, int threads) {
 
 }  // namespace
 
-size_t yet_index_scratch_bytes(int64_t n_events) {
-  return sizeof(unsigned long long) * static_cast<size_t>(n_events) + sort_pairs_scratch_bytes(n_events) + 256;
+int64_t yet_grid_cells(int64_t n_trials, int grid_shift) {
+  return n_trials > 0 ? ((n_trials - 1) >> grid_shift) + 1 : 0;
+}
+
+size_t yet_index_scratch_bytes(int64_t n_events, int32_t catalogue) {
+  return sizeof(unsigned long long) * static_cast<size_t>(n_events) + sort_pairs_scratch_bytes(n_events) +
+         sizeof(uint32_t) * (static_cast<size_t>(catalogue) + 2) + 512;
 }
 
 cudaError_t build_yet_index(const int64_t* off, const int32_t* ids, int64_t n_trials, int64_t n_events,
-                            int32_t catalogue, unsigned long long* occ, uint32_t* ev_off, void* scratch,
-                            cudaStream_t s, int* n_launch) {
+                            int32_t catalogue, int grid_shift, unsigned long long* occ, uint32_t* ev_grid,
+                            void* scratch, cudaStream_t s, int* n_launch) {
   unsigned long long* keys = static_cast<unsigned long long*>(scratch);
-  void* sort_scratch = keys + n_events;
+  uint32_t* ev_off = reinterpret_cast<uint32_t*>(keys + n_events);  // [catalogue + 1]
+  void* sort_scratch = reinterpret_cast<char*>(scratch) + sizeof(unsigned long long) * static_cast<size_t>(n_events) +
+                       ((sizeof(uint32_t) * (static_cast<size_t>(catalogue) + 2) + 255) & ~size_t{255});
+  const int64_t cells = yet_grid_cells(n_trials, grid_shift);
+  const int64_t n_entries = static_cast<int64_t>(catalogue) * (cells + 1);
   k_fill_u32<<<grid_of(static_cast<int64_t>(catalogue) + 1, 256), 256, 0, s>>>(ev_off, static_cast<int64_t>(catalogue) + 1,
                                                                               static_cast<uint32_t>(n_events));
   cudaError_t err = cudaGetLastError();
-  if (err != cudaSuccess || n_events == 0) return err;
-  k_yet_pairs<<<grid_of(n_trials * 32, 256), 256, 0, s>>>(off, ids, n_trials, keys, reinterpret_cast<int64_t*>(occ));
-  if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  int key_bits = 1;
-  while (key_bits < 31 && (1ll << key_bits) < static_cast<int64_t>(catalogue)) ++key_bits;
-  if ((err = sort_pairs_ascending(keys, reinterpret_cast<int64_t*>(occ), n_events, key_bits, sort_scratch, s,
-                                  n_launch)) != cudaSuccess)
-    return err;
-  k_event_starts<<<grid_of(n_events, 256), 256, 0, s>>>(keys, n_events, ev_off);
-  if (n_launch) *n_launch += 3;
+  if (err != cudaSuccess) return err;
+  int launched = 1;
+  if (n_events > 0) {
+    k_yet_pairs<<<grid_of(n_trials * 32, 256), 256, 0, s>>>(off, ids, n_trials, keys, reinterpret_cast<int64_t*>(occ));
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    int key_bits = 1;
+    while (key_bits < 31 && (1ll << key_bits) < static_cast<int64_t>(catalogue)) ++key_bits;
+    if ((err = sort_pairs_ascending(keys, reinterpret_cast<int64_t*>(occ), n_events, key_bits, sort_scratch, s,
+                                    n_launch)) != cudaSuccess)
+      return err;
+    k_event_starts<<<grid_of(n_events, 256), 256, 0, s>>>(keys, n_events, ev_off);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    launched += 2;
+  }
+  if (n_entries > 0) {
+    k_event_grid<<<grid_of(n_entries, 256), 256, 0, s>>>(occ, ev_off, n_entries, cells, grid_shift, ev_grid);
+    ++launched;
+  }
+  if (n_launch) *n_launch += launched;
   return cudaGetLastError();
 }
 
