@@ -631,7 +631,7 @@ def _batched_leg(eng, synth, torch, dev, stream, n_trials, n_events, seed, args)
             "ms_batched_by_item": ms_items,
             "without_yet_index": {"item": names[st_no_index["batch_item"]], "ms_batched": ms_no_index,
                                   "speedup": ms_plain / ms_no_index},
-            "yet_index": {"bytes": index["bytes"], "build_ms": index["build_ms"],
+            "yet_index": {"bytes": index["bytes"], "build_ms": index["build_ms"], "method": index["method"],
                           "note": "built once per YET (ara_build_yet_index); ara_run_layer (ms_plain) streams the YET"},
             "autotuned": {"item": names[st["batch_item"]], "blocks_per_sm": st["batch_blocks_per_sm"],
                           "tuned": bool(st["batch_tuned"])},
@@ -761,7 +761,7 @@ def _serving_leg(eng, synth, offsets, args):
                         "[1e4, 1e6], RP 100/250, percentile terms per request (tests/golden/serving_terms.json)",
             "time": "real: Poisson arrivals in wall time; latency = arrival to the poll that returns the result",
             "passes": "batched passes through the YET's event-major index (built once per YET, before the sweep)",
-            "yet_index": {"bytes": index["bytes"], "build_ms": index["build_ms"]},
+            "yet_index": {"bytes": index["bytes"], "build_ms": index["build_ms"], "method": index["method"]},
             "chunk_trials": eng.serve_stats()["chunk_trials"], "rates": results}
 
 

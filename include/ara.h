@@ -326,8 +326,10 @@ ARA_API int ara_set_batch_config(ara_ctx *ctx, int32_t item, int32_t blocks_per_
 
 /* The event-major index of the loaded YET (Section 2.1's lookup taken from the
  * ELT side): for each catalogue event, its occurrences (trial, event index) in
- * trial order, built on the device by a stable radix sort of the YET's events
- * by id.  Once built, batched passes (ara_run_layers and the serving loop)
+ * trial order, built on the device: each occurrence is counted into and placed
+ * in a bucket per (event, 131,072-trial cell), and each bucket sorted; where a
+ * bucket would hold more than 2,048 occurrences, by a stable radix sort of the
+ * YET's events by id instead (the same index).  Once built, batched passes (ara_run_layers and the serving loop)
  * default to ARA_BATCH_ITEM_INDEXED, which reaches a pass's hit events through
  * its ELTs' events instead of streaming every trial's events; the year losses
  * are the same bits as the other work items'.  ara_run_layer (one layer, with
@@ -336,12 +338,14 @@ ARA_API int ara_set_batch_config(ara_ctx *ctx, int32_t item, int32_t blocks_per_
  * 131,072 trials (the serving chunk), so that a pass's slices of trials find
  * their occurrences without a search.  It takes 8 bytes per YET event and
  * 4 * (ceil(n_trials / 131072) + 1) per catalogue id, and lasts until the next
- * YET load; the build needs about 24 bytes per event of scratch besides.  Errors: ARA_ENOTLOADED; ARA_EINVAL (served requests queued or
+ * YET load; the bucket build needs 4 bytes per (catalogue id, cell) of
+ * scratch besides, the radix sort about 24 bytes per event.  Errors: ARA_ENOTLOADED; ARA_EINVAL (served requests queued or
  * running, or 2^32 or more events); ARA_ENOMEM; ARA_ECUDA.
- * ara_yet_index_info reports whether the index is built, its bytes and the
- * device time of its build (any pointer may be NULL). */
+ * ara_yet_index_info reports whether the index is built, its bytes, the
+ * device time of its build and how it was built (0 buckets, 1 radix sort, -1
+ * not built); any pointer may be NULL. */
 ARA_API int ara_build_yet_index(ara_ctx *ctx);
-ARA_API int ara_yet_index_info(const ara_ctx *ctx, int32_t *built, int64_t *bytes, float *build_ms);
+ARA_API int ara_yet_index_info(const ara_ctx *ctx, int32_t *built, int64_t *bytes, float *build_ms, int32_t *method);
 
 /* Serving: layer requests against the resident YET and ELT pool, with
  * continuous batching.  The paper has no serving system; a portfolio's

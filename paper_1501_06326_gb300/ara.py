@@ -168,7 +168,7 @@ def load_library(path: str = LIB_PATH):
     lib.ara_run_layers.argtypes = [P, i32, ctypes.POINTER(Layer), u64, i64, i64, P]
     lib.ara_set_batch_config.argtypes = [P, i32, i32]
     lib.ara_build_yet_index.argtypes = [P]
-    lib.ara_yet_index_info.argtypes = [P, P, P, P]
+    lib.ara_yet_index_info.argtypes = [P, P, P, P, P]
     lib.ara_run_layer_events.argtypes = [P, ctypes.POINTER(Layer), u64, i64, i64, P, ctypes.POINTER(EventRows)]
     lib.ara_submit.argtypes = [P, ctypes.POINTER(Layer), u64, i64, P, i32, P]
     lib.ara_serve_step.argtypes = [P, P]
@@ -303,8 +303,8 @@ def ara_build_yet_index(h):
     return load_library().ara_build_yet_index(h)
 
 
-def ara_yet_index_info(h, built, nbytes, build_ms):
-    return load_library().ara_yet_index_info(h, built, nbytes, build_ms)
+def ara_yet_index_info(h, built, nbytes, build_ms, method):
+    return load_library().ara_yet_index_info(h, built, nbytes, build_ms, method)
 
 
 def ara_serve_stats(h, out):
@@ -524,12 +524,16 @@ class Ara:
         self._check(ara_build_yet_index(self._h))
 
     def yet_index_info(self) -> dict:
-        """Whether the YET's index is built, its bytes and its build's device time."""
+        """Whether the YET's index is built, its bytes, its build's device time and
+        how it was built ("buckets", "radix sort", or None when not built)."""
         built = np.zeros(1, np.int32)
         nbytes = np.zeros(1, np.int64)
         ms = np.zeros(1, np.float32)
-        self._check(ara_yet_index_info(self._h, built.ctypes.data, nbytes.ctypes.data, ms.ctypes.data))
-        return {"built": bool(built[0]), "bytes": int(nbytes[0]), "build_ms": float(ms[0])}
+        method = np.zeros(1, np.int32)
+        self._check(ara_yet_index_info(self._h, built.ctypes.data, nbytes.ctypes.data, ms.ctypes.data,
+                                       method.ctypes.data))
+        return {"built": bool(built[0]), "bytes": int(nbytes[0]), "build_ms": float(ms[0]),
+                "method": {0: "buckets", 1: "radix sort"}.get(int(method[0]))}
 
     def submit(self, elt_ids, layer_terms, seed: int, trial_end: int, return_periods,
                primary_only: bool = False, shared_z: bool = False) -> int:

@@ -24,6 +24,9 @@ namespace {
 // in L2 while the occurrences stream through it (16 layers: 2^19 trials; measured on batched-16,
 // 6.2 ms a pass against 8.1 ms in one slice and 6.6 ms at 2^18).
 constexpr int kYetGridShift = 17;
+// The index is built by buckets per (event, grid cell) while no bucket holds more occurrences than this
+// (each bucket is sorted by one thread), else by the radix sort.
+constexpr uint32_t kYetBucketSortMax = 2048;
 constexpr int64_t kIdxSliceBytes = int64_t{64} << 20;
 int idx_slice_shift(int n_layers) {
   int k = kYetGridShift;
@@ -110,6 +113,7 @@ struct ara_ctx {
   // event-major index of the YET (ara_build_yet_index) and the indexed passes' buffers
   DevBuf yix_occ, yix_grid;
   bool yix_ready = false;
+  bool yix_sorted = false;  // built by the radix sort (a bucket was too large)
   float yix_build_ms = 0.0f;
   DevBuf u_flags, u_scan, u_event, u_first, idx_acc;
   DevBuf def_acc;           // per-trial FP64 sums of deferred occurrence losses
@@ -1240,26 +1244,50 @@ int ara_build_yet_index(ara_ctx* c) {
   if (c->n_events >= (int64_t(1) << 32) - 1)
     return fail(c, ARA_EINVAL, "%s: the YET holds 2^32 or more events", who);
   const int64_t n = c->n_events;
+  const int64_t cells = ara::yet_grid_cells(c->n_trials, kYetGridShift);
   DevBuf scratch;
   if ((rc = reserve(c, c->yix_occ, sizeof(unsigned long long) * (n + 1))) ||
-      (rc = reserve(c, c->yix_grid, sizeof(uint32_t) * (static_cast<size_t>(c->catalogue) *
-                                                           (ara::yet_grid_cells(c->n_trials, kYetGridShift) + 1) + 1))) ||
-      (rc = reserve(c, scratch, ara::yet_index_scratch_bytes(n, c->catalogue)))) {
+      (rc = reserve(c, c->yix_grid, sizeof(uint32_t) * (static_cast<size_t>(c->catalogue) * (cells + 1) + 1))) ||
+      (rc = reserve(c, scratch, ara::yet_bucket_scratch_bytes(c->catalogue, cells)))) {
     release(c, scratch);
     release(c, c->yix_occ);
     release(c, c->yix_grid);
     return rc;
   }
+  const int64_t* off = static_cast<const int64_t*>(c->yet_off.ptr);
+  const int32_t* ids = static_cast<const int32_t*>(c->yet_ids.ptr);
+  unsigned long long* occ = static_cast<unsigned long long*>(c->yix_occ.ptr);
+  uint32_t* grid = static_cast<uint32_t*>(c->yix_grid.ptr);
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
   if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
   int launched = 0;
+  // buckets per (event, grid cell) while the largest is small; else the radix sort
+  uint32_t max_bucket = 0;
   if (e == cudaSuccess)
-    e = ara::build_yet_index(static_cast<const int64_t*>(c->yet_off.ptr), static_cast<const int32_t*>(c->yet_ids.ptr),
-                             c->n_trials, n, c->catalogue, kYetGridShift,
-                             static_cast<unsigned long long*>(c->yix_occ.ptr), static_cast<uint32_t*>(c->yix_grid.ptr),
-                             scratch.ptr, c->stream, &launched);
+    e = ara::yet_index_count(off, ids, c->n_trials, c->catalogue, kYetGridShift, grid, scratch.ptr, c->stream,
+                             &launched);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&max_bucket, ara::yet_index_max_bucket(scratch.ptr, c->catalogue, cells), sizeof max_bucket,
+                        cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  const bool buckets = max_bucket <= kYetBucketSortMax;
+  if (e == cudaSuccess && buckets)
+    e = ara::yet_index_fill(off, ids, c->n_trials, c->catalogue, kYetGridShift, grid, occ, scratch.ptr, c->stream,
+                            &launched);
+  if (e == cudaSuccess && !buckets) {
+    release(c, scratch);
+    if ((rc = reserve(c, scratch, ara::yet_index_scratch_bytes(n, c->catalogue)))) {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+      release(c, c->yix_occ);
+      release(c, c->yix_grid);
+      return rc;
+    }
+    e = ara::build_yet_index(off, ids, c->n_trials, n, c->catalogue, kYetGridShift, occ, grid, scratch.ptr, c->stream,
+                             &launched);
+  }
   if (e == cudaSuccess) e = cudaEventRecord(b, c->stream);
   if (e == cudaSuccess) e = cudaEventSynchronize(b);
   float ms = 0.0f;
@@ -1274,15 +1302,17 @@ int ara_build_yet_index(ara_ctx* c) {
     release(c, c->yix_grid);
     return fail(c, ARA_ECUDA, "%s: %s", who, cudaGetErrorString(e));
   }
+  c->yix_sorted = !buckets;
   c->yix_ready = true;
   c->yix_build_ms = ms;
   c->serve_ready = false;  // the serving arena is sized again around the index
   return ARA_OK;
 }
 
-int ara_yet_index_info(const ara_ctx* c, int32_t* built, int64_t* bytes, float* build_ms) {
+int ara_yet_index_info(const ara_ctx* c, int32_t* built, int64_t* bytes, float* build_ms, int32_t* method) {
   if (!c) return ARA_EINVAL;
   if (built) *built = c->yix_ready ? 1 : 0;
+  if (method) *method = c->yix_ready ? (c->yix_sorted ? 1 : 0) : -1;
   if (bytes) *bytes = c->yix_ready ? static_cast<int64_t>(c->yix_occ.bytes + c->yix_grid.bytes) : 0;
   if (build_ms) *build_ms = c->yix_ready ? c->yix_build_ms : 0.0f;
   return ARA_OK;

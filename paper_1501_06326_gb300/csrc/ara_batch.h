@@ -26,6 +26,21 @@ cudaError_t sort_pairs_ascending(unsigned long long* keys, int64_t* vals, int64_
 // cells = yet_grid_cells(n_trials, grid_shift).  n_events < 2^32.  `scratch`
 // holds yet_index_scratch_bytes(n_events, catalogue).
 int64_t yet_grid_cells(int64_t n_trials, int grid_shift);
+// The bucket build.  yet_index_count counts each (event, grid cell)'s
+// occurrences and scans the counts into ev_grid; the largest count is left in
+// device memory at yet_index_max_bucket(scratch, ...).  yet_index_fill then
+// places each occurrence in its bucket (an atomic slot claim) and sorts each
+// bucket by one thread's insertion sort: fast while buckets are small.
+// `scratch` holds yet_bucket_scratch_bytes(catalogue, cells) for both.
+size_t yet_bucket_scratch_bytes(int32_t catalogue, int64_t cells);
+cudaError_t yet_index_count(const int64_t* off, const int32_t* ids, int64_t n_trials, int32_t catalogue, int grid_shift,
+                            uint32_t* ev_grid, void* scratch, cudaStream_t s, int* n_launch);
+const uint32_t* yet_index_max_bucket(const void* scratch, int32_t catalogue, int64_t cells);
+cudaError_t yet_index_fill(const int64_t* off, const int32_t* ids, int64_t n_trials, int32_t catalogue, int grid_shift,
+                           const uint32_t* ev_grid, unsigned long long* occ, void* scratch, cudaStream_t s,
+                           int* n_launch);
+// The sort build (any bucket sizes): a stable radix sort of the YET's events
+// by id, then the grid by a binary search per (event, cell).
 size_t yet_index_scratch_bytes(int64_t n_events, int32_t catalogue);
 cudaError_t build_yet_index(const int64_t* off, const int32_t* ids, int64_t n_trials, int64_t n_events,
                             int32_t catalogue, int grid_shift, unsigned long long* occ, uint32_t* ev_grid,

@@ -342,6 +342,29 @@ def test_indexed_pass_across_slices_and_grid_cells(eng):
         check_ylt(out[l], oracle.run_layer(yet, sub, terms, seed=8, trials=np.arange(t0, t1)))
 
 
+def test_yet_index_by_radix_sort_where_an_event_is_frequent(eng):
+    """An event in every trial of a 3,000-trial YET (a bucket of 3,000
+    occurrences, above the bucket build's 2,048) has the index built by the
+    radix sort; the indexed passes give the dense item's bits there, and on
+    the same YET without the frequent event, built by buckets."""
+    pool = synth.make_elt_pool(6, 400, 1500, 72)
+    e_hot = int(pool.event_ids[0])  # an event of ELT 0
+    base = synth.make_yet(3000, 30.0, 1500, 71)
+    lens = np.diff(base.offsets) + 1
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    offsets[1:] = np.cumsum(lens)
+    ev = np.empty(offsets[-1], np.int32)
+    for t in range(base.n_trials):  # the frequent event first in every trial, then the trial's own events
+        ev[offsets[t]] = e_hot
+        ev[offsets[t] + 1: offsets[t + 1]] = base.event_ids[base.offsets[t]: base.offsets[t + 1]]
+    hot = synth.YET(offsets, ev, 1500)
+    layers = [(np.array(ids, np.int32), (10.0, 5e5, 1e2, 5e6), None) for ids in ([0, 1], [1, 2, 3], [0, 4, 5])]
+    for yet, method in ((hot, "radix sort"), (base, "buckets")):
+        for t0, t1 in ((0, yet.n_trials), (17, 2903)):
+            _assert_same_bits(_run_items(eng, yet, pool, layers, 3, t0, t1))
+            assert eng.yet_index_info()["method"] == method
+
+
 def test_batch_config_errors(eng):
     from paper_1501_06326_gb300 import ara
 
@@ -376,7 +399,7 @@ def test_yet_index_default_and_errors(eng, small_batch):
     indexed = _run_batch(eng, yet, pool, layers, 8, index=True)
     assert eng.stats()["batch_item"] == ara.ARA_BATCH_ITEM_INDEXED
     info = eng.yet_index_info()
-    assert info["built"] and info["bytes"] >= 8 * yet.n_events
+    assert info["built"] and info["bytes"] >= 8 * yet.n_events and info["method"] == "buckets"
     assert np.array_equal(dense, indexed)
     eng.load_yet(yet.offsets, yet.event_ids, yet.catalogue_size)
-    assert not eng.yet_index_info()["built"]
+    assert not eng.yet_index_info()["built"] and eng.yet_index_info()["method"] is None
