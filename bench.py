@@ -751,9 +751,10 @@ def _serving_leg(eng, synth, offsets, args):
         s1 = eng.serve_stats()
         lat_ms = 1e3 * np.asarray(lat)
         passes = s1["passes_launched"] - s0["passes_launched"]
+        offered = sum(int(offsets[t_end]) * len(ids) for ids, t_end in reqs) / float(arrivals[-1])
         results.append({"rate_per_s": rate, "requests": len(lat), "p50_ms": float(np.percentile(lat_ms, 50)),
                         "p99_ms": float(np.percentile(lat_ms, 99)), "max_ms": float(lat_ms.max()),
-                        "wall_s": wall, "evals_per_s": evals / wall,
+                        "wall_s": wall, "evals_per_s": evals / wall, "offered_evals_per_s": offered,
                         "rounds": s1["rounds_launched"] - s0["rounds_launched"], "passes": passes,
                         "max_pending": max_pending})
     return {"workload": f"serving: the paper-1m YET, a pool of {spec['n_elts']} ELTs x {spec['entries']:,} records, "
@@ -786,7 +787,7 @@ def main(argv=None):
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-latency sweep")
     ap.add_argument("--no-stress", action="store_true", help="skip the precision-stress layer")
     ap.add_argument("--serve-requests", type=int, default=10_000, help="requests per rate of the serving sweep")
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 800.0, 1600.0, 3200.0],
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 800.0, 1600.0, 3200.0, 4800.0],
                     help="request arrival rates (per second) of the serving sweep")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)  # at least three untimed warm-up steps

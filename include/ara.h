@@ -327,7 +327,7 @@ ARA_API int ara_set_batch_config(ara_ctx *ctx, int32_t item, int32_t blocks_per_
 /* The event-major index of the loaded YET (Section 2.1's lookup taken from the
  * ELT side): for each catalogue event, its occurrences (trial, event index) in
  * trial order, built on the device: each occurrence is counted into and placed
- * in a bucket per (event, 131,072-trial cell), and each bucket sorted; where a
+ * in a bucket per (event, 262,144-trial cell), and each bucket sorted; where a
  * bucket would hold more than 2,048 occurrences, by a stable radix sort of the
  * YET's events by id instead (the same index).  Once built, batched passes (ara_run_layers and the serving loop)
  * default to ARA_BATCH_ITEM_INDEXED, which reaches a pass's hit events through
@@ -335,9 +335,9 @@ ARA_API int ara_set_batch_config(ara_ctx *ctx, int32_t item, int32_t blocks_per_
  * are the same bits as the other work items'.  ara_run_layer (one layer, with
  * its double-float sums and hit diagnostics) keeps streaming the YET.
  * With each event's occurrences the index keeps their offsets at every
- * 131,072 trials (the serving chunk), so that a pass's slices of trials find
+ * 262,144 trials (the serving chunk), so that a pass's slices of trials find
  * their occurrences without a search.  It takes 8 bytes per YET event and
- * 4 * (ceil(n_trials / 131072) + 1) per catalogue id, and lasts until the next
+ * 4 * (ceil(n_trials / 262144) + 1) per catalogue id, and lasts until the next
  * YET load; the bucket build needs 4 bytes per (catalogue id, cell) of
  * scratch besides, the radix sort about 24 bytes per event.  Errors: ARA_ENOTLOADED; ARA_EINVAL (served requests queued or
  * running, or 2^32 or more events); ARA_ENOMEM; ARA_ECUDA.

@@ -19,11 +19,13 @@
 namespace {
 
 // The YET index keeps each event's occurrence offsets at every 2^kYetGridShift trials (the serving
-// chunk). An indexed pass runs in slices of 2^k trials, k >= kYetGridShift, the largest whose sums
-// (8 bytes per layer and trial) fit kIdxSliceBytes, about half of L2: the sums' atomic adds then stay
-// in L2 while the occurrences stream through it (16 layers: 2^19 trials; measured on batched-16,
-// 6.2 ms a pass against 8.1 ms in one slice and 6.6 ms at 2^18).
-constexpr int kYetGridShift = 17;
+// chunk: 262,144 trials measured better than 131,072 on the serving workload, p99 18.6 against 35.8 ms
+// at 3,200 requests/s and 7.0e12 against 6.6e12 evals/s at saturation; 65,536 far worse). An indexed
+// pass runs in slices of 2^k trials, k >= kYetGridShift, the largest whose sums (8 bytes per layer and
+// trial) fit kIdxSliceBytes, about half of L2: the sums' atomic adds then stay in L2 while the
+// occurrences stream through it (16 layers: 2^19 trials; measured on batched-16, 6.2 ms a pass against
+// 8.1 ms in one slice and 6.6 ms at 2^18).
+constexpr int kYetGridShift = 18;
 // The index is built by buckets per (event, grid cell) while no bucket holds more occurrences than this
 // (each bucket is sorted by one thread), else by the radix sort.
 constexpr uint32_t kYetBucketSortMax = 2048;
@@ -1418,7 +1420,7 @@ int ara_get_timing(ara_ctx* c, ara_timing* out, int reset) {
 // rounds are in flight.
 namespace {
 
-constexpr int64_t kServeChunk = 131072;        // trials per chunk
+constexpr int64_t kServeChunk = 262144;        // trials per chunk
 static_assert(kServeChunk == int64_t{1} << kYetGridShift, "served chunks' bounds are the YET index's grid bounds");
 constexpr size_t kServeMaxInFlight = 2;        // rounds launched and not retired
 constexpr int kServePassesPerRound = 16;       // a round's passes under a long backlog

@@ -323,22 +323,24 @@ def test_work_items_on_empty_and_long_trials(eng):
 
 
 def test_indexed_pass_across_slices_and_grid_cells(eng):
-    """A YET of 600,000 trials (five slices of the indexed pass, five cells of
-    the index's trial grid): passes whose bounds are on the grid, inside a cell,
-    inside one cell at both ends, and up to the YET's end; the indexed item gives
-    the dense item's bits on each, and sampled trials match the oracle."""
+    """A YET of 600,000 trials and 32 layers: the indexed pass runs in three
+    slices of 262,144 trials, over three cells of the index's trial grid.
+    Passes whose bounds are on the grid, inside a cell, inside one cell at both
+    ends, and up to the YET's end; the indexed item gives the dense item's bits
+    on each, and sampled trials match the oracle."""
     yet = synth.make_yet(600_000, 4.0, 3000, 61)
     pool = synth.make_elt_pool(8, 1000, 3000, 62)
-    layers = [(np.array(ids, np.int32), (10.0, 5e5, 1e2, 5e6), pool.subset(ids))
-              for ids in ([0, 1, 2], [2, 3], [4, 5, 6, 7], [1, 7])]
-    for t0, t1 in ((0, 600_000), (131_072, 524_288), (70_001, 590_001), (131_073, 131_999),
+    layer_ids = synth.draw_layers(32, pool.elt_ids, 4, 63)
+    layers = [(ids, (10.0, 5e5, 1e2, 5e6), pool.subset([int(i) for i in ids])) for ids in layer_ids]
+    for t0, t1 in ((0, 600_000), (262_144, 524_288), (70_001, 590_001), (262_145, 262_999),
                    (262_143, 600_000), (599_999, 600_000)):
         out = _assert_same_bits(_run_items(eng, yet, pool, layers, 8, t0, t1))
         assert np.count_nonzero(out) > 0
-    # trials on both sides of a grid (and slice) bound, against the oracle
+    # trials on both sides of a grid and slice bound, against the oracle
     t0, t1 = 262_000, 262_300
     out = _assert_same_bits(_run_items(eng, yet, pool, layers, 8, t0, t1))
-    for l, (ids, terms, sub) in enumerate(layers):
+    for l in (0, 11, 31):
+        ids, terms, sub = layers[l]
         check_ylt(out[l], oracle.run_layer(yet, sub, terms, seed=8, trials=np.arange(t0, t1)))
 
 

@@ -50,8 +50,8 @@ def world():
 
 @pytest.fixture(scope="module")
 def long_world():
-    # 600,000 trials x Poisson(20) over 50,000 events: a whole-YET request spans several chunks
-    yet = synth.make_yet(600_000, 20.0, 50_000, 611)
+    # 900,000 trials x Poisson(20) over 50,000 events: a whole-YET request spans several chunks
+    yet = synth.make_yet(900_000, 20.0, 50_000, 611)
     pool = synth.make_elt_pool(6, 3000, 50_000, 612)
     return yet, pool
 
