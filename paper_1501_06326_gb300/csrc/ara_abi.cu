@@ -1421,11 +1421,19 @@ int ara_get_timing(ara_ctx* c, ara_timing* out, int reset) {
 namespace {
 
 constexpr int64_t kServeChunk = 262144;        // trials per chunk
+constexpr size_t kServeSelectPool = size_t{256} << 20;  // scratch of a pass's batched selects, at most
 static_assert(kServeChunk == int64_t{1} << kYetGridShift, "served chunks' bounds are the YET index's grid bounds");
 constexpr size_t kServeMaxInFlight = 2;        // rounds launched and not retired
 constexpr int kServePassesPerRound = 16;       // a round's passes under a long backlog
 constexpr int kServePassesShort = 4;           // ... and under a short one
 constexpr size_t kServeShortBacklog = 128;     // requests with chunks to run, at most, for a short backlog
+
+// The pool of a pass's batched selects: a batch of the largest jobs (a whole-YET prefix and four
+// return periods) within kServeSelectPool, and never less than one of them.
+size_t serve_select_pool_bytes(int64_t n_trials) {
+  const size_t one = ara::select_job_bytes(n_trials, 4);
+  return std::max(one, std::min(kServeSelectPool, one * 32));
+}
 constexpr int32_t kServeSlots = 1024;          // result slots: admitted requests at most
 constexpr int64_t kServeArenaRequests = 96;    // default arena: year losses of this many whole-YET requests
 constexpr size_t kArenaAlign = 256;
@@ -1500,7 +1508,7 @@ std::vector<std::pair<DevBuf*, size_t>> serve_workspace(ara_ctx* c) {
       {&c->pairs_hot, sizeof(ara::PairHot) * (n_recs + 1)},
       {&c->pairs_ev, sizeof(int32_t) * (n_recs + 1)},
       {&c->scan_tmp, sizeof(uint32_t) * (tmp_words + 8)},
-      {&c->serve_sel, ara::select_scratch_bytes(c->n_trials)},
+      {&c->serve_sel, serve_select_pool_bytes(c->n_trials)},
       {&c->u_flags, sizeof(uint32_t) * (n_recs + 1)},
       {&c->u_scan, sizeof(uint32_t) * (n_recs + 1)},
       {&c->u_event, sizeof(int32_t) * (n_recs + 1)},
@@ -1697,30 +1705,34 @@ int serve_launch_round(ara_ctx* c, const char* who, int32_t* n_failed) {
       outs[m] = arena + q.ylt_off / sizeof(double) + t0;
     }
     int rc = run_layers_impl(c, nm, layers.data(), a.seed, t0, t1, nullptr, t_ends.data(), outs.data());
-    bool joined = false;
+    // the requests whose last chunk this pass was: their PML/TVaR over their whole prefixes in one
+    // batched select, then the results to the host, on the side stream once the pass is done (they
+    // overlap the round's later passes)
+    std::vector<ara::SelectSpec> specs;
+    std::vector<int64_t> done;
     for (int32_t m = 0; m < nm && !rc; ++m) {
       ServeReq& q = c->serve_reqs[members[m]];
       if (++q.next_chunk < q.n_chunks) continue;
-      // the request's last chunk: its PML/TVaR over its whole prefix, then the results to the host,
-      // on the side stream once the pass is done (they overlap the round's later passes)
-      cudaError_t e = cudaSuccess;
-      if (!joined) {
-        e = cudaEventRecord(c->serve_join, c->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->serve_side, c->serve_join, 0);
-        joined = true;
-      }
       double* slot = d_out + static_cast<size_t>(q.slot) * 2 * ARA_SERVE_MAX_RP;
+      specs.push_back({arena + q.ylt_off / sizeof(double), q.t_end, q.rps.data(), static_cast<int32_t>(q.rps.size()),
+                       slot, slot + ARA_SERVE_MAX_RP});
+      done.push_back(members[m]);
+    }
+    if (!rc && !specs.empty()) {
+      cudaError_t e = cudaEventRecord(c->serve_join, c->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->serve_side, c->serve_join, 0);
       int launched = 0;
       if (e == cudaSuccess)
-        e = ara::pml_tvar_device(arena + q.ylt_off / sizeof(double), q.t_end, q.rps.data(),
-                                 static_cast<int32_t>(q.rps.size()), slot, slot + ARA_SERVE_MAX_RP, c->serve_sel.ptr,
-                                 c->serve_sel.bytes, c->serve_side, &launched);
+        e = ara::pml_tvar_batch(specs.data(), static_cast<int>(specs.size()), c->serve_sel.ptr, c->serve_sel.bytes,
+                                c->serve_side, &launched);
       c->launches += launched;
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->serve_host + static_cast<size_t>(q.slot) * 2 * ARA_SERVE_MAX_RP, slot,
+      for (size_t k = 0; k < done.size() && e == cudaSuccess; ++k) {
+        const ServeReq& q = c->serve_reqs[done[k]];
+        e = cudaMemcpyAsync(c->serve_host + static_cast<size_t>(q.slot) * 2 * ARA_SERVE_MAX_RP, specs[k].pml,
                             2 * sizeof(double) * ARA_SERVE_MAX_RP, cudaMemcpyDeviceToHost, c->serve_side);
+      }
       if (e != cudaSuccess) rc = fail(c, ARA_ECUDA, "%s: %s", who, cudaGetErrorString(e));
-      else round.finishing.push_back(members[m]);
+      else round.finishing.insert(round.finishing.end(), done.begin(), done.end());
     }
     if (rc) {
       // the pass's requests end with its error; the others of the round go on

@@ -17,6 +17,26 @@ size_t sort_pairs_scratch_bytes(int64_t n);
 cudaError_t sort_pairs_ascending(unsigned long long* keys, int64_t* vals, int64_t n, int key_bits, void* scratch,
                                  cudaStream_t s, int* n_launch);
 
+// --------------------------------------------------------------- batched PML/TVaR
+// Several YLTs' PML/TVaR in one set of five launches per batch of up to 32
+// jobs (a YLT and a group of up to four return periods), each job with its own
+// grid and scratch, so that it gives the bits pml_tvar_device gives on its YLT.
+// rps: host arrays, read during the call; pml/tvar: device arrays of n_rp.
+// pool: the jobs' scratch, at least select_job_bytes(n, n_rp) for each YLT;
+// jobs that do not fit together go in later batches that reuse the pool in
+// stream order.  n >= 1 and 1 <= n_rp, else cudaErrorInvalidValue.
+struct SelectSpec {
+  const double* ylt;
+  int64_t n;
+  const double* rps;
+  int32_t n_rp;
+  double* pml;
+  double* tvar;
+};
+size_t select_job_bytes(int64_t n, int n_rp);
+cudaError_t pml_tvar_batch(const SelectSpec* specs, int n_specs, void* pool, size_t pool_bytes, cudaStream_t s,
+                           int* n_launch);
+
 // --------------------------------------------------------------- event-major YET index
 // occ[i] = (trial << 32) | event index, grouped by event id and in trial order
 // within an event.  ev_grid[e * (cells + 1) + k], k = 0..cells, is the first

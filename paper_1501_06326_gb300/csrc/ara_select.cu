@@ -29,6 +29,7 @@ constexpr int kSelBlocks = 152;  // fixed grid: deterministic reduction order
 constexpr int kSelThreads = 1024;
 constexpr int kSelUnroll = 4;  // loads in flight per thread
 constexpr int kSelGroup = 4;     // return periods selected together (one pass over the YLT serves all)
+constexpr int kSelBatchMax = 32;  // jobs of one batched select
 
 __device__ __forceinline__ unsigned long long key_of(double v) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
@@ -72,7 +73,7 @@ struct SelFast {
 constexpr size_t kSelStateBytes = (sizeof(SelScratch) + 255) & ~size_t(255);
 constexpr size_t kSelFastBytes = (sizeof(SelFast) + 255) & ~size_t(255);
 
-__global__ void k_sel_init(SelScratch* sc, SelMs ms, int g) {
+__device__ __forceinline__ void sel_init(SelScratch* sc, const SelMs& ms, int g) {
   if (threadIdx.x < g) {
     SelState& st = sc->st[threadIdx.x];
     st.prefix = 0;
@@ -85,13 +86,15 @@ __global__ void k_sel_init(SelScratch* sc, SelMs ms, int g) {
   if (threadIdx.x == 0) sc->done = 0;
 }
 
+__global__ void k_sel_init(SelScratch* sc, SelMs ms, int g) { sel_init(sc, ms, g); }
+
 // True in the block that is the last of the grid to arrive (after each block
 // published its part with a fence); that block then sees every part.
-__device__ __forceinline__ bool last_block_arrives(SelScratch* sc) {
+__device__ __forceinline__ bool last_block_arrives(SelScratch* sc, int n_blocks) {
   __shared__ bool s_last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(&sc->done, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) s_last = (atomicAdd(&sc->done, 1u) == static_cast<unsigned int>(n_blocks) - 1u);
   __syncthreads();
   if (s_last) __threadfence();
   return s_last;
@@ -101,8 +104,10 @@ __device__ __forceinline__ bool last_block_arrives(SelScratch* sc) {
 // the digit among the keys that match each period's prefix (warp-aggregated
 // shared-memory counts, then one global add per digit and block); the last
 // block to finish picks each period's digit and clears the histogram.
-// blk_hist (or NULL): each block also stores its own counts there.
-__global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, int shift, unsigned int* blk_hist) {
+// blk_hist (or NULL): each block also stores its own counts there.  The
+// select's grid is nb blocks; this is block bx.
+__device__ __forceinline__ void sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, int shift,
+                                         unsigned int* blk_hist, int nb, int bx) {
   __shared__ unsigned int sh[kSelGroup][256];
   for (int i = threadIdx.x; i < kSelGroup * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
   unsigned long long prefix[kSelGroup], mask[kSelGroup];
@@ -112,12 +117,12 @@ __global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, 
     mask[r] = r < g ? sc->st[r].mask : 0ull;
   }
   __syncthreads();
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t stride = static_cast<int64_t>(nb) * blockDim.x;
   bool nan = false;
   // whole warps take part in every round (the match below needs all lanes)
   const int64_t span = stride * kSelUnroll;
   const int64_t n_round = ((n + span - 1) / span) * span;
-  for (int64_t i0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i0 < n_round; i0 += span) {
+  for (int64_t i0 = bx * static_cast<int64_t>(blockDim.x) + threadIdx.x; i0 < n_round; i0 += span) {
     double v[kSelUnroll];
 #pragma unroll
     for (int u = 0; u < kSelUnroll; ++u) {
@@ -151,9 +156,9 @@ __global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, 
   for (int i = threadIdx.x; i < g * 256; i += blockDim.x) {
     const unsigned int c = (&sh[0][0])[i];
     if (c) atomicAdd(&(&sc->hist[0][0])[i], c);
-    if (blk_hist) blk_hist[static_cast<size_t>(blockIdx.x) * kSelGroup * 256 + i] = c;
+    if (blk_hist) blk_hist[static_cast<size_t>(bx) * kSelGroup * 256 + i] = c;
   }
-  if (!last_block_arrives(sc)) return;
+  if (!last_block_arrives(sc, nb)) return;
   // ---- pick: per period, the digit holding the wanted rank (a suffix scan of
   // the counts from digit 255 down, thread t holding digit 255 - t)
   __shared__ unsigned int s_warp[kSelThreads / 32];
@@ -184,6 +189,10 @@ __global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, 
   }
   for (int i = threadIdx.x; i < kSelGroup * 256; i += blockDim.x) (&sc->hist[0][0])[i] = 0;
   if (threadIdx.x == 0) sc->done = 0;
+}
+
+__global__ void k_sel_hist(const double* ylt, int64_t n, SelScratch* sc, int g, int shift, unsigned int* blk_hist) {
+  sel_hist(ylt, n, sc, g, shift, blk_hist, static_cast<int>(gridDim.x), static_cast<int>(blockIdx.x));
 }
 
 // Sum and count of the values whose key exceeds each selected key.
@@ -242,7 +251,7 @@ __global__ void k_sel_tail(const double* ylt, int64_t n, SelScratch* sc, int g, 
     sc->part_sum[blockIdx.x][r] = t;
     sc->part_cnt[blockIdx.x][r] = c;
   }
-  if (!last_block_arrives(sc)) return;
+  if (!last_block_arrives(sc, static_cast<int>(gridDim.x))) return;
   // ---- finish (the last block): one thread per part, then a tree of fixed
   // shape over the parts, so the sum is deterministic
   __shared__ double s_ps[kSelBlocks];
@@ -278,9 +287,9 @@ __global__ void k_sel_tail(const double* ylt, int64_t n, SelScratch* sc, int g, 
 // number of bucket keys of the blocks before it (from the second pass's
 // per-block counts); each block also publishes the FP64 sum and the count of
 // its values above the bucket.  Same grid and element assignment as
-// k_sel_hist.
-__global__ void k_sel_compact(const double* ylt, int64_t n, const SelScratch* sc, SelFast* sf, int g,
-                              unsigned long long* cand) {
+// k_sel_hist (a grid of nb blocks; this is block bx).
+__device__ __forceinline__ void sel_compact(const double* ylt, int64_t n, const SelScratch* sc, SelFast* sf, int g,
+                                            unsigned long long* cand, int nb, int bx) {
   __shared__ unsigned int s_wcnt[kSelThreads / 32][kSelGroup];
   __shared__ unsigned int s_off[kSelGroup];
   __shared__ double s_sum[kSelThreads / 32][kSelGroup];
@@ -299,7 +308,7 @@ __global__ void k_sel_compact(const double* ylt, int64_t n, const SelScratch* sc
     unsigned int part[kSelGroup];
 #pragma unroll
     for (int r = 0; r < kSelGroup; ++r) part[r] = 0u;
-    for (unsigned int b = threadIdx.x; b < blockIdx.x; b += blockDim.x) {
+    for (unsigned int b = threadIdx.x; b < static_cast<unsigned int>(bx); b += blockDim.x) {
 #pragma unroll
       for (int r = 0; r < kSelGroup; ++r)
         if (r < g) part[r] += sf->blk_hist[b][r][static_cast<unsigned int>(prefix[r] >> 48) & 255u];
@@ -317,7 +326,7 @@ __global__ void k_sel_compact(const double* ylt, int64_t n, const SelScratch* sc
     }
     __syncthreads();
   }
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t stride = static_cast<int64_t>(nb) * blockDim.x;
   const int64_t span = stride * kSelUnroll;
   const int64_t n_round = ((n + span - 1) / span) * span;
   double sum[kSelGroup];
@@ -327,7 +336,7 @@ __global__ void k_sel_compact(const double* ylt, int64_t n, const SelScratch* sc
     sum[r] = 0.0;
     cnt[r] = 0;
   }
-  for (int64_t i0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i0 < n_round; i0 += span) {
+  for (int64_t i0 = bx * static_cast<int64_t>(blockDim.x) + threadIdx.x; i0 < n_round; i0 += span) {
 #pragma unroll 1
     for (int u = 0; u < kSelUnroll; ++u) {
       const bool in = i0 + u * stride < n;
@@ -393,18 +402,23 @@ __global__ void k_sel_compact(const double* ylt, int64_t n, const SelScratch* sc
       t += s_sum[w][r];
       c += s_cnt[w][r];
     }
-    sf->above_sum[blockIdx.x][r] = t;
-    sf->above_cnt[blockIdx.x][r] = c;
+    sf->above_sum[bx][r] = t;
+    sf->above_cnt[bx][r] = c;
   }
+}
+
+__global__ void k_sel_compact(const double* ylt, int64_t n, const SelScratch* sc, SelFast* sf, int g,
+                              unsigned long long* cand) {
+  sel_compact(ylt, n, sc, sf, g, cand, static_cast<int>(gridDim.x), static_cast<int>(blockIdx.x));
 }
 
 // The fast path's finish, one block per period: the remaining six digits of
 // the m-th key over the bucket's keys, then TVaR from the sums above the
 // bucket (the blocks' parts, a tree of fixed shape) and the bucket keys above
 // the m-th key (a fixed assignment of keys to threads and a fixed tree).
-__global__ void __launch_bounds__(kSelThreads) k_sel_finish(int64_t n, SelScratch* sc, const SelFast* sf, int g,
-                                                             int n_blk, const unsigned long long* cand, double* pml,
-                                                             double* tvar) {
+// Period r's finish (a block).
+__device__ __forceinline__ void sel_finish(int64_t n, SelScratch* sc, const SelFast* sf, int n_blk,
+                                           const unsigned long long* cand, double* pml, double* tvar, int r) {
   __shared__ unsigned int s_hist[256];
   __shared__ unsigned int s_warp[kSelThreads / 32];
   __shared__ unsigned long long s_prefix, s_mask, s_want;
@@ -413,7 +427,6 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_finish(int64_t n, SelScratc
   __shared__ unsigned long long s_pc[256];
   const unsigned int t = threadIdx.x, lane = t & 31;
   {
-    const int r = blockIdx.x;
     if (t == 0) {
       s_prefix = sc->st[r].prefix;
       s_mask = sc->st[r].mask;
@@ -513,7 +526,133 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_finish(int64_t n, SelScratc
   }
 }
 
+__global__ void __launch_bounds__(kSelThreads) k_sel_finish(int64_t n, SelScratch* sc, const SelFast* sf, int n_blk,
+                                                             const unsigned long long* cand, double* pml,
+                                                             double* tvar) {
+  sel_finish(n, sc, sf, n_blk, cand, pml, tvar, static_cast<int>(blockIdx.x));
+}
+
+// ---- batched selects: one launch per pass for several YLTs (jobs), blockIdx.y
+// the job; each job runs on its own grid size and scratch exactly as the
+// single select does, so it gives the same bits
+struct SelJob {
+  const double* ylt;
+  int64_t n;
+  SelScratch* sc;
+  SelFast* sf;
+  unsigned long long* cand;  // [g][n]
+  double* pml;
+  double* tvar;
+  SelMs ms;
+  int g;
+  int grid;
+};
+struct SelBatch {
+  SelJob job[kSelBatchMax];
+};
+
+__global__ void k_sel_init_batch(const __grid_constant__ SelBatch b) {
+  const SelJob& j = b.job[blockIdx.y];
+  sel_init(j.sc, j.ms, j.g);
+}
+
+__global__ void k_sel_hist_batch(const __grid_constant__ SelBatch b, int shift, int with_blk) {
+  const SelJob& j = b.job[blockIdx.y];
+  if (static_cast<int>(blockIdx.x) >= j.grid) return;
+  sel_hist(j.ylt, j.n, j.sc, j.g, shift, with_blk ? &j.sf->blk_hist[0][0][0] : nullptr, j.grid,
+           static_cast<int>(blockIdx.x));
+}
+
+__global__ void k_sel_compact_batch(const __grid_constant__ SelBatch b) {
+  const SelJob& j = b.job[blockIdx.y];
+  if (static_cast<int>(blockIdx.x) >= j.grid) return;
+  sel_compact(j.ylt, j.n, j.sc, j.sf, j.g, j.cand, j.grid, static_cast<int>(blockIdx.x));
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_finish_batch(const __grid_constant__ SelBatch b) {
+  const SelJob& j = b.job[blockIdx.y];
+  if (static_cast<int>(blockIdx.x) >= j.g) return;
+  sel_finish(j.n, j.sc, j.sf, j.grid, j.cand, j.pml, j.tvar, static_cast<int>(blockIdx.x));
+}
+
+int sel_grid(int64_t n) {
+  const int64_t blocks = (n + kSelThreads - 1) / kSelThreads;
+  return static_cast<int>(blocks < kSelBlocks ? blocks : kSelBlocks);
+}
+
+// m = ceil(n / rp), within [1, n]
+unsigned long long sel_rank(int64_t n, double rp) {
+  int64_t m = static_cast<int64_t>(std::ceil(static_cast<double>(n) / rp));
+  if (m < 1) m = 1;
+  if (m > n) m = n;
+  return static_cast<unsigned long long>(m);
+}
+
+cudaError_t launch_sel_batch(const SelBatch& b, int n_jobs, int max_grid, int max_g, cudaStream_t s) {
+  const dim3 one(1, n_jobs), wide(max_grid, n_jobs), fin(max_g, n_jobs);
+  k_sel_init_batch<<<one, 256, 0, s>>>(b);
+  k_sel_hist_batch<<<wide, kSelThreads, 0, s>>>(b, 56, 0);
+  k_sel_hist_batch<<<wide, kSelThreads, 0, s>>>(b, 48, 1);
+  k_sel_compact_batch<<<wide, kSelThreads, 0, s>>>(b);
+  k_sel_finish_batch<<<fin, kSelThreads, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t select_job_bytes(int64_t n, int n_rp) {
+  const int g = n_rp < kSelGroup ? n_rp : kSelGroup;
+  const int groups = (n_rp + kSelGroup - 1) / kSelGroup;
+  return static_cast<size_t>(groups) * (kSelStateBytes + kSelFastBytes +
+                                        ((sizeof(unsigned long long) * g * static_cast<size_t>(n) + 255) & ~size_t(255)));
+}
+
+cudaError_t pml_tvar_batch(const SelectSpec* specs, int n_specs, void* pool, size_t pool_bytes, cudaStream_t s,
+                           int* n_launch) {
+  SelBatch b;
+  int n_jobs = 0, max_grid = 1, max_g = 1;
+  size_t used = 0;
+  unsigned char* base = static_cast<unsigned char*>(pool);
+  auto flush = [&]() -> cudaError_t {
+    if (n_jobs == 0) return cudaSuccess;
+    const cudaError_t e = launch_sel_batch(b, n_jobs, max_grid, max_g, s);
+    if (n_launch) *n_launch += 5;
+    n_jobs = 0;
+    max_grid = max_g = 1;
+    used = 0;
+    return e;
+  };
+  for (int i = 0; i < n_specs; ++i) {
+    const SelectSpec& q = specs[i];
+    if (q.n < 1 || q.n_rp < 1) return cudaErrorInvalidValue;
+    for (int r0 = 0; r0 < q.n_rp; r0 += kSelGroup) {
+      const int g = (q.n_rp - r0 < kSelGroup) ? (q.n_rp - r0) : kSelGroup;
+      const size_t need = kSelStateBytes + kSelFastBytes +
+                          ((sizeof(unsigned long long) * g * static_cast<size_t>(q.n) + 255) & ~size_t(255));
+      if (need > pool_bytes) return cudaErrorInvalidValue;
+      if (n_jobs == kSelBatchMax || used + need > pool_bytes) {
+        const cudaError_t e = flush();
+        if (e != cudaSuccess) return e;
+      }
+      SelJob& j = b.job[n_jobs++];
+      j.ylt = q.ylt;
+      j.n = q.n;
+      j.sc = reinterpret_cast<SelScratch*>(base + used);
+      j.sf = reinterpret_cast<SelFast*>(base + used + kSelStateBytes);
+      j.cand = reinterpret_cast<unsigned long long*>(base + used + kSelStateBytes + kSelFastBytes);
+      j.pml = q.pml + r0;
+      j.tvar = q.tvar + r0;
+      j.ms = SelMs{};
+      for (int r = 0; r < g; ++r) j.ms.m[r] = sel_rank(q.n, q.rps[r0 + r]);
+      j.g = g;
+      j.grid = sel_grid(q.n);
+      max_grid = j.grid > max_grid ? j.grid : max_grid;
+      max_g = g > max_g ? g : max_g;
+      used += need;
+    }
+  }
+  return flush();
+}
 
 size_t select_scratch_bytes(int64_t n) {
   return kSelStateBytes + kSelFastBytes + sizeof(unsigned long long) * kSelGroup * static_cast<size_t>(n) + 64;
@@ -527,23 +666,17 @@ cudaError_t pml_tvar_device(const double* ylt, int64_t n, const double* rps_host
   unsigned long long* cand =
       fast ? reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(scratch) + kSelStateBytes + kSelFastBytes)
            : nullptr;
-  const int64_t blocks = (n + kSelThreads - 1) / kSelThreads;
-  const int grid = static_cast<int>(blocks < kSelBlocks ? blocks : kSelBlocks);
+  const int grid = sel_grid(n);
   for (int32_t r0 = 0; r0 < n_rp; r0 += kSelGroup) {
     const int g = (n_rp - r0 < kSelGroup) ? (n_rp - r0) : kSelGroup;
     SelMs ms{};
-    for (int r = 0; r < g; ++r) {
-      int64_t m = static_cast<int64_t>(std::ceil(static_cast<double>(n) / rps_host[r0 + r]));
-      if (m < 1) m = 1;
-      if (m > n) m = n;
-      ms.m[r] = static_cast<unsigned long long>(m);
-    }
+    for (int r = 0; r < g; ++r) ms.m[r] = sel_rank(n, rps_host[r0 + r]);
     k_sel_init<<<1, 256, 0, s>>>(sc, ms, g);
     if (fast) {
       k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, 56, nullptr);
       k_sel_hist<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, g, 48, &sf->blk_hist[0][0][0]);
       k_sel_compact<<<grid, kSelThreads, 0, s>>>(ylt, n, sc, sf, g, cand);
-      k_sel_finish<<<g, kSelThreads, 0, s>>>(n, sc, sf, g, grid, cand, pml + r0, tvar + r0);
+      k_sel_finish<<<g, kSelThreads, 0, s>>>(n, sc, sf, grid, cand, pml + r0, tvar + r0);
       if (n_launch) *n_launch += 5;
     } else {
       for (int shift = 56; shift >= 0; shift -= 8)

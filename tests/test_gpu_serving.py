@@ -88,6 +88,27 @@ def test_results_identical_alone_and_in_a_mix(eng, world):
         assert np.array_equal(alone[0][0], res[0]) and np.array_equal(alone[0][1], res[1])
 
 
+def test_batched_selects_give_the_selects_bits(eng, world):
+    """The requests that a pass finishes get their PML/TVaR from one batched
+    select.  40 requests at once (passes of 32 and 8) with 1, 2, 5 or 16 return
+    periods (one to four groups of periods each, so that a pass's selects span
+    two batches); each result equals ara_pml_tvar over the request's year losses
+    from ara_run_layers, bit for bit."""
+    yet, pool, reqs = world
+    _load(eng, yet, pool)
+    rp_sets = [(10.0,), (10.0, 40.0), (2.0, 5.0, 10.0, 40.0, 100.0), tuple(np.geomspace(1.0, 900.0, 16))]
+    subs = [(*reqs[i % len(reqs)][:3], rp_sets[i % 4]) for i in range(40)]
+    s0 = eng.serve_stats()
+    tks = [eng.submit(ids, terms, 13, t_end, rps) for ids, terms, t_end, rps in subs]
+    got = [eng.wait(tk, len(rps)) for tk, (_, _, _, rps) in zip(tks, subs)]
+    assert eng.serve_stats()["passes_launched"] - s0["passes_launched"] == 2
+    for (ids, terms, t_end, rps), res in zip(subs, got):
+        ylt = np.zeros((1, t_end))
+        eng.run_layers([(ids, terms)], 13, 0, t_end, ylt)
+        pml, tvar = eng.pml_tvar(ylt[0], rps)
+        assert np.array_equal(pml, res[0]) and np.array_equal(tvar, res[1])
+
+
 def test_a_short_request_overtakes_a_long_one_in_flight(eng, long_world):
     """A whole-YET request is launched; a 10,000-trial request submitted while its
     first round is on the device joins the next round and finishes first.  Both
