@@ -1019,6 +1019,10 @@ __global__ void __launch_bounds__(kIdxThreads, kIdxBlocksPerSm)
   const uint32_t n_u = *q.n_u;
   unsigned long long nc = 0ull;
   uint32_t n_pairs = 0;
+  // the occurrences (read once) are the first to leave L2, so that the trials' sums, which the atomic
+  // adds revisit, stay (batched-16: 5.98 against 6.07 ms a pass)
+  uint64_t occ_pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(occ_pol));
 
   // the queue's groups: kIdxClaim events over one trial slice, every event of a slice before the next
   // slice, so that the sums being added to stay within a slice's trials; a warp moves to the next slice
@@ -1074,7 +1078,9 @@ __global__ void __launch_bounds__(kIdxThreads, kIdxBlocksPerSm)
       for (uint32_t r = lo; r < hi; r += 32) {
         const uint32_t i = r + lane;
         const bool valid = i < hi;
-        const unsigned long long o = valid ? __ldg(q.occ + i) : 0ull;
+        unsigned long long o = 0ull;
+        if (valid)
+          asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(o) : "l"(q.occ + i), "l"(occ_pol));
         const int64_t trial = static_cast<int64_t>(o >> 32);
         const uint32_t k = static_cast<uint32_t>(o);
         uint32_t act = 0u;  // the layers whose trials reach this one
