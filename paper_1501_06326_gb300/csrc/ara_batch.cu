@@ -1080,7 +1080,9 @@ __global__ void __launch_bounds__(kIdxThreads, kIdxBlocksPerSm)
         const bool valid = i < hi;
         unsigned long long o = 0ull;
         if (valid)
-          asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(o) : "l"(q.occ + i), "l"(occ_pol));
+          asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;"
+                       : "=l"(o)
+                       : "l"(q.occ + i), "l"(occ_pol));
         const int64_t trial = static_cast<int64_t>(o >> 32);
         const uint32_t k = static_cast<uint32_t>(o);
         uint32_t act = 0u;  // the layers whose trials reach this one
